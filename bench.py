@@ -1,0 +1,381 @@
+"""Monte-Carlo beamforming throughput on GB300.
+
+One step = the whole hot path over one batch of trials of the headline
+workload (100 GHz ULA, N = 16384 elements, K = 32 users at r in [3, 30] m,
+theta in [-60, 60] deg, free-space spherical-wave channel, MMSE at 10 dB
+per-user received SNR with FP64 Cholesky, 10^4 trials):
+  exact Gram (generated channel, no HBM channel matrix) -> MMSE SINR and
+  capacity -> sum rate; closed-form Gram -> modified ZF judged on the exact
+  channel -> sum rate; per-trial saturation interval.
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2503_18118_gb300 import inputs  # noqa: E402
+
+PATHS = {"f64": 0, "f32": 1, "bf16x3": 3}
+KERNEL_OF_PATH = {"f64": "gram_f64_kernel", "f32": "gram_f32_kernel", "bf16x3": "gram_tc_kernel"}
+SRC_OF_PATH = {"f64": "gram_simt.cu", "f32": "gram_simt.cu", "bf16x3": "gram_tc.cu"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--path", default="auto", choices=["auto", "f64", "f32", "bf16x3"])
+    ap.add_argument("--trials", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------- oracle (CPU) -----
+def oracle_pipeline(oracle, wl, users):
+    """The same per-trial work as one GPU step, on the CPU oracle."""
+    B = users.shape[0]
+    G = oracle.gram(wl.model, wl.n_ant, wl.wavelength, wl.spacing, 1.0, users)
+    s, _, cap = oracle.beamform(G, wl.power(B), wl.noise(B), oracle.MMSE, oracle.POWER_RXSNR, want_capacity=True)
+    r, _ = oracle.sumrate(s)
+    Gc = oracle.closed_form(wl.model, wl.n_ant, wl.wavelength, wl.spacing, 1.0, users)
+    sm, _, _ = oracle.beamform(Gc, wl.power(B), wl.noise(B), oracle.ZF, oracle.POWER_RXSNR, gram_true=G)
+    oracle.sumrate(sm)
+    oracle.saturation(users, 0.9, wl.spacing)
+    return r, cap
+
+
+def cpu_trials_per_s(oracle, wl, budget_s=12.0, max_trials=4096):
+    """Oracle timed on a bounded sample: calibrate on 16 trials, then run a
+    sample sized to about budget_s seconds."""
+    users = wl.users(max_trials)
+    t0 = time.perf_counter()
+    oracle_pipeline(oracle, wl, users[:16])
+    t16 = time.perf_counter() - t0
+    n = int(min(max_trials, max(16, budget_s / max(t16 / 16, 1e-9))))
+    t0 = time.perf_counter()
+    oracle_pipeline(oracle, wl, users[:n])
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt
+
+
+def reference_arm(args, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    users = wl.users(4096)
+    # each step is a bounded sample of the workload, sized from a calibration run
+    t0 = time.perf_counter()
+    oracle_pipeline(oracle, wl, users[:16])
+    per = (time.perf_counter() - t0) / 16
+    total_budget = 90.0
+    n = int(max(8, min(4096, total_budget / max(args.steps + args.warmup, 1) / max(per, 1e-9))))
+    for _ in range(args.warmup):
+        oracle_pipeline(oracle, wl, users[:n])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_pipeline(oracle, wl, users[:n])
+    dt = time.perf_counter() - t0
+    v = args.steps * n / dt
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": "mc_beamforming_trials_per_s", "value": v, "unit": "trials/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "n_ant": wl.n_ant, "users": wl.k, "trials_per_step": n,
+                   "freq_ghz": wl.freq_hz / 1e9, "scheme": "mmse+modified_zf"},
+        "cpu_baseline": {"value": v, "unit": "trials/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{n} trials of the workload per step, {args.steps} steps"},
+        "e2e": {"value": v, "unit": "trials/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ GPU arm -------
+def traffic_from_profile(path_name):
+    """DRAM bytes per launch recorded by the committed ncu summary of the
+    dominant kernel, valid only while the kernel source is unchanged."""
+    prof = os.path.join(ROOT, "profiles", f"{KERNEL_OF_PATH[path_name]}_headline.md")
+    src = os.path.join(ROOT, "paper_2503_18118_gb300", "csrc", SRC_OF_PATH[path_name])
+    if not os.path.exists(prof):
+        return None
+    text = open(prof).read()
+    m = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m or not t:
+        return None
+    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    deps = [os.path.join(ROOT, "paper_2503_18118_gb300", "csrc", f) for f in ("chan_gen.cuh", "common.cuh")]
+    for d in deps:
+        if os.path.exists(d):
+            cur = hashlib.sha256((cur + hashlib.sha256(open(d, "rb").read()).hexdigest()).encode()).hexdigest()
+    return float(t.group(1)) if m.group(1) == cur else None
+
+
+def main():
+    args = parse()
+    wl = inputs.HEADLINE
+    if args.trials:
+        wl.trials = args.trials
+    if args.impl == "reference":
+        reference_arm(args, wl)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2503_18118_gb300 import xlmimo as xl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    path = args.path
+    if path == "auto":
+        path = "f32"
+    prec = PATHS[path]
+
+    B, K, N = wl.trials, wl.k, wl.n_ant
+    # weak scaling: rank r takes its own block of trials (different seed stream)
+    users_h = inputs.users_polar(wl.seed + 1000 * rank, B, K, wl.r_range, wl.theta_deg)
+    arr = xl.array(N, wl.wavelength, wl.spacing, 1.0, wl.model)
+    stream = torch.cuda.current_stream()
+    U = torch.from_numpy(users_h).cuda()
+    snr = torch.from_numpy(wl.power()).cuda()
+    noise = torch.from_numpy(wl.noise()).cuda()
+    G = torch.empty((B, K, K), dtype=torch.complex128, device="cuda")
+    Gc = torch.empty_like(G)
+    sinr = torch.empty((B, K), dtype=torch.float64, device="cuda")
+    sinr2 = torch.empty_like(sinr)
+    status = torch.empty((B,), dtype=torch.int32, device="cuda")
+    cap = torch.empty((B,), dtype=torch.float64, device="cuda")
+    rate = torch.empty((B,), dtype=torch.float64, device="cuda")
+    rate2 = torch.empty_like(rate)
+    stats = torch.empty((3,), dtype=torch.float64, device="cuda")
+    stats2 = torch.empty_like(stats)
+    sat = torch.empty((B, 3), dtype=torch.float64, device="cuda")
+    flush = torch.empty((64 << 20,), dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def step(gram_prec, ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        xl.xlmimo_channel_gram(arr, U, gram_prec, G)
+        if ev is not None:
+            ev[1].record(stream)
+        xl.xlmimo_beamform(G, snr, noise, xl.MMSE, xl.POWER_RXSNR, capacity=True, sinr=sinr, status=status, cap=cap)
+        xl.xlmimo_sumrate(sinr, rate, stats)
+        xl.xlmimo_corr_closed_form(arr, U, Gc)
+        xl.xlmimo_beamform(Gc, snr, noise, xl.ZF, xl.POWER_RXSNR, gram_true=G, sinr=sinr2, status=status)
+        xl.xlmimo_sumrate(sinr2, rate2, stats2)
+        xl.xlmimo_saturation(U, 0.9, wl.spacing, sat)
+
+    launches_per_step = 1 + 1 + 2 + 1 + 1 + 2 + 1  # gram, beamform, sumrate+stats, closed, beamform, sumrate+stats, sat
+
+    def timed(gram_prec, steps, warmup, sample_clocks=False):
+        for _ in range(warmup):
+            step(gram_prec)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local) if sample_clocks else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+                torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.zero_()
+            evs[i][0].record(stream)
+            step(gram_prec, (evs[i][2], evs[i][3]))
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        total_ms = sum(e[0].elapsed_time(e[1]) for e in evs)
+        gram_ms = sum(e[2].elapsed_time(e[3]) for e in evs) / steps
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item()), gram_ms, clocks
+
+    total_ms, gram_ms, clocks = timed(prec, args.steps, args.warmup, sample_clocks=(rank == 0))
+    ms_per_step = total_ms / args.steps
+    value = world * B * args.steps / (total_ms / 1e3)
+
+    # plain FP64 GPU path (the metric's baseline), same pipeline, fewer steps
+    fp64 = None
+    if not args.no_fp64_baseline and path != "f64":
+        t64, g64, _ = timed(PATHS["f64"], 2, 1)
+        fp64 = {"trials_per_s": world * B * 2 / (t64 / 1e3), "gram_ms": g64, "ms_per_step": t64 / 2}
+
+    # end to end through the C ABI from pinned host buffers: inputs H2D, result D2H
+    users_pin = torch.from_numpy(users_h).pin_memory()
+    rate_pin = torch.empty((B,), dtype=torch.float64).pin_memory()
+    stats_pin = torch.empty((3,), dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        U.copy_(users_pin, non_blocking=True)
+        step(prec)
+        rate_pin.copy_(rate, non_blocking=True)
+        stats_pin.copy_(stats, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 5))
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        U.copy_(users_pin, non_blocking=True)
+        step(prec)
+        rate_pin.copy_(rate, non_blocking=True)
+        stats_pin.copy_(stats, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * B / (float(te.item()) / 1e3)
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # accuracy on sampled trials against the oracle (outside the timed region)
+    import oracle
+    oracle.build()
+    idx = np.array([0, 1, B // 2, B - 1])
+    step(prec)
+    torch.cuda.synchronize()
+    r_ref, _ = oracle_pipeline(oracle, wl, users_h[idx])
+    r_gpu = rate.cpu().numpy()[idx]
+    sumrate_rel_err = float(np.max(np.abs(r_gpu - r_ref) / np.abs(r_ref)))
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    # FP32 pipe peak from unit counts and clock: SMs x 128 FMA lanes x 2 flop x max SM clock
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = sms * 128 * 2 * max_mhz * 1e6 / 1e12
+    gram_flops = 8.0 * N * K * (K + 1) / 2 * B  # complex MACs of the Hermitian half, 8 flop each
+    achieved = gram_flops / (gram_ms / 1e3) / 1e12
+    if path == "f64":
+        peak_v, peak_kind = 1.25, "nominal FP64 (no measured FP64 peak)"
+    else:
+        peak_v, peak_kind = fp32_peak, f"FP32 FMA pipe: {sms} SMs x 128 lanes x 2 flop x {max_mhz:.0f} MHz"
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_v, "unit": "TFLOP/s", "frac": achieved / peak_v,
+            "traffic": traffic_from_profile(path), "kernel": KERNEL_OF_PATH[path],
+            "kernel_ms": gram_ms, "peak_source": peak_kind,
+            "algorithmic": "8 flop x N K (K+1)/2 complex MACs per trial x trials per launch"}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, n, dt = cpu_trials_per_s(oracle, wl)
+        cpu = {"value": v, "unit": "trials/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"{n} trials of the workload ({dt:.1f} s), OpenMP over trials"}
+
+    line = {
+        "metric": "mc_beamforming_trials_per_s", "value": value, "unit": "trials/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": path, "data": "synthetic",
+        "config": {"workload": wl.name, "n_ant": N, "users": K, "trials_per_step": B, "freq_ghz": wl.freq_hz / 1e9,
+                   "scheme": "mmse+modified_zf", "gram_path": path, "solve": "f64 cholesky",
+                   "l2": "flushed between timed steps (256 MB write)"},
+        "sumrate_rel_err": sumrate_rel_err,
+        "fp64_baseline": fp64,
+        "speedup_vs_fp64_gpu": (value / fp64["trials_per_s"]) if fp64 else None,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "trials/s", "h2d_bytes_per_step": int(users_h.nbytes),
+                "d2h_bytes_per_step": int(rate_pin.numel() * 8 + 24)},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

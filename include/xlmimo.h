@@ -1,0 +1,223 @@
+/*
+ * xlmimo.h -- C interface of the GB300 (sm_103a) Monte-Carlo engine for
+ * near-field XL-MIMO multiuser beamforming (Cui, Park, Alouini, "Channel
+ * Capacity Saturation Point and Beamforming Acceleration for Near-Field
+ * XL-MIMO Multiuser Communications").
+ *
+ * Problem statement (Sec. II): an uplink with one base station whose
+ * uniform linear array of N elements lies on the y axis, centred at the
+ * origin, element n = 0..N-1 at y_n = (n - (N-1)/2) * spacing (Sec. II-A);
+ * K single-antenna users at (x_k, y_k), x_k > 0; carrier wavelength lambda;
+ * transmit power p_k per user (E[x x^H] = P I in Eq. 1, generalised to
+ * diag(p)); white noise of power sigma^2 per element (Eq. 1).
+ *
+ * Conventions for every call:
+ *   - All array arguments are DEVICE pointers owned by the caller unless a
+ *     comment says "host".  The library never frees caller memory.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t; NULL = the
+ *     legacy default stream) and makes no implicit device synchronisation,
+ *     except those documented as synchronous.
+ *   - Returns an xlmimo_status.  XLMIMO_EINVAL is returned before any work is
+ *     enqueued; the reason is in xlmimo_last_error() (thread-local).
+ *     XLMIMO_ECUDA reports a CUDA launch or runtime error.  No C++ exception
+ *     crosses this interface.
+ *   - B == 0 is a valid empty batch: nothing is enqueued, XLMIMO_OK.
+ *   - Complex numbers are interleaved (re, im) doubles.  A Gram matrix batch
+ *     is [B][K][K] complex, row-major, G[b][i][j] = h_i^H h_j (conjugate on
+ *     the row user, as rho_ij of Sec. III), both triangles written.
+ *   - User positions are [B][K][2] doubles (x, y) in metres.  A trial with a
+ *     user at x <= 0 or a non-finite coordinate gets a NaN Gram matrix.
+ *   - K is limited to 1..XLMIMO_MAX_USERS.
+ */
+#ifndef XLMIMO_H
+#define XLMIMO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define XLMIMO_MAX_USERS 64
+
+typedef enum {
+    XLMIMO_OK = 0,
+    XLMIMO_EINVAL = 1,       /* bad argument; nothing enqueued */
+    XLMIMO_ECUDA = 2,        /* CUDA runtime or launch error */
+    XLMIMO_ENOMEM = 3,       /* device workspace allocation failed */
+    XLMIMO_ESINGULAR = 4,    /* per-trial status: receiver matrix singular */
+    XLMIMO_ETIMEOUT = 5,     /* a bounded device-side wait gave up */
+    XLMIMO_EUNSUPPORTED = 6  /* valid request this build or device cannot serve */
+} xlmimo_status;
+
+/* Channel models.
+ *   XLMIMO_PNUSW    Eq. (3): h_k(n) = sqrt(beta0) e^{-j 2 pi r/lambda} / r * sqrt(x_k / r)
+ *   XLMIMO_FSPL_USW free-space spherical wave: h_k(n) = lambda / (4 pi r) e^{-j 2 pi r/lambda}
+ *   XLMIMO_UPW      planar wave (the far-field model compared in Sec. V-A):
+ *                   h_k(n) = sqrt(beta0) / r_k e^{-j 2 pi (r_k - y_n sin theta_k) / lambda}
+ *   with r = sqrt(x_k^2 + (y_n - y_k)^2), r_k = sqrt(x_k^2 + y_k^2),
+ *   sin theta_k = y_k / r_k. */
+typedef enum { XLMIMO_PNUSW = 0, XLMIMO_FSPL_USW = 1, XLMIMO_UPW = 2 } xlmimo_model;
+
+/* Arithmetic of the exact Gram accumulation.
+ *   XLMIMO_F64    FP64 generation and FP64 accumulation (SIMT).
+ *   XLMIMO_F32    FP32 generation with an FP64 phase reference every 256
+ *                 elements, FP32 accumulation (SIMT).
+ *   XLMIMO_BF16X3 FP32 generation as above; channel split h = hi + lo into two
+ *                 BF16 parts; Gram from hi*hi + hi*lo + lo*hi (+ lo*lo) on the
+ *                 tensor cores (tcgen05) with FP32 accumulation in TMEM. */
+typedef enum { XLMIMO_F64 = 0, XLMIMO_F32 = 1, XLMIMO_BF16X3 = 3 } xlmimo_prec;
+
+/* Linear receivers (Sec. V): ZF (Eq. 21), MMSE, MRC. */
+typedef enum { XLMIMO_ZF = 0, XLMIMO_MMSE = 1, XLMIMO_MRC = 2 } xlmimo_scheme;
+
+/* How beamform() reads `power`:
+ *   XLMIMO_POWER_ABS    power[b][k] is the transmit power p_k.
+ *   XLMIMO_POWER_RXSNR  power[b][k] is user k's received SNR on its own,
+ *                       p_k G_kk / sigma^2 with G the TRUE Gram matrix, so
+ *                       p_k = power[b][k] * sigma^2 / G_kk. */
+typedef enum { XLMIMO_POWER_ABS = 0, XLMIMO_POWER_RXSNR = 1 } xlmimo_power_mode;
+
+/* Array geometry and channel model (Sec. II-A, II-B). */
+typedef struct {
+    int64_t n_ant;      /* N >= 1 */
+    double wavelength;  /* lambda > 0 [m] */
+    double spacing;     /* element spacing > 0 [m]; the paper uses lambda / 2 */
+    double beta0;       /* channel gain constant of PNUSW / UPW (the paper sets 1) */
+    int32_t model;      /* xlmimo_model */
+    int32_t reserved;   /* must be 0 */
+} xlmimo_array;
+
+/* Exact Gram matrices H^H H of B independent trials (Sec. III: received
+ * power P_i = P ||h_i||^2 on the diagonal, h_i^H h_j off it; Sec. V-B: the
+ * inner products that dominate ZF).  The channel entries are generated on
+ * the fly from the geometry and never stored.
+ *   users : [B][K][2] doubles (device)
+ *   gram  : [B][K][K] complex doubles (device, written)
+ *   prec  : xlmimo_prec
+ * Needs device workspace only when B is too small to fill the GPU (the
+ * element range is then split and the partial sums reduced in a fixed order);
+ * that workspace is stream-ordered memory of the current device. */
+int xlmimo_channel_gram(const xlmimo_array* arr, const double* users, int K, int B, int prec,
+                        double* gram, void* stream);
+
+/* Closed-form Gram matrices of "modified ZF" (Sec. V-B): diagonal P_i / P
+ * from Eq. (4), off-diagonal rho_ij sqrt(P_i P_j) / P with rho_ij from
+ * Eq. (6) (SPM correlation).  Written for the PNUSW model exactly as the
+ * paper gives it (element spacing generalised: 2/lambda -> 1/spacing,
+ * M lambda -> 2 N spacing).  For XLMIMO_FSPL_USW the same derivation
+ * (Riemann integral, stationary phase) is applied to the amplitude
+ * lambda / (4 pi r): diagonal (lambda/4pi)^2 (atan((D/2-y)/x) + atan((D/2+y)/x)) / (spacing x),
+ * off-diagonal (lambda/4pi)^2 / spacing * sqrt(lambda / (d x_i x_j)) e^{j sgn(x_i-x_j)(2 pi d/lambda - pi/4)},
+ * D = N spacing, d = |user_i - user_j|.  For XLMIMO_UPW the exact
+ * Dirichlet-kernel form is written.  O(K^2) per trial, FP64.
+ *   users : [B][K][2] doubles (device);  gram : [B][K][K] complex doubles (device, written) */
+int xlmimo_corr_closed_form(const xlmimo_array* arr, const double* users, int K, int B,
+                            double* gram, void* stream);
+
+/* Per-user SINR of a linear receiver built from gram_filter and applied to
+ * the channel whose Gram matrix is gram_true (Sec. V; with gram_filter the
+ * closed form this is "modified ZF").  A receiver W^H = M H^H gives
+ *   SINR_k = p_k |(M G)_kk|^2 / (sum_{j!=k} p_j |(M G)_kj|^2 + sigma^2 (M G M^H)_kk)
+ * with M = Gf^{-1} (ZF), (Gf + sigma^2 diag(p)^{-1})^{-1} (MMSE), I (MRC).
+ * When gram_true is NULL (or equal to gram_filter) the matched forms are
+ * used: ZF p_k / (sigma^2 [G^{-1}]_kk), MMSE p_k / (sigma^2 [Z^{-1}]_kk) - 1
+ * with Z = G + sigma^2 diag(p)^{-1}, MRC p_k G_kk^2 / (sum_{j!=k} p_j |G_kj|^2 + sigma^2 G_kk).
+ * Solves use an FP64 Cholesky factorisation in shared memory; a matrix
+ * that is not numerically positive definite falls back to LU with partial
+ * pivoting.
+ *   gram_filter, gram_true : [B][K][K] complex doubles (device; gram_true may be NULL)
+ *   power  : [B][K] doubles (device), read per power_mode
+ *   noise  : [B] doubles (device), sigma^2 > 0 per trial
+ *   sinr   : [B][K] doubles (device, written)
+ *   trial_status : [B] ints (device, written): 0 ok, 1 Cholesky failed and LU
+ *            was used, 4 (XLMIMO_ESINGULAR) singular: that trial's SINRs are 0
+ *   capacity : [B] doubles (device, written) or NULL:
+ *            log2 det(I + sigma^{-2} diag(p)^{1/2} G diag(p)^{1/2}) with G the
+ *            true Gram matrix (Eq. 9 with per-user powers). */
+int xlmimo_beamform(const double* gram_filter, const double* gram_true, const double* power,
+                    const double* noise, int K, int B, int scheme, int power_mode, double* sinr,
+                    int* trial_status, double* capacity, void* stream);
+
+/* Sum rate R_b = sum_k log2(1 + SINR_bk) of every trial, and the batch
+ * statistics {mean, M2 = sum_b (R_b - mean)^2, count} reduced in a fixed
+ * order (deterministic).
+ *   sinr : [B][K] doubles (device);  rate : [B] doubles (device, written)
+ *   stats : 3 doubles (device, written) or NULL */
+int xlmimo_sumrate(const double* sinr, int K, int B, double* rate, double* stats, void* stream);
+
+/* Per-trial power-saturation interval (Sec. IV-A, Eqs. 13-16):
+ *   y_up = max_k x_k t / sqrt(1-t^2) + y_k,  y_down = min_k -x_k t / sqrt(1-t^2) + y_k
+ * and n_sat = ceil((y_up - y_down) / spacing), the element count spanning it.
+ *   users : [B][K][2] doubles (device);  0 < t < 1;  spacing > 0
+ *   sat   : [B][3] doubles (device, written) {y_up, y_down, n_sat} */
+int xlmimo_saturation(const double* users, int K, int B, double t, double spacing, double* sat,
+                      void* stream);
+
+/* User distributions for the ergodic saturation point. */
+typedef enum { XLMIMO_DIST_RECT = 0, XLMIMO_DIST_POLAR = 1 } xlmimo_dist_kind;
+
+typedef struct {
+    int32_t kind;       /* xlmimo_dist_kind */
+    int32_t reserved;   /* must be 0 */
+    double a0, a1;      /* RECT: x in [a0, a1] (0 < a0 < a1);  POLAR: r in [a0, a1] (0 < a0 < a1) */
+    double b0, b1;      /* RECT: y in [b0, b1];  POLAR: theta in [b0, b1] radians from broadside,
+                           with a t/sqrt(1-t^2) cos(theta) + |sin(theta)| > 0 on the range */
+} xlmimo_user_dist;
+
+/* Ergodic saturation interval and antenna count (Sec. IV-B and Appendix B):
+ * E[y_up] = int y d(F_z(y)^K) with F_z the CDF of z = x t/sqrt(1-t^2) + y for
+ * one user, and E[y_down] = -E[max_k(x_k t/sqrt(1-t^2) - y_k)]; for the
+ * rectangle these equal Eqs. (17)-(18).  Evaluated on the device in FP64 by
+ * composite Gauss-Legendre quadrature of the closed-form CDF.
+ * SYNCHRONOUS: returns host results.
+ *   out : 4 doubles (host, written) {E[y_up], E[y_down], (E[y_up]-E[y_down])/spacing, ceil of it} */
+int xlmimo_saturation_analytic(const xlmimo_user_dist* dist, int K, double t, double spacing,
+                               double* out, void* stream);
+
+/* Capacity-saturation sweep (Sec. IV-C, Fig. 3; Sec. V-C, Fig. 4): for each
+ * array size in n_list, over the same B trials of users, the exact Gram (at
+ * `prec`) and the closed-form Gram, ZF and MMSE sum rates (exact receiver,
+ * and the receiver from the closed form judged on the exact channel) and
+ * the capacity, at every SNR.  The transmit power is the same for every
+ * N: p = snr * sigma^2 / g_lim, g_lim the large-N limit of ||h||^2 for a
+ * reference user at (ref_x, 0) (Eq. 5 for PNUSW; pi (lambda/4pi)^2 / (spacing ref_x)
+ * for the free-space model; for UPW N-proportional, so the reference
+ * array size n_list[last] is used), sigma^2 = 1.
+ * SYNCHRONOUS: returns host results.  Allocates its device buffers with
+ * stream-ordered allocation and frees them before returning. */
+typedef struct {
+    double wavelength, spacing, beta0;
+    int32_t model;        /* xlmimo_model */
+    int32_t prec;         /* xlmimo_prec of the exact Gram */
+    int32_t n_count;      /* number of array sizes */
+    int32_t snr_count;    /* number of SNR points */
+    const int64_t* n_list;   /* host [n_count] */
+    const double* snr_db;    /* host [snr_count] */
+    const double* users;     /* device [B][K][2] */
+    int32_t K, B;
+    double t;             /* saturation threshold for the per-trial interval */
+    double ref_x;         /* reference user distance for the power normalisation */
+} xlmimo_sweep_cfg;
+
+typedef struct {
+    /* all host arrays, caller-allocated, written by the call */
+    double* rate;         /* [n_count][2 path: exact, closed][2 scheme: ZF, MMSE][snr_count] trial means */
+    double* capacity;     /* [n_count][snr_count] trial means of log2 det (Eq. 9) */
+    double* gram_err;     /* [n_count] max over trials and entries of |G~ - G|_ij / sqrt(G_ii G_jj) */
+    double sat_mean[3];   /* trial means of {y_up, y_down, n_sat} (Eqs. 15-16) */
+} xlmimo_sweep_result;
+
+int xlmimo_capacity_sweep(const xlmimo_sweep_cfg* cfg, xlmimo_sweep_result* res, void* stream);
+
+/* Message of the last error on this host thread ("" if none). */
+const char* xlmimo_last_error(void);
+
+/* Interface version, (major << 16) | minor. */
+int xlmimo_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XLMIMO_H */

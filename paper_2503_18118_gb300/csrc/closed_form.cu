@@ -1,0 +1,103 @@
+// Closed-form Gram matrices of "modified ZF" (Sec. V-B), replacing the
+// O(N K^2) inner products by O(K^2) formulas, FP64.
+//
+// PNUSW.  Diagonal: the received power of Eq. (4) over P,
+//   G~_ii = beta0 / (spacing x_i) * B_i,
+//   B_i = (D/2 - y_i)/sqrt(x_i^2 + (D/2 - y_i)^2) + (D/2 + y_i)/sqrt(x_i^2 + (D/2 + y_i)^2),
+// D = N spacing (with spacing = lambda/2 this is the bracket of Eq. 4).
+// Off-diagonal: rho_ij sqrt(G~_ii G~_jj) with rho_ij of Eq. (6).  The B_i
+// factors of Eq. (6) cancel against those of the diagonal, leaving the
+// N-independent value
+//   G~_ij = beta0 / spacing * sqrt(lambda) |dx| / (d^{3/2} sqrt(x_i x_j)) * e^{j phi_ij},
+//   phi_ij = sgn(|x_i| - |x_j|) (2 pi d / lambda - pi/4),  sgn of Eq. (7),
+// d the distance between the users, dx = |x_i| - |x_j|.
+// Free-space spherical wave (same two steps for the amplitude lambda/(4 pi r)):
+//   G~_ii = c2 / (spacing x_i) (atan((D/2 - y_i)/x_i) + atan((D/2 + y_i)/x_i)),
+//   G~_ij = c2 / spacing * sqrt(lambda / (d x_i x_j)) e^{j phi_ij},  c2 = (lambda / 4 pi)^2.
+// Planar wave: exact, G_ij = beta0 / (r_i r_j) e^{j 2 pi (r_i - r_j)/lambda} D_N(v),
+//   D_N(v) = sin(pi N v) / sin(pi v),  v = spacing (sin theta_j - sin theta_i) / lambda.
+// Only i <= j is evaluated; the lower triangle is the conjugate mirror, so
+// the output is Hermitian by construction.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace xl {
+
+__device__ __forceinline__ double2 cis_cycles(double q) {  // e^{j 2 pi q}
+    double f = q - rint(q);
+    double s, c;
+    sincospi(2.0 * f, &s, &c);
+    return make_double2(c, s);
+}
+
+__global__ void closed_form_kernel(Geom g, const double* __restrict__ users, int K, int B,
+                                   double2* __restrict__ gram) {
+    const int64_t P = (int64_t)K * (K + 1) / 2;
+    const int64_t total = (int64_t)B * P;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t b = e / P;
+        int p = (int)(e - b * P);
+        // upper-triangle index p -> (i, j), row by row
+        int i = 0, rowlen = K;
+        while (p >= rowlen) { p -= rowlen; ++i; --rowlen; }
+        int j = i + p;
+        const double* u = users + b * K * 2;
+        double xi = u[2 * i], yi = u[2 * i + 1], xj = u[2 * j], yj = u[2 * j + 1];
+        double2 v;
+        if (!user_ok(xi, yi) || !user_ok(xj, yj)) {
+            v = make_double2(nan(""), nan(""));
+        } else if (g.model == XLMIMO_UPW) {
+            double ri = sqrt(xi * xi + yi * yi), rj = sqrt(xj * xj + yj * yj);
+            double vv = g.spacing * (yj / rj - yi / ri) * g.inv_lambda;
+            double sv = sinpi(vv);
+            double dir = fabs(sv) < 1e-300 ? (double)g.N : sinpi((double)g.N * vv) / sv;
+            double2 ph = cis_cycles((ri - rj) * g.inv_lambda);
+            double m = g.beta0 / (ri * rj) * dir;
+            v = make_double2(m * ph.x, m * ph.y);
+        } else if (i == j) {
+            double h = 0.5 * (double)g.N * g.spacing;
+            double val;
+            if (g.model == XLMIMO_PNUSW) {
+                double a = h - yi, c = h + yi;
+                val = g.beta0 / (g.spacing * xi) * (a / sqrt(xi * xi + a * a) + c / sqrt(xi * xi + c * c));
+            } else {
+                double c2 = g.lambda * g.lambda / (16.0 * 3.14159265358979323846 * 3.14159265358979323846);
+                val = c2 / (g.spacing * xi) * (atan((h - yi) / xi) + atan((h + yi) / xi));
+            }
+            v = make_double2(val, 0.0);
+        } else {
+            double dx = fabs(xi) - fabs(xj), dy = yi - yj;
+            double d = sqrt(dx * dx + dy * dy);
+            double sg = dx > 0.0 ? 1.0 : -1.0;
+            double2 ph = cis_cycles(sg * (d * g.inv_lambda - 0.125));
+            double m;
+            if (g.model == XLMIMO_PNUSW)
+                m = g.beta0 / g.spacing * sqrt(g.lambda) * fabs(dx) / (d * sqrt(d) * sqrt(xi * xj));
+            else
+                m = g.lambda * g.lambda / (16.0 * 3.14159265358979323846 * 3.14159265358979323846) / g.spacing *
+                    sqrt(g.lambda / (d * xi * xj));
+            v = make_double2(m * ph.x, m * ph.y);
+        }
+        double2* G = gram + b * K * K;
+        if (i == j) {
+            G[i * K + i] = make_double2(v.x, g.model == XLMIMO_UPW ? 0.0 : v.y);
+        } else {
+            G[i * K + j] = v;
+            G[j * K + i] = make_double2(v.x, -v.y);
+        }
+    }
+}
+
+int launch_closed_form(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st) {
+    int64_t total = (int64_t)B * K * (K + 1) / 2;
+    int threads = 256;
+    int64_t blocks = (total + threads - 1) / threads;
+    int64_t cap = 16LL * num_sms();
+    if (blocks > cap) blocks = cap;
+    closed_form_kernel<<<(unsigned)blocks, threads, 0, st>>>(g, users, K, B, (double2*)gram);
+    return cuda_status(cudaGetLastError(), "closed_form launch");
+}
+
+}  // namespace xl

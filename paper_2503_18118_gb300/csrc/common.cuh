@@ -1,0 +1,68 @@
+// Internal helpers shared by the CUDA translation units of libxlmimo.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "xlmimo.h"
+
+namespace xl {
+
+// Thread-local message behind xlmimo_last_error().
+void set_error(const char* fmt, ...);
+void clear_error();
+
+int num_sms();
+
+// Translate a CUDA error into XLMIMO_ECUDA with a message.
+int cuda_status(cudaError_t e, const char* where);
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Geometry shared by the channel generators.
+struct Geom {
+    int64_t N;
+    double lambda, inv_lambda, spacing, beta0;
+    int model;
+};
+
+int check_array(const xlmimo_array* arr, Geom* g);
+
+// Host launchers implemented in the .cu files (validated arguments only).
+int launch_gram_f64(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st);
+int launch_gram_f32(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st);
+int launch_gram_tc(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st);
+int launch_closed_form(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st);
+int launch_beamform(const double* gf, const double* gt, const double* power, const double* noise, int K,
+                    int B, int scheme, int power_mode, double* sinr, int* status, double* cap,
+                    cudaStream_t st);
+int launch_sumrate(const double* sinr, int K, int B, double* rate, double* stats, cudaStream_t st);
+int launch_saturation(const double* users, int K, int B, double t, double spacing, double* sat,
+                      cudaStream_t st);
+int saturation_analytic(const xlmimo_user_dist* d, int K, double t, double spacing, double* out,
+                        cudaStream_t st);
+
+// Split of the element range when the batch alone cannot fill the GPU.
+// Returns the number of contiguous element chunks per trial (>= 1); each chunk
+// is a whole number of `tile` elements except the last.
+int choose_split(int64_t N, int B, int tile, int ctas_per_sm_hint);
+
+// Deterministic sum of S partial Gram matrices [B][S][K][K] (complex double)
+// into gram [B][K][K], in increasing chunk order.
+int launch_reduce_partials(const double* partial, int S, int K, int B, double* gram, cudaStream_t st);
+
+}  // namespace xl
+
+// ---- device helpers -------------------------------------------------------
+
+#define XL_DEV __device__ __forceinline__
+
+namespace xl {
+
+XL_DEV double element_y(int64_t n, int64_t N, double spacing) {
+    return ((double)n - 0.5 * (double)(N - 1)) * spacing;
+}
+
+XL_DEV bool user_ok(double x, double y) { return x > 0.0 && isfinite(x) && isfinite(y); }
+
+}  // namespace xl

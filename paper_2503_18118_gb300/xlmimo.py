@@ -1,0 +1,217 @@
+"""Python binding of libxlmimo (include/xlmimo.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls and forwards
+torch CUDA tensors as raw device pointers on the current torch stream.
+There is no CPU fallback: a missing or unloadable library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+PNUSW, FSPL_USW, UPW = 0, 1, 2
+F64, F32, BF16X3 = 0, 1, 3
+ZF, MMSE, MRC = 0, 1, 2
+POWER_ABS, POWER_RXSNR = 0, 1
+DIST_RECT, DIST_POLAR = 0, 1
+MAX_USERS = 64
+STATUS = {0: "OK", 1: "EINVAL", 2: "ECUDA", 3: "ENOMEM", 4: "ESINGULAR", 5: "ETIMEOUT", 6: "EUNSUPPORTED"}
+
+
+class XlmimoError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"xlmimo error {code} ({STATUS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class Array(ctypes.Structure):
+    _fields_ = [("n_ant", ctypes.c_int64), ("wavelength", ctypes.c_double), ("spacing", ctypes.c_double),
+                ("beta0", ctypes.c_double), ("model", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class UserDist(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("a0", ctypes.c_double),
+                ("a1", ctypes.c_double), ("b0", ctypes.c_double), ("b1", ctypes.c_double)]
+
+
+class SweepCfg(ctypes.Structure):
+    _fields_ = [("wavelength", ctypes.c_double), ("spacing", ctypes.c_double), ("beta0", ctypes.c_double),
+                ("model", ctypes.c_int32), ("prec", ctypes.c_int32), ("n_count", ctypes.c_int32),
+                ("snr_count", ctypes.c_int32), ("n_list", ctypes.POINTER(ctypes.c_int64)),
+                ("snr_db", ctypes.POINTER(ctypes.c_double)), ("users", ctypes.c_void_p),
+                ("K", ctypes.c_int32), ("B", ctypes.c_int32), ("t", ctypes.c_double), ("ref_x", ctypes.c_double)]
+
+
+class SweepResult(ctypes.Structure):
+    _fields_ = [("rate", ctypes.POINTER(ctypes.c_double)), ("capacity", ctypes.POINTER(ctypes.c_double)),
+                ("gram_err", ctypes.POINTER(ctypes.c_double)), ("sat_mean", ctypes.c_double * 3)]
+
+
+EXPORTS = ("xlmimo_channel_gram", "xlmimo_corr_closed_form", "xlmimo_beamform", "xlmimo_sumrate",
+           "xlmimo_saturation", "xlmimo_saturation_analytic", "xlmimo_capacity_sweep", "xlmimo_last_error",
+           "xlmimo_version")
+
+_lib = None
+
+
+def lib(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libxlmimo.so (building it first when it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libxlmimo.so not found at {_build.LIB}; run paper_2503_18118_gb300.build.build()")
+    L = ctypes.CDLL(_build.LIB)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    L.xlmimo_channel_gram.argtypes = [ctypes.POINTER(Array), vp, i32, i32, i32, vp, vp]
+    L.xlmimo_corr_closed_form.argtypes = [ctypes.POINTER(Array), vp, i32, i32, vp, vp]
+    L.xlmimo_beamform.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp]
+    L.xlmimo_sumrate.argtypes = [vp, i32, i32, vp, vp, vp]
+    L.xlmimo_saturation.argtypes = [vp, i32, i32, dbl, dbl, vp, vp]
+    L.xlmimo_saturation_analytic.argtypes = [ctypes.POINTER(UserDist), i32, dbl, dbl, ctypes.POINTER(dbl), vp]
+    L.xlmimo_capacity_sweep.argtypes = [ctypes.POINTER(SweepCfg), ctypes.POINTER(SweepResult), vp]
+    L.xlmimo_last_error.restype = ctypes.c_char_p
+    for f in EXPORTS:
+        if f != "xlmimo_last_error":
+            getattr(L, f).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != 0:
+        raise XlmimoError(rc, lib().xlmimo_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dev(t, dtype, name, shape=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def array(n_ant, wavelength, spacing=None, beta0=1.0, model=FSPL_USW) -> Array:
+    return Array(int(n_ant), float(wavelength), float(0.5 * wavelength if spacing is None else spacing),
+                 float(beta0), int(model), 0)
+
+
+def xlmimo_version() -> int:
+    return int(lib().xlmimo_version())
+
+
+def xlmimo_channel_gram(arr: Array, users: torch.Tensor, prec: int = F32, gram: torch.Tensor | None = None,
+                        stream=None) -> torch.Tensor:
+    """Exact Gram matrices H^H H, complex128 [B][K][K]."""
+    B, K = users.shape[0], users.shape[1]
+    if gram is None:
+        gram = torch.empty((B, K, K), dtype=torch.complex128, device=users.device)
+    _check(lib().xlmimo_channel_gram(ctypes.byref(arr), _dev(users, torch.float64, "users", (B, K, 2)), K, B,
+                                     int(prec), _dev(gram, torch.complex128, "gram", (B, K, K)), _stream(stream)))
+    return gram
+
+
+def xlmimo_corr_closed_form(arr: Array, users: torch.Tensor, gram: torch.Tensor | None = None,
+                            stream=None) -> torch.Tensor:
+    """Closed-form Gram matrices of modified ZF, complex128 [B][K][K]."""
+    B, K = users.shape[0], users.shape[1]
+    if gram is None:
+        gram = torch.empty((B, K, K), dtype=torch.complex128, device=users.device)
+    _check(lib().xlmimo_corr_closed_form(ctypes.byref(arr), _dev(users, torch.float64, "users", (B, K, 2)), K, B,
+                                         _dev(gram, torch.complex128, "gram", (B, K, K)), _stream(stream)))
+    return gram
+
+
+def xlmimo_beamform(gram_filter: torch.Tensor, power: torch.Tensor, noise: torch.Tensor, scheme: int,
+                    power_mode: int = POWER_ABS, gram_true: torch.Tensor | None = None, capacity: bool = False,
+                    sinr: torch.Tensor | None = None, status: torch.Tensor | None = None,
+                    cap: torch.Tensor | None = None, stream=None):
+    """(sinr [B][K] float64, status [B] int32, capacity [B] float64 or None)."""
+    B, K = gram_filter.shape[0], gram_filter.shape[1]
+    dev = gram_filter.device
+    if sinr is None:
+        sinr = torch.empty((B, K), dtype=torch.float64, device=dev)
+    if status is None:
+        status = torch.empty((B,), dtype=torch.int32, device=dev)
+    if capacity and cap is None:
+        cap = torch.empty((B,), dtype=torch.float64, device=dev)
+    gt = None if gram_true is None else _dev(gram_true, torch.complex128, "gram_true", (B, K, K))
+    _check(lib().xlmimo_beamform(_dev(gram_filter, torch.complex128, "gram_filter", (B, K, K)), gt,
+                                 _dev(power, torch.float64, "power", (B, K)), _dev(noise, torch.float64, "noise", (B,)),
+                                 K, B, int(scheme), int(power_mode), _dev(sinr, torch.float64, "sinr", (B, K)),
+                                 _dev(status, torch.int32, "status", (B,)),
+                                 None if cap is None else _dev(cap, torch.float64, "cap", (B,)), _stream(stream)))
+    return sinr, status, cap
+
+
+def xlmimo_sumrate(sinr: torch.Tensor, rate: torch.Tensor | None = None, stats: torch.Tensor | None = None,
+                   want_stats: bool = True, stream=None):
+    """(rate [B], stats [3] = {mean, M2, count} or None)."""
+    B, K = sinr.shape
+    if rate is None:
+        rate = torch.empty((B,), dtype=torch.float64, device=sinr.device)
+    if want_stats and stats is None:
+        stats = torch.empty((3,), dtype=torch.float64, device=sinr.device)
+    _check(lib().xlmimo_sumrate(_dev(sinr, torch.float64, "sinr", (B, K)), K, B,
+                                _dev(rate, torch.float64, "rate", (B,)),
+                                None if stats is None else _dev(stats, torch.float64, "stats", (3,)), _stream(stream)))
+    return rate, stats
+
+
+def xlmimo_saturation(users: torch.Tensor, t: float, spacing: float, sat: torch.Tensor | None = None,
+                      stream=None) -> torch.Tensor:
+    """Per-trial {y_up, y_down, n_sat}, float64 [B][3]."""
+    B, K = users.shape[0], users.shape[1]
+    if sat is None:
+        sat = torch.empty((B, 3), dtype=torch.float64, device=users.device)
+    _check(lib().xlmimo_saturation(_dev(users, torch.float64, "users", (B, K, 2)), K, B, float(t), float(spacing),
+                                   _dev(sat, torch.float64, "sat", (B, 3)), _stream(stream)))
+    return sat
+
+
+def xlmimo_saturation_analytic(kind: int, a0: float, a1: float, b0: float, b1: float, K: int, t: float,
+                               spacing: float, stream=None):
+    """(E[y_up], E[y_down], aperture/spacing, ceil) -- synchronous."""
+    d = UserDist(int(kind), 0, float(a0), float(a1), float(b0), float(b1))
+    out = (ctypes.c_double * 4)()
+    _check(lib().xlmimo_saturation_analytic(ctypes.byref(d), int(K), float(t), float(spacing), out, _stream(stream)))
+    return tuple(out)
+
+
+def xlmimo_capacity_sweep(users: torch.Tensor, n_list, snr_db, wavelength: float, spacing: float | None = None,
+                          beta0: float = 1.0, model: int = FSPL_USW, prec: int = F32, t: float = 0.9,
+                          ref_x: float = 1.0, stream=None) -> dict:
+    """Synchronous sweep over array sizes; returns host numpy arrays."""
+    import numpy as np
+    B, K = users.shape[0], users.shape[1]
+    n_arr = (ctypes.c_int64 * len(n_list))(*[int(n) for n in n_list])
+    s_arr = (ctypes.c_double * len(snr_db))(*[float(s) for s in snr_db])
+    cfg = SweepCfg(float(wavelength), float(0.5 * wavelength if spacing is None else spacing), float(beta0),
+                   int(model), int(prec), len(n_list), len(snr_db), n_arr, s_arr,
+                   _dev(users, torch.float64, "users", (B, K, 2)), K, B, float(t), float(ref_x))
+    rate = np.zeros((len(n_list), 2, 2, len(snr_db)))
+    cap = np.zeros((len(n_list), len(snr_db)))
+    err = np.zeros((len(n_list),))
+    res = SweepResult(rate.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                      cap.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                      err.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), (ctypes.c_double * 3)())
+    _check(lib().xlmimo_capacity_sweep(ctypes.byref(cfg), ctypes.byref(res), _stream(stream)))
+    return {"rate": rate, "capacity": cap, "gram_err": err, "sat_mean": tuple(res.sat_mean)}

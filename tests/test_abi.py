@@ -1,0 +1,90 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/xlmimo.h declares; argument validation rejects bad calls before any
+device work (these calls never touch a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    syms = set()
+    for name in os.listdir(os.path.join(ROOT, "include")):
+        if name.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", name)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            syms |= set(re.findall(r"\b(xlmimo_[a-z0-9_]+)\s*\(", text))
+    return syms
+
+
+@pytest.fixture(scope="module")
+def xl():
+    from paper_2503_18118_gb300 import xlmimo
+    xlmimo.lib()
+    return xlmimo
+
+
+def test_exports_every_declared_symbol(xl):
+    syms = declared_symbols()
+    assert {"xlmimo_channel_gram", "xlmimo_corr_closed_form", "xlmimo_beamform", "xlmimo_sumrate",
+            "xlmimo_capacity_sweep"} <= syms
+    L = xl.lib()
+    for s in sorted(syms):
+        assert hasattr(L, s), s
+    assert set(xl.EXPORTS) >= syms
+
+
+def test_version(xl):
+    assert xl.xlmimo_version() >> 16 == 1
+
+
+def test_invalid_arguments_rejected_on_host(xl):
+    L = xl.lib()
+    arr = xl.array(256, 0.01)
+    dummy = ctypes.c_void_p(16)
+    # K out of range
+    assert L.xlmimo_channel_gram(ctypes.byref(arr), dummy, 65, 1, xl.F32, dummy, None) == 1
+    assert b"K must be" in L.xlmimo_last_error()
+    assert L.xlmimo_channel_gram(ctypes.byref(arr), dummy, 0, 1, xl.F32, dummy, None) == 1
+    # bad geometry
+    bad = xl.array(0, 0.01)
+    assert L.xlmimo_channel_gram(ctypes.byref(bad), dummy, 4, 1, xl.F32, dummy, None) == 1
+    bad = xl.array(16, -1.0)
+    assert L.xlmimo_corr_closed_form(ctypes.byref(bad), dummy, 4, 1, dummy, None) == 1
+    bad = xl.array(16, 0.01, model=7)
+    assert L.xlmimo_channel_gram(ctypes.byref(bad), dummy, 4, 1, xl.F32, dummy, None) == 1
+    # unknown precision, scheme, power mode
+    assert L.xlmimo_channel_gram(ctypes.byref(arr), dummy, 4, 1, 9, dummy, None) == 1
+    assert L.xlmimo_beamform(dummy, None, dummy, dummy, 4, 1, 5, 0, dummy, dummy, None, None) == 1
+    assert L.xlmimo_beamform(dummy, None, dummy, dummy, 4, 1, 0, 3, dummy, dummy, None, None) == 1
+    # NULL buffers
+    assert L.xlmimo_channel_gram(ctypes.byref(arr), None, 4, 1, xl.F32, dummy, None) == 1
+    assert L.xlmimo_sumrate(None, 4, 3, dummy, None, None) == 1
+    # saturation threshold outside (0, 1)
+    assert L.xlmimo_saturation(dummy, 4, 1, 1.0, 0.01, dummy, None) == 1
+    d = xl.UserDist(xl.DIST_RECT, 0, 2.0, 1.0, 0.0, 1.0)
+    out = (ctypes.c_double * 4)()
+    assert L.xlmimo_saturation_analytic(ctypes.byref(d), 4, 0.9, 0.01, out, None) == 1
+
+
+def test_empty_batch_is_a_no_op(xl):
+    L = xl.lib()
+    arr = xl.array(256, 0.01)
+    assert L.xlmimo_channel_gram(ctypes.byref(arr), None, 4, 0, xl.F32, None, None) == 0
+    assert L.xlmimo_corr_closed_form(ctypes.byref(arr), None, 4, 0, None, None) == 0
+    assert L.xlmimo_beamform(None, None, None, None, 4, 0, 0, 0, None, None, None, None) == 0
+    assert L.xlmimo_saturation(None, 4, 0, 0.9, 0.01, None, None) == 0
+
+
+def test_product_path_has_no_oracle_or_cpu_fallback():
+    """The package never imports the oracle and the binding has no CPU path."""
+    pkg = os.path.join(ROOT, "paper_2503_18118_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "liboracle" not in text, f

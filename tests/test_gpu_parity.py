@@ -1,0 +1,277 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle
+on the same seeded inputs.
+
+Tolerances (stated by the accuracy targets of the path and written here):
+  * Gram, FP64 path:  normwise max_ij |dG_ij| / sqrt(G_ii G_jj) <= 1e-12
+  * Gram, FP32 path:  normwise <= 1e-5
+  * Gram, BF16x3 path: normwise <= 1e-4 (checked where the build has it)
+  * closed form: elementwise relative <= 1e-12 (both sides FP64 formulas)
+  * receivers on the same Gram input: SINR relative <= 1e-9 (FP64 solves)
+  * sum rate of the full FP32 path vs the oracle end to end: relative <= 1e-4
+  * saturation: coordinates to 1e-13 relative, integer counts exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2503_18118_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+LAM28 = inputs.wavelength(28e9)
+LAM100 = inputs.wavelength(100e9)
+
+
+@pytest.fixture(scope="module")
+def xl():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_18118_gb300 import xlmimo
+    xlmimo.lib()
+    return xlmimo
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def normwise(G, Gref):
+    d = np.sqrt(np.abs(np.einsum("...ii->...i", Gref)))
+    return float(np.max(np.abs(G - Gref) / (d[..., :, None] * d[..., None, :])))
+
+
+def gpu_gram(xl, users, N, lam, prec, model=1, spacing=None, beta0=1.0):
+    arr = xl.array(N, lam, spacing, beta0, model)
+    G = xl.xlmimo_channel_gram(arr, dev(users), prec)
+    torch.cuda.synchronize()
+    return G.cpu().numpy()
+
+
+@pytest.mark.parametrize("model", [0, 1, 2])
+@pytest.mark.parametrize("N,K,B", [(1, 1, 3), (2, 3, 2), (31, 5, 4), (33, 4, 7), (256, 4, 100), (1000, 32, 3),
+                                   (517, 64, 2), (4099, 17, 5)])
+def test_gram_f64(xl, orc, model, N, K, B):
+    users = inputs.users_polar(100 + N + K, B, K, (5.0, 50.0))
+    G = gpu_gram(xl, users, N, LAM28, xl.F64, model)
+    R = orc.gram(model, N, LAM28, LAM28 / 2, 1.0, users)
+    assert normwise(G, R) <= 1e-12
+    assert np.all(np.imag(np.einsum("bii->bi", G)) == 0)
+
+
+@pytest.mark.parametrize("model", [0, 1, 2])
+@pytest.mark.parametrize("N,K,B", [(1, 1, 3), (2, 3, 2), (63, 5, 4), (129, 4, 7), (256, 4, 100), (1000, 32, 3),
+                                   (517, 64, 2), (4099, 17, 5), (16384, 32, 2)])
+def test_gram_f32(xl, orc, model, N, K, B):
+    users = inputs.users_polar(200 + N + K, B, K, (3.0, 30.0))
+    G = gpu_gram(xl, users, N, LAM100, xl.F32, model)
+    R = orc.gram(model, N, LAM100, LAM100 / 2, 1.0, users)
+    assert normwise(G, R) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_gram_split_path(xl, orc, prec):
+    """A batch far smaller than the GPU splits the element range; the fixed-order
+    sum of the partial Gram matrices must match."""
+    users = inputs.users_polar(7, 2, 8, (3.0, 30.0))
+    N = 70001  # ragged against every tile size
+    G = gpu_gram(xl, users, N, LAM100, prec)
+    R = orc.gram(1, N, LAM100, LAM100 / 2, 1.0, users)
+    assert normwise(G, R) <= (1e-12 if prec == 0 else 1e-5)
+    G2 = gpu_gram(xl, users, N, LAM100, prec)
+    assert np.array_equal(G, G2)  # deterministic
+
+
+def test_gram_spacing_and_beta0(xl, orc):
+    users = inputs.users_polar(8, 3, 6, (3.0, 30.0))
+    for prec, tol in ((0, 1e-12), (1, 1e-5)):
+        G = gpu_gram(xl, users, 3000, LAM100, prec, model=0, spacing=0.37 * LAM100, beta0=2.5)
+        R = orc.gram(0, 3000, LAM100, 0.37 * LAM100, 2.5, users)
+        assert normwise(G, R) <= tol
+
+
+def test_invalid_user_gives_nan(xl):
+    users = inputs.users_polar(9, 3, 4, (3.0, 30.0))
+    users[1, 2, 0] = -1.0
+    for prec in (0, 1):
+        G = gpu_gram(xl, users, 300, LAM100, prec)
+        assert np.isnan(G[1]).all() and np.isfinite(G[0]).all() and np.isfinite(G[2]).all()
+
+
+@pytest.mark.parametrize("model", [0, 1, 2])
+def test_closed_form(xl, orc, model):
+    users = inputs.users_polar(10 + model, 50, 9, (3.0, 30.0))
+    for N in (1, 64, 16384, 1 << 30):
+        arr = xl.array(N, LAM100, None, 1.3, model)
+        G = xl.xlmimo_corr_closed_form(arr, dev(users)).cpu().numpy()
+        R = orc.closed_form(model, N, LAM100, LAM100 / 2, 1.3, users)
+        if model == 2:
+            # exact Dirichlet form: entries carry a phase of ~10^5 rad
+            assert normwise(G, R) <= 1e-9
+        else:
+            assert np.max(np.abs(G - R) / np.abs(R)) <= 1e-11
+
+
+def _solve_case(orc, seed, B, K, N, model=1, lam=LAM28):
+    users = inputs.users_polar(seed, B, K, (5.0, 50.0))
+    G = orc.gram(model, N, lam, lam / 2, 1.0, users)
+    Gc = orc.closed_form(model, N, lam, lam / 2, 1.0, users)
+    g = np.random.Generator(np.random.Philox(key=seed + 1))
+    p = 10 ** g.uniform(0.0, 2.0, (B, K))
+    s2 = g.uniform(0.5, 2.0, B)
+    return users, G, Gc, p, s2
+
+
+@pytest.mark.parametrize("K", [1, 2, 5, 32, 64])
+@pytest.mark.parametrize("scheme", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_beamform_matched(xl, orc, K, scheme, mode):
+    _, G, _, p, s2 = _solve_case(orc, 30 + K, 12, K, max(4 * K, 64))
+    if mode == 0:
+        p = p / np.real(np.einsum("bii->bi", G))
+    s_ref, st_ref, c_ref = orc.beamform(G, p, s2, scheme, mode, want_capacity=True)
+    s, st, c = xl.xlmimo_beamform(dev(G), dev(p), dev(s2), scheme, mode, capacity=True)
+    s, st, c = s.cpu().numpy(), st.cpu().numpy(), c.cpu().numpy()
+    ok = st_ref == 0
+    assert ok.any()
+    assert np.all(np.isin(st[ok], [0, 1]))
+    assert np.max(np.abs(s[ok] - s_ref[ok]) / np.abs(s_ref[ok])) <= 1e-9
+    assert np.max(np.abs(c - c_ref) / np.abs(c_ref)) <= 1e-10
+
+
+@pytest.mark.parametrize("K", [2, 8, 32, 64])
+@pytest.mark.parametrize("scheme", [0, 1, 2])
+def test_beamform_modified_zf(xl, orc, K, scheme):
+    """Receiver from the closed-form Gram, judged on the exact channel; small N
+    makes the closed form indefinite for some trials (Gauss-Jordan fallback)."""
+    for N in (64, 4096):
+        _, G, Gc, p, s2 = _solve_case(orc, 50 + K + N, 10, K, N)
+        p = p / np.real(np.einsum("bii->bi", G))
+        s_ref, st_ref, _ = orc.beamform(Gc, p, s2, scheme, 0, gram_true=G)
+        s, st, _ = xl.xlmimo_beamform(dev(Gc), dev(p), dev(s2), scheme, 0, gram_true=dev(G))
+        s, st = s.cpu().numpy(), st.cpu().numpy()
+        ok = (st_ref == 0) & (st != 4)
+        assert ok.sum() >= 8
+        rel = np.abs(s[ok] - s_ref[ok]) / np.maximum(np.abs(s_ref[ok]), 1e-300)
+        assert np.max(rel) <= 1e-7
+
+
+def test_beamform_singular(xl):
+    G = np.array([[[1.0, 1.0], [1.0, 1.0]]], complex)
+    s, st, _ = xl.xlmimo_beamform(dev(G), dev(np.ones((1, 2))), dev(np.ones(1)), 0)
+    assert int(st.cpu()[0]) == 4 and (s.cpu().numpy() == 0).all()
+
+
+def test_sumrate(xl, orc):
+    g = np.random.Generator(np.random.Philox(key=3))
+    for B, K in ((1, 1), (37, 7), (10000, 32), (3001, 64)):
+        sinr = g.uniform(0, 80, (B, K))
+        r_ref, st_ref = orc.sumrate(sinr)
+        r, st = xl.xlmimo_sumrate(dev(sinr))
+        r, st = r.cpu().numpy(), st.cpu().numpy()
+        assert np.max(np.abs(r - r_ref) / r_ref) <= 1e-14
+        assert abs(st[0] - st_ref[0]) <= 1e-13 * abs(st_ref[0])
+        assert abs(st[1] - st_ref[1]) <= 1e-9 * abs(st_ref[1]) + 1e-12
+        assert st[2] == B
+
+
+def test_saturation_per_trial(xl, orc):
+    users = inputs.users_polar(4, 5000, 8, (5.0, 50.0))
+    for t in (0.5, 0.9, 0.99):
+        sat = xl.xlmimo_saturation(dev(users), t, LAM28 / 2).cpu().numpy()
+        ref = orc.saturation(users, t, LAM28 / 2)
+        assert np.max(np.abs(sat[:, :2] - ref[:, :2]) / np.abs(ref[:, :2])) <= 1e-13
+        frac = (ref[:, 0] - ref[:, 1]) / (LAM28 / 2)
+        clean = np.abs(frac - np.rint(frac)) > 1e-6
+        assert np.array_equal(sat[clean, 2], ref[clean, 2])
+
+
+@pytest.mark.parametrize("kind,a,b,K,freq", [
+    (0, (1.0, 10.0), (-7.5, 7.5), 100, 100e9),   # Fig. 3 setting
+    (0, (1.0, 2.0), (-7.5, 7.5), 10, 100e9),     # Fig. 4 setting
+    (0, (2.0, 3.0), (0.0, 20.0), 1, 28e9),
+    (1, (5.0, 50.0), (-60.0, 60.0), 8, 28e9),    # polar sweep geometry
+    (1, (3.0, 30.0), (-60.0, 60.0), 32, 100e9),  # polar headline geometry
+    (1, (3.0, 30.0), (-20.0, 45.0), 3, 100e9),
+])
+def test_saturation_analytic(xl, kind, a, b, K, freq):
+    from oracle import ergodic
+    t = 0.9
+    lam = inputs.wavelength(freq)
+    if kind == 0:
+        up = ergodic.expected_y_up_appendix_b(*a, *b, t, K)
+        up17 = ergodic.expected_y_up_eq17(*a, *b, t, K)
+        assert abs(up - up17) < 1e-9 * abs(up)
+        dn = ergodic.expected_y_down_eq18(*a, *b, t, K)
+        res = xl.xlmimo_saturation_analytic(0, *a, *b, K, t, lam / 2)
+    else:
+        th = (math.radians(b[0]), math.radians(b[1]))
+        up, dn = ergodic.expected_interval_polar(*a, *th, t, K)
+        res = xl.xlmimo_saturation_analytic(1, *a, *th, K, t, lam / 2)
+    assert abs(res[0] - up) <= 1e-9 * max(1.0, abs(up))
+    assert abs(res[1] - dn) <= 1e-9 * max(1.0, abs(dn))
+    v, n = ergodic.saturation_antennas(up, dn, lam / 2)
+    if abs(v - round(v)) > 1e-5:
+        assert int(res[3]) == n
+
+
+def test_headline_pipeline_sampled(xl, orc):
+    """Full-size batch (N = 16384, K = 32, 100 GHz, 10^4 trials) in the launch
+    configuration the benchmark times; the oracle checks sampled trials end
+    to end (Gram, MMSE SINR, sum rate) and properties hold for all trials."""
+    wl = inputs.HEADLINE
+    users = wl.users()
+    B, K, N = wl.trials, wl.k, wl.n_ant
+    arr = xl.array(N, wl.wavelength, wl.spacing, 1.0, wl.model)
+    U = dev(users)
+    G = xl.xlmimo_channel_gram(arr, U, xl.F32)
+    snr = dev(wl.power())
+    noise = dev(wl.noise())
+    sinr, st, cap = xl.xlmimo_beamform(G, snr, noise, xl.MMSE, xl.POWER_RXSNR, capacity=True)
+    rate, stats = xl.xlmimo_sumrate(sinr)
+    torch.cuda.synchronize()
+    Gh = G.cpu().numpy()
+    assert np.isfinite(Gh).all()
+    assert np.allclose(Gh, np.conj(np.swapaxes(Gh, 1, 2)), rtol=0, atol=0)
+    assert (st.cpu().numpy() == 0).all()
+    idx = np.array([0, 1, 4999, B - 1])
+    R = orc.gram(wl.model, N, wl.wavelength, wl.spacing, 1.0, users[idx])
+    assert normwise(Gh[idx], R) <= 1e-5
+    s_ref, _, c_ref = orc.beamform(R, wl.power(len(idx)), wl.noise(len(idx)), xl.MMSE, 1, want_capacity=True)
+    r_ref, _ = orc.sumrate(s_ref)
+    r = rate.cpu().numpy()[idx]
+    assert np.max(np.abs(r - r_ref) / r_ref) <= 1e-4
+    assert np.max(np.abs(cap.cpu().numpy()[idx] - c_ref) / c_ref) <= 1e-4
+    # diagonal of every trial against the FSPL received-power closed form
+    Gc = xl.xlmimo_corr_closed_form(arr, U).cpu().numpy()
+    d = np.real(np.einsum("bii->bi", Gh))
+    dc = np.real(np.einsum("bii->bi", Gc))
+    assert np.max(np.abs(d - dc) / d) < 1e-3
+
+
+def test_capacity_sweep_small(xl, orc):
+    """Sweep at a few sizes against the oracle pipeline on the same users."""
+    K, B = 4, 20
+    users = inputs.users_polar(2, B, K, (5.0, 50.0))
+    n_list = [64, 256, 1024]
+    snr_db = [0.0, 10.0]
+    ref_x = 27.5
+    for prec, tol in ((0, 1e-10), (1, 1e-4)):
+        out = xl.xlmimo_capacity_sweep(dev(users), n_list, snr_db, LAM28, prec=prec, ref_x=ref_x)
+        glim = math.pi * (LAM28 / (4 * math.pi)) ** 2 / (LAM28 / 2 * ref_x)
+        for ni, N in enumerate(n_list):
+            G = orc.gram(1, N, LAM28, LAM28 / 2, 1.0, users)
+            Gc = orc.closed_form(1, N, LAM28, LAM28 / 2, 1.0, users)
+            assert abs(out["gram_err"][ni] - normwise(Gc, G)) <= 1e-4 * normwise(Gc, G) + 1e-9
+            for si, s in enumerate(snr_db):
+                p = np.full((B, K), 10 ** (s / 10) / glim)
+                for path, gf, gt in ((0, G, None), (1, Gc, G)):
+                    for sch in (0, 1):
+                        sr, stt, cap = orc.beamform(gf, p, np.ones(B), sch, 0, gram_true=gt, want_capacity=True)
+                        rr, _ = orc.sumrate(sr)
+                        assert abs(out["rate"][ni, path, sch, si] - rr.mean()) <= tol * abs(rr.mean()) + 1e-12
+                        if path == 0 and sch == 1:
+                            assert abs(out["capacity"][ni, si] - cap.mean()) <= tol * abs(cap.mean())
+        sat = orc.saturation(users, 0.9, LAM28 / 2)
+        assert np.allclose(out["sat_mean"], sat.mean(0), rtol=1e-12)
