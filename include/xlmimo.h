@@ -101,6 +101,34 @@ typedef struct {
 int xlmimo_channel_gram(const xlmimo_array* arr, const double* users, int K, int B, int prec,
                         double* gram, void* stream);
 
+/* Size of the fixed device scratch used by xlmimo_channel_gram_noalloc, in MiB. */
+#define XLMIMO_NOALLOC_SCRATCH_MIB 16
+
+/* xlmimo_channel_gram without any device memory allocation.  The paper has
+ * no counterpart: this serves callers that cannot allocate device memory
+ * while they run -- for example an application that reserves the GPU's
+ * memory for its own pool at start-up and forbids later allocations, or a
+ * latency-critical loop that cannot accept cudaMalloc / cudaFree, which may
+ * block or synchronise the device.  Arguments, results and precisions
+ * (XLMIMO_F64 and XLMIMO_F32; XLMIMO_BF16X3 returns XLMIMO_EUNSUPPORTED) are
+ * those of xlmimo_channel_gram, with the same element split and the same
+ * summation order.
+ * When the batch is too small to fill the GPU, the partial Gram matrices of
+ * the element chunks go to a fixed device array of XLMIMO_NOALLOC_SCRATCH_MIB
+ * MiB that every GPU which loads this library holds until the process exits.
+ * A call whose split needs more than that (B x chunks x K x K x 16 bytes) is
+ * rejected with XLMIMO_EINVAL and a message saying how much it needed;
+ * nothing is enqueued.  Every call shares the array and it keeps the last
+ * call's contents; nothing in it needs to start at zero, because each chunk's
+ * partial is written in full before it is summed.  Calls that overlap on the
+ * GPU (on different streams, or from different host threads) race on it:
+ * serialise them.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) once for that device; make that first call
+ * before any stream capture.  No cudaMalloc, cudaFree or allocating library
+ * routine is called. */
+int xlmimo_channel_gram_noalloc(const xlmimo_array* arr, const double* users, int K, int B, int prec,
+                                double* gram, void* stream);
+
 /* Closed-form Gram matrices of "modified ZF" (Sec. V-B): diagonal P_i / P
  * from Eq. (4), off-diagonal rho_ij sqrt(P_i P_j) / P with rho_ij from
  * Eq. (6) (SPM correlation).  Written for the PNUSW model exactly as the

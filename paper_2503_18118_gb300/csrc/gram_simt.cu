@@ -310,3 +310,41 @@ int launch_gram_f32(const Geom& g, const double* users, int K, int B, double* gr
 }
 
 }  // namespace xl
+
+namespace xl {
+
+// Same element split and kernels as launch_gram_f64 / launch_gram_f32, with
+// the partial Gram matrices written to caller-provided device scratch instead
+// of stream-ordered allocations.  Rejects the call (nothing enqueued) when the
+// split needs more than scratch_bytes.
+int launch_gram_into_scratch(const Geom& g, const double* users, int K, int B, int prec, double* gram,
+                             double* scratch, size_t scratch_bytes, cudaStream_t st) {
+    int tile = prec == XLMIMO_F64 ? F64_T : REF_SPAN;
+    int S = choose_split(g.N, B, tile, 4);
+    int64_t tiles = (g.N + tile - 1) / tile;
+    int64_t chunk = ((tiles + S - 1) / S) * tile;
+    S = (int)((g.N + chunk - 1) / chunk);
+    size_t need = S > 1 ? (size_t)B * S * K * K * sizeof(double2) : 0;
+    if (need > scratch_bytes) {
+        set_error("this batch splits each trial into %d element chunks and needs %zu bytes of scratch; the static "
+                  "scratch holds %zu bytes (use fewer trials per call, or xlmimo_channel_gram)",
+                  S, need, scratch_bytes);
+        return XLMIMO_EINVAL;
+    }
+    double2* out = (double2*)(S == 1 ? gram : scratch);
+    dim3 grid(B, S);
+    if (prec == XLMIMO_F64) {
+        gram_f64_kernel<<<grid, F64_THREADS, 0, st>>>(g, users, K, S, chunk, out);
+    } else {
+        F32Plan p = plan_f32(K);
+        cudaError_t e = cudaFuncSetAttribute(gram_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        if (e != cudaSuccess) return cuda_status(e, "gram_f32 attribute");
+        gram_f32_kernel<<<grid, p.threads, p.smem, st>>>(g, users, K, p.nb, p.nblk, p.ssub, p.tps, p.ks, S, chunk,
+                                                         out);
+    }
+    int rc = cuda_status(cudaGetLastError(), "gram launch");
+    if (!rc && S > 1) rc = launch_reduce_partials(scratch, S, K, B, gram, st);
+    return rc;
+}
+
+}  // namespace xl

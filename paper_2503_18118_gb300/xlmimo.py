@@ -51,7 +51,7 @@ class SweepResult(ctypes.Structure):
                 ("gram_err", ctypes.POINTER(ctypes.c_double)), ("sat_mean", ctypes.c_double * 3)]
 
 
-EXPORTS = ("xlmimo_channel_gram", "xlmimo_corr_closed_form", "xlmimo_beamform", "xlmimo_sumrate",
+EXPORTS = ("xlmimo_channel_gram", "xlmimo_channel_gram_noalloc", "xlmimo_corr_closed_form", "xlmimo_beamform", "xlmimo_sumrate",
            "xlmimo_saturation", "xlmimo_saturation_analytic", "xlmimo_capacity_sweep", "xlmimo_last_error",
            "xlmimo_version")
 
@@ -70,6 +70,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L = ctypes.CDLL(_build.LIB)
     vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
     L.xlmimo_channel_gram.argtypes = [ctypes.POINTER(Array), vp, i32, i32, i32, vp, vp]
+    L.xlmimo_channel_gram_noalloc.argtypes = [ctypes.POINTER(Array), vp, i32, i32, i32, vp, vp]
     L.xlmimo_corr_closed_form.argtypes = [ctypes.POINTER(Array), vp, i32, i32, vp, vp]
     L.xlmimo_beamform.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp]
     L.xlmimo_sumrate.argtypes = [vp, i32, i32, vp, vp, vp]
@@ -126,6 +127,24 @@ def xlmimo_channel_gram(arr: Array, users: torch.Tensor, prec: int = F32, gram: 
         gram = torch.empty((B, K, K), dtype=torch.complex128, device=users.device)
     _check(lib().xlmimo_channel_gram(ctypes.byref(arr), _dev(users, torch.float64, "users", (B, K, 2)), K, B,
                                      int(prec), _dev(gram, torch.complex128, "gram", (B, K, K)), _stream(stream)))
+    return gram
+
+
+def xlmimo_channel_gram_noalloc(arr: Array, users: torch.Tensor, prec: int = F32, gram: torch.Tensor | None = None,
+                                stream=None) -> torch.Tensor:
+    """Exact Gram matrices like xlmimo_channel_gram, for callers that cannot
+    allocate device memory while they run (a host that reserves the GPU's
+    memory for its own pool, or a latency-critical loop that cannot accept
+    cudaMalloc / cudaFree).  The library itself allocates nothing here: the
+    split partial sums use a fixed 16 MiB device array, so a batch whose split
+    needs more is rejected.  Calls that overlap on the GPU race on that array.
+    Pass `gram` to avoid the one torch allocation this wrapper would make."""
+    B, K = users.shape[0], users.shape[1]
+    if gram is None:
+        gram = torch.empty((B, K, K), dtype=torch.complex128, device=users.device)
+    _check(lib().xlmimo_channel_gram_noalloc(ctypes.byref(arr), _dev(users, torch.float64, "users", (B, K, 2)), K, B,
+                                             int(prec), _dev(gram, torch.complex128, "gram", (B, K, K)),
+                                             _stream(stream)))
     return gram
 
 
