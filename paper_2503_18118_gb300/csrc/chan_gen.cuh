@@ -1,94 +1,128 @@
 // On-the-fly channel generation (Sec. II-B) shared by the FP32 SIMT and the
 // tensor-core Gram kernels.  Channel entries are produced in registers and
-// go straight into shared memory tiles; they are never written to HBM.
+// go straight into shared-memory tiles; they are never written to HBM.
 //
-// FP32 phase with an FP64 reference.  The phase 2 pi r_k(n) / lambda reaches
-// ~10^5 rad, far beyond FP32 resolution, so every kernel keeps, per user and
-// per span of REF_SPAN elements, a reference element n_c at the span centre
-// whose quantities are computed in FP64:
+// FP32 phase with an accurate per-span reference.  The phase 2 pi r_k(n)/lambda
+// reaches ~10^5 rad, far beyond FP32 resolution, so for every user and every
+// span of REF_SPAN elements a reference element n_c at the span centre is
+// evaluated to ~48 bits in double-float arithmetic (ff.cuh):
 //   frac0 = r(n_c)/lambda - rint(r(n_c)/lambda)          (cycles, |.| <= 1/2)
-//   A     = (spacing/lambda) (y_{n_c} - y_k) / r(n_c)     (d r / d n at n_c, cycles per element)
-// For element n = n_c + m, with u = m spacing/lambda and all lengths in
+//   A     = (spacing/lambda) (y_{n_c} - y_k) / r(n_c)     (dr/dn at n_c, cycles per element)
+// For element n = n_c + m, with u = m spacing/lambda and lengths in
 // wavelengths, the distance splits exactly into
 //   r(n) - r(n_c) = m A + R,   R = 2 u^2 x^2 / (r_c ((r_c + r - u)(r_c + r + u)))
 // (subtract the tangent line from r - r_c = (2 e_c u + u^2)/(r + r_c) and
-// simplify; no term cancels because r_c + r > |u| for x > 0).  m A is
-// formed as an exact FP32 product plus FMA residual against the FP64 slope
-// split in two floats, and every partial sum is reduced modulo one cycle
-// before it is added, so the phase error stays near 1e-6 rad for spans of
-// 128 elements at 3 m from a 16384-element 100 GHz array.
-// The planar-wave model is the linear term alone (R = 0).
+// simplify; no term cancels because r_c + r > |u| for x > 0).  m A is formed
+// as an exact FP32 product plus FMA residual against A held as two floats,
+// and every partial sum is reduced modulo one cycle before it is added; the
+// emulated worst-case phase error is ~1e-6 rad at 3 m from a 16384-element
+// 100 GHz array.  The planar-wave model is the linear term alone (R = 0).
 #pragma once
 
 #include "common.cuh"
+#include "ff.cuh"
 
 namespace xl {
 
-constexpr int REF_SPAN = 128;  // elements per FP64 phase reference
+constexpr int REF_SPAN = 128;  // elements per phase reference
 
-struct UserConst {  // per user, per kernel
-    float xl2;   // (x/lambda)^2
-    float x2x2;  // 2 (x/lambda)^2
-    float ampc;  // amplitude constant (model dependent, see make_user_const)
-    float pad;
+// Per launch, prepared on the host from the FP64 geometry.
+struct GenParams {
+    ff delta;       // element spacing [m]
+    ff inv_lambda;  // 1/lambda [1/m]
+    ff dprime;      // spacing / lambda
+    float dprime_f;
+    int model;
+    long long nm1;  // N - 1
 };
 
-struct UserRef {  // per user, per reference span
-    float frac0;
-    float a_hi, a_lo;
-    float e0;  // (y_{n_c} - y_k) / lambda
-    float r0;  // r(n_c) / lambda
-    float pad[3];
+// Per user, built once per CTA from the FP64 position.
+struct UserGeo {
+    ff x, y, x2;   // metres, metres^2
+    ff r0u, su;    // planar model: |user| and sin(theta)
+    float xl2;     // (x/lambda)^2
+    float x2x2;    // 2 (x/lambda)^2
+    float ampc;    // amplitude constant (model dependent)
+    int ok;        // valid position
 };
 
-__device__ __forceinline__ UserConst make_user_const(const Geom& g, double x, double y) {
-    UserConst c;
-    double xl = x * g.inv_lambda;
-    c.xl2 = (float)(xl * xl);
-    c.x2x2 = (float)(2.0 * xl * xl);
-    if (g.model == XLMIMO_FSPL_USW) {
-        c.ampc = (float)(1.0 / (4.0 * 3.14159265358979323846));  // lambda/(4 pi r) = 1/(4 pi r')
-    } else if (g.model == XLMIMO_PNUSW) {
-        c.ampc = (float)(sqrt(g.beta0) * sqrt(xl) * g.inv_lambda);  // times r'^{-3/2}
-    } else {
-        c.ampc = (float)(sqrt(g.beta0) / sqrt(x * x + y * y));  // constant over the array
-    }
-    c.pad = 0.f;
-    return c;
+// Per user, per reference span.
+struct UserRef {
+    float frac0, a_hi, a_lo, e0, r0;
+};
+
+inline GenParams make_gen_params(const Geom& g) {
+    auto split = [](double d) {
+        float h = (float)d;
+        return ff{h, (float)(d - (double)h)};
+    };
+    GenParams p;
+    p.delta = split(g.spacing);
+    p.inv_lambda = split(g.inv_lambda);
+    p.dprime = split(g.spacing * g.inv_lambda);
+    p.dprime_f = (float)(g.spacing * g.inv_lambda);
+    p.model = g.model;
+    p.nm1 = (long long)(g.N - 1);
+    return p;
 }
 
-// FP64 reference quantities of user (x, y) at element n_c.
-__device__ __forceinline__ UserRef make_user_ref(const Geom& g, double x, double y, int64_t nc) {
+__device__ __forceinline__ UserGeo make_user_geo(const Geom& g, double x, double y) {
+    UserGeo u;
+    u.ok = user_ok(x, y);
+    if (!u.ok) { x = 1.0; y = 0.0; }
+    u.x = ff_from_double(x);
+    u.y = ff_from_double(y);
+    u.x2 = ff_from_double(x * x);
+    u.x2.lo += (float)fma(x, x, -(double)u.x2.hi - (double)u.x2.lo);  // x^2 to ~2^-48
+    double r0 = sqrt(x * x + y * y);
+    u.r0u = ff_from_double(r0);
+    u.su = ff_from_double(y / r0);
+    double xl = x * g.inv_lambda;
+    u.xl2 = (float)(xl * xl);
+    u.x2x2 = (float)(2.0 * xl * xl);
+    if (g.model == XLMIMO_FSPL_USW)
+        u.ampc = (float)(1.0 / (4.0 * 3.14159265358979323846));  // lambda/(4 pi r) = 1/(4 pi r')
+    else if (g.model == XLMIMO_PNUSW)
+        u.ampc = (float)(sqrt(g.beta0) * sqrt(xl) * g.inv_lambda);  // times r'^{-3/2}
+    else
+        u.ampc = (float)(sqrt(g.beta0) / r0);
+    return u;
+}
+
+// Reference quantities of user u at element nc, in double-float.
+__device__ __forceinline__ UserRef make_user_ref(const GenParams& p, const UserGeo& u, long long nc) {
+    // y_{n_c} = (n_c - (N-1)/2) spacing = (2 n_c - (N-1)) * spacing / 2, exact integer split
+    ff half_idx = ff_from_int64(2 * nc - p.nm1);
+    half_idx.hi *= 0.5f;
+    half_idx.lo *= 0.5f;
+    ff ync = ff_mul(half_idx, p.delta);
     UserRef R;
-    double ync = element_y(nc, g.N, g.spacing);
-    double q0, A;
-    if (g.model == XLMIMO_UPW) {
-        double r0 = sqrt(x * x + y * y);
-        double s = y / r0;
-        q0 = (r0 - ync * s) * g.inv_lambda;
-        A = -g.spacing * s * g.inv_lambda;
+    ff q0, A;
+    if (p.model == XLMIMO_UPW) {
+        q0 = ff_mul(ff_sub(u.r0u, ff_mul(ync, u.su)), p.inv_lambda);
+        A = ff_neg(ff_mul(p.dprime, u.su));
         R.e0 = 0.f;
         R.r0 = 1.f;
     } else {
-        double e0 = ync - y;
-        double r0 = sqrt(fma(e0, e0, x * x));
-        q0 = r0 * g.inv_lambda;
-        A = g.spacing * g.inv_lambda * (e0 / r0);
-        R.e0 = (float)(e0 * g.inv_lambda);
-        R.r0 = (float)q0;
+        ff e0 = ff_sub(ync, u.y);
+        ff r0 = ff_sqrt(ff_add(u.x2, ff_mul(e0, e0)));
+        q0 = ff_mul(r0, p.inv_lambda);
+        A = ff_div(ff_mul(p.dprime, e0), r0);
+        R.e0 = e0.hi * p.inv_lambda.hi;
+        R.r0 = q0.hi;
     }
-    R.frac0 = (float)(q0 - rint(q0));
-    R.a_hi = (float)A;
-    R.a_lo = (float)(A - (double)R.a_hi);
-    R.pad[0] = R.pad[1] = R.pad[2] = 0.f;
+    R.frac0 = __fadd_rn(__fsub_rn(q0.hi, rintf(q0.hi)), q0.lo);
+    R.frac0 -= rintf(R.frac0);
+    R.a_hi = A.hi;
+    R.a_lo = A.lo;
     return R;
 }
 
 // Channel entry h_k(n_c + m) as FP32 complex (re, im) = amp (cos phi, -sin phi).
-__device__ __forceinline__ float2 gen_entry_f32(int model, float dprime, const UserConst& c, const UserRef& R,
-                                                int m) {
+__device__ __forceinline__ float2 gen_entry_f32(int model, float dprime, float xl2, float x2x2, float ampc,
+                                                const UserRef& R, int m) {
     float mf = (float)m;
-    // linear term m*A, exact product plus residual, reduced modulo one cycle
+    // linear term m*A: exact product plus residual, reduced modulo one cycle
     float p = mf * R.a_hi;
     float pe = fmaf(mf, R.a_hi, -p);
     float pf = p - rintf(p);
@@ -96,20 +130,20 @@ __device__ __forceinline__ float2 gen_entry_f32(int model, float dprime, const U
     g -= rintf(g);
     float amp;
     if (model == XLMIMO_UPW) {
-        amp = c.ampc;
+        amp = ampc;
     } else {
         float u = mf * dprime;
         float en = R.e0 + u;
-        float r2 = fmaf(en, en, c.xl2);
+        float r2 = fmaf(en, en, xl2);
         float rs = rsqrtf(r2);
         float rp = r2 * rs;
         float sum = R.r0 + rp;
         float den = R.r0 * ((sum - u) * (sum + u));
-        float rem = __fdividef(c.x2x2 * u * u, den);
+        float rem = __fdividef(x2x2 * u * u, den);
         rem -= rintf(rem);
         g += rem;
         g -= rintf(g);
-        amp = (model == XLMIMO_FSPL_USW) ? c.ampc * rs : c.ampc * rs * rsqrtf(rp);
+        amp = (model == XLMIMO_FSPL_USW) ? ampc * rs : ampc * rs * rsqrtf(rp);
     }
     float s, co;
     __sincosf(6.283185307179586f * g, &s, &co);

@@ -119,16 +119,31 @@ __global__ void __launch_bounds__(F64_THREADS) gram_f64_kernel(Geom g, const dou
 }
 
 // ---------------------------------------------------------------- FP32 ----
+// Tile layout in shared memory: row t (one element) holds the K users'
+// entries in 4-user blocks of 6 complex slots (4 used), so the 16-byte loads
+// of up to eight different blocks of one row hit distinct banks.
+//
+// Pair mapping.  The upper triangle of 4x4 complex blocks (nblk blocks) is
+// accumulated by (block, sub-stream) threads; sub-stream s owns elements
+// [s*tps, (s+1)*tps) of every tile.
+//   mode 1 (nb == 8, K = 29..32, 36 blocks, 8 sub-streams, 9 warps): warp w < 8
+//     is sub-stream w with lane = block 0..31, so each of its loads reads one
+//     row; warp 8 takes blocks 32..35 of all eight sub-streams.
+//   mode 0 (other K): thread -> (tid % nblk, tid / nblk).
 constexpr int F32_T = 64;          // elements per tile
 constexpr int F32_MAXTHREADS = 288;
+constexpr int F32_BLK = 6;         // complex slots per 4-user block in a tile row
 
 struct F32Plan {
     int nb;      // 4-user blocks per side
     int nblk;    // upper-triangle blocks
     int ssub;    // element sub-streams per tile
     int tps;     // elements per sub-stream per tile
+    int mode;
     int threads;
     int ks;      // row stride of the shared tile, in complex entries
+    int kp;      // users rounded up to a power of two (generation lanes per element)
+    int gen_threads;
     size_t smem;
 };
 
@@ -136,31 +151,43 @@ static F32Plan plan_f32(int K) {
     F32Plan p;
     p.nb = (K + 3) / 4;
     p.nblk = p.nb * (p.nb + 1) / 2;
-    p.ssub = 16;
-    while (p.ssub > 1 && p.nblk * p.ssub > F32_MAXTHREADS) p.ssub >>= 1;
+    if (p.nb == 8) {
+        p.mode = 1;
+        p.ssub = 8;
+        p.threads = 288;
+    } else {
+        p.mode = 0;
+        p.ssub = 16;
+        while (p.ssub > 1 && p.nblk * p.ssub > F32_MAXTHREADS) p.ssub >>= 1;
+        p.threads = ((p.nblk * p.ssub + 31) / 32) * 32;
+    }
     p.tps = F32_T / p.ssub;
-    p.threads = ((p.nblk * p.ssub + 31) / 32) * 32;
-    p.ks = 4 * p.nb + 4;
+    p.ks = F32_BLK * p.nb;
+    p.kp = 1;
+    while (p.kp < K) p.kp <<= 1;
+    int warps = p.threads / 32, gw = 1;
+    while (gw * 2 <= warps && gw * 2 <= 8) gw *= 2;
+    p.gen_threads = 32 * gw;
+    if (p.gen_threads < p.kp) p.gen_threads = p.kp;  // K > 32 needs two warps (always available)
     size_t tile = (size_t)F32_T * p.ks * sizeof(float2);
     size_t red = (size_t)p.nblk * p.ssub * 16 * sizeof(float2);
     size_t big = tile > red ? tile : red;
-    p.smem = big + XLMIMO_MAX_USERS * (sizeof(UserConst) + sizeof(UserRef)) + p.nblk * 2;
+    p.smem = big + XLMIMO_MAX_USERS * sizeof(UserGeo) + p.nblk * 2;
     return p;
 }
 
-__global__ void __launch_bounds__(F32_MAXTHREADS) gram_f32_kernel(Geom g, const double* __restrict__ users,
-                                                                 int K, int nb, int nblk, int ssub, int tps, int ks,
+__global__ void __launch_bounds__(F32_MAXTHREADS, 3) gram_f32_kernel(Geom g, GenParams gp,
+                                                                 const double* __restrict__ users, int K, F32Plan pl,
                                                                  int S, int64_t chunk, double2* __restrict__ out) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int nthr = nblk * ssub;
+    const int nb = pl.nb, nblk = pl.nblk, ssub = pl.ssub, tps = pl.tps, ks = pl.ks;
     size_t tile_bytes = (size_t)F32_T * ks * sizeof(float2);
     size_t red_bytes = (size_t)nblk * ssub * 16 * sizeof(float2);
     size_t big = tile_bytes > red_bytes ? tile_bytes : red_bytes;
     float2* H = reinterpret_cast<float2*>(smem);
     float2* red = reinterpret_cast<float2*>(smem);
-    UserConst* uc = reinterpret_cast<UserConst*>(smem + big);
-    UserRef* ur = reinterpret_cast<UserRef*>(smem + big + XLMIMO_MAX_USERS * sizeof(UserConst));
-    unsigned char* bi = reinterpret_cast<unsigned char*>(ur + XLMIMO_MAX_USERS);
+    UserGeo* ug = reinterpret_cast<UserGeo*>(smem + big);
+    unsigned char* bi = reinterpret_cast<unsigned char*>(ug + XLMIMO_MAX_USERS);
     unsigned char* bj = bi + nblk;
     __shared__ int bad;
 
@@ -173,12 +200,11 @@ __global__ void __launch_bounds__(F32_MAXTHREADS) gram_f32_kernel(Geom g, const 
             for (int ib = 0; ib <= jb; ++ib) { bi[q] = (unsigned char)ib; bj[q] = (unsigned char)jb; ++q; }
     }
     __syncthreads();
-    double xk = 0.0, yk = 0.0;
     if (tid < K) {
-        xk = users[((int64_t)b * K + tid) * 2];
-        yk = users[((int64_t)b * K + tid) * 2 + 1];
-        if (!user_ok(xk, yk)) atomicOr(&bad, 1);
-        uc[tid] = make_user_const(g, xk, yk);
+        double x = users[((int64_t)b * K + tid) * 2], y = users[((int64_t)b * K + tid) * 2 + 1];
+        UserGeo u = make_user_geo(g, x, y);
+        if (!u.ok) atomicOr(&bad, 1);
+        ug[tid] = u;
     }
     __syncthreads();
     double2* o = out + ((int64_t)b * S + s) * K * K;
@@ -186,12 +212,32 @@ __global__ void __launch_bounds__(F32_MAXTHREADS) gram_f32_kernel(Geom g, const 
         for (int e = tid; e < K * K; e += blockDim.x) o[e] = make_double2(nan(""), nan(""));
         return;
     }
-    const bool active = tid < nthr;
-    const int blk = active ? tid % nblk : 0;
-    const int sub = active ? tid / nblk : 0;
+    // pair mapping
+    int blk, sub;
+    bool active;
+    if (pl.mode == 1) {
+        const int w = tid >> 5, l = tid & 31;
+        if (w < 8) { blk = l; sub = w; } else { blk = 32 + (l & 3); sub = l >> 2; }
+        active = true;
+    } else {
+        active = tid < nblk * ssub;
+        blk = active ? tid % nblk : 0;
+        sub = active ? tid / nblk : 0;
+    }
     const int ib = bi[blk], jb = bj[blk];
-    const float dprime = (float)(g.spacing * g.inv_lambda);
-    const int kp = 4 * nb;  // padded user count (extra users generate zeros)
+    // generation mapping: thread -> fixed user, strided elements
+    const bool gen = tid < pl.gen_threads;
+    const int kmask = pl.kp - 1;
+    int lk = 0;
+    while ((1 << lk) < pl.kp) ++lk;
+    const int gk = tid & kmask;                  // user of this generating thread
+    const int gt0 = tid >> lk;                   // first element of this thread in a tile
+    const int gts = pl.gen_threads >> lk;        // element stride
+    const bool gen_user = gen && gk < K;
+    float xl2 = 0.f, x2x2 = 0.f, ampc = 0.f;
+    if (gen_user) { xl2 = ug[gk].xl2; x2x2 = ug[gk].x2x2; ampc = ug[gk].ampc; }
+    const int slot = (gk >> 2) * F32_BLK + (gk & 3);
+    UserRef ref = {0.f, 0.f, 0.f, 0.f, 1.f};
 
     float ar[16], ai[16];
 #pragma unroll
@@ -203,25 +249,25 @@ __global__ void __launch_bounds__(F32_MAXTHREADS) gram_f32_kernel(Geom g, const 
     for (int64_t n0 = nbeg; n0 < nend; n0 += F32_T) {
         if (((n0 - nbeg) % REF_SPAN) == 0) {
             nc = n0 + REF_SPAN / 2;
-            if (tid < K) ur[tid] = make_user_ref(g, xk, yk, nc);
+            if (gen_user) ref = make_user_ref(gp, ug[gk], (long long)nc);
         }
-        __syncthreads();
-        // generate the tile: entry (t, k) -> H[t * ks + k]
-        for (int e = tid; e < F32_T * kp; e += blockDim.x) {
-            int t = e / kp, k = e - t * kp;
-            int64_t n = n0 + t;
-            float2 h = make_float2(0.f, 0.f);
-            if (k < K && n < nend) h = gen_entry_f32(g.model, dprime, uc[k], ur[k], (int)(n - nc));
-            H[t * ks + k] = h;
+        __syncthreads();  // previous tile consumed
+        if (gen && gk < pl.kp) {
+            for (int t = gt0; t < F32_T; t += gts) {
+                int64_t n = n0 + t;
+                float2 h = make_float2(0.f, 0.f);
+                if (gen_user && n < nend) h = gen_entry_f32(gp.model, gp.dprime_f, xl2, x2x2, ampc, ref, (int)(n - nc));
+                if (gk < 4 * nb) H[t * ks + slot] = h;
+            }
         }
         __syncthreads();
         if (active) {
-            for (int tt = 0; tt < tps; ++tt) {
-                const float2* row = H + (sub * tps + tt) * ks;
-                float4 a01 = *reinterpret_cast<const float4*>(row + 4 * ib);
-                float4 a23 = *reinterpret_cast<const float4*>(row + 4 * ib + 2);
-                float4 c01 = *reinterpret_cast<const float4*>(row + 4 * jb);
-                float4 c23 = *reinterpret_cast<const float4*>(row + 4 * jb + 2);
+            const float2* rowp = H + (sub * tps) * ks;
+            for (int tt = 0; tt < tps; ++tt, rowp += ks) {
+                float4 a01 = *reinterpret_cast<const float4*>(rowp + F32_BLK * ib);
+                float4 a23 = *reinterpret_cast<const float4*>(rowp + F32_BLK * ib + 2);
+                float4 c01 = *reinterpret_cast<const float4*>(rowp + F32_BLK * jb);
+                float4 c23 = *reinterpret_cast<const float4*>(rowp + F32_BLK * jb + 2);
                 float are[4] = {a01.x, a01.z, a23.x, a23.z}, aim[4] = {a01.y, a01.w, a23.y, a23.w};
                 float cre[4] = {c01.x, c01.z, c23.x, c23.z}, cim[4] = {c01.y, c01.w, c23.y, c23.w};
 #pragma unroll
@@ -301,7 +347,7 @@ int launch_gram_f32(const Geom& g, const double* users, int K, int B, double* gr
     int rc = run_split(S, K, B, gram, &part, st);
     if (rc) return rc;
     dim3 grid(B, S);
-    gram_f32_kernel<<<grid, p.threads, p.smem, st>>>(g, users, K, p.nb, p.nblk, p.ssub, p.tps, p.ks, S, chunk,
+    gram_f32_kernel<<<grid, p.threads, p.smem, st>>>(g, make_gen_params(g), users, K, p, S, chunk,
                                                      (double2*)(S == 1 ? gram : part));
     rc = cuda_status(cudaGetLastError(), "gram_f32 launch");
     if (!rc && S > 1) rc = launch_reduce_partials(part, S, K, B, gram, st);
@@ -339,8 +385,7 @@ int launch_gram_into_scratch(const Geom& g, const double* users, int K, int B, i
         F32Plan p = plan_f32(K);
         cudaError_t e = cudaFuncSetAttribute(gram_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
         if (e != cudaSuccess) return cuda_status(e, "gram_f32 attribute");
-        gram_f32_kernel<<<grid, p.threads, p.smem, st>>>(g, users, K, p.nb, p.nblk, p.ssub, p.tps, p.ks, S, chunk,
-                                                         out);
+        gram_f32_kernel<<<grid, p.threads, p.smem, st>>>(g, make_gen_params(g), users, K, p, S, chunk, out);
     }
     int rc = cuda_status(cudaGetLastError(), "gram launch");
     if (!rc && S > 1) rc = launch_reduce_partials(scratch, S, K, B, gram, st);

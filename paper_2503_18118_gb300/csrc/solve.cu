@@ -40,37 +40,44 @@ __device__ __forceinline__ cd cdiv(cd a, cd b) {
 }
 
 // In-place lower Cholesky of the Hermitian K x K matrix A (row-major, lower
-// triangle used).  Returns 1 on success.  Also accumulates sum log2 L_kk.
-__device__ int chol_lower(cd* A, int K, double* log2det, int* flag) {
+// triangle used).  Returns 1 on success and sum_k log2 L_kk in *log2det;
+// dinv[k] = 1 / L_kk.  Column k is scaled during the pivot phase of column
+// k+1 (the trailing update of column k uses the unscaled column and 1/d_k),
+// so each column costs two barriers.
+__device__ int chol_lower(cd* A, int K, double* log2det, int* flag, double* dinv) {
     const int tid = threadIdx.x, nt = blockDim.x;
     double ld = 0.0;
     for (int k = 0; k < K; ++k) {
+        // pivot of column k; scale column k-1 by 1/L_{k-1,k-1}
         if (tid == 0) {
             double d = A[k * K + k].x;
             if (!(d > 0.0) || !isfinite(d)) {
                 *flag = 1;
             } else {
-                A[k * K + k] = cmk(sqrt(d), 0.0);
+                double l = sqrt(d);
+                A[k * K + k] = cmk(l, 0.0);
+                dinv[k] = 1.0 / l;
             }
+        }
+        if (k > 0) {
+            const double iv = dinv[k - 1];
+            for (int i = k + tid; i < K; i += nt) A[i * K + k - 1] = cmk(A[i * K + k - 1].x * iv, A[i * K + k - 1].y * iv);
         }
         __syncthreads();
         const int failed = *flag;
         __syncthreads();  // every thread has read the flag before anyone may reset it
         if (failed) return 0;
-        double lkk = A[k * K + k].x;
+        const double lkk = A[k * K + k].x;
         ld += log2(lkk);
-        for (int i = k + 1 + tid; i < K; i += nt) A[i * K + k] = cdivr(A[i * K + k], lkk);
-        __syncthreads();
-        int m = K - k - 1;  // trailing size
-        int tri = m * (m + 1) / 2;
-        for (int q = tid; q < tri; q += nt) {
-            // q -> (i, j) with k < j <= i, row-wise over the lower triangle
-            int r = (int)((sqrt(8.0 * q + 1.0) - 1.0) * 0.5);
-            while ((r + 1) * (r + 2) / 2 <= q) ++r;
-            while (r * (r + 1) / 2 > q) --r;
-            int c = q - r * (r + 1) / 2;
-            int i = k + 1 + r, j = k + 1 + c;
-            A[i * K + j] = csub(A[i * K + j], cmulc(A[i * K + k], A[j * K + k]));
+        // trailing update with the unscaled column: A_ij -= A_ik conj(A_jk) / d_k
+        const double id2 = dinv[k] * dinv[k];
+        const int m = K - k - 1;
+        for (int e = tid; e < m * m; e += nt) {
+            const int r = e / m, c = e - r * m;
+            if (c > r) continue;
+            const int i = k + 1 + r, j = k + 1 + c;
+            cd t = cmulc(A[i * K + k], A[j * K + k]);
+            A[i * K + j] = cmk(A[i * K + j].x - t.x * id2, A[i * K + j].y - t.y * id2);
         }
         __syncthreads();
     }
@@ -79,16 +86,16 @@ __device__ int chol_lower(cd* A, int K, double* log2det, int* flag) {
 }
 
 // X = L^{-1} (lower), by forward substitution on the columns of I in parallel.
-__device__ void tri_inverse(const cd* L, cd* X, int K) {
+__device__ void tri_inverse(const cd* L, cd* X, int K, const double* dinv) {
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int e = tid; e < K * K; e += nt) X[e] = cmk(0.0, 0.0);
     __syncthreads();
     for (int i = 0; i < K; ++i) {
-        double lii = L[i * K + i].x;
+        const double iv = dinv[i];
         for (int j = tid; j <= i; j += nt) {
             cd acc = cmk(i == j ? 1.0 : 0.0, 0.0);
             for (int k = j; k < i; ++k) acc = csub(acc, cmul(L[i * K + k], X[k * K + j]));
-            X[i * K + j] = cdivr(acc, lii);
+            X[i * K + j] = cmk(acc.x * iv, acc.y * iv);
         }
         __syncthreads();
     }
@@ -163,6 +170,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* 
     cd* G = X + KK;  // true Gram (mismatched only)
     double* p = reinterpret_cast<double*>(G + (matched ? 0 : KK));
     double* dg = p + XLMIMO_MAX_USERS;
+    __shared__ double dinv[XLMIMO_MAX_USERS];
     __shared__ int flag, piv, st;
     __shared__ double ld_cap;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -189,7 +197,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* 
         }
         __syncthreads();
         double ld = 0.0;
-        int ok = chol_lower(Z, K, &ld, &flag);
+        int ok = chol_lower(Z, K, &ld, &flag, dinv);
         if (tid == 0) {
             double s = 0.0;
             for (int k = 0; k < K; ++k) s += log2(p[k] / s2);
@@ -213,14 +221,14 @@ __global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* 
         }
         __syncthreads();
         double ld = 0.0;
-        int ok = chol_lower(Z, K, &ld, &flag);
+        int ok = chol_lower(Z, K, &ld, &flag, dinv);
         if (ok) {
             if (mmse_reuse && cap && tid == 0) {
                 double s = 0.0;
                 for (int k = 0; k < K; ++k) s += log2(p[k] / s2);
                 cap[b] = s + ld;
             }
-            tri_inverse(Z, X, K);  // X = L^{-1}
+            tri_inverse(Z, X, K, dinv);  // X = L^{-1}
             if (matched) {
                 for (int k = tid; k < K; k += nt) {
                     double acc = 0.0;
@@ -273,7 +281,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* 
                 }
                 __syncthreads();
                 double ld2 = 0.0;
-                int ok3 = chol_lower(Z, K, &ld2, &flag);
+                int ok3 = chol_lower(Z, K, &ld2, &flag, dinv);
                 if (tid == 0) {
                     double s = 0.0;
                     for (int k = 0; k < K; ++k) s += log2(p[k] / s2);
