@@ -29,26 +29,62 @@ struct cd {
 __device__ __forceinline__ cd cmk(double a, double b) { return {a, b}; }
 __device__ __forceinline__ cd cadd(cd a, cd b) { return {a.x + b.x, a.y + b.y}; }
 __device__ __forceinline__ cd csub(cd a, cd b) { return {a.x - b.x, a.y - b.y}; }
-__device__ __forceinline__ cd cmul(cd a, cd b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
-__device__ __forceinline__ cd cmulc(cd a, cd b) { return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y}; }  // a conj(b)
-__device__ __forceinline__ cd cconjmul(cd a, cd b) { return {a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x}; }  // conj(a) b
-__device__ __forceinline__ double cabs2(cd a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ cd cmul(cd a, cd b) { return {fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x)}; }
+__device__ __forceinline__ cd cmulc(cd a, cd b) { return {fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y)}; }  // a conj(b)
+__device__ __forceinline__ double cabs2(cd a) { return fma(a.x, a.x, a.y * a.y); }
 __device__ __forceinline__ cd cdivr(cd a, double r) { return {a.x / r, a.y / r}; }
 __device__ __forceinline__ cd cdiv(cd a, cd b) {
     double d = b.x * b.x + b.y * b.y;
     return {(a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d};
 }
+// acc + a b, acc - a b, acc - a conj(b), acc + conj(a) b: four FP64 FMAs each
+__device__ __forceinline__ cd cmac(cd acc, cd a, cd b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+    return acc;
+}
+__device__ __forceinline__ cd cmsub(cd acc, cd a, cd b) {
+    acc.x = fma(-a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(-a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+    return acc;
+}
+__device__ __forceinline__ cd cmsubc(cd acc, cd a, cd b) {
+    acc.x = fma(-a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(-a.y, b.x, acc.y);
+    acc.y = fma(a.x, b.y, acc.y);
+    return acc;
+}
+__device__ __forceinline__ cd cmacc(cd acc, cd a, cd b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+    return acc;
+}
+
+// Row r and column c of the q-th entry of a lower triangle stored row by
+// row (c <= r), without FP64 arithmetic.
+__device__ __forceinline__ void tri_index(int q, int* r, int* c) {
+    int rr = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+    while ((rr + 1) * (rr + 2) / 2 <= q) ++rr;
+    while (rr * (rr + 1) / 2 > q) --rr;
+    *r = rr;
+    *c = q - rr * (rr + 1) / 2;
+}
 
 // In-place lower Cholesky of the Hermitian K x K matrix A (row-major, lower
 // triangle used).  Returns 1 on success and sum_k log2 L_kk in *log2det;
-// dinv[k] = 1 / L_kk.  Column k is scaled during the pivot phase of column
-// k+1 (the trailing update of column k uses the unscaled column and 1/d_k),
-// so each column costs two barriers.
+// dinv[k] = 1 / L_kk.  Per column: pivot, column scale, trailing update of
+// the lower triangle (every lane of every warp busy in the update).
 __device__ int chol_lower(cd* A, int K, double* log2det, int* flag, double* dinv) {
     const int tid = threadIdx.x, nt = blockDim.x;
     double ld = 0.0;
     for (int k = 0; k < K; ++k) {
-        // pivot of column k; scale column k-1 by 1/L_{k-1,k-1}
         if (tid == 0) {
             double d = A[k * K + k].x;
             if (!(d > 0.0) || !isfinite(d)) {
@@ -59,25 +95,23 @@ __device__ int chol_lower(cd* A, int K, double* log2det, int* flag, double* dinv
                 dinv[k] = 1.0 / l;
             }
         }
-        if (k > 0) {
-            const double iv = dinv[k - 1];
-            for (int i = k + tid; i < K; i += nt) A[i * K + k - 1] = cmk(A[i * K + k - 1].x * iv, A[i * K + k - 1].y * iv);
-        }
         __syncthreads();
         const int failed = *flag;
-        __syncthreads();  // every thread has read the flag before anyone may reset it
-        if (failed) return 0;
-        const double lkk = A[k * K + k].x;
-        ld += log2(lkk);
-        // trailing update with the unscaled column: A_ij -= A_ik conj(A_jk) / d_k
-        const double id2 = dinv[k] * dinv[k];
+        if (failed) {
+            __syncthreads();  // every thread has read the flag before anyone may reset it
+            return 0;
+        }
+        const double iv = dinv[k];
+        ld += log2(A[k * K + k].x);
+        for (int i = k + 1 + tid; i < K; i += nt) A[i * K + k] = cmk(A[i * K + k].x * iv, A[i * K + k].y * iv);
+        __syncthreads();
         const int m = K - k - 1;
-        for (int e = tid; e < m * m; e += nt) {
-            const int r = e / m, c = e - r * m;
-            if (c > r) continue;
+        const int tri = m * (m + 1) / 2;
+        for (int q = tid; q < tri; q += nt) {
+            int r, c;
+            tri_index(q, &r, &c);
             const int i = k + 1 + r, j = k + 1 + c;
-            cd t = cmulc(A[i * K + k], A[j * K + k]);
-            A[i * K + j] = cmk(A[i * K + j].x - t.x * id2, A[i * K + j].y - t.y * id2);
+            A[i * K + j] = cmsubc(A[i * K + j], A[i * K + k], A[j * K + k]);  // -= L_ik conj(L_jk)
         }
         __syncthreads();
     }
@@ -85,17 +119,38 @@ __device__ int chol_lower(cd* A, int K, double* log2det, int* flag, double* dinv
     return 1;
 }
 
-// X = L^{-1} (lower), by forward substitution on the columns of I in parallel.
+// X = L^{-1} (lower triangular) by right-looking elimination on the identity:
+// for k = 0..K-1 scale row k by 1/L_kk, then subtract L_ik * row k from every
+// row i > k.  Each step updates the (K-k-1) x (k+1) block in parallel.
 __device__ void tri_inverse(const cd* L, cd* X, int K, const double* dinv) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int e = tid; e < K * K; e += nt) X[e] = cmk(0.0, 0.0);
+    for (int e = tid; e < K * K; e += nt) X[e] = cmk((e / K) == (e % K) ? 1.0 : 0.0, 0.0);
     __syncthreads();
-    for (int i = 0; i < K; ++i) {
-        const double iv = dinv[i];
-        for (int j = tid; j <= i; j += nt) {
-            cd acc = cmk(i == j ? 1.0 : 0.0, 0.0);
-            for (int k = j; k < i; ++k) acc = csub(acc, cmul(L[i * K + k], X[k * K + j]));
-            X[i * K + j] = cmk(acc.x * iv, acc.y * iv);
+    for (int k = 0; k < K; ++k) {
+        const double iv = dinv[k];
+        for (int j = tid; j <= k; j += nt) X[k * K + j] = cmk(X[k * K + j].x * iv, X[k * K + j].y * iv);
+        __syncthreads();
+        const int rows = K - k - 1, cols = k + 1;
+        for (int e = tid; e < rows * cols; e += nt) {
+            const int i = k + 1 + e / cols, j = e - (e / cols) * cols;
+            X[i * K + j] = cmsub(X[i * K + j], L[i * K + k], X[k * K + j]);
+        }
+        __syncthreads();
+    }
+}
+
+// M = X^H X for lower-triangular X, as the sum of the outer products of the
+// rows of X (row l is nonzero in columns 0..l): balanced element-parallel
+// rank-1 updates.
+__device__ void gram_of_lower(const cd* X, cd* M, int K) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < K * K; e += nt) M[e] = cmk(0.0, 0.0);
+    __syncthreads();
+    for (int l = 0; l < K; ++l) {
+        const int w = l + 1;
+        for (int e = tid; e < w * w; e += nt) {
+            const int r = e / w, c = e - r * w;
+            M[r * K + c] = cmacc(M[r * K + c], X[l * K + r], X[l * K + c]);  // += conj(X_lr) X_lc
         }
         __syncthreads();
     }
@@ -237,15 +292,8 @@ __global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* 
                 }
                 __syncthreads();
             } else {
-                // M = X^H X into Z (Z no longer needed)
-                for (int e = tid; e < KK; e += nt) {
-                    int r = e / K, c = e - r * K;
-                    int l0 = r > c ? r : c;
-                    cd acc = cmk(0.0, 0.0);
-                    for (int l = l0; l < K; ++l) acc = cadd(acc, cconjmul(X[l * K + r], X[l * K + c]));
-                    Z[e] = acc;
-                }
-                __syncthreads();
+                // M = X^H X into Z (the factor is no longer needed), then M back into X
+                gram_of_lower(X, Z, K);
                 for (int e = tid; e < KK; e += nt) X[e] = Z[e];
                 __syncthreads();
             }
@@ -311,17 +359,23 @@ __global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* 
             sinr[(int64_t)b * K + k] = v;
         }
     } else {
-        // row k of A = M G (M in X) formed on the fly
+        // A = M G (M in X) into Z, element-parallel with uniform dot length
+        for (int e = tid; e < KK; e += nt) {
+            const int r = e / K, c = e - r * K;
+            cd acc = cmk(0.0, 0.0);
+            for (int l = 0; l < K; ++l) acc = cmac(acc, X[r * K + l], G[l * K + c]);
+            Z[e] = acc;
+        }
+        __syncthreads();
         for (int k = tid; k < K; k += nt) {
-            double sig = 0.0, itf = 0.0, nz = 0.0;
+            double sig = p[k] * cabs2(Z[k * K + k]);
+            double itf = 0.0, nz = 0.0;
             for (int j = 0; j < K; ++j) {
-                cd a = cmk(0.0, 0.0);
-                for (int l = 0; l < K; ++l) a = cadd(a, cmul(X[k * K + l], G[l * K + j]));
-                if (j == k) sig = p[k] * cabs2(a);
-                else itf += p[j] * cabs2(a);
-                nz += cmulc(a, X[k * K + j]).x;  // (A M^H)_kk term
+                cd a = Z[k * K + j];
+                if (j != k) itf = fma(p[j], cabs2(a), itf);
+                nz += cmulc(a, X[k * K + j]).x;  // (A M^H)_kk
             }
-            sinr[(int64_t)b * K + k] = sig / (itf + s2 * nz);
+            sinr[(int64_t)b * K + k] = sig / fma(s2, nz, itf);
         }
     }
     if (tid == 0) status[b] = st;
