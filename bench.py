@@ -207,7 +207,7 @@ def main():
         dist.init_process_group("nccl")
     path = args.path
     if path == "auto":
-        path = "f32"
+        path = "bf16x3"
     prec = PATHS[path]
 
     B, K, N = wl.trials, wl.k, wl.n_ant

@@ -1,12 +1,356 @@
-// Tensor-core (tcgen05) exact Gram with BF16 hi/lo split channel entries.
+// Exact Gram matrices on the 5th-generation tensor cores (tcgen05), BF16
+// hi/lo split with FP32 accumulation in tensor memory.
+//
+// The complex Gram G = H^H H of K users is a real contraction over the
+// elements: with X = [Re H ; Im H] (2K rows, one column per element),
+//   Re G_ij = (X X^T)_{i,j} + (X X^T)_{K+i,K+j},  Im G_ij = (X X^T)_{i,K+j} - (X X^T)_{K+i,j}.
+// Each FP32 channel entry is split into two BF16 numbers v = hi + lo
+// (|v - hi - lo| <= 2^-18 |v|).  Stacking Y = [X_hi ; X_lo] (4K = 128 rows
+// for K <= 32), one M = N = 128 MMA stream accumulates D = Y Y^T, and
+//   X X^T ~= X_hi X_hi^T + X_hi X_lo^T + X_lo X_hi^T + X_lo X_lo^T
+// is the sum of D's four 64 x 64 blocks.
+//
+// Pipeline (one CTA per trial chunk, 9 warps):
+//   warps 0-7  generate 64-element stages: lane = user, warp = 8-element
+//              slice; each thread writes 16-byte rows of the K-major,
+//              128-byte-swizzled BF16 tile, fences the async proxy and
+//              arrives on the stage's "full" barrier;
+//   warp 8     allocates 128 TMEM columns; one thread waits for each full
+//              stage, issues four K=16 tcgen05.mma into TMEM and commits to
+//              the stage's "empty" barrier (generators reuse the stage once
+//              it fires) and, at the end, to "done";
+//   warps 0-3  read the accumulator back (tcgen05.ld), fold the blocks and
+//              write the complex Gram in FP64.
+// Every wait is bounded; a wait that gives up marks the trial (NaN output),
+// lets outstanding MMAs drain and frees the tensor memory.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "chan_gen.cuh"
 #include "common.cuh"
 
 namespace xl {
 
+constexpr int TC_STAGES = 3;
+constexpr int TC_T = 64;              // elements per stage
+constexpr int TC_ROWS = 128;          // Y rows (4 components x 32 users)
+constexpr int TC_STAGE_BYTES = TC_ROWS * TC_T * 2;  // 16 KB, BF16
+constexpr int TC_THREADS = 288;
+constexpr int TC_GEN_THREADS = 256;
+constexpr int TC_TMEM_COLS = 128;
+constexpr int TC_REF_SPAN = 256;      // elements per phase reference (4 stages)
+constexpr uint64_t TC_WAIT_NS = 4000000000ull;  // 4 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the phase with the given parity.  Every wait in this
+// kernel is a per-stage hand-off (microseconds); after TC_WAIT_NS of wall
+// time, or once another thread has aborted, it gives up, sets *abort and
+// returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 63u) {
+            if (*abort) return false;
+            if (global_ns() - t0 > TC_WAIT_NS) {
+                *abort = 1;
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// SMEM matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;              // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+    d |= (uint64_t)1 << 46;              // descriptor version
+    d |= (uint64_t)2 << 61;              // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major, M = N = 128.
+constexpr uint32_t TC_IDESC = (1u << 4)            // D format F32
+                              | (1u << 7)          // A format BF16
+                              | (1u << 10)         // B format BF16
+                              | ((128u >> 3) << 17)  // N / 8
+                              | ((128u >> 4) << 24); // M / 16
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+struct TcShared {
+    uint64_t full[TC_STAGES];
+    uint64_t empty[TC_STAGES];
+    uint64_t done;
+    uint32_t tmem_base;
+    int abort;
+    int bad;
+    UserGeo ug[32];
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 3) gram_tc_kernel(Geom g, GenParams gp, const double* __restrict__ users,
+                                                               int K, int S, int64_t chunk,
+                                                               double2* __restrict__ out) {
+    extern __shared__ unsigned char smem_raw[];
+    // stages must be 1024-byte aligned for the 128-byte swizzle
+    unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    unsigned char* stages = base;
+    TcShared* sh = reinterpret_cast<TcShared*>(base + TC_STAGES * TC_STAGE_BYTES);
+    float* fold = reinterpret_cast<float*>(base);  // epilogue reuses the stages: 128 x 65 floats
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int b = blockIdx.x, s = blockIdx.y;
+
+    if (tid == 0) {
+        for (int i = 0; i < TC_STAGES; ++i) {
+            mbar_init(&sh->full[i], TC_GEN_THREADS);
+            mbar_init(&sh->empty[i], 1);
+        }
+        mbar_init(&sh->done, 1);
+        sh->abort = 0;
+        sh->bad = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 8) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid < 32) {
+        double x = 1.0, y = 0.0;
+        if (tid < K) {
+            x = users[((int64_t)b * K + tid) * 2];
+            y = users[((int64_t)b * K + tid) * 2 + 1];
+        }
+        UserGeo u = make_user_geo(g, x, y);
+        if (tid < K && !u.ok) atomicOr(&sh->bad, 1);
+        sh->ug[tid] = u;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tmem_base;
+    volatile int* abort = &sh->abort;
+
+    const int64_t nbeg = (int64_t)s * chunk;
+    const int64_t nend = min(g.N, nbeg + chunk);
+    const int nst = (int)((nend - nbeg + TC_T - 1) / TC_T);
+
+    if (warp < 8) {
+        // ---------------- generators: lane = user, warp = 8-element slice
+        const int k = lane;
+        const bool live = k < K;
+        const float xl2 = sh->ug[k].xl2, x2x2 = sh->ug[k].x2x2, ampc = sh->ug[k].ampc;
+        UserRef ref = {0.f, 0.f, 0.f, 0.f, 1.f};
+        int64_t nc = 0;
+        for (int it = 0; it < nst; ++it) {
+            const int st = it % TC_STAGES;
+            if (it >= TC_STAGES && !mbar_wait(&sh->empty[st], ((it / TC_STAGES) - 1) & 1, abort)) break;
+            const int64_t n0 = nbeg + (int64_t)it * TC_T;
+            if (((n0 - nbeg) % TC_REF_SPAN) == 0) {
+                nc = n0 + TC_REF_SPAN / 2;
+                if (live) ref = make_user_ref(gp, sh->ug[k], (long long)nc);
+            }
+            uint32_t w[4][4];  // [component][packed pair]
+#pragma unroll
+            for (int i = 0; i < 8; i += 2) {
+                float2 h0 = make_float2(0.f, 0.f), h1 = make_float2(0.f, 0.f);
+                const int64_t na = n0 + warp * 8 + i;
+                if (live && na < nend) h0 = gen_entry_f32(gp.model, gp.dprime_f, xl2, x2x2, ampc, ref, (int)(na - nc));
+                if (live && na + 1 < nend)
+                    h1 = gen_entry_f32(gp.model, gp.dprime_f, xl2, x2x2, ampc, ref, (int)(na + 1 - nc));
+                __nv_bfloat16 rh0 = __float2bfloat16_rn(h0.x), rh1 = __float2bfloat16_rn(h1.x);
+                __nv_bfloat16 ih0 = __float2bfloat16_rn(h0.y), ih1 = __float2bfloat16_rn(h1.y);
+                __nv_bfloat16 rl0 = __float2bfloat16_rn(h0.x - __bfloat162float(rh0));
+                __nv_bfloat16 rl1 = __float2bfloat16_rn(h1.x - __bfloat162float(rh1));
+                __nv_bfloat16 il0 = __float2bfloat16_rn(h0.y - __bfloat162float(ih0));
+                __nv_bfloat16 il1 = __float2bfloat16_rn(h1.y - __bfloat162float(ih1));
+                w[0][i >> 1] = pack_bf16(rh0, rh1);
+                w[1][i >> 1] = pack_bf16(ih0, ih1);
+                w[2][i >> 1] = pack_bf16(rl0, rl1);
+                w[3][i >> 1] = pack_bf16(il0, il1);
+            }
+            unsigned char* sb = stages + st * TC_STAGE_BYTES;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int f = 32 * c + k;  // row of Y
+                const int rin = f & 7;
+                uint32_t addr = smem_u32(sb + (f >> 3) * 1024 + rin * 128 + ((warp ^ rin) << 4));
+                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(w[c][0]), "r"(w[c][1]),
+                             "r"(w[c][2]), "r"(w[c][3])
+                             : "memory");
+            }
+            fence_async_smem();
+            mbar_arrive(&sh->full[st]);
+        }
+    } else {
+        // ---------------- MMA issuer (one lane; the others wait at the warp barrier)
+        if (lane == 0) {
+        for (int it = 0; it < nst; ++it) {
+            const int st = it % TC_STAGES;
+            if (!mbar_wait(&sh->full[st], (it / TC_STAGES) & 1, abort)) break;
+            tc_fence_after();
+            const uint32_t sa = smem_u32(stages + st * TC_STAGE_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < TC_T / 16; ++kk) {
+                const uint64_t d = desc_sw128(sa + kk * 32);
+                umma(tmem, d, d, (it > 0 || kk > 0) ? 1u : 0u);
+            }
+            umma_commit(&sh->empty[st]);
+        }
+        umma_commit(&sh->done);  // fires once every issued MMA has completed
+        }
+        __syncwarp();
+    }
+
+    // ---------------- epilogue (warps 0-3 own TMEM lanes 0-127)
+    double2* o = out + ((int64_t)b * S + s) * K * K;
+    // every thread of the CTA waits for the accumulator (bounded), so the
+    // stage buffers are free for the fold
+    bool ok = mbar_wait(&sh->done, 0, abort);
+    tc_fence_after();
+    __syncthreads();
+    ok = ok && !*abort && !sh->bad;
+    if (ok && warp < 4) {
+        const int m = warp * 32 + lane;  // row of D
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        float v[32], u[32];
+#pragma unroll
+        for (int cb = 0; cb < 2; ++cb) {
+            tmem_ld32(trow + cb * 32, v);
+            tmem_ld32(trow + 64 + cb * 32, u);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) fold[m * 65 + cb * 32 + j] = v[j] + u[j];
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (ok) {
+        // R = P[0:64] + P[64:128] (P = row-folded D);  complex Gram from R
+        const int P = K * (K + 1) / 2;
+        for (int q = tid; q < P; q += TC_THREADS) {
+            int i = 0, rl = K, p = q;
+            while (p >= rl) { p -= rl; ++i; --rl; }
+            const int j = i + p;
+            auto R = [&](int r, int c) { return fold[r * 65 + c] + fold[(r + 64) * 65 + c]; };
+            const float re = R(i, j) + R(32 + i, 32 + j);
+            const float im = R(i, 32 + j) - R(32 + i, j);
+            if (i == j) {
+                o[i * K + i] = make_double2((double)re, 0.0);
+            } else {
+                o[i * K + j] = make_double2((double)re, (double)im);
+                o[j * K + i] = make_double2((double)re, -(double)im);
+            }
+        }
+    } else {
+        for (int e = tid; e < K * K; e += TC_THREADS) o[e] = make_double2(nan(""), nan(""));
+    }
+    __syncthreads();
+    if (warp == 8) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+    }
+}
+
+static size_t tc_smem_bytes() { return 1024 + TC_STAGES * TC_STAGE_BYTES + sizeof(TcShared); }
+
 int launch_gram_tc(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st) {
-    (void)g; (void)users; (void)K; (void)B; (void)gram; (void)st;
-    set_error("XLMIMO_BF16X3 is not available in this build");
-    return XLMIMO_EUNSUPPORTED;
+    if (K > 32) {
+        set_error("XLMIMO_BF16X3 supports K <= 32 in this build");
+        return XLMIMO_EUNSUPPORTED;
+    }
+    int dev = 0, major = 0, minor = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10 || minor != 3) {
+        set_error("XLMIMO_BF16X3 needs an sm_103 device (tcgen05)");
+        return XLMIMO_EUNSUPPORTED;
+    }
+    size_t smem = tc_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_status(e, "gram_tc attribute");
+    int S = choose_split(g.N, B, TC_REF_SPAN, 4);
+    int64_t spans = (g.N + TC_REF_SPAN - 1) / TC_REF_SPAN;
+    int64_t chunk = ((spans + S - 1) / S) * TC_REF_SPAN;
+    S = (int)((g.N + chunk - 1) / chunk);
+    double* part = nullptr;
+    if (S > 1) {
+        int rc = cuda_status(cudaMallocAsync((void**)&part, (size_t)B * S * K * K * sizeof(double2), st),
+                             "workspace allocation");
+        if (rc) return rc;
+    }
+    dim3 grid(B, S);
+    gram_tc_kernel<<<grid, TC_THREADS, smem, st>>>(g, make_gen_params(g), users, K, S, chunk,
+                                                   (double2*)(S == 1 ? gram : part));
+    int rc = cuda_status(cudaGetLastError(), "gram_tc launch");
+    if (!rc && S > 1) rc = launch_reduce_partials(part, S, K, B, gram, st);
+    if (part) cudaFreeAsync(part, st);
+    return rc;
 }
 
 }  // namespace xl

@@ -227,13 +227,12 @@ __global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* 
     double* dg = p + XLMIMO_MAX_USERS;
     __shared__ double dinv[XLMIMO_MAX_USERS];
     __shared__ int flag, piv, st;
-    __shared__ double ld_cap;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int b = blockIdx.x;
     const double2* gf = gfil + (int64_t)b * KK;
     const double2* gt = gtru + (int64_t)b * KK;
     const double s2 = noise[b];
-    if (tid == 0) { flag = 0; st = 0; ld_cap = 0.0; }
+    if (tid == 0) { flag = 0; st = 0; }
     for (int k = tid; k < K; k += nt) {
         double v = power[(int64_t)b * K + k];
         p[k] = (power_mode == XLMIMO_POWER_RXSNR) ? v * s2 / gt[k * K + k].x : v;

@@ -86,7 +86,27 @@ def test_gram_f32(xl, orc, model, N, K, B):
     assert normwise(G, R) <= 1e-5
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("model", [0, 1, 2])
+@pytest.mark.parametrize("N,K,B", [(1, 1, 3), (2, 3, 2), (63, 5, 4), (64, 32, 3), (65, 32, 3), (256, 4, 50),
+                                   (1000, 32, 3), (4099, 17, 5), (16384, 32, 2), (16384, 31, 2)])
+def test_gram_bf16x3(xl, orc, model, N, K, B):
+    """Tensor-core Gram (BF16 hi/lo split, FP32 accumulation): each product
+    carries at most ~2 x 2^-16 relative split error, so normwise <= 1e-4."""
+    users = inputs.users_polar(300 + N + K, B, K, (3.0, 30.0))
+    G = gpu_gram(xl, users, N, LAM100, xl.BF16X3, model)
+    R = orc.gram(model, N, LAM100, LAM100 / 2, 1.0, users)
+    assert normwise(G, R) <= 1e-4
+    assert np.allclose(G, np.conj(np.swapaxes(G, 1, 2)), rtol=0, atol=0)
+
+
+def test_gram_bf16x3_rejects_large_k(xl):
+    users = inputs.users_polar(5, 1, 33, (3.0, 30.0))
+    with pytest.raises(xl.XlmimoError) as e:
+        gpu_gram(xl, users, 256, LAM100, xl.BF16X3)
+    assert e.value.code == 6
+
+
+@pytest.mark.parametrize("prec", [0, 1, 3])
 def test_gram_split_path(xl, orc, prec):
     """A batch far smaller than the GPU splits the element range; the fixed-order
     sum of the partial Gram matrices must match."""
@@ -94,7 +114,7 @@ def test_gram_split_path(xl, orc, prec):
     N = 70001  # ragged against every tile size
     G = gpu_gram(xl, users, N, LAM100, prec)
     R = orc.gram(1, N, LAM100, LAM100 / 2, 1.0, users)
-    assert normwise(G, R) <= (f64_tol(users, N, LAM100) if prec == 0 else 1e-5)
+    assert normwise(G, R) <= {0: f64_tol(users, N, LAM100), 1: 1e-5, 3: 1e-4}[prec]
     G2 = gpu_gram(xl, users, N, LAM100, prec)
     assert np.array_equal(G, G2)  # deterministic
 
@@ -236,16 +256,18 @@ def test_saturation_analytic(xl, kind, a, b, K, freq):
         assert int(res[3]) == n
 
 
-def test_headline_pipeline_sampled(xl, orc):
+@pytest.mark.parametrize("prec,gtol,rtol", [(1, 1e-5, 1e-4), (3, 1e-4, 1e-3)])
+def test_headline_pipeline_sampled(xl, orc, prec, gtol, rtol):
     """Full-size batch (N = 16384, K = 32, 100 GHz, 10^4 trials) in the launch
     configuration the benchmark times; the oracle checks sampled trials end
-    to end (Gram, MMSE SINR, sum rate) and properties hold for all trials."""
+    to end (Gram, MMSE SINR, sum rate) and properties hold for all trials.
+    Sum-rate tolerance: 1e-4 (FP32 path), 1e-3 (BF16x3 tensor-core path)."""
     wl = inputs.HEADLINE
     users = wl.users()
     B, K, N = wl.trials, wl.k, wl.n_ant
     arr = xl.array(N, wl.wavelength, wl.spacing, 1.0, wl.model)
     U = dev(users)
-    G = xl.xlmimo_channel_gram(arr, U, xl.F32)
+    G = xl.xlmimo_channel_gram(arr, U, prec)
     snr = dev(wl.power())
     noise = dev(wl.noise())
     sinr, st, cap = xl.xlmimo_beamform(G, snr, noise, xl.MMSE, xl.POWER_RXSNR, capacity=True)
@@ -257,12 +279,12 @@ def test_headline_pipeline_sampled(xl, orc):
     assert (st.cpu().numpy() == 0).all()
     idx = np.array([0, 1, 4999, B - 1])
     R = orc.gram(wl.model, N, wl.wavelength, wl.spacing, 1.0, users[idx])
-    assert normwise(Gh[idx], R) <= 1e-5
+    assert normwise(Gh[idx], R) <= gtol
     s_ref, _, c_ref = orc.beamform(R, wl.power(len(idx)), wl.noise(len(idx)), xl.MMSE, 1, want_capacity=True)
     r_ref, _ = orc.sumrate(s_ref)
     r = rate.cpu().numpy()[idx]
-    assert np.max(np.abs(r - r_ref) / r_ref) <= 1e-4
-    assert np.max(np.abs(cap.cpu().numpy()[idx] - c_ref) / c_ref) <= 1e-4
+    assert np.max(np.abs(r - r_ref) / r_ref) <= rtol
+    assert np.max(np.abs(cap.cpu().numpy()[idx] - c_ref) / c_ref) <= rtol
     # diagonal of every trial against the FSPL received-power closed form
     Gc = xl.xlmimo_corr_closed_form(arr, U).cpu().numpy()
     d = np.real(np.einsum("bii->bi", Gh))
