@@ -118,16 +118,22 @@ __device__ __forceinline__ UserRef make_user_ref(const GenParams& p, const UserG
     return R;
 }
 
-// Channel entry h_k(n_c + m) as FP32 complex (re, im) = amp (cos phi, -sin phi).
+// x - rint(x) for |x| < 2^22 by adding and removing 1.5 * 2^23 (exact in
+// round-to-nearest), which keeps the reduction on the FMA pipe.
+__device__ __forceinline__ float frac_rn(float x) {
+    const float magic = 12582912.0f;
+    float t = __fsub_rn(__fadd_rn(x, magic), magic);
+    return __fsub_rn(x, t);
+}
+
+// Channel entry h_k(n_c + m) as FP32 complex (re, im) = amp (cos phi, -sin phi);
+// mf = (float)m, an exact small integer.
 __device__ __forceinline__ float2 gen_entry_f32(int model, float dprime, float xl2, float x2x2, float ampc,
-                                                const UserRef& R, int m) {
-    float mf = (float)m;
+                                                const UserRef& R, float mf) {
     // linear term m*A: exact product plus residual, reduced modulo one cycle
-    float p = mf * R.a_hi;
+    float p = __fmul_rn(mf, R.a_hi);
     float pe = fmaf(mf, R.a_hi, -p);
-    float pf = p - rintf(p);
-    float g = R.frac0 + pf + fmaf(mf, R.a_lo, pe);
-    g -= rintf(g);
+    float g = R.frac0 + frac_rn(p) + fmaf(mf, R.a_lo, pe);
     float amp;
     if (model == XLMIMO_UPW) {
         amp = ampc;
@@ -138,13 +144,12 @@ __device__ __forceinline__ float2 gen_entry_f32(int model, float dprime, float x
         float rs = rsqrtf(r2);
         float rp = r2 * rs;
         float sum = R.r0 + rp;
-        float den = R.r0 * ((sum - u) * (sum + u));
-        float rem = __fdividef(x2x2 * u * u, den);
-        rem -= rintf(rem);
-        g += rem;
-        g -= rintf(g);
+        float u2 = u * u;
+        float den = R.r0 * fmaf(sum, sum, -u2);  // r_c ((r_c + r)^2 - u^2), no cancellation
+        g += frac_rn(__fdividef(x2x2 * u2, den));
         amp = (model == XLMIMO_FSPL_USW) ? ampc * rs : ampc * rs * rsqrtf(rp);
     }
+    g = frac_rn(g);
     float s, co;
     __sincosf(6.283185307179586f * g, &s, &co);
     return make_float2(amp * co, -amp * s);

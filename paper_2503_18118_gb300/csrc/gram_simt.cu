@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(F32_MAXTHREADS, 3) gram_f32_kernel(Geom g, Gen
             for (int t = gt0; t < F32_T; t += gts) {
                 int64_t n = n0 + t;
                 float2 h = make_float2(0.f, 0.f);
-                if (gen_user && n < nend) h = gen_entry_f32(gp.model, gp.dprime_f, xl2, x2x2, ampc, ref, (int)(n - nc));
+                if (gen_user && n < nend) h = gen_entry_f32(gp.model, gp.dprime_f, xl2, x2x2, ampc, ref, (float)(int)(n - nc));
                 if (gk < 4 * nb) H[t * ks + slot] = h;
             }
         }

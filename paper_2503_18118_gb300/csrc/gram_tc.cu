@@ -137,10 +137,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
-    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
-}
-
 struct TcShared {
     uint64_t full[TC_STAGES];
     uint64_t empty[TC_STAGES];
@@ -216,23 +212,23 @@ __global__ void __launch_bounds__(TC_THREADS, 3) gram_tc_kernel(Geom g, GenParam
                 if (live) ref = make_user_ref(gp, sh->ug[k], (long long)nc);
             }
             uint32_t w[4][4];  // [component][packed pair]
+            const int rem = (int)min((int64_t)TC_T, nend - n0) - warp * 8;  // valid elements of this slice
+            const float mf0 = (float)(int)(n0 + warp * 8 - nc);
 #pragma unroll
             for (int i = 0; i < 8; i += 2) {
                 float2 h0 = make_float2(0.f, 0.f), h1 = make_float2(0.f, 0.f);
-                const int64_t na = n0 + warp * 8 + i;
-                if (live && na < nend) h0 = gen_entry_f32(gp.model, gp.dprime_f, xl2, x2x2, ampc, ref, (int)(na - nc));
-                if (live && na + 1 < nend)
-                    h1 = gen_entry_f32(gp.model, gp.dprime_f, xl2, x2x2, ampc, ref, (int)(na + 1 - nc));
-                __nv_bfloat16 rh0 = __float2bfloat16_rn(h0.x), rh1 = __float2bfloat16_rn(h1.x);
-                __nv_bfloat16 ih0 = __float2bfloat16_rn(h0.y), ih1 = __float2bfloat16_rn(h1.y);
-                __nv_bfloat16 rl0 = __float2bfloat16_rn(h0.x - __bfloat162float(rh0));
-                __nv_bfloat16 rl1 = __float2bfloat16_rn(h1.x - __bfloat162float(rh1));
-                __nv_bfloat16 il0 = __float2bfloat16_rn(h0.y - __bfloat162float(ih0));
-                __nv_bfloat16 il1 = __float2bfloat16_rn(h1.y - __bfloat162float(ih1));
-                w[0][i >> 1] = pack_bf16(rh0, rh1);
-                w[1][i >> 1] = pack_bf16(ih0, ih1);
-                w[2][i >> 1] = pack_bf16(rl0, rl1);
-                w[3][i >> 1] = pack_bf16(il0, il1);
+                if (live && i < rem) h0 = gen_entry_f32(gp.model, gp.dprime_f, xl2, x2x2, ampc, ref, mf0 + (float)i);
+                if (live && i + 1 < rem)
+                    h1 = gen_entry_f32(gp.model, gp.dprime_f, xl2, x2x2, ampc, ref, mf0 + (float)(i + 1));
+                // hi = RN_bf16(v), lo = RN_bf16(v - hi), two values per conversion
+                __nv_bfloat162 rh = __floats2bfloat162_rn(h0.x, h1.x), ih = __floats2bfloat162_rn(h0.y, h1.y);
+                float2 rhf = __bfloat1622float2(rh), ihf = __bfloat1622float2(ih);
+                __nv_bfloat162 rl = __floats2bfloat162_rn(h0.x - rhf.x, h1.x - rhf.y);
+                __nv_bfloat162 il = __floats2bfloat162_rn(h0.y - ihf.x, h1.y - ihf.y);
+                w[0][i >> 1] = *reinterpret_cast<uint32_t*>(&rh);
+                w[1][i >> 1] = *reinterpret_cast<uint32_t*>(&ih);
+                w[2][i >> 1] = *reinterpret_cast<uint32_t*>(&rl);
+                w[3][i >> 1] = *reinterpret_cast<uint32_t*>(&il);
             }
             unsigned char* sb = stages + st * TC_STAGE_BYTES;
 #pragma unroll

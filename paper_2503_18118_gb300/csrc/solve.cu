@@ -93,6 +93,7 @@ __device__ int chol_lower(cd* A, int K, double* log2det, int* flag, double* dinv
                 double l = sqrt(d);
                 A[k * K + k] = cmk(l, 0.0);
                 dinv[k] = 1.0 / l;
+                ld += log2(d);  // one thread: FP64 transcendentals are costly on this part
             }
         }
         __syncthreads();
@@ -102,7 +103,6 @@ __device__ int chol_lower(cd* A, int K, double* log2det, int* flag, double* dinv
             return 0;
         }
         const double iv = dinv[k];
-        ld += log2(A[k * K + k].x);
         for (int i = k + 1 + tid; i < K; i += nt) A[i * K + k] = cmk(A[i * K + k].x * iv, A[i * K + k].y * iv);
         __syncthreads();
         const int m = K - k - 1;
@@ -115,7 +115,7 @@ __device__ int chol_lower(cd* A, int K, double* log2det, int* flag, double* dinv
         }
         __syncthreads();
     }
-    *log2det = 2.0 * ld;
+    *log2det = ld;  // sum_k log2 d_k = 2 sum_k log2 L_kk, valid in thread 0
     return 1;
 }
 
