@@ -155,4 +155,83 @@ __device__ __forceinline__ float2 gen_entry_f32(int model, float dprime, float x
     return make_float2(amp * co, -amp * s);
 }
 
+// ---- paired generation on the packed FP32x2 pipe ----------------------------
+// Two consecutive elements of one user per call; every FP32 operation is a
+// packed two-lane instruction (the transcendental ones stay scalar).  The
+// algebra is that of gen_entry_f32 with some terms carried negated so that
+// each step is a single packed multiply, add or FMA.
+
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+__device__ __forceinline__ float rcp_approx(float x) {  // relative error ~2^-23
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float2 frac2(float2 x) {  // x - rint(x), |x| < 2^22
+    const float2 m = f2(12582912.0f), nm = f2(-12582912.0f);
+    float2 t = __fadd2_rn(__fadd2_rn(x, m), nm);
+    return __ffma2_rn(t, f2(-1.0f), x);
+}
+
+// Packed per-span constants of one user.
+struct PairConst {
+    float2 frac0, nahi, ahi, alo, e0, r0, xl2, x2x2, dp, ndp, ampc;
+};
+
+__device__ __forceinline__ PairConst make_pair_const(const UserRef& R, float dprime, float xl2, float x2x2,
+                                                     float ampc) {
+    PairConst c;
+    c.frac0 = f2(R.frac0);
+    c.nahi = f2(-R.a_hi);
+    c.ahi = f2(R.a_hi);
+    c.alo = f2(R.a_lo);
+    c.e0 = f2(R.e0);
+    c.r0 = f2(R.r0);
+    c.xl2 = f2(xl2);
+    c.x2x2 = f2(x2x2);
+    c.dp = f2(dprime);
+    c.ndp = f2(-dprime);
+    c.ampc = f2(ampc);
+    return c;
+}
+
+// Entries at offsets mf.x, mf.y from the span centre: re = amp cos(phi),
+// im = -amp sin(phi) for each of the two.
+template <int MODEL>
+__device__ __forceinline__ void gen_pair(const PairConst& c, float2 mf, float2& re, float2& im) {
+    const float2 m1 = f2(-1.0f);
+    float2 np = __fmul2_rn(mf, c.nahi);          // -p = -m a_hi (exact product)
+    float2 pe = __ffma2_rn(mf, c.ahi, np);       // m a_hi - p (exact residual)
+    float2 g = __fadd2_rn(c.frac0, __ffma2_rn(mf, c.alo, pe));
+    g = __ffma2_rn(frac2(np), m1, g);           // + frac(p)
+    float2 amp;
+    if (MODEL == XLMIMO_UPW) {
+        amp = c.ampc;
+    } else {
+        float2 u = __fmul2_rn(mf, c.dp);
+        float2 nu2 = __fmul2_rn(u, __fmul2_rn(mf, c.ndp));  // -u^2
+        float2 en = __fadd2_rn(c.e0, u);
+        float2 r2 = __ffma2_rn(en, en, c.xl2);
+        float2 rs = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+        float2 sum = __ffma2_rn(r2, rs, c.r0);      // r_c + r
+        float2 den = __fmul2_rn(c.r0, __ffma2_rn(sum, sum, nu2));
+        float2 inv = make_float2(rcp_approx(den.x), rcp_approx(den.y));
+        float2 nR = __fmul2_rn(__fmul2_rn(c.x2x2, nu2), inv);  // -R
+        g = __ffma2_rn(frac2(nR), m1, g);
+        amp = __fmul2_rn(c.ampc, rs);
+        if (MODEL == XLMIMO_PNUSW) {
+            float2 rp = __fmul2_rn(r2, rs);
+            amp = __fmul2_rn(amp, make_float2(rsqrtf(rp.x), rsqrtf(rp.y)));
+        }
+    }
+    g = __fmul2_rn(frac2(g), f2(6.283185307179586f));
+    float s0, c0, s1, c1;
+    __sincosf(g.x, &s0, &c0);
+    __sincosf(g.y, &s1, &c1);
+    re = __fmul2_rn(amp, make_float2(c0, c1));
+    im = __fmul2_rn(__fmul2_rn(amp, m1), make_float2(s0, s1));
+}
+
 }  // namespace xl

@@ -147,6 +147,7 @@ struct TcShared {
     UserGeo ug[32];
 };
 
+template <int MODEL>
 __global__ void __launch_bounds__(TC_THREADS, 3) gram_tc_kernel(Geom g, GenParams gp, const double* __restrict__ users,
                                                                int K, int S, int64_t chunk,
                                                                double2* __restrict__ out) {
@@ -200,8 +201,8 @@ __global__ void __launch_bounds__(TC_THREADS, 3) gram_tc_kernel(Geom g, GenParam
         // ---------------- generators: lane = user, warp = 8-element slice
         const int k = lane;
         const bool live = k < K;
-        const float xl2 = sh->ug[k].xl2, x2x2 = sh->ug[k].x2x2, ampc = sh->ug[k].ampc;
-        UserRef ref = {0.f, 0.f, 0.f, 0.f, 1.f};
+        const float xl2 = sh->ug[k].xl2, x2x2 = sh->ug[k].x2x2, ampc = live ? sh->ug[k].ampc : 0.f;
+        PairConst pc = make_pair_const(UserRef{0.f, 0.f, 0.f, 0.f, 1.f}, gp.dprime_f, xl2, x2x2, 0.f);
         int64_t nc = 0;
         for (int it = 0; it < nst; ++it) {
             const int st = it % TC_STAGES;
@@ -209,26 +210,27 @@ __global__ void __launch_bounds__(TC_THREADS, 3) gram_tc_kernel(Geom g, GenParam
             const int64_t n0 = nbeg + (int64_t)it * TC_T;
             if (((n0 - nbeg) % TC_REF_SPAN) == 0) {
                 nc = n0 + TC_REF_SPAN / 2;
-                if (live) ref = make_user_ref(gp, sh->ug[k], (long long)nc);
+                UserRef ref = make_user_ref(gp, sh->ug[k], (long long)nc);
+                pc = make_pair_const(ref, gp.dprime_f, xl2, x2x2, ampc);
             }
             uint32_t w[4][4];  // [component][packed pair]
             const int rem = (int)min((int64_t)TC_T, nend - n0) - warp * 8;  // valid elements of this slice
             const float mf0 = (float)(int)(n0 + warp * 8 - nc);
 #pragma unroll
             for (int i = 0; i < 8; i += 2) {
-                float2 h0 = make_float2(0.f, 0.f), h1 = make_float2(0.f, 0.f);
-                if (live && i < rem) h0 = gen_entry_f32(gp.model, gp.dprime_f, xl2, x2x2, ampc, ref, mf0 + (float)i);
-                if (live && i + 1 < rem)
-                    h1 = gen_entry_f32(gp.model, gp.dprime_f, xl2, x2x2, ampc, ref, mf0 + (float)(i + 1));
+                float2 re, im;
+                gen_pair<MODEL>(pc, make_float2(mf0 + (float)i, mf0 + (float)(i + 1)), re, im);
+                if (i >= rem) { re.x = 0.f; im.x = 0.f; }
+                if (i + 1 >= rem) { re.y = 0.f; im.y = 0.f; }
                 // hi = RN_bf16(v), lo = RN_bf16(v - hi), two values per conversion
-                __nv_bfloat162 rh = __floats2bfloat162_rn(h0.x, h1.x), ih = __floats2bfloat162_rn(h0.y, h1.y);
-                float2 rhf = __bfloat1622float2(rh), ihf = __bfloat1622float2(ih);
-                __nv_bfloat162 rl = __floats2bfloat162_rn(h0.x - rhf.x, h1.x - rhf.y);
-                __nv_bfloat162 il = __floats2bfloat162_rn(h0.y - ihf.x, h1.y - ihf.y);
+                __nv_bfloat162 rh = __floats2bfloat162_rn(re.x, re.y), ih = __floats2bfloat162_rn(im.x, im.y);
+                float2 rl = __ffma2_rn(__bfloat1622float2(rh), f2(-1.0f), re);
+                float2 il = __ffma2_rn(__bfloat1622float2(ih), f2(-1.0f), im);
+                __nv_bfloat162 rlb = __floats2bfloat162_rn(rl.x, rl.y), ilb = __floats2bfloat162_rn(il.x, il.y);
                 w[0][i >> 1] = *reinterpret_cast<uint32_t*>(&rh);
                 w[1][i >> 1] = *reinterpret_cast<uint32_t*>(&ih);
-                w[2][i >> 1] = *reinterpret_cast<uint32_t*>(&rl);
-                w[3][i >> 1] = *reinterpret_cast<uint32_t*>(&il);
+                w[2][i >> 1] = *reinterpret_cast<uint32_t*>(&rlb);
+                w[3][i >> 1] = *reinterpret_cast<uint32_t*>(&ilb);
             }
             unsigned char* sb = stages + st * TC_STAGE_BYTES;
 #pragma unroll
@@ -328,7 +330,10 @@ int launch_gram_tc(const Geom& g, const double* users, int K, int B, double* gra
         return XLMIMO_EUNSUPPORTED;
     }
     size_t smem = tc_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = g.model == XLMIMO_PNUSW ? gram_tc_kernel<XLMIMO_PNUSW>
+              : g.model == XLMIMO_UPW   ? gram_tc_kernel<XLMIMO_UPW>
+                                        : gram_tc_kernel<XLMIMO_FSPL_USW>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e, "gram_tc attribute");
     int S = choose_split(g.N, B, TC_REF_SPAN, 4);
     int64_t spans = (g.N + TC_REF_SPAN - 1) / TC_REF_SPAN;
@@ -341,8 +346,7 @@ int launch_gram_tc(const Geom& g, const double* users, int K, int B, double* gra
         if (rc) return rc;
     }
     dim3 grid(B, S);
-    gram_tc_kernel<<<grid, TC_THREADS, smem, st>>>(g, make_gen_params(g), users, K, S, chunk,
-                                                   (double2*)(S == 1 ? gram : part));
+    kern<<<grid, TC_THREADS, smem, st>>>(g, make_gen_params(g), users, K, S, chunk, (double2*)(S == 1 ? gram : part));
     int rc = cuda_status(cudaGetLastError(), "gram_tc launch");
     if (!rc && S > 1) rc = launch_reduce_partials(part, S, K, B, gram, st);
     if (part) cudaFreeAsync(part, st);
