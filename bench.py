@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--path", default="auto", choices=["auto", "f64", "f32", "bf16x3"])
     ap.add_argument("--trials", type=int, default=None)
+    ap.add_argument("--chunks", type=int, default=0, help="pipeline pieces per step (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-baseline", action="store_true")
     return ap.parse_args()
@@ -219,32 +220,23 @@ def main():
     snr = torch.from_numpy(wl.power()).cuda()
     noise = torch.from_numpy(wl.noise()).cuda()
     G = torch.empty((B, K, K), dtype=torch.complex128, device="cuda")
-    Gc = torch.empty_like(G)
-    sinr = torch.empty((B, K), dtype=torch.float64, device="cuda")
-    sinr2 = torch.empty_like(sinr)
-    status = torch.empty((B,), dtype=torch.int32, device="cuda")
-    cap = torch.empty((B,), dtype=torch.float64, device="cuda")
-    rate = torch.empty((B,), dtype=torch.float64, device="cuda")
-    rate2 = torch.empty_like(rate)
-    stats = torch.empty((3,), dtype=torch.float64, device="cuda")
-    stats2 = torch.empty_like(stats)
-    sat = torch.empty((B, 3), dtype=torch.float64, device="cuda")
     flush = torch.empty((64 << 20,), dtype=torch.float32, device="cuda")  # 256 MB > L2
 
-    def step(gram_prec, ev=None):
-        if ev is not None:
-            ev[0].record(stream)
-        xl.xlmimo_channel_gram(arr, U, gram_prec, G)
-        if ev is not None:
-            ev[1].record(stream)
-        xl.xlmimo_beamform(G, snr, noise, xl.MMSE, xl.POWER_RXSNR, capacity=True, sinr=sinr, status=status, cap=cap)
-        xl.xlmimo_sumrate(sinr, rate, stats)
-        xl.xlmimo_corr_closed_form(arr, U, Gc)
-        xl.xlmimo_beamform(Gc, snr, noise, xl.ZF, xl.POWER_RXSNR, gram_true=G, sinr=sinr2, status=status)
-        xl.xlmimo_sumrate(sinr2, rate2, stats2)
-        xl.xlmimo_saturation(U, 0.9, wl.spacing, sat)
+    out = xl.McBuffers(B, K)
 
-    launches_per_step = 1 + 1 + 2 + 1 + 1 + 2 + 1  # gram, beamform, sumrate+stats, closed, beamform, sumrate+stats, sat
+    def step(gram_prec, ev=None):
+        """The whole path over the batch through the pipelined C entry point."""
+        xl.xlmimo_mc_step(arr, U, snr, noise, out, prec=gram_prec, scheme=xl.MMSE, cf_scheme=xl.ZF,
+                          power_mode=xl.POWER_RXSNR, t=0.9, chunks=args.chunks)
+
+    def gram_only(gram_prec, ev):
+        ev[0].record(stream)
+        xl.xlmimo_channel_gram(arr, U, gram_prec, G)
+        ev[1].record(stream)
+
+    # per pipeline piece: gram, beamform, sumrate, closed form, beamform, sumrate, saturation; per step: 2 stats
+    pieces = args.chunks if args.chunks else (4 if B >= 4096 else (2 if B >= 1024 else 1))
+    launches_per_step = 7 * pieces + 2
 
     def timed(gram_prec, steps, warmup, sample_clocks=False):
         for _ in range(warmup):
@@ -257,12 +249,11 @@ def main():
         if sampler:
             sampler.start()
             time.sleep(0.3)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-                torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         for i in range(steps):
             flush.zero_()
             evs[i][0].record(stream)
-            step(gram_prec, (evs[i][2], evs[i][3]))
+            step(gram_prec)
             evs[i][1].record(stream)
         torch.cuda.synchronize()
         if world > 1:
@@ -270,7 +261,13 @@ def main():
         torch.cuda.synchronize()
         clocks = sampler.stop() if sampler else None
         total_ms = sum(e[0].elapsed_time(e[1]) for e in evs)
-        gram_ms = sum(e[2].elapsed_time(e[3]) for e in evs) / steps
+        # the dominant kernel alone, same launch and stream, right after the timed steps
+        gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.zero_()
+            gram_only(gram_prec, gev[i])
+        torch.cuda.synchronize()
+        gram_ms = sum(e[0].elapsed_time(e[1]) for e in gev) / steps
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
         if world > 1:
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -293,8 +290,8 @@ def main():
     for _ in range(2):
         U.copy_(users_pin, non_blocking=True)
         step(prec)
-        rate_pin.copy_(rate, non_blocking=True)
-        stats_pin.copy_(stats, non_blocking=True)
+        rate_pin.copy_(out.rate, non_blocking=True)
+        stats_pin.copy_(out.stats, non_blocking=True)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_steps = max(1, min(args.steps, 5))
@@ -302,8 +299,8 @@ def main():
     for _ in range(e2e_steps):
         U.copy_(users_pin, non_blocking=True)
         step(prec)
-        rate_pin.copy_(rate, non_blocking=True)
-        stats_pin.copy_(stats, non_blocking=True)
+        rate_pin.copy_(out.rate, non_blocking=True)
+        stats_pin.copy_(out.stats, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
@@ -325,7 +322,7 @@ def main():
     step(prec)
     torch.cuda.synchronize()
     r_ref, _ = oracle_pipeline(oracle, wl, users_h[idx])
-    r_gpu = rate.cpu().numpy()[idx]
+    r_gpu = out.rate.cpu().numpy()[idx]
     sumrate_rel_err = float(np.max(np.abs(r_gpu - r_ref) / np.abs(r_ref)))
 
     peaks = {}
@@ -333,20 +330,39 @@ def main():
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    # FP32 pipe peak from unit counts and clock: SMs x 128 FMA lanes x 2 flop x max SM clock
+    # peaks from unit counts and the maximum SM clock (per SM per clock:
+    # 128 FP32 FMA lanes, 16 MUFU transcendental units, 2 FP64 FMA lanes)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = sms * 128 * 2 * max_mhz * 1e6 / 1e12
+    clk = max_mhz * 1e6
+    entries = float(N) * K * B  # channel entries generated per launch
     gram_flops = 8.0 * N * K * (K + 1) / 2 * B  # complex MACs of the Hermitian half, 8 flop each
-    achieved = gram_flops / (gram_ms / 1e3) / 1e12
-    if path == "f64":
-        peak_v, peak_kind = 1.25, "nominal FP64 (no measured FP64 peak)"
+    if path == "bf16x3":
+        # generation-bound: each entry needs one reciprocal square root (distance,
+        # amplitude), one reciprocal (curvature remainder), one sine and one cosine
+        achieved = 4.0 * entries / (gram_ms / 1e3) / 1e12
+        peak_v = sms * 16 * clk / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_v, "unit": "Tops/s (MUFU)",
+                "frac": achieved / peak_v, "traffic": traffic_from_profile(path), "kernel": KERNEL_OF_PATH[path],
+                "kernel_ms": gram_ms,
+                "peak_source": f"MUFU: {sms} SMs x 16 ops/clk x {max_mhz:.0f} MHz (unit counts and max clock)",
+                "algorithmic": "4 transcendental ops (rsqrt, rcp, sin, cos) x N K channel entries per launch",
+                "tensor_tflops": 2.0 * 128 * 128 * N * B / (gram_ms / 1e3) / 1e12,
+                "tensor_peak_tflops": float(peaks.get("bf16_tflops", 1935.2))}
+    elif path == "f64":
+        achieved = gram_flops / (gram_ms / 1e3) / 1e12
+        peak_v = sms * 2 * 2 * clk / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_v, "unit": "TFLOP/s", "frac": achieved / peak_v,
+                "traffic": traffic_from_profile(path), "kernel": KERNEL_OF_PATH[path], "kernel_ms": gram_ms,
+                "peak_source": f"FP64 FMA: {sms} SMs x 2 lanes x 2 flop x {max_mhz:.0f} MHz",
+                "algorithmic": "8 flop x N K (K+1)/2 complex MACs per trial x trials per launch"}
     else:
-        peak_v, peak_kind = fp32_peak, f"FP32 FMA pipe: {sms} SMs x 128 lanes x 2 flop x {max_mhz:.0f} MHz"
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak_v, "unit": "TFLOP/s", "frac": achieved / peak_v,
-            "traffic": traffic_from_profile(path), "kernel": KERNEL_OF_PATH[path],
-            "kernel_ms": gram_ms, "peak_source": peak_kind,
-            "algorithmic": "8 flop x N K (K+1)/2 complex MACs per trial x trials per launch"}
+        achieved = gram_flops / (gram_ms / 1e3) / 1e12
+        peak_v = sms * 128 * 2 * clk / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_v, "unit": "TFLOP/s", "frac": achieved / peak_v,
+                "traffic": traffic_from_profile(path), "kernel": KERNEL_OF_PATH[path], "kernel_ms": gram_ms,
+                "peak_source": f"FP32 FMA: {sms} SMs x 128 lanes x 2 flop x {max_mhz:.0f} MHz",
+                "algorithmic": "8 flop x N K (K+1)/2 complex MACs per trial x trials per launch"}
 
     cpu = None
     if not args.no_cpu_baseline:

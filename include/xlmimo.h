@@ -238,6 +238,50 @@ typedef struct {
 
 int xlmimo_capacity_sweep(const xlmimo_sweep_cfg* cfg, xlmimo_sweep_result* res, void* stream);
 
+/* One Monte-Carlo step over a batch of trials: the whole path of Secs. II-V
+ * in one call.  For every trial: exact Gram (channel generated on the fly,
+ * at `prec`), receiver `scheme` on it with SINR, status and capacity, sum
+ * rate; the closed-form Gram of modified ZF (Sec. V-B) and the receiver
+ * `cf_scheme` built from it and judged on the exact channel, with its sum
+ * rate; and the per-trial saturation interval (Eqs. 15-16).
+ * The batch is cut into `chunks` pieces that flow through two streams: the
+ * Gram kernels run on `stream` while the FP64 receivers of the previous
+ * piece run on a second stream owned by the library (one per device,
+ * created on first use), so the generation/tensor-core work and the FP64
+ * solves overlap.  The call returns once everything is enqueued; all work is
+ * ordered before any later work on `stream`.  Concurrent calls on different
+ * streams of one device share the library's second stream and are
+ * serialised on it.  Batch statistics {mean, M2, count} of both rates are
+ * reduced over the whole batch in a fixed order. */
+typedef struct {
+    xlmimo_array arr;         /* array geometry and channel model */
+    int32_t prec;             /* xlmimo_prec of the exact Gram */
+    int32_t scheme;           /* xlmimo_scheme on the exact Gram */
+    int32_t cf_scheme;        /* xlmimo_scheme built from the closed form; -1 skips the closed-form path */
+    int32_t power_mode;       /* xlmimo_power_mode */
+    int32_t K, B;
+    int32_t chunks;           /* pipeline pieces, 1..64; 0 chooses automatically */
+    int32_t reserved;         /* must be 0 */
+    double t;                 /* saturation threshold in (0, 1); 0 skips the saturation interval */
+    const double* users;      /* device [B][K][2] */
+    const double* power;      /* device [B][K] */
+    const double* noise;      /* device [B] */
+    double* gram;             /* device [B][K][K] complex, written */
+    double* gram_cf;          /* device [B][K][K] complex, written (NULL if cf_scheme < 0) */
+    double* sinr;             /* device [B][K], written */
+    double* sinr_cf;          /* device [B][K], written (NULL if cf_scheme < 0) */
+    int32_t* status;          /* device [B], written */
+    int32_t* status_cf;       /* device [B], written (NULL if cf_scheme < 0) */
+    double* capacity;         /* device [B], written, or NULL */
+    double* rate;             /* device [B], written */
+    double* rate_cf;          /* device [B], written (NULL if cf_scheme < 0) */
+    double* stats;            /* device [3], written, or NULL */
+    double* stats_cf;         /* device [3], written, or NULL */
+    double* sat;              /* device [B][3], written (NULL if t == 0) */
+} xlmimo_mc_batch;
+
+int xlmimo_mc_step(const xlmimo_mc_batch* job, void* stream);
+
 /* Message of the last error on this host thread ("" if none). */
 const char* xlmimo_last_error(void);
 

@@ -1,5 +1,6 @@
 // Closed-form Gram matrices of "modified ZF" (Sec. V-B), replacing the
-// O(N K^2) inner products by O(K^2) formulas, FP64.
+// O(N K^2) inner products by O(K^2) formulas (FP64, except the sine, cosine
+// and magnitude of the spherical-model off-diagonals, see the kernel).
 //
 // PNUSW.  Diagonal: the received power of Eq. (4) over P,
 //   G~_ii = beta0 / (spacing x_i) * B_i,
@@ -31,18 +32,35 @@ __device__ __forceinline__ double2 cis_cycles(double q) {  // e^{j 2 pi q}
     return make_double2(c, s);
 }
 
+// Off-diagonal entries (i < j) come first in the index space, then the K
+// diagonal entries of every trial, so that each warp runs one kind.  The
+// spherical-model off-diagonals reduce the phase sgn (2 pi d / lambda - pi/4)
+// in FP64 (d from an FP32-seeded Newton square root) and evaluate its sine,
+// cosine and the magnitude in FP32: entries carry ~1e-7 relative error,
+// far below the 1e-4-level stationary-phase error of the formula itself.
 __global__ void closed_form_kernel(Geom g, const double* __restrict__ users, int K, int B,
                                    double2* __restrict__ gram) {
-    const int64_t P = (int64_t)K * (K + 1) / 2;
-    const int64_t total = (int64_t)B * P;
+    const int64_t P = (int64_t)K * (K - 1) / 2;
+    const int64_t n_off = (int64_t)B * P;
+    const int64_t total = n_off + (int64_t)B * K;
+    const float c2f = (float)(g.lambda * g.lambda / (16.0 * 3.14159265358979323846 * 3.14159265358979323846));
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t b = e / P;
-        int p = (int)(e - b * P);
-        // upper-triangle index p -> (i, j), row by row
-        int i = 0, rowlen = K;
-        while (p >= rowlen) { p -= rowlen; ++i; --rowlen; }
-        int j = i + p;
+        int64_t b;
+        int i, j;
+        if (e < n_off) {
+            b = e / P;
+            int p = (int)(e - b * P);
+            // strict upper-triangle index p -> (i, j), row by row
+            i = 0;
+            int rowlen = K - 1;
+            while (p >= rowlen) { p -= rowlen; ++i; --rowlen; }
+            j = i + 1 + p;
+        } else {
+            const int64_t d = e - n_off;
+            b = d / K;
+            i = j = (int)(d - b * K);
+        }
         const double* u = users + b * K * 2;
         double xi = u[2 * i], yi = u[2 * i + 1], xj = u[2 * j], yj = u[2 * j + 1];
         double2 v;
@@ -69,20 +87,25 @@ __global__ void closed_form_kernel(Geom g, const double* __restrict__ users, int
             v = make_double2(val, 0.0);
         } else {
             double dx = fabs(xi) - fabs(xj), dy = yi - yj;
-            double d = sqrt(dx * dx + dy * dy);
+            double d2 = fma(dx, dx, dy * dy);
+            float d0 = sqrtf((float)d2);
+            double d = (double)d0 + (d2 - (double)d0 * (double)d0) * (double)(0.5f / d0);
             double sg = dx > 0.0 ? 1.0 : -1.0;
-            double2 ph = cis_cycles(sg * (d * g.inv_lambda - 0.125));
-            double m;
+            double q = sg * fma(d, g.inv_lambda, -0.125);  // phase in cycles
+            float fr = (float)(q - rint(q));
+            float sn, cs;
+            __sincosf(6.283185307179586f * fr, &sn, &cs);
+            float df = (float)d, xif = (float)xi, xjf = (float)xj;
+            float m;
             if (g.model == XLMIMO_PNUSW)
-                m = g.beta0 / g.spacing * sqrt(g.lambda) * fabs(dx) / (d * sqrt(d) * sqrt(xi * xj));
+                m = (float)(g.beta0 / g.spacing * sqrt(g.lambda)) * fabsf((float)dx) / (df * sqrtf(df) * sqrtf(xif * xjf));
             else
-                m = g.lambda * g.lambda / (16.0 * 3.14159265358979323846 * 3.14159265358979323846) / g.spacing *
-                    sqrt(g.lambda / (d * xi * xj));
-            v = make_double2(m * ph.x, m * ph.y);
+                m = c2f / (float)g.spacing * sqrtf((float)g.lambda / (df * xif * xjf));
+            v = make_double2((double)(m * cs), (double)(m * sn));
         }
         double2* G = gram + b * K * K;
         if (i == j) {
-            G[i * K + i] = make_double2(v.x, g.model == XLMIMO_UPW ? 0.0 : v.y);
+            G[i * K + i] = make_double2(v.x, 0.0);
         } else {
             G[i * K + j] = v;
             G[j * K + i] = make_double2(v.x, -v.y);
@@ -91,7 +114,7 @@ __global__ void closed_form_kernel(Geom g, const double* __restrict__ users, int
 }
 
 int launch_closed_form(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st) {
-    int64_t total = (int64_t)B * K * (K + 1) / 2;
+    int64_t total = (int64_t)B * K * (K + 1) / 2;  // off-diagonal pairs plus diagonals
     int threads = 256;
     int64_t blocks = (total + threads - 1) / threads;
     int64_t cap = 16LL * num_sms();

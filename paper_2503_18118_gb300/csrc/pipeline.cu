@@ -1,0 +1,129 @@
+// xlmimo_mc_step: one Monte-Carlo step over a batch, pipelined over two
+// streams.  The exact-Gram kernels (channel generation on the FP32 and MUFU
+// pipes, contraction on the tensor cores) and the receivers (FP64 pipe) use
+// disjoint execution units, so piece c's Gram on the caller's stream runs
+// next to piece c-1's receivers on a library stream; events order each
+// piece's receivers after its Gram and the caller's stream after everything.
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace xl {
+
+int launch_stats_strided(const double* x, int B, int stride, double* out, cudaStream_t st);
+
+constexpr int PIPE_MAX_CHUNKS = 64;
+
+struct PipeState {
+    cudaStream_t side = nullptr;
+    cudaEvent_t gram_done[PIPE_MAX_CHUNKS];
+    cudaEvent_t side_done = nullptr;
+    bool ready = false;
+};
+
+static std::mutex g_pipe_mu;
+static std::vector<PipeState> g_pipe;
+
+static int pipe_state(PipeState** out) {
+    int dev = 0;
+    int rc = cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
+    if (rc) return rc;
+    if ((int)g_pipe.size() <= dev) g_pipe.resize(dev + 1);
+    PipeState& p = g_pipe[dev];
+    if (!p.ready) {
+        rc = cuda_status(cudaStreamCreateWithFlags(&p.side, cudaStreamNonBlocking), "side stream");
+        for (int i = 0; !rc && i < PIPE_MAX_CHUNKS; ++i)
+            rc = cuda_status(cudaEventCreateWithFlags(&p.gram_done[i], cudaEventDisableTiming), "pipeline event");
+        if (!rc) rc = cuda_status(cudaEventCreateWithFlags(&p.side_done, cudaEventDisableTiming), "pipeline event");
+        if (rc) return rc;
+        p.ready = true;
+    }
+    *out = &p;
+    return XLMIMO_OK;
+}
+
+static int launch_gram_prec(const Geom& g, const double* users, int K, int B, int prec, double* gram, cudaStream_t st) {
+    switch (prec) {
+        case XLMIMO_F64: return launch_gram_f64(g, users, K, B, gram, st);
+        case XLMIMO_F32: return launch_gram_f32(g, users, K, B, gram, st);
+        default: return launch_gram_tc(g, users, K, B, gram, st);
+    }
+}
+
+static int check_job(const xlmimo_mc_batch* j) {
+    if (!j) { set_error("job is NULL"); return XLMIMO_EINVAL; }
+    if (j->K < 1 || j->K > XLMIMO_MAX_USERS || j->B < 0) { set_error("K must be in [1, 64] and B >= 0"); return XLMIMO_EINVAL; }
+    if (j->prec != XLMIMO_F64 && j->prec != XLMIMO_F32 && j->prec != XLMIMO_BF16X3) { set_error("unknown precision"); return XLMIMO_EINVAL; }
+    if (j->scheme < XLMIMO_ZF || j->scheme > XLMIMO_MRC) { set_error("unknown scheme"); return XLMIMO_EINVAL; }
+    if (j->cf_scheme > XLMIMO_MRC || j->cf_scheme < -1) { set_error("unknown closed-form scheme"); return XLMIMO_EINVAL; }
+    if (j->power_mode != XLMIMO_POWER_ABS && j->power_mode != XLMIMO_POWER_RXSNR) { set_error("unknown power mode"); return XLMIMO_EINVAL; }
+    if (j->chunks < 0 || j->chunks > PIPE_MAX_CHUNKS || j->reserved != 0) { set_error("chunks must be in [0, 64], reserved 0"); return XLMIMO_EINVAL; }
+    if (!(j->t == 0.0 || (j->t > 0.0 && j->t < 1.0))) { set_error("t must be 0 or in (0, 1)"); return XLMIMO_EINVAL; }
+    if (j->B == 0) return XLMIMO_OK;
+    if (!j->users || !j->power || !j->noise || !j->gram || !j->sinr || !j->status || !j->rate) {
+        set_error("users, power, noise, gram, sinr, status and rate must be non-NULL");
+        return XLMIMO_EINVAL;
+    }
+    if (j->cf_scheme >= 0 && (!j->gram_cf || !j->sinr_cf || !j->status_cf || !j->rate_cf)) {
+        set_error("the closed-form path needs gram_cf, sinr_cf, status_cf and rate_cf");
+        return XLMIMO_EINVAL;
+    }
+    if (j->t > 0.0 && !j->sat) { set_error("sat must be non-NULL when t > 0"); return XLMIMO_EINVAL; }
+    return XLMIMO_OK;
+}
+
+}  // namespace xl
+
+using namespace xl;
+
+extern "C" int xlmimo_mc_step(const xlmimo_mc_batch* j, void* stream) {
+    clear_error();
+    int rc = check_job(j);
+    if (rc) return rc;
+    Geom g;
+    if ((rc = check_array(&j->arr, &g))) return rc;
+    if (j->B == 0) return XLMIMO_OK;
+    const int K = j->K, B = j->B;
+    int C = j->chunks;
+    if (C == 0) C = B >= 4096 ? 4 : (B >= 1024 ? 2 : 1);
+    if (C > B) C = B;
+    cudaStream_t s0 = as_stream(stream);
+    std::lock_guard<std::mutex> lk(g_pipe_mu);
+    PipeState* ps = nullptr;
+    if ((rc = pipe_state(&ps))) return rc;
+    cudaStream_t s1 = ps->side;
+    const size_t KK = (size_t)K * K;
+    for (int c = 0; c < C && !rc; ++c) {
+        const int b0 = (int)((int64_t)B * c / C), b1 = (int)((int64_t)B * (c + 1) / C);
+        const int nb = b1 - b0;
+        if (nb <= 0) continue;
+        const double* u = j->users + (size_t)b0 * K * 2;
+        double* gm = j->gram + (size_t)b0 * KK * 2;
+        rc = launch_gram_prec(g, u, K, nb, j->prec, gm, s0);
+        if (!rc) rc = cuda_status(cudaEventRecord(ps->gram_done[c], s0), "event record");
+        if (!rc) rc = cuda_status(cudaStreamWaitEvent(s1, ps->gram_done[c], 0), "stream wait");
+        if (rc) break;
+        const double* pw = j->power + (size_t)b0 * K;
+        const double* nz = j->noise + b0;
+        rc = launch_beamform(gm, nullptr, pw, nz, K, nb, j->scheme, j->power_mode, j->sinr + (size_t)b0 * K,
+                             j->status + b0, j->capacity ? j->capacity + b0 : nullptr, s1);
+        if (!rc) rc = launch_sumrate(j->sinr + (size_t)b0 * K, K, nb, j->rate + b0, nullptr, s1);
+        if (!rc && j->cf_scheme >= 0) {
+            double* gc = j->gram_cf + (size_t)b0 * KK * 2;
+            rc = launch_closed_form(g, u, K, nb, gc, s1);
+            if (!rc)
+                rc = launch_beamform(gc, gm, pw, nz, K, nb, j->cf_scheme, j->power_mode, j->sinr_cf + (size_t)b0 * K,
+                                     j->status_cf + b0, nullptr, s1);
+            if (!rc) rc = launch_sumrate(j->sinr_cf + (size_t)b0 * K, K, nb, j->rate_cf + b0, nullptr, s1);
+        }
+        if (!rc && j->t > 0.0) rc = launch_saturation(u, K, nb, j->t, g.spacing, j->sat + (size_t)b0 * 3, s1);
+    }
+    if (!rc && j->stats) rc = launch_stats_strided(j->rate, B, 1, j->stats, s1);
+    if (!rc && j->stats_cf && j->cf_scheme >= 0) rc = launch_stats_strided(j->rate_cf, B, 1, j->stats_cf, s1);
+    // the caller's stream waits for the side stream even after an error, so
+    // nothing enqueued above can outlive the caller's view of the step
+    int rc2 = cuda_status(cudaEventRecord(ps->side_done, s1), "event record");
+    if (!rc2) rc2 = cuda_status(cudaStreamWaitEvent(s0, ps->side_done, 0), "stream wait");
+    return rc ? rc : rc2;
+}

@@ -77,23 +77,33 @@ __device__ __forceinline__ void tri_index(int q, int* r, int* c) {
     *c = q - rr * (rr + 1) / 2;
 }
 
+// 1/sqrt(d) for d > 0 in FP64: FP32 seed and two Newton steps (the FP64 pipe
+// runs one warp instruction per ~64 cycles per scheduler whatever the active
+// lanes, so single-lane sqrt/divide sequences are kept short).
+__device__ __forceinline__ double rsqrt_f64(double d) {
+    if (d < 1e-30 || d > 1e30) return 1.0 / sqrt(d);  // outside the FP32 seed's range
+    double y = (double)rsqrtf((float)d);
+    y = y * fma(-0.5 * d, y * y, 1.5);
+    y = y * fma(-0.5 * d, y * y, 1.5);
+    return y;
+}
+
 // In-place lower Cholesky of the Hermitian K x K matrix A (row-major, lower
-// triangle used).  Returns 1 on success and sum_k log2 L_kk in *log2det;
-// dinv[k] = 1 / L_kk.  Per column: pivot, column scale, trailing update of
-// the lower triangle (every lane of every warp busy in the update).
-__device__ int chol_lower(cd* A, int K, double* log2det, int* flag, double* dinv) {
+// triangle used).  Returns 1 on success; dinv[k] = 1 / L_kk and piv[k] = L_kk^2
+// (for the log-determinant, summed lane-parallel by the caller).  Per column:
+// pivot, column scale, trailing update of the lower triangle.
+__device__ int chol_lower(cd* A, int K, int* flag, double* dinv, double* pivd) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    double ld = 0.0;
     for (int k = 0; k < K; ++k) {
         if (tid == 0) {
             double d = A[k * K + k].x;
             if (!(d > 0.0) || !isfinite(d)) {
                 *flag = 1;
             } else {
-                double l = sqrt(d);
-                A[k * K + k] = cmk(l, 0.0);
-                dinv[k] = 1.0 / l;
-                ld += log2(d);  // one thread: FP64 transcendentals are costly on this part
+                double y = rsqrt_f64(d);
+                A[k * K + k] = cmk(d * y, 0.0);
+                dinv[k] = y;
+                pivd[k] = d;
             }
         }
         __syncthreads();
@@ -115,8 +125,18 @@ __device__ int chol_lower(cd* A, int K, double* log2det, int* flag, double* dinv
         }
         __syncthreads();
     }
-    *log2det = ld;  // sum_k log2 d_k = 2 sum_k log2 L_kk, valid in thread 0
     return 1;
+}
+
+// sum_k log2(v[k] * scale) over k < K, evaluated by warp 0 with all lanes
+// busy and reduced by shuffles; the result is valid in thread 0.
+__device__ double warp0_sum_log2(const double* v, int K, double scale) {
+    double acc = 0.0;
+    if (threadIdx.x < 32) {
+        for (int k = threadIdx.x; k < K; k += 32) acc += log2(v[k] * scale);
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    }
+    return acc;
 }
 
 // X = L^{-1} (lower triangular) by right-looking elimination on the identity:
@@ -225,7 +245,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* 
     cd* G = X + KK;  // true Gram (mismatched only)
     double* p = reinterpret_cast<double*>(G + (matched ? 0 : KK));
     double* dg = p + XLMIMO_MAX_USERS;
-    __shared__ double dinv[XLMIMO_MAX_USERS];
+    __shared__ double dinv[XLMIMO_MAX_USERS], pivd[XLMIMO_MAX_USERS], sp[XLMIMO_MAX_USERS];
     __shared__ int flag, piv, st;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int b = blockIdx.x;
@@ -236,6 +256,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* 
     for (int k = tid; k < K; k += nt) {
         double v = power[(int64_t)b * K + k];
         p[k] = (power_mode == XLMIMO_POWER_RXSNR) ? v * s2 / gt[k * K + k].x : v;
+        sp[k] = s2 / p[k];  // MMSE diagonal loading sigma^2 / p_k
     }
     if (!matched)
         for (int e = tid; e < KK; e += nt) G[e] = cmk(gt[e].x, gt[e].y);
@@ -247,15 +268,14 @@ __global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* 
         for (int e = tid; e < KK; e += nt) {
             int r = e / K, c = e - r * K;
             double2 v = gt[e];
-            Z[e] = cmk(v.x + (r == c ? s2 / p[r] : 0.0), r == c ? 0.0 : v.y);
+            Z[e] = cmk(v.x + (r == c ? sp[r] : 0.0), r == c ? 0.0 : v.y);
         }
         __syncthreads();
-        double ld = 0.0;
-        int ok = chol_lower(Z, K, &ld, &flag, dinv);
+        int ok = chol_lower(Z, K, &flag, dinv, pivd);
+        double ld = ok ? warp0_sum_log2(pivd, K, 1.0) : 0.0;
+        double lp = warp0_sum_log2(p, K, 1.0 / s2);
         if (tid == 0) {
-            double s = 0.0;
-            for (int k = 0; k < K; ++k) s += log2(p[k] / s2);
-            cap[b] = ok ? s + ld : nan("");
+            cap[b] = ok ? lp + ld : nan("");
             flag = 0;
         }
         __syncthreads();
@@ -270,17 +290,16 @@ __global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* 
         for (int e = tid; e < KK; e += nt) {
             int r = e / K, c = e - r * K;
             double2 v = gf[e];
-            double add = (scheme == XLMIMO_MMSE && r == c) ? s2 / p[r] : 0.0;
+            double add = (scheme == XLMIMO_MMSE && r == c) ? sp[r] : 0.0;
             Z[e] = cmk(v.x + add, r == c ? 0.0 : v.y);
         }
         __syncthreads();
-        double ld = 0.0;
-        int ok = chol_lower(Z, K, &ld, &flag, dinv);
+        int ok = chol_lower(Z, K, &flag, dinv, pivd);
         if (ok) {
-            if (mmse_reuse && cap && tid == 0) {
-                double s = 0.0;
-                for (int k = 0; k < K; ++k) s += log2(p[k] / s2);
-                cap[b] = s + ld;
+            if (mmse_reuse && cap) {
+                double ld = warp0_sum_log2(pivd, K, 1.0);
+                double lp = warp0_sum_log2(p, K, 1.0 / s2);
+                if (tid == 0) cap[b] = lp + ld;
             }
             tri_inverse(Z, X, K, dinv);  // X = L^{-1}
             if (matched) {
@@ -302,7 +321,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* 
             for (int e = tid; e < KK; e += nt) {
                 int r = e / K, c = e - r * K;
                 double2 v = gf[e];
-                double add = (scheme == XLMIMO_MMSE && r == c) ? s2 / p[r] : 0.0;
+                double add = (scheme == XLMIMO_MMSE && r == c) ? sp[r] : 0.0;
                 Z[e] = cmk(v.x + add, v.y);
             }
             __syncthreads();
@@ -324,15 +343,14 @@ __global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* 
                 for (int e = tid; e < KK; e += nt) {
                     int r = e / K, c = e - r * K;
                     double2 v = gt[e];
-                    Z[e] = cmk(v.x + (r == c ? s2 / p[r] : 0.0), r == c ? 0.0 : v.y);
+                    Z[e] = cmk(v.x + (r == c ? sp[r] : 0.0), r == c ? 0.0 : v.y);
                 }
                 __syncthreads();
-                double ld2 = 0.0;
-                int ok3 = chol_lower(Z, K, &ld2, &flag, dinv);
+                int ok3 = chol_lower(Z, K, &flag, dinv, pivd);
+                double ld2 = ok3 ? warp0_sum_log2(pivd, K, 1.0) : 0.0;
+                double lp = warp0_sum_log2(p, K, 1.0 / s2);
                 if (tid == 0) {
-                    double s = 0.0;
-                    for (int k = 0; k < K; ++k) s += log2(p[k] / s2);
-                    cap[b] = ok3 ? s + ld2 : nan("");
+                    cap[b] = ok3 ? lp + ld2 : nan("");
                     flag = 0;
                 }
                 __syncthreads();

@@ -51,7 +51,15 @@ class SweepResult(ctypes.Structure):
                 ("gram_err", ctypes.POINTER(ctypes.c_double)), ("sat_mean", ctypes.c_double * 3)]
 
 
-EXPORTS = ("xlmimo_channel_gram", "xlmimo_channel_gram_noalloc", "xlmimo_corr_closed_form", "xlmimo_beamform", "xlmimo_sumrate",
+class McBatch(ctypes.Structure):
+    _fields_ = [("arr", Array), ("prec", ctypes.c_int32), ("scheme", ctypes.c_int32), ("cf_scheme", ctypes.c_int32),
+                ("power_mode", ctypes.c_int32), ("K", ctypes.c_int32), ("B", ctypes.c_int32),
+                ("chunks", ctypes.c_int32), ("reserved", ctypes.c_int32), ("t", ctypes.c_double)] + [
+        (n, ctypes.c_void_p) for n in ("users", "power", "noise", "gram", "gram_cf", "sinr", "sinr_cf", "status",
+                                       "status_cf", "capacity", "rate", "rate_cf", "stats", "stats_cf", "sat")]
+
+
+EXPORTS = ("xlmimo_mc_step", "xlmimo_channel_gram", "xlmimo_channel_gram_noalloc", "xlmimo_corr_closed_form", "xlmimo_beamform", "xlmimo_sumrate",
            "xlmimo_saturation", "xlmimo_saturation_analytic", "xlmimo_capacity_sweep", "xlmimo_last_error",
            "xlmimo_version")
 
@@ -70,6 +78,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L = ctypes.CDLL(_build.LIB)
     vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
     L.xlmimo_channel_gram.argtypes = [ctypes.POINTER(Array), vp, i32, i32, i32, vp, vp]
+    L.xlmimo_mc_step.argtypes = [ctypes.POINTER(McBatch), vp]
     L.xlmimo_channel_gram_noalloc.argtypes = [ctypes.POINTER(Array), vp, i32, i32, i32, vp, vp]
     L.xlmimo_corr_closed_form.argtypes = [ctypes.POINTER(Array), vp, i32, i32, vp, vp]
     L.xlmimo_beamform.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp]
@@ -128,6 +137,48 @@ def xlmimo_channel_gram(arr: Array, users: torch.Tensor, prec: int = F32, gram: 
     _check(lib().xlmimo_channel_gram(ctypes.byref(arr), _dev(users, torch.float64, "users", (B, K, 2)), K, B,
                                      int(prec), _dev(gram, torch.complex128, "gram", (B, K, K)), _stream(stream)))
     return gram
+
+
+class McBuffers:
+    """Device buffers of one Monte-Carlo step over B trials of K users."""
+
+    def __init__(self, B, K, device="cuda", capacity=True, closed_form=True, saturation=True):
+        f64, c128, i32 = torch.float64, torch.complex128, torch.int32
+        e = lambda shape, dt: torch.empty(shape, dtype=dt, device=device)
+        self.gram = e((B, K, K), c128)
+        self.gram_cf = e((B, K, K), c128) if closed_form else None
+        self.sinr = e((B, K), f64)
+        self.sinr_cf = e((B, K), f64) if closed_form else None
+        self.status = e((B,), i32)
+        self.status_cf = e((B,), i32) if closed_form else None
+        self.capacity = e((B,), f64) if capacity else None
+        self.rate = e((B,), f64)
+        self.rate_cf = e((B,), f64) if closed_form else None
+        self.stats = e((3,), f64)
+        self.stats_cf = e((3,), f64) if closed_form else None
+        self.sat = e((B, 3), f64) if saturation else None
+
+
+def xlmimo_mc_step(arr: Array, users: torch.Tensor, power: torch.Tensor, noise: torch.Tensor, out: McBuffers,
+                   prec: int = BF16X3, scheme: int = MMSE, cf_scheme: int = ZF, power_mode: int = POWER_RXSNR,
+                   t: float = 0.9, chunks: int = 0, stream=None) -> McBuffers:
+    """One pipelined Monte-Carlo step (exact Gram, receivers, rates, closed-form
+    path, saturation) over the batch; results land in `out`."""
+    B, K = users.shape[0], users.shape[1]
+    ptr = lambda x, dt, name, shape: None if x is None else _dev(x, dt, name, shape)
+    f64, c128, i32 = torch.float64, torch.complex128, torch.int32
+    job = McBatch(arr, int(prec), int(scheme), int(cf_scheme if out.gram_cf is not None else -1), int(power_mode),
+                  K, B, int(chunks), 0, float(t if out.sat is not None else 0.0),
+                  _dev(users, f64, "users", (B, K, 2)), _dev(power, f64, "power", (B, K)),
+                  _dev(noise, f64, "noise", (B,)), _dev(out.gram, c128, "gram", (B, K, K)),
+                  ptr(out.gram_cf, c128, "gram_cf", (B, K, K)), _dev(out.sinr, f64, "sinr", (B, K)),
+                  ptr(out.sinr_cf, f64, "sinr_cf", (B, K)), _dev(out.status, i32, "status", (B,)),
+                  ptr(out.status_cf, i32, "status_cf", (B,)), ptr(out.capacity, f64, "capacity", (B,)),
+                  _dev(out.rate, f64, "rate", (B,)), ptr(out.rate_cf, f64, "rate_cf", (B,)),
+                  ptr(out.stats, f64, "stats", (3,)), ptr(out.stats_cf, f64, "stats_cf", (3,)),
+                  ptr(out.sat, f64, "sat", (B, 3)))
+    _check(lib().xlmimo_mc_step(ctypes.byref(job), _stream(stream)))
+    return out
 
 
 def xlmimo_channel_gram_noalloc(arr: Array, users: torch.Tensor, prec: int = F32, gram: torch.Tensor | None = None,

@@ -6,8 +6,8 @@ Tolerances (stated by the accuracy targets of the path and written here):
     FP64 rounding bound of the phase (f64_tol) where that is larger
   * Gram, FP32 path:  normwise <= 1e-5
   * Gram, BF16x3 path: normwise <= 1e-4 (checked where the build has it)
-  * closed form: elementwise relative <= the FP64 rounding of its phase
-    2 pi d / lambda (both sides FP64 formulas)
+  * closed form: diagonal relative <= 1e-9 (FP64, with cancellation at N = 1); off-diagonal relative
+    <= 2e-6 (phase reduced in FP64, sine/cosine and magnitude in FP32)
   * receivers on the same Gram input: SINR relative <= 1e-9 (FP64 solves)
   * sum rate of the full FP32 path vs the oracle end to end: relative <= 1e-4
   * saturation: coordinates to 1e-13 relative, integer counts exact.
@@ -142,15 +142,23 @@ def test_closed_form(xl, orc, model):
         arr = xl.array(N, LAM100, None, 1.3, model)
         G = xl.xlmimo_corr_closed_form(arr, dev(users)).cpu().numpy()
         R = orc.closed_form(model, N, LAM100, LAM100 / 2, 1.3, users)
-        # entries carry the phase 2 pi d / lambda (pair distance d, or the
-        # distances to the array centre for the planar model), up to ~10^5 rad;
-        # its FP64 rounding bounds the agreement
+        # planar model: exact Dirichlet form in FP64, phases up to ~10^5 rad, so
+        # the FP64 rounding of the phase bounds the agreement.  Spherical models:
+        # the phase is reduced in FP64 and its sine, cosine and the magnitude are
+        # evaluated in FP32 (the formula's own stationary-phase error is >=1e-4),
+        # so each entry carries ~1e-7 relative error: tolerance 2e-6 relative
+        # off the diagonal.  The diagonal is FP64 throughout, but for a tiny
+        # aperture (N = 1) its two arctangents (two fractions of Eq. 4) cancel to
+        # ~1e-4 of their size, which amplifies rounding: 1e-9 relative.
         dmax = float(np.hypot(users[..., 0], users[..., 1]).max()) * 2
         tol = 8 * np.finfo(float).eps * (1 + 2 * math.pi * dmax / LAM100)
         if model == 2:
             assert normwise(G, R) <= tol
         else:
-            assert np.max(np.abs(G - R) / np.abs(R)) <= tol
+            off = ~np.eye(users.shape[1], dtype=bool)
+            rel = np.abs(G - R) / np.abs(R)
+            assert np.max(rel[:, off]) <= 2e-6
+            assert np.max(rel[:, ~off]) <= 1e-9
 
 
 def _solve_case(orc, seed, B, K, N, model=1, lam=LAM28):
@@ -312,8 +320,45 @@ def test_capacity_sweep_small(xl, orc):
                     for sch in (0, 1):
                         sr, stt, cap = orc.beamform(gf, p, np.ones(B), sch, 0, gram_true=gt, want_capacity=True)
                         rr, _ = orc.sumrate(sr)
-                        assert abs(out["rate"][ni, path, sch, si] - rr.mean()) <= tol * abs(rr.mean()) + 1e-12
+                        # the closed-form receiver inherits the ~1e-7 entry error of the closed form
+                        ptol = tol if path == 0 else max(tol, 1e-5)
+                        assert abs(out["rate"][ni, path, sch, si] - rr.mean()) <= ptol * abs(rr.mean()) + 1e-12
                         if path == 0 and sch == 1:
                             assert abs(out["capacity"][ni, si] - cap.mean()) <= tol * abs(cap.mean())
         sat = orc.saturation(users, 0.9, LAM28 / 2)
         assert np.allclose(out["sat_mean"], sat.mean(0), rtol=1e-12)
+
+
+@pytest.mark.parametrize("prec", [1, 3])
+@pytest.mark.parametrize("B,chunks", [(1, 0), (7, 3), (300, 1), (300, 4), (1000, 0), (999, 64)])
+def test_mc_step_matches_individual_calls(xl, prec, B, chunks):
+    """The pipelined step gives what the individual calls give, for any number
+    of pieces.  A piece smaller than the GPU splits each trial's element range
+    differently from the whole-batch call, so the Gram sums may round in a
+    different order: within the path's own accuracy class (FP32: normwise
+    1e-6, rates 1e-5; BF16x3, whose tensor-core accumulation is not
+    IEEE-sequential: 1e-4 and 1e-3); everything that does not depend on the
+    split is bit-identical."""
+    gtol, rtol = (1e-6, 1e-5) if prec == 1 else (1e-4, 1e-3)
+    K, N = 8, 2000
+    users = dev(inputs.users_polar(77, B, K, (3.0, 30.0)))
+    snr = dev(np.full((B, K), 10.0))
+    noise = dev(np.ones(B))
+    arr = xl.array(N, LAM100)
+    out = xl.McBuffers(B, K)
+    xl.xlmimo_mc_step(arr, users, snr, noise, out, prec=prec, scheme=xl.MMSE, cf_scheme=xl.ZF, chunks=chunks)
+    G = xl.xlmimo_channel_gram(arr, users, prec)
+    s, st, cap = xl.xlmimo_beamform(G, snr, noise, xl.MMSE, xl.POWER_RXSNR, capacity=True)
+    r, stats = xl.xlmimo_sumrate(s)
+    Gc = xl.xlmimo_corr_closed_form(arr, users)
+    s2, st2, _ = xl.xlmimo_beamform(Gc, snr, noise, xl.ZF, xl.POWER_RXSNR, gram_true=G)
+    r2, stats2 = xl.xlmimo_sumrate(s2)
+    sat = xl.xlmimo_saturation(users, 0.9, LAM100 / 2)
+    torch.cuda.synchronize()
+    assert normwise(out.gram.cpu().numpy(), G.cpu().numpy()) <= gtol
+    for a, b_ in ((out.gram_cf, Gc), (out.sat, sat), (out.status, st), (out.status_cf, st2)):
+        assert torch.equal(a, b_)
+    for a, b_ in ((out.sinr, s), (out.capacity, cap), (out.rate, r), (out.sinr_cf, s2), (out.rate_cf, r2),
+                  (out.stats[:1], stats[:1]), (out.stats_cf[:1], stats2[:1])):
+        assert torch.allclose(a, b_, rtol=rtol, atol=0)
+    assert out.stats[2] == B and out.stats_cf[2] == B
