@@ -235,7 +235,7 @@ def main():
         ev[1].record(stream)
 
     # per pipeline piece: gram, beamform, sumrate, closed form, beamform, sumrate, saturation; per step: 2 stats
-    pieces = args.chunks if args.chunks else (4 if B >= 4096 else (2 if B >= 1024 else 1))
+    pieces = args.chunks if args.chunks else 1
     launches_per_step = 7 * pieces + 2
 
     def timed(gram_prec, steps, warmup, sample_clocks=False):

@@ -316,7 +316,10 @@ __global__ void __launch_bounds__(TC_THREADS, 3) gram_tc_kernel(Geom g, GenParam
 
 static size_t tc_smem_bytes() { return 1024 + TC_STAGES * TC_STAGE_BYTES + sizeof(TcShared); }
 
-int launch_gram_tc(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st) {
+// ctas_per_sm > 0 caps the kernel's residency by sizing its shared memory, so
+// that kernels on other streams (the FP64 receivers of the pipelined step)
+// can run on the same SMs; 0 leaves the residency to the register budget.
+int launch_gram_tc(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st, int ctas_per_sm) {
     if (K > 32) {
         set_error("XLMIMO_BF16X3 supports K <= 32 in this build");
         return XLMIMO_EUNSUPPORTED;
@@ -330,6 +333,13 @@ int launch_gram_tc(const Geom& g, const double* users, int K, int B, double* gra
         return XLMIMO_EUNSUPPORTED;
     }
     size_t smem = tc_smem_bytes();
+    if (ctas_per_sm > 0) {
+        int dev = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        size_t want = (size_t)per_sm / (size_t)(ctas_per_sm + 1) + 1024;  // more than 1/(c+1) of the SM
+        if (want > smem) smem = want;
+    }
     auto kern = g.model == XLMIMO_PNUSW ? gram_tc_kernel<XLMIMO_PNUSW>
               : g.model == XLMIMO_UPW   ? gram_tc_kernel<XLMIMO_UPW>
                                         : gram_tc_kernel<XLMIMO_FSPL_USW>;
