@@ -61,12 +61,25 @@ typedef enum { XLMIMO_PNUSW = 0, XLMIMO_FSPL_USW = 1, XLMIMO_UPW = 2 } xlmimo_mo
 
 /* Arithmetic of the exact Gram accumulation.
  *   XLMIMO_F64    FP64 generation and FP64 accumulation (SIMT).
- *   XLMIMO_F32    FP32 generation with an FP64 phase reference every 256
+ *   XLMIMO_F32    FP32 generation with a double-float phase reference every 128
  *                 elements, FP32 accumulation (SIMT).
- *   XLMIMO_BF16X3 FP32 generation as above; channel split h = hi + lo into two
- *                 BF16 parts; Gram from hi*hi + hi*lo + lo*hi (+ lo*lo) on the
- *                 tensor cores (tcgen05) with FP32 accumulation in TMEM. */
-typedef enum { XLMIMO_F64 = 0, XLMIMO_F32 = 1, XLMIMO_BF16X3 = 3 } xlmimo_prec;
+ *   XLMIMO_BF16   FP32 generation (reference every 256 elements); each entry
+ *                 rounded to one BF16 number; tensor cores (tcgen05) with FP32
+ *                 accumulation in TMEM.  Accuracy class ~1e-2.
+ *   XLMIMO_BF16X3 as XLMIMO_BF16 with each entry split h = hi + lo into two BF16
+ *                 parts and the products hi*hi + hi*lo + lo*hi (+ lo*lo for
+ *                 K <= 32) accumulated.  Accuracy class ~1e-5.
+ *   XLMIMO_F16X3  as XLMIMO_BF16X3 in FP16, after scaling user k's entries by
+ *                 1/|h_k| at the array centre (undone in FP64).  Accuracy class
+ *                 ~1e-6 (limited by the FP32 generation and accumulation).
+ * The tensor-core precisions need an sm_103 device. */
+typedef enum {
+    XLMIMO_F64 = 0,
+    XLMIMO_F32 = 1,
+    XLMIMO_BF16 = 2,
+    XLMIMO_BF16X3 = 3,
+    XLMIMO_F16X3 = 4
+} xlmimo_prec;
 
 /* Linear receivers (Sec. V): ZF (Eq. 21), MMSE, MRC. */
 typedef enum { XLMIMO_ZF = 0, XLMIMO_MMSE = 1, XLMIMO_MRC = 2 } xlmimo_scheme;
@@ -110,7 +123,8 @@ int xlmimo_channel_gram(const xlmimo_array* arr, const double* users, int K, int
  * memory for its own pool at start-up and forbids later allocations, or a
  * latency-critical loop that cannot accept cudaMalloc / cudaFree, which may
  * block or synchronise the device.  Arguments, results and precisions
- * (XLMIMO_F64 and XLMIMO_F32; XLMIMO_BF16X3 returns XLMIMO_EUNSUPPORTED) are
+ * (XLMIMO_F64 and XLMIMO_F32; the tensor-core precisions return
+ * XLMIMO_EUNSUPPORTED) are
  * those of xlmimo_channel_gram, with the same element split and the same
  * summation order.
  * When the batch is too small to fill the GPU, the partial Gram matrices of

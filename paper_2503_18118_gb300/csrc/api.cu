@@ -132,7 +132,9 @@ int xlmimo_channel_gram(const xlmimo_array* arr, const double* users, int K, int
     switch (prec) {
         case XLMIMO_F64: return launch_gram_f64(g, users, K, B, gram, as_stream(stream));
         case XLMIMO_F32: return launch_gram_f32(g, users, K, B, gram, as_stream(stream));
-        case XLMIMO_BF16X3: return launch_gram_tc(g, users, K, B, gram, as_stream(stream));
+        case XLMIMO_BF16:
+        case XLMIMO_BF16X3:
+        case XLMIMO_F16X3: return launch_gram_tc(g, users, K, B, prec, gram, as_stream(stream));
         default: set_error("unknown precision %d", prec); return XLMIMO_EINVAL;
     }
 }

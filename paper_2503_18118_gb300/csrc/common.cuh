@@ -31,7 +31,7 @@ int check_array(const xlmimo_array* arr, Geom* g);
 // Host launchers implemented in the .cu files (validated arguments only).
 int launch_gram_f64(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st);
 int launch_gram_f32(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st);
-int launch_gram_tc(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st,
+int launch_gram_tc(const Geom& g, const double* users, int K, int B, int prec, double* gram, cudaStream_t st,
                    int ctas_per_sm = 0);
 int launch_closed_form(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st);
 int launch_beamform(const double* gf, const double* gt, const double* power, const double* noise, int K,

@@ -56,7 +56,7 @@ extern "C" int xlmimo_channel_gram_noalloc(const xlmimo_array* arr, const double
     if (B < 0) { set_error("B must be >= 0, got %d", B); return XLMIMO_EINVAL; }
     if (prec != XLMIMO_F64 && prec != XLMIMO_F32) {
         set_error("xlmimo_channel_gram_noalloc supports XLMIMO_F64 and XLMIMO_F32 only");
-        return prec == XLMIMO_BF16X3 ? XLMIMO_EUNSUPPORTED : XLMIMO_EINVAL;
+        return (prec >= XLMIMO_BF16 && prec <= XLMIMO_F16X3) ? XLMIMO_EUNSUPPORTED : XLMIMO_EINVAL;
     }
     if (B == 0) return XLMIMO_OK;
     if (!users || !gram) { set_error("users and gram must be non-NULL"); return XLMIMO_EINVAL; }

@@ -1,14 +1,19 @@
-// Exact Gram matrices on the 5th-generation tensor cores (tcgen05), BF16
-// hi/lo split with FP32 accumulation in tensor memory.
+// Exact Gram matrices on the 5th-generation tensor cores (tcgen05) with FP32
+// accumulation in tensor memory: BF16 (one term), BF16 hi/lo split, or FP16
+// hi/lo split of per-user scaled entries.
 //
 // The complex Gram G = H^H H of K users is a real contraction over the
 // elements: with X = [Re H ; Im H] (2K rows, one column per element),
 //   Re G_ij = (X X^T)_{i,j} + (X X^T)_{K+i,K+j},  Im G_ij = (X X^T)_{i,K+j} - (X X^T)_{K+i,j}.
-// Each FP32 channel entry is split into two BF16 numbers v = hi + lo
-// (|v - hi - lo| <= 2^-18 |v|).  Stacking Y = [X_hi ; X_lo] (4K = 128 rows
-// for K <= 32), one M = N = 128 MMA stream accumulates D = Y Y^T, and
-//   X X^T ~= X_hi X_hi^T + X_hi X_lo^T + X_lo X_hi^T + X_lo X_lo^T
-// is the sum of D's four 64 x 64 blocks.
+// Each FP32 channel entry is split v = hi + lo in BF16 (|v - hi - lo| <=
+// 2^-16 |v|) or, after scaling user k's entries by s_k = 1/|h_k| at the
+// array centre so that they sit near 1, in FP16 (<= 2^-22 |v|; the scale is
+// divided out in FP64 at the end).  For K <= 32, Y = [X_hi ; X_lo] has 128
+// rows and one M = N = 128 MMA stream accumulates D = Y Y^T, whose four
+// 64 x 64 blocks sum to X_hi X_hi^T + X_hi X_lo^T + X_lo X_hi^T + X_lo X_lo^T.
+// For 32 < K <= 64, X_hi and X_lo have 128 rows each and three MMAs per
+// k-step accumulate X_hi X_hi^T + X_lo X_hi^T + X_hi X_lo^T into one
+// 128 x 128 accumulator.  The single-term BF16 variant keeps X_hi only.
 //
 // Pipeline (one CTA per trial chunk, 9 warps):
 //   warps 0-7  generate 64-element stages: lane = user, warp = 8-element
@@ -24,6 +29,7 @@
 // Every wait is bounded; a wait that gives up marks the trial (NaN output),
 // lets outstanding MMAs drain and frees the tensor memory.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "chan_gen.cuh"
@@ -33,13 +39,22 @@ namespace xl {
 
 constexpr int TC_STAGES = 3;
 constexpr int TC_T = 64;              // elements per stage
-constexpr int TC_ROWS = 128;          // Y rows (4 components x 32 users)
-constexpr int TC_STAGE_BYTES = TC_ROWS * TC_T * 2;  // 16 KB, BF16
 constexpr int TC_THREADS = 288;
 constexpr int TC_GEN_THREADS = 256;
 constexpr int TC_TMEM_COLS = 128;
 constexpr int TC_REF_SPAN = 256;      // elements per phase reference (4 stages)
 constexpr uint64_t TC_WAIT_NS = 4000000000ull;  // 4 s
+
+enum { TCP_BF16 = 0, TCP_BF16X3 = 1, TCP_F16X3 = 2 };
+
+template <int KMAX>
+struct TcCfg {
+    static constexpr int ROWS = 4 * KMAX;                   // hi and lo rows of Re and Im
+    static constexpr int STAGE_BYTES = ROWS * TC_T * 2;     // 16-bit entries
+    static constexpr int LO_OFFSET = 2 * KMAX * 128;        // bytes to the lo block
+    static constexpr int SLOTS = KMAX / 32;                 // users per generator lane
+    static constexpr int FOLD_LD = KMAX == 32 ? 65 : 129;   // epilogue row stride (floats)
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -100,18 +115,24 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major, M = N = 128.
-constexpr uint32_t TC_IDESC = (1u << 4)            // D format F32
-                              | (1u << 7)          // A format BF16
-                              | (1u << 10)         // B format BF16
-                              | ((128u >> 3) << 17)  // N / 8
-                              | ((128u >> 4) << 24); // M / 16
+// Instruction descriptor, kind::f16: 16-bit A and B (format 1 = BF16, 0 = F16),
+// FP32 accumulator, both K-major, M = N = 128.
+template <int PREC>
+__device__ __forceinline__ uint32_t tc_idesc() {
+    const uint32_t fmt = PREC == TCP_F16X3 ? 0u : 1u;
+    return (1u << 4)               // D format F32
+           | (fmt << 7)            // A format
+           | (fmt << 10)           // B format
+           | ((128u >> 3) << 17)   // N / 8
+           | ((128u >> 4) << 24);  // M / 16
+}
 
-__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                     uint32_t accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(accumulate)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -137,6 +158,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+template <int KMAX>
 struct TcShared {
     uint64_t full[TC_STAGES];
     uint64_t empty[TC_STAGES];
@@ -144,19 +166,43 @@ struct TcShared {
     uint32_t tmem_base;
     int abort;
     int bad;
-    UserGeo ug[32];
+    UserGeo ug[KMAX];
+    float scale[KMAX];  // FP16 path: per-user entry scale
 };
 
-template <int MODEL>
-__global__ void __launch_bounds__(TC_THREADS, 3) gram_tc_kernel(Geom g, GenParams gp, const double* __restrict__ users,
-                                                               int K, int S, int64_t chunk,
-                                                               double2* __restrict__ out) {
+// hi/lo (or hi only) 16-bit conversion of two values, packed
+template <int PREC>
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    if (PREC == TCP_F16X3) {
+        __half2 h = __floats2half2_rn(a, b);
+        float2 hf = __half22float2(h);
+        __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+        hi = *reinterpret_cast<uint32_t*>(&h);
+        lo = *reinterpret_cast<uint32_t*>(&l);
+    } else {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        hi = *reinterpret_cast<uint32_t*>(&h);
+        if (PREC == TCP_BF16X3) {
+            float2 hf = __bfloat1622float2(h);
+            __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+            lo = *reinterpret_cast<uint32_t*>(&l);
+        } else {
+            lo = 0u;
+        }
+    }
+}
+
+template <int MODEL, int KMAX, int PREC>
+__global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
+    gram_tc_kernel(Geom g, GenParams gp, const double* __restrict__ users, int K, int S, int64_t chunk,
+                   double2* __restrict__ out) {
+    using C = TcCfg<KMAX>;
     extern __shared__ unsigned char smem_raw[];
     // stages must be 1024-byte aligned for the 128-byte swizzle
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     unsigned char* stages = base;
-    TcShared* sh = reinterpret_cast<TcShared*>(base + TC_STAGES * TC_STAGE_BYTES);
-    float* fold = reinterpret_cast<float*>(base);  // epilogue reuses the stages: 128 x 65 floats
+    TcShared<KMAX>* sh = reinterpret_cast<TcShared<KMAX>*>(base + TC_STAGES * C::STAGE_BYTES);
+    float* fold = reinterpret_cast<float*>(base);  // epilogue reuses the stages
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int b = blockIdx.x, s = blockIdx.y;
@@ -177,7 +223,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) gram_tc_kernel(Geom g, GenParam
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid < 32) {
+    if (tid < KMAX) {
         double x = 1.0, y = 0.0;
         if (tid < K) {
             x = users[((int64_t)b * K + tid) * 2];
@@ -185,7 +231,18 @@ __global__ void __launch_bounds__(TC_THREADS, 3) gram_tc_kernel(Geom g, GenParam
         }
         UserGeo u = make_user_geo(g, x, y);
         if (tid < K && !u.ok) atomicOr(&sh->bad, 1);
+        float sc = 1.0f;
+        if (PREC == TCP_F16X3) {
+            // 1 / |h| at the array centre, so the scaled entries sit near 1
+            const double rc = sqrt(x * x + y * y) * g.inv_lambda;  // distance in wavelengths
+            double amp_c = (MODEL == XLMIMO_UPW) ? (double)u.ampc
+                         : (MODEL == XLMIMO_PNUSW) ? (double)u.ampc / (rc * sqrt(rc))
+                                                   : (double)u.ampc / rc;
+            sc = (float)(1.0 / amp_c);
+            u.ampc *= sc;
+        }
         sh->ug[tid] = u;
+        sh->scale[tid] = sc;
     }
     tc_fence_before();
     __syncthreads();
@@ -198,49 +255,51 @@ __global__ void __launch_bounds__(TC_THREADS, 3) gram_tc_kernel(Geom g, GenParam
     const int nst = (int)((nend - nbeg + TC_T - 1) / TC_T);
 
     if (warp < 8) {
-        // ---------------- generators: lane = user, warp = 8-element slice
-        const int k = lane;
-        const bool live = k < K;
-        const float xl2 = sh->ug[k].xl2, x2x2 = sh->ug[k].x2x2, ampc = live ? sh->ug[k].ampc : 0.f;
-        PairConst pc = make_pair_const(UserRef{0.f, 0.f, 0.f, 0.f, 1.f}, gp.dprime_f, xl2, x2x2, 0.f);
+        // ---------------- generators: lane = user (and user + 32), warp = 8-element slice
+        UserRef ref[C::SLOTS];
+        PairConst pc = make_pair_const(UserRef{0.f, 0.f, 0.f, 0.f, 1.f}, gp.dprime_f, 0.f, 0.f, 0.f);
         int64_t nc = 0;
         for (int it = 0; it < nst; ++it) {
             const int st = it % TC_STAGES;
             if (it >= TC_STAGES && !mbar_wait(&sh->empty[st], ((it / TC_STAGES) - 1) & 1, abort)) break;
             const int64_t n0 = nbeg + (int64_t)it * TC_T;
-            if (((n0 - nbeg) % TC_REF_SPAN) == 0) {
-                nc = n0 + TC_REF_SPAN / 2;
-                UserRef ref = make_user_ref(gp, sh->ug[k], (long long)nc);
-                pc = make_pair_const(ref, gp.dprime_f, xl2, x2x2, ampc);
-            }
-            uint32_t w[4][4];  // [component][packed pair]
+            const bool new_span = ((n0 - nbeg) % TC_REF_SPAN) == 0;
+            if (new_span) nc = n0 + TC_REF_SPAN / 2;
             const int rem = (int)min((int64_t)TC_T, nend - n0) - warp * 8;  // valid elements of this slice
             const float mf0 = (float)(int)(n0 + warp * 8 - nc);
+            unsigned char* sb = stages + st * C::STAGE_BYTES;
 #pragma unroll
-            for (int i = 0; i < 8; i += 2) {
-                float2 re, im;
-                gen_pair<MODEL>(pc, make_float2(mf0 + (float)i, mf0 + (float)(i + 1)), re, im);
-                if (i >= rem) { re.x = 0.f; im.x = 0.f; }
-                if (i + 1 >= rem) { re.y = 0.f; im.y = 0.f; }
-                // hi = RN_bf16(v), lo = RN_bf16(v - hi), two values per conversion
-                __nv_bfloat162 rh = __floats2bfloat162_rn(re.x, re.y), ih = __floats2bfloat162_rn(im.x, im.y);
-                float2 rl = __ffma2_rn(__bfloat1622float2(rh), f2(-1.0f), re);
-                float2 il = __ffma2_rn(__bfloat1622float2(ih), f2(-1.0f), im);
-                __nv_bfloat162 rlb = __floats2bfloat162_rn(rl.x, rl.y), ilb = __floats2bfloat162_rn(il.x, il.y);
-                w[0][i >> 1] = *reinterpret_cast<uint32_t*>(&rh);
-                w[1][i >> 1] = *reinterpret_cast<uint32_t*>(&ih);
-                w[2][i >> 1] = *reinterpret_cast<uint32_t*>(&rlb);
-                w[3][i >> 1] = *reinterpret_cast<uint32_t*>(&ilb);
-            }
-            unsigned char* sb = stages + st * TC_STAGE_BYTES;
+            for (int slot = 0; slot < C::SLOTS; ++slot) {
+                const int k = lane + 32 * slot;
+                const UserGeo& u = sh->ug[k];
+                const float ampc = k < K ? u.ampc : 0.f;
+                if (new_span) ref[slot] = make_user_ref(gp, u, (long long)nc);
+                if (C::SLOTS == 1) {
+                    if (new_span) pc = make_pair_const(ref[slot], gp.dprime_f, u.xl2, u.x2x2, ampc);
+                } else {
+                    pc = make_pair_const(ref[slot], gp.dprime_f, u.xl2, u.x2x2, ampc);
+                }
+                uint32_t w[4][4];  // [component: Re hi, Im hi, Re lo, Im lo][packed pair]
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int f = 32 * c + k;  // row of Y
-                const int rin = f & 7;
-                uint32_t addr = smem_u32(sb + (f >> 3) * 1024 + rin * 128 + ((warp ^ rin) << 4));
-                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(w[c][0]), "r"(w[c][1]),
-                             "r"(w[c][2]), "r"(w[c][3])
-                             : "memory");
+                for (int i = 0; i < 8; i += 2) {
+                    float2 re, im;
+                    gen_pair<MODEL>(pc, make_float2(mf0 + (float)i, mf0 + (float)(i + 1)), re, im);
+                    if (i >= rem) { re.x = 0.f; im.x = 0.f; }
+                    if (i + 1 >= rem) { re.y = 0.f; im.y = 0.f; }
+                    split2<PREC>(re.x, re.y, w[0][i >> 1], w[2][i >> 1]);
+                    split2<PREC>(im.x, im.y, w[1][i >> 1], w[3][i >> 1]);
+                }
+                const int ncomp = (PREC == TCP_BF16 && KMAX == 64) ? 2 : 4;  // the one-term K>32 MMA reads hi only
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (c >= ncomp) break;
+                    const int f = KMAX * c + k;  // row of the stage tile
+                    const int rin = f & 7;
+                    uint32_t addr = smem_u32(sb + (f >> 3) * 1024 + rin * 128 + ((warp ^ rin) << 4));
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(w[c][0]), "r"(w[c][1]),
+                                 "r"(w[c][2]), "r"(w[c][3])
+                                 : "memory");
+                }
             }
             fence_async_smem();
             mbar_arrive(&sh->full[st]);
@@ -248,27 +307,36 @@ __global__ void __launch_bounds__(TC_THREADS, 3) gram_tc_kernel(Geom g, GenParam
     } else {
         // ---------------- MMA issuer (one lane; the others wait at the warp barrier)
         if (lane == 0) {
-        for (int it = 0; it < nst; ++it) {
-            const int st = it % TC_STAGES;
-            if (!mbar_wait(&sh->full[st], (it / TC_STAGES) & 1, abort)) break;
-            tc_fence_after();
-            const uint32_t sa = smem_u32(stages + st * TC_STAGE_BYTES);
+            const uint32_t idesc = tc_idesc<PREC>();
+            for (int it = 0; it < nst; ++it) {
+                const int st = it % TC_STAGES;
+                if (!mbar_wait(&sh->full[st], (it / TC_STAGES) & 1, abort)) break;
+                tc_fence_after();
+                const uint32_t sa = smem_u32(stages + st * C::STAGE_BYTES);
 #pragma unroll
-            for (int kk = 0; kk < TC_T / 16; ++kk) {
-                const uint64_t d = desc_sw128(sa + kk * 32);
-                umma(tmem, d, d, (it > 0 || kk > 0) ? 1u : 0u);
+                for (int kk = 0; kk < TC_T / 16; ++kk) {
+                    const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+                    const uint64_t hi = desc_sw128(sa + kk * 32);
+                    if (KMAX == 32) {
+                        umma(tmem, hi, hi, idesc, acc);  // D += Y Y^T
+                    } else {
+                        umma(tmem, hi, hi, idesc, acc);
+                        if (PREC != TCP_BF16) {
+                            const uint64_t lo = desc_sw128(sa + C::LO_OFFSET + kk * 32);
+                            umma(tmem, lo, hi, idesc, 1u);
+                            umma(tmem, hi, lo, idesc, 1u);
+                        }
+                    }
+                }
+                umma_commit(&sh->empty[st]);
             }
-            umma_commit(&sh->empty[st]);
-        }
-        umma_commit(&sh->done);  // fires once every issued MMA has completed
+            umma_commit(&sh->done);  // fires once every issued MMA has completed
         }
         __syncwarp();
     }
 
     // ---------------- epilogue (warps 0-3 own TMEM lanes 0-127)
     double2* o = out + ((int64_t)b * S + s) * K * K;
-    // every thread of the CTA waits for the accumulator (bounded), so the
-    // stage buffers are free for the fold
     bool ok = mbar_wait(&sh->done, 0, abort);
     tc_fence_after();
     __syncthreads();
@@ -277,31 +345,47 @@ __global__ void __launch_bounds__(TC_THREADS, 3) gram_tc_kernel(Geom g, GenParam
         const int m = warp * 32 + lane;  // row of D
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
         float v[32], u[32];
+        if (KMAX == 32) {
 #pragma unroll
-        for (int cb = 0; cb < 2; ++cb) {
-            tmem_ld32(trow + cb * 32, v);
-            tmem_ld32(trow + 64 + cb * 32, u);
+            for (int cb = 0; cb < 2; ++cb) {
+                tmem_ld32(trow + cb * 32, v);
+                tmem_ld32(trow + 64 + cb * 32, u);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) fold[m * 65 + cb * 32 + j] = v[j] + u[j];
+                for (int j = 0; j < 32; ++j) fold[m * C::FOLD_LD + cb * 32 + j] = v[j] + u[j];
+            }
+        } else {
+#pragma unroll
+            for (int cb = 0; cb < 4; ++cb) {
+                tmem_ld32(trow + cb * 32, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) fold[m * C::FOLD_LD + cb * 32 + j] = v[j];
+            }
         }
     }
     tc_fence_before();
     __syncthreads();
     if (ok) {
-        // R = P[0:64] + P[64:128] (P = row-folded D);  complex Gram from R
+        // R (2 KMAX square) from the fold; complex Gram from R; FP16 scale removed
         const int P = K * (K + 1) / 2;
         for (int q = tid; q < P; q += TC_THREADS) {
             int i = 0, rl = K, p = q;
             while (p >= rl) { p -= rl; ++i; --rl; }
             const int j = i + p;
-            auto R = [&](int r, int c) { return fold[r * 65 + c] + fold[(r + 64) * 65 + c]; };
-            const float re = R(i, j) + R(32 + i, 32 + j);
-            const float im = R(i, 32 + j) - R(32 + i, j);
+            auto R = [&](int r, int c) {
+                return KMAX == 32 ? fold[r * C::FOLD_LD + c] + fold[(r + 64) * C::FOLD_LD + c] : fold[r * C::FOLD_LD + c];
+            };
+            double re = (double)(R(i, j) + R(KMAX + i, KMAX + j));
+            double im = (double)(R(i, KMAX + j) - R(KMAX + i, j));
+            if (PREC == TCP_F16X3) {
+                const double us = 1.0 / ((double)sh->scale[i] * (double)sh->scale[j]);
+                re *= us;
+                im *= us;
+            }
             if (i == j) {
-                o[i * K + i] = make_double2((double)re, 0.0);
+                o[i * K + i] = make_double2(re, 0.0);
             } else {
-                o[i * K + j] = make_double2((double)re, (double)im);
-                o[j * K + i] = make_double2((double)re, -(double)im);
+                o[i * K + j] = make_double2(re, im);
+                o[j * K + i] = make_double2(re, -im);
             }
         }
     } else {
@@ -314,35 +398,49 @@ __global__ void __launch_bounds__(TC_THREADS, 3) gram_tc_kernel(Geom g, GenParam
     }
 }
 
-static size_t tc_smem_bytes() { return 1024 + TC_STAGES * TC_STAGE_BYTES + sizeof(TcShared); }
+template <int KMAX>
+static size_t tc_smem_bytes() {
+    return 1024 + TC_STAGES * TcCfg<KMAX>::STAGE_BYTES + sizeof(TcShared<KMAX>);
+}
+
+using TcKernel = void (*)(Geom, GenParams, const double*, int, int, int64_t, double2*);
+
+template <int MODEL, int KMAX>
+static TcKernel pick_prec(int prec) {
+    return prec == XLMIMO_BF16 ? gram_tc_kernel<MODEL, KMAX, TCP_BF16>
+         : prec == XLMIMO_F16X3 ? gram_tc_kernel<MODEL, KMAX, TCP_F16X3>
+                                : gram_tc_kernel<MODEL, KMAX, TCP_BF16X3>;
+}
+
+template <int KMAX>
+static TcKernel pick(int model, int prec) {
+    return model == XLMIMO_PNUSW ? pick_prec<XLMIMO_PNUSW, KMAX>(prec)
+         : model == XLMIMO_UPW   ? pick_prec<XLMIMO_UPW, KMAX>(prec)
+                                 : pick_prec<XLMIMO_FSPL_USW, KMAX>(prec);
+}
 
 // ctas_per_sm > 0 caps the kernel's residency by sizing its shared memory, so
-// that kernels on other streams (the FP64 receivers of the pipelined step)
-// can run on the same SMs; 0 leaves the residency to the register budget.
-int launch_gram_tc(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st, int ctas_per_sm) {
-    if (K > 32) {
-        set_error("XLMIMO_BF16X3 supports K <= 32 in this build");
-        return XLMIMO_EUNSUPPORTED;
-    }
+// that kernels on other streams can run on the same SMs; 0 leaves the
+// residency to the register and shared-memory budget.
+int launch_gram_tc(const Geom& g, const double* users, int K, int B, int prec, double* gram, cudaStream_t st,
+                   int ctas_per_sm) {
     int dev = 0, major = 0, minor = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
     if (major != 10 || minor != 3) {
-        set_error("XLMIMO_BF16X3 needs an sm_103 device (tcgen05)");
+        set_error("the tensor-core precisions need an sm_103 device (tcgen05)");
         return XLMIMO_EUNSUPPORTED;
     }
-    size_t smem = tc_smem_bytes();
+    const bool wide = K > 32;
+    TcKernel kern = wide ? pick<64>(g.model, prec) : pick<32>(g.model, prec);
+    size_t smem = wide ? tc_smem_bytes<64>() : tc_smem_bytes<32>();
     if (ctas_per_sm > 0) {
-        int dev = 0, per_sm = 0;
-        cudaGetDevice(&dev);
+        int per_sm = 0;
         cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
         size_t want = (size_t)per_sm / (size_t)(ctas_per_sm + 1) + 1024;  // more than 1/(c+1) of the SM
         if (want > smem) smem = want;
     }
-    auto kern = g.model == XLMIMO_PNUSW ? gram_tc_kernel<XLMIMO_PNUSW>
-              : g.model == XLMIMO_UPW   ? gram_tc_kernel<XLMIMO_UPW>
-                                        : gram_tc_kernel<XLMIMO_FSPL_USW>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e, "gram_tc attribute");
     int S = choose_split(g.N, B, TC_REF_SPAN, 4);

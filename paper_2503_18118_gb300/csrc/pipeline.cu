@@ -48,14 +48,14 @@ static int launch_gram_prec(const Geom& g, const double* users, int K, int B, in
     switch (prec) {
         case XLMIMO_F64: return launch_gram_f64(g, users, K, B, gram, st);
         case XLMIMO_F32: return launch_gram_f32(g, users, K, B, gram, st);
-        default: return launch_gram_tc(g, users, K, B, gram, st, leave_room ? 2 : 0);
+        default: return launch_gram_tc(g, users, K, B, prec, gram, st, leave_room ? 2 : 0);
     }
 }
 
 static int check_job(const xlmimo_mc_batch* j) {
     if (!j) { set_error("job is NULL"); return XLMIMO_EINVAL; }
     if (j->K < 1 || j->K > XLMIMO_MAX_USERS || j->B < 0) { set_error("K must be in [1, 64] and B >= 0"); return XLMIMO_EINVAL; }
-    if (j->prec != XLMIMO_F64 && j->prec != XLMIMO_F32 && j->prec != XLMIMO_BF16X3) { set_error("unknown precision"); return XLMIMO_EINVAL; }
+    if (j->prec < XLMIMO_F64 || j->prec > XLMIMO_F16X3) { set_error("unknown precision"); return XLMIMO_EINVAL; }
     if (j->scheme < XLMIMO_ZF || j->scheme > XLMIMO_MRC) { set_error("unknown scheme"); return XLMIMO_EINVAL; }
     if (j->cf_scheme > XLMIMO_MRC || j->cf_scheme < -1) { set_error("unknown closed-form scheme"); return XLMIMO_EINVAL; }
     if (j->power_mode != XLMIMO_POWER_ABS && j->power_mode != XLMIMO_POWER_RXSNR) { set_error("unknown power mode"); return XLMIMO_EINVAL; }

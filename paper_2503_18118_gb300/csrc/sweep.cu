@@ -96,7 +96,7 @@ static int sweep_impl(const xlmimo_sweep_cfg* c, xlmimo_sweep_result* r, cudaStr
         switch (c->prec) {
             case XLMIMO_F64: rc = launch_gram_f64(g, c->users, K, B, g_ex, st); break;
             case XLMIMO_F32: rc = launch_gram_f32(g, c->users, K, B, g_ex, st); break;
-            default: rc = launch_gram_tc(g, c->users, K, B, g_ex, st); break;
+            default: rc = launch_gram_tc(g, c->users, K, B, c->prec, g_ex, st); break;
         }
         if (!rc) rc = launch_closed_form(g, c->users, K, B, g_cf, st);
         if (!rc) {
@@ -169,7 +169,7 @@ extern "C" int xlmimo_capacity_sweep(const xlmimo_sweep_cfg* c, xlmimo_sweep_res
         return XLMIMO_EINVAL;
     }
     if (c->model < XLMIMO_PNUSW || c->model > XLMIMO_UPW) { set_error("unknown model"); return XLMIMO_EINVAL; }
-    if (c->prec != XLMIMO_F64 && c->prec != XLMIMO_F32 && c->prec != XLMIMO_BF16X3) {
+    if (c->prec < XLMIMO_F64 || c->prec > XLMIMO_F16X3) {
         set_error("unknown precision");
         return XLMIMO_EINVAL;
     }
