@@ -296,6 +296,53 @@ typedef struct {
 
 int xlmimo_mc_step(const xlmimo_mc_batch* job, void* stream);
 
+/* ---- Ragged batches --------------------------------------------------------
+ * Many independent instances with their own array size, user count,
+ * receiver and noise, evaluated together: exact Gram (tensor cores), receiver
+ * SINR and sum rate per instance.  A plan fixes the instance list once
+ * (host side: work items ordered longest first, instances grouped by user
+ * count, device tables and workspace allocated, tile shapes optionally
+ * chosen by timing candidates on sample inputs); running a plan only
+ * enqueues kernels -- no allocation, no synchronisation -- so it may be
+ * captured in a CUDA graph and replayed.  The paper's problem is one
+ * instance; batching many is this library's Monte-Carlo engine. */
+typedef struct {
+    int64_t n_ant;     /* N of this instance, 1 .. 2^40 */
+    int32_t k;         /* users, 1 .. XLMIMO_MAX_USERS */
+    int32_t scheme;    /* xlmimo_scheme of its receiver (matched, on the exact Gram) */
+    int64_t user_off;  /* first user of the instance in the packed users / power / sinr arrays */
+    int64_t gram_off;  /* first complex entry of its K x K Gram in the packed Gram array */
+    double noise;      /* sigma^2 > 0 */
+} xlmimo_inst;
+
+typedef struct xlmimo_batch_plan_st* xlmimo_batch_plan;
+
+/* Build a plan for `count` instances (host array `insts`) sharing the
+ * wavelength, spacing, beta0 and model of *geo (geo->n_ant is ignored).
+ * prec: XLMIMO_BF16, XLMIMO_BF16X3 or XLMIMO_F16X3.  If tune_users (device,
+ * packed [sum K][2]) is non-NULL the plan times its candidate tilings (element
+ * chunk per work item, resident CTAs per SM) on those users and keeps the
+ * fastest; otherwise it takes the defaults (8192 elements, 2 CTAs per SM).
+ * Element chunks are kept to a few thousand elements (candidates 4096, 8192,
+ * 16384) because the tensor cores' FP32 accumulation rounds towards zero:
+ * a long chunk of many small terms added to a large sum loses up to
+ * ~chunk x 2^-24 of it.  SYNCHRONOUS on `stream`. */
+int xlmimo_batch_plan_create(const xlmimo_array* geo, const xlmimo_inst* insts, int count, int prec,
+                             const double* tune_users, xlmimo_batch_plan* plan, void* stream);
+
+/* Run a plan: users [sum K][2], power [sum K] (read per power_mode) in;
+ * gram (packed complex, at each gram_off), sinr [sum K], status [count],
+ * rate [count] out (all device).  Asynchronous on `stream`; capturable. */
+int xlmimo_batch_run(xlmimo_batch_plan plan, const double* users, const double* power, int power_mode,
+                     double* gram, double* sinr, int32_t* status, double* rate, void* stream);
+
+/* Plan facts (host, written): {work items, element chunk per item, resident
+ * CTAs per SM, instances with K <= 32, instances with K > 32, workspace bytes,
+ * tuned (0/1), candidates timed}. */
+int xlmimo_batch_plan_info(xlmimo_batch_plan plan, int64_t* info8);
+
+int xlmimo_batch_plan_destroy(xlmimo_batch_plan plan);
+
 /* Message of the last error on this host thread ("" if none). */
 const char* xlmimo_last_error(void);
 

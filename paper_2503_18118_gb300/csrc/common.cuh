@@ -43,6 +43,22 @@ int launch_saturation(const double* users, int K, int B, double t, double spacin
 int saturation_analytic(const xlmimo_user_dist* d, int K, double t, double spacing, double* out,
                         cudaStream_t st);
 
+// One instance of a ragged batch, device copy (see xlmimo_inst).
+struct DevInst {
+    long long n_ant;
+    int k, scheme;
+    long long user_off, gram_off;
+    double noise;
+    long long part_off;  // first complex entry of its chunk partials (-1: single work item)
+    int nchunks, pad;
+};
+
+// Receivers of the instances list[0..n) of a ragged batch (matched, on their
+// exact Gram), shared memory sized for kmax users.
+void beamform_trial_launch_bucket(const DevInst* insts, const int* list, int n, int kmax, const double* gram,
+                                  const double* power, int power_mode, double* sinr, int* status, cudaStream_t st);
+int beamform_ragged_prepare();  // one-time kernel attribute, outside any stream capture
+
 // Split of the element range when the batch alone cannot fill the GPU.
 // Returns the number of contiguous element chunks per trial (>= 1); each chunk
 // is a whole number of `tile` elements except the last.

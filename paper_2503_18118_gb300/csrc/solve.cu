@@ -231,13 +231,13 @@ __device__ int gj_inverse_dev(cd* A, cd* X, int K, int* flag, int* piv) {
     return 1;
 }
 
-__global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* __restrict__ gfil,
-                                                                 const double2* __restrict__ gtru, int matched,
-                                                                 const double* __restrict__ power,
-                                                                 const double* __restrict__ noise, int K,
-                                                                 int scheme, int power_mode,
-                                                                 double* __restrict__ sinr, int* __restrict__ status,
-                                                                 double* __restrict__ cap) {
+// One trial's receiver, executed by the whole CTA.  gf/gt: this trial's Gram
+// matrices (gt == gf when matched); pw: its K powers; s2: its noise power;
+// sinr_t, status_t, cap_t: its outputs (cap_t may be NULL).  Dynamic shared
+// memory: (matched ? 2 : 3) K^2 complex doubles plus 2 XLMIMO_MAX_USERS doubles.
+__device__ void beamform_trial(const double2* __restrict__ gf, const double2* __restrict__ gt, int matched,
+                               const double* __restrict__ pw, double s2, int K, int scheme, int power_mode,
+                               double* __restrict__ sinr_t, int* __restrict__ status_t, double* __restrict__ cap_t) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int KK = K * K;
     cd* Z = reinterpret_cast<cd*>(smem);
@@ -248,13 +248,9 @@ __global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* 
     __shared__ double dinv[XLMIMO_MAX_USERS], pivd[XLMIMO_MAX_USERS], sp[XLMIMO_MAX_USERS];
     __shared__ int flag, piv, st;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int b = blockIdx.x;
-    const double2* gf = gfil + (int64_t)b * KK;
-    const double2* gt = gtru + (int64_t)b * KK;
-    const double s2 = noise[b];
     if (tid == 0) { flag = 0; st = 0; }
     for (int k = tid; k < K; k += nt) {
-        double v = power[(int64_t)b * K + k];
+        double v = pw[k];
         p[k] = (power_mode == XLMIMO_POWER_RXSNR) ? v * s2 / gt[k * K + k].x : v;
         sp[k] = s2 / p[k];  // MMSE diagonal loading sigma^2 / p_k
     }
@@ -264,7 +260,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* 
 
     // ---- capacity: Cholesky of G + s2 diag(p)^-1 (the MMSE matrix of the true channel)
     const bool mmse_reuse = matched && scheme == XLMIMO_MMSE;
-    if (cap && !mmse_reuse) {
+    if (cap_t && !mmse_reuse) {
         for (int e = tid; e < KK; e += nt) {
             int r = e / K, c = e - r * K;
             double2 v = gt[e];
@@ -275,7 +271,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* 
         double ld = ok ? warp0_sum_log2(pivd, K, 1.0) : 0.0;
         double lp = warp0_sum_log2(p, K, 1.0 / s2);
         if (tid == 0) {
-            cap[b] = ok ? lp + ld : nan("");
+            *cap_t = ok ? lp + ld : nan("");
             flag = 0;
         }
         __syncthreads();
@@ -296,10 +292,10 @@ __global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* 
         __syncthreads();
         int ok = chol_lower(Z, K, &flag, dinv, pivd);
         if (ok) {
-            if (mmse_reuse && cap) {
+            if (mmse_reuse && cap_t) {
                 double ld = warp0_sum_log2(pivd, K, 1.0);
                 double lp = warp0_sum_log2(p, K, 1.0 / s2);
-                if (tid == 0) cap[b] = lp + ld;
+                if (tid == 0) *cap_t = lp + ld;
             }
             tri_inverse(Z, X, K, dinv);  // X = L^{-1}
             if (matched) {
@@ -329,16 +325,16 @@ __global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* 
             if (!ok2) {
                 if (tid == 0) st = XLMIMO_ESINGULAR;
                 __syncthreads();
-                for (int k = tid; k < K; k += nt) sinr[(int64_t)b * K + k] = 0.0;
-                if (tid == 0) status[b] = st;
-                if (cap && mmse_reuse && tid == 0) cap[b] = nan("");
+                for (int k = tid; k < K; k += nt) sinr_t[k] = 0.0;
+                if (tid == 0) *status_t = st;
+                if (cap_t && mmse_reuse && tid == 0) *cap_t = nan("");
                 return;
             }
             if (matched) {
                 for (int k = tid; k < K; k += nt) dg[k] = X[k * K + k].x;
                 __syncthreads();
             }
-            if (cap && mmse_reuse) {
+            if (cap_t && mmse_reuse) {
                 // recompute the capacity on its own factorisation
                 for (int e = tid; e < KK; e += nt) {
                     int r = e / K, c = e - r * K;
@@ -350,7 +346,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* 
                 double ld2 = ok3 ? warp0_sum_log2(pivd, K, 1.0) : 0.0;
                 double lp = warp0_sum_log2(p, K, 1.0 / s2);
                 if (tid == 0) {
-                    cap[b] = ok3 ? lp + ld2 : nan("");
+                    *cap_t = ok3 ? lp + ld2 : nan("");
                     flag = 0;
                 }
                 __syncthreads();
@@ -373,7 +369,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* 
                 v = p[k] / (s2 * dg[k]);
                 if (scheme == XLMIMO_MMSE) v -= 1.0;
             }
-            sinr[(int64_t)b * K + k] = v;
+            sinr_t[k] = v;
         }
     } else {
         // A = M G (M in X) into Z, element-parallel with uniform dot length
@@ -392,10 +388,49 @@ __global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* 
                 if (j != k) itf = fma(p[j], cabs2(a), itf);
                 nz += cmulc(a, X[k * K + j]).x;  // (A M^H)_kk
             }
-            sinr[(int64_t)b * K + k] = sig / fma(s2, nz, itf);
+            sinr_t[k] = sig / fma(s2, nz, itf);
         }
     }
-    if (tid == 0) status[b] = st;
+    if (tid == 0) *status_t = st;
+}
+
+
+__global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* __restrict__ gfil,
+                                                                 const double2* __restrict__ gtru, int matched,
+                                                                 const double* __restrict__ power,
+                                                                 const double* __restrict__ noise, int K,
+                                                                 int scheme, int power_mode,
+                                                                 double* __restrict__ sinr, int* __restrict__ status,
+                                                                 double* __restrict__ cap) {
+    const int64_t b = blockIdx.x;
+    const int64_t KK = (int64_t)K * K;
+    beamform_trial(gfil + b * KK, gtru + b * KK, matched, power + b * K, noise[b], K, scheme, power_mode,
+                   sinr + b * K, status + b, cap ? cap + b : nullptr);
+}
+
+__global__ void __launch_bounds__(SOLVE_THREADS) beamform_ragged_kernel(const DevInst* __restrict__ insts,
+                                                                        const int* __restrict__ list,
+                                                                        const double2* __restrict__ gram,
+                                                                        const double* __restrict__ power, int power_mode,
+                                                                        double* __restrict__ sinr,
+                                                                        int* __restrict__ status) {
+    const int inst = list[blockIdx.x];
+    const DevInst in = insts[inst];
+    const double2* gm = gram + in.gram_off;
+    beamform_trial(gm, gm, 1, power + in.user_off, in.noise, in.k, in.scheme, power_mode, sinr + in.user_off,
+                   status + inst, nullptr);
+}
+
+int beamform_ragged_prepare() {
+    return cuda_status(cudaFuncSetAttribute(beamform_ragged_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
+                       "ragged receiver attribute");
+}
+
+void beamform_trial_launch_bucket(const DevInst* insts, const int* list, int n, int kmax, const double* gram,
+                                  const double* power, int power_mode, double* sinr, int* status, cudaStream_t st) {
+    size_t smem = 2 * (size_t)kmax * kmax * sizeof(cd) + 2 * XLMIMO_MAX_USERS * sizeof(double);
+    beamform_ragged_kernel<<<n, SOLVE_THREADS, smem, st>>>(insts, list, (const double2*)gram, power, power_mode, sinr,
+                                                            status);
 }
 
 int launch_beamform(const double* gf, const double* gt, const double* power, const double* noise, int K, int B,

@@ -59,7 +59,13 @@ class McBatch(ctypes.Structure):
                                        "status_cf", "capacity", "rate", "rate_cf", "stats", "stats_cf", "sat")]
 
 
-EXPORTS = ("xlmimo_mc_step", "xlmimo_channel_gram", "xlmimo_channel_gram_noalloc", "xlmimo_corr_closed_form", "xlmimo_beamform", "xlmimo_sumrate",
+class Inst(ctypes.Structure):
+    _fields_ = [("n_ant", ctypes.c_int64), ("k", ctypes.c_int32), ("scheme", ctypes.c_int32),
+                ("user_off", ctypes.c_int64), ("gram_off", ctypes.c_int64), ("noise", ctypes.c_double)]
+
+
+EXPORTS = ("xlmimo_batch_plan_create", "xlmimo_batch_run", "xlmimo_batch_plan_info", "xlmimo_batch_plan_destroy",
+           "xlmimo_mc_step", "xlmimo_channel_gram", "xlmimo_channel_gram_noalloc", "xlmimo_corr_closed_form", "xlmimo_beamform", "xlmimo_sumrate",
            "xlmimo_saturation", "xlmimo_saturation_analytic", "xlmimo_capacity_sweep", "xlmimo_last_error",
            "xlmimo_version")
 
@@ -79,6 +85,11 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
     L.xlmimo_channel_gram.argtypes = [ctypes.POINTER(Array), vp, i32, i32, i32, vp, vp]
     L.xlmimo_mc_step.argtypes = [ctypes.POINTER(McBatch), vp]
+    L.xlmimo_batch_plan_create.argtypes = [ctypes.POINTER(Array), ctypes.POINTER(Inst), i32, i32, vp,
+                                           ctypes.POINTER(vp), vp]
+    L.xlmimo_batch_run.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp]
+    L.xlmimo_batch_plan_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    L.xlmimo_batch_plan_destroy.argtypes = [vp]
     L.xlmimo_channel_gram_noalloc.argtypes = [ctypes.POINTER(Array), vp, i32, i32, i32, vp, vp]
     L.xlmimo_corr_closed_form.argtypes = [ctypes.POINTER(Array), vp, i32, i32, vp, vp]
     L.xlmimo_beamform.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, vp, vp, vp, vp]
@@ -285,3 +296,53 @@ def xlmimo_capacity_sweep(users: torch.Tensor, n_list, snr_db, wavelength: float
                       err.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), (ctypes.c_double * 3)())
     _check(lib().xlmimo_capacity_sweep(ctypes.byref(cfg), ctypes.byref(res), _stream(stream)))
     return {"rate": rate, "capacity": cap, "gram_err": err, "sat_mean": tuple(res.sat_mean)}
+
+
+class BatchPlan:
+    """A ragged batch of instances (own N, K, receiver, noise) sharing the array
+    geometry of `arr` (its n_ant is ignored).  Users, powers and SINRs are packed
+    per instance in order; Gram matrices are packed K_i x K_i blocks."""
+
+    def __init__(self, arr: Array, n_ant, k, scheme, noise, prec: int = BF16X3, tune_users: torch.Tensor | None = None,
+                 stream=None):
+        import numpy as np
+        n_ant, k = np.asarray(n_ant, np.int64), np.asarray(k, np.int64)
+        scheme, noise = np.asarray(scheme, np.int64), np.asarray(noise, np.float64)
+        self.count = len(n_ant)
+        self.k = k
+        self.user_off = np.concatenate([[0], np.cumsum(k)[:-1]]).astype(np.int64)
+        self.gram_off = np.concatenate([[0], np.cumsum(k * k)[:-1]]).astype(np.int64)
+        self.users_total = int(k.sum())
+        self.gram_total = int((k * k).sum())
+        insts = (Inst * self.count)(*[Inst(int(n_ant[i]), int(k[i]), int(scheme[i]), int(self.user_off[i]),
+                                           int(self.gram_off[i]), float(noise[i])) for i in range(self.count)])
+        h = ctypes.c_void_p()
+        tu = None if tune_users is None else _dev(tune_users, torch.float64, "tune_users", (self.users_total, 2))
+        _check(lib().xlmimo_batch_plan_create(ctypes.byref(arr), insts, self.count, int(prec), tu, ctypes.byref(h),
+                                              _stream(stream)))
+        self._h = h
+
+    def run(self, users, power, power_mode, gram, sinr, status, rate, stream=None):
+        U, n = self.users_total, self.count
+        _check(lib().xlmimo_batch_run(self._h, _dev(users, torch.float64, "users", (U, 2)),
+                                      _dev(power, torch.float64, "power", (U,)), int(power_mode),
+                                      _dev(gram, torch.complex128, "gram", (self.gram_total,)),
+                                      _dev(sinr, torch.float64, "sinr", (U,)), _dev(status, torch.int32, "status", (n,)),
+                                      _dev(rate, torch.float64, "rate", (n,)), _stream(stream)))
+
+    def info(self) -> dict:
+        v = (ctypes.c_int64 * 8)()
+        _check(lib().xlmimo_batch_plan_info(self._h, v))
+        keys = ("items", "chunk", "ctas_per_sm", "small", "large", "workspace_bytes", "tuned", "candidates")
+        return dict(zip(keys, list(v)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().xlmimo_batch_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
