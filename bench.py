@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--chunks", type=int, default=0, help="pipeline pieces per step (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the precision table and the ragged batch")
     return ap.parse_args()
 
 
@@ -187,6 +188,50 @@ def traffic_from_profile(path_name):
     return float(t.group(1)) if m.group(1) == cur else None
 
 
+def ragged_bench(xl, torch):
+    """Ragged batch of 2^14 instances: N = round(2^U[10,17]), K ~ U{2..64},
+    ZF or MMSE with probability 1/2, SNR ~ U[0, 30] dB, users as the headline
+    geometry; autotuned plan, run captured in a CUDA graph and replayed."""
+    count = 1 << 14
+    n, k, scheme, snr_db = inputs.ragged_instances(4, count)
+    lam = inputs.wavelength(100e9)
+    users = inputs.users_polar(4, 1, int(k.sum()), (3.0, 30.0))[0]
+    snr = np.repeat(inputs.db_to_lin(snr_db), k)
+    U = torch.from_numpy(users).cuda()
+    P = torch.from_numpy(np.ascontiguousarray(snr)).cuda()
+    t0 = time.perf_counter()
+    plan = xl.BatchPlan(xl.array(1, lam), n, k, scheme, np.ones(count), prec=xl.BF16X3, tune_users=U)
+    plan_s = time.perf_counter() - t0
+    out = dict(gram=torch.empty(plan.gram_total, dtype=torch.complex128, device="cuda"),
+               sinr=torch.empty(plan.users_total, dtype=torch.float64, device="cuda"),
+               status=torch.empty(count, dtype=torch.int32, device="cuda"),
+               rate=torch.empty(count, dtype=torch.float64, device="cuda"))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        plan.run(U, P, xl.POWER_RXSNR, **out, stream=s)  # warm
+        s.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            plan.run(U, P, xl.POWER_RXSNR, **out, stream=s)
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record()
+    for _ in range(reps):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    info = plan.info()
+    plan.close()
+    return {"workload": "2^14 instances, N=2^U[10,17], K~U{2..64}, ZF/MMSE, SNR~U[0,30] dB, 100 GHz",
+            "instances_per_s": count / (ms / 1e3), "ms_per_batch": ms, "channel_entries": int((n * k).sum()),
+            "plan": info, "plan_seconds": plan_s, "cuda_graph": True, "gram": "bf16x3"}
+
+
 def main():
     args = parse()
     wl = inputs.HEADLINE
@@ -325,6 +370,23 @@ def main():
     r_gpu = out.rate.cpu().numpy()[idx]
     sumrate_rel_err = float(np.max(np.abs(r_gpu - r_ref) / np.abs(r_ref)))
 
+    # precision study on the same workload: every Gram arithmetic, same step,
+    # sum-rate error on the sampled trials against the oracle
+    paths = None
+    ragged = None
+    if not args.no_extras and world == 1:
+        paths = {}
+        for name in ("f64", "f32", "bf16", "bf16x3", "f16x3"):
+            pp = {"f64": 0, "f32": 1, "bf16": 2, "bf16x3": 3, "f16x3": 4}[name]
+            nsteps = 1 if name == "f64" else 3
+            t_ms, _, _ = timed(pp, nsteps, 1)
+            step(pp)
+            torch.cuda.synchronize()
+            rg = out.rate.cpu().numpy()[idx]
+            paths[name] = {"trials_per_s": world * B * nsteps / (t_ms / 1e3),
+                           "sumrate_rel_err": float(np.max(np.abs(rg - r_ref) / np.abs(r_ref)))}
+        ragged = ragged_bench(xl, torch)
+
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -379,6 +441,8 @@ def main():
                    "l2": "flushed between timed steps (256 MB write)"},
         "sumrate_rel_err": sumrate_rel_err,
         "fp64_baseline": fp64,
+        "precisions": paths,
+        "ragged": ragged,
         "speedup_vs_fp64_gpu": (value / fp64["trials_per_s"]) if fp64 else None,
         "roofline": roof,
         "cpu_baseline": cpu,
