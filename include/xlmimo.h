@@ -343,6 +343,96 @@ int xlmimo_batch_plan_info(xlmimo_batch_plan plan, int64_t* info8);
 
 int xlmimo_batch_plan_destroy(xlmimo_batch_plan plan);
 
+/* ---- Learned correlation surrogate ------------------------------------------
+ * Not part of the paper.  A multilayer perceptron corrects the closed-form
+ * correlation of modified ZF (Sec. V-B, Eqs. 4 and 6, and its free-space
+ * analogue): for a user pair i < j it predicts t_ij from the pair's geometry,
+ * and the surrogate Gram is G~_ij (1 + t_ij) off the diagonal (its conjugate
+ * mirrored below), the closed-form G~_ii on it.  It is trained on targets
+ * t_ij = G_ij / G~_ij - 1 from the exact Gram: the ratio removes the fast
+ * 2 pi d / lambda phase that the closed form already carries, so what is
+ * left is a smooth function of the geometry (about 1 where the stationary
+ * point of the phase lies inside the aperture, about -1 where it lies
+ * outside and the exact entry is small).
+ *
+ * Architecture: XLMIMO_MLP_IN features -> XLMIMO_MLP_HIDDEN hidden layers of
+ * XLMIMO_MLP_WIDTH units with SiLU, silu(z) = z / (1 + e^-z) -> XLMIMO_MLP_OUT
+ * outputs (Re t, Im t).  Parameters: one FP32 buffer of XLMIMO_MLP_PARAMS
+ * floats, layer by layer, each layer's W [in][out] (row-major) followed by
+ * its bias [out].
+ * Features of a pair (r the user's distance to the array centre, theta its
+ * angle from broadside, atan2(y, x)):
+ *   ((ln(r_i/lambda) - 7.5)/2, theta_i/(pi/3), (ln(r_j/lambda) - 7.5)/2,
+ *    theta_j/(pi/3), (log2 N - 14)/4, (spacing/lambda - 1/2) * 4)
+ * Pair rows: trial-major, then i, then j (i < j): B * K(K-1)/2 rows.
+ * Numerics (training and inference alike): the first (6 -> 256) and last
+ * (256 -> 2) layers in FP32; the three 256 x 256 layers multiply BF16-rounded
+ * (round to nearest even) inputs by BF16-rounded weights with FP32
+ * accumulation.  Gradients pass through the rounding unchanged.  Inference
+ * runs those layers on the tensor cores and evaluates the SiLU feeding them
+ * with the hardware tanh approximation (silu(z) = z/2 (1 + tanh(z/2))),
+ * whose error is below the BF16 rounding that follows it. */
+#define XLMIMO_MLP_IN 6
+#define XLMIMO_MLP_WIDTH 256
+#define XLMIMO_MLP_HIDDEN 4
+#define XLMIMO_MLP_OUT 2
+#define XLMIMO_MLP_PARAMS 199682
+/* floats per row of the forward cache: pre-activation z and activation h of
+ * every hidden layer, stored as [layer][z | h][M][256] */
+#define XLMIMO_MLP_CACHE_PER_ROW (2 * XLMIMO_MLP_HIDDEN * XLMIMO_MLP_WIDTH)
+/* bytes of the packed inference image written by xlmimo_mlp_pack */
+#define XLMIMO_MLP_PACKED_BYTES 405760
+
+/* Features (and optionally targets and weights) of every pair of every trial.
+ * users [B][K][2], K >= 2.  feat [B*P][6] out, P = K(K-1)/2.  If gram (exact)
+ * and gram_cf (closed form) are both non-NULL, target [B*P][2] gets
+ * (Re, Im) of G_ij / G~_ij - 1; if weight is non-NULL it gets
+ * |G~_ij|^2 / (G~_ii G~_jj) (needs gram_cf).  Features are computed in FP32
+ * from the FP64 positions, targets and weights in FP64; all outputs FP32. */
+int xlmimo_pair_features(const xlmimo_array* arr, const double* users, int K, int B, const double* gram,
+                         const double* gram_cf, float* feat, float* target, float* weight, void* stream);
+
+/* Forward pass over M rows: x [M][6] -> out [M][2].  cache is NULL or
+ * [M * XLMIMO_MLP_CACHE_PER_ROW] floats (needed by xlmimo_mlp_backward). */
+int xlmimo_mlp_forward(const float* params, const float* x, int M, float* out, float* cache, void* stream);
+
+/* Loss 0.5/M * sum_m w_m |out_m - target_m|^2 into *loss (device float) and
+ * its gradient dout [M][2].  weight NULL means w = 1. */
+int xlmimo_mlp_loss(const float* out, const float* target, const float* weight, int M, float* dout, float* loss,
+                    void* stream);
+
+/* Floats of device workspace xlmimo_mlp_backward needs for M rows. */
+int64_t xlmimo_mlp_work_floats(int M);
+
+/* Backward pass: grad [XLMIMO_MLP_PARAMS] (overwritten) of the loss whose
+ * output gradient is dout [M][2], from the forward cache of the same x. */
+int xlmimo_mlp_backward(const float* params, const float* x, const float* cache, const float* dout, int M,
+                        float* grad, float* work, void* stream);
+
+/* One Adam step (Kingma and Ba) on params with moments m, v (all
+ * [XLMIMO_MLP_PARAMS], updated in place): m = b1 m + (1-b1) g,
+ * v = b2 v + (1-b2) g^2, p -= lr * (m/(1-b1^step)) / (sqrt(v/(1-b2^step)) + eps).
+ * step >= 1. */
+int xlmimo_mlp_adam(float* params, float* m, float* v, const float* grad, int64_t step, double lr, double beta1,
+                    double beta2, double eps, void* stream);
+
+/* Forward, loss, backward and Adam on one batch, in that order (out [M][2],
+ * cache, work as above; loss may be NULL). */
+int xlmimo_mlp_train_step(float* params, float* m, float* v, float* grad, int64_t step, double lr, const float* x,
+                          const float* target, const float* weight, int M, float* out, float* cache, float* work,
+                          float* loss, void* stream);
+
+/* BF16 inference image of params (packed: XLMIMO_MLP_PACKED_BYTES, 16-byte
+ * aligned) for xlmimo_surrogate_gram. */
+int xlmimo_mlp_pack(const float* params, void* packed, void* stream);
+
+/* Surrogate Gram [B][K][K]: the closed form of xlmimo_corr_closed_form with
+ * every off-diagonal entry multiplied by 1 + t_ij from the network in
+ * `packed`.  One fused tensor-core launch evaluates the network on all pairs.
+ * A bounded device-side wait that gives up leaves NaN in its pairs. */
+int xlmimo_surrogate_gram(const xlmimo_array* arr, const double* users, int K, int B, const void* packed,
+                          double* gram, void* stream);
+
 /* Message of the last error on this host thread ("" if none). */
 const char* xlmimo_last_error(void);
 

@@ -110,5 +110,38 @@ def ragged_instances(seed: int, count: int, n_log2=(10.0, 17.0), k_range=(2, 64)
     return n, k, scheme, snr
 
 
+def mlp_init_params(seed: int, dims=(6, 256, 256, 256, 256, 2)) -> np.ndarray:
+    """Initial network parameters, float32, in the library's layout (per layer
+    W [in][out] row-major, then b [out]): W ~ U(-1/sqrt(in), 1/sqrt(in)), b = 0."""
+    g = _gen(seed)
+    parts = []
+    for a, b in zip(dims[:-1], dims[1:]):
+        lim = 1.0 / math.sqrt(a)
+        parts.append(((g.random((a, b)) * 2.0 - 1.0) * lim).reshape(-1))
+        parts.append(np.zeros(b))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def surrogate_trials(seed: int, trials: int, k: int, n_log2=(10.0, 18.0), bands=((28e9, (5.0, 50.0)), (100e9, (3.0, 30.0))),
+                     theta_deg=(-60.0, 60.0)):
+    """Training trials of the correlation surrogate: per trial N = round(2^U[n_log2]),
+    a carrier band drawn uniformly from `bands` (frequency, distance range), and
+    k users drawn as in users_polar.  Returns (n [T] int64, freq [T], users [T][k][2])."""
+    g = _gen(seed)
+    u = g.random((trials, 2))
+    n = np.rint(2.0 ** (n_log2[0] + (n_log2[1] - n_log2[0]) * u[:, 0])).astype(np.int64)
+    band = np.minimum((u[:, 1] * len(bands)).astype(np.int64), len(bands) - 1)
+    freq = np.array([bands[b][0] for b in band])
+    w = g.random((trials, k, 2))
+    users = np.empty((trials, k, 2))
+    for t in range(trials):
+        lo, hi = bands[band[t]][1]
+        r = lo + (hi - lo) * w[t, :, 0]
+        th = np.deg2rad(theta_deg[0] + (theta_deg[1] - theta_deg[0]) * w[t, :, 1])
+        users[t, :, 0] = r * np.cos(th)
+        users[t, :, 1] = r * np.sin(th)
+    return n, freq, users
+
+
 def deg(x):
     return math.radians(x)

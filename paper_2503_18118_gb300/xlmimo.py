@@ -66,8 +66,14 @@ class Inst(ctypes.Structure):
 
 EXPORTS = ("xlmimo_batch_plan_create", "xlmimo_batch_run", "xlmimo_batch_plan_info", "xlmimo_batch_plan_destroy",
            "xlmimo_mc_step", "xlmimo_channel_gram", "xlmimo_channel_gram_noalloc", "xlmimo_corr_closed_form", "xlmimo_beamform", "xlmimo_sumrate",
-           "xlmimo_saturation", "xlmimo_saturation_analytic", "xlmimo_capacity_sweep", "xlmimo_last_error",
-           "xlmimo_version")
+           "xlmimo_saturation", "xlmimo_saturation_analytic", "xlmimo_capacity_sweep", "xlmimo_pair_features",
+           "xlmimo_mlp_forward", "xlmimo_mlp_loss", "xlmimo_mlp_work_floats", "xlmimo_mlp_backward", "xlmimo_mlp_adam",
+           "xlmimo_mlp_train_step", "xlmimo_mlp_pack", "xlmimo_surrogate_gram", "xlmimo_last_error", "xlmimo_version")
+
+MLP_IN, MLP_WIDTH, MLP_HIDDEN, MLP_OUT = 6, 256, 4, 2
+MLP_PARAMS = 199682
+MLP_CACHE_PER_ROW = 2 * MLP_HIDDEN * MLP_WIDTH
+MLP_PACKED_BYTES = 405760
 
 _lib = None
 
@@ -97,9 +103,19 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.xlmimo_saturation.argtypes = [vp, i32, i32, dbl, dbl, vp, vp]
     L.xlmimo_saturation_analytic.argtypes = [ctypes.POINTER(UserDist), i32, dbl, dbl, ctypes.POINTER(dbl), vp]
     L.xlmimo_capacity_sweep.argtypes = [ctypes.POINTER(SweepCfg), ctypes.POINTER(SweepResult), vp]
+    L.xlmimo_pair_features.argtypes = [ctypes.POINTER(Array), vp, i32, i32, vp, vp, vp, vp, vp, vp]
+    L.xlmimo_mlp_forward.argtypes = [vp, vp, i32, vp, vp, vp]
+    L.xlmimo_mlp_loss.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+    L.xlmimo_mlp_work_floats.argtypes = [i32]
+    L.xlmimo_mlp_work_floats.restype = i64
+    L.xlmimo_mlp_backward.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp]
+    L.xlmimo_mlp_adam.argtypes = [vp, vp, vp, vp, i64, dbl, dbl, dbl, dbl, vp]
+    L.xlmimo_mlp_train_step.argtypes = [vp, vp, vp, vp, i64, dbl, vp, vp, vp, i32, vp, vp, vp, vp, vp]
+    L.xlmimo_mlp_pack.argtypes = [vp, vp, vp]
+    L.xlmimo_surrogate_gram.argtypes = [ctypes.POINTER(Array), vp, i32, i32, vp, vp, vp]
     L.xlmimo_last_error.restype = ctypes.c_char_p
     for f in EXPORTS:
-        if f != "xlmimo_last_error":
+        if f not in ("xlmimo_last_error", "xlmimo_mlp_work_floats"):
             getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
@@ -346,3 +362,120 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+# ---- learned correlation surrogate -------------------------------------------------------------
+
+def _opt(t, dtype, name, shape=None):
+    return ctypes.c_void_p(0) if t is None else _dev(t, dtype, name, shape)
+
+
+def xlmimo_pair_features(arr: Array, users: torch.Tensor, gram: torch.Tensor | None = None,
+                         gram_cf: torch.Tensor | None = None, weights: bool = False, stream=None):
+    """(feat [B*P][6], target [B*P][2] or None, weight [B*P] or None), float32, P = K(K-1)/2."""
+    B, K = users.shape[0], users.shape[1]
+    rows = B * (K * (K - 1) // 2)
+    dev = users.device
+    feat = torch.empty((rows, MLP_IN), dtype=torch.float32, device=dev)
+    target = torch.empty((rows, MLP_OUT), dtype=torch.float32, device=dev) if gram is not None else None
+    weight = torch.empty((rows,), dtype=torch.float32, device=dev) if weights else None
+    _check(lib().xlmimo_pair_features(ctypes.byref(arr), _dev(users, torch.float64, "users", (B, K, 2)), K, B,
+                                      _opt(gram, torch.complex128, "gram", (B, K, K)),
+                                      _opt(gram_cf, torch.complex128, "gram_cf", (B, K, K)),
+                                      _dev(feat, torch.float32, "feat"), _opt(target, torch.float32, "target"),
+                                      _opt(weight, torch.float32, "weight"), _stream(stream)))
+    return feat, target, weight
+
+
+def xlmimo_mlp_forward(params: torch.Tensor, x: torch.Tensor, cache: torch.Tensor | None = None,
+                       out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Network output [M][2] float32 (cache, if given, receives z and h of every hidden layer)."""
+    M = x.shape[0]
+    if out is None:
+        out = torch.empty((M, MLP_OUT), dtype=torch.float32, device=x.device)
+    _check(lib().xlmimo_mlp_forward(_dev(params, torch.float32, "params", (MLP_PARAMS,)),
+                                    _dev(x, torch.float32, "x", (M, MLP_IN)), M,
+                                    _dev(out, torch.float32, "out", (M, MLP_OUT)),
+                                    _opt(cache, torch.float32, "cache", (M * MLP_CACHE_PER_ROW,)), _stream(stream)))
+    return out
+
+
+def xlmimo_mlp_loss(out: torch.Tensor, target: torch.Tensor, weight: torch.Tensor | None = None,
+                    dout: torch.Tensor | None = None, loss: torch.Tensor | None = None, stream=None):
+    """(dout [M][2], loss [1]) float32."""
+    M = out.shape[0]
+    if dout is None:
+        dout = torch.empty_like(out)
+    if loss is None:
+        loss = torch.empty((1,), dtype=torch.float32, device=out.device)
+    _check(lib().xlmimo_mlp_loss(_dev(out, torch.float32, "out", (M, MLP_OUT)),
+                                 _dev(target, torch.float32, "target", (M, MLP_OUT)),
+                                 _opt(weight, torch.float32, "weight", (M,)), M,
+                                 _dev(dout, torch.float32, "dout", (M, MLP_OUT)), _dev(loss, torch.float32, "loss"),
+                                 _stream(stream)))
+    return dout, loss
+
+
+def xlmimo_mlp_work_floats(M: int) -> int:
+    return int(lib().xlmimo_mlp_work_floats(int(M)))
+
+
+def xlmimo_mlp_backward(params: torch.Tensor, x: torch.Tensor, cache: torch.Tensor, dout: torch.Tensor,
+                        grad: torch.Tensor | None = None, work: torch.Tensor | None = None, stream=None):
+    """Gradient [MLP_PARAMS] float32 of the loss whose output gradient is dout."""
+    M = x.shape[0]
+    if grad is None:
+        grad = torch.empty((MLP_PARAMS,), dtype=torch.float32, device=x.device)
+    if work is None:
+        work = torch.empty((max(1, xlmimo_mlp_work_floats(M)),), dtype=torch.float32, device=x.device)
+    _check(lib().xlmimo_mlp_backward(_dev(params, torch.float32, "params", (MLP_PARAMS,)),
+                                     _dev(x, torch.float32, "x", (M, MLP_IN)),
+                                     _dev(cache, torch.float32, "cache", (M * MLP_CACHE_PER_ROW,)),
+                                     _dev(dout, torch.float32, "dout", (M, MLP_OUT)), M,
+                                     _dev(grad, torch.float32, "grad", (MLP_PARAMS,)), _dev(work, torch.float32, "work"),
+                                     _stream(stream)))
+    return grad
+
+
+def xlmimo_mlp_adam(params: torch.Tensor, m: torch.Tensor, v: torch.Tensor, grad: torch.Tensor, step: int,
+                    lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, stream=None):
+    for t, n in ((params, "params"), (m, "m"), (v, "v"), (grad, "grad")):
+        _dev(t, torch.float32, n, (MLP_PARAMS,))
+    _check(lib().xlmimo_mlp_adam(_dev(params, torch.float32, "params"), _dev(m, torch.float32, "m"),
+                                 _dev(v, torch.float32, "v"), _dev(grad, torch.float32, "grad"), int(step), float(lr),
+                                 float(beta1), float(beta2), float(eps), _stream(stream)))
+
+
+def xlmimo_mlp_train_step(params, m, v, grad, step: int, lr: float, x, target, weight, out, cache, work, loss,
+                          stream=None):
+    """Forward, loss, backward and Adam on one batch (all buffers caller-owned, see the C header)."""
+    M = x.shape[0]
+    _check(lib().xlmimo_mlp_train_step(
+        _dev(params, torch.float32, "params", (MLP_PARAMS,)), _dev(m, torch.float32, "m", (MLP_PARAMS,)),
+        _dev(v, torch.float32, "v", (MLP_PARAMS,)), _dev(grad, torch.float32, "grad", (MLP_PARAMS,)), int(step),
+        float(lr), _dev(x, torch.float32, "x", (M, MLP_IN)), _dev(target, torch.float32, "target", (M, MLP_OUT)),
+        _opt(weight, torch.float32, "weight", (M,)), M, _dev(out, torch.float32, "out", (M, MLP_OUT)),
+        _dev(cache, torch.float32, "cache", (M * MLP_CACHE_PER_ROW,)), _dev(work, torch.float32, "work"),
+        _opt(loss, torch.float32, "loss"), _stream(stream)))
+
+
+def xlmimo_mlp_pack(params: torch.Tensor, packed: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """BF16 inference image (uint8 [MLP_PACKED_BYTES]) for xlmimo_surrogate_gram."""
+    if packed is None:
+        packed = torch.empty((MLP_PACKED_BYTES,), dtype=torch.uint8, device=params.device)
+    _check(lib().xlmimo_mlp_pack(_dev(params, torch.float32, "params", (MLP_PARAMS,)),
+                                 _dev(packed, torch.uint8, "packed", (MLP_PACKED_BYTES,)), _stream(stream)))
+    return packed
+
+
+def xlmimo_surrogate_gram(arr: Array, users: torch.Tensor, packed: torch.Tensor, gram: torch.Tensor | None = None,
+                          stream=None) -> torch.Tensor:
+    """Surrogate Gram matrices, complex128 [B][K][K]: closed form corrected by the network."""
+    B, K = users.shape[0], users.shape[1]
+    if gram is None:
+        gram = torch.empty((B, K, K), dtype=torch.complex128, device=users.device)
+    _check(lib().xlmimo_surrogate_gram(ctypes.byref(arr), _dev(users, torch.float64, "users", (B, K, 2)), K, B,
+                                       _dev(packed, torch.uint8, "packed", (MLP_PACKED_BYTES,)),
+                                       _dev(gram, torch.complex128, "gram", (B, K, K)), _stream(stream)))
+    return gram
+

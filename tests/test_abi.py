@@ -88,3 +88,27 @@ def test_product_path_has_no_oracle_or_cpu_fallback():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "liboracle" not in text, f
+
+
+def test_surrogate_entries_validate_on_host(xl):
+    L = xl.lib()
+    dummy = ctypes.c_void_p(16)
+    arr = xl.array(1024, 0.01)
+    assert L.xlmimo_pair_features(ctypes.byref(arr), dummy, 1, 1, None, None, dummy, None, None, None) == 1
+    assert L.xlmimo_pair_features(ctypes.byref(arr), dummy, 4, 1, None, None, dummy, dummy, None, None) == 1
+    assert b"targets need" in L.xlmimo_last_error()
+    assert L.xlmimo_pair_features(ctypes.byref(arr), None, 4, 0, None, None, None, None, None, None) == 0
+    assert L.xlmimo_mlp_adam(dummy, dummy, dummy, dummy, 0, 1e-3, 0.9, 0.999, 1e-8, None) == 1
+    assert L.xlmimo_mlp_adam(dummy, dummy, dummy, dummy, 1, 1e-3, 1.0, 0.999, 1e-8, None) == 1
+    assert L.xlmimo_mlp_forward(dummy, dummy, -1, dummy, None, None) == 1
+    assert L.xlmimo_mlp_forward(dummy, dummy, 0, dummy, None, None) == 0
+    assert L.xlmimo_mlp_pack(dummy, ctypes.c_void_p(24), None) == 1
+    assert b"16-byte" in L.xlmimo_last_error()
+    assert L.xlmimo_surrogate_gram(ctypes.byref(arr), dummy, 4, 1, ctypes.c_void_p(8), dummy, None) == 1
+    assert L.xlmimo_surrogate_gram(ctypes.byref(arr), dummy, 65, 1, dummy, dummy, None) == 1
+    assert L.xlmimo_surrogate_gram(ctypes.byref(arr), None, 4, 0, None, None, None) == 0
+    assert L.xlmimo_mlp_train_step(dummy, dummy, dummy, dummy, 1, 1e-3, dummy, dummy, None, 0, dummy, dummy,
+                                   dummy, None, None) == 1
+    # workspace: two [M][256] slabs plus one [257][256] partial per 512 rows
+    assert L.xlmimo_mlp_work_floats(0) == 0
+    assert L.xlmimo_mlp_work_floats(1000) == 2 * 1000 * 256 + 2 * 257 * 256
