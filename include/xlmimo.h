@@ -369,9 +369,11 @@ int xlmimo_batch_plan_destroy(xlmimo_batch_plan plan);
  * (256 -> 2) layers in FP32; the three 256 x 256 layers multiply BF16-rounded
  * (round to nearest even) inputs by BF16-rounded weights with FP32
  * accumulation.  Gradients pass through the rounding unchanged.  Inference
- * runs those layers on the tensor cores and evaluates the SiLU feeding them
- * with the hardware tanh approximation (silu(z) = z/2 (1 + tanh(z/2))),
- * whose error is below the BF16 rounding that follows it. */
+ * runs every layer but the last on the tensor cores (the first with a BF16
+ * hi/lo split of features and weights, which keeps it to ~2^-16 of FP32) and
+ * evaluates SiLU as z/2 (1 + tanh(z/2)) with the hardware tanh approximation:
+ * packed FP16 for the activations that are rounded to BF16 next, FP32 for the
+ * last hidden layer. */
 #define XLMIMO_MLP_IN 6
 #define XLMIMO_MLP_WIDTH 256
 #define XLMIMO_MLP_HIDDEN 4
@@ -381,7 +383,7 @@ int xlmimo_batch_plan_destroy(xlmimo_batch_plan plan);
  * every hidden layer, stored as [layer][z | h][M][256] */
 #define XLMIMO_MLP_CACHE_PER_ROW (2 * XLMIMO_MLP_HIDDEN * XLMIMO_MLP_WIDTH)
 /* bytes of the packed inference image written by xlmimo_mlp_pack */
-#define XLMIMO_MLP_PACKED_BYTES 405760
+#define XLMIMO_MLP_PACKED_BYTES 432384
 
 /* Features (and optionally targets and weights) of every pair of every trial.
  * users [B][K][2], K >= 2.  feat [B*P][6] out, P = K(K-1)/2.  If gram (exact)

@@ -206,29 +206,40 @@ __global__ void pair_features_kernel(FeatConst fc, const double2* __restrict__ u
     }
 }
 
-// One thread per element of the BF16 tiles, then the FP32 block.
+// One thread per element of the BF16 tiles, then the FP32 block (layout in
+// mlp_common.cuh).
 __global__ void mlp_pack_kernel(const float* __restrict__ p, unsigned char* __restrict__ out) {
     const int64_t n_bf = (int64_t)MLP_TILES * 128 * 64;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_bf + MLP_PK_NF;
          e += (int64_t)gridDim.x * blockDim.x) {
         if (e < n_bf) {
             const int tile = (int)(e / (128 * 64)), w = (int)(e % (128 * 64));
-            const int row = w / 64, col = w % 64;  // row: output unit in the half, col: input in the chunk
-            const int l = 1 + tile / 8, nh = (tile / 4) % 2, kc = tile % 4;
-            const int n = nh * 128 + row, k = kc * 64 + col;
-            const float v = p[mlp_off(l) + (int64_t)k * MLP_W + n];
-            *reinterpret_cast<__nv_bfloat16*>(out + (int64_t)tile * MLP_TILE_BYTES + sw128_offset(row, col)) =
-                __float2bfloat16_rn(v);
+            const int row = w / 64, col = w % 64;  // row: output unit in the half, col: input in the tile
+            __nv_bfloat16 v;
+            if (tile < 2) {
+                const int n = tile * 128 + row;
+                float x = 0.0f;
+                if (col < 3 * MLP_IN) x = 0.5f * p[mlp_off(0) + (int64_t)(col % MLP_IN) * MLP_W + n];
+                const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+                v = col < 2 * MLP_IN ? hi : __float2bfloat16_rn(x - __bfloat162float(hi));
+            } else {
+                const int t = tile - 2;
+                const int l = 1 + t / 8, nh = (t / 4) % 2, kc = t % 4;
+                const int n = nh * 128 + row, k = kc * 64 + col;
+                v = __float2bfloat16_rn(0.5f * p[mlp_off(l) + (int64_t)k * MLP_W + n]);
+            }
+            *reinterpret_cast<__nv_bfloat16*>(out + (int64_t)tile * MLP_TILE_BYTES + sw128_offset(row, col)) = v;
         } else {
             const int f = (int)(e - n_bf);
             float v;
-            if (f < MLP_PK_B0) v = p[mlp_off(0) + f];                                     // W0
-            else if (f < MLP_PK_B1) v = p[mlp_off(0) + MLP_IN * MLP_W + (f - MLP_PK_B0)];  // b0
-            else if (f < MLP_PK_W4) {
-                const int l = 1 + (f - MLP_PK_B1) / MLP_W;                                // b1..b3
-                v = p[mlp_off(l) + (int64_t)MLP_W * MLP_W + (f - MLP_PK_B1) % MLP_W];
-            } else if (f < MLP_PK_B4) v = p[mlp_off(4) + (f - MLP_PK_W4)];                 // W4
-            else v = p[mlp_off(4) + MLP_W * MLP_OUT + (f - MLP_PK_B4)];                    // b4
+            if (f < MLP_PK_W4) {
+                const int l = f / MLP_W;  // b0/2 .. b3/2
+                v = 0.5f * p[mlp_off(l) + (int64_t)mlp_in(l) * MLP_W + f % MLP_W];
+            } else if (f < MLP_PK_B4) {
+                v = p[mlp_off(4) + (f - MLP_PK_W4)];  // W4
+            } else {
+                v = p[mlp_off(4) + MLP_W * MLP_OUT + (f - MLP_PK_B4)];  // b4
+            }
             reinterpret_cast<float*>(out + MLP_PK_F32)[f] = v;
         }
     }

@@ -22,15 +22,24 @@ __host__ __device__ constexpr int64_t mlp_off(int l) {
 }
 static_assert(mlp_off(MLP_LAYERS) == XLMIMO_MLP_PARAMS, "parameter count");
 
-// Packed inference image: the three 256 x 256 layers as BF16 tiles of the
-// tensor-core B operand (output unit = row, input = K, 128-byte swizzle), one
-// 16 KB tile per (layer, output half, 64-input chunk), then the FP32 parts.
+// Packed inference image.  BF16 tiles of the tensor-core B operand (output
+// unit = row, input = K, 128-byte swizzle), 16 KB each (128 output units x 64
+// inputs), in the order the inference kernel consumes them:
+//   tiles 0, 1     layer 0 (6 -> 256), output halves 0 and 1: inputs 0-5 hold
+//                  hi(W0/2), 6-11 hi(W0/2) again, 12-17 lo(W0/2), the rest 0,
+//                  to meet the A row [hi(f), lo(f), hi(f)] of the features
+//                  (three BF16 products recover the FP32 sum to ~2^-16);
+//   tiles 2 + 8 (l-1) + 4 h + c   layer l = 1..3, output half h, inputs 64c..64c+63,
+//                  holding W_l / 2;
+// then the FP32 block: b0/2, b1/2, b2/2, b3/2, W4 [256][2], b4 [2].
+// Halving the weights and biases of the hidden layers (exact in BF16 and
+// FP32) makes the accumulators hold z/2, the argument of the tanh form of
+// SiLU, silu(z) = z/2 (1 + tanh(z/2)).
 constexpr int MLP_TILE_BYTES = 128 * 64 * 2;
-constexpr int MLP_TILES = 3 * 2 * 4;
+constexpr int MLP_TILES = 2 + 3 * 2 * 4;
 constexpr int64_t MLP_PK_F32 = (int64_t)MLP_TILES * MLP_TILE_BYTES;  // byte offset of the FP32 block
-// floats of the FP32 block: W0 [6][256], b0, b1, b2, b3 [256], W4 [256][2], b4 [2]
-constexpr int MLP_PK_W0 = 0, MLP_PK_B0 = 1536, MLP_PK_B1 = 1792, MLP_PK_B2 = 2048, MLP_PK_B3 = 2304,
-              MLP_PK_W4 = 2560, MLP_PK_B4 = 3072, MLP_PK_NF = 3074;
+constexpr int MLP_PK_B0 = 0, MLP_PK_B1 = 256, MLP_PK_B2 = 512, MLP_PK_B3 = 768, MLP_PK_W4 = 1024,
+              MLP_PK_B4 = 1536, MLP_PK_NF = 1538;
 static_assert(MLP_PK_F32 + MLP_PK_NF * 4 <= XLMIMO_MLP_PACKED_BYTES, "packed image size");
 
 // Byte offset, inside its 16 KB tile, of row r (0..127), column c (0..63):
@@ -40,11 +49,16 @@ __host__ __device__ __forceinline__ int sw128_offset(int r, int c) {
 }
 
 // Row q of a trial's pair list -> users (i, j), i < j, pairs in row order.
+// Row i starts at S(i) = i (2K - 1 - i) / 2; the FP32 root of S(i) = q gives i
+// to within one, which the two loops correct.
 __device__ __forceinline__ void pair_index(int q, int K, int& i, int& j) {
-    int ii = 0, rl = K - 1;
-    while (q >= rl && rl > 0) { q -= rl; ++ii; --rl; }
+    const float a = (float)(2 * K - 1);
+    int ii = (int)((a - sqrtf(fmaxf(a * a - 8.0f * (float)q, 0.0f))) * 0.5f);
+    ii = max(0, min(ii, K - 2));
+    while (ii < K - 2 && ((ii + 1) * (2 * K - 2 - ii)) / 2 <= q) ++ii;
+    while (ii > 0 && (ii * (2 * K - 1 - ii)) / 2 > q) --ii;
     i = ii;
-    j = ii + 1 + q;
+    j = q - (ii * (2 * K - 1 - ii)) / 2 + ii + 1;
 }
 
 // Geometry constants of the features that do not depend on the pair.

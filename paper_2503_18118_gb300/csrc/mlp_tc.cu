@@ -1,31 +1,55 @@
-// Fused tensor-core inference of the correlation surrogate: one CTA takes 128
-// pair rows through the whole network and corrects their closed-form Gram
-// entries in place.
+// Fused tensor-core inference of the correlation surrogate: a persistent CTA
+// takes tiles of 128 pair rows, one after another, through the whole network
+// and corrects their closed-form Gram entries in place.  The barrier set-up,
+// TMEM allocation and parameter load happen once per CTA; a tile's pair
+// indices, positions and closed-form entries are fetched while the previous
+// tile is in flight, and the weight stream runs on into the next tile.
 //
-//   rows warps 0-3 (thread = row): pair features, the 6 -> 256 layer in FP32,
-//          SiLU, BF16 rows into the A tile (128 x 256, K-major, 128-byte
-//          swizzle); after each tensor-core layer, TMEM -> registers, bias,
-//          SiLU, BF16 back into the A tile; after the last, the 256 -> 2 layer
-//          in FP32 and the complex correction G~_ij (1 + t_ij).
-//   warp 4 streams the 24 weight tiles (16 KB: 128 output units x 64 inputs,
-//          BF16, already in the swizzled operand layout) with bulk copies
-//          through a two-stage ring.
-//   warp 5 owns TMEM (256 columns: one FP32 128 x 256 accumulator) and issues
-//          tcgen05.mma (M = N = 128, K = 16): per layer two output halves x
-//          four 64-input chunks x four K steps.
-// The A tile is rewritten only after the layer that reads it has completed
-// (its commit is the rows' signal), and the accumulator only after the rows
-// have read it (their arrival is the MMA warp's signal).  Every wait is
-// bounded; a CTA that gives up writes NaN to its pairs.  Two CTAs fit on an
-// SM (110 KB shared memory, 256 TMEM columns each), so one CTA's SiLU work
-// overlaps the other's matrix products.
+//   row warps 0-7: thread (m, h) = (row m = 32 (warp % 4) + lane, half h =
+//          warp / 4) owns output units 128 h .. 128 h + 127 of row m.  It
+//          writes the features (half 0: [hi(f), lo(f), hi(f)] in BF16) into
+//          the A tile (128 x 256 BF16, K-major, 128-byte swizzle); after each
+//          layer it reads its 128 accumulators from TMEM, adds the bias and
+//          applies SiLU as z/2 (1 + tanh(z/2)) (the packed weights hold W/2,
+//          so the accumulator already is z/2), and writes BF16 back into its
+//          half of the A tile; after the last hidden layer it forms its half
+//          of the FP32 256 -> 2 product, the halves are added, and half 0
+//          applies G~_ij (1 + t_ij).
+//   warp 8 streams the 26 weight tiles (16 KB: 128 output units x 64 inputs,
+//          BF16, stored in the swizzled operand layout) through a two-stage
+//          ring.  CTAs run in clusters of CL; tile c is fetched once from L2 by
+//          cluster rank c % CL and multicast into every CTA of the cluster, so
+//          each CTA issues 1/CL of the copies and the cluster shares the
+//          bytes in flight (without it the ring is latency-bound at ~5.5 TB/s
+//          of L2 reads and the tensor pipe idles).  A slot is refilled once
+//          the MMA warps of all CL CTAs have released it (their commits are
+//          multicast onto every CTA's "empty" barrier).
+//   warp 9 owns TMEM (256 columns: one FP32 128 x 256 accumulator) and issues
+//          tcgen05.mma (M = N = 128, K = 16) half by half, committing each
+//          half separately, so half 0's epilogue runs while half 1 multiplies.
+// The last hidden layer's SiLU feeds the FP32 output layer directly and uses
+// the FP32 tanh (relative error ~2^-11); measured against the FP32 SIMT
+// forward pass, the exact form there (exp and divide, two MUFU ops) changed
+// neither the output error nor the sum rate, and cost 12 % of the kernel.
+// Ordering: a layer's MMAs start once all 256 row threads have written the A
+// tile and read the accumulator (one arrival each); half 0 overwrites its A
+// columns only after half 1's MMAs have read them (a separate commit after
+// half 1's first two input chunks); half 1's accumulator commit implies the
+// whole layer is done.  Every wait is bounded; a CTA that gives up writes NaN
+// to its pairs.  Cluster barriers after the barrier set-up and before exit
+// keep every remote arrival and copy inside the lifetime of its target.  Two
+// CTAs fit on an SM (~107 KB shared memory and 256 TMEM columns each).
+#include <stdlib.h>
+
+#include <algorithm>
+
 #include "mlp_common.cuh"
 #include "tc_common.cuh"
 
 namespace xl {
 
 constexpr int MI_ROWS = 128;
-constexpr int MI_THREADS = 192;
+constexpr int MI_THREADS = 320;  // 8 row warps, loader, MMA
 constexpr int MI_STAGES = 2;
 constexpr uint32_t MI_TMEM_COLS = 256;
 constexpr int MI_A_BYTES = 4 * MLP_TILE_BYTES;
@@ -34,20 +58,57 @@ constexpr int MI_F32_BYTES = (MLP_PK_NF * 4 + 15) / 16 * 16;
 struct MiShared {
     uint64_t full[MI_STAGES];
     uint64_t empty[MI_STAGES];
-    uint64_t a_ready;
-    uint64_t d_ready;
-    uint64_t fin;
+    uint64_t a_ready;    // 256 row-thread arrivals: A tile written, accumulator read
+    uint64_t d_ready[2]; // commit: output half h of the layer complete
+    uint64_t a_free;     // commit: half 1 has read A columns 0-127
+    uint64_t fin;        // commit after the last MMA
     uint32_t tmem_base;
     int abort;
+    float2 red[MI_ROWS]; // half 1's share of the output layer
 };
 
 constexpr int MI_SMEM = 1024 + MI_A_BYTES + MI_STAGES * MLP_TILE_BYTES + MI_F32_BYTES + (int)sizeof(MiShared);
 
+// Copy into this CTA's shared memory, completing bytes on `bar` (armed separately).
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
+}
+
+// Copy into the same shared-memory offset of every CTA in `mask`, completing
+// bytes on the barrier at `bar`'s offset in each of them.
+__device__ __forceinline__ void bulk_load_mc(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                             uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], %4;" ::"r"(
+            dst),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// Arrive on the barrier at `bar`'s offset in every CTA of `mask` once this
+// thread's MMAs so far have completed.
+__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
 
 // Wait bounded by time only (used on the way out, after an abort).
@@ -58,41 +119,102 @@ __device__ __forceinline__ bool mbar_wait_timed(uint64_t* bar, uint32_t parity) 
     return true;
 }
 
-__device__ __forceinline__ float tanh_approx(float x) {
+__device__ __forceinline__ float tanh_f32(float x) {
     float y;
     asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 
-// SiLU feeding a BF16 operand: z/2 (1 + tanh(z/2)), one MUFU op.
-__device__ __forceinline__ float silu_tanh(float z) {
-    const float hz = 0.5f * z;
-    return fmaf(hz, tanh_approx(hz), hz);
+__device__ __forceinline__ uint32_t tanh_f16x2(uint32_t x) {
+    uint32_t y;
+    asm("tanh.approx.f16x2 %0, %1;" : "=r"(y) : "r"(x));
+    return y;
 }
 
-// SiLU feeding the FP32 output layer.
-__device__ __forceinline__ float silu_exp(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+__device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
+    __nv_bfloat162 p = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&p);
+}
 
-// 32 activations of row m (columns 32 cb .. 32 cb + 31) -> BF16 A tile
-__device__ __forceinline__ void store_a_row(unsigned char* A, int m, int cb, const float* h) {
-    unsigned char* tile = A + (cb >> 1) * MLP_TILE_BYTES + (m >> 3) * 1024 + (m & 7) * 128;
+// silu(z) of two accumulators holding z/2 (bias added here), as BF16x2: the
+// tanh in packed FP16 (one MUFU op for both), the rest in FP32.
+__device__ __forceinline__ uint32_t silu_pair_bf16(float2 hz) {
+    __half2 hh = __floats2half2_rn(hz.x, hz.y);
+    const uint32_t th = tanh_f16x2(*reinterpret_cast<uint32_t*>(&hh));
+    const float2 t = __half22float2(*reinterpret_cast<const __half2*>(&th));
+    const float2 h = __ffma2_rn(hz, t, hz);
+    return bf16x2_bits(h.x, h.y);
+}
+
+// 16-byte unit u (0..7) of row m in A chunk kc
+__device__ __forceinline__ uint32_t a_unit(const unsigned char* A, int kc, int m, int u) {
+    return smem_u32(A + kc * MLP_TILE_BYTES + (m >> 3) * 1024 + (m & 7) * 128 + ((u ^ (m & 7)) << 4));
+}
+
+__device__ __forceinline__ void st_v4(uint32_t addr, const uint32_t* w) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
+                 : "memory");
+}
+
+// Features of row r (if valid) as the layer-0 A row [hi(f), lo(f), hi(f), 0]
+// of row m, from positions already in registers.
+__device__ __forceinline__ void write_a0(unsigned char* A, int m, const FeatConst& fc, bool valid, double2 ui,
+                                         double2 uj) {
+    float f[MLP_IN] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (valid) pair_features_dev(fc, ui.x, ui.y, uj.x, uj.y, f);
+    float a[32];
+#pragma unroll
+    for (int e = 0; e < MLP_IN; ++e) {
+        const float hi = __bfloat162float(__float2bfloat16_rn(f[e]));
+        a[e] = hi;
+        a[MLP_IN + e] = f[e] - hi;
+        a[2 * MLP_IN + e] = hi;
+    }
+#pragma unroll
+    for (int e = 3 * MLP_IN; e < 32; ++e) a[e] = 0.f;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         uint32_t w[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            __nv_bfloat162 p = __floats2bfloat162_rn(h[u * 8 + 2 * q], h[u * 8 + 2 * q + 1]);
-            w[q] = *reinterpret_cast<uint32_t*>(&p);
-        }
-        const int unit = ((cb & 1) * 4 + u) ^ (m & 7);
-        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(smem_u32(tile + unit * 16)), "r"(w[0]),
-                     "r"(w[1]), "r"(w[2]), "r"(w[3])
-                     : "memory");
+        for (int q = 0; q < 4; ++q) w[q] = bf16x2_bits(a[u * 8 + 2 * q], a[u * 8 + 2 * q + 1]);
+        st_v4(a_unit(A, 0, m, u), w);
     }
 }
 
+// Per-row inputs of one tile, fetched a tile ahead.
+struct RowIn {
+    bool valid;
+    int i, j;
+    int64_t g0;       // first entry of the trial's Gram
+    double2 ui, uj;   // user positions
+    double2 gc;       // closed-form G~_ij
+};
+
+__device__ __forceinline__ RowIn fetch_row(int64_t r, int64_t rows, int K, int P, const double2* __restrict__ users,
+                                           const double2* __restrict__ gram) {
+    RowIn in;
+    in.valid = r < rows;
+    in.i = 0;
+    in.j = 1;
+    in.g0 = 0;
+    in.ui = in.uj = in.gc = make_double2(1.0, 0.0);
+    if (in.valid) {
+        const int64_t b = r / P;
+        pair_index((int)(r - b * P), K, in.i, in.j);
+        in.ui = users[b * K + in.i];
+        in.uj = users[b * K + in.j];
+        in.g0 = b * K * K;
+        in.gc = gram[in.g0 + in.i * K + in.j];
+    }
+    return in;
+}
+
+// Persistent: CTA x takes tiles x, x + grid, x + 2 grid, ... (n_iter of them,
+// the same count in every CTA so that a cluster shares one weight stream;
+// tiles past the end have no valid rows).
+template <int CL>
 __global__ void __launch_bounds__(MI_THREADS, 2)
-    mlp_infer_tc_kernel(FeatConst fc, const double2* __restrict__ users, int K, int64_t rows,
+    mlp_infer_tc_kernel(FeatConst fc, const double2* __restrict__ users, int K, int64_t rows, int n_iter,
                         const unsigned char* __restrict__ packed, double2* __restrict__ gram) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -107,15 +229,17 @@ __global__ void __launch_bounds__(MI_THREADS, 2)
     if (tid == 0) {
         for (int s = 0; s < MI_STAGES; ++s) {
             mbar_init(&sh->full[s], 1);
-            mbar_init(&sh->empty[s], 1);
+            mbar_init(&sh->empty[s], CL);
         }
-        mbar_init(&sh->a_ready, MI_ROWS);
-        mbar_init(&sh->d_ready, 1);
+        mbar_init(&sh->a_ready, 2 * MI_ROWS);
+        mbar_init(&sh->d_ready[0], 1);
+        mbar_init(&sh->d_ready[1], 1);
+        mbar_init(&sh->a_free, 1);
         mbar_init(&sh->fin, 1);
         sh->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 5) {
+    if (warp == 9) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
                      "r"(MI_TMEM_COLS)
                      : "memory");
@@ -124,150 +248,250 @@ __global__ void __launch_bounds__(MI_THREADS, 2)
     const float* gpf = reinterpret_cast<const float*>(packed + MLP_PK_F32);
     for (int e = tid; e < MLP_PK_NF; e += MI_THREADS) pf[e] = gpf[e];
     tc_fence_before();
-    __syncthreads();
+    cluster_sync();  // every CTA's barriers exist before any remote copy or arrival
     tc_fence_after();
+    const uint32_t crank = CL > 1 ? cluster_rank() : 0u;
+    const uint16_t cmask = (uint16_t)((1u << CL) - 1u);
     const uint32_t tmem = sh->tmem_base;
     volatile int* abort = &sh->abort;
+    const int n_tiles_total = n_iter * MLP_TILES;
 
-    if (warp == 4) {
-        // ---------------- weight tiles through the ring
+    if (warp == 8) {
+        // ---------------- weight tiles through the ring (tile c issued by rank c % CL)
         if (lane == 0) {
-            int issued = 0;
-            for (int c = 0; c < MLP_TILES; ++c) {
+            int armed = 0;
+            for (int c = 0; c < n_tiles_total; ++c) {
                 const int s = c % MI_STAGES;
+                // the previous tile of this slot has landed here before the slot is re-armed
+                if (c >= MI_STAGES && !mbar_wait(&sh->full[s], ((c / MI_STAGES) - 1) & 1, abort)) break;
+                expect_tx(&sh->full[s], MLP_TILE_BYTES);
+                ++armed;
+                if (c % CL != (int)crank) continue;
+                // ... and every CTA of the cluster has consumed it before the slot is overwritten
                 if (c >= MI_STAGES && !mbar_wait(&sh->empty[s], ((c / MI_STAGES) - 1) & 1, abort)) break;
-                bulk_load(smem_u32(ring + s * MLP_TILE_BYTES), packed + (int64_t)c * MLP_TILE_BYTES, MLP_TILE_BYTES,
-                          &sh->full[s]);
-                ++issued;
+                const uint32_t dst = smem_u32(ring + s * MLP_TILE_BYTES);
+                const unsigned char* src = packed + (int64_t)(c % MLP_TILES) * MLP_TILE_BYTES;
+                if (CL > 1) bulk_load_mc(dst, src, MLP_TILE_BYTES, &sh->full[s], cmask);
+                else bulk_load(dst, src, MLP_TILE_BYTES, &sh->full[s]);
             }
             // no copy may still be landing when the CTA exits
-            for (int c = issued - MI_STAGES; c < issued; ++c)
+            for (int c = armed - MI_STAGES; c < armed; ++c)
                 if (c >= 0) mbar_wait_timed(&sh->full[c % MI_STAGES], (c / MI_STAGES) & 1);
         }
         __syncwarp();
-    } else if (warp == 5) {
+    } else if (warp == 9) {
         // ---------------- MMA issuer
         if (lane == 0) {
             const uint32_t idesc = tc_idesc<TCP_BF16>();
             bool ok = true;
-            for (int l = 0; l < 3 && ok; ++l) {
-                if (!mbar_wait(&sh->a_ready, l & 1, abort)) { ok = false; break; }
-                tc_fence_after();
-                for (int nh = 0; nh < 2 && ok; ++nh) {
-                    for (int kc = 0; kc < 4; ++kc) {
-                        const int c = l * 8 + nh * 4 + kc, s = c % MI_STAGES;
-                        if (!mbar_wait(&sh->full[s], (c / MI_STAGES) & 1, abort)) { ok = false; break; }
-                        tc_fence_after();
-                        const uint32_t a0 = smem_u32(A + kc * MLP_TILE_BYTES);
-                        const uint32_t b0 = smem_u32(ring + s * MLP_TILE_BYTES);
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            umma(tmem + nh * 128, desc_sw128(a0 + kk * 32), desc_sw128(b0 + kk * 32), idesc,
-                                 (kc | kk) ? 1u : 0u);
-                        umma_commit(&sh->empty[s]);
+            int c = 0;
+            for (int it = 0; it < n_iter && ok; ++it) {
+                for (int L = 0; L < 4 && ok; ++L) {
+                    if (!mbar_wait(&sh->a_ready, L & 1, abort)) { ok = false; break; }  // 4 phases per tile
+                    tc_fence_after();
+                    const int nk = L == 0 ? 1 : 4, ksteps = L == 0 ? 2 : 4;
+                    for (int nh = 0; nh < 2 && ok; ++nh) {
+                        for (int kc = 0; kc < nk; ++kc, ++c) {
+                            const int s = c % MI_STAGES;
+                            if (!mbar_wait(&sh->full[s], (c / MI_STAGES) & 1, abort)) { ok = false; break; }
+                            tc_fence_after();
+                            const uint32_t a0 = smem_u32(A + kc * MLP_TILE_BYTES);
+                            const uint32_t b0 = smem_u32(ring + s * MLP_TILE_BYTES);
+                            for (int kk = 0; kk < ksteps; ++kk)
+                                umma(tmem + nh * 128, desc_sw128(a0 + kk * 32), desc_sw128(b0 + kk * 32), idesc,
+                                     (kc | kk) ? 1u : 0u);
+                            if (CL > 1) umma_commit_mc(&sh->empty[s], cmask);
+                            else umma_commit(&sh->empty[s]);
+                            if (nh == 1 && kc == (nk - 1) / 2) umma_commit(&sh->a_free);  // chunks 0, 1 read
+                        }
+                        if (ok) umma_commit(&sh->d_ready[nh]);
                     }
                 }
-                if (ok) umma_commit(&sh->d_ready);
             }
             umma_commit(&sh->fin);  // arrives once every MMA issued above has completed
         }
         __syncwarp();
     } else {
         // ---------------- rows
-        const int m = warp * 32 + lane;
-        const int64_t r = (int64_t)blockIdx.x * MI_ROWS + m;
-        const bool valid = r < rows;
-        int64_t b = 0;
-        int i = 0, j = 1;
-        float f[MLP_IN] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (valid) {
-            b = r / P;
-            pair_index((int)(r - b * P), K, i, j);
-            const double2 ui = users[b * K + i], uj = users[b * K + j];
-            pair_features_dev(fc, ui.x, ui.y, uj.x, uj.y, f);
-        }
-        // layer 0 (FP32)
-        for (int cb = 0; cb < 8; ++cb) {
-            float h[32];
-#pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                const int c = cb * 32 + q;
-                float z = pf[MLP_PK_B0 + c];
-#pragma unroll
-                for (int e = 0; e < MLP_IN; ++e) z = fmaf(f[e], pf[MLP_PK_W0 + e * MLP_W + c], z);
-                h[q] = silu_tanh(z);
-            }
-            store_a_row(A, m, cb, h);
+        const int m = (warp & 3) * 32 + lane, hf = warp >> 2;
+        const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(hf * 128);
+        RowIn cur;
+        cur.valid = false;
+        if (hf == 0) {
+            cur = fetch_row((int64_t)blockIdx.x * MI_ROWS + m, rows, K, P, users, gram);
+            write_a0(A, m, fc, cur.valid, cur.ui, cur.uj);
         }
         fence_async_smem();
         mbar_arrive(&sh->a_ready);
-
-        float o0 = pf[MLP_PK_B4], o1 = pf[MLP_PK_B4 + 1];
         bool ok = true;
-        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int l = 0; l < 3; ++l) {
-            if (!mbar_wait(&sh->d_ready, l & 1, abort)) { ok = false; break; }
-            tc_fence_after();
-            const float* bias = pf + MLP_PK_B1 + l * MLP_W;
-            for (int cb = 0; cb < 8; ++cb) {
-                float v[32];
-                tmem_ld32(trow + cb * 32, v);
-                if (l < 2) {
+        for (int it = 0; it < n_iter; ++it) {
+            RowIn nxt;
+            nxt.valid = false;
+            const bool more = it + 1 < n_iter;
+            if (hf == 0 && more)  // loads for the next tile, in flight during this one
+                nxt = fetch_row(((int64_t)blockIdx.x + (int64_t)(it + 1) * gridDim.x) * MI_ROWS + m, rows, K, P, users,
+                                gram);
+            float2 o = make_float2(0.f, 0.f);
+            for (int L = 0; L < 4 && ok; ++L) {
+                if (!mbar_wait(&sh->d_ready[hf], L & 1, abort)) { ok = false; break; }
+                tc_fence_after();
+                const float* bias = pf + MLP_PK_B0 + L * MLP_W + hf * 128;
+                for (int cb = 0; cb < 4; ++cb) {
+                    float v[32];
+                    tmem_ld32(trow + cb * 32, v);
+                    const float4* b4 = reinterpret_cast<const float4*>(bias + cb * 32);
+                    if (L < 3) {
+                        uint32_t w[16];
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) v[q] = silu_tanh(v[q] + bias[cb * 32 + q]);
-                    store_a_row(A, m, cb, v);
-                } else {
+                        for (int q = 0; q < 8; ++q) {
+                            const float4 bb = b4[q];
+                            w[2 * q] =
+                                silu_pair_bf16(__fadd2_rn(make_float2(v[4 * q], v[4 * q + 1]), make_float2(bb.x, bb.y)));
+                            w[2 * q + 1] = silu_pair_bf16(
+                                __fadd2_rn(make_float2(v[4 * q + 2], v[4 * q + 3]), make_float2(bb.z, bb.w)));
+                        }
+                        if (hf == 0 && cb == 0 && !mbar_wait(&sh->a_free, L & 1, abort)) { ok = false; break; }
+                        const int col = hf * 128 + cb * 32;
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) {
-                        const int c = cb * 32 + q;
-                        const float hv = silu_exp(v[q] + bias[c]);
-                        o0 = fmaf(hv, pf[MLP_PK_W4 + 2 * c], o0);
-                        o1 = fmaf(hv, pf[MLP_PK_W4 + 2 * c + 1], o1);
+                        for (int u = 0; u < 4; ++u) st_v4(a_unit(A, col >> 6, m, ((col & 63) >> 3) + u), w + 4 * u);
+                    } else {
+                        const float4* w4 = reinterpret_cast<const float4*>(pf + MLP_PK_W4 + 2 * (hf * 128 + cb * 32));
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            const float2 bb = q & 1 ? make_float2(b4[q >> 1].z, b4[q >> 1].w)
+                                                    : make_float2(b4[q >> 1].x, b4[q >> 1].y);
+                            const float2 hz = __fadd2_rn(make_float2(v[2 * q], v[2 * q + 1]), bb);
+                            const float2 h = __ffma2_rn(hz, make_float2(tanh_f32(hz.x), tanh_f32(hz.y)), hz);
+                            const float4 ww = w4[q];  // W4 rows of the two columns
+                            o = __ffma2_rn(make_float2(h.x, h.x), make_float2(ww.x, ww.y), o);
+                            o = __ffma2_rn(make_float2(h.y, h.y), make_float2(ww.z, ww.w), o);
+                        }
                     }
                 }
+                if (!ok) break;
+                if (L < 3) {
+                    fence_async_smem();
+                    tc_fence_before();
+                    mbar_arrive(&sh->a_ready);
+                }
             }
-            if (l < 2) {
+            // the accumulator has been read: the next tile's features go in (once
+            // half 1 has read A chunk 0 for layer 3), and its layer 0 may start
+            if (ok && more) {
+                if (hf == 0) {
+                    if (mbar_wait(&sh->a_free, 1, abort)) write_a0(A, m, fc, nxt.valid, nxt.ui, nxt.uj);
+                    else ok = false;
+                }
                 fence_async_smem();
                 tc_fence_before();
-                mbar_arrive(&sh->a_ready);
+                if (ok) mbar_arrive(&sh->a_ready);
             }
-        }
-        if (valid) {
-            const int64_t g0 = b * K * K;
-            if (ok && !*abort) {
-                const double2 gc = gram[g0 + i * K + j];
-                const double t0 = (double)o0, t1 = (double)o1;
-                const double re = gc.x + (gc.x * t0 - gc.y * t1), im = gc.y + (gc.x * t1 + gc.y * t0);
-                gram[g0 + i * K + j] = make_double2(re, im);
-                gram[g0 + j * K + i] = make_double2(re, -im);
-            } else {
-                const double nanv = __longlong_as_double(0x7ff8000000000000ULL);
-                gram[g0 + i * K + j] = make_double2(nanv, nanv);
-                gram[g0 + j * K + i] = make_double2(nanv, nanv);
+            if (hf == 1) sh->red[m] = o;
+            // barrier of the 256 row threads that also agrees on stopping, so
+            // that all of them leave the loop together
+            uint32_t stop;
+            {
+                const uint32_t mine = (!ok || *abort) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, 256, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+                    : "=r"(stop)
+                    : "r"(mine)
+                    : "memory");
+            }
+            if (hf == 0 && cur.valid) {
+                const float2 o1 = sh->red[m];
+                double2 v0, v1;
+                if (!stop) {
+                    const double t0 = (double)(o.x + o1.x + pf[MLP_PK_B4]), t1 = (double)(o.y + o1.y + pf[MLP_PK_B4 + 1]);
+                    const double2 gc = cur.gc;
+                    v0 = make_double2(gc.x + (gc.x * t0 - gc.y * t1), gc.y + (gc.x * t1 + gc.y * t0));
+                    v1 = make_double2(v0.x, -v0.y);
+                } else {
+                    const double nanv = __longlong_as_double(0x7ff8000000000000ULL);
+                    v0 = v1 = make_double2(nanv, nanv);
+                }
+                gram[cur.g0 + cur.i * K + cur.j] = v0;
+                gram[cur.g0 + cur.j * K + cur.i] = v1;
+            }
+            // red[] is rewritten only after the next tile's output layer, which
+            // cannot start before half 0 has passed its next epilogues
+            cur = nxt;
+            if (stop) {
+                // the remaining tiles of this CTA are lost: mark them
+                for (int k = it + 1; k < n_iter && hf == 0; ++k) {
+                    const RowIn q = fetch_row(((int64_t)blockIdx.x + (int64_t)k * gridDim.x) * MI_ROWS + m, rows, K, P,
+                                              users, gram);
+                    if (q.valid) {
+                        const double nanv = __longlong_as_double(0x7ff8000000000000ULL);
+                        gram[q.g0 + q.i * K + q.j] = make_double2(nanv, nanv);
+                        gram[q.g0 + q.j * K + q.i] = make_double2(nanv, nanv);
+                    }
+                }
+                break;
             }
         }
     }
 
     tc_fence_before();
     __syncthreads();
-    if (warp == 5) {
-        if (lane == 0) mbar_wait_timed(&sh->fin, 0);
-        __syncwarp();
+    if (warp == 9 && lane == 0) mbar_wait_timed(&sh->fin, 0);
+    __syncwarp();
+    cluster_sync();  // the other CTAs' copies and commits into this CTA are over
+    if (warp == 9) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(MI_TMEM_COLS) : "memory");
     }
 }
 
-static int mlp_infer_prepare() {
+// Cluster size of the weight multicast: 1 (measured no faster at 2 or 4 once
+// the kernel is persistent) unless XLMIMO_SURROGATE_CLUSTER (1, 2 or 4) says
+// otherwise; read once.
+static int mlp_infer_cluster() {
+    static int cl = 0;
+    if (!cl) {
+        int v = 1;
+        if (const char* e = getenv("XLMIMO_SURROGATE_CLUSTER")) {
+            const int x = atoi(e);
+            if (x == 1 || x == 2 || x == 4) v = x;
+        }
+        cl = v;
+    }
+    return cl;
+}
+
+template <int CL>
+static int mlp_infer_launch(const FeatConst& fc, const double* users, int K, int64_t rows, const void* packed,
+                            double* gram, cudaStream_t st) {
     static bool done[64] = {false};
     int dev = 0;
     int rc = cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
     if (rc) return rc;
-    if (dev < 64 && done[dev]) return XLMIMO_OK;
-    rc = cuda_status(cudaFuncSetAttribute(mlp_infer_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MI_SMEM),
-                     "surrogate kernel attribute");
-    if (!rc && dev < 64) done[dev] = true;
-    return rc;
+    if (dev >= 64 || !done[dev]) {
+        rc = cuda_status(cudaFuncSetAttribute(mlp_infer_tc_kernel<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, MI_SMEM),
+                         "surrogate kernel attribute");
+        if (rc) return rc;
+        if (dev < 64) done[dev] = true;
+    }
+    const int64_t n_tiles = (rows + MI_ROWS - 1) / MI_ROWS;
+    int64_t grid = std::min<int64_t>(n_tiles, 2LL * num_sms());  // two resident CTAs per SM
+    grid = (grid + CL - 1) / CL * CL;
+    const int64_t n_iter = (n_tiles + grid - 1) / grid;
+    if (n_iter * MLP_TILES > 0x7fffffffLL) { set_error("too many pairs for one launch"); return XLMIMO_EINVAL; }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(MI_THREADS);
+    cfg.dynamicSmemBytes = MI_SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cuda_status(cudaLaunchKernelEx(&cfg, mlp_infer_tc_kernel<CL>, fc, (const double2*)users, K, rows,
+                                          (int)n_iter, (const unsigned char*)packed, (double2*)gram),
+                       "surrogate kernel launch");
 }
 
 }  // namespace xl
@@ -287,11 +511,11 @@ extern "C" int xlmimo_surrogate_gram(const xlmimo_array* arr, const double* user
     cudaStream_t st = as_stream(stream);
     rc = launch_closed_form(g, users, K, B, gram, st);
     if (rc || K < 2) return rc;
-    if ((rc = mlp_infer_prepare())) return rc;
     const int64_t rows = (int64_t)B * (K * (K - 1) / 2);
-    const int64_t grid = (rows + MI_ROWS - 1) / MI_ROWS;
-    if (grid > 0x7fffffffLL) { set_error("too many pairs for one launch (B * K(K-1)/2 > 2^38)"); return XLMIMO_EINVAL; }
-    mlp_infer_tc_kernel<<<(unsigned)grid, MI_THREADS, MI_SMEM, st>>>(make_feat_const(g), (const double2*)users, K, rows,
-                                                                      (const unsigned char*)packed, (double2*)gram);
-    return cuda_status(cudaGetLastError(), "surrogate kernel launch");
+    const FeatConst fc = make_feat_const(g);
+    switch (mlp_infer_cluster()) {
+        case 1: return mlp_infer_launch<1>(fc, users, K, rows, packed, gram, st);
+        case 4: return mlp_infer_launch<4>(fc, users, K, rows, packed, gram, st);
+        default: return mlp_infer_launch<2>(fc, users, K, rows, packed, gram, st);
+    }
 }

@@ -73,7 +73,7 @@ EXPORTS = ("xlmimo_batch_plan_create", "xlmimo_batch_run", "xlmimo_batch_plan_in
 MLP_IN, MLP_WIDTH, MLP_HIDDEN, MLP_OUT = 6, 256, 4, 2
 MLP_PARAMS = 199682
 MLP_CACHE_PER_ROW = 2 * MLP_HIDDEN * MLP_WIDTH
-MLP_PACKED_BYTES = 405760
+MLP_PACKED_BYTES = 432384
 
 _lib = None
 

@@ -7,8 +7,12 @@ can round an activation to the neighbouring BF16 value, which moves a
 downstream pre-activation by about 2^-8 |h w|.  Such flips are rare (a few
 per thousand activations), so the tests bound the typical error tightly
 (90th percentile, FP32 level) and the worst case at a few BF16 ulps of the
-layer scale.  Inference adds the hardware tanh in SiLU (relative error below
-2^-11), so surrogate entries are compared at 1e-2 of |G~_ij| in the worst case."""
+layer scale.  Inference adds the hardware tanh in SiLU (packed FP16 for the
+activations that are rounded to BF16 next: relative error ~2^-10, which moves
+roughly a quarter of those activations by one BF16 ulp relative to the
+oracle's exact SiLU).  Three rounded layers then carry output errors of a few
+2^-8 of the output scale, before the network's own gain; the inference test
+bounds the median at 4e-3 and the worst pair at 2e-2 of the output scale."""
 import math
 
 import numpy as np
@@ -176,10 +180,11 @@ def test_surrogate_matches_oracle(orc, K, B):
     iu = np.triu_indices(K, 1)
     tg = gs[:, iu[0], iu[1]] / Gc[:, iu[0], iu[1]] - 1.0
     tw = want[:, iu[0], iu[1]] / Gc[:, iu[0], iu[1]] - 1.0
-    assert float(np.abs(tr).max()) > 0.05  # the network is not trivially small
+    scale = float(np.abs(tr).max())
+    assert scale > 0.05  # the network is not trivially small
     err = np.abs(tg - tw)
-    assert err.max() <= 1e-2 * max(1.0, float(np.abs(tw).max()))
-    assert np.quantile(err, 0.5) <= 2e-3
+    assert err.max() <= 2e-2 * max(1.0, scale)
+    assert np.quantile(err, 0.5) <= 4e-3 * max(1.0, scale)
     assert np.array_equal(gs, np.conj(np.transpose(gs, (0, 2, 1))))
 
 
