@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--chunks", type=int, default=0, help="pipeline pieces per step (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-baseline", action="store_true")
+    ap.add_argument("--source-hash", metavar="KERNEL", help="print the source hash a profile summary records, and exit")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the precision table, the ragged batch and the surrogate")
     return ap.parse_args()
@@ -169,11 +170,31 @@ def reference_arm(args, wl):
 
 
 # ------------------------------------------------------------ GPU arm -------
-def traffic_from_profile(path_name):
-    """DRAM bytes per launch recorded by the committed ncu summary of the
-    dominant kernel, valid only while the kernel source is unchanged."""
-    prof = os.path.join(ROOT, "profiles", f"{KERNEL_OF_PATH[path_name]}_headline.md")
-    src = os.path.join(ROOT, "paper_2503_18118_gb300", "csrc", SRC_OF_PATH[path_name])
+# sources whose bytes the committed ncu summary of each kernel was taken on
+PROFILE_SOURCES = {
+    "gram_tc_kernel": ["gram_tc.cu", "tc_common.cuh", "chan_gen.cuh", "common.cuh"],
+    "gram_f32_kernel": ["gram_simt.cu", "chan_gen.cuh", "common.cuh"],
+    "gram_f64_kernel": ["gram_simt.cu", "chan_gen.cuh", "common.cuh"],
+    "mlp_infer_tc_kernel": ["mlp_tc.cu", "mlp_common.cuh", "tc_common.cuh", "common.cuh"],
+}
+PROFILE_OF_KERNEL = {"gram_tc_kernel": "gram_tc_kernel_headline.md", "gram_f32_kernel": "gram_f32_kernel_headline.md",
+                     "gram_f64_kernel": "gram_f64_kernel_headline.md",
+                     "mlp_infer_tc_kernel": "mlp_infer_tc_kernel_surrogate.md"}
+
+
+def source_hash(kernel):
+    """sha256 chained over the kernel's source files (PROFILE_SOURCES order)."""
+    h = ""
+    for f in PROFILE_SOURCES[kernel]:
+        d = hashlib.sha256(open(os.path.join(ROOT, "paper_2503_18118_gb300", "csrc", f), "rb").read()).hexdigest()
+        h = hashlib.sha256((h + d).encode()).hexdigest()
+    return h
+
+
+def traffic_from_profile(kernel):
+    """DRAM bytes per full launch recorded by the committed ncu summary of the
+    kernel, valid only while the kernel's sources are unchanged."""
+    prof = os.path.join(ROOT, "profiles", PROFILE_OF_KERNEL[kernel])
     if not os.path.exists(prof):
         return None
     text = open(prof).read()
@@ -181,12 +202,7 @@ def traffic_from_profile(path_name):
     t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
     if not m or not t:
         return None
-    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    deps = [os.path.join(ROOT, "paper_2503_18118_gb300", "csrc", f) for f in ("chan_gen.cuh", "common.cuh")]
-    for d in deps:
-        if os.path.exists(d):
-            cur = hashlib.sha256((cur + hashlib.sha256(open(d, "rb").read()).hexdigest()).encode()).hexdigest()
-    return float(t.group(1)) if m.group(1) == cur else None
+    return float(t.group(1)) if m.group(1) == source_hash(kernel) else None
 
 
 def ragged_bench(xl, torch):
@@ -305,6 +321,7 @@ def surrogate_bench(xl, torch, peaks):
         "gram_rms_err": {"closed_form": float(np.mean(res["gram_err_cf"])),
                          "surrogate": float(np.mean(res["gram_err_sur"]))},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": traffic_from_profile("mlp_infer_tc_kernel"),
                      "kernel": "mlp_infer_tc_kernel", "kernel_ms": t_mlp,
                      "algorithmic": "2 x (6x256 + 3x256^2 + 256x2) flop per pair x B K(K-1)/2 pairs",
                      "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured)"},
@@ -313,6 +330,9 @@ def surrogate_bench(xl, torch, peaks):
 
 def main():
     args = parse()
+    if args.source_hash:
+        print(source_hash(args.source_hash))
+        return
     wl = inputs.HEADLINE
     if args.trials:
         wl.trials = args.trials
@@ -486,7 +506,7 @@ def main():
         achieved = 4.0 * entries / (gram_ms / 1e3) / 1e12
         peak_v = sms * 16 * clk / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_v, "unit": "Tops/s (MUFU)",
-                "frac": achieved / peak_v, "traffic": traffic_from_profile(path), "kernel": KERNEL_OF_PATH[path],
+                "frac": achieved / peak_v, "traffic": traffic_from_profile(KERNEL_OF_PATH[path]), "kernel": KERNEL_OF_PATH[path],
                 "kernel_ms": gram_ms,
                 "peak_source": f"MUFU: {sms} SMs x 16 ops/clk x {max_mhz:.0f} MHz (unit counts and max clock)",
                 "algorithmic": "4 transcendental ops (rsqrt, rcp, sin, cos) x N K channel entries per launch",
@@ -496,14 +516,14 @@ def main():
         achieved = gram_flops / (gram_ms / 1e3) / 1e12
         peak_v = sms * 2 * 2 * clk / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_v, "unit": "TFLOP/s", "frac": achieved / peak_v,
-                "traffic": traffic_from_profile(path), "kernel": KERNEL_OF_PATH[path], "kernel_ms": gram_ms,
+                "traffic": traffic_from_profile(KERNEL_OF_PATH[path]), "kernel": KERNEL_OF_PATH[path], "kernel_ms": gram_ms,
                 "peak_source": f"FP64 FMA: {sms} SMs x 2 lanes x 2 flop x {max_mhz:.0f} MHz",
                 "algorithmic": "8 flop x N K (K+1)/2 complex MACs per trial x trials per launch"}
     else:
         achieved = gram_flops / (gram_ms / 1e3) / 1e12
         peak_v = sms * 128 * 2 * clk / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_v, "unit": "TFLOP/s", "frac": achieved / peak_v,
-                "traffic": traffic_from_profile(path), "kernel": KERNEL_OF_PATH[path], "kernel_ms": gram_ms,
+                "traffic": traffic_from_profile(KERNEL_OF_PATH[path]), "kernel": KERNEL_OF_PATH[path], "kernel_ms": gram_ms,
                 "peak_source": f"FP32 FMA: {sms} SMs x 128 lanes x 2 flop x {max_mhz:.0f} MHz",
                 "algorithmic": "8 flop x N K (K+1)/2 complex MACs per trial x trials per launch"}
 

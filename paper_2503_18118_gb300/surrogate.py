@@ -129,3 +129,64 @@ def compare(arr, users, packed, snr_db=10.0, prec=X.BF16X3, scheme=X.ZF):
         e = ((gh - g).abs() / nrm)[:, off]
         out["gram_err_" + name] = torch.sqrt((e ** 2).mean(dim=1)).cpu().numpy()
     return out
+
+
+def main(argv=None):
+    """Command line: `train` labels pairs, trains and saves a checkpoint;
+    `infer` runs the fused inference on one batch (weights from a checkpoint,
+    or the seeded initial ones) and prints its time."""
+    import argparse
+    import time
+
+    ap = argparse.ArgumentParser(prog="python -m paper_2503_18118_gb300.surrogate")
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    t = sub.add_parser("train")
+    t.add_argument("--pairs", type=float, default=1e7)
+    t.add_argument("--k", type=int, default=64)
+    t.add_argument("--steps", type=int, default=8000)
+    t.add_argument("--batch", type=int, default=16384)
+    t.add_argument("--lr", type=float, default=1e-3)
+    t.add_argument("--seed", type=int, default=5)
+    t.add_argument("--out", required=True)
+    i = sub.add_parser("infer")
+    i.add_argument("--checkpoint")
+    i.add_argument("--trials", type=int, default=300)
+    i.add_argument("--k", type=int, default=64)
+    i.add_argument("--n", type=int, default=262144)
+    i.add_argument("--freq-ghz", type=float, default=100.0)
+    i.add_argument("--repeat", type=int, default=2)
+    i.add_argument("--seed", type=int, default=6)
+    a = ap.parse_args(argv)
+    if a.cmd == "train":
+        trials = int(math.ceil(a.pairs / (a.k * (a.k - 1) // 2)))
+        n, freq, users = inputs.surrogate_trials(a.seed, trials, a.k)
+        feat, target, _ = label_pairs(n, freq, users)
+        tr = Trainer(torch.from_numpy(inputs.mlp_init_params(a.seed)).cuda(), batch=a.batch, lr=a.lr, seed=a.seed)
+        t0 = time.perf_counter()
+        log = tr.fit(feat, target, steps=a.steps, log_every=max(1, a.steps // 10))
+        torch.cuda.synchronize()
+        for s, l in log:
+            print(f"step {s} loss {l:.6g}")
+        print(f"trained {a.steps} steps on {feat.shape[0]} pairs in {time.perf_counter() - t0:.2f} s")
+        tr.save(a.out)
+    else:
+        params = torch.from_numpy(inputs.mlp_init_params(a.seed)).cuda()
+        if a.checkpoint:
+            params.copy_(torch.from_numpy(np.load(a.checkpoint)["params"]).cuda())
+        packed = X.xlmimo_mlp_pack(params)
+        arr = X.array(a.n, inputs.wavelength(a.freq_ghz * 1e9))
+        r = (3.0, 30.0) if a.freq_ghz >= 60 else (5.0, 50.0)
+        u = torch.from_numpy(inputs.users_polar(a.seed, a.trials, a.k, r)).cuda()
+        g = torch.empty((a.trials, a.k, a.k), dtype=torch.complex128, device="cuda")
+        for _ in range(a.repeat):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            X.xlmimo_surrogate_gram(arr, u, packed, g)
+            e1.record()
+            torch.cuda.synchronize()
+            print(f"surrogate Gram of {a.trials} trials (K={a.k}, N={a.n}): {e0.elapsed_time(e1):.3f} ms, "
+                  f"finite {bool(torch.isfinite(g).all())}")
+
+
+if __name__ == "__main__":
+    main()
