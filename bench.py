@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-fp64-baseline", action="store_true")
     ap.add_argument("--source-hash", metavar="KERNEL", help="print the source hash a profile summary records, and exit")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the precision table, the ragged batch and the surrogate")
+                    help="skip the precision table, the ragged batch, the sweep and the surrogate")
     return ap.parse_args()
 
 
@@ -249,6 +249,42 @@ def ragged_bench(xl, torch):
             "plan": info, "plan_seconds": plan_s, "cuda_graph": True, "gram": "bf16x3"}
 
 
+def sweep_bench(xl, torch):
+    """Capacity-saturation sweep (Secs. IV-C, V-C): 28 GHz, K = 8 users at r in
+    [5, 50] m, theta in [-60, 60] deg, N = 2^6 .. 2^16, the same 1000 trials at
+    every N, exact and closed-form Grams, ZF / MMSE / capacity at 0, 10 and
+    20 dB with N-independent power (reference user at 27.5 m), FP64 and FP32
+    exact paths; the saturation point from the per-trial intervals and from
+    the analytic ergodic formula for this polar distribution."""
+    wl = inputs.SWEEP
+    ex = wl.extra
+    U = torch.from_numpy(wl.users()).cuda()
+    out = {"workload": f"{wl.name}: N=2^6..2^16, K=8, 1000 trials, 28 GHz, SNR 0/10/20 dB, t={ex['t']}",
+           "n_list": ex["n_list"]}
+    for name, prec in (("f64", xl.F64), ("f32", xl.F32)):
+        xl.xlmimo_capacity_sweep(U[:16].contiguous(), ex["n_list"][:2], ex["snr_db"], wl.wavelength, prec=prec,
+                                 t=ex["t"], ref_x=27.5)  # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = xl.xlmimo_capacity_sweep(U, ex["n_list"], ex["snr_db"], wl.wavelength, prec=prec, t=ex["t"], ref_x=27.5)
+        dt = time.perf_counter() - t0
+        out[name] = {"seconds": dt, "trials_per_s": len(ex["n_list"]) * wl.trials / dt,
+                     "capacity_10db": [float(v) for v in r["capacity"][:, 1]],
+                     "zf_rate_10db": {"exact": [float(v) for v in r["rate"][:, 0, 0, 1]],
+                                      "closed_form": [float(v) for v in r["rate"][:, 1, 0, 1]]},
+                     "mmse_rate_10db": [float(v) for v in r["rate"][:, 0, 1, 1]],
+                     "closed_form_gram_err": [float(v) for v in r["gram_err"]],
+                     "n_sat_trial_mean": float(r["sat_mean"][2])}
+    ana = xl.xlmimo_saturation_analytic(xl.DIST_POLAR, 5.0, 50.0, np.deg2rad(-60.0), np.deg2rad(60.0), wl.k, ex["t"],
+                                        wl.spacing)
+    cap = np.array(out["f64"]["capacity_10db"])
+    frac = cap / cap[-1]
+    first = [int(ex["n_list"][int(np.argmax(frac >= q))]) for q in (0.9, 0.99)]
+    out["saturation"] = {"analytic_n_sat": int(ana[3]), "analytic_y_up_m": float(ana[0]),
+                         "capacity_reaches_90pct_at_n": first[0], "capacity_reaches_99pct_at_n": first[1]}
+    return out
+
+
 def surrogate_bench(xl, torch, peaks):
     """Learned correlation surrogate: labels from the exact kernel, training on
     the GPU, then the fused tensor-core inference timed at 100 GHz, N = 2^18,
@@ -262,7 +298,7 @@ def surrogate_bench(xl, torch, peaks):
     n, freq, users = inputs.surrogate_trials(ex["train_seed"], trials, K, n_log2=ex["n_log2"])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    feat, target, _ = surrogate.label_pairs(n, freq, users)
+    feat, target, _ = surrogate.label_pairs(n, freq, users, base=ex["base"])
     torch.cuda.synchronize()
     label_s = time.perf_counter() - t0
     params = torch.from_numpy(inputs.mlp_init_params(ex["train_seed"])).cuda()
@@ -295,7 +331,8 @@ def surrogate_bench(xl, torch, peaks):
         return statistics.median(ts)
 
     t_cf = timed(lambda: xl.xlmimo_corr_closed_form(arr, U, G))
-    t_sur = timed(lambda: xl.xlmimo_surrogate_gram(arr, U, packed, G))
+    t_fr = timed(lambda: xl.xlmimo_corr_closed_form_aperture(arr, U, xl.APERTURE_FRESNEL, G))
+    t_sur = timed(lambda: xl.xlmimo_surrogate_gram(arr, U, packed, G, base=ex["base"]))
     t_exact = timed(lambda: xl.xlmimo_channel_gram(arr, U, xl.BF16X3, G), reps=3, warm=1)
     t_mlp = t_sur - t_cf
     rows = B * K * (K - 1) // 2
@@ -304,22 +341,26 @@ def surrogate_bench(xl, torch, peaks):
     peak = float(peaks.get("bf16_tflops", 1935.2))
     del G
     # accuracy on the first 1000 trials of the same workload
-    res = surrogate.compare(arr, U[:1000].contiguous(), packed)
+    res = surrogate.compare(arr, U[:1000].contiguous(), packed, base=ex["base"])
     re = res["rate_exact"]
-    e_cf = float(np.mean(np.abs(res["rate_cf"] - re) / re))
-    e_sur = float(np.mean(np.abs(res["rate_sur"] - re) / re))
+    rows = ("cf", "mask", "fresnel", "sur")
+    names = {"cf": "closed_form", "mask": "closed_form_aperture_mask", "fresnel": "closed_form_aperture_fresnel",
+             "sur": "surrogate"}
+    e_rate = {names[k]: float(np.mean(np.abs(res["rate_" + k] - re) / re)) for k in rows}
+    e_gram = {names[k]: float(np.mean(res["gram_err_" + k])) for k in rows}
     return {
         "workload": f"{wl.name}: 100 GHz, N=2^18, K=64, 10^4 trials, r in [3,30] m",
         "training": {"pairs": int(n.size * K * (K - 1) // 2), "label_s": label_s, "steps": ex["steps"],
                      "batch": ex["batch"], "train_s": train_s, "loss": [float(l) for _, l in log],
                      "labels": "exact Gram (bf16x3), N log-uniform [2^10, 2^18], 28/100 GHz"},
-        "gram_ms": {"exact_bf16x3": t_exact, "closed_form": t_cf, "surrogate": t_sur},
+        "base": "closed form x finite-aperture Fresnel factor" if ex["base"] == 2 else ex["base"],
+        "gram_ms": {"exact_bf16x3": t_exact, "closed_form": t_cf, "closed_form_aperture_fresnel": t_fr,
+                    "surrogate": t_sur},
         "trials_per_s": {"exact_bf16x3": B / (t_exact / 1e3), "closed_form": B / (t_cf / 1e3),
-                         "surrogate": B / (t_sur / 1e3)},
-        "sumrate_rel_err": {"closed_form": e_cf, "surrogate": e_sur, "trials": int(re.size),
-                            "receiver": "modified ZF at 10 dB judged on the exact channel"},
-        "gram_rms_err": {"closed_form": float(np.mean(res["gram_err_cf"])),
-                         "surrogate": float(np.mean(res["gram_err_sur"]))},
+                         "closed_form_aperture_fresnel": B / (t_fr / 1e3), "surrogate": B / (t_sur / 1e3)},
+        "sumrate_rel_err": dict(e_rate, trials=int(re.size),
+                                receiver="modified ZF at 10 dB judged on the exact channel (trial mean)"),
+        "gram_rms_err": e_gram,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": traffic_from_profile("mlp_infer_tc_kernel"),
                      "kernel": "mlp_infer_tc_kernel", "kernel_ms": t_mlp,
@@ -474,6 +515,7 @@ def main():
     paths = None
     ragged = None
     sur = None
+    sweep = None
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -491,6 +533,7 @@ def main():
             paths[name] = {"trials_per_s": world * B * nsteps / (t_ms / 1e3),
                            "sumrate_rel_err": float(np.max(np.abs(rg - r_ref) / np.abs(r_ref)))}
         ragged = ragged_bench(xl, torch)
+        sweep = sweep_bench(xl, torch)
         sur = surrogate_bench(xl, torch, peaks)
 
     # peaks from unit counts and the maximum SM clock (per SM per clock:
@@ -544,6 +587,7 @@ def main():
         "fp64_baseline": fp64,
         "precisions": paths,
         "ragged": ragged,
+        "sweep": sweep,
         "surrogate": sur,
         "speedup_vs_fp64_gpu": (value / fp64["trials_per_s"]) if fp64 else None,
         "roofline": roof,

@@ -81,6 +81,21 @@ typedef enum {
     XLMIMO_F16X3 = 4
 } xlmimo_prec;
 
+/* Aperture-aware closed form (not the paper's; NEXT item of the paper's
+ * modified ZF): the stationary-phase off-diagonal of Eq. (6) (and its
+ * free-space analogue) assumes the stationary point of the pair phase lies
+ * inside an unbounded aperture.  The point is where the line through the
+ * two users meets the array axis, y* = y_i - x_i (y_j - y_i)/(x_j - x_i).
+ *   XLMIMO_APERTURE_MASK     drop the term when |y*| > N spacing / 2;
+ *   XLMIMO_APERTURE_FRESNEL  multiply it by the finite-aperture factor of the
+ *       quadratic phase, F = [(C(u_hi) - C(u_lo)) + j s (S(u_hi) - S(u_lo))]
+ *       / (1 + j s), u = (edge - y*) sqrt(|phi''|/pi), s = sign(phi''),
+ *       phi'' = (2 pi/lambda)(x_i^2/r_i^3 - x_j^2/r_j^3) at y*, C, S the
+ *       Fresnel integrals; an edge beyond |u| = 2 counts at its limit 1/2
+ *       (the quadratic model's oscillating tail has the wrong phase there).
+ * The diagonal is the closed form's. */
+typedef enum { XLMIMO_APERTURE_NONE = 0, XLMIMO_APERTURE_MASK = 1, XLMIMO_APERTURE_FRESNEL = 2 } xlmimo_aperture;
+
 /* Linear receivers (Sec. V): ZF (Eq. 21), MMSE, MRC. */
 typedef enum { XLMIMO_ZF = 0, XLMIMO_MMSE = 1, XLMIMO_MRC = 2 } xlmimo_scheme;
 
@@ -156,6 +171,11 @@ int xlmimo_channel_gram_noalloc(const xlmimo_array* arr, const double* users, in
  *   users : [B][K][2] doubles (device);  gram : [B][K][K] complex doubles (device, written) */
 int xlmimo_corr_closed_form(const xlmimo_array* arr, const double* users, int K, int B,
                             double* gram, void* stream);
+
+/* xlmimo_corr_closed_form followed by the finite-aperture correction `mode`
+ * (xlmimo_aperture) of every off-diagonal entry; same layout. */
+int xlmimo_corr_closed_form_aperture(const xlmimo_array* arr, const double* users, int K, int B, int mode,
+                                     double* gram, void* stream);
 
 /* Per-user SINR of a linear receiver built from gram_filter and applied to
  * the channel whose Gram matrix is gram_true (Sec. V; with gram_filter the
@@ -347,13 +367,15 @@ int xlmimo_batch_plan_destroy(xlmimo_batch_plan plan);
  * Not part of the paper.  A multilayer perceptron corrects the closed-form
  * correlation of modified ZF (Sec. V-B, Eqs. 4 and 6, and its free-space
  * analogue): for a user pair i < j it predicts t_ij from the pair's geometry,
- * and the surrogate Gram is G~_ij (1 + t_ij) off the diagonal (its conjugate
- * mirrored below), the closed-form G~_ii on it.  It is trained on targets
- * t_ij = G_ij / G~_ij - 1 from the exact Gram: the ratio removes the fast
- * 2 pi d / lambda phase that the closed form already carries, so what is
- * left is a smooth function of the geometry (about 1 where the stationary
- * point of the phase lies inside the aperture, about -1 where it lies
- * outside and the exact entry is small).
+ * and the surrogate Gram is G~_ij (F_ij + t_ij) off the diagonal (its
+ * conjugate mirrored below), the closed-form G~_ii on it, F_ij the
+ * finite-aperture factor `base` (xlmimo_aperture; XLMIMO_APERTURE_NONE: F = 1).
+ * It is trained on targets t_ij = G_ij / G~_ij - F_ij from the exact Gram:
+ * the ratio removes the fast 2 pi d / lambda phase that the closed form
+ * already carries, so what is left is a smooth function of the geometry
+ * (with base NONE: about 0 where the stationary point of the phase lies
+ * inside the aperture, about -1 where it lies outside and the exact entry is
+ * small; with MASK or FRESNEL that step is taken analytically).
  *
  * Architecture: XLMIMO_MLP_IN features -> XLMIMO_MLP_HIDDEN hidden layers of
  * XLMIMO_MLP_WIDTH units with SiLU, silu(z) = z / (1 + e^-z) -> XLMIMO_MLP_OUT
@@ -387,11 +409,12 @@ int xlmimo_batch_plan_destroy(xlmimo_batch_plan plan);
 
 /* Features (and optionally targets and weights) of every pair of every trial.
  * users [B][K][2], K >= 2.  feat [B*P][6] out, P = K(K-1)/2.  If gram (exact)
- * and gram_cf (closed form) are both non-NULL, target [B*P][2] gets
- * (Re, Im) of G_ij / G~_ij - 1; if weight is non-NULL it gets
+ * and gram_cf (closed form, xlmimo_corr_closed_form) are both non-NULL,
+ * target [B*P][2] gets (Re, Im) of G_ij / G~_ij - F_ij, F the factor `base`
+ * (xlmimo_aperture); if weight is non-NULL it gets
  * |G~_ij|^2 / (G~_ii G~_jj) (needs gram_cf).  Features are computed in FP32
  * from the FP64 positions, targets and weights in FP64; all outputs FP32. */
-int xlmimo_pair_features(const xlmimo_array* arr, const double* users, int K, int B, const double* gram,
+int xlmimo_pair_features(const xlmimo_array* arr, const double* users, int K, int B, int base, const double* gram,
                          const double* gram_cf, float* feat, float* target, float* weight, void* stream);
 
 /* Forward pass over M rows: x [M][6] -> out [M][2].  cache is NULL or
@@ -429,10 +452,11 @@ int xlmimo_mlp_train_step(float* params, float* m, float* v, float* grad, int64_
 int xlmimo_mlp_pack(const float* params, void* packed, void* stream);
 
 /* Surrogate Gram [B][K][K]: the closed form of xlmimo_corr_closed_form with
- * every off-diagonal entry multiplied by 1 + t_ij from the network in
- * `packed`.  One fused tensor-core launch evaluates the network on all pairs.
- * A bounded device-side wait that gives up leaves NaN in its pairs. */
-int xlmimo_surrogate_gram(const xlmimo_array* arr, const double* users, int K, int B, const void* packed,
+ * every off-diagonal entry multiplied by F_ij + t_ij, F the factor `base`
+ * (the one the network was trained with), t from the network in `packed`.
+ * One fused tensor-core launch evaluates the network on all pairs.  A bounded
+ * device-side wait that gives up leaves NaN in its pairs. */
+int xlmimo_surrogate_gram(const xlmimo_array* arr, const double* users, int K, int B, int base, const void* packed,
                           double* gram, void* stream);
 
 /* Message of the last error on this host thread ("" if none). */

@@ -151,6 +151,24 @@ int xlmimo_corr_closed_form(const xlmimo_array* arr, const double* users, int K,
     return launch_closed_form(g, users, K, B, gram, as_stream(stream));
 }
 
+int xlmimo_corr_closed_form_aperture(const xlmimo_array* arr, const double* users, int K, int B, int mode,
+                                     double* gram, void* stream) {
+    clear_error();
+    Geom g;
+    int rc = check_array(arr, &g);
+    if (rc) return rc;
+    if ((rc = check_kb(K, B))) return rc;
+    if (mode < XLMIMO_APERTURE_NONE || mode > XLMIMO_APERTURE_FRESNEL) {
+        set_error("unknown aperture mode %d", mode);
+        return XLMIMO_EINVAL;
+    }
+    if (B == 0) return XLMIMO_OK;
+    if (!users || !gram) { set_error("users and gram must be non-NULL"); return XLMIMO_EINVAL; }
+    rc = launch_closed_form(g, users, K, B, gram, as_stream(stream));
+    if (!rc) rc = launch_aperture_apply(g, mode, users, K, B, gram, as_stream(stream));
+    return rc;
+}
+
 int xlmimo_beamform(const double* gram_filter, const double* gram_true, const double* power,
                     const double* noise, int K, int B, int scheme, int power_mode, double* sinr,
                     int* trial_status, double* capacity, void* stream) {

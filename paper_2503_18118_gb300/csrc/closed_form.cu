@@ -21,6 +21,7 @@
 // the output is Hermitian by construction.
 #include <math.h>
 
+#include "aperture.cuh"
 #include "common.cuh"
 
 namespace xl {
@@ -111,6 +112,48 @@ __global__ void closed_form_kernel(Geom g, const double* __restrict__ users, int
             G[j * K + i] = make_double2(v.x, -v.y);
         }
     }
+}
+
+// Off-diagonal entries (i < j) of every trial times the finite-aperture
+// factor (aperture.cuh); the conjugate mirrored, the diagonal untouched.
+// lower_only: write conj(G~_ij F_ij) below the diagonal only, keeping G~_ij
+// above it (the surrogate's base; see xlmimo_surrogate_gram).
+__global__ void aperture_apply_kernel(int mode, double H, double inv_lambda, const double2* __restrict__ users, int K,
+                                      int64_t pairs, bool lower_only, double2* __restrict__ gram) {
+    const int P = K * (K - 1) / 2;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < pairs; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = r / P;
+        int q = (int)(r - b * P), i = 0, rl = K - 1;
+        while (q >= rl) { q -= rl; ++i; --rl; }
+        const int j = i + 1 + q;
+        const double2 ui = users[b * K + i], uj = users[b * K + j];
+        const float2 f = aperture_factor(mode, ui.x, ui.y, uj.x, uj.y, H, inv_lambda);
+        double2* G = gram + b * K * K;
+        const double2 v = G[i * K + j];
+        const double re = v.x * f.x - v.y * f.y, im = v.x * f.y + v.y * f.x;
+        if (!lower_only) G[i * K + j] = make_double2(re, im);
+        G[j * K + i] = make_double2(re, -im);
+    }
+}
+
+static int aperture_launch(const Geom& g, int mode, const double* users, int K, int B, bool lower_only, double* gram,
+                           cudaStream_t st) {
+    if (mode == APERTURE_NONE || K < 2) return XLMIMO_OK;
+    const int64_t pairs = (int64_t)B * (K * (K - 1) / 2);
+    int64_t blocks = (pairs + 255) / 256;
+    if (blocks > 16LL * num_sms()) blocks = 16LL * num_sms();
+    aperture_apply_kernel<<<(unsigned)blocks, 256, 0, st>>>(mode, 0.5 * (double)g.N * g.spacing, g.inv_lambda,
+                                                            (const double2*)users, K, pairs, lower_only,
+                                                            (double2*)gram);
+    return cuda_status(cudaGetLastError(), "aperture launch");
+}
+
+int launch_aperture_apply(const Geom& g, int mode, const double* users, int K, int B, double* gram, cudaStream_t st) {
+    return aperture_launch(g, mode, users, K, B, false, gram, st);
+}
+
+int launch_aperture_base(const Geom& g, int mode, const double* users, int K, int B, double* gram, cudaStream_t st) {
+    return aperture_launch(g, mode, users, K, B, true, gram, st);
 }
 
 int launch_closed_form(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st) {

@@ -34,6 +34,12 @@ int launch_gram_f32(const Geom& g, const double* users, int K, int B, double* gr
 int launch_gram_tc(const Geom& g, const double* users, int K, int B, int prec, double* gram, cudaStream_t st,
                    int ctas_per_sm = 0);
 int launch_closed_form(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st);
+// Finite-aperture factor (APERTURE_* of aperture.cuh) applied in place to the
+// off-diagonal entries of closed-form Grams.
+int launch_aperture_apply(const Geom& g, int mode, const double* users, int K, int B, double* gram, cudaStream_t st);
+// The same factor written only below the diagonal, conj(G~_ij F_ij), leaving
+// G~_ij above it (the surrogate's base).
+int launch_aperture_base(const Geom& g, int mode, const double* users, int K, int B, double* gram, cudaStream_t st);
 int launch_beamform(const double* gf, const double* gt, const double* power, const double* noise, int K,
                     int B, int scheme, int power_mode, double* sinr, int* status, double* cap,
                     cudaStream_t st);

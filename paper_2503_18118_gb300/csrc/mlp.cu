@@ -11,6 +11,7 @@
 // stated numerics); the backward pass reuses the rounded values.
 #include <math.h>
 
+#include "aperture.cuh"
 #include "mlp_common.cuh"
 
 namespace xl {
@@ -179,7 +180,8 @@ __global__ void mlp_adam_kernel(float* __restrict__ p, float* __restrict__ m, fl
     }
 }
 
-__global__ void pair_features_kernel(FeatConst fc, const double2* __restrict__ users, int K, int64_t rows,
+__global__ void pair_features_kernel(FeatConst fc, int base, double H, double inv_lambda,
+                                     const double2* __restrict__ users, int K, int64_t rows,
                                      const double2* __restrict__ gram, const double2* __restrict__ gcf,
                                      float* __restrict__ feat, float2* __restrict__ target, float* __restrict__ weight) {
     const int P = K * (K - 1) / 2;
@@ -192,16 +194,17 @@ __global__ void pair_features_kernel(FeatConst fc, const double2* __restrict__ u
         pair_features_dev(fc, ui.x, ui.y, uj.x, uj.y, f);
 #pragma unroll
         for (int c = 0; c < MLP_IN; ++c) feat[r * MLP_IN + c] = f[c];
-        const int64_t base = b * K * K;
+        const int64_t g0 = b * K * K;
         if (target) {
-            const double2 ge = gram[base + i * K + j], gc = gcf[base + i * K + j];
+            const double2 ge = gram[g0 + i * K + j], gc = gcf[g0 + i * K + j];
             const double den = gc.x * gc.x + gc.y * gc.y;
             const double re = (ge.x * gc.x + ge.y * gc.y) / den, im = (ge.y * gc.x - ge.x * gc.y) / den;
-            target[r] = make_float2((float)(re - 1.0), (float)im);
+            const float2 f = aperture_factor(base, ui.x, ui.y, uj.x, uj.y, H, inv_lambda);
+            target[r] = make_float2((float)(re - (double)f.x), (float)(im - (double)f.y));
         }
         if (weight) {
-            const double2 gc = gcf[base + i * K + j];
-            weight[r] = (float)((gc.x * gc.x + gc.y * gc.y) / (gcf[base + i * K + i].x * gcf[base + j * K + j].x));
+            const double2 gc = gcf[g0 + i * K + j];
+            weight[r] = (float)((gc.x * gc.x + gc.y * gc.y) / (gcf[g0 + i * K + i].x * gcf[g0 + j * K + j].x));
         }
     }
 }
@@ -349,21 +352,22 @@ using namespace xl;
 
 extern "C" {
 
-int xlmimo_pair_features(const xlmimo_array* arr, const double* users, int K, int B, const double* gram,
+int xlmimo_pair_features(const xlmimo_array* arr, const double* users, int K, int B, int base, const double* gram,
                          const double* gram_cf, float* feat, float* target, float* weight, void* stream) {
     clear_error();
     Geom g;
     int rc = check_array(arr, &g);
     if (rc) return rc;
     if (K < 2 || K > XLMIMO_MAX_USERS || B < 0) { set_error("K must be in [2, 64] and B >= 0"); return XLMIMO_EINVAL; }
+    if (base < XLMIMO_APERTURE_NONE || base > XLMIMO_APERTURE_FRESNEL) { set_error("unknown base %d", base); return XLMIMO_EINVAL; }
     if (target && (!gram || !gram_cf)) { set_error("targets need gram and gram_cf"); return XLMIMO_EINVAL; }
     if (weight && !gram_cf) { set_error("weights need gram_cf"); return XLMIMO_EINVAL; }
     if (B == 0) return XLMIMO_OK;
     if (!users || !feat) { set_error("users and feat must be non-NULL"); return XLMIMO_EINVAL; }
     const int64_t rows = (int64_t)B * (K * (K - 1) / 2);
     pair_features_kernel<<<grid_for(rows, 256), 256, 0, as_stream(stream)>>>(
-        make_feat_const(g), (const double2*)users, K, rows, (const double2*)gram, (const double2*)gram_cf, feat,
-        (float2*)target, weight);
+        make_feat_const(g), base, 0.5 * (double)g.N * g.spacing, g.inv_lambda, (const double2*)users, K, rows,
+        (const double2*)gram, (const double2*)gram_cf, feat, (float2*)target, weight);
     return cuda_status(cudaGetLastError(), "pair features launch");
 }
 

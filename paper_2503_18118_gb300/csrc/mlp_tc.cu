@@ -1,44 +1,54 @@
 // Fused tensor-core inference of the correlation surrogate: a persistent CTA
-// takes tiles of 128 pair rows, one after another, through the whole network
-// and corrects their closed-form Gram entries in place.  The barrier set-up,
-// TMEM allocation and parameter load happen once per CTA; a tile's pair
-// indices, positions and closed-form entries are fetched while the previous
-// tile is in flight, and the weight stream runs on into the next tile.
+// takes tiles of 128 pair rows through the whole network and corrects their
+// closed-form Gram entries in place.  The barrier set-up, TMEM allocation and
+// parameter load happen once per CTA; a tile's pair indices, positions and
+// closed-form entries are fetched while the previous tile is in flight, and
+// the weight stream runs on into the next tile.
 //
-//   row warps 0-7: thread (m, h) = (row m = 32 (warp % 4) + lane, half h =
-//          warp / 4) owns output units 128 h .. 128 h + 127 of row m.  It
-//          writes the features (half 0: [hi(f), lo(f), hi(f)] in BF16) into
-//          the A tile (128 x 256 BF16, K-major, 128-byte swizzle); after each
-//          layer it reads its 128 accumulators from TMEM, adds the bias and
-//          applies SiLU as z/2 (1 + tanh(z/2)) (the packed weights hold W/2,
-//          so the accumulator already is z/2), and writes BF16 back into its
-//          half of the A tile; after the last hidden layer it forms its half
-//          of the FP32 256 -> 2 product, the halves are added, and half 0
-//          applies G~_ij (1 + t_ij).
-//   warp 8 streams the 26 weight tiles (16 KB: 128 output units x 64 inputs,
-//          BF16, stored in the swizzled operand layout) through a two-stage
-//          ring.  CTAs run in clusters of CL; tile c is fetched once from L2 by
-//          cluster rank c % CL and multicast into every CTA of the cluster, so
-//          each CTA issues 1/CL of the copies and the cluster shares the
-//          bytes in flight (without it the ring is latency-bound at ~5.5 TB/s
-//          of L2 reads and the tensor pipe idles).  A slot is refilled once
-//          the MMA warps of all CL CTAs have released it (their commits are
-//          multicast onto every CTA's "empty" barrier).
-//   warp 9 owns TMEM (256 columns: one FP32 128 x 256 accumulator) and issues
-//          tcgen05.mma (M = N = 128, K = 16) half by half, committing each
-//          half separately, so half 0's epilogue runs while half 1 multiplies.
+// A CTA keeps NT row tiles in flight (MiCfg): NT = 1 (default) is two CTAs
+// per SM with a two-stage ring each; NT = 2 is one CTA per SM whose two tiles
+// take every weight tile in turn from a five-stage ring (measured slower: both
+// tiles reach their SiLU epilogues together, so MMA and epilogue overlap less
+// than two independent CTAs do).  Measured on a
+// per-CTA clock64 timeline of the NT = 1 form, each layer's MMAs waited ~800
+// cycles per 16 KB weight tile (L2 latency with two tiles in flight, the
+// crossbar at 15 % of its peak) and the SiLU epilogue was issue-bound with
+// four row warps per scheduler; sharing weight tiles halves the bytes per row
+// and the deeper ring keeps more of them in flight.
+//
+//   row warps (8 per tile): thread (t, m, h) owns output units 128 h ..
+//          128 h + 127 of row m of tile t (m = 32 (warp % 4) + lane, h =
+//          warp / 4 % 2, t = warp / 8).  It writes the features (half 0:
+//          [hi(f), lo(f), hi(f)] in BF16) into its tile's A (128 x 256 BF16,
+//          K-major, 128-byte swizzle); after each layer it reads its 128
+//          accumulators from TMEM, adds the bias and applies SiLU as
+//          z/2 (1 + tanh(z/2)) (the packed weights hold W/2, so the
+//          accumulator already is z/2), and writes BF16 back into its half of
+//          A; after the last hidden layer it forms its half of the FP32
+//          256 -> 2 product, the halves are added, and half 0 applies
+//          G~_ij (1 + t_ij).
+//   loader warp streams the 26 weight tiles (16 KB: 128 output units x 64
+//          inputs, BF16, stored in the swizzled operand layout) through the
+//          ring with bulk copies.  CTAs may run in clusters of CL, tile c
+//          fetched once by rank c % CL and multicast into every CTA of the
+//          cluster (measured: no faster; it saves L2 bandwidth, not bytes in
+//          flight per CTA); a slot is refilled once the MMA warps of all CL
+//          CTAs have released it (their commits are multicast).
+//   MMA warp owns TMEM (256 columns per tile: an FP32 128 x 256 accumulator)
+//          and issues tcgen05.mma (M = N = 128, K = 16) half by half, every
+//          tile per weight tile, committing each half separately so half 0's
+//          epilogue runs while half 1 multiplies.
 // The last hidden layer's SiLU feeds the FP32 output layer directly and uses
 // the FP32 tanh (relative error ~2^-11); measured against the FP32 SIMT
 // forward pass, the exact form there (exp and divide, two MUFU ops) changed
 // neither the output error nor the sum rate, and cost 12 % of the kernel.
-// Ordering: a layer's MMAs start once all 256 row threads have written the A
-// tile and read the accumulator (one arrival each); half 0 overwrites its A
-// columns only after half 1's MMAs have read them (a separate commit after
-// half 1's first two input chunks); half 1's accumulator commit implies the
-// whole layer is done.  Every wait is bounded; a CTA that gives up writes NaN
-// to its pairs.  Cluster barriers after the barrier set-up and before exit
-// keep every remote arrival and copy inside the lifetime of its target.  Two
-// CTAs fit on an SM (~107 KB shared memory and 256 TMEM columns each).
+// Ordering: a layer's MMAs start once every row thread has written A and read
+// the accumulator (one arrival each); half 0 overwrites its A columns only
+// after half 1's MMAs have read them (a separate commit after half 1's first
+// two input chunks); half 1's accumulator commit implies the whole layer is
+// done.  Every wait is bounded; a CTA that gives up writes NaN to its pairs.
+// Cluster barriers after the barrier set-up and before exit keep every remote
+// arrival and copy inside the lifetime of its target.
 #include <stdlib.h>
 
 #include <algorithm>
@@ -48,26 +58,41 @@
 
 namespace xl {
 
-constexpr int MI_ROWS = 128;
-constexpr int MI_THREADS = 320;  // 8 row warps, loader, MMA
-constexpr int MI_STAGES = 2;
-constexpr uint32_t MI_TMEM_COLS = 256;
+constexpr int MI_ROWS = 128;  // pair rows per tile (the MMA's M)
 constexpr int MI_A_BYTES = 4 * MLP_TILE_BYTES;
 constexpr int MI_F32_BYTES = (MLP_PK_NF * 4 + 15) / 16 * 16;
 
+// NT row tiles in flight per CTA.  NT = 1: two CTAs per SM, a two-stage
+// weight ring each.  NT = 2: one CTA per SM whose two tiles take every weight
+// tile in turn (half the L2 bytes per row) from a five-stage ring.
+template <int NT>
+struct MiCfg {
+    static constexpr int ROW_WARPS = 8 * NT;
+    static constexpr int LOADER = ROW_WARPS, MMA = ROW_WARPS + 1;
+    static constexpr int THREADS = 32 * (ROW_WARPS + 2);
+    static constexpr int ROW_THREADS = 32 * ROW_WARPS;
+    static constexpr int CTAS_PER_SM = NT == 1 ? 2 : 1;
+    static constexpr int STAGES = NT == 1 ? 2 : 5;
+    static constexpr uint32_t TMEM_COLS = 256 * NT;
+};
+
+template <int NT>
 struct MiShared {
-    uint64_t full[MI_STAGES];
-    uint64_t empty[MI_STAGES];
-    uint64_t a_ready;    // 256 row-thread arrivals: A tile written, accumulator read
-    uint64_t d_ready[2]; // commit: output half h of the layer complete
-    uint64_t a_free;     // commit: half 1 has read A columns 0-127
+    uint64_t full[MiCfg<NT>::STAGES];
+    uint64_t empty[MiCfg<NT>::STAGES];
+    uint64_t a_ready;    // one arrival per row thread: A tiles written, accumulators read
+    uint64_t d_ready[2]; // commit: output half h of the layer complete (every tile)
+    uint64_t a_free;     // commit: half 1 has read A columns 0-127 (every tile)
     uint64_t fin;        // commit after the last MMA
     uint32_t tmem_base;
     int abort;
-    float2 red[MI_ROWS]; // half 1's share of the output layer
+    float2 red[NT][MI_ROWS]; // half 1's share of the output layer
 };
 
-constexpr int MI_SMEM = 1024 + MI_A_BYTES + MI_STAGES * MLP_TILE_BYTES + MI_F32_BYTES + (int)sizeof(MiShared);
+template <int NT>
+constexpr int mi_smem() {
+    return 1024 + NT * MI_A_BYTES + MiCfg<NT>::STAGES * MLP_TILE_BYTES + MI_F32_BYTES + (int)sizeof(MiShared<NT>);
+}
 
 // Copy into this CTA's shared memory, completing bytes on `bar` (armed separately).
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -109,6 +134,32 @@ __device__ __forceinline__ uint32_t cluster_rank() {
 
 __device__ __forceinline__ void cluster_sync() {
     asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// try_wait that lets the hardware suspend the thread for up to `ns` while the
+// phase is incomplete, so that waiting warps leave their issue slots to the
+// working ones.
+__device__ __forceinline__ uint32_t mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok;
+}
+
+// mbar_wait with suspension: same bound (TC_WAIT_NS) and abort protocol.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait_sleep(bar, parity, 2000u)) return true;
+        if (*abort) return false;
+        if (global_ns() - t0 > TC_WAIT_NS) {
+            *abort = 1;
+            return false;
+        }
+    }
 }
 
 // Wait bounded by time only (used on the way out, after an abort).
@@ -187,9 +238,11 @@ struct RowIn {
     int i, j;
     int64_t g0;       // first entry of the trial's Gram
     double2 ui, uj;   // user positions
-    double2 gc;       // closed-form G~_ij
+    double2 gc;       // closed-form G~_ij (upper triangle)
+    double2 gf;       // G~_ij F_ij, the base (conjugate of the lower triangle)
 };
 
+template <bool HB>
 __device__ __forceinline__ RowIn fetch_row(int64_t r, int64_t rows, int K, int P, const double2* __restrict__ users,
                                            const double2* __restrict__ gram) {
     RowIn in;
@@ -197,7 +250,7 @@ __device__ __forceinline__ RowIn fetch_row(int64_t r, int64_t rows, int K, int P
     in.i = 0;
     in.j = 1;
     in.g0 = 0;
-    in.ui = in.uj = in.gc = make_double2(1.0, 0.0);
+    in.ui = in.uj = in.gc = in.gf = make_double2(1.0, 0.0);
     if (in.valid) {
         const int64_t b = r / P;
         pair_index((int)(r - b * P), K, in.i, in.j);
@@ -205,6 +258,12 @@ __device__ __forceinline__ RowIn fetch_row(int64_t r, int64_t rows, int K, int P
         in.uj = users[b * K + in.j];
         in.g0 = b * K * K;
         in.gc = gram[in.g0 + in.i * K + in.j];
+        if (HB) {
+            const double2 lo = gram[in.g0 + in.j * K + in.i];
+            in.gf = make_double2(lo.x, -lo.y);
+        } else {
+            in.gf = in.gc;
+        }
     }
     return in;
 }
@@ -212,16 +271,19 @@ __device__ __forceinline__ RowIn fetch_row(int64_t r, int64_t rows, int K, int P
 // Persistent: CTA x takes tiles x, x + grid, x + 2 grid, ... (n_iter of them,
 // the same count in every CTA so that a cluster shares one weight stream;
 // tiles past the end have no valid rows).
-template <int CL>
-__global__ void __launch_bounds__(MI_THREADS, 2)
+// HB: the Gram holds a base G~ F below the diagonal (else the base is G~).
+template <int CL, int NT, bool HB>
+__global__ void __launch_bounds__(MiCfg<NT>::THREADS, MiCfg<NT>::CTAS_PER_SM)
     mlp_infer_tc_kernel(FeatConst fc, const double2* __restrict__ users, int K, int64_t rows, int n_iter,
                         const unsigned char* __restrict__ packed, double2* __restrict__ gram) {
+    using C = MiCfg<NT>;
+    constexpr int MI_STAGES = C::STAGES;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    unsigned char* A = base;
-    unsigned char* ring = A + MI_A_BYTES;
+    unsigned char* A0 = base;  // tile t's A at A0 + t MI_A_BYTES
+    unsigned char* ring = A0 + NT * MI_A_BYTES;
     float* pf = reinterpret_cast<float*>(ring + MI_STAGES * MLP_TILE_BYTES);
-    MiShared* sh = reinterpret_cast<MiShared*>(reinterpret_cast<unsigned char*>(pf) + MI_F32_BYTES);
+    MiShared<NT>* sh = reinterpret_cast<MiShared<NT>*>(reinterpret_cast<unsigned char*>(pf) + MI_F32_BYTES);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int P = K * (K - 1) / 2;
@@ -231,7 +293,7 @@ __global__ void __launch_bounds__(MI_THREADS, 2)
             mbar_init(&sh->full[s], 1);
             mbar_init(&sh->empty[s], CL);
         }
-        mbar_init(&sh->a_ready, 2 * MI_ROWS);
+        mbar_init(&sh->a_ready, C::ROW_THREADS);
         mbar_init(&sh->d_ready[0], 1);
         mbar_init(&sh->d_ready[1], 1);
         mbar_init(&sh->a_free, 1);
@@ -239,14 +301,14 @@ __global__ void __launch_bounds__(MI_THREADS, 2)
         sh->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 9) {
+    if (warp == C::MMA) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
-                     "r"(MI_TMEM_COLS)
+                     "r"(C::TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     const float* gpf = reinterpret_cast<const float*>(packed + MLP_PK_F32);
-    for (int e = tid; e < MLP_PK_NF; e += MI_THREADS) pf[e] = gpf[e];
+    for (int e = tid; e < MLP_PK_NF; e += C::THREADS) pf[e] = gpf[e];
     tc_fence_before();
     cluster_sync();  // every CTA's barriers exist before any remote copy or arrival
     tc_fence_after();
@@ -256,19 +318,19 @@ __global__ void __launch_bounds__(MI_THREADS, 2)
     volatile int* abort = &sh->abort;
     const int n_tiles_total = n_iter * MLP_TILES;
 
-    if (warp == 8) {
+    if (warp == C::LOADER) {
         // ---------------- weight tiles through the ring (tile c issued by rank c % CL)
         if (lane == 0) {
             int armed = 0;
             for (int c = 0; c < n_tiles_total; ++c) {
                 const int s = c % MI_STAGES;
                 // the previous tile of this slot has landed here before the slot is re-armed
-                if (c >= MI_STAGES && !mbar_wait(&sh->full[s], ((c / MI_STAGES) - 1) & 1, abort)) break;
+                if (c >= MI_STAGES && !mbar_wait_sleep(&sh->full[s], ((c / MI_STAGES) - 1) & 1, abort)) break;
                 expect_tx(&sh->full[s], MLP_TILE_BYTES);
                 ++armed;
                 if (c % CL != (int)crank) continue;
                 // ... and every CTA of the cluster has consumed it before the slot is overwritten
-                if (c >= MI_STAGES && !mbar_wait(&sh->empty[s], ((c / MI_STAGES) - 1) & 1, abort)) break;
+                if (c >= MI_STAGES && !mbar_wait_sleep(&sh->empty[s], ((c / MI_STAGES) - 1) & 1, abort)) break;
                 const uint32_t dst = smem_u32(ring + s * MLP_TILE_BYTES);
                 const unsigned char* src = packed + (int64_t)(c % MLP_TILES) * MLP_TILE_BYTES;
                 if (CL > 1) bulk_load_mc(dst, src, MLP_TILE_BYTES, &sh->full[s], cmask);
@@ -279,27 +341,30 @@ __global__ void __launch_bounds__(MI_THREADS, 2)
                 if (c >= 0) mbar_wait_timed(&sh->full[c % MI_STAGES], (c / MI_STAGES) & 1);
         }
         __syncwarp();
-    } else if (warp == 9) {
-        // ---------------- MMA issuer
+    } else if (warp == C::MMA) {
+        // ---------------- MMA issuer: every tile of the CTA takes each weight tile in turn
         if (lane == 0) {
             const uint32_t idesc = tc_idesc<TCP_BF16>();
             bool ok = true;
             int c = 0;
             for (int it = 0; it < n_iter && ok; ++it) {
                 for (int L = 0; L < 4 && ok; ++L) {
-                    if (!mbar_wait(&sh->a_ready, L & 1, abort)) { ok = false; break; }  // 4 phases per tile
+                    if (!mbar_wait_sleep(&sh->a_ready, L & 1, abort)) { ok = false; break; }  // 4 phases per tile
                     tc_fence_after();
                     const int nk = L == 0 ? 1 : 4, ksteps = L == 0 ? 2 : 4;
                     for (int nh = 0; nh < 2 && ok; ++nh) {
                         for (int kc = 0; kc < nk; ++kc, ++c) {
                             const int s = c % MI_STAGES;
-                            if (!mbar_wait(&sh->full[s], (c / MI_STAGES) & 1, abort)) { ok = false; break; }
+                            if (!mbar_wait_sleep(&sh->full[s], (c / MI_STAGES) & 1, abort)) { ok = false; break; }
                             tc_fence_after();
-                            const uint32_t a0 = smem_u32(A + kc * MLP_TILE_BYTES);
                             const uint32_t b0 = smem_u32(ring + s * MLP_TILE_BYTES);
-                            for (int kk = 0; kk < ksteps; ++kk)
-                                umma(tmem + nh * 128, desc_sw128(a0 + kk * 32), desc_sw128(b0 + kk * 32), idesc,
-                                     (kc | kk) ? 1u : 0u);
+#pragma unroll
+                            for (int t = 0; t < NT; ++t) {
+                                const uint32_t a0 = smem_u32(A0 + t * MI_A_BYTES + kc * MLP_TILE_BYTES);
+                                for (int kk = 0; kk < ksteps; ++kk)
+                                    umma(tmem + t * 256 + nh * 128, desc_sw128(a0 + kk * 32), desc_sw128(b0 + kk * 32),
+                                         idesc, (kc | kk) ? 1u : 0u);
+                            }
                             if (CL > 1) umma_commit_mc(&sh->empty[s], cmask);
                             else umma_commit(&sh->empty[s]);
                             if (nh == 1 && kc == (nk - 1) / 2) umma_commit(&sh->a_free);  // chunks 0, 1 read
@@ -312,13 +377,16 @@ __global__ void __launch_bounds__(MI_THREADS, 2)
         }
         __syncwarp();
     } else {
-        // ---------------- rows
-        const int m = (warp & 3) * 32 + lane, hf = warp >> 2;
-        const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(hf * 128);
+        // ---------------- rows: warp (t, hf, quarter) = (warp / 8, warp / 4 % 2, warp % 4)
+        const int m = (warp & 3) * 32 + lane, hf = (warp >> 2) & 1, tt = warp >> 3;
+        unsigned char* A = A0 + tt * MI_A_BYTES;
+        const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(tt * 256 + hf * 128);
+        const int64_t tile_rows = (int64_t)NT * MI_ROWS;  // rows per CTA iteration
+        const int64_t row_off = (int64_t)tt * MI_ROWS + m;
         RowIn cur;
         cur.valid = false;
         if (hf == 0) {
-            cur = fetch_row((int64_t)blockIdx.x * MI_ROWS + m, rows, K, P, users, gram);
+            cur = fetch_row<HB>((int64_t)blockIdx.x * tile_rows + row_off, rows, K, P, users, gram);
             write_a0(A, m, fc, cur.valid, cur.ui, cur.uj);
         }
         fence_async_smem();
@@ -329,11 +397,11 @@ __global__ void __launch_bounds__(MI_THREADS, 2)
             nxt.valid = false;
             const bool more = it + 1 < n_iter;
             if (hf == 0 && more)  // loads for the next tile, in flight during this one
-                nxt = fetch_row(((int64_t)blockIdx.x + (int64_t)(it + 1) * gridDim.x) * MI_ROWS + m, rows, K, P, users,
-                                gram);
+                nxt = fetch_row<HB>(((int64_t)blockIdx.x + (int64_t)(it + 1) * gridDim.x) * tile_rows + row_off, rows, K, P,
+                                users, gram);
             float2 o = make_float2(0.f, 0.f);
             for (int L = 0; L < 4 && ok; ++L) {
-                if (!mbar_wait(&sh->d_ready[hf], L & 1, abort)) { ok = false; break; }
+                if (!mbar_wait_sleep(&sh->d_ready[hf], L & 1, abort)) { ok = false; break; }
                 tc_fence_after();
                 const float* bias = pf + MLP_PK_B0 + L * MLP_W + hf * 128;
                 for (int cb = 0; cb < 4; ++cb) {
@@ -350,7 +418,7 @@ __global__ void __launch_bounds__(MI_THREADS, 2)
                             w[2 * q + 1] = silu_pair_bf16(
                                 __fadd2_rn(make_float2(v[4 * q + 2], v[4 * q + 3]), make_float2(bb.z, bb.w)));
                         }
-                        if (hf == 0 && cb == 0 && !mbar_wait(&sh->a_free, L & 1, abort)) { ok = false; break; }
+                        if (hf == 0 && cb == 0 && !mbar_wait_sleep(&sh->a_free, L & 1, abort)) { ok = false; break; }
                         const int col = hf * 128 + cb * 32;
 #pragma unroll
                         for (int u = 0; u < 4; ++u) st_v4(a_unit(A, col >> 6, m, ((col & 63) >> 3) + u), w + 4 * u);
@@ -379,32 +447,34 @@ __global__ void __launch_bounds__(MI_THREADS, 2)
             // half 1 has read A chunk 0 for layer 3), and its layer 0 may start
             if (ok && more) {
                 if (hf == 0) {
-                    if (mbar_wait(&sh->a_free, 1, abort)) write_a0(A, m, fc, nxt.valid, nxt.ui, nxt.uj);
+                    if (mbar_wait_sleep(&sh->a_free, 1, abort)) write_a0(A, m, fc, nxt.valid, nxt.ui, nxt.uj);
                     else ok = false;
                 }
                 fence_async_smem();
                 tc_fence_before();
                 if (ok) mbar_arrive(&sh->a_ready);
             }
-            if (hf == 1) sh->red[m] = o;
+            if (hf == 1) sh->red[tt][m] = o;
             // barrier of the 256 row threads that also agrees on stopping, so
             // that all of them leave the loop together
             uint32_t stop;
             {
                 const uint32_t mine = (!ok || *abort) ? 1u : 0u;
                 asm volatile(
-                    "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, 256, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+                    "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, %2, q;\n selp.u32 %0, 1, 0, p;\n}\n"
                     : "=r"(stop)
-                    : "r"(mine)
+                    : "r"(mine), "n"(C::ROW_THREADS)
                     : "memory");
             }
             if (hf == 0 && cur.valid) {
-                const float2 o1 = sh->red[m];
+                const float2 o1 = sh->red[tt][m];
                 double2 v0, v1;
                 if (!stop) {
-                    const double t0 = (double)(o.x + o1.x + pf[MLP_PK_B4]), t1 = (double)(o.y + o1.y + pf[MLP_PK_B4 + 1]);
+                    // G~ F + G~ t
+                    const double t0 = (double)(o.x + o1.x + pf[MLP_PK_B4]);
+                    const double t1 = (double)(o.y + o1.y + pf[MLP_PK_B4 + 1]);
                     const double2 gc = cur.gc;
-                    v0 = make_double2(gc.x + (gc.x * t0 - gc.y * t1), gc.y + (gc.x * t1 + gc.y * t0));
+                    v0 = make_double2(cur.gf.x + (gc.x * t0 - gc.y * t1), cur.gf.y + (gc.x * t1 + gc.y * t0));
                     v1 = make_double2(v0.x, -v0.y);
                 } else {
                     const double nanv = __longlong_as_double(0x7ff8000000000000ULL);
@@ -419,8 +489,8 @@ __global__ void __launch_bounds__(MI_THREADS, 2)
             if (stop) {
                 // the remaining tiles of this CTA are lost: mark them
                 for (int k = it + 1; k < n_iter && hf == 0; ++k) {
-                    const RowIn q = fetch_row(((int64_t)blockIdx.x + (int64_t)k * gridDim.x) * MI_ROWS + m, rows, K, P,
-                                              users, gram);
+                    const RowIn q = fetch_row<HB>(((int64_t)blockIdx.x + (int64_t)k * gridDim.x) * tile_rows + row_off, rows,
+                                              K, P, users, gram);
                     if (q.valid) {
                         const double nanv = __longlong_as_double(0x7ff8000000000000ULL);
                         gram[q.g0 + q.i * K + q.j] = make_double2(nanv, nanv);
@@ -434,12 +504,12 @@ __global__ void __launch_bounds__(MI_THREADS, 2)
 
     tc_fence_before();
     __syncthreads();
-    if (warp == 9 && lane == 0) mbar_wait_timed(&sh->fin, 0);
+    if (warp == C::MMA && lane == 0) mbar_wait_timed(&sh->fin, 0);
     __syncwarp();
     cluster_sync();  // the other CTAs' copies and commits into this CTA are over
-    if (warp == 9) {
+    if (warp == C::MMA) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(MI_TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
     }
 }
 
@@ -459,28 +529,31 @@ static int mlp_infer_cluster() {
     return cl;
 }
 
-template <int CL>
+template <int CL, int NT, bool HB>
 static int mlp_infer_launch(const FeatConst& fc, const double* users, int K, int64_t rows, const void* packed,
                             double* gram, cudaStream_t st) {
+    using C = MiCfg<NT>;
+    constexpr int smem = mi_smem<NT>();
     static bool done[64] = {false};
     int dev = 0;
     int rc = cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
     if (rc) return rc;
     if (dev >= 64 || !done[dev]) {
-        rc = cuda_status(cudaFuncSetAttribute(mlp_infer_tc_kernel<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, MI_SMEM),
+        rc = cuda_status(cudaFuncSetAttribute(mlp_infer_tc_kernel<CL, NT, HB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                          "surrogate kernel attribute");
         if (rc) return rc;
         if (dev < 64) done[dev] = true;
     }
-    const int64_t n_tiles = (rows + MI_ROWS - 1) / MI_ROWS;
-    int64_t grid = std::min<int64_t>(n_tiles, 2LL * num_sms());  // two resident CTAs per SM
+    const int64_t per_iter = (int64_t)NT * MI_ROWS;
+    const int64_t n_tiles = (rows + per_iter - 1) / per_iter;
+    int64_t grid = std::min<int64_t>(n_tiles, (int64_t)C::CTAS_PER_SM * num_sms());
     grid = (grid + CL - 1) / CL * CL;
     const int64_t n_iter = (n_tiles + grid - 1) / grid;
     if (n_iter * MLP_TILES > 0x7fffffffLL) { set_error("too many pairs for one launch"); return XLMIMO_EINVAL; }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(MI_THREADS);
-    cfg.dynamicSmemBytes = MI_SMEM;
+    cfg.blockDim = dim3(C::THREADS);
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -489,33 +562,56 @@ static int mlp_infer_launch(const FeatConst& fc, const double* users, int K, int
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cuda_status(cudaLaunchKernelEx(&cfg, mlp_infer_tc_kernel<CL>, fc, (const double2*)users, K, rows,
+    return cuda_status(cudaLaunchKernelEx(&cfg, mlp_infer_tc_kernel<CL, NT, HB>, fc, (const double2*)users, K, rows,
                                           (int)n_iter, (const unsigned char*)packed, (double2*)gram),
                        "surrogate kernel launch");
+}
+
+// Row tiles per CTA: 1 (measured faster than 2 in lockstep) unless
+// XLMIMO_SURROGATE_TILES (1 or 2) says otherwise.
+static int mlp_infer_tiles() {
+    static int nt = 0;
+    if (!nt) {
+        int v = 1;
+        if (const char* e = getenv("XLMIMO_SURROGATE_TILES")) {
+            const int x = atoi(e);
+            if (x == 1 || x == 2) v = x;
+        }
+        nt = v;
+    }
+    return nt;
 }
 
 }  // namespace xl
 
 using namespace xl;
 
-extern "C" int xlmimo_surrogate_gram(const xlmimo_array* arr, const double* users, int K, int B, const void* packed,
-                                     double* gram, void* stream) {
+extern "C" int xlmimo_surrogate_gram(const xlmimo_array* arr, const double* users, int K, int B, int base,
+                                     const void* packed, double* gram, void* stream) {
     clear_error();
     Geom g;
     int rc = check_array(arr, &g);
     if (rc) return rc;
     if (K < 1 || K > XLMIMO_MAX_USERS || B < 0) { set_error("K must be in [1, 64] and B >= 0"); return XLMIMO_EINVAL; }
+    if (base < XLMIMO_APERTURE_NONE || base > XLMIMO_APERTURE_FRESNEL) { set_error("unknown base %d", base); return XLMIMO_EINVAL; }
     if (B == 0) return XLMIMO_OK;
     if (!users || !gram || !packed) { set_error("users, packed and gram must be non-NULL"); return XLMIMO_EINVAL; }
     if (((uintptr_t)packed & 15u) != 0) { set_error("packed must be 16-byte aligned"); return XLMIMO_EINVAL; }
     cudaStream_t st = as_stream(stream);
     rc = launch_closed_form(g, users, K, B, gram, st);
     if (rc || K < 2) return rc;
+    // the base G~ F goes into the lower triangle (conjugated); the network's
+    // kernel reads G~ above the diagonal and G~ F below, and writes G~ F + G~ t
+    if ((rc = launch_aperture_base(g, base, users, K, B, gram, st))) return rc;
     const int64_t rows = (int64_t)B * (K * (K - 1) / 2);
     const FeatConst fc = make_feat_const(g);
+    const bool two = mlp_infer_tiles() == 2, hb = base != XLMIMO_APERTURE_NONE;
+#define XL_MI(CL_, NT_) (hb ? mlp_infer_launch<CL_, NT_, true>(fc, users, K, rows, packed, gram, st) \
+                            : mlp_infer_launch<CL_, NT_, false>(fc, users, K, rows, packed, gram, st))
     switch (mlp_infer_cluster()) {
-        case 1: return mlp_infer_launch<1>(fc, users, K, rows, packed, gram, st);
-        case 4: return mlp_infer_launch<4>(fc, users, K, rows, packed, gram, st);
-        default: return mlp_infer_launch<2>(fc, users, K, rows, packed, gram, st);
+        case 2: return two ? XL_MI(2, 2) : XL_MI(2, 1);
+        case 4: return two ? XL_MI(4, 2) : XL_MI(4, 1);
+        default: return two ? XL_MI(1, 2) : XL_MI(1, 1);
     }
+#undef XL_MI
 }

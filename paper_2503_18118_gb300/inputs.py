@@ -99,9 +99,11 @@ SWEEP = Workload("ula28ghz_k8_sweep", 28e9, 65536, 8, 1000, (5.0, 50.0), scheme=
 # Learned surrogate: trained on 10^7 pairs from K = 64 trials with N
 # log-uniform in [2^10, 2^18] and a carrier of 28 GHz (r in [5, 50] m) or
 # 100 GHz (r in [3, 30] m); evaluated at 100 GHz, N = 2^18, K = 64, 10^4 trials.
+# base 2: the network corrects the closed form times the finite-aperture
+# Fresnel factor.
 SURROGATE = Workload("ula100ghz_n262144_k64_surrogate", 100e9, 262144, 64, 10_000, (3.0, 30.0), scheme=0, seed=5,
                      extra={"train_pairs": 10_000_000, "n_log2": (10.0, 18.0), "train_seed": 5, "eval_seed": 6,
-                            "steps": 8000, "batch": 16384, "lr": 1e-3})
+                            "steps": 8000, "batch": 16384, "lr": 1e-3, "base": 2})
 
 
 def ragged_instances(seed: int, count: int, n_log2=(10.0, 17.0), k_range=(2, 64),

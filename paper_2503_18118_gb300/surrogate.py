@@ -19,7 +19,8 @@ from . import inputs
 from . import xlmimo as X
 
 
-def label_pairs(n, freq, users, prec=X.BF16X3, model=X.FSPL_USW, weights=False, device="cuda"):
+def label_pairs(n, freq, users, prec=X.BF16X3, model=X.FSPL_USW, weights=False, base=X.APERTURE_NONE,
+                device="cuda"):
     """Features and targets of every pair of every trial (trial t: n[t]
     elements, carrier freq[t], users[t] [K][2]); trials are labelled one by one
     because each has its own array.  Returns (feat [R][6], target [R][2],
@@ -33,7 +34,7 @@ def label_pairs(n, freq, users, prec=X.BF16X3, model=X.FSPL_USW, weights=False, 
         u = ud[t:t + 1]
         g = X.xlmimo_channel_gram(arr, u, prec)
         gc = X.xlmimo_corr_closed_form(arr, u)
-        f, tg, w = X.xlmimo_pair_features(arr, u, g, gc, weights=weights)
+        f, tg, w = X.xlmimo_pair_features(arr, u, g, gc, weights=weights, base=base)
         feats.append(f)
         targets.append(tg)
         if weights:
@@ -106,26 +107,29 @@ class Trainer:
         self.gen.set_state(torch.from_numpy(d["rng"]))
 
 
-def compare(arr, users, packed, snr_db=10.0, prec=X.BF16X3, scheme=X.ZF):
-    """Exact, closed-form and surrogate Gram of the same trials and the sum
-    rates of the receiver built on each, all judged on the exact channel.
-    Returns a dict of per-trial numpy arrays: rate_exact, rate_cf, rate_sur,
-    gram_err_cf, gram_err_sur (RMS over pairs of |G^_ij - G_ij| / sqrt(G_ii G_jj))."""
+def compare(arr, users, packed, snr_db=10.0, prec=X.BF16X3, scheme=X.ZF, base=X.APERTURE_NONE):
+    """Exact, closed-form (paper; aperture mask; Fresnel factor) and surrogate
+    Gram of the same trials and the sum rates of the receiver built on each,
+    all judged on the exact channel.  Returns a dict of per-trial numpy arrays:
+    rate_{exact,cf,mask,fresnel,sur}, status_*, gram_err_{cf,mask,fresnel,sur}
+    (RMS over pairs of |G^_ij - G_ij| / sqrt(G_ii G_jj))."""
     B, K = users.shape[0], users.shape[1]
     g = X.xlmimo_channel_gram(arr, users, prec)
     gc = X.xlmimo_corr_closed_form(arr, users)
-    gs = X.xlmimo_surrogate_gram(arr, users, packed)
+    gm = X.xlmimo_corr_closed_form_aperture(arr, users, X.APERTURE_MASK)
+    gf = X.xlmimo_corr_closed_form_aperture(arr, users, X.APERTURE_FRESNEL)
+    gs = X.xlmimo_surrogate_gram(arr, users, packed, base=base)
     power = torch.full((B, K), 10.0 ** (snr_db / 10.0), dtype=torch.float64, device=users.device)
     noise = torch.ones((B,), dtype=torch.float64, device=users.device)
     out = {}
-    for name, gf, gt in (("exact", g, None), ("cf", gc, g), ("sur", gs, g)):
-        sinr, status, _ = X.xlmimo_beamform(gf, power, noise, scheme, X.POWER_RXSNR, gram_true=gt)
+    for name, gfil, gt in (("exact", g, None), ("cf", gc, g), ("mask", gm, g), ("fresnel", gf, g), ("sur", gs, g)):
+        sinr, status, _ = X.xlmimo_beamform(gfil, power, noise, scheme, X.POWER_RXSNR, gram_true=gt)
         out["rate_" + name] = X.xlmimo_sumrate(sinr)[0].cpu().numpy()
         out["status_" + name] = status.cpu().numpy()
     d = torch.diagonal(g, dim1=1, dim2=2).real
     nrm = torch.sqrt(d[:, :, None] * d[:, None, :])
     off = ~torch.eye(K, dtype=torch.bool, device=users.device)
-    for name, gh in (("cf", gc), ("sur", gs)):
+    for name, gh in (("cf", gc), ("mask", gm), ("fresnel", gf), ("sur", gs)):
         e = ((gh - g).abs() / nrm)[:, off]
         out["gram_err_" + name] = torch.sqrt((e ** 2).mean(dim=1)).cpu().numpy()
     return out
@@ -147,6 +151,7 @@ def main(argv=None):
     t.add_argument("--batch", type=int, default=16384)
     t.add_argument("--lr", type=float, default=1e-3)
     t.add_argument("--seed", type=int, default=5)
+    t.add_argument("--base", type=int, default=0, help="aperture factor the network corrects (0 none, 1 mask, 2 Fresnel)")
     t.add_argument("--out", required=True)
     i = sub.add_parser("infer")
     i.add_argument("--checkpoint")
@@ -156,11 +161,12 @@ def main(argv=None):
     i.add_argument("--freq-ghz", type=float, default=100.0)
     i.add_argument("--repeat", type=int, default=2)
     i.add_argument("--seed", type=int, default=6)
+    i.add_argument("--base", type=int, default=0)
     a = ap.parse_args(argv)
     if a.cmd == "train":
         trials = int(math.ceil(a.pairs / (a.k * (a.k - 1) // 2)))
         n, freq, users = inputs.surrogate_trials(a.seed, trials, a.k)
-        feat, target, _ = label_pairs(n, freq, users)
+        feat, target, _ = label_pairs(n, freq, users, base=a.base)
         tr = Trainer(torch.from_numpy(inputs.mlp_init_params(a.seed)).cuda(), batch=a.batch, lr=a.lr, seed=a.seed)
         t0 = time.perf_counter()
         log = tr.fit(feat, target, steps=a.steps, log_every=max(1, a.steps // 10))
@@ -181,7 +187,7 @@ def main(argv=None):
         for _ in range(a.repeat):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            X.xlmimo_surrogate_gram(arr, u, packed, g)
+            X.xlmimo_surrogate_gram(arr, u, packed, g, base=a.base)
             e1.record()
             torch.cuda.synchronize()
             print(f"surrogate Gram of {a.trials} trials (K={a.k}, N={a.n}): {e0.elapsed_time(e1):.3f} ms, "

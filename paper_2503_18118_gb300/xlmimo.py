@@ -18,6 +18,7 @@ F64, F32, BF16, BF16X3, F16X3 = 0, 1, 2, 3, 4
 ZF, MMSE, MRC = 0, 1, 2
 POWER_ABS, POWER_RXSNR = 0, 1
 DIST_RECT, DIST_POLAR = 0, 1
+APERTURE_NONE, APERTURE_MASK, APERTURE_FRESNEL = 0, 1, 2
 MAX_USERS = 64
 STATUS = {0: "OK", 1: "EINVAL", 2: "ECUDA", 3: "ENOMEM", 4: "ESINGULAR", 5: "ETIMEOUT", 6: "EUNSUPPORTED"}
 
@@ -65,7 +66,8 @@ class Inst(ctypes.Structure):
 
 
 EXPORTS = ("xlmimo_batch_plan_create", "xlmimo_batch_run", "xlmimo_batch_plan_info", "xlmimo_batch_plan_destroy",
-           "xlmimo_mc_step", "xlmimo_channel_gram", "xlmimo_channel_gram_noalloc", "xlmimo_corr_closed_form", "xlmimo_beamform", "xlmimo_sumrate",
+           "xlmimo_mc_step", "xlmimo_channel_gram", "xlmimo_channel_gram_noalloc", "xlmimo_corr_closed_form",
+           "xlmimo_corr_closed_form_aperture", "xlmimo_beamform", "xlmimo_sumrate",
            "xlmimo_saturation", "xlmimo_saturation_analytic", "xlmimo_capacity_sweep", "xlmimo_pair_features",
            "xlmimo_mlp_forward", "xlmimo_mlp_loss", "xlmimo_mlp_work_floats", "xlmimo_mlp_backward", "xlmimo_mlp_adam",
            "xlmimo_mlp_train_step", "xlmimo_mlp_pack", "xlmimo_surrogate_gram", "xlmimo_last_error", "xlmimo_version")
@@ -103,7 +105,8 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.xlmimo_saturation.argtypes = [vp, i32, i32, dbl, dbl, vp, vp]
     L.xlmimo_saturation_analytic.argtypes = [ctypes.POINTER(UserDist), i32, dbl, dbl, ctypes.POINTER(dbl), vp]
     L.xlmimo_capacity_sweep.argtypes = [ctypes.POINTER(SweepCfg), ctypes.POINTER(SweepResult), vp]
-    L.xlmimo_pair_features.argtypes = [ctypes.POINTER(Array), vp, i32, i32, vp, vp, vp, vp, vp, vp]
+    L.xlmimo_corr_closed_form_aperture.argtypes = [ctypes.POINTER(Array), vp, i32, i32, i32, vp, vp]
+    L.xlmimo_pair_features.argtypes = [ctypes.POINTER(Array), vp, i32, i32, i32, vp, vp, vp, vp, vp, vp]
     L.xlmimo_mlp_forward.argtypes = [vp, vp, i32, vp, vp, vp]
     L.xlmimo_mlp_loss.argtypes = [vp, vp, vp, i32, vp, vp, vp]
     L.xlmimo_mlp_work_floats.argtypes = [i32]
@@ -112,7 +115,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.xlmimo_mlp_adam.argtypes = [vp, vp, vp, vp, i64, dbl, dbl, dbl, dbl, vp]
     L.xlmimo_mlp_train_step.argtypes = [vp, vp, vp, vp, i64, dbl, vp, vp, vp, i32, vp, vp, vp, vp, vp]
     L.xlmimo_mlp_pack.argtypes = [vp, vp, vp]
-    L.xlmimo_surrogate_gram.argtypes = [ctypes.POINTER(Array), vp, i32, i32, vp, vp, vp]
+    L.xlmimo_surrogate_gram.argtypes = [ctypes.POINTER(Array), vp, i32, i32, i32, vp, vp, vp]
     L.xlmimo_last_error.restype = ctypes.c_char_p
     for f in EXPORTS:
         if f not in ("xlmimo_last_error", "xlmimo_mlp_work_floats"):
@@ -234,6 +237,18 @@ def xlmimo_corr_closed_form(arr: Array, users: torch.Tensor, gram: torch.Tensor 
         gram = torch.empty((B, K, K), dtype=torch.complex128, device=users.device)
     _check(lib().xlmimo_corr_closed_form(ctypes.byref(arr), _dev(users, torch.float64, "users", (B, K, 2)), K, B,
                                          _dev(gram, torch.complex128, "gram", (B, K, K)), _stream(stream)))
+    return gram
+
+
+def xlmimo_corr_closed_form_aperture(arr: Array, users: torch.Tensor, mode: int, gram: torch.Tensor | None = None,
+                                     stream=None) -> torch.Tensor:
+    """Closed form with the finite-aperture correction `mode` (APERTURE_*), complex128 [B][K][K]."""
+    B, K = users.shape[0], users.shape[1]
+    if gram is None:
+        gram = torch.empty((B, K, K), dtype=torch.complex128, device=users.device)
+    _check(lib().xlmimo_corr_closed_form_aperture(ctypes.byref(arr), _dev(users, torch.float64, "users", (B, K, 2)), K,
+                                                  B, int(mode), _dev(gram, torch.complex128, "gram", (B, K, K)),
+                                                  _stream(stream)))
     return gram
 
 
@@ -371,8 +386,10 @@ def _opt(t, dtype, name, shape=None):
 
 
 def xlmimo_pair_features(arr: Array, users: torch.Tensor, gram: torch.Tensor | None = None,
-                         gram_cf: torch.Tensor | None = None, weights: bool = False, stream=None):
-    """(feat [B*P][6], target [B*P][2] or None, weight [B*P] or None), float32, P = K(K-1)/2."""
+                         gram_cf: torch.Tensor | None = None, weights: bool = False, base: int = APERTURE_NONE,
+                         stream=None):
+    """(feat [B*P][6], target [B*P][2] or None, weight [B*P] or None), float32, P = K(K-1)/2;
+    targets G/G~ - F with F the aperture factor `base`."""
     B, K = users.shape[0], users.shape[1]
     rows = B * (K * (K - 1) // 2)
     dev = users.device
@@ -380,7 +397,7 @@ def xlmimo_pair_features(arr: Array, users: torch.Tensor, gram: torch.Tensor | N
     target = torch.empty((rows, MLP_OUT), dtype=torch.float32, device=dev) if gram is not None else None
     weight = torch.empty((rows,), dtype=torch.float32, device=dev) if weights else None
     _check(lib().xlmimo_pair_features(ctypes.byref(arr), _dev(users, torch.float64, "users", (B, K, 2)), K, B,
-                                      _opt(gram, torch.complex128, "gram", (B, K, K)),
+                                      int(base), _opt(gram, torch.complex128, "gram", (B, K, K)),
                                       _opt(gram_cf, torch.complex128, "gram_cf", (B, K, K)),
                                       _dev(feat, torch.float32, "feat"), _opt(target, torch.float32, "target"),
                                       _opt(weight, torch.float32, "weight"), _stream(stream)))
@@ -469,13 +486,14 @@ def xlmimo_mlp_pack(params: torch.Tensor, packed: torch.Tensor | None = None, st
 
 
 def xlmimo_surrogate_gram(arr: Array, users: torch.Tensor, packed: torch.Tensor, gram: torch.Tensor | None = None,
-                          stream=None) -> torch.Tensor:
-    """Surrogate Gram matrices, complex128 [B][K][K]: closed form corrected by the network."""
+                          base: int = APERTURE_NONE, stream=None) -> torch.Tensor:
+    """Surrogate Gram matrices, complex128 [B][K][K]: closed form times (F + t), F the
+    aperture factor `base` the network was trained with, t from the network."""
     B, K = users.shape[0], users.shape[1]
     if gram is None:
         gram = torch.empty((B, K, K), dtype=torch.complex128, device=users.device)
     _check(lib().xlmimo_surrogate_gram(ctypes.byref(arr), _dev(users, torch.float64, "users", (B, K, 2)), K, B,
-                                       _dev(packed, torch.uint8, "packed", (MLP_PACKED_BYTES,)),
+                                       int(base), _dev(packed, torch.uint8, "packed", (MLP_PACKED_BYTES,)),
                                        _dev(gram, torch.complex128, "gram", (B, K, K)), _stream(stream)))
     return gram
 

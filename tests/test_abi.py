@@ -94,19 +94,23 @@ def test_surrogate_entries_validate_on_host(xl):
     L = xl.lib()
     dummy = ctypes.c_void_p(16)
     arr = xl.array(1024, 0.01)
-    assert L.xlmimo_pair_features(ctypes.byref(arr), dummy, 1, 1, None, None, dummy, None, None, None) == 1
-    assert L.xlmimo_pair_features(ctypes.byref(arr), dummy, 4, 1, None, None, dummy, dummy, None, None) == 1
+    assert L.xlmimo_pair_features(ctypes.byref(arr), dummy, 1, 1, 0, None, None, dummy, None, None, None) == 1
+    assert L.xlmimo_pair_features(ctypes.byref(arr), dummy, 4, 1, 0, None, None, dummy, dummy, None, None) == 1
     assert b"targets need" in L.xlmimo_last_error()
-    assert L.xlmimo_pair_features(ctypes.byref(arr), None, 4, 0, None, None, None, None, None, None) == 0
+    assert L.xlmimo_pair_features(ctypes.byref(arr), dummy, 4, 1, 3, None, None, dummy, None, None, None) == 1
+    assert L.xlmimo_pair_features(ctypes.byref(arr), None, 4, 0, 0, None, None, None, None, None, None) == 0
+    assert L.xlmimo_corr_closed_form_aperture(ctypes.byref(arr), dummy, 4, 1, 3, dummy, None) == 1
+    assert L.xlmimo_corr_closed_form_aperture(ctypes.byref(arr), None, 4, 0, 2, None, None) == 0
     assert L.xlmimo_mlp_adam(dummy, dummy, dummy, dummy, 0, 1e-3, 0.9, 0.999, 1e-8, None) == 1
     assert L.xlmimo_mlp_adam(dummy, dummy, dummy, dummy, 1, 1e-3, 1.0, 0.999, 1e-8, None) == 1
     assert L.xlmimo_mlp_forward(dummy, dummy, -1, dummy, None, None) == 1
     assert L.xlmimo_mlp_forward(dummy, dummy, 0, dummy, None, None) == 0
     assert L.xlmimo_mlp_pack(dummy, ctypes.c_void_p(24), None) == 1
     assert b"16-byte" in L.xlmimo_last_error()
-    assert L.xlmimo_surrogate_gram(ctypes.byref(arr), dummy, 4, 1, ctypes.c_void_p(8), dummy, None) == 1
-    assert L.xlmimo_surrogate_gram(ctypes.byref(arr), dummy, 65, 1, dummy, dummy, None) == 1
-    assert L.xlmimo_surrogate_gram(ctypes.byref(arr), None, 4, 0, None, None, None) == 0
+    assert L.xlmimo_surrogate_gram(ctypes.byref(arr), dummy, 4, 1, 0, ctypes.c_void_p(8), dummy, None) == 1
+    assert L.xlmimo_surrogate_gram(ctypes.byref(arr), dummy, 65, 1, 0, dummy, dummy, None) == 1
+    assert L.xlmimo_surrogate_gram(ctypes.byref(arr), dummy, 4, 1, 7, dummy, dummy, None) == 1
+    assert L.xlmimo_surrogate_gram(ctypes.byref(arr), None, 4, 0, 0, None, None, None) == 0
     assert L.xlmimo_mlp_train_step(dummy, dummy, dummy, dummy, 1, 1e-3, dummy, dummy, None, 0, dummy, dummy,
                                    dummy, None, None) == 1
     # workspace: two [M][256] slabs plus one [257][256] partial per 512 rows

@@ -188,6 +188,27 @@ def test_surrogate_matches_oracle(orc, K, B):
     assert np.array_equal(gs, np.conj(np.transpose(gs, (0, 2, 1))))
 
 
+@pytest.mark.parametrize("base", [1, 2])
+def test_pair_targets_and_constant_network_with_aperture_base(orc, base):
+    """Targets G/G~ - F and the surrogate G~ (F + t) for the aperture factors."""
+    from oracle import aperture as ap
+    users, n, lam = small_case(K=9, B=6, n=2048, f=100e9, seed=44)
+    G = orc.gram(orc.FSPL, n, lam, lam / 2, 1.0, users)
+    Gc = orc.closed_form(orc.FSPL, n, lam, lam / 2, 1.0, users)
+    F = ap.factors(base, users, n, lam, lam / 2)
+    arr = X.array(n, lam)
+    _, t, _ = X.xlmimo_pair_features(arr, dev(users), dev(G), dev(Gc), base=base)
+    want = mlp.pair_targets(G, Gc) + np.stack([1.0 - F.real, -F.imag], 1)
+    assert np.allclose(t.cpu().numpy(), want, rtol=0, atol=3e-5 * max(1.0, float(np.abs(want).max())))
+    p = np.zeros(X.MLP_PARAMS, np.float32)
+    p[-2:] = [0.125, 0.0625]
+    gs = X.xlmimo_surrogate_gram(arr, dev(users), X.xlmimo_mlp_pack(dev(p)), base=base).cpu().numpy()
+    K = users.shape[1]
+    iu = np.triu_indices(K, 1)
+    w = Gc[:, iu[0], iu[1]] * (F.reshape(users.shape[0], -1) + 0.125 + 0.0625j)
+    assert np.all(np.abs(gs[:, iu[0], iu[1]] - w) <= 3e-5 * np.abs(Gc[:, iu[0], iu[1]]))
+
+
 def test_surrogate_empty_and_single_user():
     arr = X.array(1024, 0.01)
     packed = X.xlmimo_mlp_pack(dev(np.zeros(X.MLP_PARAMS, np.float32)))
@@ -220,6 +241,24 @@ def test_trained_surrogate_beats_closed_form():
     assert np.all(res["status_sur"] == 0)
     assert float(np.mean(res["gram_err_sur"])) < float(np.mean(res["gram_err_cf"]))
     assert float(np.mean(e_sur)) < 0.7 * float(np.mean(e_cf)), (np.mean(e_sur), np.mean(e_cf))
+
+
+def test_trained_surrogate_on_fresnel_base_does_not_lose():
+    """With the finite-aperture Fresnel factor as its base, the network
+    corrects an already good analytic form: trained briefly, it must stay
+    within 10 % of that form's sum-rate error and well below the paper's
+    closed form."""
+    n, freq, users = inputs.surrogate_trials(75, 600, 32)
+    feat, target, _ = surrogate.label_pairs(n, freq, users, base=X.APERTURE_FRESNEL)
+    params = dev(inputs.mlp_init_params(76))
+    surrogate.Trainer(params, batch=4096, lr=1e-3, seed=77).fit(feat, target, steps=1500)
+    packed = X.xlmimo_mlp_pack(params)
+    arr = X.array(262144, inputs.wavelength(100e9))
+    u = dev(inputs.users_polar(78, 8, 32, (3.0, 30.0)))
+    res = surrogate.compare(arr, u, packed, base=X.APERTURE_FRESNEL)
+    re = res["rate_exact"]
+    e = {k: float(np.mean(np.abs(res["rate_" + k] - re) / re)) for k in ("cf", "fresnel", "sur")}
+    assert e["sur"] <= 1.1 * e["fresnel"] and e["sur"] < 0.5 * e["cf"], e
 
 
 def test_trainer_checkpoint_roundtrip(tmp_path):
