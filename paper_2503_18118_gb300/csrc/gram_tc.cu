@@ -128,8 +128,8 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
                     gen_pair<MODEL>(pc, make_float2(mf0 + (float)i, mf0 + (float)(i + 1)), re, im);
                     if (i >= rem) { re.x = 0.f; im.x = 0.f; }
                     if (i + 1 >= rem) { re.y = 0.f; im.y = 0.f; }
-                    split2<PREC>(re.x, re.y, w[0][i >> 1], w[2][i >> 1]);
-                    split2<PREC>(im.x, im.y, w[1][i >> 1], w[3][i >> 1]);
+                    split2<PREC, KMAX == 32>(re.x, re.y, w[0][i >> 1], w[2][i >> 1]);
+                    split2<PREC, KMAX == 32>(im.x, im.y, w[1][i >> 1], w[3][i >> 1]);
                 }
                 const int ncomp = (PREC == TCP_BF16 && KMAX == 64) ? 2 : 4;  // the one-term K>32 MMA reads hi only
 #pragma unroll

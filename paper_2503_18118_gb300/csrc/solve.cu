@@ -176,6 +176,101 @@ __device__ void gram_of_lower(const cd* X, cd* M, int K) {
     }
 }
 
+// ---- double-float (FP32 pair) arithmetic for the long dot products --------
+// The mismatched receiver's products M = X^H X and A = M G cancel heavily
+// (A = I + a small remainder), so FP32 is not enough; FP64 on this GPU issues
+// a warp instruction every ~64 cycles per scheduler.  These two products run
+// in double-float on the FP32 pipe instead: a value is hi + lo (|lo| <= half
+// an ulp of hi), products by Dekker's exact two-product (FMA residual) with
+// the cross terms hi*lo + lo*hi, sums by Knuth's two-sum on the hi parts with
+// the low-order parts summed alongside (~2^-48 relative over K <= 64 terms).
+// Real and imaginary lanes travel together through packed FP32x2 operations.
+struct cf {
+    float2 hi, lo;  // (re, im) high and low parts; same 16 bytes as a cd
+};
+
+__device__ __forceinline__ cf to_cf(cd a) {
+    const float rh = (float)a.x, ih = (float)a.y;
+    return {make_float2(rh, ih), make_float2((float)(a.x - (double)rh), (float)(a.y - (double)ih))};
+}
+
+__device__ __forceinline__ cd from_cf(cf a) {
+    return cmk((double)a.hi.x + (double)a.lo.x, (double)a.hi.y + (double)a.lo.y);
+}
+
+// (s, c) += x * y, lane-wise on two lanes: x, y double-float (hi, lo).
+__device__ __forceinline__ void ff2_mac(float2& s, float2& c, float2 xh, float2 xl, float2 yh, float2 yl) {
+    const float2 p = __fmul2_rn(xh, yh);
+    float2 e = __ffma2_rn(xh, yh, make_float2(-p.x, -p.y));  // exact: xh yh = p + e
+    e = __ffma2_rn(xh, yl, e);
+    e = __ffma2_rn(xl, yh, e);
+    const float2 t = __fadd2_rn(s, p);  // two-sum: s + p = t + err exactly
+    const float2 bb = __fadd2_rn(t, make_float2(-s.x, -s.y));
+    const float2 ea = __fadd2_rn(s, make_float2(-(t.x - bb.x), -(t.y - bb.y)));
+    const float2 eb = __fadd2_rn(p, make_float2(-bb.x, -bb.y));
+    s = t;
+    c = __fadd2_rn(c, __fadd2_rn(__fadd2_rn(ea, eb), e));
+}
+
+// acc += a b (conj_a: conj(a) b), complex double-float: the real lanes carry
+// (re a re b, re a im b) and the imaginary ones (-+ im a im b, +- im a re b).
+__device__ __forceinline__ void cf_mac(float2& s, float2& c, const cf& a, const cf& b, bool conj_a) {
+    ff2_mac(s, c, make_float2(a.hi.x, a.hi.x), make_float2(a.lo.x, a.lo.x), b.hi, b.lo);
+    const float sg = conj_a ? 1.0f : -1.0f;  // re: -/+ im a im b; im: +/- im a re b
+    ff2_mac(s, c, make_float2(sg * a.hi.y, -sg * a.hi.y), make_float2(sg * a.lo.y, -sg * a.lo.y),
+            make_float2(b.hi.y, b.hi.x), make_float2(b.lo.y, b.lo.x));
+}
+
+__device__ __forceinline__ cd cf_result(float2 s, float2 c) { return cmk((double)s.x + (double)c.x, (double)s.y + (double)c.y); }
+
+// In place: a K x K complex FP64 matrix becomes double-float (same bytes).
+__device__ void to_cf_inplace(cd* A, int K) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    cf* F = reinterpret_cast<cf*>(A);
+    for (int e = tid; e < K * K; e += nt) {
+        const cf v = to_cf(A[e]);
+        F[e] = v;
+    }
+    __syncthreads();
+}
+
+// M = X^H X for lower-triangular X (converted to double-float in place):
+// M_rc = sum_{l >= max(r, c)} conj(X_lr) X_lc, upper triangle computed and
+// mirrored, written as FP64.
+__device__ void gram_of_lower_ff(cd* X, cd* M, int K) {
+    to_cf_inplace(X, K);
+    const cf* F = reinterpret_cast<const cf*>(X);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int P = K * (K + 1) / 2;
+    for (int q = tid; q < P; q += nt) {
+        int r = 0, rl = K, w = q;
+        while (w >= rl) { w -= rl; ++r; --rl; }
+        const int c = r + w;  // r <= c
+        float2 s = make_float2(0.f, 0.f), cc = make_float2(0.f, 0.f);
+        for (int l = c; l < K; ++l) cf_mac(s, cc, F[l * K + r], F[l * K + c], true);
+        const cd v = cf_result(s, cc);
+        M[r * K + c] = v;
+        M[c * K + r] = cmk(v.x, -v.y);
+    }
+    __syncthreads();
+}
+
+// Z = M G, both converted to double-float in place, written as FP64.
+__device__ void prod_ff(cd* Mx, cd* G, cd* Z, int K) {
+    to_cf_inplace(Mx, K);
+    to_cf_inplace(G, K);
+    const cf* FM = reinterpret_cast<const cf*>(Mx);
+    const cf* FG = reinterpret_cast<const cf*>(G);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < K * K; e += nt) {
+        const int r = e / K, c = e - r * K;
+        float2 s = make_float2(0.f, 0.f), cc = make_float2(0.f, 0.f);
+        for (int l = 0; l < K; ++l) cf_mac(s, cc, FM[r * K + l], FG[l * K + c], false);
+        Z[e] = cf_result(s, cc);
+    }
+    __syncthreads();
+}
+
 // Gauss-Jordan inverse with partial pivoting: A is destroyed, X = A^{-1}.
 __device__ int gj_inverse_dev(cd* A, cd* X, int K, int* flag, int* piv) {
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -307,7 +402,7 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
                 __syncthreads();
             } else {
                 // M = X^H X into Z (the factor is no longer needed), then M back into X
-                gram_of_lower(X, Z, K);
+                gram_of_lower_ff(X, Z, K);
                 for (int e = tid; e < KK; e += nt) X[e] = Z[e];
                 __syncthreads();
             }
@@ -372,21 +467,16 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
             sinr_t[k] = v;
         }
     } else {
-        // A = M G (M in X) into Z, element-parallel with uniform dot length
-        for (int e = tid; e < KK; e += nt) {
-            const int r = e / K, c = e - r * K;
-            cd acc = cmk(0.0, 0.0);
-            for (int l = 0; l < K; ++l) acc = cmac(acc, X[r * K + l], G[l * K + c]);
-            Z[e] = acc;
-        }
-        __syncthreads();
+        // A = M G (M in X) into Z in double-float; X and G are left in double-float
+        prod_ff(X, G, Z, K);
+        const cf* FM = reinterpret_cast<const cf*>(X);
         for (int k = tid; k < K; k += nt) {
             double sig = p[k] * cabs2(Z[k * K + k]);
             double itf = 0.0, nz = 0.0;
             for (int j = 0; j < K; ++j) {
                 cd a = Z[k * K + j];
                 if (j != k) itf = fma(p[j], cabs2(a), itf);
-                nz += cmulc(a, X[k * K + j]).x;  // (A M^H)_kk
+                nz += cmulc(a, from_cf(FM[k * K + j])).x;  // (A M^H)_kk
             }
             sinr_t[k] = sig / fma(s2, nz, itf);
         }

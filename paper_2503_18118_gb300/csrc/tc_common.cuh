@@ -144,14 +144,28 @@ struct TcShared {
     float scale[KMAX];  // FP16 path: per-user entry scale
 };
 
-// hi/lo (or hi only) 16-bit conversion of two values, packed
-template <int PREC>
+// hi/lo (or hi only) 16-bit conversion of two values, packed.  TRUNC (BF16
+// hi/lo only): hi by truncation, for the K <= 32 kernels whose products keep
+// the lo*lo term, so only lo's own rounding (2^-17 relative instead of 2^-18)
+// is given up; the K <= 64 kernels drop lo*lo and need the round-to-nearest
+// hi, whose remainder is half as large.
+template <int PREC, bool TRUNC = false>
 __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
     if (PREC == TCP_F16X3) {
         __half2 h = __floats2half2_rn(a, b);
         float2 hf = __half22float2(h);
         __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
         hi = *reinterpret_cast<uint32_t*>(&h);
+        lo = *reinterpret_cast<uint32_t*>(&l);
+    } else if (PREC == TCP_BF16X3 && TRUNC) {
+        // hi = the upper 16 bits of each float (truncation: one byte permute
+        // packs both), lo = the exact remainder rounded to BF16; |lo| < 2^-7 |x|,
+        // so hi + lo carries x to ~2^-16 relative
+        const uint32_t xa = __float_as_uint(a), xb = __float_as_uint(b);
+        hi = __byte_perm(xa, xb, 0x7632);
+        const float2 r = __fadd2_rn(make_float2(a, b), make_float2(-__uint_as_float(xa & 0xFFFF0000u),
+                                                                    -__uint_as_float(xb & 0xFFFF0000u)));
+        __nv_bfloat162 l = __floats2bfloat162_rn(r.x, r.y);
         lo = *reinterpret_cast<uint32_t*>(&l);
     } else {
         __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
