@@ -97,29 +97,67 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
     const int nst = (int)((nend - nbeg + TC_T - 1) / TC_T);
 
     if (warp < 8) {
-        // ---------------- generators: lane = user (and user + 32), warp = 8-element slice
-        UserRef ref[C::SLOTS];
+        // ---------------- generators: lane = user (and user + 32), warp = 8-element slice.
+        // The double-float phase references of a span (TC_REF_SPAN elements)
+        // are made once per CTA: warp (sp + 1) % 8 prepares span sp + 1 into
+        // the other half of a double buffer while span sp is generated, and
+        // the eight generator warps meet at a named barrier at every span
+        // start.  That barrier also votes on stopping, so that after an abort
+        // all 256 generator threads leave the loop together.
+        constexpr int SPAN_ST = TC_REF_SPAN / TC_T;  // stages per span
+        const int nsp = (nst + SPAN_ST - 1) / SPAN_ST;
+        auto make_refs = [&](int sp) {
+            const long long ncs = (long long)(nbeg + (int64_t)sp * TC_REF_SPAN + TC_REF_SPAN / 2);
+            for (int kk = lane; kk < KMAX; kk += 32) sh->ref[sp & 1][kk] = make_user_ref(gp, sh->ug[kk], ncs);
+        };
+        if (warp == 0 && nsp > 0) make_refs(0);
+        // stage-tile offsets of this lane's four component rows (slot 0, slot 1)
+        uint32_t soff[C::SLOTS][4];
+#pragma unroll
+        for (int slot = 0; slot < C::SLOTS; ++slot)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int f = KMAX * c + lane + 32 * slot;  // row of the stage tile
+                const int rin = f & 7;
+                soff[slot][c] = (uint32_t)((f >> 3) * 1024 + rin * 128 + ((warp ^ rin) << 4));
+            }
         PairConst pc = make_pair_const(UserRef{0.f, 0.f, 0.f, 0.f, 1.f}, gp.dprime_f, 0.f, 0.f, 0.f);
         int64_t nc = 0;
+        bool dead = false;
         for (int it = 0; it < nst; ++it) {
             const int st = it % TC_STAGES;
-            if (it >= TC_STAGES && !mbar_wait(&sh->empty[st], ((it / TC_STAGES) - 1) & 1, abort)) break;
+            const int sp = it / SPAN_ST;
+            if (it % SPAN_ST == 0) {
+                uint32_t stop;
+                const uint32_t mine = (dead || *abort) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, 256, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+                    : "=r"(stop)
+                    : "r"(mine)
+                    : "memory");
+                if (stop) break;
+                nc = nbeg + (int64_t)sp * TC_REF_SPAN + TC_REF_SPAN / 2;
+                if (C::SLOTS == 1) {
+                    const UserGeo& u = sh->ug[lane];
+                    pc = make_pair_const(sh->ref[sp & 1][lane], gp.dprime_f, u.xl2, u.x2x2, lane < K ? u.ampc : 0.f);
+                }
+                if (warp == ((sp + 1) & 7) && sp + 1 < nsp) make_refs(sp + 1);
+            }
+            if (dead) continue;
+            if (it >= TC_STAGES && !mbar_wait(&sh->empty[st], ((it / TC_STAGES) - 1) & 1, abort)) {
+                dead = true;
+                continue;
+            }
             const int64_t n0 = nbeg + (int64_t)it * TC_T;
-            const bool new_span = ((n0 - nbeg) % TC_REF_SPAN) == 0;
-            if (new_span) nc = n0 + TC_REF_SPAN / 2;
             const int rem = (int)min((int64_t)TC_T, nend - n0) - warp * 8;  // valid elements of this slice
             const float mf0 = (float)(int)(n0 + warp * 8 - nc);
-            unsigned char* sb = stages + st * C::STAGE_BYTES;
+            const uint32_t sb = smem_u32(stages + st * C::STAGE_BYTES);
 #pragma unroll
             for (int slot = 0; slot < C::SLOTS; ++slot) {
                 const int k = lane + 32 * slot;
-                const UserGeo& u = sh->ug[k];
-                const float ampc = k < K ? u.ampc : 0.f;
-                if (new_span) ref[slot] = make_user_ref(gp, u, (long long)nc);
-                if (C::SLOTS == 1) {
-                    if (new_span) pc = make_pair_const(ref[slot], gp.dprime_f, u.xl2, u.x2x2, ampc);
-                } else {
-                    pc = make_pair_const(ref[slot], gp.dprime_f, u.xl2, u.x2x2, ampc);
+                if (C::SLOTS > 1) {
+                    const UserGeo& u = sh->ug[k];
+                    pc = make_pair_const(sh->ref[sp & 1][k], gp.dprime_f, u.xl2, u.x2x2, k < K ? u.ampc : 0.f);
                 }
                 uint32_t w[4][4];  // [component: Re hi, Im hi, Re lo, Im lo][packed pair]
 #pragma unroll
@@ -135,11 +173,8 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     if (c >= ncomp) break;
-                    const int f = KMAX * c + k;  // row of the stage tile
-                    const int rin = f & 7;
-                    uint32_t addr = smem_u32(sb + (f >> 3) * 1024 + rin * 128 + ((warp ^ rin) << 4));
-                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(w[c][0]), "r"(w[c][1]),
-                                 "r"(w[c][2]), "r"(w[c][3])
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(sb + soff[slot][c]), "r"(w[c][0]),
+                                 "r"(w[c][1]), "r"(w[c][2]), "r"(w[c][3])
                                  : "memory");
                 }
             }
