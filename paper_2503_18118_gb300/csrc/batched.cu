@@ -16,6 +16,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <type_traits>
+
 #include "tc_common.cuh"
 
 namespace xl {
@@ -38,6 +40,7 @@ struct RgShared {
     int item;
     UserGeo ug[RG_KMAX];
     float scale[RG_KMAX];
+    UserRef ref[2][RG_KMAX];  // phase references of the current and the next span
 };
 
 template <int MODEL, int PREC>
@@ -116,35 +119,76 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         gpi.nm1 = in.n_ant - 1;
 
         if (warp < 8) {
-            UserRef ref[2];
+            // generators (see gram_tc_kernel): span references made once per
+            // CTA by a rotating warp into a double buffer, met at a named
+            // barrier that votes on stopping; store offsets computed once; full
+            // slices without per-element checks
+            constexpr int SPAN_ST = TC_REF_SPAN / TC_T;
+            const int nsp = (nst + SPAN_ST - 1) / SPAN_ST;
+            auto make_refs = [&](int sp) {
+                const long long ncs = (long long)(nbeg + (int64_t)sp * TC_REF_SPAN + TC_REF_SPAN / 2);
+                for (int kk = lane; kk < RG_KMAX; kk += 32) sh->ref[sp & 1][kk] = make_user_ref(gpi, sh->ug[kk], ncs);
+            };
+            if (warp == 0 && nsp > 0) make_refs(0);
+            uint32_t soff[2][4];
+#pragma unroll
+            for (int slot = 0; slot < 2; ++slot)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int f = RG_KMAX * c + lane + 32 * slot;
+                    const int rin = f & 7;
+                    soff[slot][c] = (uint32_t)((f >> 3) * 1024 + rin * 128 + ((warp ^ rin) << 4));
+                }
             int64_t nc = 0;
+            bool dead = false;
             for (int it = 0; it < nst; ++it) {
                 const long long gsi = gs + it;
                 const int st = (int)(gsi % TC_STAGES);
-                if (gsi >= TC_STAGES && !mbar_wait(&sh->empty[st], (uint32_t)(((gsi / TC_STAGES) - 1) & 1), abort)) break;
+                const int sp = it / SPAN_ST;
+                if (it % SPAN_ST == 0) {
+                    uint32_t stop;
+                    const uint32_t mine = (dead || *abort) ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, 256, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+                        : "=r"(stop)
+                        : "r"(mine)
+                        : "memory");
+                    if (stop) break;
+                    nc = nbeg + (int64_t)sp * TC_REF_SPAN + TC_REF_SPAN / 2;
+                    if (warp == ((sp + 1) & 7) && sp + 1 < nsp) make_refs(sp + 1);
+                }
+                if (dead) continue;
+                if (gsi >= TC_STAGES && !mbar_wait(&sh->empty[st], (uint32_t)(((gsi / TC_STAGES) - 1) & 1), abort)) {
+                    dead = true;
+                    continue;
+                }
                 const int64_t n0 = nbeg + (int64_t)it * TC_T;
-                const bool new_span = ((n0 - nbeg) % TC_REF_SPAN) == 0;
-                if (new_span) nc = n0 + TC_REF_SPAN / 2;
                 const int rem = (int)min((int64_t)TC_T, nend - n0) - warp * 8;
                 const float mf0 = (float)(int)(n0 + warp * 8 - nc);
-                unsigned char* sb = stages + st * RCfg::STAGE_BYTES;
+                const uint32_t sb = smem_u32(stages + st * RCfg::STAGE_BYTES);
 #pragma unroll
                 for (int slot = 0; slot < 2; ++slot) {
                     const int k = lane + 32 * slot;
                     uint32_t wv[4][4];
                     if (k < K || slot == 0) {
                         const UserGeo& u = sh->ug[k];
-                        if (new_span) ref[slot] = make_user_ref(gpi, u, (long long)nc);
-                        PairConst pc = make_pair_const(ref[slot], gpi.dprime_f, u.xl2, u.x2x2, k < K ? u.ampc : 0.f);
+                        const PairConst pc =
+                            make_pair_const(sh->ref[sp & 1][k], gpi.dprime_f, u.xl2, u.x2x2, k < K ? u.ampc : 0.f);
+                        auto slice = [&](auto partial) {
 #pragma unroll
-                        for (int i = 0; i < 8; i += 2) {
-                            float2 re, im;
-                            gen_pair<MODEL>(pc, make_float2(mf0 + (float)i, mf0 + (float)(i + 1)), re, im);
-                            if (i >= rem) { re.x = 0.f; im.x = 0.f; }
-                            if (i + 1 >= rem) { re.y = 0.f; im.y = 0.f; }
-                            split2<PREC>(re.x, re.y, wv[0][i >> 1], wv[2][i >> 1]);
-                            split2<PREC>(im.x, im.y, wv[1][i >> 1], wv[3][i >> 1]);
-                        }
+                            for (int i = 0; i < 8; i += 2) {
+                                float2 re, im;
+                                gen_pair<MODEL>(pc, make_float2(mf0 + (float)i, mf0 + (float)(i + 1)), re, im);
+                                if (decltype(partial)::value) {
+                                    if (i >= rem) { re.x = 0.f; im.x = 0.f; }
+                                    if (i + 1 >= rem) { re.y = 0.f; im.y = 0.f; }
+                                }
+                                split2<PREC>(re.x, re.y, wv[0][i >> 1], wv[2][i >> 1]);
+                                split2<PREC>(im.x, im.y, wv[1][i >> 1], wv[3][i >> 1]);
+                            }
+                        };
+                        if (rem >= 8) slice(std::integral_constant<bool, false>());
+                        else slice(std::integral_constant<bool, true>());
                     } else {
 #pragma unroll
                         for (int c = 0; c < 4; ++c)
@@ -155,11 +199,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
                         if (c >= ncomp) break;
-                        const int f = RG_KMAX * c + k;
-                        const int rin = f & 7;
-                        uint32_t addr = smem_u32(sb + (f >> 3) * 1024 + rin * 128 + ((warp ^ rin) << 4));
-                        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(wv[c][0]),
-                                     "r"(wv[c][1]), "r"(wv[c][2]), "r"(wv[c][3])
+                        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(sb + soff[slot][c]),
+                                     "r"(wv[c][0]), "r"(wv[c][1]), "r"(wv[c][2]), "r"(wv[c][3])
                                      : "memory");
                     }
                 }

@@ -30,6 +30,8 @@
 // lets outstanding MMAs drain and frees the tensor memory.
 #include <math.h>
 
+#include <type_traits>
+
 #include "tc_common.cuh"
 
 namespace xl {
@@ -160,15 +162,23 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
                     pc = make_pair_const(sh->ref[sp & 1][k], gp.dprime_f, u.xl2, u.x2x2, k < K ? u.ampc : 0.f);
                 }
                 uint32_t w[4][4];  // [component: Re hi, Im hi, Re lo, Im lo][packed pair]
+                // two instances of the slice: full (no per-element checks; every
+                // stage but a chunk's last) and partial (elements past the end are 0)
+                auto slice = [&](auto partial) {
 #pragma unroll
-                for (int i = 0; i < 8; i += 2) {
-                    float2 re, im;
-                    gen_pair<MODEL>(pc, make_float2(mf0 + (float)i, mf0 + (float)(i + 1)), re, im);
-                    if (i >= rem) { re.x = 0.f; im.x = 0.f; }
-                    if (i + 1 >= rem) { re.y = 0.f; im.y = 0.f; }
-                    split2<PREC, KMAX == 32>(re.x, re.y, w[0][i >> 1], w[2][i >> 1]);
-                    split2<PREC, KMAX == 32>(im.x, im.y, w[1][i >> 1], w[3][i >> 1]);
-                }
+                    for (int i = 0; i < 8; i += 2) {
+                        float2 re, im;
+                        gen_pair<MODEL>(pc, make_float2(mf0 + (float)i, mf0 + (float)(i + 1)), re, im);
+                        if (decltype(partial)::value) {
+                            if (i >= rem) { re.x = 0.f; im.x = 0.f; }
+                            if (i + 1 >= rem) { re.y = 0.f; im.y = 0.f; }
+                        }
+                        split2<PREC, KMAX == 32>(re.x, re.y, w[0][i >> 1], w[2][i >> 1]);
+                        split2<PREC, KMAX == 32>(im.x, im.y, w[1][i >> 1], w[3][i >> 1]);
+                    }
+                };
+                if (rem >= 8) slice(std::integral_constant<bool, false>());
+                else slice(std::integral_constant<bool, true>());
                 const int ncomp = (PREC == TCP_BF16 && KMAX == 64) ? 2 : 4;  // the one-term K>32 MMA reads hi only
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
