@@ -139,48 +139,13 @@ __device__ double warp0_sum_log2(const double* v, int K, double scale) {
     return acc;
 }
 
-// X = L^{-1} (lower triangular) by right-looking elimination on the identity:
-// for k = 0..K-1 scale row k by 1/L_kk, then subtract L_ik * row k from every
-// row i > k.  Each step updates the (K-k-1) x (k+1) block in parallel.
-__device__ void tri_inverse(const cd* L, cd* X, int K, const double* dinv) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int e = tid; e < K * K; e += nt) X[e] = cmk((e / K) == (e % K) ? 1.0 : 0.0, 0.0);
-    __syncthreads();
-    for (int k = 0; k < K; ++k) {
-        const double iv = dinv[k];
-        for (int j = tid; j <= k; j += nt) X[k * K + j] = cmk(X[k * K + j].x * iv, X[k * K + j].y * iv);
-        __syncthreads();
-        const int rows = K - k - 1, cols = k + 1;
-        for (int e = tid; e < rows * cols; e += nt) {
-            const int i = k + 1 + e / cols, j = e - (e / cols) * cols;
-            X[i * K + j] = cmsub(X[i * K + j], L[i * K + k], X[k * K + j]);
-        }
-        __syncthreads();
-    }
-}
-
-// M = X^H X for lower-triangular X, as the sum of the outer products of the
-// rows of X (row l is nonzero in columns 0..l): balanced element-parallel
-// rank-1 updates.
-__device__ void gram_of_lower(const cd* X, cd* M, int K) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int e = tid; e < K * K; e += nt) M[e] = cmk(0.0, 0.0);
-    __syncthreads();
-    for (int l = 0; l < K; ++l) {
-        const int w = l + 1;
-        for (int e = tid; e < w * w; e += nt) {
-            const int r = e / w, c = e - r * w;
-            M[r * K + c] = cmacc(M[r * K + c], X[l * K + r], X[l * K + c]);  // += conj(X_lr) X_lc
-        }
-        __syncthreads();
-    }
-}
-
-// ---- double-float (FP32 pair) arithmetic for the long dot products --------
-// The mismatched receiver's products M = X^H X and A = M G cancel heavily
-// (A = I + a small remainder), so FP32 is not enough; FP64 on this GPU issues
-// a warp instruction every ~64 cycles per scheduler.  These two products run
-// in double-float on the FP32 pipe instead: a value is hi + lo (|lo| <= half
+// ---- double-float (FP32 pair) arithmetic for the triangular inverse and the
+// receiver products.  The Cholesky factorisation stays FP64; what follows it
+// -- the inverse X = L^{-1}, and for the mismatched receiver M = X^H X and
+// A = M G, which cancel heavily (A = I + a small remainder) -- needs more
+// than FP32, and FP64 on this GPU issues a warp instruction every ~64 cycles
+// per scheduler.  These run in double-float on the FP32 pipe instead
+// (48-bit significand): a value is hi + lo (|lo| <= half
 // an ulp of hi), products by Dekker's exact two-product (FMA residual) with
 // the cross terms hi*lo + lo*hi, sums by Knuth's two-sum on the hi parts with
 // the low-order parts summed alongside (~2^-48 relative over K <= 64 terms).
@@ -223,6 +188,25 @@ __device__ __forceinline__ void cf_mac(float2& s, float2& c, const cf& a, const 
 
 __device__ __forceinline__ cd cf_result(float2 s, float2 c) { return cmk((double)s.x + (double)c.x, (double)s.y + (double)c.y); }
 
+// acc - a b for normalized double-float complex values (one two-product per
+// real term, then renormalized by a fast two-sum).
+__device__ __forceinline__ cf cf_fms(const cf& acc, const cf& a, const cf& b) {
+    float2 s = acc.hi, c = acc.lo;
+    const cf na = {make_float2(-a.hi.x, -a.hi.y), make_float2(-a.lo.x, -a.lo.y)};
+    cf_mac(s, c, na, b, false);
+    const float2 t = __fadd2_rn(s, c);
+    return {t, __fadd2_rn(__fadd2_rn(s, make_float2(-t.x, -t.y)), c)};
+}
+
+// a * v for a double-float complex a and a real FP64 v (as hi + lo).
+__device__ __forceinline__ cf cf_scale(const cf& a, double v) {
+    const float vh = (float)v, vl = (float)(v - (double)vh);
+    float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+    ff2_mac(s, c, a.hi, a.lo, make_float2(vh, vh), make_float2(vl, vl));
+    const float2 t = __fadd2_rn(s, c);
+    return {t, __fadd2_rn(__fadd2_rn(s, make_float2(-t.x, -t.y)), c)};
+}
+
 // In place: a K x K complex FP64 matrix becomes double-float (same bytes).
 __device__ void to_cf_inplace(cd* A, int K) {
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -237,8 +221,8 @@ __device__ void to_cf_inplace(cd* A, int K) {
 // M = X^H X for lower-triangular X (converted to double-float in place):
 // M_rc = sum_{l >= max(r, c)} conj(X_lr) X_lc, upper triangle computed and
 // mirrored, written as FP64.
-__device__ void gram_of_lower_ff(cd* X, cd* M, int K) {
-    to_cf_inplace(X, K);
+__device__ void gram_of_lower_ff(cd* X, cd* M, int K, bool x_is_cf = false) {
+    if (!x_is_cf) to_cf_inplace(X, K);
     const cf* F = reinterpret_cast<const cf*>(X);
     const int tid = threadIdx.x, nt = blockDim.x;
     const int P = K * (K + 1) / 2;
@@ -253,6 +237,32 @@ __device__ void gram_of_lower_ff(cd* X, cd* M, int K) {
         M[c * K + r] = cmk(v.x, -v.y);
     }
     __syncthreads();
+}
+
+// X = L^{-1} (lower triangular) in double-float by right-looking elimination
+// on the identity: for k = 0..K-1 scale row k by 1/L_kk, then subtract L_ik
+// times row k from every row i > k, the (K-k-1) x (k+1) block in parallel.
+// The FP64 factor L is converted in place, X is left in double-float;
+// dinv[k] = 1 / L_kk (FP64).
+__device__ void tri_inverse_ff(cd* L, cd* X, int K, const double* dinv) {
+    to_cf_inplace(L, K);
+    const cf* FL = reinterpret_cast<const cf*>(L);
+    cf* FX = reinterpret_cast<cf*>(X);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < K * K; e += nt)
+        FX[e] = {make_float2((e / K) == (e % K) ? 1.0f : 0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+    __syncthreads();
+    for (int k = 0; k < K; ++k) {
+        const double iv = dinv[k];
+        for (int j = tid; j <= k; j += nt) FX[k * K + j] = cf_scale(FX[k * K + j], iv);
+        __syncthreads();
+        const int rows = K - k - 1, cols = k + 1;
+        for (int e = tid; e < rows * cols; e += nt) {
+            const int i = k + 1 + e / cols, j = e - (e / cols) * cols;
+            FX[i * K + j] = cf_fms(FX[i * K + j], FL[i * K + k], FX[k * K + j]);
+        }
+        __syncthreads();
+    }
 }
 
 // Z = M G, both converted to double-float in place, written as FP64.
@@ -392,17 +402,18 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
                 double lp = warp0_sum_log2(p, K, 1.0 / s2);
                 if (tid == 0) *cap_t = lp + ld;
             }
-            tri_inverse(Z, X, K, dinv);  // X = L^{-1}
+            tri_inverse_ff(Z, X, K, dinv);  // X = L^{-1}, double-float
             if (matched) {
+                const cf* FX = reinterpret_cast<const cf*>(X);
                 for (int k = tid; k < K; k += nt) {
                     double acc = 0.0;
-                    for (int i = k; i < K; ++i) acc += cabs2(X[i * K + k]);
+                    for (int i = k; i < K; ++i) acc += cabs2(from_cf(FX[i * K + k]));
                     dg[k] = acc;
                 }
                 __syncthreads();
             } else {
                 // M = X^H X into Z (the factor is no longer needed), then M back into X
-                gram_of_lower_ff(X, Z, K);
+                gram_of_lower_ff(X, Z, K, true);
                 for (int e = tid; e < KK; e += nt) X[e] = Z[e];
                 __syncthreads();
             }
