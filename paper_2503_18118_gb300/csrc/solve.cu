@@ -218,12 +218,12 @@ __device__ void to_cf_inplace(cd* A, int K) {
     __syncthreads();
 }
 
-// M = X^H X for lower-triangular X (converted to double-float in place):
-// M_rc = sum_{l >= max(r, c)} conj(X_lr) X_lc, upper triangle computed and
-// mirrored, written as FP64.
-__device__ void gram_of_lower_ff(cd* X, cd* M, int K, bool x_is_cf = false) {
-    if (!x_is_cf) to_cf_inplace(X, K);
+// M = X^H X for lower-triangular X (double-float): M_rc = sum_{l >= max(r, c)}
+// conj(X_lr) X_lc, upper triangle computed and mirrored, written in
+// double-float (normalized) into M.
+__device__ void gram_of_lower_ff(const cd* X, cd* M, int K) {
     const cf* F = reinterpret_cast<const cf*>(X);
+    cf* FM = reinterpret_cast<cf*>(M);
     const int tid = threadIdx.x, nt = blockDim.x;
     const int P = K * (K + 1) / 2;
     for (int q = tid; q < P; q += nt) {
@@ -232,9 +232,10 @@ __device__ void gram_of_lower_ff(cd* X, cd* M, int K, bool x_is_cf = false) {
         const int c = r + w;  // r <= c
         float2 s = make_float2(0.f, 0.f), cc = make_float2(0.f, 0.f);
         for (int l = c; l < K; ++l) cf_mac(s, cc, F[l * K + r], F[l * K + c], true);
-        const cd v = cf_result(s, cc);
-        M[r * K + c] = v;
-        M[c * K + r] = cmk(v.x, -v.y);
+        const float2 t = __fadd2_rn(s, cc);
+        const float2 lo = __fadd2_rn(__fadd2_rn(s, make_float2(-t.x, -t.y)), cc);
+        FM[r * K + c] = {t, lo};
+        FM[c * K + r] = {make_float2(t.x, -t.y), make_float2(lo.x, -lo.y)};
     }
     __syncthreads();
 }
@@ -242,10 +243,21 @@ __device__ void gram_of_lower_ff(cd* X, cd* M, int K, bool x_is_cf = false) {
 // X = L^{-1} (lower triangular) in double-float by right-looking elimination
 // on the identity: for k = 0..K-1 scale row k by 1/L_kk, then subtract L_ik
 // times row k from every row i > k, the (K-k-1) x (k+1) block in parallel.
-// The FP64 factor L is converted in place, X is left in double-float;
-// dinv[k] = 1 / L_kk (FP64).
+// The strictly lower triangle of the FP64 factor L is converted in place (the
+// only part read), X is left in double-float; dinv[k] = 1 / L_kk (FP64).
 __device__ void tri_inverse_ff(cd* L, cd* X, int K, const double* dinv) {
-    to_cf_inplace(L, K);
+    {
+        cf* F = reinterpret_cast<cf*>(L);
+        const int P = K * (K - 1) / 2;
+        for (int q = threadIdx.x; q < P; q += blockDim.x) {
+            int r = 1, w = q;
+            while (w >= r) { w -= r; ++r; }
+            const int e = r * K + w;  // row r > column w
+            const cf v = to_cf(L[e]);
+            F[e] = v;
+        }
+        __syncthreads();
+    }
     const cf* FL = reinterpret_cast<const cf*>(L);
     cf* FX = reinterpret_cast<cf*>(X);
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -265,9 +277,10 @@ __device__ void tri_inverse_ff(cd* L, cd* X, int K, const double* dinv) {
     }
 }
 
-// Z = M G, both converted to double-float in place, written as FP64.
-__device__ void prod_ff(cd* Mx, cd* G, cd* Z, int K) {
-    to_cf_inplace(Mx, K);
+// Z = M G with M already in double-float (mcf) or FP64 (converted in place),
+// G converted in place; Z written as FP64.
+__device__ void prod_ff(cd* Mx, bool mcf, cd* G, cd* Z, int K) {
+    if (!mcf) to_cf_inplace(Mx, K);
     to_cf_inplace(G, K);
     const cf* FM = reinterpret_cast<const cf*>(Mx);
     const cf* FG = reinterpret_cast<const cf*>(G);
@@ -353,6 +366,7 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
     __shared__ double dinv[XLMIMO_MAX_USERS], pivd[XLMIMO_MAX_USERS], sp[XLMIMO_MAX_USERS];
     __shared__ int flag, piv, st;
     const int tid = threadIdx.x, nt = blockDim.x;
+    bool m_is_cf = false;  // X holds M in double-float (else FP64)
     if (tid == 0) { flag = 0; st = 0; }
     for (int k = tid; k < K; k += nt) {
         double v = pw[k];
@@ -404,18 +418,23 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
             }
             tri_inverse_ff(Z, X, K, dinv);  // X = L^{-1}, double-float
             if (matched) {
+                // dg_k = sum_{i >= k} |X_ik|^2 in double-float, one conversion per k
                 const cf* FX = reinterpret_cast<const cf*>(X);
                 for (int k = tid; k < K; k += nt) {
-                    double acc = 0.0;
-                    for (int i = k; i < K; ++i) acc += cabs2(from_cf(FX[i * K + k]));
-                    dg[k] = acc;
+                    float2 s2a = make_float2(0.f, 0.f), c2a = make_float2(0.f, 0.f);
+                    for (int i = k; i < K; ++i) {
+                        const cf x = FX[i * K + k];
+                        ff2_mac(s2a, c2a, x.hi, x.lo, x.hi, x.lo);  // (re^2, im^2)
+                    }
+                    dg[k] = ((double)s2a.x + (double)c2a.x) + ((double)s2a.y + (double)c2a.y);
                 }
                 __syncthreads();
             } else {
-                // M = X^H X into Z (the factor is no longer needed), then M back into X
-                gram_of_lower_ff(X, Z, K, true);
+                // M = X^H X (double-float) into Z (the factor is no longer needed), then back into X
+                gram_of_lower_ff(X, Z, K);
                 for (int e = tid; e < KK; e += nt) X[e] = Z[e];
                 __syncthreads();
+                m_is_cf = true;
             }
         } else {
             // not positive definite: Gauss-Jordan on a fresh copy
@@ -479,7 +498,7 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
         }
     } else {
         // A = M G (M in X) into Z in double-float; X and G are left in double-float
-        prod_ff(X, G, Z, K);
+        prod_ff(X, m_is_cf, G, Z, K);
         const cf* FM = reinterpret_cast<const cf*>(X);
         for (int k = tid; k < K; k += nt) {
             double sig = p[k] * cabs2(Z[k * K + k]);
