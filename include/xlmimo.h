@@ -393,9 +393,8 @@ int xlmimo_batch_plan_destroy(xlmimo_batch_plan plan);
  * accumulation.  Gradients pass through the rounding unchanged.  Inference
  * runs every layer but the last on the tensor cores (the first with a BF16
  * hi/lo split of features and weights, which keeps it to ~2^-16 of FP32) and
- * evaluates SiLU as z/2 (1 + tanh(z/2)) with the hardware tanh approximation:
- * packed FP16 for the activations that are rounded to BF16 next, FP32 for the
- * last hidden layer. */
+ * evaluates SiLU as z/2 (1 + tanh(z/2)) with the FP32 hardware tanh
+ * approximation (relative error ~2^-11, below the BF16 rounding that follows). */
 #define XLMIMO_MLP_IN 6
 #define XLMIMO_MLP_WIDTH 256
 #define XLMIMO_MLP_HIDDEN 4

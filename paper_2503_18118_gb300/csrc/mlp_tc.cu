@@ -38,10 +38,10 @@
 //          and issues tcgen05.mma (M = N = 128, K = 16) half by half, every
 //          tile per weight tile, committing each half separately so half 0's
 //          epilogue runs while half 1 multiplies.
-// The last hidden layer's SiLU feeds the FP32 output layer directly and uses
-// the FP32 tanh (relative error ~2^-11); measured against the FP32 SIMT
-// forward pass, the exact form there (exp and divide, two MUFU ops) changed
-// neither the output error nor the sum rate, and cost 12 % of the kernel.
+// SiLU uses the FP32 tanh (relative error ~2^-11) in every layer; in the last
+// hidden layer, which feeds the FP32 output layer directly, the exact form
+// (exp and divide, two MUFU ops) was measured to change neither the output
+// error nor the sum rate, and cost 12 % of the kernel.
 // Ordering: a layer's MMAs start once every row thread has written A and read
 // the accumulator (one arrival each); half 0 overwrites its A columns only
 // after half 1's MMAs have read them (a separate commit after half 1's first
@@ -65,21 +65,22 @@ constexpr int MI_F32_BYTES = (MLP_PK_NF * 4 + 15) / 16 * 16;
 // NT row tiles in flight per CTA.  NT = 1: two CTAs per SM, a two-stage
 // weight ring each.  NT = 2: one CTA per SM whose two tiles take every weight
 // tile in turn (half the L2 bytes per row) from a five-stage ring.
-template <int NT>
+template <int NT, int CPS>
 struct MiCfg {
     static constexpr int ROW_WARPS = 8 * NT;
     static constexpr int LOADER = ROW_WARPS, MMA = ROW_WARPS + 1;
     static constexpr int THREADS = 32 * (ROW_WARPS + 2);
     static constexpr int ROW_THREADS = 32 * ROW_WARPS;
-    static constexpr int CTAS_PER_SM = NT == 1 ? 2 : 1;
-    static constexpr int STAGES = NT == 1 ? 2 : 5;
+    static constexpr int CTAS_PER_SM = CPS;
+    // ring depth: what the shared memory left by NT A tiles and CPS CTAs holds
+    static constexpr int STAGES = NT == 2 ? 5 : (CPS == 2 ? 2 : 9);
     static constexpr uint32_t TMEM_COLS = 256 * NT;
 };
 
-template <int NT>
+template <int NT, int CPS>
 struct MiShared {
-    uint64_t full[MiCfg<NT>::STAGES];
-    uint64_t empty[MiCfg<NT>::STAGES];
+    uint64_t full[MiCfg<NT, CPS>::STAGES];
+    uint64_t empty[MiCfg<NT, CPS>::STAGES];
     uint64_t a_ready;    // one arrival per row thread: A tiles written, accumulators read
     uint64_t d_ready[2]; // commit: output half h of the layer complete (every tile)
     uint64_t a_free;     // commit: half 1 has read A columns 0-127 (every tile)
@@ -89,9 +90,10 @@ struct MiShared {
     float2 red[NT][MI_ROWS]; // half 1's share of the output layer
 };
 
-template <int NT>
+template <int NT, int CPS>
 constexpr int mi_smem() {
-    return 1024 + NT * MI_A_BYTES + MiCfg<NT>::STAGES * MLP_TILE_BYTES + MI_F32_BYTES + (int)sizeof(MiShared<NT>);
+    return 1024 + NT * MI_A_BYTES + MiCfg<NT, CPS>::STAGES * MLP_TILE_BYTES + MI_F32_BYTES +
+           (int)sizeof(MiShared<NT, CPS>);
 }
 
 // Copy into this CTA's shared memory, completing bytes on `bar` (armed separately).
@@ -163,24 +165,17 @@ __device__ __forceinline__ float tanh_f32(float x) {
     return y;
 }
 
-__device__ __forceinline__ uint32_t tanh_f16x2(uint32_t x) {
-    uint32_t y;
-    asm("tanh.approx.f16x2 %0, %1;" : "=r"(y) : "r"(x));
-    return y;
-}
 
 __device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
     __nv_bfloat162 p = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&p);
 }
 
-// silu(z) of two accumulators holding z/2 (bias added here), as BF16x2: the
-// tanh in packed FP16 (one MUFU op for both), the rest in FP32.
+// silu(z) of two accumulators holding z/2 (bias added here), as BF16x2: FP32
+// tanh (measured faster than the packed-FP16 tanh, whose float/half
+// conversions cost more than the MUFU op they save, and more accurate).
 __device__ __forceinline__ uint32_t silu_pair_bf16(float2 hz) {
-    __half2 hh = __floats2half2_rn(hz.x, hz.y);
-    const uint32_t th = tanh_f16x2(*reinterpret_cast<uint32_t*>(&hh));
-    const float2 t = __half22float2(*reinterpret_cast<const __half2*>(&th));
-    const float2 h = __ffma2_rn(hz, t, hz);
+    const float2 h = __ffma2_rn(hz, make_float2(tanh_f32(hz.x), tanh_f32(hz.y)), hz);
     return bf16x2_bits(h.x, h.y);
 }
 
@@ -259,18 +254,19 @@ __device__ __forceinline__ RowIn fetch_row(int64_t r, int64_t rows, int K, int P
 // the same count in every CTA so that a cluster shares one weight stream;
 // tiles past the end have no valid rows).
 // HB: the Gram holds a base G~ F below the diagonal (else the base is G~).
-template <int CL, int NT, bool HB>
-__global__ void __launch_bounds__(MiCfg<NT>::THREADS, MiCfg<NT>::CTAS_PER_SM)
+template <int CL, int NT, bool HB, int CPS>
+__global__ void __launch_bounds__(MiCfg<NT, CPS>::THREADS, CPS)
     mlp_infer_tc_kernel(FeatConst fc, const double2* __restrict__ users, int K, int64_t rows, int n_iter,
                         const unsigned char* __restrict__ packed, double2* __restrict__ gram) {
-    using C = MiCfg<NT>;
+    using C = MiCfg<NT, CPS>;
     constexpr int MI_STAGES = C::STAGES;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     unsigned char* A0 = base;  // tile t's A at A0 + t MI_A_BYTES
     unsigned char* ring = A0 + NT * MI_A_BYTES;
     float* pf = reinterpret_cast<float*>(ring + MI_STAGES * MLP_TILE_BYTES);
-    MiShared<NT>* sh = reinterpret_cast<MiShared<NT>*>(reinterpret_cast<unsigned char*>(pf) + MI_F32_BYTES);
+    MiShared<NT, CPS>* sh =
+        reinterpret_cast<MiShared<NT, CPS>*>(reinterpret_cast<unsigned char*>(pf) + MI_F32_BYTES);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int P = K * (K - 1) / 2;
@@ -516,17 +512,17 @@ static int mlp_infer_cluster() {
     return cl;
 }
 
-template <int CL, int NT, bool HB>
+template <int CL, int NT, bool HB, int CPS>
 static int mlp_infer_launch(const FeatConst& fc, const double* users, int K, int64_t rows, const void* packed,
                             double* gram, cudaStream_t st) {
-    using C = MiCfg<NT>;
-    constexpr int smem = mi_smem<NT>();
+    using C = MiCfg<NT, CPS>;
+    constexpr int smem = mi_smem<NT, CPS>();
     static bool done[64] = {false};
     int dev = 0;
     int rc = cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
     if (rc) return rc;
     if (dev >= 64 || !done[dev]) {
-        rc = cuda_status(cudaFuncSetAttribute(mlp_infer_tc_kernel<CL, NT, HB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+        rc = cuda_status(cudaFuncSetAttribute(mlp_infer_tc_kernel<CL, NT, HB, CPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                          "surrogate kernel attribute");
         if (rc) return rc;
         if (dev < 64) done[dev] = true;
@@ -549,20 +545,21 @@ static int mlp_infer_launch(const FeatConst& fc, const double* users, int K, int
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cuda_status(cudaLaunchKernelEx(&cfg, mlp_infer_tc_kernel<CL, NT, HB>, fc, (const double2*)users, K, rows,
+    return cuda_status(cudaLaunchKernelEx(&cfg, mlp_infer_tc_kernel<CL, NT, HB, CPS>, fc, (const double2*)users, K, rows,
                                           (int)n_iter, (const unsigned char*)packed, (double2*)gram),
                        "surrogate kernel launch");
 }
 
-// Row tiles per CTA: 1 (measured faster than 2 in lockstep) unless
-// XLMIMO_SURROGATE_TILES (1 or 2) says otherwise.
+// Configuration: 1 = one tile per CTA, two CTAs per SM (default); 2 = two
+// lockstep tiles per CTA; 3 = one tile per CTA, one CTA per SM with a deep
+// weight ring.  XLMIMO_SURROGATE_TILES (1, 2 or 3) overrides; read once.
 static int mlp_infer_tiles() {
     static int nt = 0;
     if (!nt) {
         int v = 1;
         if (const char* e = getenv("XLMIMO_SURROGATE_TILES")) {
             const int x = atoi(e);
-            if (x == 1 || x == 2) v = x;
+            if (x >= 1 && x <= 3) v = x;
         }
         nt = v;
     }
@@ -592,13 +589,18 @@ extern "C" int xlmimo_surrogate_gram(const xlmimo_array* arr, const double* user
     if ((rc = launch_aperture_base(g, base, users, K, B, gram, st))) return rc;
     const int64_t rows = (int64_t)B * (K * (K - 1) / 2);
     const FeatConst fc = make_feat_const(g);
-    const bool two = mlp_infer_tiles() == 2, hb = base != XLMIMO_APERTURE_NONE;
-#define XL_MI(CL_, NT_) (hb ? mlp_infer_launch<CL_, NT_, true>(fc, users, K, rows, packed, gram, st) \
-                            : mlp_infer_launch<CL_, NT_, false>(fc, users, K, rows, packed, gram, st))
+    const int nt = mlp_infer_tiles(), hb_ = base != XLMIMO_APERTURE_NONE;
+    const bool hb = hb_;
+    // (tiles per CTA, CTAs per SM): (1, 2) two CTAs with a 2-stage ring each,
+    // (2, 1) two lockstep tiles with a 5-stage ring, (1, 1) one tile with a 9-stage ring
+#define XL_MI1(CL_, NT_, CPS_) (hb ? mlp_infer_launch<CL_, NT_, true, CPS_>(fc, users, K, rows, packed, gram, st) \
+                                   : mlp_infer_launch<CL_, NT_, false, CPS_>(fc, users, K, rows, packed, gram, st))
+#define XL_MI(CL_) (nt == 2 ? XL_MI1(CL_, 2, 1) : nt == 3 ? XL_MI1(CL_, 1, 1) : XL_MI1(CL_, 1, 2))
     switch (mlp_infer_cluster()) {
-        case 2: return two ? XL_MI(2, 2) : XL_MI(2, 1);
-        case 4: return two ? XL_MI(4, 2) : XL_MI(4, 1);
-        default: return two ? XL_MI(1, 2) : XL_MI(1, 1);
+        case 2: return XL_MI(2);
+        case 4: return XL_MI(4);
+        default: return XL_MI(1);
     }
+#undef XL_MI1
 #undef XL_MI
 }

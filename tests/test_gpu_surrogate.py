@@ -7,12 +7,12 @@ can round an activation to the neighbouring BF16 value, which moves a
 downstream pre-activation by about 2^-8 |h w|.  Such flips are rare (a few
 per thousand activations), so the tests bound the typical error tightly
 (90th percentile, FP32 level) and the worst case at a few BF16 ulps of the
-layer scale.  Inference adds the hardware tanh in SiLU (packed FP16 for the
-activations that are rounded to BF16 next: relative error ~2^-10, which moves
-roughly a quarter of those activations by one BF16 ulp relative to the
-oracle's exact SiLU).  Three rounded layers then carry output errors of a few
-2^-8 of the output scale, before the network's own gain; the inference test
-bounds the median at 4e-3 and the worst pair at 2e-2 of the output scale."""
+layer scale.  Inference adds the FP32 hardware tanh in SiLU (relative error
+~2^-11, which moves roughly an eighth of the BF16-rounded activations by one
+BF16 ulp relative to the oracle's exact SiLU).  Three rounded layers then
+carry output errors of a few 2^-8 of the output scale, before the network's
+own gain; the inference test bounds the median at 4e-3 and the worst pair at
+2e-2 of the output scale."""
 import math
 
 import numpy as np
