@@ -383,6 +383,7 @@ def main():
 
     import torch
     import torch.distributed as dist
+    from paper_2503_18118_gb300 import mc
     from paper_2503_18118_gb300 import xlmimo as xl
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -398,7 +399,7 @@ def main():
 
     B, K, N = wl.trials, wl.k, wl.n_ant
     # weak scaling: rank r takes its own block of trials (different seed stream)
-    users_h = inputs.users_polar(wl.seed + 1000 * rank, B, K, wl.r_range, wl.theta_deg)
+    users_h = inputs.users_polar(mc.rank_seed(wl.seed, rank), B, K, wl.r_range, wl.theta_deg)
     arr = xl.array(N, wl.wavelength, wl.spacing, 1.0, wl.model)
     stream = torch.cuda.current_stream()
     U = torch.from_numpy(users_h).cuda()
@@ -453,14 +454,11 @@ def main():
             gram_only(gram_prec, gev[i])
         torch.cuda.synchronize()
         gram_ms = sum(e[0].elapsed_time(e[1]) for e in gev) / steps
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item()), gram_ms, clocks
+        return mc.max_over_ranks(total_ms, dist if world > 1 else None, "cuda"), gram_ms, clocks
 
     total_ms, gram_ms, clocks = timed(prec, args.steps, args.warmup, sample_clocks=(rank == 0))
     ms_per_step = total_ms / args.steps
-    value = world * B * args.steps / (total_ms / 1e3)
+    value = mc.throughput(world, B, args.steps, total_ms)
 
     # plain FP64 GPU path (the metric's baseline), same pipeline, fewer steps
     fp64 = None
@@ -489,10 +487,7 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * B / (float(te.item()) / 1e3)
+    e2e_value = mc.throughput(world, B, 1, mc.max_over_ranks(e2e_ms, dist if world > 1 else None, "cuda"))
 
     if rank != 0:
         if world > 1:
