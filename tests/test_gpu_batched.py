@@ -28,6 +28,23 @@ def normwise(G, Gref):
     return float(np.max(np.abs(G - Gref) / (d[..., :, None] * d[..., None, :])))
 
 
+def sinr_rate_close(s, rate, s_ref, R, delta, snr, noise, scheme):
+    """GPU SINR and rate (from the GPU Gram) against the oracle's (from the
+    oracle Gram).  The receivers are parity-tested on identical input
+    elsewhere; here the Gram matrices differ by the measured normwise delta,
+    which moves the diagonal of the inverse of the receiver matrix A (R for ZF,
+    R + sigma^2 diag(p)^-1 for MMSE) by at most ~K cond(A) delta relative, and
+    the SINR by that times (1 + 1/SINR)."""
+    K = R.shape[0]
+    p = snr * noise / np.real(np.diag(R))
+    A = R + (np.diag(noise / p) if scheme == 1 else 0)
+    amp = 2.0 * K * np.linalg.cond(A) * delta * (1.0 + 1.0 / np.min(s_ref))
+    tol = amp + 1e-9
+    ok_s = np.max(np.abs(s - s_ref) / np.abs(s_ref)) <= tol
+    r_ref = np.log2(1 + s_ref).sum()
+    return ok_s and abs(rate - r_ref) <= tol * abs(r_ref)
+
+
 def make_batch(seed, count, n_range=(256, 40000), k_range=(1, 64)):
     g = np.random.Generator(np.random.Philox(key=seed))
     n = np.rint(np.exp(g.uniform(np.log(n_range[0]), np.log(n_range[1]), count))).astype(np.int64)
@@ -59,20 +76,21 @@ def test_batch_matches_oracle(xl, orc, prec, gtol):
     info = plan.info()
     assert info["items"] >= len(n) and info["small"] + info["large"] == len(n)
     out = run_plan(xl, plan, users, snr)
+    compared = 0
     for i in range(len(n)):
         K, uo, go = int(k[i]), int(plan.user_off[i]), int(plan.gram_off[i])
         u = users[uo:uo + K][None]
         G = out["gram"][go:go + K * K].reshape(1, K, K)
         R = orc.gram(orc.FSPL, int(n[i]), LAM, LAM / 2, 1.0, u)
-        assert normwise(G, R) <= gtol, i
-        # receiver and rate on the same (GPU) Gram: FP64 solves on both sides,
-        # agreeing to the FP64 rounding amplified by the Gram's conditioning
-        s_ref, st_ref, _ = orc.beamform(G, snr[uo:uo + K][None], noise[i:i + 1], int(scheme[i]), orc.POWER_RXSNR)
-        s = out["sinr"][uo:uo + K]
-        tol = max(1e-9, 1e-14 * np.linalg.cond(G[0]))
-        if st_ref[0] == 0:
-            assert np.max(np.abs(s - s_ref[0]) / np.abs(s_ref[0])) <= tol, i
-            assert abs(out["rate"][i] - np.log2(1 + s_ref[0]).sum()) <= tol * abs(out["rate"][i]), i
+        delta = normwise(G, R)
+        assert delta <= gtol, i
+        s_ref, st_ref, _ = orc.beamform(R, snr[uo:uo + K][None], noise[i:i + 1], int(scheme[i]), orc.POWER_RXSNR)
+        if st_ref[0] != 0:
+            continue
+        assert sinr_rate_close(out["sinr"][uo:uo + K], out["rate"][i], s_ref[0], R[0], delta, snr[uo:uo + K],
+                               noise[i], int(scheme[i])), i
+        compared += 1
+    assert compared >= len(n) // 2
 
 
 def test_batch_split_instances(xl, orc):
@@ -127,3 +145,34 @@ def test_batch_graph_capture_and_autotune(xl):
         torch.cuda.synchronize()
         for kk in ref:
             assert torch.equal(out[kk], ref[kk]), kk
+
+
+def test_ragged_bench_batch_sampled(xl, orc):
+    """The benchmark's ragged batch at full size (2^14 instances, N =
+    round(2^U[10,17]), K ~ U{2..64}, ZF/MMSE, SNR ~ U[0,30] dB, 100 GHz) in the
+    launch configuration the bench times (autotuned plan); the oracle checks
+    sampled instances (the smallest, a median and the largest work) and
+    properties hold for all."""
+    count = 1 << 14
+    n, k, scheme, snr_db = inputs.ragged_instances(4, count)
+    users = inputs.users_polar(4, 1, int(k.sum()), (3.0, 30.0))[0]
+    snr = np.repeat(inputs.db_to_lin(snr_db), k)
+    U = torch.from_numpy(users).cuda()
+    plan = xl.BatchPlan(xl.array(1, LAM), n, k, scheme, np.ones(count), prec=3, tune_users=U)
+    out = run_plan(xl, plan, users, snr)
+    assert np.isfinite(out["gram"]).all() and np.isfinite(out["rate"]).all()
+    assert (out["status"] == 0).mean() > 0.99
+    work = n * k * k
+    order = np.argsort(work)
+    idx = [int(order[0]), int(order[1]), int(order[count // 2]), int(order[-1])]
+    for i in idx:
+        K, uo, go = int(k[i]), int(plan.user_off[i]), int(plan.gram_off[i])
+        G = out["gram"][go:go + K * K].reshape(1, K, K)
+        R = orc.gram(orc.FSPL, int(n[i]), LAM, LAM / 2, 1.0, users[uo:uo + K][None])
+        delta = normwise(G, R)
+        assert delta <= 2e-4, (i, delta)
+        s_ref, st_ref, _ = orc.beamform(R, snr[uo:uo + K][None], np.ones(1), int(scheme[i]), orc.POWER_RXSNR)
+        if st_ref[0] == 0:
+            assert sinr_rate_close(out["sinr"][uo:uo + K], out["rate"][i], s_ref[0], R[0], delta, snr[uo:uo + K],
+                                   1.0, int(scheme[i])), i
+    plan.close()

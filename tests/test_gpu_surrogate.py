@@ -209,6 +209,38 @@ def test_pair_targets_and_constant_network_with_aperture_base(orc, base):
     assert np.all(np.abs(gs[:, iu[0], iu[1]] - w) <= 3e-5 * np.abs(Gc[:, iu[0], iu[1]]))
 
 
+def test_surrogate_full_size_sampled(orc):
+    """The benchmark's surrogate workload at full size (10^4 trials, K = 64, N =
+    2^18, 100 GHz, Fresnel base) in the configuration the bench times; the
+    oracle network on the oracle closed form checks sampled trials."""
+    from oracle import aperture as ap
+    wl = inputs.SURROGATE
+    users = wl.users()
+    B, K, n, lam = wl.trials, wl.k, wl.n_ant, wl.wavelength
+    p = params_np(91, 1.5)
+    arr = X.array(n, lam)
+    gs = X.xlmimo_surrogate_gram(arr, dev(users), X.xlmimo_mlp_pack(dev(p)), base=X.APERTURE_FRESNEL)
+    gh = gs.cpu().numpy()
+    assert np.isfinite(gh).all()
+    assert np.array_equal(gh, np.conj(np.transpose(gh, (0, 2, 1))))
+    idx = np.array([0, 1, B // 2, B - 1])
+    u = users[idx]
+    Gc = orc.closed_form(orc.FSPL, n, lam, lam / 2, 1.0, u)
+    F = ap.factors(ap.FRESNEL, u, n, lam, lam / 2)
+    tr, _ = mlp.forward(mlp.unflatten(p), mlp.pair_features(u, n, lam, lam / 2), qlayers=Q)
+    want = ap.apply(Gc, F + tr[:, 0] + 1j * tr[:, 1])
+    iu = np.triu_indices(K, 1)
+    c = np.abs(Gc[:, iu[0], iu[1]])
+    err = np.abs(gh[idx][:, iu[0], iu[1]] - want[:, iu[0], iu[1]]) / c
+    # pairs whose Fresnel cut sits within rounding of |u| = 2 may take either side
+    from test_gpu_aperture import borderline
+    keep = ~borderline(u, n, lam).reshape(len(idx), -1)
+    assert keep.mean() > 0.99
+    scale = max(1.0, float(np.abs(tr).max()))
+    assert np.quantile(err[keep], 0.5) <= 4e-3 * scale
+    assert err[keep].max() <= 2e-2 * scale
+
+
 def test_surrogate_empty_and_single_user():
     arr = X.array(1024, 0.01)
     packed = X.xlmimo_mlp_pack(dev(np.zeros(X.MLP_PARAMS, np.float32)))
