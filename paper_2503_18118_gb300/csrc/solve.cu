@@ -77,63 +77,130 @@ __device__ __forceinline__ void tri_index(int q, int* r, int* c) {
     *c = q - rr * (rr + 1) / 2;
 }
 
-// 1/sqrt(d) for d > 0 in FP64: FP32 seed and two Newton steps (the FP64 pipe
-// runs one warp instruction per ~64 cycles per scheduler whatever the active
-// lanes, so single-lane sqrt/divide sequences are kept short).
-__device__ __forceinline__ double rsqrt_f64(double d) {
-    if (d < 1e-30 || d > 1e30) return 1.0 / sqrt(d);  // outside the FP32 seed's range
-    double y = (double)rsqrtf((float)d);
-    y = y * fma(-0.5 * d, y * y, 1.5);
-    y = y * fma(-0.5 * d, y * y, 1.5);
-    return y;
+// Split of an FP64 value into two floats, hi + lo = d to ~2^-48 relative,
+// with integer and FP32 instructions only (FP64 <-> FP32 conversions occupy
+// the FP64 pipe): hi is d truncated to 24 significant bits (sign, rebiased
+// exponent, top 23 stored mantissa bits); the remaining 29 mantissa bits m
+// give lo = RN(m) 2^(e - 1075), RN(m) formed exactly from m's low 23 and high
+// 6 bits (2^23 + a is exact in FP32) by one FMA.  Values whose hi or lo would
+// leave the normal FP32 range (zero, |d| < 2^-74, |d| >= 2^128, inf, NaN)
+// take the FP64 conversion.
+__device__ __forceinline__ void split_f64(double d, float& hi, float& lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const uint32_t bh = (uint32_t)(b >> 32), bl = (uint32_t)b;
+    const uint32_t e = (bh >> 20) & 0x7FFu;  // biased exponent
+    if (e - 949u <= 1150u - 949u) {
+        const uint32_t sg = bh & 0x80000000u;
+        hi = __uint_as_float(sg | ((e - 896u) << 23) | ((bh & 0xFFFFFu) << 3) | (bl >> 29));
+        const uint32_t m = bl & 0x1FFFFFFFu;
+        const float fa = __fsub_rn(__uint_as_float(0x4B000000u | (m & 0x7FFFFFu)), 8388608.0f);
+        const float fb = __fsub_rn(__uint_as_float(0x4B000000u | (m >> 23)), 8388608.0f);
+        const float l = __fmul_rn(__fmaf_rn(fb, 8388608.0f, fa), __uint_as_float((e - 948u) << 23));
+        lo = __uint_as_float(__float_as_uint(l) | sg);
+    } else {
+        hi = (float)d;
+        lo = (float)(d - (double)hi);
+    }
 }
 
-// In-place lower Cholesky of the Hermitian K x K matrix A (row-major, lower
-// triangle used).  Returns 1 on success; dinv[k] = 1 / L_kk and piv[k] = L_kk^2
-// (for the log-determinant, summed lane-parallel by the caller).  Per column:
-// pivot, column scale, trailing update of the lower triangle.
-__device__ int chol_lower(cd* A, int K, int* flag, double* dinv, double* pivd) {
+// Pivot of the Cholesky factorisation: y = 1/sqrt(d) in FP64 with five FP64
+// instructions.  The FP32 seed comes from d's high mantissa bits and goes back
+// to FP64 exactly, both by integer operations; one third-order step
+//   y = y0 (1 + r/2 + 3 r^2/8),  r = 1 - d y0^2  (y0^2 exact in FP64)
+// leaves a truncation error (5/16) r^3 ~ 2^-64, below FP64 rounding (the FP64
+// pipe issues one warp instruction per ~64 cycles per scheduler whatever the
+// active lanes, so the single-lane pivot chain is kept short).  Returns false
+// unless d is a positive finite number.
+__device__ __forceinline__ bool rsqrt_pivot(double d, double& y) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const uint32_t bh = (uint32_t)(b >> 32), bl = (uint32_t)b;
+    const uint32_t e = bh >> 20;  // sign and biased exponent: negative d lands above 2047
+    if (e - 923u <= 1122u - 923u) {  // 2^-100 <= d < 2^100
+        const float sf = __uint_as_float(((e - 896u) << 23) | ((bh & 0xFFFFFu) << 3) | (bl >> 29));
+        const uint32_t yb = __float_as_uint(rsqrtf(sf));
+        const double y0 = __hiloint2double((int)((((yb >> 23) + 896u) << 20) | ((yb & 0x7FFFFFu) >> 3)),
+                                           (int)((yb & 7u) << 29));
+        const double r = fma(-d, y0 * y0, 1.0);
+        y = fma(y0 * r, fma(r, 0.375, 0.5), y0);
+        return true;
+    }
+    if (!(d > 0.0) || !isfinite(d)) return false;
+    y = 1.0 / sqrt(d);
+    return true;
+}
+
+// Pivot and scale of column k of chol_lower, by warp 0 (every lane forms the
+// same pivot; lane 0 publishes it).  Returns false when the pivot is not a
+// positive finite number.
+__device__ __forceinline__ bool chol_pivot(cd* Lk, int k, int K, int lane, float2* dinvf, double* pivd) {
+    const double d = Lk[k].x;
+    double y = 0.0;
+    const bool ok = rsqrt_pivot(d, y);
+    if (ok) {
+        for (int i = k + 1 + lane; i < K; i += 32) Lk[i] = cmk(Lk[i].x * y, Lk[i].y * y);
+    }
+    __syncwarp();  // every lane has read the pivot before lane 0 replaces it
+    if (lane == 0 && ok) {
+        Lk[k] = cmk(d * y, 0.0);
+        float yh, yl;
+        split_f64(y, yh, yl);
+        dinvf[k] = make_float2(yh, yl);
+        pivd[k] = d;
+    }
+    return ok;
+}
+
+// In-place lower Cholesky of a Hermitian K x K matrix whose lower triangle
+// is stored column by column: T[j K + i] = A_ij for i >= j, so that the
+// column being scaled and the trailing entries that a warp updates together
+// are contiguous in shared memory (a row-major walk down a column hits one
+// bank group 32 times).  Returns 1 on success; T then holds L the same way,
+// dinvf[k] = 1 / L_kk as a float pair (hi, lo) and piv[k] = L_kk^2 (for the
+// log-determinant, summed lane-parallel by the caller).
+// One CTA barrier per column, by look-ahead: while the other warps apply
+// column k to the trailing columns k+2.., warp 0 applies it to column k+1
+// alone and goes on to that column's pivot and scaling.  The trailing
+// triangle is taken from its last column backwards so that consecutive lanes
+// walk down one column.  Needs blockDim.x > 32.
+__device__ int chol_lower(cd* T, int K, int* flag, float2* dinvf, double* pivd) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int k = 0; k < K; ++k) {
-        if (tid == 0) {
-            double d = A[k * K + k].x;
-            if (!(d > 0.0) || !isfinite(d)) {
-                *flag = 1;
-            } else {
-                double y = rsqrt_f64(d);
-                A[k * K + k] = cmk(d * y, 0.0);
-                dinv[k] = y;
-                pivd[k] = d;
-            }
-        }
-        __syncthreads();
-        const int failed = *flag;
-        if (failed) {
+    if (tid < 32 && !chol_pivot(T, 0, K, tid, dinvf, pivd) && tid == 0) *flag = 1;
+    __syncthreads();
+    for (int k = 0;; ++k) {
+        if (*flag) {
             __syncthreads();  // every thread has read the flag before anyone may reset it
             return 0;
         }
-        const double iv = dinv[k];
-        for (int i = k + 1 + tid; i < K; i += nt) A[i * K + k] = cmk(A[i * K + k].x * iv, A[i * K + k].y * iv);
-        __syncthreads();
-        const int m = K - k - 1;
-        const int tri = m * (m + 1) / 2;
-        for (int q = tid; q < tri; q += nt) {
-            int r, c;
-            tri_index(q, &r, &c);
-            const int i = k + 1 + r, j = k + 1 + c;
-            A[i * K + j] = cmsubc(A[i * K + j], A[i * K + k], A[j * K + k]);  // -= L_ik conj(L_jk)
+        if (k == K - 1) return 1;
+        const cd* Lk = T + k * K;
+        if (tid < 32) {
+            cd* L1 = T + (k + 1) * K;
+            const cd l1 = Lk[k + 1];
+            for (int i = k + 1 + tid; i < K; i += 32) L1[i] = cmsubc(L1[i], Lk[i], l1);  // A_i,k+1 -= L_ik conj(L_k+1,k)
+            __syncwarp();
+            if (!chol_pivot(L1, k + 1, K, tid, dinvf, pivd) && tid == 0) *flag = 1;
+        } else {
+            const int m = K - k - 2;
+            const int tri = m * (m + 1) / 2;
+            for (int q = tid - 32; q < tri; q += nt - 32) {
+                int cr, s;
+                tri_index(q, &cr, &s);  // column m-1-cr of the block, entry s down from its diagonal
+                const int j = K - 1 - cr, i = j + s;
+                T[j * K + i] = cmsubc(T[j * K + i], Lk[i], Lk[j]);  // A_ij -= L_ik conj(L_jk)
+            }
         }
         __syncthreads();
     }
-    return 1;
 }
 
-// sum_k log2(v[k] * scale) over k < K, evaluated by warp 0 with all lanes
-// busy and reduced by shuffles; the result is valid in thread 0.
-__device__ double warp0_sum_log2(const double* v, int K, double scale) {
+// sum_k log2(a[k] b[k] scale) over k < K, evaluated by warp 0 with all lanes
+// busy and reduced by shuffles; the result is valid in thread 0.  The
+// capacity sum_k log2(p_k / sigma^2) + sum_k log2 L_kk^2 takes one logarithm
+// per user this way.
+__device__ double warp0_sum_log2(const double* a, const double* b, int K, double scale) {
     double acc = 0.0;
     if (threadIdx.x < 32) {
-        for (int k = threadIdx.x; k < K; k += 32) acc += log2(v[k] * scale);
+        for (int k = threadIdx.x; k < K; k += 32) acc += log2(a[k] * b[k] * scale);
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
     }
     return acc;
@@ -155,12 +222,10 @@ struct cf {
 };
 
 __device__ __forceinline__ cf to_cf(cd a) {
-    const float rh = (float)a.x, ih = (float)a.y;
-    return {make_float2(rh, ih), make_float2((float)(a.x - (double)rh), (float)(a.y - (double)ih))};
-}
-
-__device__ __forceinline__ cd from_cf(cf a) {
-    return cmk((double)a.hi.x + (double)a.lo.x, (double)a.hi.y + (double)a.lo.y);
+    cf r;
+    split_f64(a.x, r.hi.x, r.lo.x);
+    split_f64(a.y, r.hi.y, r.lo.y);
+    return r;
 }
 
 // (s, c) += x * y, lane-wise on two lanes: x, y double-float (hi, lo).
@@ -186,8 +251,6 @@ __device__ __forceinline__ void cf_mac(float2& s, float2& c, const cf& a, const 
             make_float2(b.hi.y, b.hi.x), make_float2(b.lo.y, b.lo.x));
 }
 
-__device__ __forceinline__ cd cf_result(float2 s, float2 c) { return cmk((double)s.x + (double)c.x, (double)s.y + (double)c.y); }
-
 // acc - a b for normalized double-float complex values (one two-product per
 // real term, then renormalized by a fast two-sum).
 __device__ __forceinline__ cf cf_fms(const cf& acc, const cf& a, const cf& b) {
@@ -198,11 +261,10 @@ __device__ __forceinline__ cf cf_fms(const cf& acc, const cf& a, const cf& b) {
     return {t, __fadd2_rn(__fadd2_rn(s, make_float2(-t.x, -t.y)), c)};
 }
 
-// a * v for a double-float complex a and a real FP64 v (as hi + lo).
-__device__ __forceinline__ cf cf_scale(const cf& a, double v) {
-    const float vh = (float)v, vl = (float)(v - (double)vh);
+// a * v for a double-float complex a and a real double-float v = (hi, lo).
+__device__ __forceinline__ cf cf_scale(const cf& a, float2 v) {
     float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
-    ff2_mac(s, c, a.hi, a.lo, make_float2(vh, vh), make_float2(vl, vl));
+    ff2_mac(s, c, a.hi, a.lo, make_float2(v.x, v.x), make_float2(v.y, v.y));
     const float2 t = __fadd2_rn(s, c);
     return {t, __fadd2_rn(__fadd2_rn(s, make_float2(-t.x, -t.y)), c)};
 }
@@ -240,56 +302,41 @@ __device__ void gram_of_lower_ff(const cd* X, cd* M, int K) {
     __syncthreads();
 }
 
-// X = L^{-1} (lower triangular) in double-float by right-looking elimination
-// on the identity: for k = 0..K-1 scale row k by 1/L_kk, then subtract L_ik
-// times row k from every row i > k, the (K-k-1) x (k+1) block in parallel.
-// The strictly lower triangle of the FP64 factor L is converted in place (the
-// only part read), X is left in double-float; dinv[k] = 1 / L_kk (FP64).
-__device__ void tri_inverse_ff(cd* L, cd* X, int K, const double* dinv) {
-    {
-        cf* F = reinterpret_cast<cf*>(L);
-        const int P = K * (K - 1) / 2;
-        for (int q = threadIdx.x; q < P; q += blockDim.x) {
-            int r = 1, w = q;
-            while (w >= r) { w -= r; ++r; }
-            const int e = r * K + w;  // row r > column w
-            const cf v = to_cf(L[e]);
-            F[e] = v;
-        }
-        __syncthreads();
-    }
-    const cf* FL = reinterpret_cast<const cf*>(L);
-    cf* FX = reinterpret_cast<cf*>(X);
+// X = L^{-1} (lower triangular, row-major) in double-float.  With L = U D,
+// U = L D^{-1} unit lower triangular and D = diag(L_kk), X = D^{-1} U^{-1}:
+// U^{-1} by right-looking elimination on the identity (for k = 0..K-2
+// subtract U_ik times row k from every row i > k, the (K-k-1) x (k+1) block in
+// parallel; one barrier per column, since the unit diagonal needs no row
+// scaling), then every row i scaled by 1/L_ii.  L comes from chol_lower,
+// column by column (L_ik at T[k K + i]); its strictly lower triangle becomes
+// U in double-float in place (the only part read).  dinvf[k] = 1 / L_kk
+// (float pair).
+__device__ void tri_inverse_ff(cd* T, cd* X, int K, const float2* dinvf) {
     const int tid = threadIdx.x, nt = blockDim.x;
+    cf* FT = reinterpret_cast<cf*>(T);
+    for (int e = tid; e < K * K; e += nt) {
+        const int k = e / K, i = e - k * K;
+        if (i > k) {
+            const cf v = cf_scale(to_cf(T[e]), dinvf[k]);
+            FT[e] = v;
+        }
+    }
+    cf* FX = reinterpret_cast<cf*>(X);
     for (int e = tid; e < K * K; e += nt)
         FX[e] = {make_float2((e / K) == (e % K) ? 1.0f : 0.0f, 0.0f), make_float2(0.0f, 0.0f)};
     __syncthreads();
-    for (int k = 0; k < K; ++k) {
-        const double iv = dinv[k];
-        for (int j = tid; j <= k; j += nt) FX[k * K + j] = cf_scale(FX[k * K + j], iv);
-        __syncthreads();
+    for (int k = 0; k < K - 1; ++k) {
+        const cf* Uk = FT + k * K;
         const int rows = K - k - 1, cols = k + 1;
         for (int e = tid; e < rows * cols; e += nt) {
-            const int i = k + 1 + e / cols, j = e - (e / cols) * cols;
-            FX[i * K + j] = cf_fms(FX[i * K + j], FL[i * K + k], FX[k * K + j]);
+            const int r = e / cols, i = k + 1 + r, j = e - r * cols;
+            FX[i * K + j] = cf_fms(FX[i * K + j], Uk[i], FX[k * K + j]);
         }
         __syncthreads();
     }
-}
-
-// Z = M G with M already in double-float (mcf) or FP64 (converted in place),
-// G converted in place; Z written as FP64.
-__device__ void prod_ff(cd* Mx, bool mcf, cd* G, cd* Z, int K) {
-    if (!mcf) to_cf_inplace(Mx, K);
-    to_cf_inplace(G, K);
-    const cf* FM = reinterpret_cast<const cf*>(Mx);
-    const cf* FG = reinterpret_cast<const cf*>(G);
-    const int tid = threadIdx.x, nt = blockDim.x;
     for (int e = tid; e < K * K; e += nt) {
-        const int r = e / K, c = e - r * K;
-        float2 s = make_float2(0.f, 0.f), cc = make_float2(0.f, 0.f);
-        for (int l = 0; l < K; ++l) cf_mac(s, cc, FM[r * K + l], FG[l * K + c], false);
-        Z[e] = cf_result(s, cc);
+        const int i = e / K, j = e - i * K;
+        if (j <= i) FX[e] = cf_scale(FX[e], dinvf[i]);
     }
     __syncthreads();
 }
@@ -349,10 +396,134 @@ __device__ int gj_inverse_dev(cd* A, cd* X, int K, int* flag, int* piv) {
     return 1;
 }
 
+// The lower triangle of c times a Hermitian Gram matrix g (row-major) into
+// shared memory column by column, as chol_lower takes it: column j of the
+// lower triangle is row j of the upper one conjugated, T[j K + i] =
+// c conj(g[j K + i]) for i > j, read and written contiguously.  add[k] (if
+// non-NULL) goes onto the diagonal, which is written by its own pass so that
+// only K lanes execute the FP64 addition; c = 1 (the usual case) costs no
+// multiplication.
+__device__ void load_lower(cd* T, const double2* __restrict__ g, int K, const double* add, double c) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < K * K; e += nt) {
+        const int j = e / K, i = e - j * K;
+        if (i > j) {
+            const double2 v = g[e];
+            T[e] = c == 1.0 ? cmk(v.x, -v.y) : cmk(v.x * c, -(v.y * c));
+        }
+    }
+    for (int k = tid; k < K; k += nt) {
+        const double d = c == 1.0 ? g[k * K + k].x : g[k * K + k].x * c;
+        T[k * K + k] = cmk(add ? d + add[k] : d, 0.0);
+    }
+}
+
+// c g (complex FP64, row-major, global) into shared memory in double-float.
+__device__ void load_cf(cd* F, const double2* __restrict__ g, int K, double c) {
+    cf* FF = reinterpret_cast<cf*>(F);
+    for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+        const double2 v = g[e];
+        const cf w = to_cf(c == 1.0 ? cmk(v.x, v.y) : cmk(v.x * c, v.y * c));
+        FF[e] = w;
+    }
+}
+
+// Power-of-two scale c that brings the largest Gram diagonal of the trial
+// near 1 when it lies outside [2^-60, 2^60] (else c = 1).  Every receiver
+// quantity is homogeneous in (G, sigma^2): scaling both Gram matrices and the
+// noise power by c leaves SINRs and the capacity unchanged, and keeps the
+// double-float stages (FP32 exponent range) away from overflow and underflow.
+// Executed by warp 0 (exponents compared as integers); valid in every lane.
+__device__ double trial_scale(const double2* __restrict__ gf, const double2* __restrict__ gt, int K) {
+    int em = 0;
+    for (int k = threadIdx.x; k < K; k += 32) {
+        const int ef = (int)(((unsigned)__double2hiint(gf[k * K + k].x) >> 20) & 0x7FFu);
+        const int et = (int)(((unsigned)__double2hiint(gt[k * K + k].x) >> 20) & 0x7FFu);
+        em = max(em, max(ef, et));
+    }
+    em = __reduce_max_sync(0xffffffffu, em);
+    if (em >= 1023 - 60 && em <= 1023 + 60) return 1.0;
+    const int sh = min(1000, max(-1000, 1023 - em));
+    return __hiloint2double((sh + 1023) << 20, 0);
+}
+
+// (s, c) += (s2, c2) lane-wise for double-float values (two-sum on the high
+// parts, low parts summed alongside).
+__device__ __forceinline__ void ff2_add(float2& s, float2& c, float2 s2, float2 c2) {
+    const float2 t = __fadd2_rn(s, s2);
+    const float2 bb = __fadd2_rn(t, make_float2(-s.x, -s.y));
+    const float2 ea = __fadd2_rn(s, make_float2(-(t.x - bb.x), -(t.y - bb.y)));
+    const float2 eb = __fadd2_rn(s2, make_float2(-bb.x, -bb.y));
+    s = t;
+    c = __fadd2_rn(__fadd2_rn(c, c2), __fadd2_rn(ea, eb));
+}
+
+// Sum of the two lanes of a double-float pair, as FP64.
+__device__ __forceinline__ double ff2_total(float2 s, float2 c) {
+    const float t = __fadd_rn(s.x, s.y);
+    const float bb = __fsub_rn(t, s.x);
+    const float err = __fadd_rn(__fsub_rn(s.x, __fsub_rn(t, bb)), __fsub_rn(s.y, bb));
+    return (double)t + (double)__fadd_rn(__fadd_rn(c.x, c.y), err);
+}
+
+// Mismatched-receiver SINR (Sec. V-B) from M and G in double-float:
+//   SINR_k = p_k |A_kk|^2 / (sum_{j != k} p_j |A_kj|^2 + sigma^2 Re (A M^H)_kk),
+//   A = M G.
+// A is never stored: warp w takes users k = w, w + nwarps, ...; lane l forms
+// A_kj for j = l (and l + 32 when K > 32) as a dot product of row k of M
+// (broadcast) with column j of G (contiguous across lanes), and adds its terms
+// to three double-float sums that the warp then reduces by shuffles and
+// converts to FP64 once, so the K^3 products cost no FP64 instruction.
+__device__ void mismatched_sinr(const cf* FM, const cf* FG, const double* p, double s2, int K, double* sinr_t) {
+    __shared__ float2 pf[XLMIMO_MAX_USERS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (int k = tid; k < K; k += blockDim.x) {
+        float h, l;
+        split_f64(p[k], h, l);
+        pf[k] = make_float2(h, l);
+    }
+    __syncthreads();
+    const float2 z = make_float2(0.f, 0.f);
+    for (int k = warp; k < K; k += nw) {
+        const cf* Mk = FM + k * K;
+        float2 ss = z, sc = z, is = z, ic = z, ns = z, nc = z;
+        for (int j = lane; j < K; j += 32) {
+            float2 as = z, ac = z;
+            for (int l = 0; l < K; ++l) cf_mac(as, ac, Mk[l], FG[l * K + j], false);
+            const float2 ah = __fadd2_rn(as, ac);  // A_kj normalized
+            const float2 al = __fadd2_rn(__fadd2_rn(as, make_float2(-ah.x, -ah.y)), ac);
+            const cf m = Mk[j];
+            ff2_mac(ns, nc, ah, al, m.hi, m.lo);  // (re a re m, im a im m)
+            if (j == k) {
+                ff2_mac(ss, sc, ah, al, ah, al);  // (re^2, im^2)
+            } else {
+                float2 ps = z, pc = z;
+                const float2 pj = pf[j];
+                ff2_mac(ps, pc, make_float2(pj.x, pj.x), make_float2(pj.y, pj.y), ah, al);  // p_j a
+                ff2_mac(is, ic, ps, pc, ah, al);
+            }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            float2 o[6];
+            const float2 v[6] = {ss, sc, is, ic, ns, nc};
+#pragma unroll
+            for (int q = 0; q < 6; ++q)
+                o[q] = make_float2(__shfl_xor_sync(0xffffffffu, v[q].x, off), __shfl_xor_sync(0xffffffffu, v[q].y, off));
+            ff2_add(ss, sc, o[0], o[1]);
+            ff2_add(is, ic, o[2], o[3]);
+            ff2_add(ns, nc, o[4], o[5]);
+        }
+        if (lane == 0) {
+            const double S = ff2_total(ss, sc), I = ff2_total(is, ic), N = ff2_total(ns, nc);
+            sinr_t[k] = p[k] * S / fma(s2, N, I);
+        }
+    }
+}
+
 // One trial's receiver, executed by the whole CTA.  gf/gt: this trial's Gram
 // matrices (gt == gf when matched); pw: its K powers; s2: its noise power;
 // sinr_t, status_t, cap_t: its outputs (cap_t may be NULL).  Dynamic shared
-// memory: (matched ? 2 : 3) K^2 complex doubles plus 2 XLMIMO_MAX_USERS doubles.
+// memory: 2 K^2 complex doubles plus 2 XLMIMO_MAX_USERS doubles.
 __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __restrict__ gt, int matched,
                                const double* __restrict__ pw, double s2, int K, int scheme, int power_mode,
                                double* __restrict__ sinr_t, int* __restrict__ status_t, double* __restrict__ cap_t) {
@@ -360,37 +531,38 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
     const int KK = K * K;
     cd* Z = reinterpret_cast<cd*>(smem);
     cd* X = Z + KK;
-    cd* G = X + KK;  // true Gram (mismatched only)
-    double* p = reinterpret_cast<double*>(G + (matched ? 0 : KK));
+    double* p = reinterpret_cast<double*>(X + KK);
     double* dg = p + XLMIMO_MAX_USERS;
-    __shared__ double dinv[XLMIMO_MAX_USERS], pivd[XLMIMO_MAX_USERS], sp[XLMIMO_MAX_USERS];
+    __shared__ double pivd[XLMIMO_MAX_USERS], sp[XLMIMO_MAX_USERS];
+    __shared__ float2 dinvf[XLMIMO_MAX_USERS];
     __shared__ int flag, piv, st;
+    __shared__ double cs;
     const int tid = threadIdx.x, nt = blockDim.x;
-    bool m_is_cf = false;  // X holds M in double-float (else FP64)
-    if (tid == 0) { flag = 0; st = 0; }
+    bool m_in_z = false;  // M in Z in double-float (else in X in FP64, from Gauss-Jordan)
+    if (tid < 32) {
+        const double c = trial_scale(gf, gt, K);
+        if (tid == 0) { flag = 0; st = 0; cs = c; }
+    }
+    __syncthreads();
+    // the matrices below are c G and the noise power c sigma^2 (s2c); the
+    // powers p and the MRC branch, which reads the Gram directly, use sigma^2
+    const double c = cs, s2c = c * s2;
     for (int k = tid; k < K; k += nt) {
         double v = pw[k];
         p[k] = (power_mode == XLMIMO_POWER_RXSNR) ? v * s2 / gt[k * K + k].x : v;
-        sp[k] = s2 / p[k];  // MMSE diagonal loading sigma^2 / p_k
+        sp[k] = s2c / p[k];  // MMSE diagonal loading sigma^2 / p_k
     }
-    if (!matched)
-        for (int e = tid; e < KK; e += nt) G[e] = cmk(gt[e].x, gt[e].y);
     __syncthreads();
 
     // ---- capacity: Cholesky of G + s2 diag(p)^-1 (the MMSE matrix of the true channel)
     const bool mmse_reuse = matched && scheme == XLMIMO_MMSE;
     if (cap_t && !mmse_reuse) {
-        for (int e = tid; e < KK; e += nt) {
-            int r = e / K, c = e - r * K;
-            double2 v = gt[e];
-            Z[e] = cmk(v.x + (r == c ? sp[r] : 0.0), r == c ? 0.0 : v.y);
-        }
+        load_lower(Z, gt, K, sp, c);
         __syncthreads();
-        int ok = chol_lower(Z, K, &flag, dinv, pivd);
-        double ld = ok ? warp0_sum_log2(pivd, K, 1.0) : 0.0;
-        double lp = warp0_sum_log2(p, K, 1.0 / s2);
+        int ok = chol_lower(Z, K, &flag, dinvf, pivd);
+        const double cp = ok ? warp0_sum_log2(pivd, p, K, 1.0 / s2c) : 0.0;
         if (tid == 0) {
-            *cap_t = ok ? lp + ld : nan("");
+            *cap_t = ok ? cp : nan("");
             flag = 0;
         }
         __syncthreads();
@@ -402,21 +574,15 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
         for (int e = tid; e < KK; e += nt) X[e] = cmk((e / K) == (e % K) ? 1.0 : 0.0, 0.0);  // M = I
         __syncthreads();
     } else {
-        for (int e = tid; e < KK; e += nt) {
-            int r = e / K, c = e - r * K;
-            double2 v = gf[e];
-            double add = (scheme == XLMIMO_MMSE && r == c) ? sp[r] : 0.0;
-            Z[e] = cmk(v.x + add, r == c ? 0.0 : v.y);
-        }
+        load_lower(Z, gf, K, scheme == XLMIMO_MMSE ? sp : nullptr, c);
         __syncthreads();
-        int ok = chol_lower(Z, K, &flag, dinv, pivd);
+        int ok = chol_lower(Z, K, &flag, dinvf, pivd);
         if (ok) {
             if (mmse_reuse && cap_t) {
-                double ld = warp0_sum_log2(pivd, K, 1.0);
-                double lp = warp0_sum_log2(p, K, 1.0 / s2);
-                if (tid == 0) *cap_t = lp + ld;
+                const double cp = warp0_sum_log2(pivd, p, K, 1.0 / s2c);
+                if (tid == 0) *cap_t = cp;
             }
-            tri_inverse_ff(Z, X, K, dinv);  // X = L^{-1}, double-float
+            tri_inverse_ff(Z, X, K, dinvf);  // X = L^{-1}, double-float
             if (matched) {
                 // dg_k = sum_{i >= k} |X_ik|^2 in double-float, one conversion per k
                 const cf* FX = reinterpret_cast<const cf*>(X);
@@ -430,20 +596,18 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
                 }
                 __syncthreads();
             } else {
-                // M = X^H X (double-float) into Z (the factor is no longer needed), then back into X
+                // M = X^H X (double-float) into Z (the factor is no longer needed)
                 gram_of_lower_ff(X, Z, K);
-                for (int e = tid; e < KK; e += nt) X[e] = Z[e];
-                __syncthreads();
-                m_is_cf = true;
+                m_in_z = true;
             }
         } else {
             // not positive definite: Gauss-Jordan on a fresh copy
             if (tid == 0) { flag = 0; st = 1; }
             for (int e = tid; e < KK; e += nt) {
-                int r = e / K, c = e - r * K;
+                int r = e / K, col = e - r * K;
                 double2 v = gf[e];
-                double add = (scheme == XLMIMO_MMSE && r == c) ? sp[r] : 0.0;
-                Z[e] = cmk(v.x + add, v.y);
+                double add = (scheme == XLMIMO_MMSE && r == col) ? sp[r] : 0.0;
+                Z[e] = cmk(fma(v.x, c, add), v.y * c);
             }
             __syncthreads();
             int ok2 = gj_inverse_dev(Z, X, K, &flag, &piv);
@@ -461,17 +625,12 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
             }
             if (cap_t && mmse_reuse) {
                 // recompute the capacity on its own factorisation
-                for (int e = tid; e < KK; e += nt) {
-                    int r = e / K, c = e - r * K;
-                    double2 v = gt[e];
-                    Z[e] = cmk(v.x + (r == c ? sp[r] : 0.0), r == c ? 0.0 : v.y);
-                }
+                load_lower(Z, gt, K, sp, c);
                 __syncthreads();
-                int ok3 = chol_lower(Z, K, &flag, dinv, pivd);
-                double ld2 = ok3 ? warp0_sum_log2(pivd, K, 1.0) : 0.0;
-                double lp = warp0_sum_log2(p, K, 1.0 / s2);
+                int ok3 = chol_lower(Z, K, &flag, dinvf, pivd);
+                const double cp = ok3 ? warp0_sum_log2(pivd, p, K, 1.0 / s2c) : 0.0;
                 if (tid == 0) {
-                    *cap_t = ok3 ? lp + ld2 : nan("");
+                    *cap_t = ok3 ? cp : nan("");
                     flag = 0;
                 }
                 __syncthreads();
@@ -491,25 +650,19 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
                     if (j != k) { double2 q = gm[k * K + j]; itf += p[j] * (q.x * q.x + q.y * q.y); }
                 v = p[k] * gkk * gkk / (itf + s2 * gkk);
             } else {
-                v = p[k] / (s2 * dg[k]);
+                v = p[k] / (s2c * dg[k]);
                 if (scheme == XLMIMO_MMSE) v -= 1.0;
             }
             sinr_t[k] = v;
         }
     } else {
-        // A = M G (M in X) into Z in double-float; X and G are left in double-float
-        prod_ff(X, m_is_cf, G, Z, K);
-        const cf* FM = reinterpret_cast<const cf*>(X);
-        for (int k = tid; k < K; k += nt) {
-            double sig = p[k] * cabs2(Z[k * K + k]);
-            double itf = 0.0, nz = 0.0;
-            for (int j = 0; j < K; ++j) {
-                cd a = Z[k * K + j];
-                if (j != k) itf = fma(p[j], cabs2(a), itf);
-                nz += cmulc(a, from_cf(FM[k * K + j])).x;  // (A M^H)_kk
-            }
-            sinr_t[k] = sig / fma(s2, nz, itf);
-        }
+        // M in double-float, the true Gram into the other buffer (double-float)
+        cd* Mb = m_in_z ? Z : X;
+        cd* Gb = m_in_z ? X : Z;
+        if (!m_in_z) to_cf_inplace(Mb, K);
+        load_cf(Gb, gt, K, c);
+        __syncthreads();
+        mismatched_sinr(reinterpret_cast<const cf*>(Mb), reinterpret_cast<const cf*>(Gb), p, s2c, K, sinr_t);
     }
     if (tid == 0) *status_t = st;
 }
@@ -558,7 +711,7 @@ int launch_beamform(const double* gf, const double* gt, const double* power, con
     int matched = (gt == nullptr || gt == gf) ? 1 : 0;
     if (!gt) gt = gf;
     size_t KK = (size_t)K * K;
-    size_t smem = (matched ? 2 : 3) * KK * sizeof(cd) + 2 * XLMIMO_MAX_USERS * sizeof(double);
+    size_t smem = 2 * KK * sizeof(cd) + 2 * XLMIMO_MAX_USERS * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(beamform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return cuda_status(e, "beamform attribute");
     beamform_kernel<<<B, SOLVE_THREADS, smem, st>>>((const double2*)gf, (const double2*)gt, matched, power, noise, K,

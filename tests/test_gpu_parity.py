@@ -209,6 +209,31 @@ def test_beamform_modified_zf(xl, orc, K, scheme):
         assert np.max(rel) <= 1e-7
 
 
+@pytest.mark.parametrize("scale_log2", [-300, -150, -80, 80, 150, 300])
+def test_beamform_scale_invariance(xl, orc, scale_log2):
+    """The receivers are homogeneous in (G, sigma^2): Gram matrices far outside
+    FP32's exponent range (where the double-float stages work) match the oracle
+    on the same scaled problem, matched with capacity and mismatched."""
+    K, N = 16, 256
+    _, G, Gc, p, s2 = _solve_case(orc, 70, 8, K, N)
+    p = p / np.real(np.einsum("bii->bi", G))
+    sc = 2.0 ** scale_log2
+    for scheme in (0, 1):
+        s_ref, st_ref, c_ref = orc.beamform(G * sc, p, s2 * sc, scheme, 0, want_capacity=True)
+        s, st, c = xl.xlmimo_beamform(dev(G * sc), dev(p), dev(s2 * sc), scheme, 0, capacity=True)
+        s, st, c = s.cpu().numpy(), st.cpu().numpy(), c.cpu().numpy()
+        ok = st_ref == 0
+        assert ok.sum() >= 4 and np.all(st[ok] == 0)
+        assert np.max(np.abs(s[ok] - s_ref[ok]) / np.abs(s_ref[ok])) <= 1e-9
+        assert np.max(np.abs(c - c_ref) / np.abs(c_ref)) <= 1e-10
+    s_ref, st_ref, _ = orc.beamform(Gc * sc, p, s2 * sc, 0, 0, gram_true=G * sc)
+    s, st, _ = xl.xlmimo_beamform(dev(Gc * sc), dev(p), dev(s2 * sc), 0, 0, gram_true=dev(G * sc))
+    s, st = s.cpu().numpy(), st.cpu().numpy()
+    ok = (st_ref == 0) & (st != 4)
+    assert ok.sum() >= 4
+    assert np.max(np.abs(s[ok] - s_ref[ok]) / np.abs(s_ref[ok])) <= 1e-7
+
+
 def test_beamform_singular(xl):
     G = np.array([[[1.0, 1.0], [1.0, 1.0]]], complex)
     s, st, _ = xl.xlmimo_beamform(dev(G), dev(np.ones((1, 2))), dev(np.ones(1)), 0)
