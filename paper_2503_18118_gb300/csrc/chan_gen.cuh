@@ -13,10 +13,13 @@
 //   r(n) - r(n_c) = m A + R,   R = 2 u^2 x^2 / (r_c ((r_c + r - u)(r_c + r + u)))
 // (subtract the tangent line from r - r_c = (2 e_c u + u^2)/(r + r_c) and
 // simplify; no term cancels because r_c + r > |u| for x > 0).  m A is formed
-// as an exact FP32 product plus FMA residual against A held as two floats,
-// and every partial sum is reduced modulo one cycle before it is added; the
-// emulated worst-case phase error is ~1e-6 rad at 3 m from a 16384-element
-// 100 GHz array.  The planar-wave model is the linear term alone (R = 0).
+// exactly against A held as two floats (an FP32 product plus FMA residual, or
+// in the packed path a 16-bit high part whose product with m is exact), and
+// every partial sum is reduced modulo one cycle before it is added.  An FP32
+// emulation puts the worst phase error at ~4e-6 rad (users 3-30 m from
+// 16384- and 131072-element 100 GHz arrays, 5-50 m from a 65536-element
+// 28 GHz array), below the BF16 hi/lo split's 2^-16.  The planar-wave model
+// is the linear term alone (R = 0).
 #pragma once
 
 #include "common.cuh"
@@ -175,43 +178,44 @@ __device__ __forceinline__ float2 frac2(float2 x) {  // x - rint(x), |x| < 2^22
     return __ffma2_rn(t, f2(-1.0f), x);
 }
 
-// Packed per-span constants of one user.
+// Packed per-span constants of one user.  The slope A = a_hi + a_lo is
+// re-split so that a_hi keeps 16 significant bits: m a_hi is then exact in
+// FP32 for |m| <= 2^8 (a span of at most 512 elements), so it needs no FMA
+// residual, and a_lo = A - a_hi (at most 2^-16 |A|) carries A to ~2^-40.
 struct PairConst {
-    float2 frac0, nahi, ahi, alo, e0, r0, xl2, x2x2, dp, ndp, ampc;
+    float2 frac0, nahi, alo, e0, r0, xl2, x2x2, dp, ampc;
 };
 
 __device__ __forceinline__ PairConst make_pair_const(const UserRef& R, float dprime, float xl2, float x2x2,
                                                      float ampc) {
     PairConst c;
+    const float ah = __uint_as_float(__float_as_uint(R.a_hi) & 0xFFFFFF00u);
     c.frac0 = f2(R.frac0);
-    c.nahi = f2(-R.a_hi);
-    c.ahi = f2(R.a_hi);
-    c.alo = f2(R.a_lo);
+    c.nahi = f2(-ah);
+    c.alo = f2(__fadd_rn(__fsub_rn(R.a_hi, ah), R.a_lo));
     c.e0 = f2(R.e0);
     c.r0 = f2(R.r0);
     c.xl2 = f2(xl2);
     c.x2x2 = f2(x2x2);
     c.dp = f2(dprime);
-    c.ndp = f2(-dprime);
     c.ampc = f2(ampc);
     return c;
 }
 
-// Entries at offsets mf.x, mf.y from the span centre: re = amp cos(phi),
-// im = -amp sin(phi) for each of the two.
+// Entries at offsets mf.x, mf.y from the span centre (|mf| <= 256):
+// re = amp cos(phi), im = -amp sin(phi) for each of the two.
 template <int MODEL>
 __device__ __forceinline__ void gen_pair(const PairConst& c, float2 mf, float2& re, float2& im) {
     const float2 m1 = f2(-1.0f);
-    float2 np = __fmul2_rn(mf, c.nahi);          // -p = -m a_hi (exact product)
-    float2 pe = __ffma2_rn(mf, c.ahi, np);       // m a_hi - p (exact residual)
-    float2 g = __fadd2_rn(c.frac0, __ffma2_rn(mf, c.alo, pe));
+    float2 np = __fmul2_rn(mf, c.nahi);          // -p = -m a_hi (exact: 16-bit a_hi)
+    float2 g = __ffma2_rn(mf, c.alo, c.frac0);
     g = __ffma2_rn(frac2(np), m1, g);           // + frac(p)
     float2 amp;
     if (MODEL == XLMIMO_UPW) {
         amp = c.ampc;
     } else {
         float2 u = __fmul2_rn(mf, c.dp);
-        float2 nu2 = __fmul2_rn(u, __fmul2_rn(mf, c.ndp));  // -u^2
+        float2 nu2 = __fmul2_rn(u, make_float2(-u.x, -u.y));  // -u^2
         float2 en = __fadd2_rn(c.e0, u);
         float2 r2 = __ffma2_rn(en, en, c.xl2);
         float2 rs = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
@@ -226,12 +230,13 @@ __device__ __forceinline__ void gen_pair(const PairConst& c, float2 mf, float2& 
             amp = __fmul2_rn(amp, make_float2(rsqrtf(rp.x), rsqrtf(rp.y)));
         }
     }
-    g = __fmul2_rn(frac2(g), f2(6.283185307179586f));
+    // the angle is -phi: its sine is the entry's -sin(phi)
+    g = __fmul2_rn(frac2(g), f2(-6.283185307179586f));
     float s0, c0, s1, c1;
     __sincosf(g.x, &s0, &c0);
     __sincosf(g.y, &s1, &c1);
     re = __fmul2_rn(amp, make_float2(c0, c1));
-    im = __fmul2_rn(__fmul2_rn(amp, m1), make_float2(s0, s1));
+    im = __fmul2_rn(amp, make_float2(s0, s1));
 }
 
 }  // namespace xl
