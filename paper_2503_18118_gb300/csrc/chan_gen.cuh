@@ -16,8 +16,9 @@
 // exactly against A held as two floats (an FP32 product plus FMA residual, or
 // in the packed path a 16-bit high part whose product with m is exact), and
 // every partial sum is reduced modulo one cycle before it is added.  An FP32
-// emulation puts the worst phase error at ~4e-6 rad (users 3-30 m from
-// 16384- and 131072-element 100 GHz arrays, 5-50 m from a 65536-element
+// emulation puts the worst phase error at ~4e-6 rad for the scalar generator
+// and ~8e-6 rad for the packed one of the tensor-core kernels (users 3-30 m
+// from 16384- and 131072-element 100 GHz arrays, 5-50 m from a 65536-element
 // 28 GHz array), below the BF16 hi/lo split's 2^-16.  The planar-wave model
 // is the linear term alone (R = 0).
 #pragma once
@@ -51,7 +52,7 @@ struct UserGeo {
 
 // Per user, per reference span.
 struct UserRef {
-    float frac0, a_hi, a_lo, e0, r0;
+    float frac0, a_hi, a_lo, e0, r0, kx;  // kx = 2 (x/lambda)^2 / r0
 };
 
 inline GenParams make_gen_params(const Geom& g) {
@@ -106,6 +107,7 @@ __device__ __forceinline__ UserRef make_user_ref(const GenParams& p, const UserG
         A = ff_neg(ff_mul(p.dprime, u.su));
         R.e0 = 0.f;
         R.r0 = 1.f;
+        R.kx = 0.f;
     } else {
         ff e0 = ff_sub(ync, u.y);
         ff r0 = ff_sqrt(ff_add(u.x2, ff_mul(e0, e0)));
@@ -113,6 +115,7 @@ __device__ __forceinline__ UserRef make_user_ref(const GenParams& p, const UserG
         A = ff_div(ff_mul(p.dprime, e0), r0);
         R.e0 = e0.hi * p.inv_lambda.hi;
         R.r0 = q0.hi;
+        R.kx = __fdiv_rn(u.x2x2, q0.hi);
     }
     R.frac0 = __fadd_rn(__fsub_rn(q0.hi, rintf(q0.hi)), q0.lo);
     R.frac0 -= rintf(R.frac0);
@@ -183,7 +186,7 @@ __device__ __forceinline__ float2 frac2(float2 x) {  // x - rint(x), |x| < 2^22
 // FP32 for |m| <= 2^8 (a span of at most 512 elements), so it needs no FMA
 // residual, and a_lo = A - a_hi (at most 2^-16 |A|) carries A to ~2^-40.
 struct PairConst {
-    float2 frac0, nahi, alo, e0, r0, xl2, x2x2, dp, ampc;
+    float2 frac0, nahi, alo, e0, r0, xl2, kx, dp, ampc;  // kx = 2 x^2 / r_c
 };
 
 __device__ __forceinline__ PairConst make_pair_const(const UserRef& R, float dprime, float xl2, float x2x2,
@@ -196,7 +199,7 @@ __device__ __forceinline__ PairConst make_pair_const(const UserRef& R, float dpr
     c.e0 = f2(R.e0);
     c.r0 = f2(R.r0);
     c.xl2 = f2(xl2);
-    c.x2x2 = f2(x2x2);
+    c.kx = f2(R.kx);
     c.dp = f2(dprime);
     c.ampc = f2(ampc);
     return c;
@@ -220,9 +223,9 @@ __device__ __forceinline__ void gen_pair(const PairConst& c, float2 mf, float2& 
         float2 r2 = __ffma2_rn(en, en, c.xl2);
         float2 rs = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
         float2 sum = __ffma2_rn(r2, rs, c.r0);      // r_c + r
-        float2 den = __fmul2_rn(c.r0, __ffma2_rn(sum, sum, nu2));
+        float2 den = __ffma2_rn(sum, sum, nu2);     // (r_c + r)^2 - u^2
         float2 inv = make_float2(rcp_approx(den.x), rcp_approx(den.y));
-        float2 nR = __fmul2_rn(__fmul2_rn(c.x2x2, nu2), inv);  // -R
+        float2 nR = __fmul2_rn(__fmul2_rn(c.kx, nu2), inv);  // -R
         g = __ffma2_rn(frac2(nR), m1, g);
         amp = __fmul2_rn(c.ampc, rs);
         if (MODEL == XLMIMO_PNUSW) {
@@ -230,8 +233,10 @@ __device__ __forceinline__ void gen_pair(const PairConst& c, float2 mf, float2& 
             amp = __fmul2_rn(amp, make_float2(rsqrtf(rp.x), rsqrtf(rp.y)));
         }
     }
-    // the angle is -phi: its sine is the entry's -sin(phi)
-    g = __fmul2_rn(frac2(g), f2(-6.283185307179586f));
+    // the angle is -phi (its sine is the entry's -sin(phi)); every term of g
+    // was reduced modulo one cycle, so |g| <= 3/2 and |angle| <= 3 pi, within
+    // the range where sin.approx / cos.approx keep their stated absolute error
+    g = __fmul2_rn(g, f2(-6.283185307179586f));
     float s0, c0, s1, c1;
     __sincosf(g.x, &s0, &c0);
     __sincosf(g.y, &s1, &c1);

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
                 const int rin = f & 7;
                 soff[slot][c] = (uint32_t)((f >> 3) * 1024 + rin * 128 + ((warp ^ rin) << 4));
             }
-        PairConst pc = make_pair_const(UserRef{0.f, 0.f, 0.f, 0.f, 1.f}, gp.dprime_f, 0.f, 0.f, 0.f);
+        PairConst pc = make_pair_const(UserRef{0.f, 0.f, 0.f, 0.f, 1.f, 0.f}, gp.dprime_f, 0.f, 0.f, 0.f);
         int64_t nc = 0;
         bool dead = false;
         for (int it = 0; it < nst; ++it) {
