@@ -39,7 +39,7 @@ struct RgShared {
     int bad;
     int item;
     UserGeo ug[RG_KMAX];
-    float scale[RG_KMAX];
+    double fac[RG_KMAX];  // per-user factor of the Gram: G_ij = fac_i fac_j (accumulated sum)
     UserRef ref[2][RG_KMAX];  // phase references of the current and the next span
 };
 
@@ -98,17 +98,19 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
             }
             UserGeo u = make_user_geo(g, x, y);
             if (tid < K && !u.ok) atomicOr(&sh->bad, 1);
-            float sc = 1.0f;
+            // the BF16 paths generate entries without the amplitude constant and
+            // apply it to the Gram in FP64; the FP16 path scales user k's entries by
+            // 1/|h_k| at the array centre so that they sit near 1, and divides it out
+            double fac = amp_const(g, x, y);
             if (PREC == TCP_F16X3) {
-                const double rc = sqrt(x * x + y * y) * g.inv_lambda;
-                double amp_c = (MODEL == XLMIMO_UPW) ? (double)u.ampc
-                             : (MODEL == XLMIMO_PNUSW) ? (double)u.ampc / (rc * sqrt(rc))
-                                                       : (double)u.ampc / rc;
-                sc = (float)(1.0 / amp_c);
+                const double rc = sqrt(x * x + y * y) * g.inv_lambda;  // distance in wavelengths
+                double amp_c = (MODEL == XLMIMO_UPW) ? fac : (MODEL == XLMIMO_PNUSW) ? fac / (rc * sqrt(rc)) : fac / rc;
+                const float sc = (float)(1.0 / amp_c);
                 u.ampc *= sc;
+                fac = 1.0 / (double)sc;
             }
             sh->ug[tid] = u;
-            sh->scale[tid] = sc;
+            sh->fac[tid] = fac;
         }
         __syncthreads();
         const int64_t nbeg = itm.n0, nend = itm.n1;
@@ -174,11 +176,13 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
                         const UserGeo& u = sh->ug[k];
                         const PairConst pc =
                             make_pair_const(sh->ref[sp & 1][k], gpi.dprime_f, u.xl2, u.x2x2, k < K ? u.ampc : 0.f);
+                        const float base = slice_base(pc, mf0 + 3.5f);  // phase at the slice centre
                         auto slice = [&](auto partial) {
 #pragma unroll
                             for (int i = 0; i < 8; i += 2) {
                                 float2 re, im;
-                                gen_pair<MODEL>(pc, make_float2(mf0 + (float)i, mf0 + (float)(i + 1)), re, im);
+                                gen_pair<MODEL, PREC != TCP_F16X3>(pc, make_float2(mf0 + (float)i, mf0 + (float)(i + 1)),
+                                                            make_float2((float)i - 3.5f, (float)i - 2.5f), base, re, im);
                                 if (decltype(partial)::value) {
                                     if (i >= rem) { re.x = 0.f; im.x = 0.f; }
                                     if (i + 1 >= rem) { re.y = 0.f; im.y = 0.f; }
@@ -265,11 +269,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
                 const float* F = fold;
                 double re = (double)(F[i * RCfg::FOLD_LD + j] + F[(64 + i) * RCfg::FOLD_LD + 64 + j]);
                 double im = (double)(F[i * RCfg::FOLD_LD + 64 + j] - F[(64 + i) * RCfg::FOLD_LD + j]);
-                if (PREC == TCP_F16X3) {
-                    const double us = 1.0 / ((double)sh->scale[i] * (double)sh->scale[j]);
-                    re *= us;
-                    im *= us;
-                }
+                const double us = sh->fac[i] * sh->fac[j];
+                re *= us;
+                im *= us;
                 if (i == j) {
                     o[i * K + i] = make_double2(re, 0.0);
                 } else {

@@ -70,6 +70,15 @@ inline GenParams make_gen_params(const Geom& g) {
     return p;
 }
 
+// Amplitude constant of the model (FP64): FSPL lambda/(4 pi r) = c / r' with
+// c = 1/(4 pi) and r' in wavelengths; PNUSW sqrt(beta0 x) r^{-3/2} = c r'^{-3/2}
+// with c = sqrt(beta0) sqrt(x/lambda) / lambda; UPW sqrt(beta0) / |user|.
+__device__ __forceinline__ double amp_const(const Geom& g, double x, double y) {
+    if (g.model == XLMIMO_FSPL_USW) return 1.0 / (4.0 * 3.14159265358979323846);
+    if (g.model == XLMIMO_PNUSW) return sqrt(g.beta0) * sqrt(x * g.inv_lambda) * g.inv_lambda;
+    return sqrt(g.beta0) / sqrt(x * x + y * y);
+}
+
 __device__ __forceinline__ UserGeo make_user_geo(const Geom& g, double x, double y) {
     UserGeo u;
     u.ok = user_ok(x, y);
@@ -84,12 +93,7 @@ __device__ __forceinline__ UserGeo make_user_geo(const Geom& g, double x, double
     double xl = x * g.inv_lambda;
     u.xl2 = (float)(xl * xl);
     u.x2x2 = (float)(2.0 * xl * xl);
-    if (g.model == XLMIMO_FSPL_USW)
-        u.ampc = (float)(1.0 / (4.0 * 3.14159265358979323846));  // lambda/(4 pi r) = 1/(4 pi r')
-    else if (g.model == XLMIMO_PNUSW)
-        u.ampc = (float)(sqrt(g.beta0) * sqrt(xl) * g.inv_lambda);  // times r'^{-3/2}
-    else
-        u.ampc = (float)(sqrt(g.beta0) / r0);
+    u.ampc = (float)amp_const(g, x, y);
     return u;
 }
 
@@ -181,21 +185,25 @@ __device__ __forceinline__ float2 frac2(float2 x) {  // x - rint(x), |x| < 2^22
     return __ffma2_rn(t, f2(-1.0f), x);
 }
 
-// Packed per-span constants of one user.  The slope A = a_hi + a_lo is
-// re-split so that a_hi keeps 16 significant bits: m a_hi is then exact in
-// FP32 for |m| <= 2^8 (a span of at most 512 elements), so it needs no FMA
-// residual, and a_lo = A - a_hi (at most 2^-16 |A|) carries A to ~2^-40.
+// Packed per-span constants of one user.  The linear phase term m A is
+// formed per 8-element slice: with the slice centre mc (a half-integer,
+// |mc| <= 2^8) and A = ah + al, ah keeping 15 significant bits, mc ah is
+// exact in FP32 and reduced modulo one cycle once per slice; an element at
+// offset t from the centre (|t| <= 7/2) then adds t A in one FMA, small
+// enough to need no reduction.
 struct PairConst {
-    float2 frac0, nahi, alo, e0, r0, xl2, kx, dp, ampc;  // kx = 2 x^2 / r_c
+    float frac0, ah, al;                          // slice base
+    float2 af, e0, r0, xl2, kx, dp, ampc;         // kx = 2 x^2 / r_c
 };
 
 __device__ __forceinline__ PairConst make_pair_const(const UserRef& R, float dprime, float xl2, float x2x2,
                                                      float ampc) {
     PairConst c;
-    const float ah = __uint_as_float(__float_as_uint(R.a_hi) & 0xFFFFFF00u);
-    c.frac0 = f2(R.frac0);
-    c.nahi = f2(-ah);
-    c.alo = f2(__fadd_rn(__fsub_rn(R.a_hi, ah), R.a_lo));
+    const float ah = __uint_as_float(__float_as_uint(R.a_hi) & 0xFFFFFE00u);
+    c.frac0 = R.frac0;
+    c.ah = ah;
+    c.al = __fadd_rn(__fsub_rn(R.a_hi, ah), R.a_lo);
+    c.af = f2(__fadd_rn(R.a_hi, R.a_lo));
     c.e0 = f2(R.e0);
     c.r0 = f2(R.r0);
     c.xl2 = f2(xl2);
@@ -205,17 +213,23 @@ __device__ __forceinline__ PairConst make_pair_const(const UserRef& R, float dpr
     return c;
 }
 
-// Entries at offsets mf.x, mf.y from the span centre (|mf| <= 256):
-// re = amp cos(phi), im = -amp sin(phi) for each of the two.
-template <int MODEL>
-__device__ __forceinline__ void gen_pair(const PairConst& c, float2 mf, float2& re, float2& im) {
+// Phase (cycles, |.| <= 1) at the slice centre mc, from the span reference.
+__device__ __forceinline__ float slice_base(const PairConst& c, float mc) {
+    return __fadd_rn(__fmaf_rn(mc, c.al, c.frac0), frac_rn(__fmul_rn(mc, c.ah)));
+}
+
+// Entries at offsets mf.x, mf.y from the span centre (|mf| <= 256), which
+// are t.x, t.y from the centre of their slice (phase base, from slice_base):
+// re = amp cos(phi), im = -amp sin(phi) for each of the two.  UNIT leaves the
+// model's amplitude constant out (the caller applies it to the Gram in FP64).
+template <int MODEL, bool UNIT = false>
+__device__ __forceinline__ void gen_pair(const PairConst& c, float2 mf, float2 t, float base, float2& re,
+                                         float2& im) {
     const float2 m1 = f2(-1.0f);
-    float2 np = __fmul2_rn(mf, c.nahi);          // -p = -m a_hi (exact: 16-bit a_hi)
-    float2 g = __ffma2_rn(mf, c.alo, c.frac0);
-    g = __ffma2_rn(frac2(np), m1, g);           // + frac(p)
-    float2 amp;
+    float2 g = __ffma2_rn(t, c.af, f2(base));   // |g| <= 1 + 7/4
+    float2 amp = f2(1.0f);
     if (MODEL == XLMIMO_UPW) {
-        amp = c.ampc;
+        if (!UNIT) amp = c.ampc;
     } else {
         float2 u = __fmul2_rn(mf, c.dp);
         float2 nu2 = __fmul2_rn(u, make_float2(-u.x, -u.y));  // -u^2
@@ -227,21 +241,26 @@ __device__ __forceinline__ void gen_pair(const PairConst& c, float2 mf, float2& 
         float2 inv = make_float2(rcp_approx(den.x), rcp_approx(den.y));
         float2 nR = __fmul2_rn(__fmul2_rn(c.kx, nu2), inv);  // -R
         g = __ffma2_rn(frac2(nR), m1, g);
-        amp = __fmul2_rn(c.ampc, rs);
+        amp = UNIT ? rs : __fmul2_rn(c.ampc, rs);
         if (MODEL == XLMIMO_PNUSW) {
             float2 rp = __fmul2_rn(r2, rs);
             amp = __fmul2_rn(amp, make_float2(rsqrtf(rp.x), rsqrtf(rp.y)));
         }
     }
-    // the angle is -phi (its sine is the entry's -sin(phi)); every term of g
-    // was reduced modulo one cycle, so |g| <= 3/2 and |angle| <= 3 pi, within
-    // the range where sin.approx / cos.approx keep their stated absolute error
+    // the angle is -phi (its sine is the entry's -sin(phi)); |g| <= 13/4, so
+    // |angle| <= 13 pi / 2, within the range where sin.approx / cos.approx
+    // keep their stated absolute error
     g = __fmul2_rn(g, f2(-6.283185307179586f));
     float s0, c0, s1, c1;
     __sincosf(g.x, &s0, &c0);
     __sincosf(g.y, &s1, &c1);
-    re = __fmul2_rn(amp, make_float2(c0, c1));
-    im = __fmul2_rn(amp, make_float2(s0, s1));
+    if (UNIT && MODEL == XLMIMO_UPW) {
+        re = make_float2(c0, c1);
+        im = make_float2(s0, s1);
+    } else {
+        re = __fmul2_rn(amp, make_float2(c0, c1));
+        im = __fmul2_rn(amp, make_float2(s0, s1));
+    }
 }
 
 }  // namespace xl

@@ -9,8 +9,12 @@
 // 2^-16 |v|) or, after scaling user k's entries by s_k = 1/|h_k| at the
 // array centre so that they sit near 1, in FP16 (<= 2^-22 |v|; the scale is
 // divided out in FP64 at the end).  For K <= 32, Y = [X_hi ; X_lo] has 128
-// rows and one M = N = 128 MMA stream accumulates D = Y Y^T, whose four
-// 64 x 64 blocks sum to X_hi X_hi^T + X_hi X_lo^T + X_lo X_hi^T + X_lo X_lo^T.
+// rows and M = 128, N = 64 MMAs accumulate D = Y X_hi^T = [P ; Q], P =
+// X_hi X_hi^T and Q = X_lo X_hi^T, so that X X^T = P + Q + Q^T up to
+// X_lo X_lo^T (below 2^-18 relative with the round-to-nearest split).  Even
+// and odd stages go to two accumulators (TMEM columns 0-63 and 64-127)
+// summed at the end: tcgen05 rounds each accumulation towards zero, and
+// halving the steps per accumulator halves that bias.
 // For 32 < K <= 64, X_hi and X_lo have 128 rows each and three MMAs per
 // k-step accumulate X_hi X_hi^T + X_lo X_hi^T + X_hi X_lo^T into one
 // 128 x 128 accumulator.  The single-term BF16 variant keeps X_hi only.
@@ -75,18 +79,19 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
         }
         UserGeo u = make_user_geo(g, x, y);
         if (tid < K && !u.ok) atomicOr(&sh->bad, 1);
-        float sc = 1.0f;
+        // the BF16 paths generate entries without the amplitude constant and
+        // apply it to the Gram in FP64; the FP16 path scales user k's entries by
+        // 1/|h_k| at the array centre so that they sit near 1, and divides it out
+        double fac = amp_const(g, x, y);
         if (PREC == TCP_F16X3) {
-            // 1 / |h| at the array centre, so the scaled entries sit near 1
             const double rc = sqrt(x * x + y * y) * g.inv_lambda;  // distance in wavelengths
-            double amp_c = (MODEL == XLMIMO_UPW) ? (double)u.ampc
-                         : (MODEL == XLMIMO_PNUSW) ? (double)u.ampc / (rc * sqrt(rc))
-                                                   : (double)u.ampc / rc;
-            sc = (float)(1.0 / amp_c);
+            double amp_c = (MODEL == XLMIMO_UPW) ? fac : (MODEL == XLMIMO_PNUSW) ? fac / (rc * sqrt(rc)) : fac / rc;
+            const float sc = (float)(1.0 / amp_c);
             u.ampc *= sc;
+            fac = 1.0 / (double)sc;
         }
         sh->ug[tid] = u;
-        sh->scale[tid] = sc;
+        sh->fac[tid] = fac;
     }
     tc_fence_before();
     __syncthreads();
@@ -164,17 +169,19 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
                 uint32_t w[4][4];  // [component: Re hi, Im hi, Re lo, Im lo][packed pair]
                 // two instances of the slice: full (no per-element checks; every
                 // stage but a chunk's last) and partial (elements past the end are 0)
+                const float base = slice_base(pc, mf0 + 3.5f);  // phase at the slice centre
                 auto slice = [&](auto partial) {
 #pragma unroll
                     for (int i = 0; i < 8; i += 2) {
                         float2 re, im;
-                        gen_pair<MODEL>(pc, make_float2(mf0 + (float)i, mf0 + (float)(i + 1)), re, im);
+                        gen_pair<MODEL, PREC != TCP_F16X3>(pc, make_float2(mf0 + (float)i, mf0 + (float)(i + 1)),
+                                                            make_float2((float)i - 3.5f, (float)i - 2.5f), base, re, im);
                         if (decltype(partial)::value) {
                             if (i >= rem) { re.x = 0.f; im.x = 0.f; }
                             if (i + 1 >= rem) { re.y = 0.f; im.y = 0.f; }
                         }
-                        split2<PREC, KMAX == 32>(re.x, re.y, w[0][i >> 1], w[2][i >> 1]);
-                        split2<PREC, KMAX == 32>(im.x, im.y, w[1][i >> 1], w[3][i >> 1]);
+                        split2<PREC>(re.x, re.y, w[0][i >> 1], w[2][i >> 1]);
+                        split2<PREC>(im.x, im.y, w[1][i >> 1], w[3][i >> 1]);
                     }
                 };
                 if (rem >= 8) slice(std::integral_constant<bool, false>());
@@ -194,7 +201,7 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
     } else {
         // ---------------- MMA issuer (one lane; the others wait at the warp barrier)
         if (lane == 0) {
-            const uint32_t idesc = tc_idesc<PREC>();
+            const uint32_t idesc = tc_idesc<PREC, KMAX == 32 ? 64u : 128u>();
             for (int it = 0; it < nst; ++it) {
                 const int st = it % TC_STAGES;
                 if (!mbar_wait(&sh->full[st], (it / TC_STAGES) & 1, abort)) break;
@@ -202,11 +209,13 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
                 const uint32_t sa = smem_u32(stages + st * C::STAGE_BYTES);
 #pragma unroll
                 for (int kk = 0; kk < TC_T / 16; ++kk) {
-                    const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
                     const uint64_t hi = desc_sw128(sa + kk * 32);
                     if (KMAX == 32) {
-                        umma(tmem, hi, hi, idesc, acc);  // D += Y Y^T
+                        // D_(it & 1) += Y X_hi^T: A is the whole stage, B its first 64 rows
+                        const uint32_t acc = (it > 1 || kk > 0) ? 1u : 0u;
+                        umma(tmem + (uint32_t)(it & 1) * 64u, hi, hi, idesc, acc);
                     } else {
+                        const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
                         umma(tmem, hi, hi, idesc, acc);
                         if (PREC != TCP_BF16) {
                             const uint64_t lo = desc_sw128(sa + C::LO_OFFSET + kk * 32);
@@ -233,12 +242,13 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
         float v[32], u[32];
         if (KMAX == 32) {
+            // the two accumulators (the odd one is unwritten when the chunk has one stage)
 #pragma unroll
             for (int cb = 0; cb < 2; ++cb) {
                 tmem_ld32(trow + cb * 32, v);
                 tmem_ld32(trow + 64 + cb * 32, u);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) fold[m * C::FOLD_LD + cb * 32 + j] = v[j] + u[j];
+                for (int j = 0; j < 32; ++j) fold[m * C::FOLD_LD + cb * 32 + j] = nst > 1 ? v[j] + u[j] : v[j];
             }
         } else {
 #pragma unroll
@@ -252,22 +262,22 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
     tc_fence_before();
     __syncthreads();
     if (ok) {
-        // R (2 KMAX square) from the fold; complex Gram from R; FP16 scale removed
+        // R (2 KMAX square) from the fold; complex Gram from R times the per-user factors
         const int P = K * (K + 1) / 2;
         for (int q = tid; q < P; q += TC_THREADS) {
             int i = 0, rl = K, p = q;
             while (p >= rl) { p -= rl; ++i; --rl; }
             const int j = i + p;
-            auto R = [&](int r, int c) {
-                return KMAX == 32 ? fold[r * C::FOLD_LD + c] + fold[(r + 64) * C::FOLD_LD + c] : fold[r * C::FOLD_LD + c];
+            auto R = [&](int r, int c) {  // (X X^T)_rc
+                return KMAX == 32 ? fold[r * C::FOLD_LD + c] + fold[(r + 64) * C::FOLD_LD + c] +
+                                        fold[(c + 64) * C::FOLD_LD + r]
+                                  : fold[r * C::FOLD_LD + c];
             };
             double re = (double)(R(i, j) + R(KMAX + i, KMAX + j));
             double im = (double)(R(i, KMAX + j) - R(KMAX + i, j));
-            if (PREC == TCP_F16X3) {
-                const double us = 1.0 / ((double)sh->scale[i] * (double)sh->scale[j]);
-                re *= us;
-                im *= us;
-            }
+            const double us = sh->fac[i] * sh->fac[j];
+            re *= us;
+            im *= us;
             if (i == j) {
                 o[i * K + i] = make_double2(re, 0.0);
             } else {

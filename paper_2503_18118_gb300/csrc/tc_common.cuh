@@ -103,14 +103,14 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
 }
 
 // Instruction descriptor, kind::f16: 16-bit A and B (format 1 = BF16, 0 = F16),
-// FP32 accumulator, both K-major, M = N = 128.
-template <int PREC>
+// FP32 accumulator, both K-major, M = 128, N = 128 or 64.
+template <int PREC, uint32_t N = 128>
 __device__ __forceinline__ uint32_t tc_idesc() {
     const uint32_t fmt = PREC == TCP_F16X3 ? 0u : 1u;
     return (1u << 4)               // D format F32
            | (fmt << 7)            // A format
            | (fmt << 10)           // B format
-           | ((128u >> 3) << 17)   // N / 8
+           | ((N >> 3) << 17)      // N / 8
            | ((128u >> 4) << 24);  // M / 16
 }
 
@@ -154,7 +154,7 @@ struct TcShared {
     int abort;
     int bad;
     UserGeo ug[KMAX];
-    float scale[KMAX];  // FP16 path: per-user entry scale
+    double fac[KMAX];  // per-user factor of the Gram: G_ij = fac_i fac_j (accumulated sum)
     UserRef ref[2][KMAX];  // phase references of the current and the next span
 };
 
