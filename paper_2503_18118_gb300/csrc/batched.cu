@@ -177,11 +177,12 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
                         const PairConst pc =
                             make_pair_const(sh->ref[sp & 1][k], gpi.dprime_f, u.xl2, u.x2x2, k < K ? u.ampc : 0.f);
                         const float base = slice_base(pc, mf0 + 3.5f);  // phase at the slice centre
+                        const float dp = pc.dp.x, u0 = mf0 * dp;        // u = m spacing/lambda
                         auto slice = [&](auto partial) {
 #pragma unroll
                             for (int i = 0; i < 8; i += 2) {
                                 float2 re, im;
-                                gen_pair<MODEL, PREC != TCP_F16X3>(pc, make_float2(mf0 + (float)i, mf0 + (float)(i + 1)),
+                                gen_pair<MODEL, PREC != TCP_F16X3>(pc, make_float2(fmaf((float)i, dp, u0), fmaf((float)(i + 1), dp, u0)),
                                                             make_float2((float)i - 3.5f, (float)i - 2.5f), base, re, im);
                                 if (decltype(partial)::value) {
                                     if (i >= rem) { re.x = 0.f; im.x = 0.f; }

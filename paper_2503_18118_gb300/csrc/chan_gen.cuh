@@ -218,12 +218,13 @@ __device__ __forceinline__ float slice_base(const PairConst& c, float mc) {
     return __fadd_rn(__fmaf_rn(mc, c.al, c.frac0), frac_rn(__fmul_rn(mc, c.ah)));
 }
 
-// Entries at offsets mf.x, mf.y from the span centre (|mf| <= 256), which
-// are t.x, t.y from the centre of their slice (phase base, from slice_base):
+// Entries at offsets m.x, m.y from the span centre (|m| <= 256; u = m
+// spacing/lambda), which are t.x, t.y from the centre of their slice (phase
+// base, from slice_base):
 // re = amp cos(phi), im = -amp sin(phi) for each of the two.  UNIT leaves the
 // model's amplitude constant out (the caller applies it to the Gram in FP64).
 template <int MODEL, bool UNIT = false>
-__device__ __forceinline__ void gen_pair(const PairConst& c, float2 mf, float2 t, float base, float2& re,
+__device__ __forceinline__ void gen_pair(const PairConst& c, float2 u, float2 t, float base, float2& re,
                                          float2& im) {
     const float2 m1 = f2(-1.0f);
     float2 g = __ffma2_rn(t, c.af, f2(base));   // |g| <= 1 + 7/4
@@ -231,7 +232,6 @@ __device__ __forceinline__ void gen_pair(const PairConst& c, float2 mf, float2 t
     if (MODEL == XLMIMO_UPW) {
         if (!UNIT) amp = c.ampc;
     } else {
-        float2 u = __fmul2_rn(mf, c.dp);
         float2 nu2 = __fmul2_rn(u, make_float2(-u.x, -u.y));  // -u^2
         float2 en = __fadd2_rn(c.e0, u);
         float2 r2 = __ffma2_rn(en, en, c.xl2);

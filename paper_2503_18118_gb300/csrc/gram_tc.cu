@@ -129,12 +129,17 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
                 soff[slot][c] = (uint32_t)((f >> 3) * 1024 + rin * 128 + ((warp ^ rin) << 4));
             }
         PairConst pc = make_pair_const(UserRef{0.f, 0.f, 0.f, 0.f, 1.f, 0.f}, gp.dprime_f, 0.f, 0.f, 0.f);
-        int64_t nc = 0;
+        // stage bookkeeping kept incremental and 32-bit: ring slot st and its
+        // wrap count, this warp's slice offset from the span centre (mf0, an
+        // exact small integer in FP32), valid elements of the last stage
+        const uint32_t sbase = smem_u32(stages);
+        const int last_rem = (int)(nend - nbeg - (int64_t)(nst - 1) * TC_T) - warp * 8;
+        int st = 0, wraps = 0;
+        float mf0 = 0.f;
         bool dead = false;
         for (int it = 0; it < nst; ++it) {
-            const int st = it % TC_STAGES;
             const int sp = it / SPAN_ST;
-            if (it % SPAN_ST == 0) {
+            if ((it & (SPAN_ST - 1)) == 0) {
                 uint32_t stop;
                 const uint32_t mine = (dead || *abort) ? 1u : 0u;
                 asm volatile(
@@ -143,22 +148,25 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
                     : "r"(mine)
                     : "memory");
                 if (stop) break;
-                nc = nbeg + (int64_t)sp * TC_REF_SPAN + TC_REF_SPAN / 2;
+                mf0 = (float)(warp * 8 - TC_REF_SPAN / 2);
                 if (C::SLOTS == 1) {
                     const UserGeo& u = sh->ug[lane];
                     pc = make_pair_const(sh->ref[sp & 1][lane], gp.dprime_f, u.xl2, u.x2x2, lane < K ? u.ampc : 0.f);
                 }
                 if (warp == ((sp + 1) & 7) && sp + 1 < nsp) make_refs(sp + 1);
+            } else {
+                mf0 += (float)TC_T;
             }
+            const int cur = st;
+            const int wcur = wraps;
+            if (++st == TC_STAGES) { st = 0; ++wraps; }
             if (dead) continue;
-            if (it >= TC_STAGES && !mbar_wait(&sh->empty[st], ((it / TC_STAGES) - 1) & 1, abort)) {
+            if (wcur > 0 && !mbar_wait(&sh->empty[cur], (wcur - 1) & 1, abort)) {
                 dead = true;
                 continue;
             }
-            const int64_t n0 = nbeg + (int64_t)it * TC_T;
-            const int rem = (int)min((int64_t)TC_T, nend - n0) - warp * 8;  // valid elements of this slice
-            const float mf0 = (float)(int)(n0 + warp * 8 - nc);
-            const uint32_t sb = smem_u32(stages + st * C::STAGE_BYTES);
+            const int rem = it == nst - 1 ? last_rem : 8;  // valid elements of this slice
+            const uint32_t sb = sbase + (uint32_t)cur * C::STAGE_BYTES;
 #pragma unroll
             for (int slot = 0; slot < C::SLOTS; ++slot) {
                 const int k = lane + 32 * slot;
@@ -170,11 +178,12 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
                 // two instances of the slice: full (no per-element checks; every
                 // stage but a chunk's last) and partial (elements past the end are 0)
                 const float base = slice_base(pc, mf0 + 3.5f);  // phase at the slice centre
+                const float dp = pc.dp.x, u0 = mf0 * dp;        // u = m spacing/lambda
                 auto slice = [&](auto partial) {
 #pragma unroll
                     for (int i = 0; i < 8; i += 2) {
                         float2 re, im;
-                        gen_pair<MODEL, PREC != TCP_F16X3>(pc, make_float2(mf0 + (float)i, mf0 + (float)(i + 1)),
+                        gen_pair<MODEL, PREC != TCP_F16X3>(pc, make_float2(fmaf((float)i, dp, u0), fmaf((float)(i + 1), dp, u0)),
                                                             make_float2((float)i - 3.5f, (float)i - 2.5f), base, re, im);
                         if (decltype(partial)::value) {
                             if (i >= rem) { re.x = 0.f; im.x = 0.f; }
@@ -196,7 +205,7 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
                 }
             }
             fence_async_smem();
-            mbar_arrive(&sh->full[st]);
+            mbar_arrive(&sh->full[cur]);
         }
     } else {
         // ---------------- MMA issuer (one lane; the others wait at the warp barrier)
