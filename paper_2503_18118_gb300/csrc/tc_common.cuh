@@ -185,8 +185,10 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t&
         __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
         hi = *reinterpret_cast<uint32_t*>(&h);
         if (PREC == TCP_BF16X3) {
-            float2 hf = __bfloat1622float2(h);
-            __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+            // exact remainders a - hi, b - hi in one packed FMA
+            const float2 hf = __bfloat1622float2(h);
+            const float2 r = __fadd2_rn(make_float2(a, b), make_float2(-hf.x, -hf.y));
+            __nv_bfloat162 l = __floats2bfloat162_rn(r.x, r.y);
             lo = *reinterpret_cast<uint32_t*>(&l);
         } else {
             lo = 0u;
