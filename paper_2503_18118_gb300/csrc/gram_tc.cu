@@ -12,22 +12,23 @@
 // rows and M = 128, N = 64 MMAs accumulate D = Y X_hi^T = [P ; Q], P =
 // X_hi X_hi^T and Q = X_lo X_hi^T, so that X X^T = P + Q + Q^T up to
 // X_lo X_lo^T (below 2^-18 relative with the round-to-nearest split).  Even
-// and odd stages go to two accumulators (TMEM columns 0-63 and 64-127)
-// summed at the end: tcgen05 rounds each accumulation towards zero, and
-// halving the steps per accumulator halves that bias.
+// and odd 64-element sub-tiles go to two accumulators (TMEM columns 0-63 and
+// 64-127) summed at the end: tcgen05 rounds each accumulation towards zero,
+// and halving the steps per accumulator halves that bias.
 // For 32 < K <= 64, X_hi and X_lo have 128 rows each and three MMAs per
 // k-step accumulate X_hi X_hi^T + X_lo X_hi^T + X_hi X_lo^T into one
 // 128 x 128 accumulator.  The single-term BF16 variant keeps X_hi only.
 //
 // Pipeline (one CTA per trial chunk, 9 warps):
-//   warps 0-7  generate 64-element stages: lane = user, warp = 8-element
-//              slice; each thread writes 16-byte rows of the K-major,
-//              128-byte-swizzled BF16 tile, fences the async proxy and
-//              arrives on the stage's "full" barrier;
+//   warps 0-7  generate ring stages (two of 128 elements for K <= 32, three
+//              of 64 for K <= 64): lane = user, warp = one 8-element slice
+//              per 64-element sub-tile; each thread writes 16-byte rows of
+//              the K-major, 128-byte-swizzled 16-bit tile, fences the async
+//              proxy and arrives on the stage's "full" barrier;
 //   warp 8     allocates 128 TMEM columns; one thread waits for each full
-//              stage, issues four K=16 tcgen05.mma into TMEM and commits to
-//              the stage's "empty" barrier (generators reuse the stage once
-//              it fires) and, at the end, to "done";
+//              stage, issues four K=16 tcgen05.mma per sub-tile into TMEM and
+//              commits to the stage's "empty" barrier (generators reuse the
+//              stage once it fires) and, at the end, to "done";
 //   warps 0-3  read the accumulator back (tcgen05.ld), fold the blocks and
 //              write the complex Gram in FP64.
 // Every wait is bounded; a wait that gives up marks the trial (NaN output),
@@ -40,23 +41,36 @@
 
 namespace xl {
 
+// Ring of the Gram kernel: NRING stages of T elements, each SUBS 64-element
+// sub-tiles of the K-major swizzled layout (TcCfg::STAGE_BYTES each).  K <= 32
+// uses two stages of 128 elements, so the per-stage bookkeeping of a
+// generator thread is paid once per 16 entries; K <= 64 three of 64.
+template <int KMAX>
+struct GtRing {
+    static constexpr int SUBS = KMAX == 32 ? 2 : 1;
+    static constexpr int T = TC_T * SUBS;
+    static constexpr int NRING = KMAX == 32 ? 2 : TC_STAGES;
+    static constexpr uint32_t BYTES = (uint32_t)TcCfg<KMAX>::STAGE_BYTES * SUBS;  // per ring stage
+};
+
 template <int MODEL, int KMAX, int PREC>
 __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
     gram_tc_kernel(Geom g, GenParams gp, const double* __restrict__ users, int K, int S, int64_t chunk,
                    double2* __restrict__ out) {
     using C = TcCfg<KMAX>;
+    using RG = GtRing<KMAX>;
     extern __shared__ unsigned char smem_raw[];
     // stages must be 1024-byte aligned for the 128-byte swizzle
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     unsigned char* stages = base;
-    TcShared<KMAX>* sh = reinterpret_cast<TcShared<KMAX>*>(base + TC_STAGES * C::STAGE_BYTES);
+    TcShared<KMAX>* sh = reinterpret_cast<TcShared<KMAX>*>(base + RG::NRING * RG::BYTES);
     float* fold = reinterpret_cast<float*>(base);  // epilogue reuses the stages
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int b = blockIdx.x, s = blockIdx.y;
 
     if (tid == 0) {
-        for (int i = 0; i < TC_STAGES; ++i) {
+        for (int i = 0; i < RG::NRING; ++i) {
             mbar_init(&sh->full[i], TC_GEN_THREADS);
             mbar_init(&sh->empty[i], 1);
         }
@@ -101,7 +115,7 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
 
     const int64_t nbeg = (int64_t)s * chunk;
     const int64_t nend = min(g.N, nbeg + chunk);
-    const int nst = (int)((nend - nbeg + TC_T - 1) / TC_T);
+    const int nst = (int)((nend - nbeg + RG::T - 1) / RG::T);
 
     if (warp < 8) {
         // ---------------- generators: lane = user (and user + 32), warp = 8-element slice.
@@ -111,7 +125,7 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
         // the eight generator warps meet at a named barrier at every span
         // start.  That barrier also votes on stopping, so that after an abort
         // all 256 generator threads leave the loop together.
-        constexpr int SPAN_ST = TC_REF_SPAN / TC_T;  // stages per span
+        constexpr int SPAN_ST = TC_REF_SPAN / RG::T;  // stages per span
         const int nsp = (nst + SPAN_ST - 1) / SPAN_ST;
         auto make_refs = [&](int sp) {
             const long long ncs = (long long)(nbeg + (int64_t)sp * TC_REF_SPAN + TC_REF_SPAN / 2);
@@ -133,7 +147,7 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
         // wrap count, this warp's slice offset from the span centre (mf0, an
         // exact small integer in FP32), valid elements of the last stage
         const uint32_t sbase = smem_u32(stages);
-        const int last_rem = (int)(nend - nbeg - (int64_t)(nst - 1) * TC_T) - warp * 8;
+        const int last_rem = (int)(nend - nbeg - (int64_t)(nst - 1) * RG::T) - warp * 8;
         int st = 0, wraps = 0;
         float mf0 = 0.f;
         bool dead = false;
@@ -155,18 +169,18 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
                 }
                 if (warp == ((sp + 1) & 7) && sp + 1 < nsp) make_refs(sp + 1);
             } else {
-                mf0 += (float)TC_T;
+                mf0 += (float)RG::T;
             }
             const int cur = st;
             const int wcur = wraps;
-            if (++st == TC_STAGES) { st = 0; ++wraps; }
+            if (++st == RG::NRING) { st = 0; ++wraps; }
             if (dead) continue;
             if (wcur > 0 && !mbar_wait(&sh->empty[cur], (wcur - 1) & 1, abort)) {
                 dead = true;
                 continue;
             }
-            const int rem = it == nst - 1 ? last_rem : 8;  // valid elements of this slice
-            const uint32_t sb = sbase + (uint32_t)cur * C::STAGE_BYTES;
+            const int rem = it == nst - 1 ? last_rem : RG::T;  // valid elements from this warp's first slice on
+            const uint32_t sb = sbase + (uint32_t)cur * RG::BYTES;
 #pragma unroll
             for (int slot = 0; slot < C::SLOTS; ++slot) {
                 const int k = lane + 32 * slot;
@@ -174,34 +188,40 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
                     const UserGeo& u = sh->ug[k];
                     pc = make_pair_const(sh->ref[sp & 1][k], gp.dprime_f, u.xl2, u.x2x2, k < K ? u.ampc : 0.f);
                 }
-                uint32_t w[4][4];  // [component: Re hi, Im hi, Re lo, Im lo][packed pair]
-                // two instances of the slice: full (no per-element checks; every
-                // stage but a chunk's last) and partial (elements past the end are 0)
-                const float base = slice_base(pc, mf0 + 3.5f);  // phase at the slice centre
-                const float dp = pc.dp.x, u0 = mf0 * dp;        // u = m spacing/lambda
-                auto slice = [&](auto partial) {
 #pragma unroll
-                    for (int i = 0; i < 8; i += 2) {
-                        float2 re, im;
-                        gen_pair<MODEL, PREC != TCP_F16X3>(pc, make_float2(fmaf((float)i, dp, u0), fmaf((float)(i + 1), dp, u0)),
-                                                            make_float2((float)i - 3.5f, (float)i - 2.5f), base, re, im);
-                        if (decltype(partial)::value) {
-                            if (i >= rem) { re.x = 0.f; im.x = 0.f; }
-                            if (i + 1 >= rem) { re.y = 0.f; im.y = 0.f; }
+                for (int sub = 0; sub < RG::SUBS; ++sub) {
+                    const float mfs = mf0 + (float)(sub * TC_T);  // this slice's first offset
+                    const int rs = rem - sub * TC_T;              // its valid elements (<= 0: none)
+                    uint32_t w[4][4];  // [component: Re hi, Im hi, Re lo, Im lo][packed pair]
+                    // two instances of the slice: full (no per-element checks; every
+                    // stage but a chunk's last) and partial (elements past the end are 0)
+                    const float base = slice_base(pc, mfs + 3.5f);  // phase at the slice centre
+                    const float dp = pc.dp.x, u0 = mfs * dp;        // u = m spacing/lambda
+                    auto slice = [&](auto partial) {
+#pragma unroll
+                        for (int i = 0; i < 8; i += 2) {
+                            float2 re, im;
+                            gen_pair<MODEL, PREC != TCP_F16X3>(pc, make_float2(fmaf((float)i, dp, u0), fmaf((float)(i + 1), dp, u0)),
+                                                                make_float2((float)i - 3.5f, (float)i - 2.5f), base, re, im);
+                            if (decltype(partial)::value) {
+                                if (i >= rs) { re.x = 0.f; im.x = 0.f; }
+                                if (i + 1 >= rs) { re.y = 0.f; im.y = 0.f; }
+                            }
+                            split2<PREC>(re.x, re.y, w[0][i >> 1], w[2][i >> 1]);
+                            split2<PREC>(im.x, im.y, w[1][i >> 1], w[3][i >> 1]);
                         }
-                        split2<PREC>(re.x, re.y, w[0][i >> 1], w[2][i >> 1]);
-                        split2<PREC>(im.x, im.y, w[1][i >> 1], w[3][i >> 1]);
-                    }
-                };
-                if (rem >= 8) slice(std::integral_constant<bool, false>());
-                else slice(std::integral_constant<bool, true>());
-                const int ncomp = (PREC == TCP_BF16 && KMAX == 64) ? 2 : 4;  // the one-term K>32 MMA reads hi only
+                    };
+                    if (rs >= 8) slice(std::integral_constant<bool, false>());
+                    else slice(std::integral_constant<bool, true>());
+                    const int ncomp = (PREC == TCP_BF16 && KMAX == 64) ? 2 : 4;  // the one-term K>32 MMA reads hi only
+                    const uint32_t ss = sb + (uint32_t)(sub * C::STAGE_BYTES);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    if (c >= ncomp) break;
-                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(sb + soff[slot][c]), "r"(w[c][0]),
-                                 "r"(w[c][1]), "r"(w[c][2]), "r"(w[c][3])
-                                 : "memory");
+                    for (int c = 0; c < 4; ++c) {
+                        if (c >= ncomp) break;
+                        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ss + soff[slot][c]), "r"(w[c][0]),
+                                     "r"(w[c][1]), "r"(w[c][2]), "r"(w[c][3])
+                                     : "memory");
+                    }
                 }
             }
             fence_async_smem();
@@ -212,24 +232,28 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
         if (lane == 0) {
             const uint32_t idesc = tc_idesc<PREC, KMAX == 32 ? 64u : 128u>();
             for (int it = 0; it < nst; ++it) {
-                const int st = it % TC_STAGES;
-                if (!mbar_wait(&sh->full[st], (it / TC_STAGES) & 1, abort)) break;
+                const int st = it % RG::NRING;
+                if (!mbar_wait(&sh->full[st], (it / RG::NRING) & 1, abort)) break;
                 tc_fence_after();
-                const uint32_t sa = smem_u32(stages + st * C::STAGE_BYTES);
+                const uint32_t sa0 = smem_u32(stages) + (uint32_t)st * RG::BYTES;
 #pragma unroll
-                for (int kk = 0; kk < TC_T / 16; ++kk) {
-                    const uint64_t hi = desc_sw128(sa + kk * 32);
-                    if (KMAX == 32) {
-                        // D_(it & 1) += Y X_hi^T: A is the whole stage, B its first 64 rows
-                        const uint32_t acc = (it > 1 || kk > 0) ? 1u : 0u;
-                        umma(tmem + (uint32_t)(it & 1) * 64u, hi, hi, idesc, acc);
-                    } else {
-                        const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
-                        umma(tmem, hi, hi, idesc, acc);
-                        if (PREC != TCP_BF16) {
-                            const uint64_t lo = desc_sw128(sa + C::LO_OFFSET + kk * 32);
-                            umma(tmem, lo, hi, idesc, 1u);
-                            umma(tmem, hi, lo, idesc, 1u);
+                for (int sub = 0; sub < RG::SUBS; ++sub) {
+                    const uint32_t sa = sa0 + (uint32_t)(sub * C::STAGE_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < TC_T / 16; ++kk) {
+                        const uint64_t hi = desc_sw128(sa + kk * 32);
+                        if (KMAX == 32) {
+                            // D_sub += Y X_hi^T: A is the whole sub-tile, B its first 64 rows
+                            const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+                            umma(tmem + (uint32_t)sub * 64u, hi, hi, idesc, acc);
+                        } else {
+                            const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+                            umma(tmem, hi, hi, idesc, acc);
+                            if (PREC != TCP_BF16) {
+                                const uint64_t lo = desc_sw128(sa + C::LO_OFFSET + kk * 32);
+                                umma(tmem, lo, hi, idesc, 1u);
+                                umma(tmem, hi, lo, idesc, 1u);
+                            }
                         }
                     }
                 }
@@ -251,13 +275,13 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
         float v[32], u[32];
         if (KMAX == 32) {
-            // the two accumulators (the odd one is unwritten when the chunk has one stage)
+            // the two accumulators (one per sub-tile of every stage)
 #pragma unroll
             for (int cb = 0; cb < 2; ++cb) {
                 tmem_ld32(trow + cb * 32, v);
                 tmem_ld32(trow + 64 + cb * 32, u);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) fold[m * C::FOLD_LD + cb * 32 + j] = nst > 1 ? v[j] + u[j] : v[j];
+                for (int j = 0; j < 32; ++j) fold[m * C::FOLD_LD + cb * 32 + j] = v[j] + u[j];
             }
         } else {
 #pragma unroll
@@ -306,7 +330,7 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
 
 template <int KMAX>
 static size_t tc_smem_bytes() {
-    return 1024 + TC_STAGES * TcCfg<KMAX>::STAGE_BYTES + sizeof(TcShared<KMAX>);
+    return 1024 + GtRing<KMAX>::NRING * GtRing<KMAX>::BYTES + sizeof(TcShared<KMAX>);
 }
 
 using TcKernel = void (*)(Geom, GenParams, const double*, int, int, int64_t, double2*);

@@ -74,6 +74,7 @@ __device__ __forceinline__ uint64_t global_ns() {
 // time, or once another thread has aborted, it gives up, sets *abort and
 // returns false.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    if (mbar_try_wait(bar, parity)) return true;  // usual case: no timer read
     const uint64_t t0 = global_ns();
     for (uint32_t it = 0;; ++it) {
         if (mbar_try_wait_sleep(bar, parity, 1000u)) return true;
