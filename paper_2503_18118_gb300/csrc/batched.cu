@@ -141,13 +141,17 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
                     const int rin = f & 7;
                     soff[slot][c] = (uint32_t)((f >> 3) * 1024 + rin * 128 + ((warp ^ rin) << 4));
                 }
-            int64_t nc = 0;
+            // stage bookkeeping incremental and 32-bit (see gram_tc_kernel): ring
+            // slot and wrap count continue from the CTA's previous items
+            const uint32_t sbase = smem_u32(stages);
+            const int last_rem = (int)(nend - nbeg - (int64_t)(nst - 1) * TC_T) - warp * 8;
+            int st = (int)(gs % TC_STAGES);
+            long long wraps = gs / TC_STAGES;
+            float mf0 = 0.f;
             bool dead = false;
             for (int it = 0; it < nst; ++it) {
-                const long long gsi = gs + it;
-                const int st = (int)(gsi % TC_STAGES);
                 const int sp = it / SPAN_ST;
-                if (it % SPAN_ST == 0) {
+                if ((it & (SPAN_ST - 1)) == 0) {
                     uint32_t stop;
                     const uint32_t mine = (dead || *abort) ? 1u : 0u;
                     asm volatile(
@@ -156,18 +160,21 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
                         : "r"(mine)
                         : "memory");
                     if (stop) break;
-                    nc = nbeg + (int64_t)sp * TC_REF_SPAN + TC_REF_SPAN / 2;
+                    mf0 = (float)(warp * 8 - TC_REF_SPAN / 2);
                     if (warp == ((sp + 1) & 7) && sp + 1 < nsp) make_refs(sp + 1);
+                } else {
+                    mf0 += (float)TC_T;
                 }
+                const int cur = st;
+                const long long wcur = wraps;
+                if (++st == TC_STAGES) { st = 0; ++wraps; }
                 if (dead) continue;
-                if (gsi >= TC_STAGES && !mbar_wait(&sh->empty[st], (uint32_t)(((gsi / TC_STAGES) - 1) & 1), abort)) {
+                if (wcur > 0 && !mbar_wait(&sh->empty[cur], (uint32_t)((wcur - 1) & 1), abort)) {
                     dead = true;
                     continue;
                 }
-                const int64_t n0 = nbeg + (int64_t)it * TC_T;
-                const int rem = (int)min((int64_t)TC_T, nend - n0) - warp * 8;
-                const float mf0 = (float)(int)(n0 + warp * 8 - nc);
-                const uint32_t sb = smem_u32(stages + st * RCfg::STAGE_BYTES);
+                const int rem = it == nst - 1 ? last_rem : 8;
+                const uint32_t sb = sbase + (uint32_t)cur * RCfg::STAGE_BYTES;
 #pragma unroll
                 for (int slot = 0; slot < 2; ++slot) {
                     const int k = lane + 32 * slot;
@@ -210,7 +217,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
                     }
                 }
                 fence_async_smem();
-                mbar_arrive(&sh->full[st]);
+                mbar_arrive(&sh->full[cur]);
             }
         } else {
             if (lane == 0) {

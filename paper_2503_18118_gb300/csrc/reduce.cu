@@ -16,11 +16,16 @@
 
 namespace xl {
 
+// One warp per trial (lane = user), summed by a fixed shuffle tree, so the
+// FP64 logarithms of a trial run side by side rather than one after another.
 __global__ void sumrate_kernel(const double* __restrict__ sinr, int K, int B, double* __restrict__ rate) {
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wpb = blockDim.x >> 5;
+    for (int64_t b = blockIdx.x * wpb + (threadIdx.x >> 5); b < B; b += (int64_t)gridDim.x * wpb) {
         double r = 0.0;
-        for (int k = 0; k < K; ++k) r += log2(1.0 + sinr[(int64_t)b * K + k]);
-        rate[b] = r;
+        for (int k = lane; k < K; k += 32) r += log2(1.0 + sinr[b * K + k]);
+        for (int off = 16; off > 0; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
+        if (lane == 0) rate[b] = r;
     }
 }
 
@@ -83,8 +88,8 @@ int launch_stats_strided(const double* x, int B, int stride, double* out, cudaSt
 }
 
 int launch_sumrate(const double* sinr, int K, int B, double* rate, double* stats, cudaStream_t st) {
-    int threads = 256;
-    int blocks = (B + threads - 1) / threads;
+    const int threads = 256, wpb = threads / 32;
+    int blocks = (B + wpb - 1) / wpb;
     if (blocks > 16 * num_sms()) blocks = 16 * num_sms();
     sumrate_kernel<<<blocks, threads, 0, st>>>(sinr, K, B, rate);
     int rc = cuda_status(cudaGetLastError(), "sumrate launch");
