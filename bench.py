@@ -548,7 +548,8 @@ def main():
                 "kernel_ms": gram_ms,
                 "peak_source": f"MUFU: {sms} SMs x 16 ops/clk x {max_mhz:.0f} MHz (unit counts and max clock)",
                 "algorithmic": "4 transcendental ops (rsqrt, rcp, sin, cos) x N K channel entries per launch",
-                "tensor_tflops": 2.0 * 128 * 128 * N * B / (gram_ms / 1e3) / 1e12,
+                # issued MMA work: K <= 32, M = 128, N = 64 per element; K <= 64, three 128 x 128
+                "tensor_tflops": (2.0 * 128 * 64 if K <= 32 else 3 * 2.0 * 128 * 128) * N * B / (gram_ms / 1e3) / 1e12,
                 "tensor_peak_tflops": float(peaks.get("bf16_tflops", 1935.2))}
     elif path == "f64":
         achieved = gram_flops / (gram_ms / 1e3) / 1e12

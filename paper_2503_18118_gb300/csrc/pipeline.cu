@@ -1,5 +1,7 @@
 // xlmimo_mc_step: one Monte-Carlo step over a batch, pipelined over two
-// streams.  The exact-Gram kernels (channel generation on the FP32 and MUFU
+// streams.  The receivers compute their sum rates themselves, and the exact
+// and the closed-form receivers share one launch so that their FP64 and FP32
+// work run side by side on every SM.  The exact-Gram kernels (channel generation on the FP32 and MUFU
 // pipes, contraction on the tensor cores) and the receivers (FP64 pipe) use
 // disjoint execution units, so piece c's Gram on the caller's stream runs
 // next to piece c-1's receivers on a library stream; events order each
@@ -107,16 +109,18 @@ extern "C" int xlmimo_mc_step(const xlmimo_mc_batch* j, void* stream) {
         if (rc) break;
         const double* pw = j->power + (size_t)b0 * K;
         const double* nz = j->noise + b0;
-        rc = launch_beamform(gm, nullptr, pw, nz, K, nb, j->scheme, j->power_mode, j->sinr + (size_t)b0 * K,
-                             j->status + b0, j->capacity ? j->capacity + b0 : nullptr, s1);
-        if (!rc) rc = launch_sumrate(j->sinr + (size_t)b0 * K, K, nb, j->rate + b0, nullptr, s1);
-        if (!rc && j->cf_scheme >= 0) {
+        const BfJob exact = {gm, nullptr, pw, nz, j->scheme, j->sinr + (size_t)b0 * K, j->status + b0,
+                             j->capacity ? j->capacity + b0 : nullptr, j->rate + b0};
+        if (j->cf_scheme >= 0) {
+            // closed form first, then both receivers (and their sum rates) in one launch
             double* gc = j->gram_cf + (size_t)b0 * KK * 2;
             rc = launch_closed_form(g, u, K, nb, gc, s1);
-            if (!rc)
-                rc = launch_beamform(gc, gm, pw, nz, K, nb, j->cf_scheme, j->power_mode, j->sinr_cf + (size_t)b0 * K,
-                                     j->status_cf + b0, nullptr, s1);
-            if (!rc) rc = launch_sumrate(j->sinr_cf + (size_t)b0 * K, K, nb, j->rate_cf + b0, nullptr, s1);
+            const BfJob cf = {gc, gm, pw, nz, j->cf_scheme, j->sinr_cf + (size_t)b0 * K, j->status_cf + b0, nullptr,
+                              j->rate_cf + b0};
+            if (!rc) rc = launch_beamform_pair(exact, cf, K, nb, j->power_mode, s1);
+        } else {
+            rc = launch_beamform(gm, nullptr, pw, nz, K, nb, j->scheme, j->power_mode, exact.sinr, exact.status,
+                                 exact.cap, s1, exact.rate);
         }
         if (!rc && j->t > 0.0) rc = launch_saturation(u, K, nb, j->t, g.spacing, j->sat + (size_t)b0 * 3, s1);
     }

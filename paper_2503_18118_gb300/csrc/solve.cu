@@ -668,17 +668,46 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
 }
 
 
+// rate_t = sum_k log2(1 + SINR_k) of the trial just computed (Sec. V-C), by
+// warp 0 in the same order as sumrate_kernel (lane-strided sums, then a fixed
+// shuffle tree).
+__device__ void trial_rate(const double* sinr_t, int K, double* rate_t) {
+    __syncthreads();  // every thread's SINR writes are visible to the CTA
+    if (threadIdx.x < 32) {
+        double r = 0.0;
+        for (int k = threadIdx.x; k < K; k += 32) r += log2(1.0 + sinr_t[k]);
+        for (int off = 16; off > 0; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
+        if (threadIdx.x == 0) *rate_t = r;
+    }
+}
+
 __global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* __restrict__ gfil,
                                                                  const double2* __restrict__ gtru, int matched,
                                                                  const double* __restrict__ power,
                                                                  const double* __restrict__ noise, int K,
                                                                  int scheme, int power_mode,
                                                                  double* __restrict__ sinr, int* __restrict__ status,
-                                                                 double* __restrict__ cap) {
+                                                                 double* __restrict__ cap, double* __restrict__ rate) {
     const int64_t b = blockIdx.x;
     const int64_t KK = (int64_t)K * K;
     beamform_trial(gfil + b * KK, gtru + b * KK, matched, power + b * K, noise[b], K, scheme, power_mode,
                    sinr + b * K, status + b, cap ? cap + b : nullptr);
+    if (rate) trial_rate(sinr + b * K, K, rate + b);
+}
+
+// Two receiver jobs over the same trials in one launch, CTAs interleaved
+// (even: job 0, odd: job 1), so that every SM holds both kinds at once: the
+// matched MMSE receiver keeps the FP64 pipe busy with its Cholesky while the
+// modified-ZF one works mostly in double-float on the FP32 pipe.
+__global__ void __launch_bounds__(SOLVE_THREADS) beamform_pair_kernel(BfJob j0, BfJob j1, int K, int power_mode) {
+    const BfJob j = (blockIdx.x & 1) ? j1 : j0;
+    const int64_t b = blockIdx.x >> 1;
+    const int64_t KK = (int64_t)K * K;
+    const double2* gf = reinterpret_cast<const double2*>(j.gf) + b * KK;
+    const double2* gt = reinterpret_cast<const double2*>(j.gt ? j.gt : j.gf) + b * KK;
+    beamform_trial(gf, gt, j.gt == nullptr ? 1 : 0, j.power + b * K, j.noise[b], K, j.scheme, power_mode,
+                   j.sinr + b * K, j.status + b, j.cap ? j.cap + b : nullptr);
+    if (j.rate) trial_rate(j.sinr + b * K, K, j.rate + b);
 }
 
 __global__ void __launch_bounds__(SOLVE_THREADS) beamform_ragged_kernel(const DevInst* __restrict__ insts,
@@ -707,7 +736,8 @@ void beamform_trial_launch_bucket(const DevInst* insts, const int* list, int n, 
 }
 
 int launch_beamform(const double* gf, const double* gt, const double* power, const double* noise, int K, int B,
-                    int scheme, int power_mode, double* sinr, int* status, double* cap, cudaStream_t st) {
+                    int scheme, int power_mode, double* sinr, int* status, double* cap, cudaStream_t st,
+                    double* rate) {
     int matched = (gt == nullptr || gt == gf) ? 1 : 0;
     if (!gt) gt = gf;
     size_t KK = (size_t)K * K;
@@ -715,7 +745,20 @@ int launch_beamform(const double* gf, const double* gt, const double* power, con
     cudaError_t e = cudaFuncSetAttribute(beamform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return cuda_status(e, "beamform attribute");
     beamform_kernel<<<B, SOLVE_THREADS, smem, st>>>((const double2*)gf, (const double2*)gt, matched, power, noise, K,
-                                                    scheme, power_mode, sinr, status, cap);
+                                                    scheme, power_mode, sinr, status, cap, rate);
+    return cuda_status(cudaGetLastError(), "beamform launch");
+}
+
+int launch_beamform_pair(const BfJob& j0, const BfJob& j1, int K, int B, int power_mode, cudaStream_t st) {
+    if (B == 0) return XLMIMO_OK;
+    BfJob a = j0, c = j1;
+    if (a.gt == a.gf) a.gt = nullptr;  // matched
+    if (c.gt == c.gf) c.gt = nullptr;
+    size_t KK = (size_t)K * K;
+    size_t smem = 2 * KK * sizeof(cd) + 2 * XLMIMO_MAX_USERS * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(beamform_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return cuda_status(e, "beamform attribute");
+    beamform_pair_kernel<<<2 * (int64_t)B, SOLVE_THREADS, smem, st>>>(a, c, K, power_mode);
     return cuda_status(cudaGetLastError(), "beamform launch");
 }
 
