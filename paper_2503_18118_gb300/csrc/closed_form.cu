@@ -45,22 +45,39 @@ __global__ void closed_form_kernel(Geom g, const double* __restrict__ users, int
     const int64_t n_off = (int64_t)B * P;
     const int64_t total = n_off + (int64_t)B * K;
     const float c2f = (float)(g.lambda * g.lambda / (16.0 * 3.14159265358979323846 * 3.14159265358979323846));
+    // 32-bit index arithmetic whenever the index space fits (a 64-bit division
+    // per entry costs more than the entry's arithmetic)
+    const bool narrow = total <= 0x7FFFFFFF;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         int64_t b;
         int i, j;
         if (e < n_off) {
-            b = e / P;
-            int p = (int)(e - b * P);
-            // strict upper-triangle index p -> (i, j), row by row
-            i = 0;
-            int rowlen = K - 1;
-            while (p >= rowlen) { p -= rowlen; ++i; --rowlen; }
-            j = i + 1 + p;
+            int p;
+            if (narrow) {
+                const int bb = (int)e / (int)P;
+                b = bb;
+                p = (int)e - bb * (int)P;
+            } else {
+                b = e / P;
+                p = (int)(e - b * P);
+            }
+            // strict upper-triangle index p -> (i, j), row by row: counted from
+            // the end it is the lower-triangle index of (K-2-i, K-1-j)
+            int ri, cj;
+            tri_index((int)P - 1 - p, &ri, &cj);
+            i = K - 2 - ri;
+            j = K - 1 - cj;
         } else {
-            const int64_t d = e - n_off;
-            b = d / K;
-            i = j = (int)(d - b * K);
+            if (narrow) {
+                const int d = (int)(e - n_off), bb = d / K;
+                b = bb;
+                i = j = d - bb * K;
+            } else {
+                const int64_t d = e - n_off;
+                b = d / K;
+                i = j = (int)(d - b * K);
+            }
         }
         const double* u = users + b * K * 2;
         double xi = u[2 * i], yi = u[2 * i + 1], xj = u[2 * j], yj = u[2 * j + 1];

@@ -40,6 +40,16 @@ int launch_aperture_apply(const Geom& g, int mode, const double* users, int K, i
 // The same factor written only below the diagonal, conj(G~_ij F_ij), leaving
 // G~_ij above it (the surrogate's base).
 int launch_aperture_base(const Geom& g, int mode, const double* users, int K, int B, double* gram, cudaStream_t st);
+// Row r and column c of the q-th entry of a lower triangle stored row by
+// row (c <= r), without FP64 arithmetic.
+__device__ __forceinline__ void tri_index(int q, int* r, int* c) {
+    int rr = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+    while ((rr + 1) * (rr + 2) / 2 <= q) ++rr;
+    while (rr * (rr + 1) / 2 > q) --rr;
+    *r = rr;
+    *c = q - rr * (rr + 1) / 2;
+}
+
 // rate (nullable): per-trial sum rate, computed by the receiver kernel itself.
 int launch_beamform(const double* gf, const double* gt, const double* power, const double* noise, int K,
                     int B, int scheme, int power_mode, double* sinr, int* status, double* cap,

@@ -67,16 +67,6 @@ __device__ __forceinline__ cd cmacc(cd acc, cd a, cd b) {
     return acc;
 }
 
-// Row r and column c of the q-th entry of a lower triangle stored row by
-// row (c <= r), without FP64 arithmetic.
-__device__ __forceinline__ void tri_index(int q, int* r, int* c) {
-    int rr = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
-    while ((rr + 1) * (rr + 2) / 2 <= q) ++rr;
-    while (rr * (rr + 1) / 2 > q) --rr;
-    *r = rr;
-    *c = q - rr * (rr + 1) / 2;
-}
-
 // Split of an FP64 value into two floats, hi + lo = d to ~2^-48 relative,
 // with integer and FP32 instructions only (FP64 <-> FP32 conversions occupy
 // the FP64 pipe): hi is d truncated to 24 significant bits (sign, rebiased
