@@ -270,10 +270,10 @@ __device__ void to_cf_inplace(cd* A, int K) {
     __syncthreads();
 }
 
-// M = X^H X for lower-triangular X (double-float): M_rc = sum_{l >= max(r, c)}
-// conj(X_lr) X_lc, upper triangle computed and mirrored, written in
-// double-float (normalized) into M.
-__device__ void gram_of_lower_ff(const cd* X, cd* M, int K) {
+// M = X^H X for lower-triangular X (double-float, row stride xs): M_rc =
+// sum_{l >= max(r, c)} conj(X_lr) X_lc, upper triangle computed and mirrored,
+// written in double-float (normalized) into M (row stride K).
+__device__ void gram_of_lower_ff(const cd* X, int xs, cd* M, int K) {
     const cf* F = reinterpret_cast<const cf*>(X);
     cf* FM = reinterpret_cast<cf*>(M);
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -283,7 +283,7 @@ __device__ void gram_of_lower_ff(const cd* X, cd* M, int K) {
         while (w >= rl) { w -= rl; ++r; --rl; }
         const int c = r + w;  // r <= c
         float2 s = make_float2(0.f, 0.f), cc = make_float2(0.f, 0.f);
-        for (int l = c; l < K; ++l) cf_mac(s, cc, F[l * K + r], F[l * K + c], true);
+        for (int l = c; l < K; ++l) cf_mac(s, cc, F[l * xs + r], F[l * xs + c], true);
         const float2 t = __fadd2_rn(s, cc);
         const float2 lo = __fadd2_rn(__fadd2_rn(s, make_float2(-t.x, -t.y)), cc);
         FM[r * K + c] = {t, lo};
@@ -300,8 +300,11 @@ __device__ void gram_of_lower_ff(const cd* X, cd* M, int K) {
 // scaling), then every row i scaled by 1/L_ii.  L comes from chol_lower,
 // column by column (L_ik at T[k K + i]); its strictly lower triangle becomes
 // U in double-float in place (the only part read).  dinvf[k] = 1 / L_kk
-// (float pair).
+// (float pair).  X has row stride K + 1: a warp whose lanes cover several
+// short rows then spreads over the shared-memory banks instead of hitting
+// one bank group once per row.
 __device__ void tri_inverse_ff(cd* T, cd* X, int K, const float2* dinvf) {
+    const int xs = K + 1;
     const int tid = threadIdx.x, nt = blockDim.x;
     cf* FT = reinterpret_cast<cf*>(T);
     for (int e = tid; e < K * K; e += nt) {
@@ -312,21 +315,23 @@ __device__ void tri_inverse_ff(cd* T, cd* X, int K, const float2* dinvf) {
         }
     }
     cf* FX = reinterpret_cast<cf*>(X);
-    for (int e = tid; e < K * K; e += nt)
-        FX[e] = {make_float2((e / K) == (e % K) ? 1.0f : 0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+    for (int e = tid; e < K * K; e += nt) {
+        const int i = e / K, j = e - i * K;
+        FX[i * xs + j] = {make_float2(i == j ? 1.0f : 0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+    }
     __syncthreads();
     for (int k = 0; k < K - 1; ++k) {
         const cf* Uk = FT + k * K;
         const int rows = K - k - 1, cols = k + 1;
         for (int e = tid; e < rows * cols; e += nt) {
             const int r = e / cols, i = k + 1 + r, j = e - r * cols;
-            FX[i * K + j] = cf_fms(FX[i * K + j], Uk[i], FX[k * K + j]);
+            FX[i * xs + j] = cf_fms(FX[i * xs + j], Uk[i], FX[k * xs + j]);
         }
         __syncthreads();
     }
     for (int e = tid; e < K * K; e += nt) {
         const int i = e / K, j = e - i * K;
-        if (j <= i) FX[e] = cf_scale(FX[e], dinvf[i]);
+        if (j <= i) FX[i * xs + j] = cf_scale(FX[i * xs + j], dinvf[i]);
     }
     __syncthreads();
 }
@@ -513,15 +518,15 @@ __device__ void mismatched_sinr(const cf* FM, const cf* FG, const double* p, dou
 // One trial's receiver, executed by the whole CTA.  gf/gt: this trial's Gram
 // matrices (gt == gf when matched); pw: its K powers; s2: its noise power;
 // sinr_t, status_t, cap_t: its outputs (cap_t may be NULL).  Dynamic shared
-// memory: 2 K^2 complex doubles plus 2 XLMIMO_MAX_USERS doubles.
+// memory: (2 K^2 + K) complex doubles plus 2 XLMIMO_MAX_USERS doubles.
 __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __restrict__ gt, int matched,
                                const double* __restrict__ pw, double s2, int K, int scheme, int power_mode,
                                double* __restrict__ sinr_t, int* __restrict__ status_t, double* __restrict__ cap_t) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int KK = K * K;
     cd* Z = reinterpret_cast<cd*>(smem);
-    cd* X = Z + KK;
-    double* p = reinterpret_cast<double*>(X + KK);
+    cd* X = Z + KK;  // K rows of K + 1 (the triangular inverse's padded stride)
+    double* p = reinterpret_cast<double*>(X + KK + K);
     double* dg = p + XLMIMO_MAX_USERS;
     __shared__ double pivd[XLMIMO_MAX_USERS], sp[XLMIMO_MAX_USERS];
     __shared__ float2 dinvf[XLMIMO_MAX_USERS];
@@ -579,7 +584,7 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
                 for (int k = tid; k < K; k += nt) {
                     float2 s2a = make_float2(0.f, 0.f), c2a = make_float2(0.f, 0.f);
                     for (int i = k; i < K; ++i) {
-                        const cf x = FX[i * K + k];
+                        const cf x = FX[i * (K + 1) + k];
                         ff2_mac(s2a, c2a, x.hi, x.lo, x.hi, x.lo);  // (re^2, im^2)
                     }
                     dg[k] = ((double)s2a.x + (double)c2a.x) + ((double)s2a.y + (double)c2a.y);
@@ -587,7 +592,7 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
                 __syncthreads();
             } else {
                 // M = X^H X (double-float) into Z (the factor is no longer needed)
-                gram_of_lower_ff(X, Z, K);
+                gram_of_lower_ff(X, K + 1, Z, K);
                 m_in_z = true;
             }
         } else {
@@ -720,7 +725,7 @@ int beamform_ragged_prepare() {
 
 void beamform_trial_launch_bucket(const DevInst* insts, const int* list, int n, int kmax, const double* gram,
                                   const double* power, int power_mode, double* sinr, int* status, cudaStream_t st) {
-    size_t smem = 2 * (size_t)kmax * kmax * sizeof(cd) + 2 * XLMIMO_MAX_USERS * sizeof(double);
+    size_t smem = (2 * (size_t)kmax * kmax + kmax) * sizeof(cd) + 2 * XLMIMO_MAX_USERS * sizeof(double);
     beamform_ragged_kernel<<<n, SOLVE_THREADS, smem, st>>>(insts, list, (const double2*)gram, power, power_mode, sinr,
                                                             status);
 }
@@ -731,7 +736,7 @@ int launch_beamform(const double* gf, const double* gt, const double* power, con
     int matched = (gt == nullptr || gt == gf) ? 1 : 0;
     if (!gt) gt = gf;
     size_t KK = (size_t)K * K;
-    size_t smem = 2 * KK * sizeof(cd) + 2 * XLMIMO_MAX_USERS * sizeof(double);
+    size_t smem = (2 * KK + K) * sizeof(cd) + 2 * XLMIMO_MAX_USERS * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(beamform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return cuda_status(e, "beamform attribute");
     beamform_kernel<<<B, SOLVE_THREADS, smem, st>>>((const double2*)gf, (const double2*)gt, matched, power, noise, K,
@@ -745,7 +750,7 @@ int launch_beamform_pair(const BfJob& j0, const BfJob& j1, int K, int B, int pow
     if (a.gt == a.gf) a.gt = nullptr;  // matched
     if (c.gt == c.gf) c.gt = nullptr;
     size_t KK = (size_t)K * K;
-    size_t smem = 2 * KK * sizeof(cd) + 2 * XLMIMO_MAX_USERS * sizeof(double);
+    size_t smem = (2 * KK + K) * sizeof(cd) + 2 * XLMIMO_MAX_USERS * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(beamform_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return cuda_status(e, "beamform attribute");
     beamform_pair_kernel<<<2 * (int64_t)B, SOLVE_THREADS, smem, st>>>(a, c, K, power_mode);
