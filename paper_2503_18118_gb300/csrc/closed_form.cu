@@ -173,9 +173,8 @@ int launch_aperture_base(const Geom& g, int mode, const double* users, int K, in
     return aperture_launch(g, mode, users, K, B, true, gram, st);
 }
 
-int launch_closed_form(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st) {
+int launch_closed_form(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st, int threads) {
     int64_t total = (int64_t)B * K * (K + 1) / 2;  // off-diagonal pairs plus diagonals
-    int threads = 256;
     int64_t blocks = (total + threads - 1) / threads;
     int64_t cap = 16LL * num_sms();
     if (blocks > cap) blocks = cap;

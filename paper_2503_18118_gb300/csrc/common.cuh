@@ -33,7 +33,10 @@ int launch_gram_f64(const Geom& g, const double* users, int K, int B, double* gr
 int launch_gram_f32(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st);
 int launch_gram_tc(const Geom& g, const double* users, int K, int B, int prec, double* gram, cudaStream_t st,
                    int ctas_per_sm = 0);
-int launch_closed_form(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st);
+// threads per block: 256 alone; 64 lets a block (44 registers a thread) fit
+// beside three tensor-core Gram CTAs on an SM, so that it runs during the Gram.
+int launch_closed_form(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st,
+                       int threads = 256);
 // Finite-aperture factor (APERTURE_* of aperture.cuh) applied in place to the
 // off-diagonal entries of closed-form Grams.
 int launch_aperture_apply(const Geom& g, int mode, const double* users, int K, int B, double* gram, cudaStream_t st);
