@@ -237,6 +237,27 @@ typedef struct {
 int xlmimo_saturation_analytic(const xlmimo_user_dist* dist, int K, double t, double spacing,
                                double* out, void* stream);
 
+/* Appendix A: the influence of the off-diagonal Gram entries on the capacity.
+ * For each trial b, with R the users' correlation matrix (r_ij = h_i^H h_j /
+ * (|h_i| |h_j|), h_k the exact channel of user k on the array) and every user
+ * at receive SNR `snr` (linear; a_i = snr is the i-th diagonal element of
+ * (P/sigma_n^2) H^H H):
+ *   out[4b + 0] = log2 det R              (-(1/K) of it is Fig. 5's -E_K[log2 lambda^R])
+ *   out[4b + 1] = log2 det(I + snr R)     (the capacity C)
+ *   out[4b + 2] = K log2(1 + snr)         (log2 U, Hadamard's upper bound)
+ *   out[4b + 3] = log2 det R + log2 U     (log2 L, the Schur-Horn lower bound)
+ * K is 1..XLMIMO_MAX_BOUNDS_USERS (Fig. 5 reaches K = 1000); users[b][k][2]
+ * positions on the device as for xlmimo_channel_gram; out on the device.
+ * Channels are generated in FP32 (span-referenced phase), the Gram and the
+ * blocked Cholesky factorisations of R and I + snr R run in FP64.  A trial
+ * whose R is not numerically positive definite (coincident users) gets NaN.
+ * Asynchronous on `stream`; allocates B*K*n_ant*8 + 3*B*Kp^2*16 bytes
+ * (Kp = K rounded up to 32) of stream-ordered workspace and frees it.
+ * XLMIMO_EINVAL for K out of range, snr < 0 or NULL pointers. */
+#define XLMIMO_MAX_BOUNDS_USERS 1024
+int xlmimo_capacity_bounds(const xlmimo_array* arr, const double* users, int K, int B, double snr,
+                           double* out, void* stream);
+
 /* Capacity-saturation sweep (Sec. IV-C, Fig. 3; Sec. V-C, Fig. 4): for each
  * array size in n_list, over the same B trials of users, the exact Gram (at
  * `prec`) and the closed-form Gram, ZF and MMSE sum rates (exact receiver,

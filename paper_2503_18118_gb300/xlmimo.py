@@ -20,6 +20,7 @@ POWER_ABS, POWER_RXSNR = 0, 1
 DIST_RECT, DIST_POLAR = 0, 1
 APERTURE_NONE, APERTURE_MASK, APERTURE_FRESNEL = 0, 1, 2
 MAX_USERS = 64
+MAX_BOUNDS_USERS = 1024
 STATUS = {0: "OK", 1: "EINVAL", 2: "ECUDA", 3: "ENOMEM", 4: "ESINGULAR", 5: "ETIMEOUT", 6: "EUNSUPPORTED"}
 
 
@@ -68,7 +69,8 @@ class Inst(ctypes.Structure):
 EXPORTS = ("xlmimo_batch_plan_create", "xlmimo_batch_run", "xlmimo_batch_plan_info", "xlmimo_batch_plan_destroy",
            "xlmimo_mc_step", "xlmimo_channel_gram", "xlmimo_channel_gram_noalloc", "xlmimo_corr_closed_form",
            "xlmimo_corr_closed_form_aperture", "xlmimo_beamform", "xlmimo_sumrate",
-           "xlmimo_saturation", "xlmimo_saturation_analytic", "xlmimo_capacity_sweep", "xlmimo_pair_features",
+           "xlmimo_saturation", "xlmimo_saturation_analytic", "xlmimo_capacity_sweep", "xlmimo_capacity_bounds",
+           "xlmimo_pair_features",
            "xlmimo_mlp_forward", "xlmimo_mlp_loss", "xlmimo_mlp_work_floats", "xlmimo_mlp_backward", "xlmimo_mlp_adam",
            "xlmimo_mlp_train_step", "xlmimo_mlp_pack", "xlmimo_surrogate_gram", "xlmimo_last_error", "xlmimo_version")
 
@@ -106,6 +108,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.xlmimo_saturation_analytic.argtypes = [ctypes.POINTER(UserDist), i32, dbl, dbl, ctypes.POINTER(dbl), vp]
     L.xlmimo_capacity_sweep.argtypes = [ctypes.POINTER(SweepCfg), ctypes.POINTER(SweepResult), vp]
     L.xlmimo_corr_closed_form_aperture.argtypes = [ctypes.POINTER(Array), vp, i32, i32, i32, vp, vp]
+    L.xlmimo_capacity_bounds.argtypes = [ctypes.POINTER(Array), vp, i32, i32, dbl, vp, vp]
     L.xlmimo_pair_features.argtypes = [ctypes.POINTER(Array), vp, i32, i32, i32, vp, vp, vp, vp, vp, vp]
     L.xlmimo_mlp_forward.argtypes = [vp, vp, i32, vp, vp, vp]
     L.xlmimo_mlp_loss.argtypes = [vp, vp, vp, i32, vp, vp, vp]
@@ -238,6 +241,19 @@ def xlmimo_corr_closed_form(arr: Array, users: torch.Tensor, gram: torch.Tensor 
     _check(lib().xlmimo_corr_closed_form(ctypes.byref(arr), _dev(users, torch.float64, "users", (B, K, 2)), K, B,
                                          _dev(gram, torch.complex128, "gram", (B, K, K)), _stream(stream)))
     return gram
+
+
+def xlmimo_capacity_bounds(arr: Array, users: torch.Tensor, snr: float, out: torch.Tensor | None = None,
+                           stream=None) -> torch.Tensor:
+    """Appendix A per trial, float64 [B][4]: log2 det R, log2 det(I + snr R),
+    log2 U = K log2(1 + snr), log2 L = log2 det R + log2 U (users [B][K][2],
+    K <= MAX_BOUNDS_USERS, snr linear)."""
+    B, K = users.shape[0], users.shape[1]
+    if out is None:
+        out = torch.empty((B, 4), dtype=torch.float64, device=users.device)
+    _check(lib().xlmimo_capacity_bounds(ctypes.byref(arr), _dev(users, torch.float64, "users", (B, K, 2)), K, B,
+                                        float(snr), _dev(out, torch.float64, "out", (B, 4)), _stream(stream)))
+    return out
 
 
 def xlmimo_corr_closed_form_aperture(arr: Array, users: torch.Tensor, mode: int, gram: torch.Tensor | None = None,

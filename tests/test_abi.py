@@ -116,3 +116,15 @@ def test_surrogate_entries_validate_on_host(xl):
     # workspace: two [M][256] slabs plus one [257][256] partial per 512 rows
     assert L.xlmimo_mlp_work_floats(0) == 0
     assert L.xlmimo_mlp_work_floats(1000) == 2 * 1000 * 256 + 2 * 257 * 256
+
+
+def test_capacity_bounds_validates_on_host(xl):
+    L = xl.lib()
+    dummy = ctypes.c_void_p(16)
+    arr = xl.array(1024, 0.01)
+    assert L.xlmimo_capacity_bounds(ctypes.byref(arr), dummy, 0, 1, 1.0, dummy, None) == 1
+    assert L.xlmimo_capacity_bounds(ctypes.byref(arr), dummy, xl.MAX_BOUNDS_USERS + 1, 1, 1.0, dummy, None) == 1
+    assert L.xlmimo_capacity_bounds(ctypes.byref(arr), dummy, 8, 1, -1.0, dummy, None) == 1
+    assert L.xlmimo_capacity_bounds(ctypes.byref(arr), dummy, 8, 1, float("nan"), dummy, None) == 1
+    assert L.xlmimo_capacity_bounds(ctypes.byref(arr), None, 8, 1, 1.0, dummy, None) == 1
+    assert L.xlmimo_capacity_bounds(ctypes.byref(arr), None, 8, 0, 1.0, None, None) == 0
