@@ -248,11 +248,13 @@ int xlmimo_saturation_analytic(const xlmimo_user_dist* dist, int K, double t, do
  *   out[4b + 3] = log2 det R + log2 U     (log2 L, the Schur-Horn lower bound)
  * K is 1..XLMIMO_MAX_BOUNDS_USERS (Fig. 5 reaches K = 1000); users[b][k][2]
  * positions on the device as for xlmimo_channel_gram; out on the device.
- * Channels are generated in FP32 (span-referenced phase), the Gram and the
- * blocked Cholesky factorisations of R and I + snr R run in FP64.  A trial
+ * Channels are generated in FP32 (span-referenced phase); the Gram sums FP32
+ * products over 32-element chunks and the chunks in double-float (~2e-6
+ * relative at worst); the blocked Cholesky factorisations of R and I + snr R
+ * run in FP64.  A trial
  * whose R is not numerically positive definite (coincident users) gets NaN.
  * Asynchronous on `stream`; allocates B*K*n_ant*8 + 3*B*Kp^2*16 bytes
- * (Kp = K rounded up to 32) of stream-ordered workspace and frees it.
+ * (Kp = K rounded up to 64) of stream-ordered workspace and frees it.
  * XLMIMO_EINVAL for K out of range, snr < 0 or NULL pointers. */
 #define XLMIMO_MAX_BOUNDS_USERS 1024
 int xlmimo_capacity_bounds(const xlmimo_array* arr, const double* users, int K, int B, double snr,

@@ -8,10 +8,10 @@
 // and -(1/K) log2 det R is the negative empirical expectation of Fig. 5.
 // K reaches 1000 there, beyond the K <= 64 receivers, so the path is:
 //   1. channel entries into HBM (FP32, the span-referenced generator of
-//      chan_gen.cuh), one CTA per (trial, user, 128-element span);
-//   2. the lower 32 x 32 user tiles of G = H^H H in FP64 (FP32 entries,
-//      FP64 products and sums);
-//   3. R and I + a R, FP64, padded to a multiple of 32 with identity rows;
+//      chan_gen.cuh), one CTA per (trial, user);
+//   2. the lower 64 x 64 user tiles of G = H^H H: FP32 products summed over
+//      32-element chunks, chunk sums in double-float, FP64 once per entry;
+//   3. R and I + a R, FP64, padded to a multiple of 64 with identity rows;
 //   4. a right-looking blocked Cholesky of all 2B matrices at once, 32
 //      columns a step: diagonal block, panel solve, trailing update, each a
 //      batched launch; the log-determinant adds 2 log2 L_kk block by block.
@@ -26,73 +26,115 @@ namespace xl {
 constexpr int BT = 32;  // tile and Cholesky block size
 
 // -------------------------------------------------------------- channels
-// H[(b K + k) N + n] = h_k(n) of trial b (FP32 complex).
-__global__ void __launch_bounds__(REF_SPAN) bounds_channel_kernel(Geom g, GenParams gp, const double* __restrict__ users,
-                                                                  int K, float2* __restrict__ H) {
+// H[(b K + k) N + n] = h_k(n) of trial b (FP32 complex).  One CTA per (trial,
+// user): the user's geometry once (FP64), then 256 span references at a time
+// (one per thread) and the entries of those spans, written contiguously.
+constexpr int CH_THREADS = 256;
+
+__global__ void __launch_bounds__(CH_THREADS) bounds_channel_kernel(Geom g, GenParams gp, const double* __restrict__ users,
+                                                                    int K, float2* __restrict__ H) {
     __shared__ UserGeo ug;
-    __shared__ UserRef ref;
-    const int64_t b = blockIdx.z;
-    const int k = blockIdx.y;
-    const int64_t n0 = (int64_t)blockIdx.x * REF_SPAN;
-    const long long nc = (long long)(n0 + REF_SPAN / 2);
-    if (threadIdx.x == 0) {
-        const double x = users[(b * K + k) * 2], y = users[(b * K + k) * 2 + 1];
-        ug = make_user_geo(g, x, y);
-        ref = make_user_ref(gp, ug, nc);
-    }
+    __shared__ UserRef refs[CH_THREADS];
+    const int64_t b = blockIdx.y;
+    const int k = blockIdx.x, tid = threadIdx.x;
+    if (tid == 0) ug = make_user_geo(g, users[(b * K + k) * 2], users[(b * K + k) * 2 + 1]);
     __syncthreads();
-    const int64_t n = n0 + threadIdx.x;
-    if (n < g.N) {
-        float2 h = gen_entry_f32(g.model, gp.dprime_f, ug.xl2, ug.x2x2, ug.ampc, ref, (float)(int)(n - nc));
-        if (!ug.ok) h = make_float2(nanf(""), nanf(""));
-        H[(b * K + k) * g.N + n] = h;
+    const int64_t nspans = (g.N + REF_SPAN - 1) / REF_SPAN;
+    float2* Hk = H + (b * K + k) * g.N;
+    for (int64_t s0 = 0; s0 < nspans; s0 += CH_THREADS) {
+        if (s0 + tid < nspans) refs[tid] = make_user_ref(gp, ug, (long long)((s0 + tid) * REF_SPAN + REF_SPAN / 2));
+        __syncthreads();
+        const int64_t nb0 = s0 * REF_SPAN;
+        const int64_t cnt = min((int64_t)CH_THREADS * REF_SPAN, g.N - nb0);
+        for (int64_t i = tid; i < cnt; i += CH_THREADS) {
+            const int sp = (int)(i / REF_SPAN), m = (int)(i - (int64_t)sp * REF_SPAN) - REF_SPAN / 2;
+            float2 h = gen_entry_f32(g.model, gp.dprime_f, ug.xl2, ug.x2x2, ug.ampc, refs[sp], (float)m);
+            if (!ug.ok) h = make_float2(nanf(""), nanf(""));
+            Hk[nb0 + i] = h;
+        }
+        __syncthreads();
     }
 }
 
 // -------------------------------------------------------------- Gram tiles
-__device__ __forceinline__ double2 cmac_conj(double2 acc, float2 a, float2 b) {  // acc + conj(a) b
-    const double ar = a.x, ai = a.y, br = b.x, bi = b.y;
-    acc.x = fma(ar, br, acc.x);
-    acc.x = fma(ai, bi, acc.x);
-    acc.y = fma(ar, bi, acc.y);
-    acc.y = fma(-ai, br, acc.y);
-    return acc;
+// (hi, lo) += v by Knuth's two-sum on the high part (double-float accumulator).
+__device__ __forceinline__ void ff_acc(float& hi, float& lo, float v) {
+    const float t = __fadd_rn(hi, v);
+    const float bb = __fsub_rn(t, hi);
+    lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bb)), __fsub_rn(v, bb)));
+    hi = t;
 }
 
-// Tile (ti, tj), ti >= tj, of trial b: G[j Kp + i] = sum_n conj(h_i(n)) h_j(n).
-// 256 threads: row r = tid / 8, columns 4 (tid % 8) .. +3 of the tile.
+// Tile (ti, tj), ti >= tj, of GT x GT users of trial b: G[j Kp + i] =
+// sum_n conj(h_i(n)) h_j(n).  256 threads; thread (ri, cj) = (tid / 16,
+// tid % 16) owns rows ri + 16 qa and columns cj + 16 qb (qa, qb < 4), so a
+// warp's column reads fall in distinct bank pairs and each element loaded
+// from shared memory feeds four complex MACs.  The products and the sum over
+// a 32-element chunk are FP32 (worst relative error 32 x 2^-24 of the chunk's
+// sum of magnitudes); chunk sums go into double-float accumulators, so the
+// sum over N loses nothing further, and the FP64 pipe is used once per entry.
+constexpr int GT = 64;
+
 __global__ void __launch_bounds__(256) bounds_gram_kernel(const float2* __restrict__ H, int K, int64_t N, int Kp,
                                                           double2* __restrict__ G) {
-    __shared__ float2 Hi[BT][BT + 1], Hj[BT][BT + 1];  // [user][element of the chunk]
+    __shared__ float2 Hi[GT][BT + 1], Hj[GT][BT + 1];  // [user][element of the chunk]
     const int64_t b = blockIdx.y;
     int ti, tj;
     tri_index(blockIdx.x, &ti, &tj);
-    const int tid = threadIdx.x, r = tid >> 3, c0 = (tid & 7) * 4;
+    const int tid = threadIdx.x, ri = tid >> 4, cj = tid & 15;
     const float2* Hb = H + b * K * N;
-    double2 acc[4];
+    float hx[4][4], lx[4][4], hy[4][4], ly[4][4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] = make_double2(0.0, 0.0);
+    for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+        for (int qb = 0; qb < 4; ++qb) hx[qa][qb] = lx[qa][qb] = hy[qa][qb] = ly[qa][qb] = 0.f;
     for (int64_t n0 = 0; n0 < N; n0 += BT) {
 #pragma unroll
-        for (int l = 0; l < 4; ++l) {
+        for (int l = 0; l < GT * BT / 256; ++l) {
             const int idx = tid + 256 * l, u = idx >> 5, e = idx & 31;  // user, element
             const int64_t n = n0 + e;
-            const int ui = ti * BT + u, uj = tj * BT + u;
+            const int ui = ti * GT + u, uj = tj * GT + u;
             Hi[u][e] = (ui < K && n < N) ? Hb[(int64_t)ui * N + n] : make_float2(0.f, 0.f);
             Hj[u][e] = (uj < K && n < N) ? Hb[(int64_t)uj * N + n] : make_float2(0.f, 0.f);
         }
         __syncthreads();
-#pragma unroll 8
-        for (int e = 0; e < BT; ++e) {
-            const float2 a = Hi[r][e];
+        float sx[4][4], sy[4][4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = cmac_conj(acc[q], a, Hj[c0 + q][e]);
+        for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+            for (int qb = 0; qb < 4; ++qb) sx[qa][qb] = sy[qa][qb] = 0.f;
+#pragma unroll 4
+        for (int e = 0; e < BT; ++e) {
+            float2 a[4], v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                a[q] = Hi[ri + 16 * q][e];
+                v[q] = Hj[cj + 16 * q][e];
+            }
+#pragma unroll
+            for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+                for (int qb = 0; qb < 4; ++qb) {  // += conj(a) v
+                    sx[qa][qb] = fmaf(a[qa].x, v[qb].x, fmaf(a[qa].y, v[qb].y, sx[qa][qb]));
+                    sy[qa][qb] = fmaf(a[qa].x, v[qb].y, fmaf(-a[qa].y, v[qb].x, sy[qa][qb]));
+                }
         }
+#pragma unroll
+        for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+            for (int qb = 0; qb < 4; ++qb) {
+                ff_acc(hx[qa][qb], lx[qa][qb], sx[qa][qb]);
+                ff_acc(hy[qa][qb], ly[qa][qb], sy[qa][qb]);
+            }
         __syncthreads();
     }
     double2* Gb = G + b * (int64_t)Kp * Kp;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) Gb[(int64_t)(tj * BT + c0 + q) * Kp + ti * BT + r] = acc[q];
+    for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+        for (int qb = 0; qb < 4; ++qb)
+            Gb[(int64_t)(tj * GT + cj + 16 * qb) * Kp + ti * GT + ri + 16 * qa] =
+                make_double2((double)hx[qa][qb] + (double)lx[qa][qb], (double)hy[qa][qb] + (double)ly[qa][qb]);
 }
 
 // -------------------------------------------------------------- R, I + aR
@@ -263,7 +305,8 @@ extern "C" int xlmimo_capacity_bounds(const xlmimo_array* arr, const double* use
         return XLMIMO_EINVAL;
     }
     cudaStream_t st = as_stream(stream);
-    const int nb = (K + BT - 1) / BT, Kp = nb * BT;
+    const int Kp = (K + GT - 1) / GT * GT;  // multiple of the Gram tile and of the Cholesky block
+    const int nb = Kp / BT, ng = Kp / GT;
     const int64_t N = g.N, per = (int64_t)Kp * Kp;
     float2* H = nullptr;
     double2 *G = nullptr, *A = nullptr;
@@ -272,17 +315,12 @@ extern "C" int xlmimo_capacity_bounds(const xlmimo_array* arr, const double* use
     if (!rc) rc = cuda_status(cudaMallocAsync((void**)&G, (size_t)B * per * sizeof(double2), st), "workspace allocation");
     if (!rc) rc = cuda_status(cudaMallocAsync((void**)&A, (size_t)2 * B * per * sizeof(double2), st), "workspace allocation");
     if (!rc) rc = cuda_status(cudaMallocAsync((void**)&ld, (size_t)2 * B * sizeof(double), st), "workspace allocation");
-    if (!rc && (N + REF_SPAN - 1) / REF_SPAN > 0x7FFFFFFF) {
-        set_error("n_ant too large for the channel kernel");
-        rc = XLMIMO_EINVAL;
-    }
     if (!rc) {
-        dim3 grid((unsigned)((N + REF_SPAN - 1) / REF_SPAN), (unsigned)K, (unsigned)B);
-        bounds_channel_kernel<<<grid, REF_SPAN, 0, st>>>(g, make_gen_params(g), users, K, H);
+        bounds_channel_kernel<<<dim3((unsigned)K, (unsigned)B), CH_THREADS, 0, st>>>(g, make_gen_params(g), users, K, H);
         rc = cuda_status(cudaGetLastError(), "bounds channel launch");
     }
     if (!rc) {
-        bounds_gram_kernel<<<dim3((unsigned)(nb * (nb + 1) / 2), (unsigned)B), 256, 0, st>>>(H, K, N, Kp, G);
+        bounds_gram_kernel<<<dim3((unsigned)(ng * (ng + 1) / 2), (unsigned)B), 256, 0, st>>>(H, K, N, Kp, G);
         rc = cuda_status(cudaGetLastError(), "bounds gram launch");
     }
     if (!rc) {

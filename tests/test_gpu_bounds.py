@@ -1,8 +1,10 @@
 """Appendix A on the GPU (xlmimo_capacity_bounds) against the oracle.
 
 Tolerance: the channel entries come from the FP32 generator (phase error
-below 1e-5 rad, amplitude to FP32 rounding), so each correlation entry
-carries |dR_ij| <= 3 eps_h with eps_h = 1e-5; the Gram sums and the
+below 1e-5 rad, amplitude to FP32 rounding) and the Gram sums FP32 products
+over 32-element chunks (relative error below 32 x 2^-24 = 2e-6 of the sum of
+magnitudes, |h_i||h_j| at most) before exact-enough double-float sums, so
+each correlation entry carries |dR_ij| <= 3 eps_h with eps_h = 1e-5; the
 Cholesky factorisations are FP64.  To first order d log det M = tr(M^-1 dM),
 so |d log2 det R| <= ||R^-1||_F ||dR||_F / ln 2 <= 3 eps_h K^1.5 / (lambda_min ln 2),
 and for M = I + a R the same with a / (1 + a lambda_min) for 1 / lambda_min;
