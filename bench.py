@@ -285,6 +285,54 @@ def sweep_bench(xl, torch):
     return out
 
 
+def appendix_a_bench(xl, torch, max_mhz):
+    """Appendix A / Fig. 5: the negative empirical expectation -E_K[log2 lambda^R]
+    = -(1/K) log2 det R and the capacity bounds at 0 dB receive SNR, for K from
+    10 to 1000 users in the Sec. V-A rectangle (x in [1, 10] m, y in [-7.5, 7.5] m,
+    100 GHz, PNUSW), N = 40000 elements (beyond the K = 1000 saturation count),
+    8 trials per K; the paper reports 0.064 at K = 1000."""
+    lam = inputs.wavelength(100e9)
+    N, B = 40000, 8
+    arr = xl.array(N, lam, model=0)
+    ks = [10, 50, 100, 200, 400, 600, 800, 1000]
+    out = {"workload": "Sec. V-A rectangle, 100 GHz, PNUSW, N=40000, 8 trials per K, receive SNR 0 dB",
+           "k": ks, "neg_expectation_mean": [], "neg_expectation_std": [], "capacity_mean": [],
+           "log2_lower_mean": [], "log2_upper": [], "ms": [], "trials_per_s": []}
+    U0 = torch.from_numpy(inputs.users_rect(21, 1, 10, (1.0, 10.0), (-7.5, 7.5))).cuda()
+    xl.xlmimo_capacity_bounds(arr, U0, 1.0)  # warm
+    flops = 0.0
+    for K in ks:
+        U = torch.from_numpy(inputs.users_rect(20 + K, B, K, (1.0, 10.0), (-7.5, 7.5))).cuda()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        o = xl.xlmimo_capacity_bounds(arr, U, 1.0)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        o = o.cpu().numpy()
+        e = -o[:, 0] / K
+        out["neg_expectation_mean"].append(float(e.mean()))
+        out["neg_expectation_std"].append(float(e.std()))
+        out["capacity_mean"].append(float(o[:, 1].mean()))
+        out["log2_lower_mean"].append(float(o[:, 3].mean()))
+        out["log2_upper"].append(float(o[0, 2]))
+        out["ms"].append(ms)
+        out["trials_per_s"].append(B / (ms / 1e3))
+        if K == ks[-1]:
+            flops = 8.0 * N * K * (K + 1) / 2 * B  # Gram complex MACs of the Hermitian half
+            t_last = ms
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * 128 * 2 * max_mhz * 1e6 / 1e12  # FP32: 128 FMA lanes per SM per clock
+    out["paper_value_at_k1000"] = 0.064
+    # the whole call against the FP32 peak of its Gram work (the Gram kernel is
+    # ~57 % of the call, the FP64 Cholesky ~32 %: profiles/bounds_appendix_a.md)
+    out["roofline"] = {"bound": "alu", "achieved": flops / (t_last / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s (FP32)",
+                       "frac": flops / (t_last / 1e3) / 1e12 / peak, "kernel": "whole xlmimo_capacity_bounds call at K = 1000",
+                       "algorithmic": "8 flop x N K(K+1)/2 Gram MACs per trial"}
+    return out
+
+
 def surrogate_bench(xl, torch, peaks):
     """Learned correlation surrogate: labels from the exact kernel, training on
     the GPU, then the fused tensor-core inference timed at 100 GHz, N = 2^18,
@@ -511,6 +559,7 @@ def main():
     ragged = None
     sur = None
     sweep = None
+    app_a = None
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -530,6 +579,7 @@ def main():
         ragged = ragged_bench(xl, torch)
         sweep = sweep_bench(xl, torch)
         sur = surrogate_bench(xl, torch, peaks)
+        app_a = appendix_a_bench(xl, torch, float(peaks.get("sm_max_mhz", 2070.0)))
 
     # peaks from unit counts and the maximum SM clock (per SM per clock:
     # 128 FP32 FMA lanes, 16 MUFU transcendental units, 2 FP64 FMA lanes)
@@ -585,6 +635,7 @@ def main():
         "ragged": ragged,
         "sweep": sweep,
         "surrogate": sur,
+        "appendix_a": app_a,
         "speedup_vs_fp64_gpu": (value / fp64["trials_per_s"]) if fp64 else None,
         "roofline": roof,
         "cpu_baseline": cpu,
