@@ -24,7 +24,7 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 PNUSW, FSPL, UPW = 0, 1, 2
-ZF, MMSE, MRC = 0, 1, 2
+ZF, MMSE, MRC, ZF_DL = 0, 1, 2, 3
 POWER_ABS, POWER_RXSNR = 0, 1
 
 

@@ -42,6 +42,7 @@ typedef double complex cplx;
 #define ORC_ZF 0
 #define ORC_MMSE 1
 #define ORC_MRC 2
+#define ORC_ZF_DL 3
 
 #define ORC_POWER_ABS 0
 #define ORC_POWER_RXSNR 1
@@ -276,6 +277,11 @@ static int gauss_log2det(int K, const cplx* A, double* out) {
  *   MRC           : M = I
  * where Gf is the Gram matrix the receiver was built from (the exact one, or
  * the closed form of Sec. V-B for modified ZF).
+ * ZF_DL: downlink ZF precoding under a total power constraint (the downlink
+ * the paper leaves to the reader, Sec. II): W = beta H M with M = Gf^{-1} and
+ * beta^2 = P_T / tr(M G M^H), P_T = sum_k p_k; user k receives
+ * beta (G M)_kj s_j, so SINR_k = beta^2 |(MG)_kk|^2 / (beta^2 sum_{j!=k}
+ * |(MG)_jk|^2 + sigma^2)  (G M = (M G)^H for Hermitian M and G).
  * power_mode 0: power[b][k] is the transmit power p_k.
  * power_mode 1: power[b][k] is the received SNR p_k G_kk / sigma^2 of user k
  *               alone (G = the true Gram matrix), so p_k = snr_k sigma^2 / G_kk.
@@ -326,19 +332,38 @@ int oracle_beamform(const double* gram_filter, const double* gram_true, const do
                     for (int l = 0; l < K; ++l) acc += M[i * K + l] * G[l * K + j];
                     A[i * K + j] = acc;
                 }
-            /* Q = A M^H, only its diagonal is used */
+            /* Q = A M^H = M G M^H, only its diagonal is used */
             for (int i = 0; i < K; ++i) {
                 cplx acc = 0.0;
                 for (int l = 0; l < K; ++l) acc += A[i * K + l] * conj(M[i * K + l]);
                 Q[i * K + i] = acc;
             }
-            for (int k = 0; k < K; ++k) {
-                double sig = p[k] * creal(A[k * K + k] * conj(A[k * K + k]));
-                double itf = 0.0;
-                for (int j = 0; j < K; ++j)
-                    if (j != k) itf += p[j] * creal(A[k * K + j] * conj(A[k * K + j]));
-                double den = itf + s2 * creal(Q[k * K + k]);
-                sinr[(size_t)b * K + k] = sig / den;
+            if (scheme == ORC_ZF_DL) {
+                /* downlink: W = beta H M, beta^2 = P_T / tr(W^H W / beta^2) = P_T / tr(M G M^H)
+                   = P_T / sum_k Q_kk (P_T = sum_k p_k); user k receives beta (G M)_k. s with
+                   G M = A^H, so SINR_k = beta^2 |A_kk|^2 / (beta^2 sum_{j != k} |A_jk|^2 + s2) */
+                double pt = 0.0, tq = 0.0;
+                for (int k = 0; k < K; ++k) {
+                    pt += p[k];
+                    tq += creal(Q[k * K + k]);
+                }
+                const double b2 = pt / tq;
+                for (int k = 0; k < K; ++k) {
+                    double sig = b2 * creal(A[k * K + k] * conj(A[k * K + k]));
+                    double itf = 0.0;
+                    for (int j = 0; j < K; ++j)
+                        if (j != k) itf += b2 * creal(A[j * K + k] * conj(A[j * K + k]));
+                    sinr[(size_t)b * K + k] = sig / (itf + s2);
+                }
+            } else {
+                for (int k = 0; k < K; ++k) {
+                    double sig = p[k] * creal(A[k * K + k] * conj(A[k * K + k]));
+                    double itf = 0.0;
+                    for (int j = 0; j < K; ++j)
+                        if (j != k) itf += p[j] * creal(A[k * K + j] * conj(A[k * K + j]));
+                    double den = itf + s2 * creal(Q[k * K + k]);
+                    sinr[(size_t)b * K + k] = sig / den;
+                }
             }
         } else {
             for (int k = 0; k < K; ++k) sinr[(size_t)b * K + k] = 0.0;

@@ -171,3 +171,31 @@ def test_per_trial_saturation(orc, t):
     assert np.allclose(out[0, :2], [2 * a + 1, -2 * a + 1])
     assert np.allclose(out[1, :2], [max(a, 3 * a - 4), min(-a, -3 * a - 4)])
     assert out[0, 2] == np.ceil((4 * a) / 0.01)
+
+
+@pytest.mark.parametrize("closed", [False, True])
+def test_downlink_zf_from_explicit_precoder(orc, closed):
+    """Downlink ZF (scheme ZF_DL): the SINR from an explicit precoder W = beta H Gf^-1
+    with ||W||_F^2 = P_T and the users' explicit channel vectors, built from the
+    exact Gram or from the closed form (modified ZF) and judged on the exact channel."""
+    B, K, N = 4, 5, 256
+    users = inputs.users_polar(31, B, K, (5.0, 50.0))
+    G = orc.gram(1, N, LAM, LAM / 2, 1.0, users)
+    Gf = orc.closed_form(1, N, LAM, LAM / 2, 1.0, users) if closed else G
+    g = np.random.Generator(np.random.Philox(key=77))
+    p = 10 ** g.uniform(-6.0, -4.0, (B, K))
+    s2 = g.uniform(0.5, 2.0, B)
+    s, st, _ = orc.beamform(Gf, p, s2, orc.ZF_DL, 0, gram_true=G)
+    for b in range(B):
+        H = np.stack([orc.channel(1, N, LAM, LAM / 2, 1.0, *users[b, k]) for k in range(K)], axis=1)
+        W = H @ np.linalg.inv(Gf[b])
+        W *= np.sqrt(p[b].sum() / np.sum(np.abs(W) ** 2))
+        E = H.conj().T @ W  # E[k, j]: what user k receives of stream j
+        sig = np.abs(np.diag(E)) ** 2
+        itf = np.sum(np.abs(E) ** 2, axis=1) - sig
+        ref = sig / (itf + s2[b])
+        if st[b] == 0:
+            assert np.allclose(s[b], ref, rtol=1e-8)
+    if not closed:
+        tr = np.real(np.trace(np.linalg.inv(G), axis1=1, axis2=2))
+        assert np.allclose(s, (p.sum(1) / (s2 * tr))[:, None], rtol=1e-10)  # all users equal
