@@ -96,8 +96,9 @@ typedef enum {
  * The diagonal is the closed form's. */
 typedef enum { XLMIMO_APERTURE_NONE = 0, XLMIMO_APERTURE_MASK = 1, XLMIMO_APERTURE_FRESNEL = 2 } xlmimo_aperture;
 
-/* Linear receivers (Sec. V): ZF (Eq. 21), MMSE, MRC. */
-typedef enum { XLMIMO_ZF = 0, XLMIMO_MMSE = 1, XLMIMO_MRC = 2 } xlmimo_scheme;
+/* Linear receivers (Sec. V): ZF (Eq. 21), MMSE, MRC; and ZF precoding on
+ * the downlink, which the paper leaves to the reader (Sec. II). */
+typedef enum { XLMIMO_ZF = 0, XLMIMO_MMSE = 1, XLMIMO_MRC = 2, XLMIMO_ZF_DL = 3 } xlmimo_scheme;
 
 /* How beamform() reads `power`:
  *   XLMIMO_POWER_ABS    power[b][k] is the transmit power p_k.
@@ -185,6 +186,10 @@ int xlmimo_corr_closed_form_aperture(const xlmimo_array* arr, const double* user
  * When gram_true is NULL (or equal to gram_filter) the matched forms are
  * used: ZF p_k / (sigma^2 [G^{-1}]_kk), MMSE p_k / (sigma^2 [Z^{-1}]_kk) - 1
  * with Z = G + sigma^2 diag(p)^{-1}, MRC p_k G_kk^2 / (sum_{j!=k} p_j |G_kj|^2 + sigma^2 G_kk).
+ * XLMIMO_ZF_DL (downlink ZF precoding, total power P_T = sum_k p_k): the
+ * precoder W = beta H M, M = Gf^{-1}, beta^2 = P_T / tr(M G M^H), gives user k
+ *   SINR_k = beta^2 |(M G)_kk|^2 / (beta^2 sum_{j!=k} |(M G)_jk|^2 + sigma^2),
+ * matched: P_T / (sigma^2 tr(G^{-1})) for every user.
  * Solves use an FP64 Cholesky factorisation in shared memory; a matrix
  * that is not numerically positive definite falls back to LU with partial
  * pivoting.

@@ -65,8 +65,8 @@ static int check_job(const xlmimo_mc_batch* j) {
     if (!j) { set_error("job is NULL"); return XLMIMO_EINVAL; }
     if (j->K < 1 || j->K > XLMIMO_MAX_USERS || j->B < 0) { set_error("K must be in [1, 64] and B >= 0"); return XLMIMO_EINVAL; }
     if (j->prec < XLMIMO_F64 || j->prec > XLMIMO_F16X3) { set_error("unknown precision"); return XLMIMO_EINVAL; }
-    if (j->scheme < XLMIMO_ZF || j->scheme > XLMIMO_MRC) { set_error("unknown scheme"); return XLMIMO_EINVAL; }
-    if (j->cf_scheme > XLMIMO_MRC || j->cf_scheme < -1) { set_error("unknown closed-form scheme"); return XLMIMO_EINVAL; }
+    if (j->scheme < XLMIMO_ZF || j->scheme > XLMIMO_ZF_DL) { set_error("unknown scheme"); return XLMIMO_EINVAL; }
+    if (j->cf_scheme > XLMIMO_ZF_DL || j->cf_scheme < -1) { set_error("unknown closed-form scheme"); return XLMIMO_EINVAL; }
     if (j->power_mode != XLMIMO_POWER_ABS && j->power_mode != XLMIMO_POWER_RXSNR) { set_error("unknown power mode"); return XLMIMO_EINVAL; }
     if (j->chunks < 0 || j->chunks > PIPE_MAX_CHUNKS || j->reserved != 0) { set_error("chunks must be in [0, 64], reserved 0"); return XLMIMO_EINVAL; }
     if (!(j->t == 0.0 || (j->t > 0.0 && j->t < 1.0))) { set_error("t must be 0 or in (0, 1)"); return XLMIMO_EINVAL; }

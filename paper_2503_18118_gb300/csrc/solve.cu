@@ -22,6 +22,9 @@
 namespace xl {
 
 constexpr int SOLVE_THREADS = 128;
+// downlink scratch of mismatched_sinr: |A_kk|^2, per-warp column sums and trace
+// shares for up to SOLVE_THREADS / 32 warps
+constexpr size_t BF_DL_EXTRA = (size_t)(XLMIMO_MAX_USERS * (1 + SOLVE_THREADS / 32) + SOLVE_THREADS / 32) * sizeof(double);
 
 struct cd {
     double x, y;
@@ -469,7 +472,8 @@ __device__ __forceinline__ double ff2_total(float2 s, float2 c) {
 // (broadcast) with column j of G (contiguous across lanes), and adds its terms
 // to three double-float sums that the warp then reduces by shuffles and
 // converts to FP64 once, so the K^3 products cost no FP64 instruction.
-__device__ void mismatched_sinr(const cf* FM, const cf* FG, const double* p, double s2, int K, double* sinr_t) {
+__device__ void mismatched_sinr(const cf* FM, const cf* FG, const double* p, double s2, int K, double* sinr_t,
+                                double* dlbuf) {
     __shared__ float2 pf[XLMIMO_MAX_USERS];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     for (int k = tid; k < K; k += blockDim.x) {
@@ -478,7 +482,12 @@ __device__ void mismatched_sinr(const cf* FM, const cf* FG, const double* p, dou
         pf[k] = make_float2(h, l);
     }
     __syncthreads();
+    const bool dl = dlbuf != nullptr;
     const float2 z = make_float2(0.f, 0.f);
+    // downlink: lane l's column sums sum_{k != j} |A_kj|^2 (j = l, l + 32) over
+    // this warp's rows, and the warp's share of tr(M G M^H) = sum_k N_k
+    float2 cs[2] = {z, z}, cc[2] = {z, z};
+    float2 ts = z, tc = z;
     for (int k = warp; k < K; k += nw) {
         const cf* Mk = FM + k * K;
         float2 ss = z, sc = z, is = z, ic = z, ns = z, nc = z;
@@ -491,6 +500,8 @@ __device__ void mismatched_sinr(const cf* FM, const cf* FG, const double* p, dou
             ff2_mac(ns, nc, ah, al, m.hi, m.lo);  // (re a re m, im a im m)
             if (j == k) {
                 ff2_mac(ss, sc, ah, al, ah, al);  // (re^2, im^2)
+            } else if (dl) {
+                ff2_mac(cs[j >> 5], cc[j >> 5], ah, al, ah, al);
             } else {
                 float2 ps = z, pc = z;
                 const float2 pj = pf[j];
@@ -510,15 +521,41 @@ __device__ void mismatched_sinr(const cf* FM, const cf* FG, const double* p, dou
         }
         if (lane == 0) {
             const double S = ff2_total(ss, sc), I = ff2_total(is, ic), N = ff2_total(ns, nc);
-            sinr_t[k] = p[k] * S / fma(s2, N, I);
+            if (dl) {
+                dlbuf[k] = S;  // |A_kk|^2
+                ff2_add(ts, tc, ns, nc);
+            } else {
+                sinr_t[k] = p[k] * S / fma(s2, N, I);
+            }
         }
+    }
+    if (!dl) return;
+    // per-warp partials, then fixed-order sums: dlbuf[0..63] |A_kk|^2,
+    // [64 + 64 w + j] warp w's column sums, [64 + 64 nw + w] warp w's trace share
+    double* colp = dlbuf + XLMIMO_MAX_USERS;
+    double* trp = colp + XLMIMO_MAX_USERS * nw;
+    for (int h = 0; h < 2; ++h) {
+        const int j = lane + 32 * h;
+        if (j < K) colp[warp * XLMIMO_MAX_USERS + j] = ff2_total(cs[h], cc[h]);
+    }
+    if (lane == 0) trp[warp] = ff2_total(ts, tc);
+    __syncthreads();
+    double pt = 0.0, tr = 0.0;
+    for (int k = 0; k < K; ++k) pt += p[k];
+    for (int w = 0; w < nw; ++w) tr += trp[w];
+    const double b2 = pt / tr;  // beta^2 = P_T / tr(M G M^H)
+    for (int k = tid; k < K; k += blockDim.x) {
+        double col = 0.0;
+        for (int w = 0; w < nw; ++w) col += colp[w * XLMIMO_MAX_USERS + k];
+        sinr_t[k] = b2 * dlbuf[k] / fma(b2, col, s2);
     }
 }
 
 // One trial's receiver, executed by the whole CTA.  gf/gt: this trial's Gram
 // matrices (gt == gf when matched); pw: its K powers; s2: its noise power;
 // sinr_t, status_t, cap_t: its outputs (cap_t may be NULL).  Dynamic shared
-// memory: (2 K^2 + K) complex doubles plus 2 XLMIMO_MAX_USERS doubles.
+// memory: (2 K^2 + K) complex doubles plus 2 XLMIMO_MAX_USERS doubles, and
+// BF_DL_EXTRA bytes more for the downlink scheme from another Gram matrix.
 __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __restrict__ gt, int matched,
                                const double* __restrict__ pw, double s2, int K, int scheme, int power_mode,
                                double* __restrict__ sinr_t, int* __restrict__ status_t, double* __restrict__ cap_t) {
@@ -636,9 +673,20 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
     // ---- SINR
     if (matched) {
         const double2* gm = gt;
+        double dl_v = 0.0;  // downlink ZF: P_T / (sigma^2 tr(G^-1)) for every user
+        if (scheme == XLMIMO_ZF_DL) {
+            double pt = 0.0, tr = 0.0;
+            for (int k = 0; k < K; ++k) {
+                pt += p[k];
+                tr += dg[k];
+            }
+            dl_v = pt / (s2c * tr);
+        }
         for (int k = tid; k < K; k += nt) {
             double v;
-            if (scheme == XLMIMO_MRC) {
+            if (scheme == XLMIMO_ZF_DL) {
+                v = dl_v;
+            } else if (scheme == XLMIMO_MRC) {
                 double gkk = gm[k * K + k].x;
                 double itf = 0.0;
                 for (int j = 0; j < K; ++j)
@@ -657,7 +705,8 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
         if (!m_in_z) to_cf_inplace(Mb, K);
         load_cf(Gb, gt, K, c);
         __syncthreads();
-        mismatched_sinr(reinterpret_cast<const cf*>(Mb), reinterpret_cast<const cf*>(Gb), p, s2c, K, sinr_t);
+        mismatched_sinr(reinterpret_cast<const cf*>(Mb), reinterpret_cast<const cf*>(Gb), p, s2c, K, sinr_t,
+                        scheme == XLMIMO_ZF_DL ? dg + XLMIMO_MAX_USERS : nullptr);
     }
     if (tid == 0) *status_t = st;
 }
@@ -737,6 +786,7 @@ int launch_beamform(const double* gf, const double* gt, const double* power, con
     if (!gt) gt = gf;
     size_t KK = (size_t)K * K;
     size_t smem = (2 * KK + K) * sizeof(cd) + 2 * XLMIMO_MAX_USERS * sizeof(double);
+    if (scheme == XLMIMO_ZF_DL) smem += BF_DL_EXTRA;
     cudaError_t e = cudaFuncSetAttribute(beamform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return cuda_status(e, "beamform attribute");
     beamform_kernel<<<B, SOLVE_THREADS, smem, st>>>((const double2*)gf, (const double2*)gt, matched, power, noise, K,
@@ -751,6 +801,7 @@ int launch_beamform_pair(const BfJob& j0, const BfJob& j1, int K, int B, int pow
     if (c.gt == c.gf) c.gt = nullptr;
     size_t KK = (size_t)K * K;
     size_t smem = (2 * KK + K) * sizeof(cd) + 2 * XLMIMO_MAX_USERS * sizeof(double);
+    if (a.scheme == XLMIMO_ZF_DL || c.scheme == XLMIMO_ZF_DL) smem += BF_DL_EXTRA;
     cudaError_t e = cudaFuncSetAttribute(beamform_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return cuda_status(e, "beamform attribute");
     beamform_pair_kernel<<<2 * (int64_t)B, SOLVE_THREADS, smem, st>>>(a, c, K, power_mode);

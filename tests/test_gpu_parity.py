@@ -391,3 +391,48 @@ def test_mc_step_matches_individual_calls(xl, prec, B, chunks):
                   (out.stats[:1], stats[:1]), (out.stats_cf[:1], stats2[:1])):
         assert torch.allclose(a, b_, rtol=rtol, atol=0)
     assert out.stats[2] == B and out.stats_cf[2] == B
+
+
+@pytest.mark.parametrize("K", [2, 8, 32, 64])
+def test_downlink_zf(xl, orc, K):
+    """Downlink ZF precoding (scheme ZF_DL) matched and from the closed form
+    (judged on the exact channel) against the oracle on identical Gram input;
+    same sizes and tolerances as the uplink receiver tests (matched: N >= 4K,
+    where tr(G^-1) is well conditioned; closed form: also N = 64)."""
+    for N in (max(4 * K, 64), 4096):
+        _, G, _, p, s2 = _solve_case(orc, 90 + K + N, 8, K, N)
+        p = p / np.real(np.einsum("bii->bi", G))
+        s_ref, st_ref, _ = orc.beamform(G, p, s2, orc.ZF_DL, 0)
+        s, st, _ = xl.xlmimo_beamform(dev(G), dev(p), dev(s2), xl.ZF_DL, 0)
+        s, st = s.cpu().numpy(), st.cpu().numpy()
+        ok = st_ref == 0
+        assert ok.any() and np.all(np.isin(st[ok], [0, 1]))
+        assert np.max(np.abs(s[ok] - s_ref[ok]) / np.abs(s_ref[ok])) <= 1e-9
+    for N in (64, 4096):
+        _, G, Gc, p, s2 = _solve_case(orc, 90 + K + N, 8, K, N)
+        p = p / np.real(np.einsum("bii->bi", G))
+        s_ref, st_ref, _ = orc.beamform(Gc, p, s2, orc.ZF_DL, 0, gram_true=G)
+        s, st, _ = xl.xlmimo_beamform(dev(Gc), dev(p), dev(s2), xl.ZF_DL, 0, gram_true=dev(G))
+        s, st = s.cpu().numpy(), st.cpu().numpy()
+        ok = (st_ref == 0) & (st != 4)
+        assert ok.sum() >= 4
+        assert np.max(np.abs(s[ok] - s_ref[ok]) / np.maximum(np.abs(s_ref[ok]), 1e-300)) <= 1e-7
+
+
+def test_mc_step_downlink(xl):
+    """The Monte-Carlo step with downlink ZF on both paths gives what the
+    individual calls give (the paired receiver launch carries the downlink scratch)."""
+    B, K, N = 50, 8, 2000
+    users = dev(inputs.users_polar(78, B, K, (3.0, 30.0)))
+    snr = dev(np.full((B, K), 10.0))
+    noise = dev(np.ones(B))
+    arr = xl.array(N, LAM100)
+    out = xl.McBuffers(B, K)
+    xl.xlmimo_mc_step(arr, users, snr, noise, out, prec=xl.F64, scheme=xl.ZF_DL, cf_scheme=xl.ZF_DL)
+    G = xl.xlmimo_channel_gram(arr, users, xl.F64)
+    s, st, _ = xl.xlmimo_beamform(G, snr, noise, xl.ZF_DL, xl.POWER_RXSNR)
+    Gc = xl.xlmimo_corr_closed_form(arr, users)
+    s2, st2, _ = xl.xlmimo_beamform(Gc, snr, noise, xl.ZF_DL, xl.POWER_RXSNR, gram_true=G)
+    torch.cuda.synchronize()
+    assert torch.equal(out.sinr, s) and torch.equal(out.sinr_cf, s2)
+    assert torch.equal(out.status, st) and torch.equal(out.status_cf, st2)
