@@ -50,11 +50,12 @@ def lib():
         L.oracle_num_threads.restype = c_int
         L.oracle_channel.argtypes = [c_int, i64, c_double, c_double, c_double, c_double, c_double, dp]
         L.oracle_gram.argtypes = [c_int, i64, c_double, c_double, c_double, dp, c_int, c_int, dp]
+        L.oracle_gram_ura.argtypes = [c_int, i64, i64, c_double, c_double, c_double, dp, c_int, c_int, dp]
         L.oracle_closed_form.argtypes = [c_int, i64, c_double, c_double, c_double, dp, c_int, c_int, dp]
         L.oracle_beamform.argtypes = [dp, dp, dp, dp, c_int, c_int, c_int, c_int, dp, ip, dp]
         L.oracle_sumrate.argtypes = [dp, c_int, c_int, dp, dp]
         L.oracle_saturation.argtypes = [dp, c_int, c_int, c_double, c_double, dp]
-        for f in ("oracle_channel", "oracle_gram", "oracle_closed_form", "oracle_beamform",
+        for f in ("oracle_channel", "oracle_gram", "oracle_gram_ura", "oracle_closed_form", "oracle_beamform",
                   "oracle_sumrate", "oracle_saturation"):
             getattr(L, f).restype = c_int
         _lib = L
@@ -89,6 +90,19 @@ def gram(model, n_ant, wavelength, spacing, beta0, users):
     rc = lib().oracle_gram(model, n_ant, wavelength, spacing, beta0, _dp(users), K, B, _dp(out))
     if rc:
         raise MemoryError("oracle_gram failed")
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def gram_ura(model, n_ant, rows, wavelength, spacing, beta0, users):
+    """Exact Gram of a URA of `rows` rows of `n_ant` elements (square lattice
+    of the given spacing in the y-z plane, users in the plane z = 0),
+    complex128 [B][K][K]."""
+    users = _f64(users)
+    B, K, _ = users.shape
+    out = np.empty((B, K, K, 2), np.float64)
+    rc = lib().oracle_gram_ura(model, n_ant, rows, wavelength, spacing, beta0, _dp(users), K, B, _dp(out))
+    if rc:
+        raise MemoryError("oracle_gram_ura failed")
     return out[..., 0] + 1j * out[..., 1]
 
 

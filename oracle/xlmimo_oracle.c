@@ -124,6 +124,63 @@ int oracle_gram(int model, int64_t N, double lambda, double spacing, double beta
     return bad ? 3 : 0;
 }
 
+/* Uniform rectangular array (URA), the planar-array extension the paper
+ * names in the footnote of Sec. II: R rows of N elements on the square
+ * lattice of the given spacing in the y-z plane, element (row q, column n) at
+ * (0, y_n, z_q) with z_q = (q - (R-1)/2) * spacing, so R = 1 is the ULA of
+ * Sec. II-A.  Users stay in the horizontal plane z = 0 through the array
+ * centre.  With the 3-D distance r = sqrt(x^2 + (y_n - y)^2 + z_q^2):
+ *   PNUSW       sqrt(beta0) e^{-j 2 pi r / lambda} / r * sqrt(x / r)
+ *               (Eq. 3: the projection of the element aperture on the
+ *               direction of arrival, cos = x / r, x along the array normal);
+ *   free space  (lambda / (4 pi r)) e^{-j 2 pi r / lambda};
+ *   UPW         the planar wave of the user's direction (elevation 0), whose
+ *               path difference across the aperture is y_n sin(theta) for
+ *               every row. */
+static cplx channel_entry_ura(int model, double lambda, double beta0, double x, double y, double yn,
+                              double zq) {
+    if (model == ORC_UPW) return channel_entry(model, lambda, beta0, x, y, yn);
+    double r = sqrt(x * x + (yn - y) * (yn - y) + zq * zq);
+    cplx ph = cexp(-I * 2.0 * ORC_PI * r / lambda);
+    if (model == ORC_PNUSW) return sqrt(beta0) * ph / r * sqrt(x / r);
+    return lambda / (4.0 * ORC_PI * r) * ph;
+}
+
+/* Exact Gram H^H H of the URA by explicit inner products over all R * N
+ * elements (row-major element order: row q, then column n). */
+int oracle_gram_ura(int model, int64_t N, int64_t R, double lambda, double spacing, double beta0,
+                    const double* users, int K, int B, double* gram) {
+    int bad = 0;
+    int64_t M = N * R;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int b = 0; b < B; ++b) {
+        cplx* H = (cplx*)malloc(sizeof(cplx) * (size_t)M * (size_t)K);
+        if (!H) { bad = 1; continue; }
+        for (int64_t q = 0; q < R; ++q) {
+            double zq = ((double)q - 0.5 * (double)(R - 1)) * spacing;
+            for (int64_t n = 0; n < N; ++n) {
+                double yn = element_y(n, N, spacing);
+                for (int k = 0; k < K; ++k) {
+                    const double* u = users + ((size_t)b * K + k) * 2;
+                    H[(size_t)(q * N + n) * K + k] = channel_entry_ura(model, lambda, beta0, u[0], u[1], yn, zq);
+                }
+            }
+        }
+        for (int i = 0; i < K; ++i) {
+            for (int j = 0; j < K; ++j) {
+                cplx acc = 0.0;
+                for (int64_t m = 0; m < M; ++m)
+                    acc += conj(H[(size_t)m * K + i]) * H[(size_t)m * K + j];
+                double* g = gram + (((size_t)b * K + i) * K + j) * 2;
+                g[0] = creal(acc);
+                g[1] = cimag(acc);
+            }
+        }
+        free(H);
+    }
+    return bad ? 3 : 0;
+}
+
 /* The bracket of Eq. (4), written with the aperture length N*spacing in
  * place of M*lambda/2 (identical for half-wavelength spacing):
  *   (ML - 4y)/sqrt(16x^2 + (ML-4y)^2) + (ML + 4y)/sqrt(16x^2 + (ML+4y)^2),
