@@ -130,6 +130,26 @@ typedef struct {
 int xlmimo_channel_gram(const xlmimo_array* arr, const double* users, int K, int B, int prec,
                         double* gram, void* stream);
 
+/* Exact Gram matrices of a uniform rectangular array (URA), the planar array
+ * the paper names as an extension in the footnote of Sec. II: `rows` rows of
+ * arr->n_ant elements on the square lattice of arr->spacing in the y-z plane,
+ * element (q, n) at (0, y_n, z_q), z_q = (q - (rows-1)/2) spacing, y_n as for
+ * the ULA; users in the plane z = 0, [B][K][2] (x, y) as above.  The channel
+ * models of xlmimo_model with the 3-D distance r = sqrt(x^2 + (y_n-y)^2 + z_q^2)
+ * (PNUSW keeps the projection sqrt(x / r) on the array normal; UPW is the
+ * planar wave of a user at elevation 0).  rows = 1 is xlmimo_channel_gram.
+ *   rows : 1..XLMIMO_MAX_URA_ROWS, n_ant * rows <= 2^40
+ *   prec : xlmimo_prec, accuracy class as for the ULA
+ *   gram : [B][K][K] complex doubles (device, written)
+ * Computed per row pair: rows at +-z_q see the users alike, so ceil(rows/2)
+ * ULA Grams of users moved to x' = sqrt(x^2 + z_q^2) are summed with the
+ * weights of the amplitude (one for UPW).  Uses up to 1 GiB of stream-ordered
+ * device workspace.  Errors: XLMIMO_EINVAL (arguments), XLMIMO_ENOMEM,
+ * XLMIMO_ECUDA. */
+#define XLMIMO_MAX_URA_ROWS 1048576
+int xlmimo_channel_gram_ura(const xlmimo_array* arr, int64_t rows, const double* users, int K, int B, int prec,
+                            double* gram, void* stream);
+
 /* Size of the fixed device scratch used by xlmimo_channel_gram_noalloc, in MiB. */
 #define XLMIMO_NOALLOC_SCRATCH_MIB 16
 

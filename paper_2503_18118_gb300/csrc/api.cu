@@ -139,6 +139,24 @@ int xlmimo_channel_gram(const xlmimo_array* arr, const double* users, int K, int
     }
 }
 
+int xlmimo_channel_gram_ura(const xlmimo_array* arr, int64_t rows, const double* users, int K, int B, int prec,
+                            double* gram, void* stream) {
+    clear_error();
+    Geom g;
+    int rc = check_array(arr, &g);
+    if (rc) return rc;
+    if ((rc = check_kb(K, B))) return rc;
+    if (rows < 1 || rows > XLMIMO_MAX_URA_ROWS || rows > ((int64_t)1 << 40) / arr->n_ant) {
+        set_error("rows must be in [1, %d] with n_ant * rows <= 2^40, got %lld", XLMIMO_MAX_URA_ROWS,
+                  (long long)rows);
+        return XLMIMO_EINVAL;
+    }
+    if (prec < XLMIMO_F64 || prec > XLMIMO_F16X3) { set_error("unknown precision %d", prec); return XLMIMO_EINVAL; }
+    if (B == 0) return XLMIMO_OK;
+    if (!users || !gram) { set_error("users and gram must be non-NULL"); return XLMIMO_EINVAL; }
+    return launch_gram_ura(g, rows, users, K, B, prec, gram, as_stream(stream));
+}
+
 int xlmimo_corr_closed_form(const xlmimo_array* arr, const double* users, int K, int B, double* gram,
                             void* stream) {
     clear_error();

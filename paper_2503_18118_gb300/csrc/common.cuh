@@ -33,6 +33,9 @@ int launch_gram_f64(const Geom& g, const double* users, int K, int B, double* gr
 int launch_gram_f32(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st);
 int launch_gram_tc(const Geom& g, const double* users, int K, int B, int prec, double* gram, cudaStream_t st,
                    int ctas_per_sm = 0);
+// URA of `rows` rows of g.N elements (rows >= 1) by row decomposition.
+int launch_gram_ura(const Geom& g, int64_t rows, const double* users, int K, int B, int prec, double* gram,
+                    cudaStream_t st);
 // threads per block: 256 alone; 64 lets a block (44 registers a thread) fit
 // beside three tensor-core Gram CTAs on an SM, so that it runs during the Gram.
 int launch_closed_form(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st,

@@ -21,6 +21,7 @@ DIST_RECT, DIST_POLAR = 0, 1
 APERTURE_NONE, APERTURE_MASK, APERTURE_FRESNEL = 0, 1, 2
 MAX_USERS = 64
 MAX_BOUNDS_USERS = 1024
+MAX_URA_ROWS = 1048576
 STATUS = {0: "OK", 1: "EINVAL", 2: "ECUDA", 3: "ENOMEM", 4: "ESINGULAR", 5: "ETIMEOUT", 6: "EUNSUPPORTED"}
 
 
@@ -67,7 +68,7 @@ class Inst(ctypes.Structure):
 
 
 EXPORTS = ("xlmimo_batch_plan_create", "xlmimo_batch_run", "xlmimo_batch_plan_info", "xlmimo_batch_plan_destroy",
-           "xlmimo_mc_step", "xlmimo_channel_gram", "xlmimo_channel_gram_noalloc", "xlmimo_corr_closed_form",
+           "xlmimo_mc_step", "xlmimo_channel_gram", "xlmimo_channel_gram_ura", "xlmimo_channel_gram_noalloc", "xlmimo_corr_closed_form",
            "xlmimo_corr_closed_form_aperture", "xlmimo_beamform", "xlmimo_sumrate",
            "xlmimo_saturation", "xlmimo_saturation_analytic", "xlmimo_capacity_sweep", "xlmimo_capacity_bounds",
            "xlmimo_pair_features",
@@ -94,6 +95,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L = ctypes.CDLL(_build.LIB)
     vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
     L.xlmimo_channel_gram.argtypes = [ctypes.POINTER(Array), vp, i32, i32, i32, vp, vp]
+    L.xlmimo_channel_gram_ura.argtypes = [ctypes.POINTER(Array), ctypes.c_int64, vp, i32, i32, i32, vp, vp]
     L.xlmimo_mc_step.argtypes = [ctypes.POINTER(McBatch), vp]
     L.xlmimo_batch_plan_create.argtypes = [ctypes.POINTER(Array), ctypes.POINTER(Inst), i32, i32, vp,
                                            ctypes.POINTER(vp), vp]
@@ -169,6 +171,19 @@ def xlmimo_channel_gram(arr: Array, users: torch.Tensor, prec: int = F32, gram: 
         gram = torch.empty((B, K, K), dtype=torch.complex128, device=users.device)
     _check(lib().xlmimo_channel_gram(ctypes.byref(arr), _dev(users, torch.float64, "users", (B, K, 2)), K, B,
                                      int(prec), _dev(gram, torch.complex128, "gram", (B, K, K)), _stream(stream)))
+    return gram
+
+
+def xlmimo_channel_gram_ura(arr: Array, rows: int, users: torch.Tensor, prec: int = F32,
+                            gram: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Exact Gram matrices of a URA of `rows` rows of arr.n_ant elements
+    (users in the plane z = 0), complex128 [B][K][K]."""
+    B, K = users.shape[0], users.shape[1]
+    if gram is None:
+        gram = torch.empty((B, K, K), dtype=torch.complex128, device=users.device)
+    _check(lib().xlmimo_channel_gram_ura(ctypes.byref(arr), ctypes.c_int64(int(rows)),
+                                         _dev(users, torch.float64, "users", (B, K, 2)), K, B, int(prec),
+                                         _dev(gram, torch.complex128, "gram", (B, K, K)), _stream(stream)))
     return gram
 
 

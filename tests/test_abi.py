@@ -128,3 +128,17 @@ def test_capacity_bounds_validates_on_host(xl):
     assert L.xlmimo_capacity_bounds(ctypes.byref(arr), dummy, 8, 1, float("nan"), dummy, None) == 1
     assert L.xlmimo_capacity_bounds(ctypes.byref(arr), None, 8, 1, 1.0, dummy, None) == 1
     assert L.xlmimo_capacity_bounds(ctypes.byref(arr), None, 8, 0, 1.0, None, None) == 0
+
+
+def test_gram_ura_validates_on_host(xl):
+    L = xl.lib()
+    dummy = ctypes.c_void_p(16)
+    arr = xl.array(1024, 0.01)
+    assert L.xlmimo_channel_gram_ura(ctypes.byref(arr), 0, dummy, 8, 1, 1, dummy, None) == 1
+    assert L.xlmimo_channel_gram_ura(ctypes.byref(arr), xl.MAX_URA_ROWS + 1, dummy, 8, 1, 1, dummy, None) == 1
+    big = xl.array(1 << 30, 0.01)
+    assert L.xlmimo_channel_gram_ura(ctypes.byref(big), 1025, dummy, 8, 1, 1, dummy, None) == 1
+    assert L.xlmimo_channel_gram_ura(ctypes.byref(arr), 4, dummy, 8, 1, 9, dummy, None) == 1
+    assert L.xlmimo_channel_gram_ura(ctypes.byref(arr), 4, None, 8, 1, 1, dummy, None) == 1
+    assert L.xlmimo_channel_gram_ura(ctypes.byref(arr), 4, dummy, xl.MAX_USERS + 1, 1, 1, dummy, None) == 1
+    assert L.xlmimo_channel_gram_ura(ctypes.byref(arr), 4, None, 8, 0, 1, None, None) == 0
