@@ -333,6 +333,63 @@ def appendix_a_bench(xl, torch, max_mhz):
     return out
 
 
+def ura_bench(xl, torch):
+    """Uniform rectangular arrays (the planar-array extension of the footnote
+    of Sec. II): the headline's users (100 GHz, K = 32, r in [3, 30] m,
+    |theta| <= 60 deg, 10^4 trials, free-space spherical wave) on URAs of 16384
+    elements, Gram time at BF16x3 and FP32 beside the ULA of the same element
+    count, and accuracy on 64 trials against the FP64 URA path (normwise Gram
+    error; MMSE sum rate at 10 dB)."""
+    wl = inputs.HEADLINE
+    U = torch.from_numpy(wl.users()).cuda()
+    B, K = U.shape[0], U.shape[1]
+    G = torch.empty((B, K, K), dtype=torch.complex128, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    snr = torch.from_numpy(wl.power(64)).cuda()
+    noise = torch.from_numpy(wl.noise(64)).cuda()
+
+    def timed(fn, reps=3, warm=1):
+        for _ in range(warm):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    def rate(Gs):
+        s, _, _ = xl.xlmimo_beamform(Gs, snr, noise, xl.MMSE, xl.POWER_RXSNR)
+        return torch.log2(1 + s).sum(1).cpu().numpy()
+
+    out = {"workload": f"{wl.name} users on 16384-element URAs (rows x columns), users in the array's horizontal plane",
+           "ula_bf16x3_ms": timed(lambda: xl.xlmimo_channel_gram(xl.array(wl.n_ant, wl.wavelength, model=wl.model),
+                                                                   U, xl.BF16X3, G)),
+           "shapes": {}}
+    for rows, cols in ((128, 128), (16, 1024)):
+        arr = xl.array(cols, wl.wavelength, model=wl.model)
+        r = {}
+        for name, pp in (("bf16x3", xl.BF16X3), ("f32", xl.F32)):
+            ms = timed(lambda: xl.xlmimo_channel_gram_ura(arr, rows, U, pp, G))
+            r[name] = {"ms": ms, "trials_per_s": B / (ms / 1e3),
+                       "entries_per_s": float(rows) * cols * K * B / (ms / 1e3)}
+        U64 = U[:64].contiguous()
+        g64 = xl.xlmimo_channel_gram_ura(arr, rows, U64, xl.F64)
+        r64 = rate(g64)
+        d = torch.sqrt(torch.diagonal(g64, dim1=1, dim2=2).real)
+        for name, pp in (("bf16x3", xl.BF16X3), ("f32", xl.F32)):
+            gx = xl.xlmimo_channel_gram_ura(arr, rows, U64, pp)
+            r[name]["gram_normwise_err"] = float(((gx - g64).abs() / (d[:, :, None] * d[:, None, :])).max())
+            r[name]["sumrate_rel_err"] = float(np.max(np.abs(rate(gx) - r64) / r64))
+        out["shapes"][f"{rows}x{cols}"] = r
+    del G, flush
+    return out
+
+
 def surrogate_bench(xl, torch, peaks):
     """Learned correlation surrogate: labels from the exact kernel, training on
     the GPU, then the fused tensor-core inference timed at 100 GHz, N = 2^18,
@@ -560,6 +617,7 @@ def main():
     sur = None
     sweep = None
     app_a = None
+    ura = None
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -580,6 +638,7 @@ def main():
         sweep = sweep_bench(xl, torch)
         sur = surrogate_bench(xl, torch, peaks)
         app_a = appendix_a_bench(xl, torch, float(peaks.get("sm_max_mhz", 2070.0)))
+        ura = ura_bench(xl, torch)
 
     # peaks from unit counts and the maximum SM clock (per SM per clock:
     # 128 FP32 FMA lanes, 16 MUFU transcendental units, 2 FP64 FMA lanes)
@@ -636,6 +695,7 @@ def main():
         "sweep": sweep,
         "surrogate": sur,
         "appendix_a": app_a,
+        "ura": ura,
         "speedup_vs_fp64_gpu": (value / fp64["trials_per_s"]) if fp64 else None,
         "roofline": roof,
         "cpu_baseline": cpu,

@@ -143,8 +143,8 @@ int xlmimo_channel_gram(const xlmimo_array* arr, const double* users, int K, int
  *   gram : [B][K][K] complex doubles (device, written)
  * Computed per row pair: rows at +-z_q see the users alike, so ceil(rows/2)
  * ULA Grams of users moved to x' = sqrt(x^2 + z_q^2) are summed with the
- * weights of the amplitude (one for UPW).  Uses up to 1 GiB of stream-ordered
- * device workspace.  Errors: XLMIMO_EINVAL (arguments), XLMIMO_ENOMEM,
+ * weights of the amplitude (one for UPW).  Uses stream-ordered device
+ * workspace: up to 1 GiB, or one trial's ceil(rows/2) K x K Grams if larger.  Errors: XLMIMO_EINVAL (arguments), XLMIMO_ENOMEM,
  * XLMIMO_ECUDA. */
 #define XLMIMO_MAX_URA_ROWS 1048576
 int xlmimo_channel_gram_ura(const xlmimo_array* arr, int64_t rows, const double* users, int K, int B, int prec,

@@ -14,9 +14,9 @@
 // row: one ULA Gram times R.
 //
 // The per-row Grams are the library's ULA Gram launchers (any precision) over
-// B * Q virtual trials, Q = ceil(R / 2), in stream-ordered workspace; a
-// combine kernel sums them in increasing q.  Work is R/2 row evaluations of N
-// elements per user instead of R.
+// B * Q virtual trials, Q = ceil(R / 2), in stream-ordered workspace, chunk
+// by chunk; a combine kernel sums them in increasing q.  Work is R/2 row
+// evaluations of N elements per user instead of R.
 #include <math.h>
 
 #include "common.cuh"
@@ -57,6 +57,7 @@ __global__ void ura_combine_kernel(const double2* __restrict__ gv, const double*
         int ij = (int)(e - b * kk);
         int i = ij / K, j = ij - i * K;
         double re = 0.0, im = 0.0;
+#pragma unroll 8
         for (int q = 0; q < Q; ++q) {
             int64_t t = b * Q + q;
             double m = model == XLMIMO_UPW ? (double)R : ((R & 1) && q == 0) ? 1.0 : 2.0;
@@ -89,10 +90,19 @@ int launch_gram_ura(const Geom& g, int64_t rows, const double* users, int K, int
                     cudaStream_t st) {
     if (rows == 1) return launch_gram_prec(g, users, K, B, prec, gram, st);
     int Q = g.model == XLMIMO_UPW ? 1 : (int)((rows + 1) / 2);
-    // workspace per trial: Q ULA Grams, Q virtual user sets and weights
+    // Workspace per trial: Q ULA Grams, Q virtual user sets and weights; up
+    // to 1 GiB a chunk.  (Chunks small enough for the per-row Grams to stay in
+    // L2 were slower: more launches with their ramp and tail, and combine
+    // grids too small to keep the loads in flight.)  Chunks are rounded to
+    // whole waves of Gram CTAs (three per SM for K <= 32, two above).
     size_t per_trial = (size_t)Q * K * ((size_t)K * sizeof(double2) + sizeof(double2) + sizeof(double));
     const size_t budget = size_t(1) << 30;
     int64_t bc = (int64_t)(budget / per_trial);
+    const int64_t wave = (int64_t)num_sms() * (K <= 32 ? 3 : 2);
+    int64_t a = wave, c = Q;  // trials per whole wave of virtual trials: wave / gcd(wave, Q)
+    while (c) { int64_t t = a % c; a = c; c = t; }
+    const int64_t step = wave / a;
+    if (bc >= step) bc -= bc % step;
     if (bc < 1) bc = 1;
     if (bc > B) bc = B;
     if (bc * Q > INT32_MAX) bc = INT32_MAX / Q;

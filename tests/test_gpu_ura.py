@@ -73,12 +73,13 @@ def test_one_row_is_the_ula_call(xl, prec):
 
 def test_workspace_chunks(xl, orc):
     """Enough rows that the 1 GiB workspace holds fewer trials than the batch
-    (K = 64, 512 row pairs: 34 MB a trial, 31 trials a chunk); trials of the
-    first and the last chunk against the oracle."""
+    (K = 64, 512 row pairs: 34 MB a trial, at most 31 trials a chunk, 19 after
+    rounding to whole waves of 152 x 2 Gram CTAs); trials on both sides of
+    those boundaries and the last one against the oracle."""
     N, R, K, B = 16, 1024, 64, 40
     users = inputs.users_rect(99, B, K, (0.5, 3.0), (-1.5, 1.5))
     G = xl.xlmimo_channel_gram_ura(xl.array(N, LAM100, model=0), R, dev(users), 1).cpu().numpy()
-    for b in (0, 30, 31, 39):
+    for b in (0, 18, 19, 30, 31, 37, 38, 39):
         ref = orc.gram_ura(0, N, R, LAM100, LAM100 / 2, 1.0, users[b:b + 1])
         assert normwise(G[b:b + 1], ref) <= 1e-5
 
