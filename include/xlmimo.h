@@ -512,6 +512,15 @@ const char* xlmimo_last_error(void);
 /* Interface version, (major << 16) | minor. */
 int xlmimo_version(void);
 
+/* Releases what the library keeps between calls: the stream and events that
+ * xlmimo_mc_step creates on first use on each device (work already enqueued
+ * there completes first).  The library stays usable; the next call creates
+ * them again.  Must not run concurrently with another library call.  The
+ * scratch of xlmimo_channel_gram_noalloc is part of the library's module
+ * and lives as long as the CUDA context.  Returns XLMIMO_OK, or
+ * XLMIMO_ECUDA if a device could not be selected or synchronised. */
+int xlmimo_shutdown(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -147,3 +147,30 @@ extern "C" int xlmimo_mc_step(const xlmimo_mc_batch* j, void* stream) {
     if (!rc2) rc2 = cuda_status(cudaStreamWaitEvent(s0, ps->side_done, 0), "stream wait");
     return rc ? rc : rc2;
 }
+
+// Release the pipeline's per-device stream and events (created by the first
+// xlmimo_mc_step on a device); work already enqueued on the side stream
+// completes first.  The next xlmimo_mc_step creates them again.
+extern "C" int xlmimo_shutdown(void) {
+    clear_error();
+    std::lock_guard<std::mutex> lk(g_pipe_mu);
+    int caller = -1, rc = XLMIMO_OK;
+    for (int dev = 0; dev < (int)g_pipe.size(); ++dev) {
+        PipeState& p = g_pipe[dev];
+        if (!p.ready) continue;
+        if (caller < 0 && (rc = cuda_status(cudaGetDevice(&caller), "cudaGetDevice"))) return rc;
+        int r = cuda_status(cudaSetDevice(dev), "cudaSetDevice");
+        if (!r) r = cuda_status(cudaStreamSynchronize(p.side), "side stream synchronize");
+        for (int i = 0; i < PIPE_MAX_CHUNKS; ++i) cudaEventDestroy(p.gram_done[i]);
+        cudaEventDestroy(p.inputs_ready);
+        cudaEventDestroy(p.side_done);
+        cudaStreamDestroy(p.side);
+        p = PipeState();
+        if (!rc) rc = r;
+    }
+    if (caller >= 0) {
+        int r = cuda_status(cudaSetDevice(caller), "cudaSetDevice");
+        if (!rc) rc = r;
+    }
+    return rc;
+}

@@ -73,7 +73,8 @@ EXPORTS = ("xlmimo_batch_plan_create", "xlmimo_batch_run", "xlmimo_batch_plan_in
            "xlmimo_saturation", "xlmimo_saturation_analytic", "xlmimo_capacity_sweep", "xlmimo_capacity_bounds",
            "xlmimo_pair_features",
            "xlmimo_mlp_forward", "xlmimo_mlp_loss", "xlmimo_mlp_work_floats", "xlmimo_mlp_backward", "xlmimo_mlp_adam",
-           "xlmimo_mlp_train_step", "xlmimo_mlp_pack", "xlmimo_surrogate_gram", "xlmimo_last_error", "xlmimo_version")
+           "xlmimo_mlp_train_step", "xlmimo_mlp_pack", "xlmimo_surrogate_gram", "xlmimo_shutdown", "xlmimo_last_error",
+           "xlmimo_version")
 
 MLP_IN, MLP_WIDTH, MLP_HIDDEN, MLP_OUT = 6, 256, 4, 2
 MLP_PARAMS = 199682
@@ -161,6 +162,11 @@ def array(n_ant, wavelength, spacing=None, beta0=1.0, model=FSPL_USW) -> Array:
 
 def xlmimo_version() -> int:
     return int(lib().xlmimo_version())
+
+
+def xlmimo_shutdown() -> None:
+    """Release the library's per-device pipeline stream and events."""
+    _check(lib().xlmimo_shutdown())
 
 
 def xlmimo_channel_gram(arr: Array, users: torch.Tensor, prec: int = F32, gram: torch.Tensor | None = None,

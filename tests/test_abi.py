@@ -142,3 +142,7 @@ def test_gram_ura_validates_on_host(xl):
     assert L.xlmimo_channel_gram_ura(ctypes.byref(arr), 4, None, 8, 1, 1, dummy, None) == 1
     assert L.xlmimo_channel_gram_ura(ctypes.byref(arr), 4, dummy, xl.MAX_USERS + 1, 1, 1, dummy, None) == 1
     assert L.xlmimo_channel_gram_ura(ctypes.byref(arr), 4, None, 8, 0, 1, None, None) == 0
+
+
+def test_shutdown_without_state_is_a_no_op(xl):
+    assert xl.lib().xlmimo_shutdown() == 0

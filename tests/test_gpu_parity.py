@@ -436,3 +436,23 @@ def test_mc_step_downlink(xl):
     torch.cuda.synchronize()
     assert torch.equal(out.sinr, s) and torch.equal(out.sinr_cf, s2)
     assert torch.equal(out.status, st) and torch.equal(out.status_cf, st2)
+
+
+def test_shutdown_releases_and_recreates(xl):
+    """xlmimo_shutdown frees the pipeline's stream and events; the next step
+    recreates them and gives the same results, bit for bit."""
+    B, K, N = 40, 8, 3000
+    users = dev(inputs.users_polar(79, B, K, (3.0, 30.0)))
+    snr = dev(np.full((B, K), 10.0))
+    noise = dev(np.ones(B))
+    arr = xl.array(N, LAM100)
+    outs = []
+    for _ in range(2):
+        out = xl.McBuffers(B, K)
+        xl.xlmimo_mc_step(arr, users, snr, noise, out, prec=xl.F32, scheme=xl.MMSE, cf_scheme=xl.ZF)
+        torch.cuda.synchronize()
+        outs.append(out)
+        xl.xlmimo_shutdown()
+        xl.xlmimo_shutdown()  # nothing left to release
+    assert torch.equal(outs[0].rate, outs[1].rate) and torch.equal(outs[0].rate_cf, outs[1].rate_cf)
+    assert torch.equal(outs[0].gram, outs[1].gram)
