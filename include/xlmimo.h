@@ -141,10 +141,13 @@ int xlmimo_channel_gram(const xlmimo_array* arr, const double* users, int K, int
  *   rows : 1..XLMIMO_MAX_URA_ROWS, n_ant * rows <= 2^40
  *   prec : xlmimo_prec, accuracy class as for the ULA
  *   gram : [B][K][K] complex doubles (device, written)
- * Computed per row pair: rows at +-z_q see the users alike, so ceil(rows/2)
- * ULA Grams of users moved to x' = sqrt(x^2 + z_q^2) are summed with the
- * weights of the amplitude (one for UPW).  Uses stream-ordered device
- * workspace: up to 1 GiB, or one trial's ceil(rows/2) K x K Grams if larger.  Errors: XLMIMO_EINVAL (arguments), XLMIMO_ENOMEM,
+ * Computed per row pair: rows at +-z_q see the users alike, and row q sees
+ * them as the ULA sees users moved to x' = sqrt(x^2 + z_q^2).  At
+ * XLMIMO_BF16X3 with n_ant a multiple of 128 up to 1024 (PNUSW, free space) the
+ * tensor-core Gram accumulates all ceil(rows/2) row pairs of a trial in one
+ * pass; otherwise ceil(rows/2) ULA Grams are summed with the weights of the
+ * amplitude (one for UPW) in stream-ordered device workspace (up to 1 GiB,
+ * or one trial's ceil(rows/2) K x K Grams if larger).  Errors: XLMIMO_EINVAL (arguments), XLMIMO_ENOMEM,
  * XLMIMO_ECUDA. */
 #define XLMIMO_MAX_URA_ROWS 1048576
 int xlmimo_channel_gram_ura(const xlmimo_array* arr, int64_t rows, const double* users, int K, int B, int prec,

@@ -33,9 +33,16 @@ int launch_gram_f64(const Geom& g, const double* users, int K, int B, double* gr
 int launch_gram_f32(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st);
 int launch_gram_tc(const Geom& g, const double* users, int K, int B, int prec, double* gram, cudaStream_t st,
                    int ctas_per_sm = 0);
-// URA of `rows` rows of g.N elements (rows >= 1) by row decomposition.
+// URA of `rows` rows of g.N elements (rows >= 1): the tensor-core Gram's URA
+// mode where it applies, else per-row-pair ULA Grams.
 int launch_gram_ura(const Geom& g, int64_t rows, const double* users, int K, int B, int prec, double* gram,
                     cudaStream_t st);
+// URA mode of the tensor-core Gram (BF16 hi/lo, spherical-wave models, rows of
+// ncol elements, ncol a multiple of 128, on an sm_103 device): all row pairs
+// of a trial accumulated in one pass.
+bool gram_tc_ura_supported(const Geom& g, int64_t ncol, int prec);
+int launch_gram_tc_ura(const Geom& g, int64_t ncol, int64_t rows, const double* users, int K, int B, double* gram,
+                       cudaStream_t st);
 // threads per block: 256 alone; 64 lets a block (44 registers a thread) fit
 // beside three tensor-core Gram CTAs on an SM, so that it runs during the Gram.
 int launch_closed_form(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st,

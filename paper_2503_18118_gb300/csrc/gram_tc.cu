@@ -53,11 +53,36 @@ struct GtRing {
     static constexpr uint32_t BYTES = (uint32_t)TcCfg<KMAX>::STAGE_BYTES * SUBS;  // per ring stage
 };
 
-template <int MODEL, int KMAX, int PREC>
+// URA mode (uniform rectangular array, users in the plane z = 0): a trial's
+// elements are its ceil(R/2) mirrored row pairs one after another, ncol per
+// row, ncol a multiple of URA_SPAN so that no reference span crosses a row.
+// Row q, at height z_q = (q + zoff) spacing, sees user (x, y) as the ULA sees
+// (x', y), x' = sqrt(x^2 + z_q^2): each span takes its phase reference and
+// distances from x'.  The amplitude constant stays the true user's (PNUSW
+// projects on the array normal: sqrt(beta0 x) r^{-3/2}) in the FP64 factor,
+// which also carries the factor 2 of the mirrored pair; the centre row of an
+// odd R (counted once) is generated with amplitude 1/sqrt(2).
+struct UraRows {
+    long long ncol;  // elements per row (0: ULA mode)
+    double zoff;     // 0 for odd R, 1/2 for even R
+    double spacing;
+    int odd;
+};
+constexpr int URA_SPAN = 128;
+
+template <int KMAX>
+struct UraShared {
+    double ux[KMAX], uy[KMAX];  // the users' true positions
+    float2 rowc[2][KMAX];       // (x'/lambda)^2 and 2 (x'/lambda)^2 of the current and the next span's row
+    float roww[2];              // amplitude weight of those rows
+};
+
+template <int MODEL, int KMAX, int PREC, bool URA>
 __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
     gram_tc_kernel(Geom g, GenParams gp, const double* __restrict__ users, int K, int S, int64_t chunk,
-                   double2* __restrict__ out) {
+                   double2* __restrict__ out, UraRows ura) {
     using C = TcCfg<KMAX>;
+    static_assert(!URA || PREC == TCP_BF16X3, "the URA mode generates weighted entries for the BF16 hi/lo split");
     using RG = GtRing<KMAX>;
     extern __shared__ unsigned char smem_raw[];
     // stages must be 1024-byte aligned for the 128-byte swizzle
@@ -65,6 +90,7 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
     unsigned char* stages = base;
     TcShared<KMAX>* sh = reinterpret_cast<TcShared<KMAX>*>(base + RG::NRING * RG::BYTES);
     float* fold = reinterpret_cast<float*>(base);  // epilogue reuses the stages
+    UraShared<KMAX>* ush = reinterpret_cast<UraShared<KMAX>*>(reinterpret_cast<unsigned char*>(sh) + sizeof(TcShared<KMAX>));
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int b = blockIdx.x, s = blockIdx.y;
@@ -97,6 +123,11 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
         // apply it to the Gram in FP64; the FP16 path scales user k's entries by
         // 1/|h_k| at the array centre so that they sit near 1, and divides it out
         double fac = amp_const(g, x, y);
+        if (URA) {
+            ush->ux[tid] = x;
+            ush->uy[tid] = y;
+            fac *= 1.4142135623730951;  // fac_i fac_j carries the 2 of a mirrored row pair
+        }
         if (PREC == TCP_F16X3) {
             const double rc = sqrt(x * x + y * y) * g.inv_lambda;  // distance in wavelengths
             double amp_c = (MODEL == XLMIMO_UPW) ? fac : (MODEL == XLMIMO_PNUSW) ? fac / (rc * sqrt(rc)) : fac / rc;
@@ -125,11 +156,26 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
         // the eight generator warps meet at a named barrier at every span
         // start.  That barrier also votes on stopping, so that after an abort
         // all 256 generator threads leave the loop together.
-        constexpr int SPAN_ST = TC_REF_SPAN / RG::T;  // stages per span
+        constexpr int SPAN = URA ? URA_SPAN : TC_REF_SPAN;
+        constexpr int SPAN_ST = SPAN / RG::T;  // stages per span
         const int nsp = (nst + SPAN_ST - 1) / SPAN_ST;
         auto make_refs = [&](int sp) {
-            const long long ncs = (long long)(nbeg + (int64_t)sp * TC_REF_SPAN + TC_REF_SPAN / 2);
-            for (int kk = lane; kk < KMAX; kk += 32) sh->ref[sp & 1][kk] = make_user_ref(gp, sh->ug[kk], ncs);
+            const long long m0 = (long long)(nbeg + (int64_t)sp * SPAN);
+            if (URA) {
+                const long long q = m0 / ura.ncol;
+                const long long ncs = m0 - q * ura.ncol + SPAN / 2;  // span centre, column index in the row
+                const double z = ((double)q + ura.zoff) * ura.spacing;
+                for (int kk = lane; kk < KMAX; kk += 32) {
+                    const double x = ush->ux[kk];
+                    const UserGeo ug = make_user_geo(g, sqrt(fma(x, x, z * z)), ush->uy[kk]);
+                    sh->ref[sp & 1][kk] = make_user_ref(gp, ug, ncs);
+                    ush->rowc[sp & 1][kk] = make_float2(ug.xl2, ug.x2x2);
+                }
+                if (lane == 0) ush->roww[sp & 1] = (ura.odd && q == 0) ? 0.70710678118654752f : 1.0f;
+            } else {
+                const long long ncs = m0 + SPAN / 2;
+                for (int kk = lane; kk < KMAX; kk += 32) sh->ref[sp & 1][kk] = make_user_ref(gp, sh->ug[kk], ncs);
+            }
         };
         if (warp == 0 && nsp > 0) make_refs(0);
         // stage-tile offsets of this lane's four component rows (slot 0, slot 1)
@@ -162,10 +208,15 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
                     : "r"(mine)
                     : "memory");
                 if (stop) break;
-                mf0 = (float)(warp * 8 - TC_REF_SPAN / 2);
+                mf0 = (float)(warp * 8 - SPAN / 2);
                 if (C::SLOTS == 1) {
-                    const UserGeo& u = sh->ug[lane];
-                    pc = make_pair_const(sh->ref[sp & 1][lane], gp.dprime_f, u.xl2, u.x2x2, lane < K ? u.ampc : 0.f);
+                    if (URA) {
+                        const float2 rc = ush->rowc[sp & 1][lane];
+                        pc = make_pair_const(sh->ref[sp & 1][lane], gp.dprime_f, rc.x, rc.y, lane < K ? ush->roww[sp & 1] : 0.f);
+                    } else {
+                        const UserGeo& u = sh->ug[lane];
+                        pc = make_pair_const(sh->ref[sp & 1][lane], gp.dprime_f, u.xl2, u.x2x2, lane < K ? u.ampc : 0.f);
+                    }
                 }
                 if (warp == ((sp + 1) & 7) && sp + 1 < nsp) make_refs(sp + 1);
             } else {
@@ -185,8 +236,13 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
             for (int slot = 0; slot < C::SLOTS; ++slot) {
                 const int k = lane + 32 * slot;
                 if (C::SLOTS > 1) {
-                    const UserGeo& u = sh->ug[k];
-                    pc = make_pair_const(sh->ref[sp & 1][k], gp.dprime_f, u.xl2, u.x2x2, k < K ? u.ampc : 0.f);
+                    if (URA) {
+                        const float2 rc = ush->rowc[sp & 1][k];
+                        pc = make_pair_const(sh->ref[sp & 1][k], gp.dprime_f, rc.x, rc.y, k < K ? ush->roww[sp & 1] : 0.f);
+                    } else {
+                        const UserGeo& u = sh->ug[k];
+                        pc = make_pair_const(sh->ref[sp & 1][k], gp.dprime_f, u.xl2, u.x2x2, k < K ? u.ampc : 0.f);
+                    }
                 }
 #pragma unroll
                 for (int sub = 0; sub < RG::SUBS; ++sub) {
@@ -201,7 +257,7 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
 #pragma unroll
                         for (int i = 0; i < 8; i += 2) {
                             float2 re, im;
-                            gen_pair<MODEL, PREC != TCP_F16X3>(pc, make_float2(fmaf((float)i, dp, u0), fmaf((float)(i + 1), dp, u0)),
+                            gen_pair<MODEL, !URA && PREC != TCP_F16X3>(pc, make_float2(fmaf((float)i, dp, u0), fmaf((float)(i + 1), dp, u0)),
                                                                 make_float2((float)i - 3.5f, (float)i - 2.5f), base, re, im);
                             if (decltype(partial)::value) {
                                 if (i >= rs) { re.x = 0.f; im.x = 0.f; }
@@ -329,17 +385,18 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
 }
 
 template <int KMAX>
-static size_t tc_smem_bytes() {
-    return 1024 + GtRing<KMAX>::NRING * GtRing<KMAX>::BYTES + sizeof(TcShared<KMAX>);
+static size_t tc_smem_bytes(bool ura = false) {
+    return 1024 + GtRing<KMAX>::NRING * GtRing<KMAX>::BYTES + sizeof(TcShared<KMAX>) +
+           (ura ? sizeof(UraShared<KMAX>) : 0);
 }
 
-using TcKernel = void (*)(Geom, GenParams, const double*, int, int, int64_t, double2*);
+using TcKernel = void (*)(Geom, GenParams, const double*, int, int, int64_t, double2*, UraRows);
 
 template <int MODEL, int KMAX>
 static TcKernel pick_prec(int prec) {
-    return prec == XLMIMO_BF16 ? gram_tc_kernel<MODEL, KMAX, TCP_BF16>
-         : prec == XLMIMO_F16X3 ? gram_tc_kernel<MODEL, KMAX, TCP_F16X3>
-                                : gram_tc_kernel<MODEL, KMAX, TCP_BF16X3>;
+    return prec == XLMIMO_BF16 ? gram_tc_kernel<MODEL, KMAX, TCP_BF16, false>
+         : prec == XLMIMO_F16X3 ? gram_tc_kernel<MODEL, KMAX, TCP_F16X3, false>
+                                : gram_tc_kernel<MODEL, KMAX, TCP_BF16X3, false>;
 }
 
 template <int KMAX>
@@ -349,16 +406,72 @@ static TcKernel pick(int model, int prec) {
                                  : pick_prec<XLMIMO_FSPL_USW, KMAX>(prec);
 }
 
+static bool tc_device(int* dev) {
+    int major = 0, minor = 0;
+    cudaGetDevice(dev);
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, *dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, *dev);
+    return major == 10 && minor == 3;
+}
+
+// Launch over B trials of g.N elements in S element chunks (multiples of
+// `span`), reducing chunk partials when S > 1.
+static int launch_tc_chunks(TcKernel kern, size_t smem, const Geom& g, const GenParams& gp, int span,
+                            const double* users, int K, int B, double* gram, const UraRows& ura, cudaStream_t st) {
+    int S = choose_split(g.N, B, span, 4);
+    int64_t spans = (g.N + span - 1) / span;
+    int64_t chunk = ((spans + S - 1) / S) * span;
+    S = (int)((g.N + chunk - 1) / chunk);
+    double* part = nullptr;
+    if (S > 1) {
+        int rc = cuda_status(cudaMallocAsync((void**)&part, (size_t)B * S * K * K * sizeof(double2), st),
+                             "workspace allocation");
+        if (rc) return rc;
+    }
+    dim3 grid(B, S);
+    kern<<<grid, TC_THREADS, smem, st>>>(g, gp, users, K, S, chunk, (double2*)(S == 1 ? gram : part), ura);
+    int rc = cuda_status(cudaGetLastError(), "gram_tc launch");
+    if (!rc && S > 1) rc = launch_reduce_partials(part, S, K, B, gram, st);
+    if (part) cudaFreeAsync(part, st);
+    return rc;
+}
+
+bool gram_tc_ura_supported(const Geom& g, int64_t ncol, int prec) {
+    int dev = 0;
+    return prec == XLMIMO_BF16X3 && g.model != XLMIMO_UPW && ncol % URA_SPAN == 0 && tc_device(&dev);
+}
+
+int launch_gram_tc_ura(const Geom& g, int64_t ncol, int64_t rows, const double* users, int K, int B, double* gram,
+                       cudaStream_t st) {
+    int dev = 0;
+    if (!tc_device(&dev) || ncol % URA_SPAN != 0 || g.model == XLMIMO_UPW) {
+        set_error("the URA mode of the tensor-core Gram needs an sm_103 device, rows of a multiple of %d "
+                  "elements and a spherical-wave model", URA_SPAN);
+        return XLMIMO_EUNSUPPORTED;
+    }
+    const bool wide = K > 32;
+    const bool pn = g.model == XLMIMO_PNUSW;
+    TcKernel kern = wide ? (pn ? gram_tc_kernel<XLMIMO_PNUSW, 64, TCP_BF16X3, true>
+                               : gram_tc_kernel<XLMIMO_FSPL_USW, 64, TCP_BF16X3, true>)
+                         : (pn ? gram_tc_kernel<XLMIMO_PNUSW, 32, TCP_BF16X3, true>
+                               : gram_tc_kernel<XLMIMO_FSPL_USW, 32, TCP_BF16X3, true>);
+    const size_t smem = wide ? tc_smem_bytes<64>(true) : tc_smem_bytes<32>(true);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_status(e, "gram_tc attribute");
+    Geom row = g, all = g;
+    row.N = ncol;                       // element positions within a row
+    all.N = ((rows + 1) / 2) * ncol;    // the trial's elements: its row pairs one after another
+    UraRows ura{(long long)ncol, (rows & 1) ? 0.0 : 0.5, g.spacing, (int)(rows & 1)};
+    return launch_tc_chunks(kern, smem, all, make_gen_params(row), URA_SPAN, users, K, B, gram, ura, st);
+}
+
 // ctas_per_sm > 0 caps the kernel's residency by sizing its shared memory, so
 // that kernels on other streams can run on the same SMs; 0 leaves the
 // residency to the register and shared-memory budget.
 int launch_gram_tc(const Geom& g, const double* users, int K, int B, int prec, double* gram, cudaStream_t st,
                    int ctas_per_sm) {
-    int dev = 0, major = 0, minor = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-    if (major != 10 || minor != 3) {
+    int dev = 0;
+    if (!tc_device(&dev)) {
         set_error("the tensor-core precisions need an sm_103 device (tcgen05)");
         return XLMIMO_EUNSUPPORTED;
     }
@@ -373,22 +486,8 @@ int launch_gram_tc(const Geom& g, const double* users, int K, int B, int prec, d
     }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e, "gram_tc attribute");
-    int S = choose_split(g.N, B, TC_REF_SPAN, 4);
-    int64_t spans = (g.N + TC_REF_SPAN - 1) / TC_REF_SPAN;
-    int64_t chunk = ((spans + S - 1) / S) * TC_REF_SPAN;
-    S = (int)((g.N + chunk - 1) / chunk);
-    double* part = nullptr;
-    if (S > 1) {
-        int rc = cuda_status(cudaMallocAsync((void**)&part, (size_t)B * S * K * K * sizeof(double2), st),
-                             "workspace allocation");
-        if (rc) return rc;
-    }
-    dim3 grid(B, S);
-    kern<<<grid, TC_THREADS, smem, st>>>(g, make_gen_params(g), users, K, S, chunk, (double2*)(S == 1 ? gram : part));
-    int rc = cuda_status(cudaGetLastError(), "gram_tc launch");
-    if (!rc && S > 1) rc = launch_reduce_partials(part, S, K, B, gram, st);
-    if (part) cudaFreeAsync(part, st);
-    return rc;
+    return launch_tc_chunks(kern, smem, g, make_gen_params(g), TC_REF_SPAN, users, K, B, gram, UraRows{0, 0.0, 0.0, 0},
+                            st);
 }
 
 }  // namespace xl

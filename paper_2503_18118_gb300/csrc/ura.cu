@@ -13,7 +13,10 @@
 // an odd R).  The planar wave of a user at elevation 0 is the same on every
 // row: one ULA Gram times R.
 //
-// The per-row Grams are the library's ULA Gram launchers (any precision) over
+// At BF16 hi/lo with rows of a multiple of 128 elements, at most 1024
+// (spherical-wave models), the tensor-core Gram runs the identity itself, all
+// row pairs of a trial in one accumulation (its URA mode).  Otherwise:
+// the per-row Grams are the library's ULA Gram launchers (any precision) over
 // B * Q virtual trials, Q = ceil(R / 2), in stream-ordered workspace, chunk
 // by chunk; a combine kernel sums them in increasing q.  Work is R/2 row
 // evaluations of N elements per user instead of R.
@@ -89,6 +92,11 @@ static int grid_for(int64_t total) {
 int launch_gram_ura(const Geom& g, int64_t rows, const double* users, int K, int B, int prec, double* gram,
                     cudaStream_t st) {
     if (rows == 1) return launch_gram_prec(g, users, K, B, prec, gram, st);
+    // measured at 10^4 trials, K = 32, 16384 elements: the URA mode takes 5.55 ms for
+    // every shape, the row pairs as ULA trials 18.4 (128 columns), 5.1-5.5 (1024)
+    // and 3.8 (4096): long rows amortise the per-trial cost of the ULA kernel
+    if (g.N <= 1024 && gram_tc_ura_supported(g, g.N, prec))
+        return launch_gram_tc_ura(g, g.N, rows, users, K, B, gram, st);
     int Q = g.model == XLMIMO_UPW ? 1 : (int)((rows + 1) / 2);
     // Workspace per trial: Q ULA Grams, Q virtual user sets and weights; up
     // to 1 GiB a chunk.  (Chunks small enough for the per-row Grams to stay in

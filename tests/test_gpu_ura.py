@@ -47,7 +47,10 @@ def f64_tol(users, N, R, model):
     return max(1e-12, 8 * np.finfo(float).eps * (1 + 2 * math.pi * rmax / LAM100) / avg)
 
 
-CASES = [(64, 2, 4, 3), (100, 5, 8, 2), (257, 8, 33, 2), (64, 64, 64, 1), (1000, 3, 32, 2)]
+# rows of a multiple of 128 elements take the tensor-core Gram's URA mode at
+# BF16 hi/lo (one trial: element chunks that cross rows)
+CASES = [(64, 2, 4, 3), (100, 5, 8, 2), (257, 8, 33, 2), (64, 64, 64, 1), (1000, 3, 32, 2),
+         (128, 4, 8, 3), (256, 7, 32, 2), (128, 33, 64, 2), (384, 2, 33, 3), (1024, 64, 16, 1)]
 
 
 @pytest.mark.parametrize("model", [0, 1, 2])
