@@ -72,7 +72,7 @@ constexpr int URA_SPAN = 128;
 
 template <int KMAX>
 struct UraShared {
-    double ux[KMAX], uy[KMAX];  // the users' true positions
+    double ux[KMAX];            // the users' true x
     float2 rowc[2][KMAX];       // (x'/lambda)^2 and 2 (x'/lambda)^2 of the current and the next span's row
     float roww[2];              // amplitude weight of those rows
 };
@@ -125,7 +125,6 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
         double fac = amp_const(g, x, y);
         if (URA) {
             ush->ux[tid] = x;
-            ush->uy[tid] = y;
             fac *= 1.4142135623730951;  // fac_i fac_j carries the 2 of a mirrored row pair
         }
         if (PREC == TCP_F16X3) {
@@ -166,8 +165,15 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
                 const long long ncs = m0 - q * ura.ncol + SPAN / 2;  // span centre, column index in the row
                 const double z = ((double)q + ura.zoff) * ura.spacing;
                 for (int kk = lane; kk < KMAX; kk += 32) {
+                    // the spherical-wave reference reads y, x^2 and 2 (x/lambda)^2 only:
+                    // the user's own geometry with x'^2 = x^2 + z^2 in their place
                     const double x = ush->ux[kk];
-                    const UserGeo ug = make_user_geo(g, sqrt(fma(x, x, z * z)), ush->uy[kk]);
+                    const double x2 = fma(x, x, z * z);
+                    const double xl2 = x2 * (g.inv_lambda * g.inv_lambda);
+                    UserGeo ug = sh->ug[kk];
+                    ug.x2 = ff_from_double(x2);
+                    ug.xl2 = (float)xl2;
+                    ug.x2x2 = (float)(2.0 * xl2);
                     sh->ref[sp & 1][kk] = make_user_ref(gp, ug, ncs);
                     ush->rowc[sp & 1][kk] = make_float2(ug.xl2, ug.x2x2);
                 }

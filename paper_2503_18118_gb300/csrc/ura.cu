@@ -92,7 +92,7 @@ static int grid_for(int64_t total) {
 int launch_gram_ura(const Geom& g, int64_t rows, const double* users, int K, int B, int prec, double* gram,
                     cudaStream_t st) {
     if (rows == 1) return launch_gram_prec(g, users, K, B, prec, gram, st);
-    // measured at 10^4 trials, K = 32, 16384 elements: the URA mode takes 5.55 ms for
+    // measured at 10^4 trials, K = 32, 16384 elements: the URA mode takes 4.42 ms for
     // every shape, the row pairs as ULA trials 18.4 (128 columns), 5.1-5.5 (1024)
     // and 3.8 (4096): long rows amortise the per-trial cost of the ULA kernel
     if (g.N <= 1024 && gram_tc_ura_supported(g, g.N, prec))
