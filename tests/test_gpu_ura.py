@@ -50,7 +50,8 @@ def f64_tol(users, N, R, model):
 # rows of a multiple of 128 elements take the tensor-core Gram's URA mode at
 # BF16 hi/lo (one trial: element chunks that cross rows)
 CASES = [(64, 2, 4, 3), (100, 5, 8, 2), (257, 8, 33, 2), (64, 64, 64, 1), (1000, 3, 32, 2),
-         (128, 4, 8, 3), (256, 7, 32, 2), (128, 33, 64, 2), (384, 2, 33, 3), (1024, 64, 16, 1)]
+         (128, 4, 8, 3), (256, 7, 32, 2), (128, 33, 64, 2), (384, 2, 33, 3), (1024, 64, 16, 1),
+         (1, 3, 1, 2), (128, 5, 1, 2)]
 
 
 @pytest.mark.parametrize("model", [0, 1, 2])
@@ -112,3 +113,9 @@ def test_ura_receivers_end_to_end(xl, orc):
         r = np.sum(np.log2(1 + s.cpu().numpy()), axis=1)
         r_ref = np.sum(np.log2(1 + s_ref), axis=1)
         assert np.max(np.abs(r - r_ref) / r_ref) <= 1e-4
+
+
+def test_empty_batch(xl):
+    users = torch.empty((0, 4, 2), dtype=torch.float64, device="cuda")
+    G = xl.xlmimo_channel_gram_ura(xl.array(128, LAM100, model=0), 3, users, xl.BF16X3)
+    assert G.shape == (0, 4, 4)
