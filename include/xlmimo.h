@@ -134,21 +134,25 @@ int xlmimo_channel_gram(const xlmimo_array* arr, const double* users, int K, int
  * the paper names as an extension in the footnote of Sec. II: `rows` rows of
  * arr->n_ant elements on the square lattice of arr->spacing in the y-z plane,
  * element (q, n) at (0, y_n, z_q), z_q = (q - (rows-1)/2) spacing, y_n as for
- * the ULA; users in the plane z = 0, [B][K][2] (x, y) as above.  The channel
- * models of xlmimo_model with the 3-D distance r = sqrt(x^2 + (y_n-y)^2 + z_q^2)
- * (PNUSW keeps the projection sqrt(x / r) on the array normal; UPW is the
- * planar wave of a user at elevation 0).  rows = 1 is xlmimo_channel_gram.
- *   rows : 1..XLMIMO_MAX_URA_ROWS, n_ant * rows <= 2^40
- *   prec : xlmimo_prec, accuracy class as for the ULA
- *   gram : [B][K][K] complex doubles (device, written)
+ * the ULA; users in the plane z = 0.  The channel models of xlmimo_model with
+ * the 3-D distance r = sqrt(x^2 + (y_n-y)^2 + z_q^2) (PNUSW keeps the
+ * projection sqrt(x / r) on the array normal; UPW is the planar wave of a user
+ * at elevation 0).  rows = 1 is xlmimo_channel_gram.
+ *   rows  : 1..XLMIMO_MAX_URA_ROWS, n_ant * rows <= 2^40
+ *   users : [B][K][2] doubles (device, caller-owned), (x, y) as for the ULA
+ *   prec  : xlmimo_prec, accuracy class as for the ULA
+ *   gram  : [B][K][K] complex doubles (device, caller-owned, written),
+ *           G[b][i][j] = h_i^H h_j over all rows * n_ant elements
  * Computed per row pair: rows at +-z_q see the users alike, and row q sees
  * them as the ULA sees users moved to x' = sqrt(x^2 + z_q^2).  At
- * XLMIMO_BF16X3 with n_ant a multiple of 128 up to 1024 (PNUSW, free space) the
- * tensor-core Gram accumulates all ceil(rows/2) row pairs of a trial in one
- * pass; otherwise ceil(rows/2) ULA Grams are summed with the weights of the
- * amplitude (one for UPW) in stream-ordered device workspace (up to 1 GiB,
- * or one trial's ceil(rows/2) K x K Grams if larger).  Errors: XLMIMO_EINVAL (arguments), XLMIMO_ENOMEM,
- * XLMIMO_ECUDA. */
+ * XLMIMO_BF16X3 with n_ant a multiple of 128 up to 1024 (PNUSW, free space)
+ * the tensor-core Gram accumulates all ceil(rows/2) row pairs of a trial in
+ * one pass; otherwise ceil(rows/2) ULA Grams are summed with the weights of
+ * the amplitude (one for UPW) in stream-ordered device workspace (up to
+ * 1 GiB, or one trial's ceil(rows/2) K x K Grams if larger).  Asynchronous on
+ * `stream`.  A trial with an invalid user (x <= 0 or not finite) gets NaN.
+ * Errors: XLMIMO_EINVAL (arguments), XLMIMO_ENOMEM, XLMIMO_EUNSUPPORTED
+ * (tensor-core precisions off sm_103), XLMIMO_ECUDA. */
 #define XLMIMO_MAX_URA_ROWS 1048576
 int xlmimo_channel_gram_ura(const xlmimo_array* arr, int64_t rows, const double* users, int K, int B, int prec,
                             double* gram, void* stream);
