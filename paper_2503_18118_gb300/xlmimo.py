@@ -68,8 +68,8 @@ class Inst(ctypes.Structure):
 
 
 EXPORTS = ("xlmimo_batch_plan_create", "xlmimo_batch_run", "xlmimo_batch_plan_info", "xlmimo_batch_plan_destroy",
-           "xlmimo_mc_step", "xlmimo_channel_gram", "xlmimo_channel_gram_ura", "xlmimo_channel_gram_noalloc", "xlmimo_corr_closed_form",
-           "xlmimo_corr_closed_form_aperture", "xlmimo_beamform", "xlmimo_sumrate",
+           "xlmimo_mc_step", "xlmimo_channel_gram", "xlmimo_channel_gram_ura", "xlmimo_channel_gram_noalloc",
+           "xlmimo_corr_closed_form", "xlmimo_corr_closed_form_aperture", "xlmimo_beamform", "xlmimo_sumrate",
            "xlmimo_saturation", "xlmimo_saturation_analytic", "xlmimo_capacity_sweep", "xlmimo_capacity_bounds",
            "xlmimo_pair_features",
            "xlmimo_mlp_forward", "xlmimo_mlp_loss", "xlmimo_mlp_work_floats", "xlmimo_mlp_backward", "xlmimo_mlp_adam",

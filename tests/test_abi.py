@@ -146,3 +146,48 @@ def test_gram_ura_validates_on_host(xl):
 
 def test_shutdown_without_state_is_a_no_op(xl):
     assert xl.lib().xlmimo_shutdown() == 0
+
+
+def test_mc_step_validates_on_host(xl):
+    L = xl.lib()
+    dummy = 16
+    good = dict(arr=xl.array(1024, 0.01), prec=xl.F32, scheme=xl.MMSE, cf_scheme=xl.ZF, power_mode=xl.POWER_RXSNR,
+                K=8, B=4, chunks=0, reserved=0, t=0.9)
+    ptrs = ("users", "power", "noise", "gram", "gram_cf", "sinr", "sinr_cf", "status", "status_cf", "rate", "rate_cf",
+            "sat")
+
+    def job(**over):
+        j = xl.McBatch(**{**good, **over})
+        for n in ptrs:
+            setattr(j, n, dummy)
+        return j
+
+    assert L.xlmimo_mc_step(None, None) == 1
+    for over in (dict(K=0), dict(K=65), dict(B=-1), dict(prec=9), dict(scheme=7), dict(cf_scheme=-2),
+                 dict(power_mode=5), dict(chunks=65), dict(reserved=1), dict(t=1.0), dict(t=-0.5),
+                 dict(arr=xl.array(0, 0.01))):
+        assert L.xlmimo_mc_step(ctypes.byref(job(**over)), None) == 1, over
+    j = job()
+    j.sat = None
+    assert L.xlmimo_mc_step(ctypes.byref(j), None) == 1  # t > 0 needs the saturation output
+    j = job()
+    j.gram_cf = None
+    assert L.xlmimo_mc_step(ctypes.byref(j), None) == 1  # the closed-form path needs its buffers
+    assert L.xlmimo_mc_step(ctypes.byref(job(B=0)), None) == 0
+
+
+def test_capacity_sweep_and_batch_plan_validate_on_host(xl):
+    L = xl.lib()
+    res = xl.SweepResult()
+    assert L.xlmimo_capacity_sweep(None, ctypes.byref(res), None) == 1
+    cfg = xl.SweepCfg(wavelength=0.01, spacing=0.005, beta0=1.0, model=xl.FSPL_USW, prec=xl.F32, n_count=0,
+                      snr_count=0, K=8, B=4, t=0.9, ref_x=10.0)
+    assert L.xlmimo_capacity_sweep(ctypes.byref(cfg), ctypes.byref(res), None) == 1  # no n_list, snr_db or users
+    geo = xl.array(1024, 0.01)
+    insts = (xl.Inst * 1)(xl.Inst(1024, 8, xl.ZF, 0, 0, 1.0))
+    plan = ctypes.c_void_p()
+    assert L.xlmimo_batch_plan_create(None, insts, 1, xl.BF16X3, None, ctypes.byref(plan), None) == 1
+    assert L.xlmimo_batch_plan_create(ctypes.byref(geo), insts, 0, xl.BF16X3, None, ctypes.byref(plan), None) == 1
+    assert L.xlmimo_batch_plan_create(ctypes.byref(geo), insts, 1, xl.F32, None, ctypes.byref(plan), None) == 1
+    bad = (xl.Inst * 1)(xl.Inst(1024, 65, xl.ZF, 0, 0, 1.0))
+    assert L.xlmimo_batch_plan_create(ctypes.byref(geo), bad, 1, xl.BF16X3, None, ctypes.byref(plan), None) == 1
