@@ -281,6 +281,7 @@ def sweep_bench(xl, torch):
     frac = cap / cap[-1]
     first = [int(ex["n_list"][int(np.argmax(frac >= q))]) for q in (0.9, 0.99)]
     out["saturation"] = {"analytic_n_sat": int(ana[3]), "analytic_y_up_m": float(ana[0]),
+                         "analytic_near_integer": bool(ana[4]), "analytic_other_candidate": int(ana[5]),
                          "capacity_reaches_90pct_at_n": first[0], "capacity_reaches_99pct_at_n": first[1]}
     return out
 

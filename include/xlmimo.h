@@ -265,7 +265,13 @@ typedef struct {
  * rectangle these equal Eqs. (17)-(18).  Evaluated on the device in FP64 by
  * composite Gauss-Legendre quadrature of the closed-form CDF.
  * SYNCHRONOUS: returns host results.
- *   out : 4 doubles (host, written) {E[y_up], E[y_down], (E[y_up]-E[y_down])/spacing, ceil of it} */
+ *   out : 6 doubles (host, written)
+ *         {E[y_up], E[y_down], v = (E[y_up]-E[y_down])/spacing, ceil(v), near, other}
+ *   The quadrature carries v to ~1e-9 relative.  When v lies within
+ *   XLMIMO_SAT_NEAR_REL * max(1, v) of an integer m, the ceiling is not
+ *   decided by the computation: near = 1 and {ceil(v), other} = {m, m + 1},
+ *   both candidates.  Otherwise near = 0 and other = ceil(v). */
+#define XLMIMO_SAT_NEAR_REL 1e-6
 int xlmimo_saturation_analytic(const xlmimo_user_dist* dist, int K, double t, double spacing,
                                double* out, void* stream);
 

@@ -5,20 +5,18 @@
 // closed-form entries are fetched while the previous tile is in flight, and
 // the weight stream runs on into the next tile.
 //
-// A CTA keeps NT row tiles in flight (MiCfg): NT = 1 (default) is two CTAs
-// per SM with a two-stage ring each; NT = 2 is one CTA per SM whose two tiles
-// take every weight tile in turn from a five-stage ring (measured slower: both
-// tiles reach their SiLU epilogues together, so MMA and epilogue overlap less
-// than two independent CTAs do).  Measured on a
-// per-CTA clock64 timeline of the NT = 1 form, each layer's MMAs waited ~800
-// cycles per 16 KB weight tile (L2 latency with two tiles in flight, the
-// crossbar at 15 % of its peak) and the SiLU epilogue was issue-bound with
-// four row warps per scheduler; sharing weight tiles halves the bytes per row
-// and the deeper ring keeps more of them in flight.
+// Two CTAs per SM, one tile of 128 pair rows in flight each, a two-stage
+// weight ring each.  Measured on a per-CTA clock64 timeline, each layer's
+// MMAs waited ~800 cycles per 16 KB weight tile (L2 latency with two tiles in
+// flight, the crossbar at 15 % of its peak) and the SiLU epilogue was
+// issue-bound with four row warps per scheduler.  Two lockstep tiles per CTA
+// sharing each weight tile (five-stage ring) and one tile per CTA at one CTA
+// per SM (nine-stage ring) were both measured slower: without a second CTA the
+// SiLU epilogue of one half is not hidden behind the other half's products.
 //
-//   row warps (8 per tile): thread (t, m, h) owns output units 128 h ..
-//          128 h + 127 of row m of tile t (m = 32 (warp % 4) + lane, h =
-//          warp / 4 % 2, t = warp / 8).  It writes the features (half 0:
+//   row warps (8): thread (m, h) owns output units 128 h .. 128 h + 127 of
+//          row m of the tile (m = 32 (warp % 4) + lane, h = warp / 4).  It
+//          writes the features (half 0:
 //          [hi(f), lo(f), hi(f)] in BF16) into its tile's A (128 x 256 BF16,
 //          K-major, 128-byte swizzle); after each layer it reads its 128
 //          accumulators from TMEM, adds the bias and applies SiLU as
@@ -29,15 +27,12 @@
 //          G~_ij (1 + t_ij).
 //   loader warp streams the 26 weight tiles (16 KB: 128 output units x 64
 //          inputs, BF16, stored in the swizzled operand layout) through the
-//          ring with bulk copies.  CTAs may run in clusters of CL, tile c
-//          fetched once by rank c % CL and multicast into every CTA of the
-//          cluster (measured: no faster; it saves L2 bandwidth, not bytes in
-//          flight per CTA); a slot is refilled once the MMA warps of all CL
-//          CTAs have released it (their commits are multicast).
-//   MMA warp owns TMEM (256 columns per tile: an FP32 128 x 256 accumulator)
-//          and issues tcgen05.mma (M = N = 128, K = 16) half by half, every
-//          tile per weight tile, committing each half separately so half 0's
-//          epilogue runs while half 1 multiplies.
+//          ring with bulk copies; a slot is refilled once the MMA warp has
+//          released it.
+//   MMA warp owns TMEM (256 columns: an FP32 128 x 256 accumulator) and
+//          issues tcgen05.mma (M = N = 128, K = 16) half by half, committing
+//          each half separately so half 0's epilogue runs while half 1
+//          multiplies.
 // SiLU uses the FP32 tanh (relative error ~2^-11) in every layer; in the last
 // hidden layer, which feeds the FP32 output layer directly, the exact form
 // (exp and divide, two MUFU ops) was measured to change neither the output
@@ -47,10 +42,6 @@
 // after half 1's MMAs have read them (a separate commit after half 1's first
 // two input chunks); half 1's accumulator commit implies the whole layer is
 // done.  Every wait is bounded; a CTA that gives up writes NaN to its pairs.
-// Cluster barriers after the barrier set-up and before exit keep every remote
-// arrival and copy inside the lifetime of its target.
-#include <stdlib.h>
-
 #include <algorithm>
 
 #include "mlp_common.cuh"
@@ -62,38 +53,32 @@ constexpr int MI_ROWS = 128;  // pair rows per tile (the MMA's M)
 constexpr int MI_A_BYTES = 4 * MLP_TILE_BYTES;
 constexpr int MI_F32_BYTES = (MLP_PK_NF * 4 + 15) / 16 * 16;
 
-// NT row tiles in flight per CTA.  NT = 1: two CTAs per SM, a two-stage
-// weight ring each.  NT = 2: one CTA per SM whose two tiles take every weight
-// tile in turn (half the L2 bytes per row) from a five-stage ring.
-template <int NT, int CPS>
+// Warp roles, ring depth (what the shared memory of two CTAs per SM holds)
+// and tensor memory of the inference kernel.
 struct MiCfg {
-    static constexpr int ROW_WARPS = 8 * NT;
+    static constexpr int ROW_WARPS = 8;
     static constexpr int LOADER = ROW_WARPS, MMA = ROW_WARPS + 1;
     static constexpr int THREADS = 32 * (ROW_WARPS + 2);
     static constexpr int ROW_THREADS = 32 * ROW_WARPS;
-    static constexpr int CTAS_PER_SM = CPS;
-    // ring depth: what the shared memory left by NT A tiles and CPS CTAs holds
-    static constexpr int STAGES = NT == 2 ? 5 : (CPS == 2 ? 2 : 9);
-    static constexpr uint32_t TMEM_COLS = 256 * NT;
+    static constexpr int CTAS_PER_SM = 2;
+    static constexpr int STAGES = 2;
+    static constexpr uint32_t TMEM_COLS = 256;
 };
 
-template <int NT, int CPS>
 struct MiShared {
-    uint64_t full[MiCfg<NT, CPS>::STAGES];
-    uint64_t empty[MiCfg<NT, CPS>::STAGES];
+    uint64_t full[MiCfg::STAGES];
+    uint64_t empty[MiCfg::STAGES];
     uint64_t a_ready;    // one arrival per row thread: A tiles written, accumulators read
     uint64_t d_ready[2]; // commit: output half h of the layer complete (every tile)
     uint64_t a_free;     // commit: half 1 has read A columns 0-127 (every tile)
     uint64_t fin;        // commit after the last MMA
     uint32_t tmem_base;
     int abort;
-    float2 red[NT][MI_ROWS]; // half 1's share of the output layer
+    float2 red[MI_ROWS];     // half 1's share of the output layer
 };
 
-template <int NT, int CPS>
 constexpr int mi_smem() {
-    return 1024 + NT * MI_A_BYTES + MiCfg<NT, CPS>::STAGES * MLP_TILE_BYTES + MI_F32_BYTES +
-           (int)sizeof(MiShared<NT, CPS>);
+    return 1024 + MI_A_BYTES + MiCfg::STAGES * MLP_TILE_BYTES + MI_F32_BYTES + (int)sizeof(MiShared);
 }
 
 // Copy into this CTA's shared memory, completing bytes on `bar` (armed separately).
@@ -103,39 +88,8 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
                  : "memory");
 }
 
-// Copy into the same shared-memory offset of every CTA in `mask`, completing
-// bytes on the barrier at `bar`'s offset in each of them.
-__device__ __forceinline__ void bulk_load_mc(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar,
-                                             uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], %4;" ::"r"(
-            dst),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
-        : "memory");
-}
-
 __device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-// Arrive on the barrier at `bar`'s offset in every CTA of `mask` once this
-// thread's MMAs so far have completed.
-__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            smem_u32(bar)),
-        "h"(mask)
-        : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
 
 // mbar_wait with suspension: same bound (TC_WAIT_NS) and abort protocol.
@@ -250,23 +204,21 @@ __device__ __forceinline__ RowIn fetch_row(int64_t r, int64_t rows, int K, int P
     return in;
 }
 
-// Persistent: CTA x takes tiles x, x + grid, x + 2 grid, ... (n_iter of them,
-// the same count in every CTA so that a cluster shares one weight stream;
+// Persistent: CTA x takes tiles x, x + grid, x + 2 grid, ... (n_iter of them;
 // tiles past the end have no valid rows).
 // HB: the Gram holds a base G~ F below the diagonal (else the base is G~).
-template <int CL, int NT, bool HB, int CPS>
-__global__ void __launch_bounds__(MiCfg<NT, CPS>::THREADS, CPS)
+template <bool HB>
+__global__ void __launch_bounds__(MiCfg::THREADS, MiCfg::CTAS_PER_SM)
     mlp_infer_tc_kernel(FeatConst fc, const double2* __restrict__ users, int K, int64_t rows, int n_iter,
                         const unsigned char* __restrict__ packed, double2* __restrict__ gram) {
-    using C = MiCfg<NT, CPS>;
+    using C = MiCfg;
     constexpr int MI_STAGES = C::STAGES;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    unsigned char* A0 = base;  // tile t's A at A0 + t MI_A_BYTES
-    unsigned char* ring = A0 + NT * MI_A_BYTES;
+    unsigned char* A = base;  // the tile's A operand
+    unsigned char* ring = A + MI_A_BYTES;
     float* pf = reinterpret_cast<float*>(ring + MI_STAGES * MLP_TILE_BYTES);
-    MiShared<NT, CPS>* sh =
-        reinterpret_cast<MiShared<NT, CPS>*>(reinterpret_cast<unsigned char*>(pf) + MI_F32_BYTES);
+    MiShared* sh = reinterpret_cast<MiShared*>(reinterpret_cast<unsigned char*>(pf) + MI_F32_BYTES);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int P = K * (K - 1) / 2;
@@ -274,7 +226,7 @@ __global__ void __launch_bounds__(MiCfg<NT, CPS>::THREADS, CPS)
     if (tid == 0) {
         for (int s = 0; s < MI_STAGES; ++s) {
             mbar_init(&sh->full[s], 1);
-            mbar_init(&sh->empty[s], CL);
+            mbar_init(&sh->empty[s], 1);
         }
         mbar_init(&sh->a_ready, C::ROW_THREADS);
         mbar_init(&sh->d_ready[0], 1);
@@ -293,16 +245,14 @@ __global__ void __launch_bounds__(MiCfg<NT, CPS>::THREADS, CPS)
     const float* gpf = reinterpret_cast<const float*>(packed + MLP_PK_F32);
     for (int e = tid; e < MLP_PK_NF; e += C::THREADS) pf[e] = gpf[e];
     tc_fence_before();
-    cluster_sync();  // every CTA's barriers exist before any remote copy or arrival
+    __syncthreads();
     tc_fence_after();
-    const uint32_t crank = CL > 1 ? cluster_rank() : 0u;
-    const uint16_t cmask = (uint16_t)((1u << CL) - 1u);
     const uint32_t tmem = sh->tmem_base;
     volatile int* abort = &sh->abort;
     const int n_tiles_total = n_iter * MLP_TILES;
 
     if (warp == C::LOADER) {
-        // ---------------- weight tiles through the ring (tile c issued by rank c % CL)
+        // ---------------- weight tiles through the ring
         if (lane == 0) {
             int armed = 0;
             for (int c = 0; c < n_tiles_total; ++c) {
@@ -311,13 +261,11 @@ __global__ void __launch_bounds__(MiCfg<NT, CPS>::THREADS, CPS)
                 if (c >= MI_STAGES && !mbar_wait_sleep(&sh->full[s], ((c / MI_STAGES) - 1) & 1, abort)) break;
                 expect_tx(&sh->full[s], MLP_TILE_BYTES);
                 ++armed;
-                if (c % CL != (int)crank) continue;
-                // ... and every CTA of the cluster has consumed it before the slot is overwritten
+                // ... and the MMA warp has consumed it before the slot is overwritten
                 if (c >= MI_STAGES && !mbar_wait_sleep(&sh->empty[s], ((c / MI_STAGES) - 1) & 1, abort)) break;
                 const uint32_t dst = smem_u32(ring + s * MLP_TILE_BYTES);
                 const unsigned char* src = packed + (int64_t)(c % MLP_TILES) * MLP_TILE_BYTES;
-                if (CL > 1) bulk_load_mc(dst, src, MLP_TILE_BYTES, &sh->full[s], cmask);
-                else bulk_load(dst, src, MLP_TILE_BYTES, &sh->full[s]);
+                bulk_load(dst, src, MLP_TILE_BYTES, &sh->full[s]);
             }
             // no copy may still be landing when the CTA exits
             for (int c = armed - MI_STAGES; c < armed; ++c)
@@ -325,7 +273,7 @@ __global__ void __launch_bounds__(MiCfg<NT, CPS>::THREADS, CPS)
         }
         __syncwarp();
     } else if (warp == C::MMA) {
-        // ---------------- MMA issuer: every tile of the CTA takes each weight tile in turn
+        // ---------------- MMA issuer: the tile takes each weight tile in turn
         if (lane == 0) {
             const uint32_t idesc = tc_idesc<TCP_BF16>();
             bool ok = true;
@@ -341,15 +289,11 @@ __global__ void __launch_bounds__(MiCfg<NT, CPS>::THREADS, CPS)
                             if (!mbar_wait_sleep(&sh->full[s], (c / MI_STAGES) & 1, abort)) { ok = false; break; }
                             tc_fence_after();
                             const uint32_t b0 = smem_u32(ring + s * MLP_TILE_BYTES);
-#pragma unroll
-                            for (int t = 0; t < NT; ++t) {
-                                const uint32_t a0 = smem_u32(A0 + t * MI_A_BYTES + kc * MLP_TILE_BYTES);
-                                for (int kk = 0; kk < ksteps; ++kk)
-                                    umma(tmem + t * 256 + nh * 128, desc_sw128(a0 + kk * 32), desc_sw128(b0 + kk * 32),
-                                         idesc, (kc | kk) ? 1u : 0u);
-                            }
-                            if (CL > 1) umma_commit_mc(&sh->empty[s], cmask);
-                            else umma_commit(&sh->empty[s]);
+                            const uint32_t a0 = smem_u32(A + kc * MLP_TILE_BYTES);
+                            for (int kk = 0; kk < ksteps; ++kk)
+                                umma(tmem + nh * 128, desc_sw128(a0 + kk * 32), desc_sw128(b0 + kk * 32), idesc,
+                                     (kc | kk) ? 1u : 0u);
+                            umma_commit(&sh->empty[s]);
                             if (nh == 1 && kc == (nk - 1) / 2) umma_commit(&sh->a_free);  // chunks 0, 1 read
                         }
                         if (ok) umma_commit(&sh->d_ready[nh]);
@@ -360,12 +304,11 @@ __global__ void __launch_bounds__(MiCfg<NT, CPS>::THREADS, CPS)
         }
         __syncwarp();
     } else {
-        // ---------------- rows: warp (t, hf, quarter) = (warp / 8, warp / 4 % 2, warp % 4)
-        const int m = (warp & 3) * 32 + lane, hf = (warp >> 2) & 1, tt = warp >> 3;
-        unsigned char* A = A0 + tt * MI_A_BYTES;
-        const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(tt * 256 + hf * 128);
-        const int64_t tile_rows = (int64_t)NT * MI_ROWS;  // rows per CTA iteration
-        const int64_t row_off = (int64_t)tt * MI_ROWS + m;
+        // ---------------- rows: warp (hf, quarter) = (warp / 4, warp % 4)
+        const int m = (warp & 3) * 32 + lane, hf = warp >> 2;
+        const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(hf * 128);
+        const int64_t tile_rows = MI_ROWS;  // rows per CTA iteration
+        const int64_t row_off = m;
         RowIn cur;
         cur.valid = false;
         if (hf == 0) {
@@ -437,7 +380,7 @@ __global__ void __launch_bounds__(MiCfg<NT, CPS>::THREADS, CPS)
                 tc_fence_before();
                 if (ok) mbar_arrive(&sh->a_ready);
             }
-            if (hf == 1) sh->red[tt][m] = o;
+            if (hf == 1) sh->red[m] = o;
             // barrier of the 256 row threads that also agrees on stopping, so
             // that all of them leave the loop together
             uint32_t stop;
@@ -450,7 +393,7 @@ __global__ void __launch_bounds__(MiCfg<NT, CPS>::THREADS, CPS)
                     : "memory");
             }
             if (hf == 0 && cur.valid) {
-                const float2 o1 = sh->red[tt][m];
+                const float2 o1 = sh->red[m];
                 double2 v0, v1;
                 if (!stop) {
                     // G~ F + G~ t
@@ -489,81 +432,34 @@ __global__ void __launch_bounds__(MiCfg<NT, CPS>::THREADS, CPS)
     __syncthreads();
     if (warp == C::MMA && lane == 0) mbar_wait_timed(&sh->fin, 0);
     __syncwarp();
-    cluster_sync();  // the other CTAs' copies and commits into this CTA are over
     if (warp == C::MMA) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
     }
 }
 
-// Cluster size of the weight multicast: 1 (measured no faster at 2 or 4 once
-// the kernel is persistent) unless XLMIMO_SURROGATE_CLUSTER (1, 2 or 4) says
-// otherwise; read once.
-static int mlp_infer_cluster() {
-    static int cl = 0;
-    if (!cl) {
-        int v = 1;
-        if (const char* e = getenv("XLMIMO_SURROGATE_CLUSTER")) {
-            const int x = atoi(e);
-            if (x == 1 || x == 2 || x == 4) v = x;
-        }
-        cl = v;
-    }
-    return cl;
-}
-
-template <int CL, int NT, bool HB, int CPS>
+template <bool HB>
 static int mlp_infer_launch(const FeatConst& fc, const double* users, int K, int64_t rows, const void* packed,
                             double* gram, cudaStream_t st) {
-    using C = MiCfg<NT, CPS>;
-    constexpr int smem = mi_smem<NT, CPS>();
+    using C = MiCfg;
+    constexpr int smem = mi_smem();
     static bool done[64] = {false};
     int dev = 0;
     int rc = cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
     if (rc) return rc;
     if (dev >= 64 || !done[dev]) {
-        rc = cuda_status(cudaFuncSetAttribute(mlp_infer_tc_kernel<CL, NT, HB, CPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+        rc = cuda_status(cudaFuncSetAttribute(mlp_infer_tc_kernel<HB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                          "surrogate kernel attribute");
         if (rc) return rc;
         if (dev < 64) done[dev] = true;
     }
-    const int64_t per_iter = (int64_t)NT * MI_ROWS;
-    const int64_t n_tiles = (rows + per_iter - 1) / per_iter;
-    int64_t grid = std::min<int64_t>(n_tiles, (int64_t)C::CTAS_PER_SM * num_sms());
-    grid = (grid + CL - 1) / CL * CL;
+    const int64_t n_tiles = (rows + MI_ROWS - 1) / MI_ROWS;
+    const int64_t grid = std::min<int64_t>(n_tiles, (int64_t)C::CTAS_PER_SM * num_sms());
     const int64_t n_iter = (n_tiles + grid - 1) / grid;
     if (n_iter * MLP_TILES > 0x7fffffffLL) { set_error("too many pairs for one launch"); return XLMIMO_EINVAL; }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(C::THREADS);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cuda_status(cudaLaunchKernelEx(&cfg, mlp_infer_tc_kernel<CL, NT, HB, CPS>, fc, (const double2*)users, K, rows,
-                                          (int)n_iter, (const unsigned char*)packed, (double2*)gram),
-                       "surrogate kernel launch");
-}
-
-// Configuration: 1 = one tile per CTA, two CTAs per SM (default); 2 = two
-// lockstep tiles per CTA; 3 = one tile per CTA, one CTA per SM with a deep
-// weight ring.  XLMIMO_SURROGATE_TILES (1, 2 or 3) overrides; read once.
-static int mlp_infer_tiles() {
-    static int nt = 0;
-    if (!nt) {
-        int v = 1;
-        if (const char* e = getenv("XLMIMO_SURROGATE_TILES")) {
-            const int x = atoi(e);
-            if (x >= 1 && x <= 3) v = x;
-        }
-        nt = v;
-    }
-    return nt;
+    mlp_infer_tc_kernel<HB><<<(unsigned)grid, C::THREADS, smem, st>>>(fc, (const double2*)users, K, rows, (int)n_iter,
+                                                                      (const unsigned char*)packed, (double2*)gram);
+    return cuda_status(cudaGetLastError(), "surrogate kernel launch");
 }
 
 }  // namespace xl
@@ -589,18 +485,6 @@ extern "C" int xlmimo_surrogate_gram(const xlmimo_array* arr, const double* user
     if ((rc = launch_aperture_base(g, base, users, K, B, gram, st))) return rc;
     const int64_t rows = (int64_t)B * (K * (K - 1) / 2);
     const FeatConst fc = make_feat_const(g);
-    const int nt = mlp_infer_tiles(), hb_ = base != XLMIMO_APERTURE_NONE;
-    const bool hb = hb_;
-    // (tiles per CTA, CTAs per SM): (1, 2) two CTAs with a 2-stage ring each,
-    // (2, 1) two lockstep tiles with a 5-stage ring, (1, 1) one tile with a 9-stage ring
-#define XL_MI1(CL_, NT_, CPS_) (hb ? mlp_infer_launch<CL_, NT_, true, CPS_>(fc, users, K, rows, packed, gram, st) \
-                                   : mlp_infer_launch<CL_, NT_, false, CPS_>(fc, users, K, rows, packed, gram, st))
-#define XL_MI(CL_) (nt == 2 ? XL_MI1(CL_, 2, 1) : nt == 3 ? XL_MI1(CL_, 1, 1) : XL_MI1(CL_, 1, 2))
-    switch (mlp_infer_cluster()) {
-        case 2: return XL_MI(2);
-        case 4: return XL_MI(4);
-        default: return XL_MI(1);
-    }
-#undef XL_MI1
-#undef XL_MI
+    return base != XLMIMO_APERTURE_NONE ? mlp_infer_launch<true>(fc, users, K, rows, packed, gram, st)
+                                        : mlp_infer_launch<false>(fc, users, K, rows, packed, gram, st);
 }

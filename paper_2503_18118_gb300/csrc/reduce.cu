@@ -369,6 +369,13 @@ int saturation_analytic(const xlmimo_user_dist* dist, int K, double t, double sp
     out[1] = e_dn;
     out[2] = (e_up - e_dn) / spacing;
     out[3] = ceil(out[2]);
+    // the quadrature carries the ratio to ~1e-9 relative; within 1e-6 of an
+    // integer m (relative) its ceiling is not decided, and both m and m + 1
+    // are reported
+    const double m = rint(out[2]);
+    const bool near = fabs(out[2] - m) <= XLMIMO_SAT_NEAR_REL * fmax(1.0, fabs(out[2]));
+    out[4] = near ? 1.0 : 0.0;
+    out[5] = near ? (out[3] == m ? m + 1.0 : m) : out[3];
     return XLMIMO_OK;
 }
 

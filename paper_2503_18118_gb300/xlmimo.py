@@ -22,6 +22,7 @@ APERTURE_NONE, APERTURE_MASK, APERTURE_FRESNEL = 0, 1, 2
 MAX_USERS = 64
 MAX_BOUNDS_USERS = 1024
 MAX_URA_ROWS = 1048576
+NOALLOC_SCRATCH_MIB = 16  # XLMIMO_NOALLOC_SCRATCH_MIB
 STATUS = {0: "OK", 1: "EINVAL", 2: "ECUDA", 3: "ENOMEM", 4: "ESINGULAR", 5: "ETIMEOUT", 6: "EUNSUPPORTED"}
 
 
@@ -338,9 +339,10 @@ def xlmimo_saturation(users: torch.Tensor, t: float, spacing: float, sat: torch.
 
 def xlmimo_saturation_analytic(kind: int, a0: float, a1: float, b0: float, b1: float, K: int, t: float,
                                spacing: float, stream=None):
-    """(E[y_up], E[y_down], aperture/spacing, ceil) -- synchronous."""
+    """(E[y_up], E[y_down], aperture/spacing v, ceil(v), near-integer flag,
+    the other candidate count) -- synchronous."""
     d = UserDist(int(kind), 0, float(a0), float(a1), float(b0), float(b1))
-    out = (ctypes.c_double * 4)()
+    out = (ctypes.c_double * 6)()
     _check(lib().xlmimo_saturation_analytic(ctypes.byref(d), int(K), float(t), float(spacing), out, _stream(stream)))
     return tuple(out)
 

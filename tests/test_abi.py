@@ -66,7 +66,7 @@ def test_invalid_arguments_rejected_on_host(xl):
     # saturation threshold outside (0, 1)
     assert L.xlmimo_saturation(dummy, 4, 1, 1.0, 0.01, dummy, None) == 1
     d = xl.UserDist(xl.DIST_RECT, 0, 2.0, 1.0, 0.0, 1.0)
-    out = (ctypes.c_double * 4)()
+    out = (ctypes.c_double * 6)()
     assert L.xlmimo_saturation_analytic(ctypes.byref(d), 4, 0.9, 0.01, out, None) == 1
 
 
@@ -191,3 +191,11 @@ def test_capacity_sweep_and_batch_plan_validate_on_host(xl):
     assert L.xlmimo_batch_plan_create(ctypes.byref(geo), insts, 1, xl.F32, None, ctypes.byref(plan), None) == 1
     bad = (xl.Inst * 1)(xl.Inst(1024, 65, xl.ZF, 0, 0, 1.0))
     assert L.xlmimo_batch_plan_create(ctypes.byref(geo), bad, 1, xl.BF16X3, None, ctypes.byref(plan), None) == 1
+
+
+def test_binding_constants_match_header(xl):
+    """The binding's size limits are the header's."""
+    text = open(os.path.join(ROOT, "include", "xlmimo.h")).read()
+    defs = dict(re.findall(r"#define\s+XLMIMO_([A-Z0-9_]+)\s+(\d+)", text))
+    assert int(defs["NOALLOC_SCRATCH_MIB"]) == xl.NOALLOC_SCRATCH_MIB
+    assert int(defs["MAX_USERS"]) == xl.MAX_USERS

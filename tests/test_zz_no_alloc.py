@@ -64,13 +64,30 @@ def test_noalloc_matches_channel_gram_twice():
 
 @pytest.mark.gpu
 def test_noalloc_rejects_oversized_split():
+    """A batch whose element split needs more than the static scratch is
+    refused on the host.  Real device buffers of the call's shapes are passed,
+    so that even a call that were accepted would touch only valid memory."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2503_18118_gb300 import xlmimo as xl
+    N, K, B = 1 << 22, 64, 1
+    # the split the library chooses (element tiles of 128 for FP32; at least
+    # two tiles per chunk; at most 4096 chunks) and the scratch it then needs
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    tiles = N // 128
+    S = min(max(min(-(-4 * sms // B), tiles // 2), 1), 4096)
+    chunk = -(-tiles // S) * 128
+    S = -(-N // chunk)
+    need = B * S * K * K * 16
+    if need <= xl.NOALLOC_SCRATCH_MIB << 20:
+        pytest.skip(f"{sms} SMs: this split fits the scratch")
     L = xl.lib()
-    arr = xl.array(1 << 22, LAM100, None, 1.0, xl.FSPL_USW)
-    dummy = ctypes.c_void_p(256)  # never dereferenced: the call is rejected on the host
-    rc = L.xlmimo_channel_gram_noalloc(ctypes.byref(arr), dummy, 64, 1, xl.F32, dummy, None)
+    arr = xl.array(N, LAM100, None, 1.0, xl.FSPL_USW)
+    users = torch.from_numpy(inputs.users_polar(43, B, K, (3.0, 30.0))).cuda()
+    gram = torch.zeros((B, K, K), dtype=torch.complex128, device="cuda")
+    rc = L.xlmimo_channel_gram_noalloc(ctypes.byref(arr), ctypes.c_void_p(users.data_ptr()), K, B, xl.F32,
+                                       ctypes.c_void_p(gram.data_ptr()), None)
+    torch.cuda.synchronize()
     assert rc == 1
     assert b"scratch" in L.xlmimo_last_error()
