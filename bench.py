@@ -172,7 +172,7 @@ def reference_arm(args, wl):
 # ------------------------------------------------------------ GPU arm -------
 # sources whose bytes the committed ncu summary of each kernel was taken on
 PROFILE_SOURCES = {
-    "gram_tc_kernel": ["gram_tc.cu", "tc_common.cuh", "chan_gen.cuh", "common.cuh"],
+    "gram_tc_kernel": ["gram_tc.cu", "gram_engine.cuh", "gen_tc.cuh", "tc_common.cuh", "chan_gen.cuh", "common.cuh"],
     "gram_f32_kernel": ["gram_simt.cu", "chan_gen.cuh", "common.cuh"],
     "gram_f64_kernel": ["gram_simt.cu", "chan_gen.cuh", "common.cuh"],
     "mlp_infer_tc_kernel": ["mlp_tc.cu", "mlp_common.cuh", "tc_common.cuh", "common.cuh"],
@@ -205,7 +205,7 @@ def traffic_from_profile(kernel):
     return float(t.group(1)) if m.group(1) == source_hash(kernel) else None
 
 
-def ragged_bench(xl, torch):
+def ragged_bench(xl, torch, mufu_peak):
     """Ragged batch of 2^14 instances: N = round(2^U[10,17]), K ~ U{2..64},
     ZF or MMSE with probability 1/2, SNR ~ U[0, 30] dB, users as the headline
     geometry; autotuned plan, run captured in a CUDA graph and replayed."""
@@ -242,11 +242,31 @@ def ragged_bench(xl, torch):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
+    # the Gram launches alone (same plan, same stream), for the roofline and
+    # the split of the batch time between the Gram and the receivers
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            plan.run_gram(U, out["gram"], stream=s)
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(s)
+        for _ in range(reps):
+            plan.run_gram(U, out["gram"], stream=s)
+        g1.record(s)
+    torch.cuda.synchronize()
+    gram_ms = g0.elapsed_time(g1) / reps
     info = plan.info()
     plan.close()
+    entries = float((n * k).sum())
+    achieved = 3.0 * entries / (gram_ms / 1e3) / 1e12
     return {"workload": "2^14 instances, N=2^U[10,17], K~U{2..64}, ZF/MMSE, SNR~U[0,30] dB, 100 GHz",
-            "instances_per_s": count / (ms / 1e3), "ms_per_batch": ms, "channel_entries": int((n * k).sum()),
-            "plan": info, "plan_seconds": plan_s, "cuda_graph": True, "gram": "bf16x3"}
+            "instances_per_s": count / (ms / 1e3), "ms_per_batch": ms, "gram_ms": gram_ms,
+            "receivers_and_rates_ms": ms - gram_ms, "channel_entries": int(entries),
+            "plan": info, "plan_seconds": plan_s, "cuda_graph": True, "gram": "bf16x3",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": mufu_peak, "unit": "Tops/s (MUFU)",
+                         "frac": achieved / mufu_peak, "traffic": None, "kernel": "gram_tc_ragged_kernel",
+                         "kernel_ms": gram_ms,
+                         "algorithmic": "3 transcendental ops (rsqrt, sin, cos) x sum of N K channel entries",
+                         "peak_source": "measured sin/cos MUFU throughput (xlmimo_measure_pipe), of measured"}}
 
 
 def sweep_bench(xl, torch):
@@ -440,14 +460,18 @@ def surrogate_bench(xl, torch, peaks):
     t_fr = timed(lambda: xl.xlmimo_corr_closed_form_aperture(arr, U, xl.APERTURE_FRESNEL, G))
     t_sur = timed(lambda: xl.xlmimo_surrogate_gram(arr, U, packed, G, base=ex["base"]))
     t_exact = timed(lambda: xl.xlmimo_channel_gram(arr, U, xl.BF16X3, G), reps=3, warm=1)
-    t_mlp = t_sur - t_cf
+    # the surrogate Gram is the base closed form (with the Fresnel factor when
+    # the network corrects that base) followed by the network kernel
+    t_base = t_fr if ex["base"] == xl.APERTURE_FRESNEL else t_cf
+    t_mlp = t_sur - t_base
     rows = B * K * (K - 1) // 2
     flop_row = 2.0 * (6 * 256 + 3 * 256 * 256 + 256 * 2)
     achieved = rows * flop_row / (t_mlp / 1e3) / 1e12
     peak = float(peaks.get("bf16_tflops", 1935.2))
     del G
-    # accuracy on the first 1000 trials of the same workload
-    res = surrogate.compare(arr, U[:1000].contiguous(), packed, base=ex["base"])
+    # accuracy on the first 256 trials of the same workload, judged on the
+    # FP64 exact Gram (parity 1e-12 against the oracle)
+    res = surrogate.compare(arr, U[:256].contiguous(), packed, prec=xl.F64, base=ex["base"])
     re = res["rate_exact"]
     rows = ("cf", "mask", "fresnel", "sur")
     names = {"cf": "closed_form", "mask": "closed_form_aperture_mask", "fresnel": "closed_form_aperture_fresnel",
@@ -464,12 +488,13 @@ def surrogate_bench(xl, torch, peaks):
                     "surrogate": t_sur},
         "trials_per_s": {"exact_bf16x3": B / (t_exact / 1e3), "closed_form": B / (t_cf / 1e3),
                          "closed_form_aperture_fresnel": B / (t_fr / 1e3), "surrogate": B / (t_sur / 1e3)},
-        "sumrate_rel_err": dict(e_rate, trials=int(re.size),
+        "sumrate_rel_err": dict(e_rate, trials=int(re.size), judge="exact Gram in FP64",
                                 receiver="modified ZF at 10 dB judged on the exact channel (trial mean)"),
         "gram_rms_err": e_gram,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": traffic_from_profile("mlp_infer_tc_kernel"),
                      "kernel": "mlp_infer_tc_kernel", "kernel_ms": t_mlp,
+                     "kernel_ms_how": "surrogate Gram time minus its base closed form's time (both CUDA events)",
                      "algorithmic": "2 x (6x256 + 3x256^2 + 256x2) flop per pair x B K(K-1)/2 pairs",
                      "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured)"},
     }
@@ -563,6 +588,7 @@ def main():
         return mc.max_over_ranks(total_ms, dist if world > 1 else None, "cuda"), gram_ms, clocks
 
     total_ms, gram_ms, clocks = timed(prec, args.steps, args.warmup, sample_clocks=(rank == 0))
+    mufu_peak = xl.xlmimo_measure_pipe(xl.PIPE_SINCOS)[0] / 1e12  # Tops/s, measured on this GPU now
     ms_per_step = total_ms / args.steps
     value = mc.throughput(world, B, args.steps, total_ms)
 
@@ -604,7 +630,7 @@ def main():
     # accuracy on sampled trials against the oracle (outside the timed region)
     import oracle
     oracle.build()
-    idx = np.array([0, 1, B // 2, B - 1])
+    idx = np.unique(np.linspace(0, B - 1, 64).astype(int))  # 64 trials spread over the batch
     step(prec)
     torch.cuda.synchronize()
     r_ref, _ = oracle_pipeline(oracle, wl, users_h[idx])
@@ -624,6 +650,9 @@ def main():
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
+    pipes = {"sincos_tops": mufu_peak, "rsqrt_tops": xl.xlmimo_measure_pipe(xl.PIPE_RSQRT)[0] / 1e12,
+             "ffma_tflops": 2.0 * xl.xlmimo_measure_pipe(xl.PIPE_FFMA)[0] / 1e12,
+             "how": "xlmimo_measure_pipe: independent dependency chains on every SM, best of 3 launches, CUDA events"}
     if not args.no_extras and world == 1:
         paths = {}
         for name in ("f64", "f32", "bf16", "bf16x3", "f16x3"):
@@ -635,7 +664,7 @@ def main():
             rg = out.rate.cpu().numpy()[idx]
             paths[name] = {"trials_per_s": world * B * nsteps / (t_ms / 1e3),
                            "sumrate_rel_err": float(np.max(np.abs(rg - r_ref) / np.abs(r_ref)))}
-        ragged = ragged_bench(xl, torch)
+        ragged = ragged_bench(xl, torch, mufu_peak)
         sweep = sweep_bench(xl, torch)
         sur = surrogate_bench(xl, torch, peaks)
         app_a = appendix_a_bench(xl, torch, float(peaks.get("sm_max_mhz", 2070.0)))
@@ -649,17 +678,25 @@ def main():
     entries = float(N) * K * B  # channel entries generated per launch
     gram_flops = 8.0 * N * K * (K + 1) / 2 * B  # complex MACs of the Hermitian half, 8 flop each
     if path == "bf16x3":
-        # generation-bound: each entry needs one reciprocal square root (distance,
-        # amplitude), one reciprocal (curvature remainder), one sine and one cosine
-        achieved = 4.0 * entries / (gram_ms / 1e3) / 1e12
-        peak_v = sms * 16 * clk / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak_v, "unit": "Tops/s (MUFU)",
-                "frac": achieved / peak_v, "traffic": traffic_from_profile(KERNEL_OF_PATH[path]), "kernel": KERNEL_OF_PATH[path],
-                "kernel_ms": gram_ms,
-                "peak_source": f"MUFU: {sms} SMs x 16 ops/clk x {max_mhz:.0f} MHz (unit counts and max clock)",
-                "algorithmic": "4 transcendental ops (rsqrt, rcp, sin, cos) x N K channel entries per launch",
-                # issued MMA work: K <= 32, M = 128, N = 64 per element; K <= 64, three 128 x 128
-                "tensor_tflops": (2.0 * 128 * 64 if K <= 32 else 3 * 2.0 * 128 * 128) * N * B / (gram_ms / 1e3) / 1e12,
+        # generation-bound.  Algorithmic count per entry: one reciprocal square
+        # root (distance, amplitude) and one sine and one cosine.  The kernel
+        # itself issues the sine and cosine per entry and a reciprocal square
+        # root and a reciprocal per 8-element slice (the slice expansion).
+        achieved = 3.0 * entries / (gram_ms / 1e3) / 1e12
+        kernel_mufu = 2.0 + 2.0 / 8.0
+        smem_per_entry = 20.0 if K <= 32 else 24.0  # stage writes + MMA operand reads, bytes
+        roof = {"bound": "alu", "achieved": achieved, "peak": mufu_peak, "unit": "Tops/s (MUFU)",
+                "frac": achieved / mufu_peak, "traffic": traffic_from_profile(KERNEL_OF_PATH[path]),
+                "kernel": KERNEL_OF_PATH[path], "kernel_ms": gram_ms,
+                "peak_source": "measured: sin.approx / cos.approx chains on every SM (xlmimo_measure_pipe), of measured; "
+                               f"unit counts x max clock would be {sms * 16 * clk / 1e12:.3f}",
+                "algorithmic": "3 transcendental ops (rsqrt, sin, cos) x N K channel entries per launch",
+                "kernel_mufu_ops_per_entry": kernel_mufu,
+                "mufu_busy_frac": kernel_mufu * entries / (gram_ms / 1e3) / 1e12 / mufu_peak,
+                "smem_bytes_per_entry": smem_per_entry,
+                "smem_frac": smem_per_entry * entries / (gram_ms / 1e3) / (sms * 128.0 * clk),
+                # issued MMA work: K <= 32, M = 128, N = 64 per element; K <= 64, two 128 x 128
+                "tensor_tflops": (2.0 * 128 * 64 if K <= 32 else 2 * 2.0 * 128 * 128) * N * B / (gram_ms / 1e3) / 1e12,
                 "tensor_peak_tflops": float(peaks.get("bf16_tflops", 1935.2))}
     elif path == "f64":
         achieved = gram_flops / (gram_ms / 1e3) / 1e12
@@ -699,6 +736,7 @@ def main():
         "ura": ura,
         "speedup_vs_fp64_gpu": (value / fp64["trials_per_s"]) if fp64 else None,
         "roofline": roof,
+        "pipe_peaks": pipes,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "trials/s", "h2d_bytes_per_step": int(users_h.nbytes),
                 "d2h_bytes_per_step": int(rate_pin.numel() * 8 + 24)},

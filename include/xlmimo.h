@@ -59,19 +59,25 @@ typedef enum {
  *   sin theta_k = y_k / r_k. */
 typedef enum { XLMIMO_PNUSW = 0, XLMIMO_FSPL_USW = 1, XLMIMO_UPW = 2 } xlmimo_model;
 
-/* Arithmetic of the exact Gram accumulation.
- *   XLMIMO_F64    FP64 generation and FP64 accumulation (SIMT).
+/* Arithmetic of the exact Gram accumulation.  Accuracy is stated normwise,
+ * max_ij |dG_ij| / sqrt(G_ii G_jj) against the FP64 definition, as measured
+ * and as the tests bound it; it does not grow with N.
+ *   XLMIMO_F64    FP64 generation and FP64 accumulation (SIMT): 1e-12, or the
+ *                 FP64 rounding of the phase 2 pi r / lambda where larger.
  *   XLMIMO_F32    FP32 generation with a double-float phase reference every 128
- *                 elements, FP32 accumulation (SIMT).
- *   XLMIMO_BF16   FP32 generation (reference every 256 elements); each entry
- *                 rounded to one BF16 number; tensor cores (tcgen05) with FP32
- *                 accumulation in TMEM.  Accuracy class ~1e-2.
+ *                 elements, FP32 accumulation (SIMT): ~5e-7 (bound 1e-5).
+ *   XLMIMO_BF16   FP32 generation (reference every 256 elements, then a local
+ *                 expansion per 8 elements); each entry rounded to one BF16
+ *                 number; tensor cores (tcgen05) with FP32 accumulation in
+ *                 TMEM, added into a running total every 64 accumulations:
+ *                 ~3e-3 (bound 1e-2).
  *   XLMIMO_BF16X3 as XLMIMO_BF16 with each entry split h = hi + lo into two BF16
- *                 parts and the products hi*hi + hi*lo + lo*hi (+ lo*lo for
- *                 K <= 32) accumulated.  Accuracy class ~1e-5.
+ *                 parts and the products hi*hi + hi*lo + lo*hi accumulated:
+ *                 ~5e-6 (bound 2e-5).
  *   XLMIMO_F16X3  as XLMIMO_BF16X3 in FP16, after scaling user k's entries by
- *                 1/|h_k| at the array centre (undone in FP64).  Accuracy class
- *                 ~1e-6 (limited by the FP32 generation and accumulation).
+ *                 1/|h_k| at the array centre (undone in FP64): ~3e-6 (bound
+ *                 2e-5; limited by the FP32 generation and the tensor cores'
+ *                 FP32 accumulation, which rounds towards zero).
  * The tensor-core precisions need an sm_103 device. */
 typedef enum {
     XLMIMO_F64 = 0,
@@ -404,16 +410,18 @@ typedef struct xlmimo_batch_plan_st* xlmimo_batch_plan;
  * packed [sum K][2]) is non-NULL the plan times its candidate tilings (element
  * chunk per work item, resident CTAs per SM) on those users and keeps the
  * fastest; otherwise it takes the defaults (8192 elements, 2 CTAs per SM).
- * Element chunks are kept to a few thousand elements (candidates 4096, 8192,
- * 16384) because the tensor cores' FP32 accumulation rounds towards zero:
- * a long chunk of many small terms added to a large sum loses up to
- * ~chunk x 2^-24 of it.  SYNCHRONOUS on `stream`. */
+ * Chunk candidates 4096, 8192, 16384, 32768 and 131072 elements, each at 1
+ * and 2 CTAs per SM; the accumulator's periodic drain keeps every chunk
+ * length accurate, so the choice trades load balance against partial sums.
+ * SYNCHRONOUS on `stream`. */
 int xlmimo_batch_plan_create(const xlmimo_array* geo, const xlmimo_inst* insts, int count, int prec,
                              const double* tune_users, xlmimo_batch_plan* plan, void* stream);
 
 /* Run a plan: users [sum K][2], power [sum K] (read per power_mode) in;
  * gram (packed complex, at each gram_off), sinr [sum K], status [count],
- * rate [count] out (all device).  Asynchronous on `stream`; capturable. */
+ * rate [count] out (all device).  Asynchronous on `stream`; capturable.
+ * With sinr, status and rate all NULL (power then unused) only the Gram
+ * matrices are computed. */
 int xlmimo_batch_run(xlmimo_batch_plan plan, const double* users, const double* power, int power_mode,
                      double* gram, double* sinr, int32_t* status, double* rate, void* stream);
 
@@ -518,6 +526,19 @@ int xlmimo_mlp_pack(const float* params, void* packed, void* stream);
  * device-side wait that gives up leaves NaN in its pairs. */
 int xlmimo_surrogate_gram(const xlmimo_array* arr, const double* users, int K, int B, int base, const void* packed,
                           double* gram, void* stream);
+
+/* Measured throughput of one pipe of the device, for the roofline of the
+ * channel generator (the paper has no counterpart).  Runs independent
+ * dependency chains of one operation on every SM (8 blocks of 256 threads
+ * per SM, 8 chains per thread) and times the best of three launches with
+ * CUDA events on `stream`.  SYNCHRONOUS.  Pipes:
+ *   XLMIMO_PIPE_SINCOS  alternating sin.approx / cos.approx (MUFU)
+ *   XLMIMO_PIPE_RSQRT   rsqrt.approx (MUFU)
+ *   XLMIMO_PIPE_FFMA    scalar FP32 FMA
+ *   out : 2 doubles (host, written) {operations per second, best launch ms}
+ * The caller samples the SM clock around the call if it needs it. */
+typedef enum { XLMIMO_PIPE_SINCOS = 0, XLMIMO_PIPE_RSQRT = 1, XLMIMO_PIPE_FFMA = 2 } xlmimo_pipe;
+int xlmimo_measure_pipe(int pipe, double* out, void* stream);
 
 /* Message of the last error on this host thread ("" if none). */
 const char* xlmimo_last_error(void);

@@ -15,7 +15,6 @@ constexpr int TC_STAGES = 3;
 constexpr int TC_T = 64;              // elements per stage
 constexpr int TC_THREADS = 288;
 constexpr int TC_GEN_THREADS = 256;
-constexpr int TC_TMEM_COLS = 128;
 constexpr int TC_REF_SPAN = 256;      // elements per phase reference (4 stages)
 constexpr uint64_t TC_WAIT_NS = 4000000000ull;  // 4 s
 
@@ -146,24 +145,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int KMAX>
-struct TcShared {
-    uint64_t full[TC_STAGES];
-    uint64_t empty[TC_STAGES];
-    uint64_t done;
-    uint32_t tmem_base;
-    int abort;
-    int bad;
-    UserGeo ug[KMAX];
-    double fac[KMAX];  // per-user factor of the Gram: G_ij = fac_i fac_j (accumulated sum)
-    UserRef ref[2][KMAX];  // phase references of the current and the next span
-};
-
 // hi/lo (or hi only) 16-bit conversion of two values, packed.  TRUNC (BF16
-// hi/lo only): hi by truncation, for the K <= 32 kernels whose products keep
-// the lo*lo term, so only lo's own rounding (2^-17 relative instead of 2^-18)
-// is given up; the K <= 64 kernels drop lo*lo and need the round-to-nearest
-// hi, whose remainder is half as large.
+// hi/lo only): hi by truncation (one byte permute packs both), lo the exact
+// remainder rounded; otherwise hi is rounded to nearest, whose remainder is
+// a quarter as large in square (what a product that drops lo*lo gives up).
 template <int PREC, bool TRUNC = false>
 __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
     if (PREC == TCP_F16X3) {

@@ -19,6 +19,7 @@ ZF, MMSE, MRC, ZF_DL = 0, 1, 2, 3
 POWER_ABS, POWER_RXSNR = 0, 1
 DIST_RECT, DIST_POLAR = 0, 1
 APERTURE_NONE, APERTURE_MASK, APERTURE_FRESNEL = 0, 1, 2
+PIPE_SINCOS, PIPE_RSQRT, PIPE_FFMA = 0, 1, 2
 MAX_USERS = 64
 MAX_BOUNDS_USERS = 1024
 MAX_URA_ROWS = 1048576
@@ -74,8 +75,8 @@ EXPORTS = ("xlmimo_batch_plan_create", "xlmimo_batch_run", "xlmimo_batch_plan_in
            "xlmimo_saturation", "xlmimo_saturation_analytic", "xlmimo_capacity_sweep", "xlmimo_capacity_bounds",
            "xlmimo_pair_features",
            "xlmimo_mlp_forward", "xlmimo_mlp_loss", "xlmimo_mlp_work_floats", "xlmimo_mlp_backward", "xlmimo_mlp_adam",
-           "xlmimo_mlp_train_step", "xlmimo_mlp_pack", "xlmimo_surrogate_gram", "xlmimo_shutdown", "xlmimo_last_error",
-           "xlmimo_version")
+           "xlmimo_mlp_train_step", "xlmimo_mlp_pack", "xlmimo_surrogate_gram", "xlmimo_measure_pipe", "xlmimo_shutdown",
+           "xlmimo_last_error", "xlmimo_version")
 
 MLP_IN, MLP_WIDTH, MLP_HIDDEN, MLP_OUT = 6, 256, 4, 2
 MLP_PARAMS = 199682
@@ -123,6 +124,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.xlmimo_mlp_train_step.argtypes = [vp, vp, vp, vp, i64, dbl, vp, vp, vp, i32, vp, vp, vp, vp, vp]
     L.xlmimo_mlp_pack.argtypes = [vp, vp, vp]
     L.xlmimo_surrogate_gram.argtypes = [ctypes.POINTER(Array), vp, i32, i32, i32, vp, vp, vp]
+    L.xlmimo_measure_pipe.argtypes = [i32, ctypes.POINTER(dbl), vp]
     L.xlmimo_last_error.restype = ctypes.c_char_p
     for f in EXPORTS:
         if f not in ("xlmimo_last_error", "xlmimo_mlp_work_floats"):
@@ -337,6 +339,13 @@ def xlmimo_saturation(users: torch.Tensor, t: float, spacing: float, sat: torch.
     return sat
 
 
+def xlmimo_measure_pipe(pipe: int, stream=None):
+    """(operations per second, best launch ms) of one pipe -- synchronous."""
+    out = (ctypes.c_double * 2)()
+    _check(lib().xlmimo_measure_pipe(int(pipe), out, _stream(stream)))
+    return out[0], out[1]
+
+
 def xlmimo_saturation_analytic(kind: int, a0: float, a1: float, b0: float, b1: float, K: int, t: float,
                                spacing: float, stream=None):
     """(E[y_up], E[y_down], aperture/spacing v, ceil(v), near-integer flag,
@@ -399,6 +408,12 @@ class BatchPlan:
                                       _dev(gram, torch.complex128, "gram", (self.gram_total,)),
                                       _dev(sinr, torch.float64, "sinr", (U,)), _dev(status, torch.int32, "status", (n,)),
                                       _dev(rate, torch.float64, "rate", (n,)), _stream(stream)))
+
+    def run_gram(self, users, gram, stream=None):
+        """The plan's Gram matrices only (no receivers)."""
+        _check(lib().xlmimo_batch_run(self._h, _dev(users, torch.float64, "users", (self.users_total, 2)), None, 0,
+                                      _dev(gram, torch.complex128, "gram", (self.gram_total,)), None, None, None,
+                                      _stream(stream)))
 
     def info(self) -> dict:
         v = (ctypes.c_int64 * 8)()

@@ -68,7 +68,7 @@ def run_plan(xl, plan, users, snr):
     return {k: v.cpu().numpy() for k, v in out.items()}
 
 
-@pytest.mark.parametrize("prec,gtol", [(3, 1e-4), (4, 5e-4), (2, 1e-2)])
+@pytest.mark.parametrize("prec,gtol", [(3, 2e-5), (4, 2e-5), (2, 1e-2)])
 def test_batch_matches_oracle(xl, orc, prec, gtol):
     n, k, scheme, noise, users, snr = make_batch(11, 60)
     arr = xl.array(1, LAM)
@@ -107,7 +107,7 @@ def test_batch_split_instances(xl, orc):
         K, uo, go = int(k[i]), int(plan.user_off[i]), int(plan.gram_off[i])
         G = out["gram"][go:go + K * K].reshape(1, K, K)
         R = orc.gram(orc.FSPL, int(n[i]), LAM, LAM / 2, 1.0, users[uo:uo + K][None])
-        assert normwise(G, R) <= 1e-4, i
+        assert normwise(G, R) <= 2e-5, i
 
 
 def test_batch_graph_capture_and_autotune(xl):
@@ -120,7 +120,7 @@ def test_batch_graph_capture_and_autotune(xl):
     arr = xl.array(1, LAM)
     plan = xl.BatchPlan(arr, n, k, scheme, noise, tune_users=U)
     info = plan.info()
-    assert info["tuned"] == 1 and info["candidates"] == 6
+    assert info["tuned"] == 1 and info["candidates"] == 10  # 5 chunk lengths x 1 or 2 CTAs per SM
     assert info["chunk"] in (4096, 8192, 16384) and info["ctas_per_sm"] in (1, 2)
     P = dev(snr)
     out = dict(gram=torch.empty(plan.gram_total, dtype=torch.complex128, device="cuda"),
