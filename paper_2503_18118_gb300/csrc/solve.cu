@@ -76,13 +76,17 @@ __device__ __forceinline__ cd cmacc(cd acc, cd a, cd b) {
 // exponent, top 23 stored mantissa bits); the remaining 29 mantissa bits m
 // give lo = RN(m) 2^(e - 1075), RN(m) formed exactly from m's low 23 and high
 // 6 bits (2^23 + a is exact in FP32) by one FMA.  Values whose hi or lo would
-// leave the normal FP32 range (zero, |d| < 2^-74, |d| >= 2^128, inf, NaN)
-// take the FP64 conversion.
+// leave the normal FP32 range (|d| < 2^-74 but not zero, |d| >= 2^128, inf,
+// NaN) take the FP64 conversion; a zero (the imaginary part of every Gram
+// diagonal) is split by integer operations too, since an FP64 instruction
+// costs a full warp's issue even when one lane takes it.
 __device__ __forceinline__ void split_f64(double d, float& hi, float& lo) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(d);
     const uint32_t bh = (uint32_t)(b >> 32), bl = (uint32_t)b;
     const uint32_t e = (bh >> 20) & 0x7FFu;  // biased exponent
-    if (e - 949u <= 1150u - 949u) {
+    if (((bh & 0x7FFFFFFFu) | bl) == 0u) {
+        hi = lo = __uint_as_float(bh);  // +0 or -0
+    } else if (e - 949u <= 1150u - 949u) {
         const uint32_t sg = bh & 0x80000000u;
         hi = __uint_as_float(sg | ((e - 896u) << 23) | ((bh & 0xFFFFFu) << 3) | (bl >> 29));
         const uint32_t m = bl & 0x1FFFFFFFu;
@@ -235,6 +239,17 @@ __device__ __forceinline__ void ff2_mac(float2& s, float2& c, float2 xh, float2 
     c = __fadd2_rn(c, __fadd2_rn(__fadd2_rn(ea, eb), e));
 }
 
+// (s, c) += (s2, c2) lane-wise for double-float values (two-sum on the high
+// parts, low parts summed alongside).
+__device__ __forceinline__ void ff2_add(float2& s, float2& c, float2 s2, float2 c2) {
+    const float2 t = __fadd2_rn(s, s2);
+    const float2 bb = __fadd2_rn(t, make_float2(-s.x, -s.y));
+    const float2 ea = __fadd2_rn(s, make_float2(-(t.x - bb.x), -(t.y - bb.y)));
+    const float2 eb = __fadd2_rn(s2, make_float2(-bb.x, -bb.y));
+    s = t;
+    c = __fadd2_rn(__fadd2_rn(c, c2), __fadd2_rn(ea, eb));
+}
+
 // acc += a b (conj_a: conj(a) b), complex double-float: the real lanes carry
 // (re a re b, re a im b) and the imaginary ones (-+ im a im b, +- im a re b).
 __device__ __forceinline__ void cf_mac(float2& s, float2& c, const cf& a, const cf& b, bool conj_a) {
@@ -285,8 +300,15 @@ __device__ void gram_of_lower_ff(const cd* X, int xs, cd* M, int K) {
         int r = 0, rl = K, w = q;
         while (w >= rl) { w -= rl; ++r; --rl; }
         const int c = r + w;  // r <= c
-        float2 s = make_float2(0.f, 0.f), cc = make_float2(0.f, 0.f);
-        for (int l = c; l < K; ++l) cf_mac(s, cc, F[l * xs + r], F[l * xs + c], true);
+        // two independent double-float chains (even and odd l) for latency, added at the end
+        float2 s = make_float2(0.f, 0.f), cc = make_float2(0.f, 0.f), s1 = s, c1 = s;
+        int l = c;
+        for (; l + 1 < K; l += 2) {
+            cf_mac(s, cc, F[l * xs + r], F[l * xs + c], true);
+            cf_mac(s1, c1, F[(l + 1) * xs + r], F[(l + 1) * xs + c], true);
+        }
+        if (l < K) cf_mac(s, cc, F[l * xs + r], F[l * xs + c], true);
+        ff2_add(s, cc, s1, c1);
         const float2 t = __fadd2_rn(s, cc);
         const float2 lo = __fadd2_rn(__fadd2_rn(s, make_float2(-t.x, -t.y)), cc);
         FM[r * K + c] = {t, lo};
@@ -445,23 +467,19 @@ __device__ double trial_scale(const double2* __restrict__ gf, const double2* __r
     return __hiloint2double((sh + 1023) << 20, 0);
 }
 
-// (s, c) += (s2, c2) lane-wise for double-float values (two-sum on the high
-// parts, low parts summed alongside).
-__device__ __forceinline__ void ff2_add(float2& s, float2& c, float2 s2, float2 c2) {
-    const float2 t = __fadd2_rn(s, s2);
-    const float2 bb = __fadd2_rn(t, make_float2(-s.x, -s.y));
-    const float2 ea = __fadd2_rn(s, make_float2(-(t.x - bb.x), -(t.y - bb.y)));
-    const float2 eb = __fadd2_rn(s2, make_float2(-bb.x, -bb.y));
-    s = t;
-    c = __fadd2_rn(__fadd2_rn(c, c2), __fadd2_rn(ea, eb));
+// Sum of the two lanes of a double-float pair as an unevaluated float pair
+// (t, e): the value is (double)t + (double)e; FP32 operations only.
+__device__ __forceinline__ float2 ff2_fold(float2 s, float2 c) {
+    const float t = __fadd_rn(s.x, s.y);
+    const float bb = __fsub_rn(t, s.x);
+    const float err = __fadd_rn(__fsub_rn(s.x, __fsub_rn(t, bb)), __fsub_rn(s.y, bb));
+    return make_float2(t, __fadd_rn(__fadd_rn(c.x, c.y), err));
 }
 
 // Sum of the two lanes of a double-float pair, as FP64.
 __device__ __forceinline__ double ff2_total(float2 s, float2 c) {
-    const float t = __fadd_rn(s.x, s.y);
-    const float bb = __fsub_rn(t, s.x);
-    const float err = __fadd_rn(__fsub_rn(s.x, __fsub_rn(t, bb)), __fsub_rn(s.y, bb));
-    return (double)t + (double)__fadd_rn(__fadd_rn(c.x, c.y), err);
+    const float2 f = ff2_fold(s, c);
+    return (double)f.x + (double)f.y;
 }
 
 // Mismatched-receiver SINR (Sec. V-B) from M and G in double-float:
@@ -470,11 +488,15 @@ __device__ __forceinline__ double ff2_total(float2 s, float2 c) {
 // A is never stored: warp w takes users k = w, w + nwarps, ...; lane l forms
 // A_kj for j = l (and l + 32 when K > 32) as a dot product of row k of M
 // (broadcast) with column j of G (contiguous across lanes), and adds its terms
-// to three double-float sums that the warp then reduces by shuffles and
-// converts to FP64 once, so the K^3 products cost no FP64 instruction.
+// to three double-float sums that the warp then reduces by shuffles, so the
+// K^3 products cost no FP64 instruction.  The warps leave each user's three
+// sums in shared memory; the conversions to FP64 and the divisions then run
+// for all users at once, one lane per user (FP64 instructions cost a full
+// warp's issue whatever the number of active lanes).
 __device__ void mismatched_sinr(const cf* FM, const cf* FG, const double* p, double s2, int K, double* sinr_t,
                                 double* dlbuf) {
     __shared__ float2 pf[XLMIMO_MAX_USERS];
+    __shared__ float2 rec[XLMIMO_MAX_USERS][3];  // per user: S, I, N, each as a float pair (t, e), t + e
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     for (int k = tid; k < K; k += blockDim.x) {
         float h, l;
@@ -485,15 +507,25 @@ __device__ void mismatched_sinr(const cf* FM, const cf* FG, const double* p, dou
     const bool dl = dlbuf != nullptr;
     const float2 z = make_float2(0.f, 0.f);
     // downlink: lane l's column sums sum_{k != j} |A_kj|^2 (j = l, l + 32) over
-    // this warp's rows, and the warp's share of tr(M G M^H) = sum_k N_k
+    // this warp's rows
     float2 cs[2] = {z, z}, cc[2] = {z, z};
-    float2 ts = z, tc = z;
     for (int k = warp; k < K; k += nw) {
         const cf* Mk = FM + k * K;
         float2 ss = z, sc = z, is = z, ic = z, ns = z, nc = z;
         for (int j = lane; j < K; j += 32) {
-            float2 as = z, ac = z;
-            for (int l = 0; l < K; ++l) cf_mac(as, ac, Mk[l], FG[l * K + j], false);
+            // four independent double-float chains over l (latency), added at the end
+            float2 as = z, ac = z, as1 = z, ac1 = z, as2 = z, ac2 = z, as3 = z, ac3 = z;
+            int l = 0;
+            for (; l + 3 < K; l += 4) {
+                cf_mac(as, ac, Mk[l], FG[l * K + j], false);
+                cf_mac(as1, ac1, Mk[l + 1], FG[(l + 1) * K + j], false);
+                cf_mac(as2, ac2, Mk[l + 2], FG[(l + 2) * K + j], false);
+                cf_mac(as3, ac3, Mk[l + 3], FG[(l + 3) * K + j], false);
+            }
+            for (; l < K; ++l) cf_mac(as, ac, Mk[l], FG[l * K + j], false);
+            ff2_add(as, ac, as1, ac1);
+            ff2_add(as2, ac2, as3, ac3);
+            ff2_add(as, ac, as2, ac2);
             const float2 ah = __fadd2_rn(as, ac);  // A_kj normalized
             const float2 al = __fadd2_rn(__fadd2_rn(as, make_float2(-ah.x, -ah.y)), ac);
             const cf m = Mk[j];
@@ -520,30 +552,39 @@ __device__ void mismatched_sinr(const cf* FM, const cf* FG, const double* p, dou
             ff2_add(ns, nc, o[4], o[5]);
         }
         if (lane == 0) {
-            const double S = ff2_total(ss, sc), I = ff2_total(is, ic), N = ff2_total(ns, nc);
-            if (dl) {
-                dlbuf[k] = S;  // |A_kk|^2
-                ff2_add(ts, tc, ns, nc);
-            } else {
-                sinr_t[k] = p[k] * S / fma(s2, N, I);
-            }
+            rec[k][0] = ff2_fold(ss, sc);
+            rec[k][1] = ff2_fold(is, ic);
+            rec[k][2] = ff2_fold(ns, nc);
         }
     }
-    if (!dl) return;
-    // per-warp partials, then fixed-order sums: dlbuf[0..63] |A_kk|^2,
-    // [64 + 64 w + j] warp w's column sums, [64 + 64 nw + w] warp w's trace share
-    double* colp = dlbuf + XLMIMO_MAX_USERS;
-    double* trp = colp + XLMIMO_MAX_USERS * nw;
-    for (int h = 0; h < 2; ++h) {
-        const int j = lane + 32 * h;
-        if (j < K) colp[warp * XLMIMO_MAX_USERS + j] = ff2_total(cs[h], cc[h]);
+    if (dl) {
+        // per-warp column sums: dlbuf[64 + 64 w + j]
+        double* colp = dlbuf + XLMIMO_MAX_USERS;
+        for (int h = 0; h < 2; ++h) {
+            const int j = lane + 32 * h;
+            if (j < K) colp[warp * XLMIMO_MAX_USERS + j] = ff2_total(cs[h], cc[h]);
+        }
     }
-    if (lane == 0) trp[warp] = ff2_total(ts, tc);
+    __syncthreads();
+    if (!dl) {
+        for (int k = tid; k < K; k += blockDim.x) {
+            const double S = (double)rec[k][0].x + (double)rec[k][0].y, I = (double)rec[k][1].x + (double)rec[k][1].y;
+            const double N = (double)rec[k][2].x + (double)rec[k][2].y;
+            sinr_t[k] = p[k] * S / fma(s2, N, I);
+        }
+        return;
+    }
+    // downlink: beta^2 = P_T / tr(M G M^H), tr = sum_k N_k; |A_kk|^2 = S_k;
+    // column sums in fixed warp order
+    double* colp = dlbuf + XLMIMO_MAX_USERS;
+    for (int k = tid; k < K; k += blockDim.x) dlbuf[k] = (double)rec[k][0].x + (double)rec[k][0].y;
     __syncthreads();
     double pt = 0.0, tr = 0.0;
-    for (int k = 0; k < K; ++k) pt += p[k];
-    for (int w = 0; w < nw; ++w) tr += trp[w];
-    const double b2 = pt / tr;  // beta^2 = P_T / tr(M G M^H)
+    for (int k = 0; k < K; ++k) {
+        pt += p[k];
+        tr += (double)rec[k][2].x + (double)rec[k][2].y;
+    }
+    const double b2 = pt / tr;
     for (int k = tid; k < K; k += blockDim.x) {
         double col = 0.0;
         for (int w = 0; w < nw; ++w) col += colp[w * XLMIMO_MAX_USERS + k];
