@@ -176,10 +176,13 @@ PROFILE_SOURCES = {
     "gram_f32_kernel": ["gram_simt.cu", "chan_gen.cuh", "common.cuh"],
     "gram_f64_kernel": ["gram_simt.cu", "chan_gen.cuh", "common.cuh"],
     "mlp_infer_tc_kernel": ["mlp_tc.cu", "mlp_common.cuh", "tc_common.cuh", "common.cuh"],
+    "gram_tc_ragged_kernel": ["batched.cu", "gram_engine.cuh", "gen_tc.cuh", "tc_common.cuh", "chan_gen.cuh",
+                              "common.cuh"],
 }
 PROFILE_OF_KERNEL = {"gram_tc_kernel": "gram_tc_kernel_headline.md", "gram_f32_kernel": "gram_f32_kernel_headline.md",
                      "gram_f64_kernel": "gram_f64_kernel_headline.md",
-                     "mlp_infer_tc_kernel": "mlp_infer_tc_kernel_surrogate.md"}
+                     "mlp_infer_tc_kernel": "mlp_infer_tc_kernel_surrogate.md",
+                     "gram_tc_ragged_kernel": "gram_tc_ragged_kernel_2048_instances.md"}
 
 
 def source_hash(kernel):
@@ -191,18 +194,23 @@ def source_hash(kernel):
     return h
 
 
-def traffic_from_profile(kernel):
+def traffic_from_profile(kernel, units=None):
     """DRAM bytes per full launch recorded by the committed ncu summary of the
-    kernel, valid only while the kernel's sources are unchanged."""
+    kernel, valid only while the kernel's sources are unchanged.  A summary
+    taken on a smaller case records its bytes per unit (dram_bytes_per_unit);
+    the full launch's is that times `units`."""
     prof = os.path.join(ROOT, "profiles", PROFILE_OF_KERNEL[kernel])
     if not os.path.exists(prof):
         return None
     text = open(prof).read()
     m = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
-    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m or not t:
+    if not m or m.group(1) != source_hash(kernel):
         return None
-    return float(t.group(1)) if m.group(1) == source_hash(kernel) else None
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if t:
+        return float(t.group(1))
+    u = re.search(r"dram_bytes_per_unit:\s*([0-9.eE+]+)", text)
+    return float(u.group(1)) * units if (u and units) else None
 
 
 def ragged_bench(xl, torch, mufu_peak):
@@ -263,7 +271,8 @@ def ragged_bench(xl, torch, mufu_peak):
             "receivers_and_rates_ms": ms - gram_ms, "channel_entries": int(entries),
             "plan": info, "plan_seconds": plan_s, "cuda_graph": True, "gram": "bf16x3",
             "roofline": {"bound": "alu", "achieved": achieved, "peak": mufu_peak, "unit": "Tops/s (MUFU)",
-                         "frac": achieved / mufu_peak, "traffic": None, "kernel": "gram_tc_ragged_kernel",
+                         "frac": achieved / mufu_peak, "kernel": "gram_tc_ragged_kernel",
+                         "traffic": traffic_from_profile("gram_tc_ragged_kernel", entries),
                          "kernel_ms": gram_ms,
                          "algorithmic": "3 transcendental ops (rsqrt, sin, cos) x sum of N K channel entries",
                          "peak_source": "measured sin/cos MUFU throughput (xlmimo_measure_pipe), of measured"}}

@@ -410,9 +410,11 @@ typedef struct xlmimo_batch_plan_st* xlmimo_batch_plan;
  * packed [sum K][2]) is non-NULL the plan times its candidate tilings (element
  * chunk per work item, resident CTAs per SM) on those users and keeps the
  * fastest; otherwise it takes the defaults (8192 elements, 2 CTAs per SM).
- * Chunk candidates 4096, 8192, 16384, 32768 and 131072 elements, each at 1
- * and 2 CTAs per SM; the accumulator's periodic drain keeps every chunk
- * length accurate, so the choice trades load balance against partial sums.
+ * Chunk candidates 4096, 8192, 16384, 32768 and 131072 elements, each in
+ * both modes (xlmimo_batch_plan_info); the accumulator's periodic drain keeps
+ * every chunk length accurate, so the choice trades load balance against
+ * partial sums.  Work items run one per CTA, K <= 32 instances in the Gram
+ * kernel's narrow layout (three CTAs per SM), the others in the wide one.
  * SYNCHRONOUS on `stream`. */
 int xlmimo_batch_plan_create(const xlmimo_array* geo, const xlmimo_inst* insts, int count, int prec,
                              const double* tune_users, xlmimo_batch_plan* plan, void* stream);
@@ -425,9 +427,10 @@ int xlmimo_batch_plan_create(const xlmimo_array* geo, const xlmimo_inst* insts, 
 int xlmimo_batch_run(xlmimo_batch_plan plan, const double* users, const double* power, int power_mode,
                      double* gram, double* sinr, int32_t* status, double* rate, void* stream);
 
-/* Plan facts (host, written): {work items, element chunk per item, resident
- * CTAs per SM, instances with K <= 32, instances with K > 32, workspace bytes,
- * tuned (0/1), candidates timed}. */
+/* Plan facts (host, written): {work items, element chunk per item, mode
+ * (1: the K <= 32 and K > 32 items launched one after the other, 2: both
+ * launches at once on two streams), instances with K <= 32, instances with
+ * K > 32, workspace bytes, tuned (0/1), candidates timed}. */
 int xlmimo_batch_plan_info(xlmimo_batch_plan plan, int64_t* info8);
 
 int xlmimo_batch_plan_destroy(xlmimo_batch_plan plan);

@@ -1,14 +1,15 @@
-// Ragged batches: many instances with their own N, K, receiver and noise in
-// one persistent tensor-core launch plus ragged receiver / rate launches.
+// Ragged batches: many instances with their own N, K, receiver and noise
+// in a few launches: per-user set-up, the tensor-core Gram of every work
+// item, the partial-sum reduction of split instances, and the ragged
+// receiver / rate launches.
 //
-// Work items are (instance, element chunk) pairs ordered longest first.
-// gram_tc_ragged_kernel runs a fixed number of CTAs per SM; each pulls the
-// next item from an atomic counter and runs the pipeline of gram_engine.cuh
-// on it, in the narrow layout (K <= 32) or the wide one (K <= 64), keeping
-// its tensor memory, its ring and its barrier phases across items.  Items
-// that cover a whole instance write its Gram directly; the chunks of a split
-// instance write partial Gram matrices that ragged_reduce_kernel sums in
-// chunk order.  The receivers run one CTA per instance, launched per user
+// Work items are (instance, element chunk) pairs.  Items of instances with
+// K > 32 run the wide layout of gram_engine.cuh (two CTAs per SM), the others
+// the narrow one (three CTAs per SM), one CTA per item, each list ordered
+// longest first so that the block scheduler hands out the long items first.
+// Items that cover a whole instance write its Gram directly; the chunks of a
+// split instance write partial Gram matrices that ragged_reduce_kernel sums
+// in chunk order.  The receivers run one CTA per instance, launched per user
 // count bucket so that shared memory is sized for the bucket.
 #include <math.h>
 #include <string.h>
@@ -25,123 +26,104 @@ struct DevItem {
     long long n0, n1;
 };
 
-constexpr int RG_NRING = 3;
-using RgShared = EngShared<64, RG_NRING>;
-
-// The current work item as thread 0 claimed it, kept in shared memory so
-// that no per-item value occupies registers across the generator loop.
-struct RgCur {
-    long long n0, n1, n_ant;
-    const double* users;  // the instance's users [K][2]
-    double2* out;         // its Gram, or this chunk's partial Gram
-    int k;
-    int valid;
+// Per-user set-up of a whole ragged batch, once per run (one warp per
+// instance), which the Gram CTAs of the instance's items then load.
+// iflags[i]: bit 0 an invalid user, bit 1 a user too close for the slice
+// expansion.
+struct RgUser {
+    UserGeo ug;
+    double fac;
 };
 
-// Work items of one layout pulled from `counter` until the list is exhausted
-// (E: the layout's engine).  gs / gd / done_count: the CTA's stage, drain and
-// item counters, carried across items and lists.  Returns true if a wait
-// gave up (the CTA then stops pulling work).
-template <class E, class SH>
-__device__ __forceinline__ bool ragged_items(SH* sh, RgCur* cur, unsigned char* base, uint32_t tmem, const Geom& g,
-                                             const GenParams& gp, const DevInst* __restrict__ insts,
-                                             const DevItem* __restrict__ items, int n_items, int* counter,
-                                             const double* __restrict__ users, double2* __restrict__ gram,
-                                             double2* __restrict__ part, int& gs, int& gd, int& gsp, int& done_count) {
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    volatile int* abort = &sh->abort;
-    for (;;) {
-        if (tid == 0) {
-            const int w = atomicAdd(counter, 1);
-            cur->valid = w < n_items;
-            if (w < n_items) {
-                const DevItem itm = items[w];
-                const DevInst in = insts[itm.inst];
-                cur->n0 = itm.n0;
-                cur->n1 = itm.n1;
-                cur->n_ant = in.n_ant;
-                cur->users = users + in.user_off * 2;
-                cur->out = in.nchunks == 1 ? gram + in.gram_off : part + in.part_off + (long long)itm.chunk * in.k * in.k;
-                cur->k = in.k;
-            }
-            sh->bad = 0;
-            sh->near = 0;
-        }
-        tc_fence_before();
-        __syncthreads();  // previous item's epilogue finished with TMEM and the stage buffers
-        tc_fence_after();
-        if (!cur->valid) return false;
-        Geom gi = g;
-        gi.N = cur->n_ant;
-        GenParams gpi = gp;
-        gpi.nm1 = cur->n_ant - 1;
-        if (tid < E::KM) E::setup_user(sh, gi, gpi, cur->users, cur->k, tid);
-        __syncthreads();
-        const int nst = E::stages(cur->n0, cur->n1);
-        if (warp < 8) {
-            E::generate(sh, smem_u32(base), tmem, gi, gpi, cur->n0, cur->n1, UraRows{0, 0.0, 0.0, 0}, gs, gd, gsp,
-                        !sh->near, warp, lane);
-        } else {
-            if (lane == 0) E::mma(sh, smem_u32(base), tmem, nst, gs, gd);
-            __syncwarp();
-        }
-        gs += nst;
-        gd += E::drains(nst);
-        gsp += E::spans(nst);
-        bool ok = mbar_wait(&sh->done, (uint32_t)(done_count & 1), abort);
-        ++done_count;
-        tc_fence_before();
-        __syncthreads();  // every MMA done and every drain's tcgen05.st complete
-        tc_fence_after();
-        ok = ok && !*abort && !sh->bad;
-        E::epilogue(sh, reinterpret_cast<float*>(base), tmem, cur->k, E::drains(nst), ok, cur->out, tid, warp, lane);
-        __syncthreads();
-        const int gave_up = *abort;  // read by every thread between two barriers
-        __syncthreads();
-        if (gave_up) return true;  // outstanding MMAs drained at "done"
+template <int MODEL, int PREC>
+__global__ void ragged_user_kernel(Geom g, GenParams gp, const DevInst* __restrict__ insts, int count,
+                                   const double* __restrict__ users, RgUser* __restrict__ out, int* __restrict__ iflags) {
+    const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (warp >= count) return;
+    const DevInst in = insts[warp];
+    int flags = 0;
+    for (int k = lane; k < in.k; k += 32) {
+        const double x = users[(in.user_off + k) * 2], y = users[(in.user_off + k) * 2 + 1];
+        const UserSetup u = user_setup<MODEL, PREC, false>(g, gp, x, y, true);
+        out[in.user_off + k] = RgUser{u.ug, u.fac};
+        flags |= (u.bad ? 1 : 0) | (u.near ? 2 : 0);
     }
+    flags = __reduce_or_sync(0xffffffffu, flags);
+    if (lane == 0) iflags[warp] = flags;
 }
 
-// Every CTA takes wide items (K > 32, counter[0]) until they are exhausted,
-// then narrow ones (counter[1]); both lists are ordered longest first.
-template <int MODEL, int PREC>
-__global__ void __launch_bounds__(TC_THREADS, 2)
-    gram_tc_ragged_kernel(Geom g, GenParams gp, const DevInst* __restrict__ insts, const DevItem* __restrict__ items,
-                          int n_wide, int n_narrow, int* __restrict__ counter, const double* __restrict__ users,
-                          double2* __restrict__ gram, double2* __restrict__ part) {
-    using EN = GramEngine<MODEL, 32, PREC, false, RG_NRING>;  // narrow, K <= 32
-    using EW = GramEngine<MODEL, 64, PREC, false, RG_NRING>;  // wide, K <= 64
-    static_assert(EN::BYTES == EW::BYTES, "both layouts share the ring");
+// One work item per CTA (items of one layout, longest first: the block
+// scheduler hands them out in that order as SMs free up), running the
+// pipeline of gram_engine.cuh on the item's element range; users come from
+// the per-run set-up.
+template <int MODEL, int KMAX, int PREC>
+__global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
+    gram_tc_items_kernel(Geom g, GenParams gp, const DevInst* __restrict__ insts, const DevItem* __restrict__ items,
+                         const RgUser* __restrict__ users, const int* __restrict__ iflags, double2* __restrict__ gram,
+                         double2* __restrict__ part) {
+    constexpr int NRING = KMAX == 32 ? 2 : 3;
+    using E = GramEngine<MODEL, KMAX, PREC, false, NRING>;
+    using SH = EngShared<KMAX, NRING>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    RgShared* sh = reinterpret_cast<RgShared*>(base + RG_NRING * EW::BYTES);
-    RgCur* cur = reinterpret_cast<RgCur*>(reinterpret_cast<unsigned char*>(sh) + sizeof(RgShared));
+    SH* sh = reinterpret_cast<SH*>(base + NRING * E::BYTES);
+    float* fold = reinterpret_cast<float*>(base);
 
-    const int tid = threadIdx.x, warp = tid >> 5;
-    if (tid == 0) eng_init_barriers(sh);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const DevItem itm = items[blockIdx.x];
+    const DevInst in = insts[itm.inst];
+    const int K = in.k;
+    if (tid == 0) {
+        eng_init_barriers(sh);
+        const int f = iflags[itm.inst];
+        sh->bad = f & 1;
+        sh->near = (f >> 1) & 1;
+    }
     __syncthreads();
     if (warp == 8) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
-                     "r"(2 * EW::WCOLS)
+                     "r"(2 * E::WCOLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    Geom gi = g;
+    gi.N = in.n_ant;
+    GenParams gpi = gp;
+    gpi.nm1 = in.n_ant - 1;
+    if (tid < KMAX) {
+        if (tid < K) {
+            const RgUser u = users[in.user_off + tid];
+            sh->ug[tid] = u.ug;
+            sh->fac[tid] = u.fac;
+        } else {
+            UserGeo pad = make_user_geo(g, 1.0, 0.0);  // padding user (1, 0), weight 0
+            pad.ampc = 0.f;
+            sh->ug[tid] = pad;
+            sh->fac[tid] = 1.0;
+        }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = sh->tmem_base;
-    int gs = 0;          // stages issued by this CTA so far (ring slots and phases run on across items)
-    int gd = 0;          // drains so far
-    int gsp = 0;         // reference spans so far
-    int done_count = 0;  // items completed by this CTA
-    if (!ragged_items<EW>(sh, cur, base, tmem, g, gp, insts, items, n_wide, counter, users, gram, part, gs, gd, gsp,
-                          done_count))
-        ragged_items<EN>(sh, cur, base, tmem, g, gp, insts, items + n_wide, n_narrow, counter + 1, users, gram, part, gs,
-                         gd, gsp, done_count);
+    const int nst = E::stages(itm.n0, itm.n1);
+    if (warp < 8) {
+        E::generate(sh, smem_u32(base), tmem, gi, gpi, itm.n0, itm.n1, UraRows{0, 0.0, 0.0, 0}, 0, 0, 0, !sh->near);
+    } else {
+        if (lane == 0) E::mma(sh, smem_u32(base), tmem, nst, 0, 0);
+        __syncwarp();
+    }
+    bool ok = mbar_wait(&sh->done, 0, &sh->abort);
+    tc_fence_before();
+    __syncthreads();  // every MMA done and every drain's tcgen05.st complete
+    tc_fence_after();
+    ok = ok && !*(volatile int*)&sh->abort && !sh->bad;
+    double2* o = in.nchunks == 1 ? gram + in.gram_off : part + in.part_off + (long long)itm.chunk * K * K;
+    E::epilogue(sh, fold, tmem, K, E::drains(nst), ok, o, tid, warp, lane);
     __syncthreads();
     if (warp == 8) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * EW::WCOLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * E::WCOLS) : "memory");
     }
 }
 
@@ -181,12 +163,15 @@ struct BatchPlan {
     std::vector<xlmimo_inst> host;
     DevInst* d_inst = nullptr;
     DevItem* d_items = nullptr;
-    int* d_counter = nullptr;
     int* d_lists = nullptr;  // [small bucket | large bucket | split instances]
     double2* d_part = nullptr;
+    RgUser* d_users = nullptr;  // per-user set-up, rewritten by every run
+    int* d_iflags = nullptr;    // per-instance flags, rewritten by every run
     int n_items = 0, n_wide = 0, n_small = 0, n_large = 0, n_split = 0;
     int64_t chunk = 0;
-    int ctas_per_sm = 2;
+    int mode = 2;  // 1: the two layouts one after the other; 2: concurrently on two streams
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     size_t part_bytes = 0;
     int tuned = 0, candidates = 0;
     size_t smem = 0;
@@ -194,17 +179,27 @@ struct BatchPlan {
 
 
 
+static void release_streams(BatchPlan* p) {
+    if (p->side) cudaStreamDestroy(p->side);
+    if (p->fork) cudaEventDestroy(p->fork);
+    if (p->join) cudaEventDestroy(p->join);
+    p->side = nullptr;
+    p->fork = p->join = nullptr;
+}
+
 static void free_tables(BatchPlan* p) {
     cudaFree(p->d_inst);
     cudaFree(p->d_items);
-    cudaFree(p->d_counter);
     cudaFree(p->d_lists);
     cudaFree(p->d_part);
+    cudaFree(p->d_users);
+    cudaFree(p->d_iflags);
     p->d_inst = nullptr;
     p->d_items = nullptr;
-    p->d_counter = nullptr;
     p->d_lists = nullptr;
     p->d_part = nullptr;
+    p->d_users = nullptr;
+    p->d_iflags = nullptr;
 }
 
 // Host tables for one element chunk: items longest first, split instances'
@@ -262,7 +257,9 @@ static int build_tables(BatchPlan* p, int64_t chunk, cudaStream_t st) {
     lists.insert(lists.end(), split.begin(), split.end());
     int rc = cuda_status(cudaMalloc((void**)&p->d_inst, sizeof(DevInst) * di.size()), "plan tables");
     if (!rc) rc = cuda_status(cudaMalloc((void**)&p->d_items, sizeof(DevItem) * items.size()), "plan tables");
-    if (!rc) rc = cuda_status(cudaMalloc((void**)&p->d_counter, 2 * sizeof(int)), "plan tables");
+    if (!rc) rc = cuda_status(cudaMalloc((void**)&p->d_users, sizeof(RgUser) * std::max<int64_t>(1, p->users_total)),
+                              "plan tables");
+    if (!rc) rc = cuda_status(cudaMalloc((void**)&p->d_iflags, sizeof(int) * p->count), "plan tables");
     if (!rc) rc = cuda_status(cudaMalloc((void**)&p->d_lists, sizeof(int) * std::max<size_t>(1, lists.size())), "plan tables");
     if (!rc && part > 0) rc = cuda_status(cudaMalloc((void**)&p->d_part, p->part_bytes), "plan workspace");
     if (!rc) rc = cuda_status(cudaMemcpyAsync(p->d_inst, di.data(), sizeof(DevInst) * di.size(), cudaMemcpyHostToDevice, st), "plan upload");
@@ -273,48 +270,87 @@ static int build_tables(BatchPlan* p, int64_t chunk, cudaStream_t st) {
     return rc;
 }
 
-using RgKernel = void (*)(Geom, GenParams, const DevInst*, const DevItem*, int, int, int*, const double*, double2*,
+using RgKernel = void (*)(Geom, GenParams, const DevInst*, const DevItem*, const RgUser*, const int*, double2*,
                           double2*);
+using RuKernel = void (*)(Geom, GenParams, const DevInst*, int, const double*, RgUser*, int*);
 
 template <int MODEL>
+static RuKernel ru_pick_prec(int prec) {
+    return prec == XLMIMO_F16X3 ? ragged_user_kernel<MODEL, TCP_F16X3> : ragged_user_kernel<MODEL, TCP_BF16X3>;
+}
+
+static RuKernel ru_pick(int model, int prec) {
+    return model == XLMIMO_PNUSW ? ru_pick_prec<XLMIMO_PNUSW>(prec)
+         : model == XLMIMO_UPW   ? ru_pick_prec<XLMIMO_UPW>(prec)
+                                 : ru_pick_prec<XLMIMO_FSPL_USW>(prec);
+}
+
+template <int MODEL, int KMAX>
 static RgKernel rg_pick_prec(int prec) {
-    return prec == XLMIMO_BF16 ? gram_tc_ragged_kernel<MODEL, TCP_BF16>
-         : prec == XLMIMO_F16X3 ? gram_tc_ragged_kernel<MODEL, TCP_F16X3>
-                                : gram_tc_ragged_kernel<MODEL, TCP_BF16X3>;
+    return prec == XLMIMO_BF16 ? gram_tc_items_kernel<MODEL, KMAX, TCP_BF16>
+         : prec == XLMIMO_F16X3 ? gram_tc_items_kernel<MODEL, KMAX, TCP_F16X3>
+                                : gram_tc_items_kernel<MODEL, KMAX, TCP_BF16X3>;
 }
 
+template <int KMAX>
 static RgKernel rg_pick(int model, int prec) {
-    return model == XLMIMO_PNUSW ? rg_pick_prec<XLMIMO_PNUSW>(prec)
-         : model == XLMIMO_UPW   ? rg_pick_prec<XLMIMO_UPW>(prec)
-                                 : rg_pick_prec<XLMIMO_FSPL_USW>(prec);
+    return model == XLMIMO_PNUSW ? rg_pick_prec<XLMIMO_PNUSW, KMAX>(prec)
+         : model == XLMIMO_UPW   ? rg_pick_prec<XLMIMO_UPW, KMAX>(prec)
+                                 : rg_pick_prec<XLMIMO_FSPL_USW, KMAX>(prec);
 }
 
-// Shared memory for a residency of ctas_per_sm CTAs per SM, and the kernel
-// attribute for it (set at plan time, outside any stream capture).
+template <int KMAX>
+static size_t items_smem() {
+    constexpr int NRING = KMAX == 32 ? 2 : 3;
+    return 1024 + NRING * GramEngine<XLMIMO_FSPL_USW, KMAX, TCP_BF16X3, false, NRING>::BYTES +
+           sizeof(EngShared<KMAX, NRING>);
+}
+
+// Kernel attributes and the second stream of the concurrent mode (at plan
+// time, outside any stream capture).
 static int prepare_gram(BatchPlan* p) {
-    RgKernel kern = rg_pick(p->g.model, p->prec);
-    size_t smem = 1024 + RG_NRING * GramEngine<XLMIMO_FSPL_USW, 64, TCP_BF16X3, false, RG_NRING>::BYTES + sizeof(RgShared) +
-                  sizeof(RgCur);
-    int dev = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    size_t want = (size_t)per_sm / (size_t)(p->ctas_per_sm + 1) + 1024;
-    if (want > smem) smem = want;
-    p->smem = smem;
-    return cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                       "ragged attribute");
+    int rc = cuda_status(cudaFuncSetAttribute(rg_pick<32>(p->g.model, p->prec),
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)items_smem<32>()),
+                         "ragged attribute");
+    if (!rc) rc = cuda_status(cudaFuncSetAttribute(rg_pick<64>(p->g.model, p->prec),
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)items_smem<64>()),
+                              "ragged attribute");
+    if (!rc && !p->side) rc = cuda_status(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking), "plan stream");
+    if (!rc && !p->fork) rc = cuda_status(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming), "plan event");
+    if (!rc && !p->join) rc = cuda_status(cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming), "plan event");
+    return rc;
 }
 
+// The Gram matrices of a run: per-user set-up, then the wide items (K > 32)
+// and the narrow ones, one CTA per item; mode 1 launches the two layouts one
+// after the other on `st`, mode 2 the narrow ones on the plan's second stream
+// so that the two launches share the GPU (a fork and a join by events).
 static int run_gram(BatchPlan* p, const double* users, double* gram, cudaStream_t st) {
-    RgKernel kern = rg_pick(p->g.model, p->prec);
-    const size_t smem = p->smem;
-    int rc = cuda_status(cudaMemsetAsync(p->d_counter, 0, 2 * sizeof(int), st), "work counter reset");
+    if (p->n_items < 1) return XLMIMO_OK;
+    const GenParams gp = make_gen_params(p->g);
+    ru_pick(p->g.model, p->prec)<<<(p->count + 7) / 8, 256, 0, st>>>(p->g, gp, p->d_inst, p->count, users, p->d_users,
+                                                                      p->d_iflags);
+    int rc = cuda_status(cudaGetLastError(), "ragged user set-up launch");
     if (rc) return rc;
-    int grid = std::min(p->n_items, num_sms() * p->ctas_per_sm);
-    if (grid < 1) return XLMIMO_OK;
-    kern<<<grid, TC_THREADS, smem, st>>>(p->g, make_gen_params(p->g), p->d_inst, p->d_items, p->n_wide,
-                                         p->n_items - p->n_wide, p->d_counter, users, (double2*)gram, p->d_part);
+    const int n_narrow = p->n_items - p->n_wide;
+    cudaStream_t sn = st;
+    if (p->mode == 2 && n_narrow > 0 && p->n_wide > 0) {
+        rc = cuda_status(cudaEventRecord(p->fork, st), "plan fork");
+        if (!rc) rc = cuda_status(cudaStreamWaitEvent(p->side, p->fork, 0), "plan fork");
+        if (rc) return rc;
+        sn = p->side;
+    }
+    if (p->n_wide > 0)
+        rg_pick<64>(p->g.model, p->prec)<<<p->n_wide, TC_THREADS, items_smem<64>(), st>>>(
+            p->g, gp, p->d_inst, p->d_items, p->d_users, p->d_iflags, (double2*)gram, p->d_part);
+    if (n_narrow > 0)
+        rg_pick<32>(p->g.model, p->prec)<<<n_narrow, TC_THREADS, items_smem<32>(), sn>>>(
+            p->g, gp, p->d_inst, p->d_items + p->n_wide, p->d_users, p->d_iflags, (double2*)gram, p->d_part);
     rc = cuda_status(cudaGetLastError(), "ragged gram launch");
+    if (!rc && sn != st) {
+        rc = cuda_status(cudaEventRecord(p->join, sn), "plan join");
+        if (!rc) rc = cuda_status(cudaStreamWaitEvent(st, p->join, 0), "plan join");
+    }
     if (!rc && p->n_split > 0) {
         ragged_reduce_kernel<<<p->n_split, 256, 0, st>>>(p->d_inst, p->d_lists + p->n_small + p->n_large, p->n_split,
                                                          p->d_part, (double2*)gram);
@@ -371,7 +407,7 @@ extern "C" int xlmimo_batch_plan_create(const xlmimo_array* geo, const xlmimo_in
     // any chunk length accurate; the chunk trades load balance against
     // partial sums)
     int64_t best_chunk = 8192;
-    int best_ctas = 2;
+    int best_mode = 2;
     if (tune_users) {
         // time the candidate tilings on the given users (Gram phase only)
         int64_t gram_total = 0;
@@ -385,9 +421,9 @@ extern "C" int xlmimo_batch_plan_create(const xlmimo_array* geo, const xlmimo_in
         const int64_t chunks[5] = {4096, 8192, 16384, 32768, 131072};
         for (int ci = 0; ci < 5 && !rc; ++ci) {
             rc = build_tables(p, chunks[ci], st);
-            for (int cp = 1; cp <= 2 && !rc; ++cp) {
-                p->ctas_per_sm = cp;
-                rc = prepare_gram(p);
+            if (!rc) rc = prepare_gram(p);
+            for (int md = 1; md <= 2 && !rc; ++md) {
+                p->mode = md;
                 if (!rc) rc = run_gram(p, tune_users, scratch, st);  // warm
                 if (!rc) rc = cuda_status(cudaEventRecord(e0, st), "tuning");
                 if (!rc) rc = run_gram(p, tune_users, scratch, st);
@@ -398,7 +434,7 @@ extern "C" int xlmimo_batch_plan_create(const xlmimo_array* geo, const xlmimo_in
                 if (!rc && ms < best) {
                     best = ms;
                     best_chunk = chunks[ci];
-                    best_ctas = cp;
+                    best_mode = md;
                 }
                 p->candidates += 1;
             }
@@ -409,13 +445,14 @@ extern "C" int xlmimo_batch_plan_create(const xlmimo_array* geo, const xlmimo_in
         p->tuned = rc ? 0 : 1;
     }
     if (!rc) {
-        p->ctas_per_sm = best_ctas;
+        p->mode = best_mode;
         rc = build_tables(p, best_chunk, st);
     }
     if (!rc) rc = prepare_gram(p);
     if (!rc) rc = beamform_ragged_prepare();
     if (rc) {
         free_tables(p);
+        release_streams(p);
         delete h;
         return rc;
     }
@@ -457,7 +494,7 @@ extern "C" int xlmimo_batch_plan_info(xlmimo_batch_plan plan, int64_t* info) {
     const BatchPlan* p = &plan->p;
     info[0] = p->n_items;
     info[1] = p->chunk;
-    info[2] = p->ctas_per_sm;
+    info[2] = p->mode;
     info[3] = p->n_small;
     info[4] = p->n_large;
     info[5] = (int64_t)p->part_bytes;
@@ -471,6 +508,7 @@ extern "C" int xlmimo_batch_plan_destroy(xlmimo_batch_plan plan) {
     if (!plan) return XLMIMO_OK;
     cudaDeviceSynchronize();
     free_tables(&plan->p);
+    release_streams(&plan->p);
     delete plan;
     return XLMIMO_OK;
 }

@@ -161,6 +161,40 @@ __device__ __forceinline__ void exact_slice_words(const PairConst& pc, float mfs
     }
 }
 
+// One user's set-up: geometry, factor of the Gram (G_ij = fac_i fac_j times
+// the accumulated sum) and the amplitude weight of its generated entries
+// (ug.ampc; 0 for padding); bad: an invalid position; near: too close to the
+// array for the slice expansion.
+struct UserSetup {
+    UserGeo ug;
+    double fac;
+    int bad, near;
+};
+
+template <int MODEL, int PREC, bool URA>
+__device__ __forceinline__ UserSetup user_setup(const Geom& g, const GenParams& gp, double x, double y, bool valid) {
+    UserSetup s;
+    s.ug = make_user_geo(g, x, y);
+    s.bad = valid && !s.ug.ok;
+    s.near = valid && !(x * g.inv_lambda >= (double)NEAR_DIST * (double)gp.dprime_f);
+    // the BF16 paths generate entries without the amplitude constant and
+    // apply it to the Gram in FP64; the FP16 path scales user k's entries by
+    // 1/|h_k| at the array centre so that they sit near 1, and divides it out
+    double fac = amp_const(g, x, y);
+    float aw = 1.0f;
+    if (URA) fac *= 1.4142135623730951;  // fac_i fac_j carries the 2 of a mirrored row pair
+    if (PREC == TCP_F16X3) {
+        const double rc = sqrt(x * x + y * y) * g.inv_lambda;  // distance in wavelengths
+        double amp_c = (MODEL == XLMIMO_UPW) ? fac : (MODEL == XLMIMO_PNUSW) ? fac / (rc * sqrt(rc)) : fac / rc;
+        const float sc = (float)(1.0 / amp_c);
+        aw = (float)(fac * (double)sc);  // entries c s_k / r^p ~ 1, c the model's constant
+        fac = 1.0 / (double)sc;
+    }
+    s.ug.ampc = valid ? aw : 0.f;
+    s.fac = fac;
+    return s;
+}
+
 template <int MODEL, int KMAX, int PREC, bool URA, int NRING>
 struct GramEngine {
     using C = TcCfg<KMAX>;
@@ -193,33 +227,14 @@ struct GramEngine {
     // KMAX - 1 are padding at (1, 0) with weight 0.
     template <class SH>
     static __device__ __forceinline__ void setup_user(SH* sh, const Geom& g, const GenParams& gp, const double* users, int K, int tid) {
-        double x = 1.0, y = 0.0;
-        if (tid < K) {
-            x = users[tid * 2];
-            y = users[tid * 2 + 1];
-        }
-        UserGeo u = make_user_geo(g, x, y);
-        if (tid < K && !u.ok) atomicOr(&sh->bad, 1);
-        if (tid < K && !(x * g.inv_lambda >= (double)NEAR_DIST * (double)gp.dprime_f)) atomicOr(&sh->near, 1);
-        // the BF16 paths generate entries without the amplitude constant and
-        // apply it to the Gram in FP64; the FP16 path scales user k's entries by
-        // 1/|h_k| at the array centre so that they sit near 1, and divides it out
-        double fac = amp_const(g, x, y);
-        float aw = 1.0f;
-        if (URA) {
-            sh->ux[tid] = x;
-            fac *= 1.4142135623730951;  // fac_i fac_j carries the 2 of a mirrored row pair
-        }
-        if (PREC == TCP_F16X3) {
-            const double rc = sqrt(x * x + y * y) * g.inv_lambda;  // distance in wavelengths
-            double amp_c = (MODEL == XLMIMO_UPW) ? fac : (MODEL == XLMIMO_PNUSW) ? fac / (rc * sqrt(rc)) : fac / rc;
-            const float sc = (float)(1.0 / amp_c);
-            aw = (float)(fac * (double)sc);  // entries c s_k / r^p ~ 1, c the model's constant
-            fac = 1.0 / (double)sc;
-        }
-        u.ampc = tid < K ? aw : 0.f;  // the amplitude weight of the generated entries
-        sh->ug[tid] = u;
-        sh->fac[tid] = fac;
+        const bool valid = tid < K;
+        const double x = valid ? users[tid * 2] : 1.0, y = valid ? users[tid * 2 + 1] : 0.0;
+        const UserSetup u = user_setup<MODEL, PREC, URA>(g, gp, x, y, valid);
+        if (u.bad) atomicOr(&sh->bad, 1);
+        if (u.near) atomicOr(&sh->near, 1);
+        if (URA) sh->ux[tid] = x;
+        sh->ug[tid] = u.ug;
+        sh->fac[tid] = u.fac;
     }
 
     // Generator warps 0-7 over the item's elements [nbeg, nend).  gs0 / gd0:
@@ -228,7 +243,14 @@ struct GramEngine {
     template <class SH>
     static __device__ __forceinline__ bool generate(SH* sh, uint32_t sbase, uint32_t tmem, const Geom& g, const GenParams& gp,
                                     int64_t nbeg, int64_t nend, const UraRows& ura, int gs0, int gd0, int gsp0,
-                                    bool fast, int warp, int lane) {
+                                    bool fast) {
+        // the thread's coordinates read afresh (an opaque read): in a
+        // persistent kernel the values derived from them below are then made
+        // per item instead of being hoisted across the whole item loop, where
+        // they would stay live through the epilogue and spill
+        uint32_t tidx;
+        asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tidx));
+        const int warp = (int)(tidx >> 5), lane = (int)(tidx & 31u);
         volatile int* abort = &sh->abort;
         const int nst = stages(nbeg, nend);
         const int ndrain = drains(nst);

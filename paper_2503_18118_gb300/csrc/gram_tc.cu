@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
     const int64_t nend = min(g.N, nbeg + chunk);
     const int nst = E::stages(nbeg, nend);
     if (warp < 8) {
-        E::generate(sh, smem_u32(base), tmem, g, gp, nbeg, nend, ura, 0, 0, 0, !sh->near, warp, lane);
+        E::generate(sh, smem_u32(base), tmem, g, gp, nbeg, nend, ura, 0, 0, 0, !sh->near);
     } else {
         if (lane == 0) E::mma(sh, smem_u32(base), tmem, nst, 0, 0);
         __syncwarp();

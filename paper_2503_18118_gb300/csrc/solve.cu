@@ -493,10 +493,11 @@ __device__ __forceinline__ double ff2_total(float2 s, float2 c) {
 // sums in shared memory; the conversions to FP64 and the divisions then run
 // for all users at once, one lane per user (FP64 instructions cost a full
 // warp's issue whatever the number of active lanes).
+// rec: shared scratch of 3 XLMIMO_MAX_USERS float pairs (the caller's pivot
+// arrays, no longer needed at this point).
 __device__ void mismatched_sinr(const cf* FM, const cf* FG, const double* p, double s2, int K, double* sinr_t,
-                                double* dlbuf) {
+                                double* dlbuf, float2 (*rec)[3]) {
     __shared__ float2 pf[XLMIMO_MAX_USERS];
-    __shared__ float2 rec[XLMIMO_MAX_USERS][3];  // per user: S, I, N, each as a float pair (t, e), t + e
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     for (int k = tid; k < K; k += blockDim.x) {
         float h, l;
@@ -606,8 +607,12 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
     cd* X = Z + KK;  // K rows of K + 1 (the triangular inverse's padded stride)
     double* p = reinterpret_cast<double*>(X + KK + K);
     double* dg = p + XLMIMO_MAX_USERS;
-    __shared__ double pivd[XLMIMO_MAX_USERS], sp[XLMIMO_MAX_USERS];
-    __shared__ float2 dinvf[XLMIMO_MAX_USERS];
+    // pivots, MMSE loading and pivot inverses; the mismatched SINR reuses the
+    // same bytes for its per-user sums once they are no longer needed
+    __shared__ double sbuf[3 * XLMIMO_MAX_USERS];
+    double* pivd = sbuf;
+    double* sp = sbuf + XLMIMO_MAX_USERS;
+    float2* dinvf = reinterpret_cast<float2*>(sbuf + 2 * XLMIMO_MAX_USERS);
     __shared__ int flag, piv, st;
     __shared__ double cs;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -747,7 +752,8 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
         load_cf(Gb, gt, K, c);
         __syncthreads();
         mismatched_sinr(reinterpret_cast<const cf*>(Mb), reinterpret_cast<const cf*>(Gb), p, s2c, K, sinr_t,
-                        scheme == XLMIMO_ZF_DL ? dg + XLMIMO_MAX_USERS : nullptr);
+                        scheme == XLMIMO_ZF_DL ? dg + XLMIMO_MAX_USERS : nullptr,
+                        reinterpret_cast<float2(*)[3]>(sbuf));
     }
     if (tid == 0) *status_t = st;
 }

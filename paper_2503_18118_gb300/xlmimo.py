@@ -418,7 +418,7 @@ class BatchPlan:
     def info(self) -> dict:
         v = (ctypes.c_int64 * 8)()
         _check(lib().xlmimo_batch_plan_info(self._h, v))
-        keys = ("items", "chunk", "ctas_per_sm", "small", "large", "workspace_bytes", "tuned", "candidates")
+        keys = ("items", "chunk", "mode", "small", "large", "workspace_bytes", "tuned", "candidates")
         return dict(zip(keys, list(v)))
 
     def close(self):

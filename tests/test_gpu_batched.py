@@ -120,8 +120,8 @@ def test_batch_graph_capture_and_autotune(xl):
     arr = xl.array(1, LAM)
     plan = xl.BatchPlan(arr, n, k, scheme, noise, tune_users=U)
     info = plan.info()
-    assert info["tuned"] == 1 and info["candidates"] == 10  # 5 chunk lengths x 1 or 2 CTAs per SM
-    assert info["chunk"] in (4096, 8192, 16384) and info["ctas_per_sm"] in (1, 2)
+    assert info["tuned"] == 1 and info["candidates"] == 10  # 5 chunk lengths x 2 modes
+    assert info["chunk"] in (4096, 8192, 16384, 32768, 131072) and info["mode"] in (1, 2)
     P = dev(snr)
     out = dict(gram=torch.empty(plan.gram_total, dtype=torch.complex128, device="cuda"),
                sinr=torch.empty(plan.users_total, dtype=torch.float64, device="cuda"),
