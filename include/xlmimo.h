@@ -292,13 +292,16 @@ int xlmimo_saturation_analytic(const xlmimo_user_dist* dist, int K, double t, do
  *   out[4b + 3] = log2 det R + log2 U     (log2 L, the Schur-Horn lower bound)
  * K is 1..XLMIMO_MAX_BOUNDS_USERS (Fig. 5 reaches K = 1000); users[b][k][2]
  * positions on the device as for xlmimo_channel_gram; out on the device.
- * Channels are generated in FP32 (span-referenced phase); the Gram sums FP32
- * products over 32-element chunks and the chunks in double-float (~2e-6
- * relative at worst); the blocked Cholesky factorisations of R and I + snr R
- * run in FP64.  A trial
- * whose R is not numerically positive definite (coincident users) gets NaN.
- * Asynchronous on `stream`; allocates B*K*n_ant*8 + 3*B*Kp^2*16 bytes
- * (Kp = K rounded up to 64) of stream-ordered workspace and frees it.
+ * Channels are generated in FP32 (span-referenced phase) and stored as a BF16
+ * split h = h_hi + h_lo; the real Gram of [Re H; Im H] runs on the tensor
+ * cores as hi*hi + lo*hi + hi*lo with FP32 totals (each product within
+ * 3 * 2^-16 of |h_i,n||h_j,n|, ~1e-6 relative per correlation entry in
+ * practice); the blocked Cholesky factorisations of R and I + snr R run in
+ * FP64.  A trial whose R is not numerically positive definite (coincident
+ * users) gets NaN.
+ * Asynchronous on `stream`; allocates 8*B*Kp*Np + 16*B*Kp^2 + 32*B*Kp^2 + 16*B
+ * bytes (Kp = K rounded up to 64, Np = n_ant rounded up to 64) of
+ * stream-ordered workspace and frees it.
  * XLMIMO_EINVAL for K out of range, snr < 0 or NULL pointers. */
 #define XLMIMO_MAX_BOUNDS_USERS 1024
 int xlmimo_capacity_bounds(const xlmimo_array* arr, const double* users, int K, int B, double snr,

@@ -7,40 +7,60 @@
 //   log2 L = log2 det R + log2 U      (the Schur-Horn lower bound),
 // and -(1/K) log2 det R is the negative empirical expectation of Fig. 5.
 // K reaches 1000 there, beyond the K <= 64 receivers, so the path is:
-//   1. channel entries into HBM (FP32, the span-referenced generator of
-//      chan_gen.cuh), one CTA per (trial, user);
-//   2. the lower 64 x 64 user tiles of G = H^H H: FP32 products summed over
-//      32-element chunks, chunk sums in double-float, FP64 once per entry;
-//   3. R and I + a R, FP64, padded to a multiple of 64 with identity rows;
+//   1. channel entries into HBM as a BF16 split of X = [Re H ; Im H] (the
+//      span-referenced FP32 generator of chan_gen.cuh), one CTA per (trial,
+//      user), users padded to Kp (a multiple of 64) and elements to Np (a
+//      multiple of 64) with zeros;
+//   2. the real Gram X X^T on the tensor cores, 128 x 128 tiles of the lower
+//      triangle, hi*hi + lo*hi + hi*lo with FP32 totals (gram_hilo_tc.cuh);
+//   3. the complex Gram from the real one, then R and I + a R, FP64, padded to
+//      a multiple of 64 with identity rows;
 //   4. a right-looking blocked Cholesky of all 2B matrices at once, 32
 //      columns a step: diagonal block, panel solve, trailing update, each a
 //      batched launch; the log-determinant adds 2 log2 L_kk block by block.
 // Matrices are column-major (element (i, j) at j * Kp + i), lower triangle.
 #include <math.h>
 
+#include <cudaTypedefs.h>
+
 #include "chan_gen.cuh"
 #include "common.cuh"
+#include "gram_hilo_tc.cuh"
 
 namespace xl {
 
 constexpr int BT = 32;  // tile and Cholesky block size
 
 // -------------------------------------------------------------- channels
-// H[(b K + k) N + n] = h_k(n) of trial b (FP32 complex).  One CTA per (trial,
-// user): the user's geometry once (FP64), then 256 span references at a time
-// (one per thread) and the entries of those spans, written contiguously.
+// X_hi, X_lo of trial b: row k = Re h_k, row Kp + k = Im h_k (elements
+// contiguous, Np per row), h = hi + lo with hi = RN_bf16(h) and lo =
+// RN_bf16(h - hi).  One CTA per (trial, user k < Kp): the user's geometry
+// once (FP64), then 256 span references at a time (one per thread) and the
+// entries of those spans.  Padding users and elements are zero.
 constexpr int CH_THREADS = 256;
 
 __global__ void __launch_bounds__(CH_THREADS) bounds_channel_kernel(Geom g, GenParams gp, const double* __restrict__ users,
-                                                                    int K, float2* __restrict__ H) {
+                                                                    int K, int Kp, int64_t Np,
+                                                                    __nv_bfloat16* __restrict__ Xhi,
+                                                                    __nv_bfloat16* __restrict__ Xlo) {
     __shared__ UserGeo ug;
     __shared__ UserRef refs[CH_THREADS];
     const int64_t b = blockIdx.y;
     const int k = blockIdx.x, tid = threadIdx.x;
+    const int64_t ro = (b * 2 * Kp + k) * Np, io = (b * 2 * Kp + Kp + k) * Np;  // rows of Re and Im
+    const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+    if (k >= K) {
+        for (int64_t n = tid; n < Np; n += CH_THREADS) {
+            Xhi[ro + n] = z;
+            Xlo[ro + n] = z;
+            Xhi[io + n] = z;
+            Xlo[io + n] = z;
+        }
+        return;
+    }
     if (tid == 0) ug = make_user_geo(g, users[(b * K + k) * 2], users[(b * K + k) * 2 + 1]);
     __syncthreads();
     const int64_t nspans = (g.N + REF_SPAN - 1) / REF_SPAN;
-    float2* Hk = H + (b * K + k) * g.N;
     for (int64_t s0 = 0; s0 < nspans; s0 += CH_THREADS) {
         if (s0 + tid < nspans) refs[tid] = make_user_ref(gp, ug, (long long)((s0 + tid) * REF_SPAN + REF_SPAN / 2));
         __syncthreads();
@@ -50,98 +70,35 @@ __global__ void __launch_bounds__(CH_THREADS) bounds_channel_kernel(Geom g, GenP
             const int sp = (int)(i / REF_SPAN), m = (int)(i - (int64_t)sp * REF_SPAN) - REF_SPAN / 2;
             float2 h = gen_entry_f32(g.model, gp.dprime_f, ug.xl2, ug.x2x2, ug.ampc, refs[sp], (float)m);
             if (!ug.ok) h = make_float2(nanf(""), nanf(""));
-            Hk[nb0 + i] = h;
+            const __nv_bfloat16 rh = __float2bfloat16_rn(h.x), ih = __float2bfloat16_rn(h.y);
+            Xhi[ro + nb0 + i] = rh;
+            Xlo[ro + nb0 + i] = __float2bfloat16_rn(h.x - __bfloat162float(rh));
+            Xhi[io + nb0 + i] = ih;
+            Xlo[io + nb0 + i] = __float2bfloat16_rn(h.y - __bfloat162float(ih));
         }
         __syncthreads();
     }
-}
-
-// -------------------------------------------------------------- Gram tiles
-// (hi, lo) += v by Knuth's two-sum on the high part (double-float accumulator).
-__device__ __forceinline__ void ff_acc(float& hi, float& lo, float v) {
-    const float t = __fadd_rn(hi, v);
-    const float bb = __fsub_rn(t, hi);
-    lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bb)), __fsub_rn(v, bb)));
-    hi = t;
-}
-
-// Tile (ti, tj), ti >= tj, of GT x GT users of trial b: G[j Kp + i] =
-// sum_n conj(h_i(n)) h_j(n).  256 threads; thread (ri, cj) = (tid / 16,
-// tid % 16) owns rows ri + 16 qa and columns cj + 16 qb (qa, qb < 4), so a
-// warp's column reads fall in distinct bank pairs and each element loaded
-// from shared memory feeds four complex MACs.  The products and the sum over
-// a 32-element chunk are FP32 (worst relative error 32 x 2^-24 of the chunk's
-// sum of magnitudes); chunk sums go into double-float accumulators, so the
-// sum over N loses nothing further, and the FP64 pipe is used once per entry.
-constexpr int GT = 64;
-
-__global__ void __launch_bounds__(256) bounds_gram_kernel(const float2* __restrict__ H, int K, int64_t N, int Kp,
-                                                          double2* __restrict__ G) {
-    __shared__ float2 Hi[GT][BT + 1], Hj[GT][BT + 1];  // [user][element of the chunk]
-    const int64_t b = blockIdx.y;
-    int ti, tj;
-    tri_index(blockIdx.x, &ti, &tj);
-    const int tid = threadIdx.x, ri = tid >> 4, cj = tid & 15;
-    const float2* Hb = H + b * K * N;
-    float hx[4][4], lx[4][4], hy[4][4], ly[4][4];
-#pragma unroll
-    for (int qa = 0; qa < 4; ++qa)
-#pragma unroll
-        for (int qb = 0; qb < 4; ++qb) hx[qa][qb] = lx[qa][qb] = hy[qa][qb] = ly[qa][qb] = 0.f;
-    for (int64_t n0 = 0; n0 < N; n0 += BT) {
-#pragma unroll
-        for (int l = 0; l < GT * BT / 256; ++l) {
-            const int idx = tid + 256 * l, u = idx >> 5, e = idx & 31;  // user, element
-            const int64_t n = n0 + e;
-            const int ui = ti * GT + u, uj = tj * GT + u;
-            Hi[u][e] = (ui < K && n < N) ? Hb[(int64_t)ui * N + n] : make_float2(0.f, 0.f);
-            Hj[u][e] = (uj < K && n < N) ? Hb[(int64_t)uj * N + n] : make_float2(0.f, 0.f);
-        }
-        __syncthreads();
-        float sx[4][4], sy[4][4];
-#pragma unroll
-        for (int qa = 0; qa < 4; ++qa)
-#pragma unroll
-            for (int qb = 0; qb < 4; ++qb) sx[qa][qb] = sy[qa][qb] = 0.f;
-#pragma unroll 4
-        for (int e = 0; e < BT; ++e) {
-            float2 a[4], v[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                a[q] = Hi[ri + 16 * q][e];
-                v[q] = Hj[cj + 16 * q][e];
-            }
-#pragma unroll
-            for (int qa = 0; qa < 4; ++qa)
-#pragma unroll
-                for (int qb = 0; qb < 4; ++qb) {  // += conj(a) v
-                    sx[qa][qb] = fmaf(a[qa].x, v[qb].x, fmaf(a[qa].y, v[qb].y, sx[qa][qb]));
-                    sy[qa][qb] = fmaf(a[qa].x, v[qb].y, fmaf(-a[qa].y, v[qb].x, sy[qa][qb]));
-                }
-        }
-#pragma unroll
-        for (int qa = 0; qa < 4; ++qa)
-#pragma unroll
-            for (int qb = 0; qb < 4; ++qb) {
-                ff_acc(hx[qa][qb], lx[qa][qb], sx[qa][qb]);
-                ff_acc(hy[qa][qb], ly[qa][qb], sy[qa][qb]);
-            }
-        __syncthreads();
+    for (int64_t n = g.N + tid; n < Np; n += CH_THREADS) {
+        Xhi[ro + n] = z;
+        Xlo[ro + n] = z;
+        Xhi[io + n] = z;
+        Xlo[io + n] = z;
     }
-    double2* Gb = G + b * (int64_t)Kp * Kp;
-#pragma unroll
-    for (int qa = 0; qa < 4; ++qa)
-#pragma unroll
-        for (int qb = 0; qb < 4; ++qb)
-            Gb[(int64_t)(tj * GT + cj + 16 * qb) * Kp + ti * GT + ri + 16 * qa] =
-                make_double2((double)hx[qa][qb] + (double)lx[qa][qb], (double)hy[qa][qb] + (double)ly[qa][qb]);
 }
 
 // -------------------------------------------------------------- R, I + aR
+// The complex Gram G_ij = h_i^H h_j from the real X X^T (Rr, 2Kp x 2Kp FP32,
+// row-major, tiles on or below the diagonal written):
+//   Re G_ij = Rr(i, j) + Rr(Kp + i, Kp + j),  Im G_ij = Rr(i, Kp + j) - Rr(Kp + i, j).
+__device__ __forceinline__ double rr_at(const float* Rr, int K2, int r, int c) {
+    return (r / GH_TILE >= c / GH_TILE) ? (double)Rr[(int64_t)r * K2 + c] : (double)Rr[(int64_t)c * K2 + r];
+}
+
 // A[2b] = R, A[2b+1] = I + a R (lower triangles), padded with identity rows.
-__global__ void bounds_normalize_kernel(const double2* __restrict__ G, int K, int Kp, double a, int B,
+__global__ void bounds_normalize_kernel(const float* __restrict__ Rr, int K, int Kp, double a, int B,
                                         double2* __restrict__ A) {
     const int64_t per = (int64_t)Kp * Kp;
+    const int K2 = 2 * Kp;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)B * per;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = e / per;
@@ -150,19 +107,57 @@ __global__ void bounds_normalize_kernel(const double2* __restrict__ G, int K, in
         if (i < j) continue;
         double2 r = make_double2(i == j ? 1.0 : 0.0, 0.0), m = r;
         if (i < K && j < K) {
-            const double2* Gb = G + b * per;
+            const float* Rb = Rr + b * (int64_t)K2 * K2;
             if (i == j) {
                 m = make_double2(1.0 + a, 0.0);
             } else {
-                const double2 v = Gb[w];
-                const double s = 1.0 / sqrt(Gb[(int64_t)i * Kp + i].x * Gb[(int64_t)j * Kp + j].x);
-                r = make_double2(v.x * s, v.y * s);
+                const double gre = rr_at(Rb, K2, i, j) + rr_at(Rb, K2, Kp + i, Kp + j);
+                const double gim = rr_at(Rb, K2, i, Kp + j) - rr_at(Rb, K2, Kp + i, j);
+                const double gii = rr_at(Rb, K2, i, i) + rr_at(Rb, K2, Kp + i, Kp + i);
+                const double gjj = rr_at(Rb, K2, j, j) + rr_at(Rb, K2, Kp + j, Kp + j);
+                const double s = 1.0 / sqrt(gii * gjj);
+                r = make_double2(gre * s, gim * s);
                 m = make_double2(a * r.x, a * r.y);
             }
         }
         A[2 * b * per + w] = r;
         A[(2 * b + 1) * per + w] = m;
     }
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// Tensor map of B trials of 2Kp rows x Np BF16 elements, boxes of 128 rows x
+// 64 elements (128 bytes: the swizzle atom), 128-byte swizzle.
+static int x_tensor_map(CUtensorMap* map, void* base, int64_t Np, int Kp, int B) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) {
+        set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return XLMIMO_ECUDA;
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)Np, (cuuint64_t)(2 * Kp), (cuuint64_t)B};
+    const cuuint64_t strides[2] = {(cuuint64_t)Np * 2, (cuuint64_t)(2 * Kp) * (cuuint64_t)Np * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)GH_BK, (cuuint32_t)GH_TILE, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return XLMIMO_ECUDA;
+    }
+    return XLMIMO_OK;
 }
 
 // -------------------------------------------------------------- blocked Cholesky
@@ -305,28 +300,40 @@ extern "C" int xlmimo_capacity_bounds(const xlmimo_array* arr, const double* use
         return XLMIMO_EINVAL;
     }
     cudaStream_t st = as_stream(stream);
-    const int Kp = (K + GT - 1) / GT * GT;  // multiple of the Gram tile and of the Cholesky block
-    const int nb = Kp / BT, ng = Kp / GT;
-    const int64_t N = g.N, per = (int64_t)Kp * Kp;
-    float2* H = nullptr;
-    double2 *G = nullptr, *A = nullptr;
+    const int Kp = (K + 63) / 64 * 64;  // 2 Kp rows: whole 128-row Gram tiles; a multiple of the Cholesky block
+    const int nb = Kp / BT, nt = 2 * Kp / GH_TILE;
+    const int64_t N = g.N, Np = (N + GH_BK - 1) / GH_BK * GH_BK, per = (int64_t)Kp * Kp;
+    const int64_t K2 = 2 * Kp;
+    __nv_bfloat16 *Xhi = nullptr, *Xlo = nullptr;
+    float* Rr = nullptr;
+    double2* A = nullptr;
     double* ld = nullptr;
-    rc = cuda_status(cudaMallocAsync((void**)&H, (size_t)B * K * N * sizeof(float2), st), "workspace allocation");
-    if (!rc) rc = cuda_status(cudaMallocAsync((void**)&G, (size_t)B * per * sizeof(double2), st), "workspace allocation");
+    rc = cuda_status(cudaMallocAsync((void**)&Xhi, (size_t)B * K2 * Np * 2, st), "workspace allocation");
+    if (!rc) rc = cuda_status(cudaMallocAsync((void**)&Xlo, (size_t)B * K2 * Np * 2, st), "workspace allocation");
+    if (!rc) rc = cuda_status(cudaMallocAsync((void**)&Rr, (size_t)B * K2 * K2 * sizeof(float), st), "workspace allocation");
     if (!rc) rc = cuda_status(cudaMallocAsync((void**)&A, (size_t)2 * B * per * sizeof(double2), st), "workspace allocation");
     if (!rc) rc = cuda_status(cudaMallocAsync((void**)&ld, (size_t)2 * B * sizeof(double), st), "workspace allocation");
+    CUtensorMap mhi, mlo;
+    if (!rc) rc = x_tensor_map(&mhi, Xhi, Np, Kp, B);
+    if (!rc) rc = x_tensor_map(&mlo, Xlo, Np, Kp, B);
+    if (!rc)
+        rc = cuda_status(cudaFuncSetAttribute(gram_hilo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)gh_smem_bytes()),
+                         "bounds gram attribute");
     if (!rc) {
-        bounds_channel_kernel<<<dim3((unsigned)K, (unsigned)B), CH_THREADS, 0, st>>>(g, make_gen_params(g), users, K, H);
+        bounds_channel_kernel<<<dim3((unsigned)Kp, (unsigned)B), CH_THREADS, 0, st>>>(g, make_gen_params(g), users, K, Kp,
+                                                                                     Np, Xhi, Xlo);
         rc = cuda_status(cudaGetLastError(), "bounds channel launch");
     }
     if (!rc) {
-        bounds_gram_kernel<<<dim3((unsigned)(ng * (ng + 1) / 2), (unsigned)B), 256, 0, st>>>(H, K, N, Kp, G);
+        gram_hilo_kernel<<<dim3((unsigned)(nt * (nt + 1) / 2), (unsigned)B), GH_THREADS, gh_smem_bytes(), st>>>(
+            mhi, mlo, (int)Np, Kp, Rr);
         rc = cuda_status(cudaGetLastError(), "bounds gram launch");
     }
     if (!rc) {
         int64_t blocks = ((int64_t)B * per + 255) / 256;
         if (blocks > 16LL * num_sms()) blocks = 16LL * num_sms();
-        bounds_normalize_kernel<<<(unsigned)blocks, 256, 0, st>>>(G, K, Kp, snr, B, A);
+        bounds_normalize_kernel<<<(unsigned)blocks, 256, 0, st>>>(Rr, K, Kp, snr, B, A);
         rc = cuda_status(cudaGetLastError(), "bounds normalize launch");
     }
     if (!rc) rc = cuda_status(cudaMemsetAsync(ld, 0, (size_t)2 * B * sizeof(double), st), "workspace clear");
@@ -346,7 +353,8 @@ extern "C" int xlmimo_capacity_bounds(const xlmimo_array* arr, const double* use
     }
     if (ld) cudaFreeAsync(ld, st);
     if (A) cudaFreeAsync(A, st);
-    if (G) cudaFreeAsync(G, st);
-    if (H) cudaFreeAsync(H, st);
+    if (Rr) cudaFreeAsync(Rr, st);
+    if (Xlo) cudaFreeAsync(Xlo, st);
+    if (Xhi) cudaFreeAsync(Xhi, st);
     return rc;
 }
