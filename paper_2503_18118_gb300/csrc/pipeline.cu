@@ -131,7 +131,10 @@ extern "C" int xlmimo_mc_step(const xlmimo_mc_batch* j, void* stream) {
                              j->capacity ? j->capacity + b0 : nullptr, j->rate + b0};
         if (gc) {
             // both receivers (and their sum rates) in one launch
-            const BfJob cf = {gc, gm, pw, nz, j->cf_scheme, j->sinr_cf + (size_t)b0 * K, j->status_cf + b0, nullptr,
+            // below the FP64 Gram the mismatched SINR takes the FP32 correction:
+            // its error stays far under the exact Gram's own
+            const int cfs = j->cf_scheme | (j->prec != XLMIMO_F64 ? XLMIMO_MISMATCH_FP32 : 0);
+            const BfJob cf = {gc, gm, pw, nz, cfs, j->sinr_cf + (size_t)b0 * K, j->status_cf + b0, nullptr,
                               j->rate_cf + b0};
             rc = launch_beamform_pair(exact, cf, K, nb, j->power_mode, s1);
         } else {

@@ -1,10 +1,13 @@
 // Linear receivers from the Gram matrix (Sec. V): ZF (Eq. 21), MMSE, MRC,
 // matched or built from another Gram matrix (modified ZF, Sec. V-B), and the
 // capacity log2 det (Eq. 9).  One CTA per trial; the K x K complex matrices
-// live in shared memory and every solve is FP64.
+// live in shared memory.
 //
 //   Z = Gf (ZF) or Gf + sigma^2 diag(p)^{-1} (MMSE) is factored Z = L L^H by
-//   a right-looking Cholesky.  X = L^{-1} by forward substitution; then
+//   a right-looking Cholesky: in FP64 for the matched receivers and the
+//   capacity, in double-float on the FP32 pipe for the filter of a
+//   mismatched receiver unless a pivot shows it ill-conditioned (closely
+//   spaced users), which goes to FP64.  X = L^{-1} by forward substitution; then
 //   [Z^{-1}]_kk = sum_i |X_ik|^2 (matched receivers) or M = Z^{-1} = X^H X
 //   (mismatched receivers).  A Z that is not numerically positive definite
 //   (possible for a closed-form Gf at small N) is inverted by Gauss-Jordan
@@ -277,6 +280,96 @@ __device__ __forceinline__ cf cf_scale(const cf& a, float2 v) {
     return {t, __fadd2_rn(__fadd2_rn(s, make_float2(-t.x, -t.y)), c)};
 }
 
+// acc - a conj(b), double-float complex, normalized: the real lanes carry
+// (-re a re b, -im a re b), then (-im a im b, +re a im b).
+__device__ __forceinline__ cf cf_fms_conj(const cf& acc, const cf& a, const cf& b) {
+    float2 s = acc.hi, c = acc.lo;
+    ff2_mac(s, c, make_float2(-a.hi.x, -a.hi.y), make_float2(-a.lo.x, -a.lo.y), make_float2(b.hi.x, b.hi.x),
+            make_float2(b.lo.x, b.lo.x));
+    ff2_mac(s, c, make_float2(-a.hi.y, a.hi.x), make_float2(-a.lo.y, a.lo.x), make_float2(b.hi.y, b.hi.y),
+            make_float2(b.lo.y, b.lo.y));
+    const float2 t = __fadd2_rn(s, c);
+    return {t, __fadd2_rn(__fadd2_rn(s, make_float2(-t.x, -t.y)), c)};
+}
+
+// ---- double-float Cholesky (the mismatched receivers' filter matrix)
+// A pivot d_k below CHOL_FF_MIN_RATIO times the matrix's own diagonal entry
+// d0_k marks the matrix as ill-conditioned (d_k >= lambda_min while
+// d0_k <= lambda_max, so the ratio falls with the condition number: closely
+// spaced users); the caller then factors it again in FP64.  Above it the
+// factor's double-float rounding (~K 2^-48 backward) stays ~2^-27 relative or
+// better in the inverse.
+constexpr float CHOL_FF_MIN_RATIO = 1.0f / 65536.0f;
+
+// 1/sqrt(d) for d = dh + dl in double-float, FP32 instructions only: the
+// MUFU seed y0, r = 1 - d y0^2 with y0^2 and dh y0^2 exact (FMA residuals;
+// 1 - t is exact since t lies within 2^-21 of 1), then one third-order step
+// y = y0 + y0 (r/2 + 3 r^2/8); |r| ~ 2^-22 leaves (5/16) r^3 ~ 2^-66 and the
+// FP32 rounding of the correction ~2^-46 relative.
+__device__ __forceinline__ float2 ff_rsqrt(float dh, float dl) {
+    const float y0 = rsqrtf(dh);
+    const float q = y0 * y0, qe = fmaf(y0, y0, -q);
+    const float t = dh * q, te = fmaf(dh, q, -t);
+    const float r = (1.0f - t) - (te + fmaf(dh, qe, dl * q));
+    const float corr = y0 * (r * fmaf(r, 0.375f, 0.5f));
+    const float yh = y0 + corr;
+    return make_float2(yh, corr - (yh - y0));
+}
+
+// Pivot and scale of column k by warp 0 (every lane forms the same pivot).
+// Returns 0, or 1 if the pivot is not a positive finite number, or 2 if it
+// is below CHOL_FF_MIN_RATIO d0 or outside [2^-100, 2^100] (FP32 range margin).
+__device__ __forceinline__ int chol_pivot_ff(cf* Lk, int k, int K, int lane, float2* dinvf, float d0) {
+    const float dh = Lk[k].hi.x, dl = Lk[k].lo.x;
+    if (!(dh > 0.0f) || !(dh <= 3.4e38f)) return 1;
+    if (dh < CHOL_FF_MIN_RATIO * d0 || dh < 0x1p-100f || dh > 0x1p100f) return 2;
+    const float2 y = ff_rsqrt(dh, dl);
+    for (int i = k + 1 + lane; i < K; i += 32) Lk[i] = cf_scale(Lk[i], y);
+    if (lane == 0) dinvf[k] = y;
+    return 0;
+}
+
+// chol_lower in double-float (T and L as cf, same layout and look-ahead):
+// returns 1 on success (T's strictly lower triangle holds L, dinvf[k] =
+// 1 / L_kk; the diagonal of T is not written), 0 if a pivot is not positive
+// (flag 1), -1 if the matrix is ill-conditioned (flag 2).  d0: the diagonal
+// entries as loaded (FP32).
+__device__ int chol_lower_ff(cf* T, int K, int* flag, float2* dinvf, const float* d0) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid < 32) {
+        const int r = chol_pivot_ff(T, 0, K, tid, dinvf, d0[0]);
+        if (r && tid == 0) *flag = r;
+    }
+    __syncthreads();
+    for (int k = 0;; ++k) {
+        const int f = *flag;
+        if (f) {
+            __syncthreads();  // every thread has read the flag before anyone may reset it
+            return f == 1 ? 0 : -1;
+        }
+        if (k == K - 1) return 1;
+        const cf* Lk = T + k * K;
+        if (tid < 32) {
+            cf* L1 = T + (k + 1) * K;
+            const cf l1 = Lk[k + 1];
+            for (int i = k + 1 + tid; i < K; i += 32) L1[i] = cf_fms_conj(L1[i], Lk[i], l1);
+            __syncwarp();
+            const int r = chol_pivot_ff(L1, k + 1, K, tid, dinvf, d0[k + 1]);
+            if (r && tid == 0) *flag = r;
+        } else {
+            const int m = K - k - 2;
+            const int tri = m * (m + 1) / 2;
+            for (int q = tid - 32; q < tri; q += nt - 32) {
+                int cr, s;
+                tri_index(q, &cr, &s);
+                const int j = K - 1 - cr, i = j + s;
+                T[j * K + i] = cf_fms_conj(T[j * K + i], Lk[i], Lk[j]);  // A_ij -= L_ik conj(L_jk)
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // In place: a K x K complex FP64 matrix becomes double-float (same bytes).
 __device__ void to_cf_inplace(cd* A, int K) {
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -323,19 +416,20 @@ __device__ void gram_of_lower_ff(const cd* X, int xs, cd* M, int K) {
 // subtract U_ik times row k from every row i > k, the (K-k-1) x (k+1) block in
 // parallel; one barrier per column, since the unit diagonal needs no row
 // scaling), then every row i scaled by 1/L_ii.  L comes from chol_lower,
-// column by column (L_ik at T[k K + i]); its strictly lower triangle becomes
-// U in double-float in place (the only part read).  dinvf[k] = 1 / L_kk
+// column by column (L_ik at T[k K + i], FP64, or double-float when t_ff); its
+// strictly lower triangle becomes U in double-float in place (the only part
+// read).  dinvf[k] = 1 / L_kk
 // (float pair).  X has row stride K + 1: a warp whose lanes cover several
 // short rows then spreads over the shared-memory banks instead of hitting
 // one bank group once per row.
-__device__ void tri_inverse_ff(cd* T, cd* X, int K, const float2* dinvf) {
+__device__ void tri_inverse_ff(cd* T, cd* X, int K, const float2* dinvf, bool t_ff) {
     const int xs = K + 1;
     const int tid = threadIdx.x, nt = blockDim.x;
     cf* FT = reinterpret_cast<cf*>(T);
     for (int e = tid; e < K * K; e += nt) {
         const int k = e / K, i = e - k * K;
         if (i > k) {
-            const cf v = cf_scale(to_cf(T[e]), dinvf[k]);
+            const cf v = cf_scale(t_ff ? FT[e] : to_cf(T[e]), dinvf[k]);
             FT[e] = v;
         }
     }
@@ -438,6 +532,24 @@ __device__ void load_lower(cd* T, const double2* __restrict__ g, int K, const do
     }
 }
 
+// load_lower in double-float (T as cf), and the diagonal as FP32 into d0.
+__device__ void load_lower_ff(cf* T, const double2* __restrict__ g, int K, const double* add, double c, float* d0) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < K * K; e += nt) {
+        const int j = e / K, i = e - j * K;
+        if (i > j) {
+            const double2 v = g[e];
+            T[e] = to_cf(c == 1.0 ? cmk(v.x, -v.y) : cmk(v.x * c, -(v.y * c)));
+        }
+    }
+    for (int k = tid; k < K; k += nt) {
+        const double d = c == 1.0 ? g[k * K + k].x : g[k * K + k].x * c;
+        const cf v = to_cf(cmk(add ? d + add[k] : d, 0.0));
+        T[k * K + k] = v;
+        d0[k] = v.hi.x;
+    }
+}
+
 // c g (complex FP64, row-major, global) into shared memory in double-float.
 __device__ void load_cf(cd* F, const double2* __restrict__ g, int K, double c) {
     cf* FF = reinterpret_cast<cf*>(F);
@@ -482,7 +594,8 @@ __device__ __forceinline__ double ff2_total(float2 s, float2 c) {
     return (double)f.x + (double)f.y;
 }
 
-// Mismatched-receiver SINR (Sec. V-B) from M and G in double-float:
+// Mismatched-receiver SINR (Sec. V-B) from M and G in double-float (the
+// default; mismatched_sinr below is the FP32-correction form):
 //   SINR_k = p_k |A_kk|^2 / (sum_{j != k} p_j |A_kj|^2 + sigma^2 Re (A M^H)_kk),
 //   A = M G.
 // A is never stored: warp w takes users k = w, w + nwarps, ...; lane l forms
@@ -495,7 +608,7 @@ __device__ __forceinline__ double ff2_total(float2 s, float2 c) {
 // warp's issue whatever the number of active lanes).
 // rec: shared scratch of 3 XLMIMO_MAX_USERS float pairs (the caller's pivot
 // arrays, no longer needed at this point).
-__device__ void mismatched_sinr(const cf* FM, const cf* FG, const double* p, double s2, int K, double* sinr_t,
+__device__ void mismatched_sinr_ff(const cf* FM, const cf* FG, const double* p, double s2, int K, double* sinr_t,
                                 double* dlbuf, float2 (*rec)[3]) {
     __shared__ float2 pf[XLMIMO_MAX_USERS];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -593,8 +706,176 @@ __device__ void mismatched_sinr(const cf* FM, const cf* FG, const double* p, dou
     }
 }
 
+// FP32 value nearest to d (within one FP32 rounding plus 2^-48 relative),
+// by integer and FP32 instructions only.
+__device__ __forceinline__ float f32_of(double d) {
+    float h, l;
+    split_f64(d, h, l);
+    return __fadd_rn(h, l);
+}
+
+// D = c (G - Gf): the true Gram minus the filter's Gram, both c-scaled, in
+// FP32 (row-major K x K); D = c G when gf is NULL.  With c = 1 (every Gram diagonal within 2^+-60)
+// each part is split into float pairs and subtracted on the FP32 pipe:
+// (Gh - Gfh) + (Gl - Gfl), whose roundings are u |D| each (u = 2^-24) plus
+// 2^-48 |G|; otherwise the difference is formed and scaled in FP64.
+__device__ void load_delta(float2* D, const double2* __restrict__ gf, const double2* __restrict__ gt, int K, double c) {
+    for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+        const double2 a = gt[e], b = gf ? gf[e] : make_double2(0.0, 0.0);
+        float2 d;
+        if (c == 1.0) {
+            float ah, al, bh, bl;
+            split_f64(a.x, ah, al);
+            split_f64(b.x, bh, bl);
+            d.x = __fadd_rn(__fsub_rn(ah, bh), __fsub_rn(al, bl));
+            split_f64(a.y, ah, al);
+            split_f64(b.y, bh, bl);
+            d.y = __fadd_rn(__fsub_rn(ah, bh), __fsub_rn(al, bl));
+        } else {
+            d = make_float2(f32_of((a.x - b.x) * c), f32_of((a.y - b.y) * c));
+        }
+        D[e] = d;
+    }
+}
+
+// Mismatched-receiver SINR (Sec. V-B).  M = Z^{-1} is the inverse of the
+// filter's matrix Z = Gf (ZF) or Gf + diag(sp) (MMSE, sp_j = sigma^2 / p_j)
+// and the receiver meets the true Gram G:
+//   SINR_k = p_k |A_kk|^2 / (sum_{j != k} p_j |A_kj|^2 + sigma^2 (A M^H)_kk),  A = M G.
+// Since M Z = I, A = I + B with B = M (G - Z) = M D - M diag(sp): only the
+// correction B is formed, and (A M^H)_kk = M_kk + sum_j B_kj conj(M_kj).
+// Besides being small where the closed form is accurate, this drops the
+// inverse's own residual M Z - I from A (its error is dM D, not dM G).
+// M is double-float (FM); B = M_hi D is a K^3 product in FP32 (two
+// independent chains), then the loading term M_kj sp_j (FMA-exact product of
+// the high parts plus the cross terms) is subtracted.  Per entry
+//   |dB_kj| <= ((K + 2) u (|M| |D|)_kj + 3 u |M_kj| sp_j + u |B_kj|,  u = 2^-24;
+// the signal, interference and noise sums are FP32 too (positive terms for
+// the interference), and M_kk enters the noise term in double-float.  Warp w
+// takes users k = w, w + nwarps, ...; lane l forms B_kj for j = l (and
+// l + 32 when K > 32) from row k of M (broadcast) and column j of D
+// (contiguous across lanes), and adds its terms to the three per-user sums,
+// reduced by shuffles.  The SINRs are then finished for all users at once,
+// one lane per user, in FP64.
+// MRC (M = I, no inverse): plus_i = false, D = c G and A = B = D.
+// rec: shared scratch of 3 XLMIMO_MAX_USERS floats.  sp: NULL for ZF.
+__device__ void mismatched_sinr(const cf* FM, const float2* D, const double* sp, bool plus_i, const double* p,
+                                double s2, int K, double* sinr_t, double* dlbuf, float (*rec)[3]) {
+    __shared__ float pf[XLMIMO_MAX_USERS];
+    __shared__ float2 spf[XLMIMO_MAX_USERS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (int k = tid; k < K; k += blockDim.x) {
+        pf[k] = f32_of(p[k]);
+        float h = 0.f, l = 0.f;
+        if (sp) split_f64(sp[k], h, l);
+        spf[k] = make_float2(h, l);
+    }
+    __syncthreads();
+    const bool dl = dlbuf != nullptr;
+    // downlink: lane l's column sums sum_{k != j} |A_kj|^2 (j = l, l + 32) over
+    // this warp's rows
+    float cs0 = 0.f, cs1 = 0.f;
+    for (int k = warp; k < K; k += nw) {
+        const cf* Mk = FM + k * K;
+        float ss = 0.f, is = 0.f, ns = 0.f;
+        for (int j = lane; j < K; j += 32) {
+            // B_kj = sum_l M_kl D_lj: (re, im) chains for even and odd l
+            float2 a0 = make_float2(0.f, 0.f), a1 = a0;
+            int l = 0;
+            for (; l + 1 < K; l += 2) {
+                const float2 m0 = Mk[l].hi, d0 = D[l * K + j];
+                const float2 m1 = Mk[l + 1].hi, d1 = D[(l + 1) * K + j];
+                a0.x = fmaf(m0.x, d0.x, a0.x);
+                a0.y = fmaf(m0.x, d0.y, a0.y);
+                a1.x = fmaf(m1.x, d1.x, a1.x);
+                a1.y = fmaf(m1.x, d1.y, a1.y);
+                a0.x = fmaf(-m0.y, d0.y, a0.x);
+                a0.y = fmaf(m0.y, d0.x, a0.y);
+                a1.x = fmaf(-m1.y, d1.y, a1.x);
+                a1.y = fmaf(m1.y, d1.x, a1.y);
+            }
+            if (l < K) {
+                const float2 m0 = Mk[l].hi, d0 = D[l * K + j];
+                a0.x = fmaf(m0.x, d0.x, a0.x);
+                a0.y = fmaf(m0.x, d0.y, a0.y);
+                a0.x = fmaf(-m0.y, d0.y, a0.x);
+                a0.y = fmaf(m0.y, d0.x, a0.y);
+            }
+            float2 b = make_float2(a0.x + a1.x, a0.y + a1.y);
+            const cf m = Mk[j];
+            if (sp) {
+                // b -= M_kj sp_j: p = M_hi sp_hi exactly as p + e
+                const float2 sj = spf[j];
+                const float2 pr = make_float2(m.hi.x * sj.x, m.hi.y * sj.x);
+                const float2 er = make_float2(fmaf(m.lo.x, sj.x, fmaf(m.hi.x, sj.y, fmaf(m.hi.x, sj.x, -pr.x))),
+                                              fmaf(m.lo.y, sj.x, fmaf(m.hi.y, sj.y, fmaf(m.hi.y, sj.x, -pr.y))));
+                b = make_float2((b.x - pr.x) - er.x, (b.y - pr.y) - er.y);
+            }
+            ns = fmaf(b.x, m.hi.x, fmaf(b.y, m.hi.y, ns));  // Re(B_kj conj(M_kj))
+            const float b2 = fmaf(b.x, b.x, b.y * b.y);
+            if (j == k) {
+                ss = plus_i ? fmaf(2.f, b.x, b2) : b2;  // |A_kk|^2 - 1, or |A_kk|^2 for MRC
+            } else if (dl) {
+                if (j < 32) cs0 += b2;
+                else cs1 += b2;
+            } else {
+                is = fmaf(pf[j], b2, is);
+            }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            ss += __shfl_xor_sync(0xffffffffu, ss, off);
+            is += __shfl_xor_sync(0xffffffffu, is, off);
+            ns += __shfl_xor_sync(0xffffffffu, ns, off);
+        }
+        if (lane == 0) {
+            rec[k][0] = ss;
+            rec[k][1] = is;
+            rec[k][2] = ns;
+        }
+    }
+    if (dl) {
+        // per-warp column sums: dlbuf[64 + 64 w + j]
+        double* colp = dlbuf + XLMIMO_MAX_USERS;
+        if (lane < K) colp[warp * XLMIMO_MAX_USERS + lane] = (double)cs0;
+        if (lane + 32 < K) colp[warp * XLMIMO_MAX_USERS + lane + 32] = (double)cs1;
+    }
+    __syncthreads();
+    // S_k = |A_kk|^2, N_k = (A M^H)_kk
+    const double one = plus_i ? 1.0 : 0.0;
+    auto nk = [&](int k) {
+        const cf m = FM[k * K + k];
+        return one * ((double)m.hi.x + (double)m.lo.x) + (double)rec[k][2];
+    };
+    if (!dl) {
+        for (int k = tid; k < K; k += blockDim.x) {
+            const double S = one + (double)rec[k][0];
+            sinr_t[k] = p[k] * S / fma(s2, nk(k), (double)rec[k][1]);
+        }
+        return;
+    }
+    // downlink: beta^2 = P_T / tr(M G M^H), tr = sum_k N_k; |A_kk|^2 = S_k;
+    // column sums in fixed warp order
+    double* colp = dlbuf + XLMIMO_MAX_USERS;
+    for (int k = tid; k < K; k += blockDim.x) dlbuf[k] = one + (double)rec[k][0];
+    __syncthreads();
+    double pt = 0.0, tr = 0.0;
+    for (int k = 0; k < K; ++k) {
+        pt += p[k];
+        tr += nk(k);
+    }
+    const double b2 = pt / tr;
+    for (int k = tid; k < K; k += blockDim.x) {
+        double col = 0.0;
+        for (int w = 0; w < nw; ++w) col += colp[w * XLMIMO_MAX_USERS + k];
+        sinr_t[k] = b2 * dlbuf[k] / fma(b2, col, s2);
+    }
+}
+
+
 // One trial's receiver, executed by the whole CTA.  gf/gt: this trial's Gram
-// matrices (gt == gf when matched); pw: its K powers; s2: its noise power;
+// matrices (gt == gf when matched); scheme may carry XLMIMO_MISMATCH_FP32
+// (the mismatched SINR from the FP32 correction); pw: its K powers; s2: its
+// noise power;
 // sinr_t, status_t, cap_t: its outputs (cap_t may be NULL).  Dynamic shared
 // memory: (2 K^2 + K) complex doubles plus 2 XLMIMO_MAX_USERS doubles, and
 // BF_DL_EXTRA bytes more for the downlink scheme from another Gram matrix.
@@ -616,6 +897,8 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
     __shared__ int flag, piv, st;
     __shared__ double cs;
     const int tid = threadIdx.x, nt = blockDim.x;
+    const bool fp32_corr = (scheme & XLMIMO_MISMATCH_FP32) != 0;
+    scheme &= ~XLMIMO_MISMATCH_FP32;
     bool m_in_z = false;  // M in Z in double-float (else in X in FP64, from Gauss-Jordan)
     if (tid < 32) {
         const double c = trial_scale(gf, gt, K);
@@ -652,15 +935,34 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
         for (int e = tid; e < KK; e += nt) X[e] = cmk((e / K) == (e % K) ? 1.0 : 0.0, 0.0);  // M = I
         __syncthreads();
     } else {
-        load_lower(Z, gf, K, scheme == XLMIMO_MMSE ? sp : nullptr, c);
-        __syncthreads();
-        int ok = chol_lower(Z, K, &flag, dinvf, pivd);
+        int ok;
+        bool z_ff = false;  // the factor in Z is double-float
+        if (!matched) {
+            // the filter of a mismatched receiver: double-float factorisation,
+            // FP64 when a pivot shows it ill-conditioned (dg is free here)
+            float* d0 = reinterpret_cast<float*>(dg);
+            load_lower_ff(reinterpret_cast<cf*>(Z), gf, K, scheme == XLMIMO_MMSE ? sp : nullptr, c, d0);
+            __syncthreads();
+            ok = chol_lower_ff(reinterpret_cast<cf*>(Z), K, &flag, dinvf, d0);
+            if (ok < 0) {
+                if (tid == 0) flag = 0;
+                load_lower(Z, gf, K, scheme == XLMIMO_MMSE ? sp : nullptr, c);
+                __syncthreads();
+                ok = chol_lower(Z, K, &flag, dinvf, pivd);
+            } else {
+                z_ff = true;
+            }
+        } else {
+            load_lower(Z, gf, K, scheme == XLMIMO_MMSE ? sp : nullptr, c);
+            __syncthreads();
+            ok = chol_lower(Z, K, &flag, dinvf, pivd);
+        }
         if (ok) {
             if (mmse_reuse && cap_t) {
                 const double cp = warp0_sum_log2(pivd, p, K, 1.0 / s2c);
                 if (tid == 0) *cap_t = cp;
             }
-            tri_inverse_ff(Z, X, K, dinvf);  // X = L^{-1}, double-float
+            tri_inverse_ff(Z, X, K, dinvf, z_ff);  // X = L^{-1}, double-float
             if (matched) {
                 // dg_k = sum_{i >= k} |X_ik|^2 in double-float, one conversion per k
                 const cf* FX = reinterpret_cast<const cf*>(X);
@@ -746,14 +1048,25 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
         }
     } else {
         // M in double-float, the true Gram into the other buffer (double-float)
+        // M in double-float; the true Gram (double-float) or D = c (G - Gf)
+        // (FP32, fp32_corr) into the other buffer
         cd* Mb = m_in_z ? Z : X;
         cd* Gb = m_in_z ? X : Z;
         if (!m_in_z) to_cf_inplace(Mb, K);
-        load_cf(Gb, gt, K, c);
-        __syncthreads();
-        mismatched_sinr(reinterpret_cast<const cf*>(Mb), reinterpret_cast<const cf*>(Gb), p, s2c, K, sinr_t,
-                        scheme == XLMIMO_ZF_DL ? dg + XLMIMO_MAX_USERS : nullptr,
-                        reinterpret_cast<float2(*)[3]>(sbuf));
+        double* dlb = scheme == XLMIMO_ZF_DL ? dg + XLMIMO_MAX_USERS : nullptr;
+        if (fp32_corr) {
+            const bool mrc = scheme == XLMIMO_MRC;
+            float2* Db = reinterpret_cast<float2*>(Gb);
+            load_delta(Db, mrc ? nullptr : gf, gt, K, c);
+            __syncthreads();
+            mismatched_sinr(reinterpret_cast<const cf*>(Mb), Db, scheme == XLMIMO_MMSE ? sp : nullptr, !mrc, p, s2c, K,
+                            sinr_t, dlb, reinterpret_cast<float(*)[3]>(sbuf));
+        } else {
+            load_cf(Gb, gt, K, c);
+            __syncthreads();
+            mismatched_sinr_ff(reinterpret_cast<const cf*>(Mb), reinterpret_cast<const cf*>(Gb), p, s2c, K, sinr_t, dlb,
+                               reinterpret_cast<float2(*)[3]>(sbuf));
+        }
     }
     if (tid == 0) *status_t = st;
 }
@@ -772,7 +1085,7 @@ __device__ void trial_rate(const double* sinr_t, int K, double* rate_t) {
     }
 }
 
-__global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* __restrict__ gfil,
+__global__ void __launch_bounds__(SOLVE_THREADS, 6) beamform_kernel(const double2* __restrict__ gfil,
                                                                  const double2* __restrict__ gtru, int matched,
                                                                  const double* __restrict__ power,
                                                                  const double* __restrict__ noise, int K,
@@ -790,7 +1103,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) beamform_kernel(const double2* 
 // (even: job 0, odd: job 1), so that every SM holds both kinds at once: the
 // matched MMSE receiver keeps the FP64 pipe busy with its Cholesky while the
 // modified-ZF one works mostly in double-float on the FP32 pipe.
-__global__ void __launch_bounds__(SOLVE_THREADS) beamform_pair_kernel(BfJob j0, BfJob j1, int K, int power_mode) {
+__global__ void __launch_bounds__(SOLVE_THREADS, 6) beamform_pair_kernel(BfJob j0, BfJob j1, int K, int power_mode) {
     const BfJob j = (blockIdx.x & 1) ? j1 : j0;
     const int64_t b = blockIdx.x >> 1;
     const int64_t KK = (int64_t)K * K;
@@ -833,7 +1146,7 @@ int launch_beamform(const double* gf, const double* gt, const double* power, con
     if (!gt) gt = gf;
     size_t KK = (size_t)K * K;
     size_t smem = (2 * KK + K) * sizeof(cd) + 2 * XLMIMO_MAX_USERS * sizeof(double);
-    if (scheme == XLMIMO_ZF_DL) smem += BF_DL_EXTRA;
+    if ((scheme & ~XLMIMO_MISMATCH_FP32) == XLMIMO_ZF_DL) smem += BF_DL_EXTRA;
     cudaError_t e = cudaFuncSetAttribute(beamform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return cuda_status(e, "beamform attribute");
     beamform_kernel<<<B, SOLVE_THREADS, smem, st>>>((const double2*)gf, (const double2*)gt, matched, power, noise, K,
@@ -848,7 +1161,8 @@ int launch_beamform_pair(const BfJob& j0, const BfJob& j1, int K, int B, int pow
     if (c.gt == c.gf) c.gt = nullptr;
     size_t KK = (size_t)K * K;
     size_t smem = (2 * KK + K) * sizeof(cd) + 2 * XLMIMO_MAX_USERS * sizeof(double);
-    if (a.scheme == XLMIMO_ZF_DL || c.scheme == XLMIMO_ZF_DL) smem += BF_DL_EXTRA;
+    if ((a.scheme & ~XLMIMO_MISMATCH_FP32) == XLMIMO_ZF_DL || (c.scheme & ~XLMIMO_MISMATCH_FP32) == XLMIMO_ZF_DL)
+        smem += BF_DL_EXTRA;
     cudaError_t e = cudaFuncSetAttribute(beamform_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return cuda_status(e, "beamform attribute");
     beamform_pair_kernel<<<2 * (int64_t)B, SOLVE_THREADS, smem, st>>>(a, c, K, power_mode);

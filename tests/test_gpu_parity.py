@@ -63,6 +63,52 @@ def receiver_mask(st, st_ref, Gf, p, s2, scheme):
     return ok & ~gpu_only
 
 
+U32 = 2.0 ** -24
+
+
+def mzf_tol(Gf, G, p, s2, scheme):
+    """Relative tolerance of each mismatched-receiver SINR (Sec. V-B, the
+    filter built from Gf and judged on G): 1e-7 for the double-float inverse,
+    plus twice the first-order effect of the FP32 correction the GPU forms.
+    With M = Z^-1, Z = Gf + diag(sp) (sp = s2 / p for MMSE, else 0), it
+    writes A = M G = I + B, B = M (G - Gf) - M diag(sp), whose entries carry
+      |dB_kj| <= eps_kj = (K + 2) u (|M| |G - Gf|)_kj + 3 u |M_kj| sp_j + u |B_kj|,  u = 2^-24,
+    and sums the signal |1 + B_kk|^2, the interference sum_{j != k} p_j |B_kj|^2
+    and the noise term N_k = M_kk + Re sum_j B_kj conj(M_kj) in FP32
+    (downlink ZF: column sums of |B_jk|^2 and beta^2 = sum p / sum N).
+    MRC inverts nothing: A = B = G in FP32 and N_k = G_kk."""
+    nb, K, _ = G.shape
+    tol = np.zeros((nb, K))
+    d = np.arange(K)
+    off = ~np.eye(K, dtype=bool)
+    for b in range(nb):
+        sp = s2[b] / p[b] if scheme == 1 else np.zeros(K)
+        if scheme == 2:
+            M, Bm = np.eye(K), G[b]
+        else:
+            M = np.linalg.inv(Gf[b] + np.diag(sp))
+            Bm = M @ (G[b] - Gf[b]) - M * sp[None, :]
+        aM, aB = np.abs(M), np.abs(Bm)
+        eps = (K + 2) * U32 * (aM @ np.abs(G[b] - (Gf[b] if scheme != 2 else 0))) + 3 * U32 * aM * sp[None, :] + U32 * aB
+        akk = np.abs((scheme != 2) + Bm[d, d])
+        S = akk ** 2
+        dS = 2 * akk * eps[d, d] + eps[d, d] ** 2 + 2 * U32 * np.abs(S - 1)
+        N = (scheme != 2) * np.real(M[d, d]) + np.real((Bm * np.conj(M)).sum(1))
+        dN = (eps * aM).sum(1) + (K + 3) * U32 * (aB * aM).sum(1)
+        de = (2 * aB * eps + eps ** 2) * off
+        if scheme == 3:
+            col = (aB ** 2 * off).sum(0)
+            dcol = de.sum(0) + (K + 3) * U32 * col
+            beta, rbeta = p[b].sum() / N.sum(), dN.sum() / N.sum()
+            rel = dS / S + beta * (dcol + col * rbeta) / (beta * col + s2[b]) + rbeta
+        else:
+            inter = (aB ** 2 * p[b][None, :] * off).sum(1)
+            dinter = (de * p[b][None, :]).sum(1) + (K + 3) * U32 * inter
+            rel = dS / S + (dinter + s2[b] * dN) / (inter + s2[b] * N)
+        tol[b] = 1e-7 + 2 * rel
+    return tol
+
+
 def f64_tol(users, N, lam, spacing=None, model=1):
     """FP64 Gram tolerance: 1e-12, or the FP64 rounding of the phase itself
     where that is larger.  Both sides round the distance r to FP64, which
@@ -228,6 +274,12 @@ def test_beamform_modified_zf(xl, orc, K, scheme):
         assert ok.sum() >= 8
         rel = np.abs(s[ok] - s_ref[ok]) / np.maximum(np.abs(s_ref[ok]), 1e-300)
         assert np.max(rel) <= 1e-7
+        # the FP32 correction, within its bound
+        s, st, _ = xl.xlmimo_beamform(dev(Gc), dev(p), dev(s2), scheme | xl.MISMATCH_FP32, 0, gram_true=dev(G))
+        s, st = s.cpu().numpy(), st.cpu().numpy()
+        ok = receiver_mask(st, st_ref, Gc, p, s2, scheme)
+        rel = np.abs(s[ok] - s_ref[ok]) / np.maximum(np.abs(s_ref[ok]), 1e-300)
+        assert np.all(rel <= mzf_tol(Gc[ok], G[ok], p[ok], s2[ok], scheme))
 
 
 @pytest.mark.parametrize("scale_log2", [-300, -150, -80, 80, 150, 300])
@@ -253,6 +305,10 @@ def test_beamform_scale_invariance(xl, orc, scale_log2):
     ok = receiver_mask(st, st_ref, Gc * sc, p, s2 * sc, 0)
     assert ok.sum() >= 4
     assert np.max(np.abs(s[ok] - s_ref[ok]) / np.abs(s_ref[ok])) <= 1e-7
+    s, st, _ = xl.xlmimo_beamform(dev(Gc * sc), dev(p), dev(s2 * sc), xl.ZF | xl.MISMATCH_FP32, 0, gram_true=dev(G * sc))
+    s, st = s.cpu().numpy(), st.cpu().numpy()
+    ok = receiver_mask(st, st_ref, Gc * sc, p, s2 * sc, 0)
+    assert np.all(np.abs(s[ok] - s_ref[ok]) / np.abs(s_ref[ok]) <= mzf_tol(Gc[ok], G[ok], p[ok], s2[ok], 0))
 
 
 def test_beamform_singular(xl):
@@ -428,7 +484,8 @@ def test_mc_step_matches_individual_calls(xl, prec, B, chunks):
     s, st, cap = xl.xlmimo_beamform(G, snr, noise, xl.MMSE, xl.POWER_RXSNR, capacity=True)
     r, stats = xl.xlmimo_sumrate(s)
     Gc = xl.xlmimo_corr_closed_form(arr, users)
-    s2, st2, _ = xl.xlmimo_beamform(Gc, snr, noise, xl.ZF, xl.POWER_RXSNR, gram_true=G)
+    # below the FP64 Gram the step's closed-form receiver takes the FP32 correction
+    s2, st2, _ = xl.xlmimo_beamform(Gc, snr, noise, xl.ZF | xl.MISMATCH_FP32, xl.POWER_RXSNR, gram_true=G)
     r2, stats2 = xl.xlmimo_sumrate(s2)
     sat = xl.xlmimo_saturation(users, 0.9, LAM100 / 2)
     torch.cuda.synchronize()
@@ -465,6 +522,11 @@ def test_downlink_zf(xl, orc, K):
         ok = receiver_mask(st, st_ref, Gc, p, s2, 3)
         assert ok.sum() >= 4
         assert np.max(np.abs(s[ok] - s_ref[ok]) / np.maximum(np.abs(s_ref[ok]), 1e-300)) <= 1e-7
+        s, st, _ = xl.xlmimo_beamform(dev(Gc), dev(p), dev(s2), xl.ZF_DL | xl.MISMATCH_FP32, 0, gram_true=dev(G))
+        s, st = s.cpu().numpy(), st.cpu().numpy()
+        ok = receiver_mask(st, st_ref, Gc, p, s2, 3)
+        rel = np.abs(s[ok] - s_ref[ok]) / np.maximum(np.abs(s_ref[ok]), 1e-300)
+        assert np.all(rel <= mzf_tol(Gc[ok], G[ok], p[ok], s2[ok], 3))
 
 
 def test_mc_step_downlink(xl):
