@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--source-hash", metavar="KERNEL", help="print the source hash a profile summary records, and exit")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the precision table, the ragged batch, the sweep and the surrogate")
+    ap.add_argument("--only", choices=["ragged", "appendix_a", "sweep", "surrogate", "ura"],
+                    help="run one extra section alone (no headline step) and print its JSON; for profiling")
+    ap.add_argument("--ragged-count", type=int, default=1 << 14, help="instances of the ragged section")
+    ap.add_argument("--no-ragged-tune", action="store_true", help="ragged section with the default tiling (no autotune)")
     return ap.parse_args()
 
 
@@ -116,9 +120,9 @@ def oracle_pipeline(oracle, wl, users):
     r, _ = oracle.sumrate(s)
     Gc = oracle.closed_form(wl.model, wl.n_ant, wl.wavelength, wl.spacing, 1.0, users)
     sm, _, _ = oracle.beamform(Gc, wl.power(B), wl.noise(B), oracle.ZF, oracle.POWER_RXSNR, gram_true=G)
-    oracle.sumrate(sm)
+    rm, _ = oracle.sumrate(sm)
     oracle.saturation(users, 0.9, wl.spacing)
-    return r, cap
+    return r, cap, rm
 
 
 def cpu_trials_per_s(oracle, wl, budget_s=12.0, max_trials=4096):
@@ -176,13 +180,15 @@ PROFILE_SOURCES = {
     "gram_f32_kernel": ["gram_simt.cu", "chan_gen.cuh", "common.cuh"],
     "gram_f64_kernel": ["gram_simt.cu", "chan_gen.cuh", "common.cuh"],
     "mlp_infer_tc_kernel": ["mlp_tc.cu", "mlp_common.cuh", "tc_common.cuh", "common.cuh"],
-    "gram_tc_ragged_kernel": ["batched.cu", "gram_engine.cuh", "gen_tc.cuh", "tc_common.cuh", "chan_gen.cuh",
+    "gram_hilo_kernel": ["bounds.cu", "gram_hilo_tc.cuh", "gen_tc.cuh", "tc_common.cuh", "chan_gen.cuh", "common.cuh"],
+    "gram_tc_items_kernel": ["batched.cu", "gram_engine.cuh", "gen_tc.cuh", "tc_common.cuh", "chan_gen.cuh",
                               "common.cuh"],
 }
 PROFILE_OF_KERNEL = {"gram_tc_kernel": "gram_tc_kernel_headline.md", "gram_f32_kernel": "gram_f32_kernel_headline.md",
                      "gram_f64_kernel": "gram_f64_kernel_headline.md",
                      "mlp_infer_tc_kernel": "mlp_infer_tc_kernel_surrogate.md",
-                     "gram_tc_ragged_kernel": "gram_tc_ragged_kernel_2048_instances.md"}
+                     "gram_tc_items_kernel": "gram_tc_items_kernel_ragged.md",
+                     "gram_hilo_kernel": "bounds_appendix_a.md"}
 
 
 def source_hash(kernel):
@@ -213,11 +219,10 @@ def traffic_from_profile(kernel, units=None):
     return float(u.group(1)) * units if (u and units) else None
 
 
-def ragged_bench(xl, torch, mufu_peak):
+def ragged_bench(xl, torch, mufu_peak, count=1 << 14, tune=True):
     """Ragged batch of 2^14 instances: N = round(2^U[10,17]), K ~ U{2..64},
     ZF or MMSE with probability 1/2, SNR ~ U[0, 30] dB, users as the headline
     geometry; autotuned plan, run captured in a CUDA graph and replayed."""
-    count = 1 << 14
     n, k, scheme, snr_db = inputs.ragged_instances(4, count)
     lam = inputs.wavelength(100e9)
     users = inputs.users_polar(4, 1, int(k.sum()), (3.0, 30.0))[0]
@@ -225,7 +230,7 @@ def ragged_bench(xl, torch, mufu_peak):
     U = torch.from_numpy(users).cuda()
     P = torch.from_numpy(np.ascontiguousarray(snr)).cuda()
     t0 = time.perf_counter()
-    plan = xl.BatchPlan(xl.array(1, lam), n, k, scheme, np.ones(count), prec=xl.BF16X3, tune_users=U)
+    plan = xl.BatchPlan(xl.array(1, lam), n, k, scheme, np.ones(count), prec=xl.BF16X3, tune_users=U if tune else None)
     plan_s = time.perf_counter() - t0
     out = dict(gram=torch.empty(plan.gram_total, dtype=torch.complex128, device="cuda"),
                sinr=torch.empty(plan.users_total, dtype=torch.float64, device="cuda"),
@@ -271,8 +276,8 @@ def ragged_bench(xl, torch, mufu_peak):
             "receivers_and_rates_ms": ms - gram_ms, "channel_entries": int(entries),
             "plan": info, "plan_seconds": plan_s, "cuda_graph": True, "gram": "bf16x3",
             "roofline": {"bound": "alu", "achieved": achieved, "peak": mufu_peak, "unit": "Tops/s (MUFU)",
-                         "frac": achieved / mufu_peak, "kernel": "gram_tc_ragged_kernel",
-                         "traffic": traffic_from_profile("gram_tc_ragged_kernel", entries),
+                         "frac": achieved / mufu_peak, "kernel": "gram_tc_items_kernel",
+                         "traffic": traffic_from_profile("gram_tc_items_kernel", entries),
                          "kernel_ms": gram_ms,
                          "algorithmic": "3 transcendental ops (rsqrt, sin, cos) x sum of N K channel entries",
                          "peak_source": "measured sin/cos MUFU throughput (xlmimo_measure_pipe), of measured"}}
@@ -353,13 +358,20 @@ def appendix_a_bench(xl, torch, max_mhz):
             flops = 8.0 * N * K * (K + 1) / 2 * B  # Gram complex MACs of the Hermitian half
             t_last = ms
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    peak = sms * 128 * 2 * max_mhz * 1e6 / 1e12  # FP32: 128 FMA lanes per SM per clock
+    peak64 = sms * 2 * 2 * max_mhz * 1e6 / 1e12  # FP64: 2 FMA lanes per SM per clock
+    Kp = (ks[-1] + 63) // 64 * 64
+    chol = 2 * B * 4.0 / 3.0 * Kp ** 3  # complex Cholesky of R and I + aR per trial, order Kp
     out["paper_value_at_k1000"] = 0.064
-    # the whole call against the FP32 peak of its Gram work (the Gram kernel is
-    # ~57 % of the call, the FP64 Cholesky ~32 %: profiles/bounds_appendix_a.md)
-    out["roofline"] = {"bound": "alu", "achieved": flops / (t_last / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s (FP32)",
-                       "frac": flops / (t_last / 1e3) / 1e12 / peak, "kernel": "whole xlmimo_capacity_bounds call at K = 1000",
-                       "algorithmic": "8 flop x N K(K+1)/2 Gram MACs per trial"}
+    # the whole call against its FP64 Cholesky work, 86 % of the call's kernel
+    # time in its ncu launch list; the tensor-core Gram is reported beside it
+    out["roofline"] = {"bound": "alu", "achieved": chol / (t_last / 1e3) / 1e12, "peak": peak64,
+                       "unit": "TFLOP/s (FP64)", "frac": chol / (t_last / 1e3) / 1e12 / peak64,
+                       "kernel": "whole xlmimo_capacity_bounds call at K = 1000 (FP64 blocked Cholesky: 86 % of it)",
+                       "algorithmic": "4/3 Kp^3 flop per complex Cholesky, 2 per trial (Kp = 1024)",
+                       "peak_source": f"FP64 FMA unit counts: {sms} SMs x 2 lanes x 2 flop x {max_mhz:.0f} MHz",
+                       "gram": {"kernel": "gram_hilo_kernel", "algorithmic_tflop": flops / 1e12,
+                                "issued_bf16_tflop": 3 * 2 * 128 * 128 * 40000 * (2 * Kp // 128) * (2 * Kp // 128 + 1) / 2
+                                * B / 1e12, "traffic": traffic_from_profile("gram_hilo_kernel")}}
     return out
 
 
@@ -526,6 +538,20 @@ def main():
     from paper_2503_18118_gb300 import mc
     from paper_2503_18118_gb300 import xlmimo as xl
 
+    if args.only:
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        xl.lib()
+        peaks = {}
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        mufu = xl.xlmimo_measure_pipe(xl.PIPE_SINCOS)[0] / 1e12
+        run = {"ragged": lambda: ragged_bench(xl, torch, mufu, args.ragged_count, not args.no_ragged_tune),
+               "appendix_a": lambda: appendix_a_bench(xl, torch, float(peaks.get("sm_max_mhz", 2070.0))),
+               "sweep": lambda: sweep_bench(xl, torch), "surrogate": lambda: surrogate_bench(xl, torch, peaks),
+               "ura": lambda: ura_bench(xl, torch)}[args.only]
+        print(json.dumps({"section": args.only, "result": run()}), flush=True)
+        return
+
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -642,9 +668,11 @@ def main():
     idx = np.unique(np.linspace(0, B - 1, 64).astype(int))  # 64 trials spread over the batch
     step(prec)
     torch.cuda.synchronize()
-    r_ref, _ = oracle_pipeline(oracle, wl, users_h[idx])
+    r_ref, _, rc_ref = oracle_pipeline(oracle, wl, users_h[idx])
     r_gpu = out.rate.cpu().numpy()[idx]
     sumrate_rel_err = float(np.max(np.abs(r_gpu - r_ref) / np.abs(r_ref)))
+    rc_gpu = out.rate_cf.cpu().numpy()[idx]
+    sumrate_rel_err_cf = float(np.max(np.abs(rc_gpu - rc_ref) / np.abs(rc_ref)))
 
     # precision study on the same workload: every Gram arithmetic, same step,
     # sum-rate error on the sampled trials against the oracle
@@ -733,9 +761,11 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": path, "data": "synthetic",
         "config": {"workload": wl.name, "n_ant": N, "users": K, "trials_per_step": B, "freq_ghz": wl.freq_hz / 1e9,
-                   "scheme": "mmse+modified_zf", "gram_path": path, "solve": "f64 cholesky",
+                   "scheme": "mmse+modified_zf", "gram_path": path,
+                   "solve": "mmse: f64 cholesky; modified zf: double-float cholesky, fp32 correction M(G-Gc)",
                    "l2": "flushed between timed steps (256 MB write)"},
         "sumrate_rel_err": sumrate_rel_err,
+        "sumrate_rel_err_modified_zf": sumrate_rel_err_cf,
         "fp64_baseline": fp64,
         "precisions": paths,
         "ragged": ragged,
