@@ -479,7 +479,10 @@ int xlmimo_batch_plan_destroy(xlmimo_batch_plan plan);
  * Numerics (training and inference alike): the first (6 -> 256) and last
  * (256 -> 2) layers in FP32; the three 256 x 256 layers multiply BF16-rounded
  * (round to nearest even) inputs by BF16-rounded weights with FP32
- * accumulation.  Gradients pass through the rounding unchanged.  Inference
+ * accumulation.  Gradients pass through the rounding unchanged.  Training
+ * runs the three 256 x 256 layers on the tensor cores (forward, input and
+ * weight gradients; the FP32 gradient enters as a BF16 hi/lo pair, within
+ * 2^-16 of each FP32 product) and the other two on FP32 SIMT.  Inference
  * runs every layer but the last on the tensor cores (the first with a BF16
  * hi/lo split of features and weights, which keeps it to ~2^-16 of FP32) and
  * evaluates SiLU as z/2 (1 + tanh(z/2)) with the FP32 hardware tanh
@@ -506,7 +509,9 @@ int xlmimo_pair_features(const xlmimo_array* arr, const double* users, int K, in
                          const double* gram_cf, float* feat, float* target, float* weight, void* stream);
 
 /* Forward pass over M rows: x [M][6] -> out [M][2].  cache is NULL or
- * [M * XLMIMO_MLP_CACHE_PER_ROW] floats (needed by xlmimo_mlp_backward). */
+ * [M * XLMIMO_MLP_CACHE_PER_ROW] floats (needed by xlmimo_mlp_backward).
+ * Allocates 786,432 bytes of stream-ordered workspace (the packed weights of
+ * the 256 x 256 layers), plus 2 * M * 256 floats when cache is NULL. */
 int xlmimo_mlp_forward(const float* params, const float* x, int M, float* out, float* cache, void* stream);
 
 /* Loss 0.5/M * sum_m w_m |out_m - target_m|^2 into *loss (device float) and
@@ -514,7 +519,8 @@ int xlmimo_mlp_forward(const float* params, const float* x, int M, float* out, f
 int xlmimo_mlp_loss(const float* out, const float* target, const float* weight, int M, float* dout, float* loss,
                     void* stream);
 
-/* Floats of device workspace xlmimo_mlp_backward needs for M rows. */
+/* Floats of device workspace xlmimo_mlp_backward and xlmimo_mlp_train_step
+ * need for M rows (the buffer 16-byte aligned). */
 int64_t xlmimo_mlp_work_floats(int M);
 
 /* Backward pass: grad [XLMIMO_MLP_PARAMS] (overwritten) of the loss whose

@@ -2,13 +2,15 @@
 // forward and backward passes, loss, Adam, and the BF16 packing of the
 // inference image.
 //
-// The training GEMMs are FP32 SIMT tiles (64 x 64 outputs, 16-deep K steps,
-// 4 x 4 outputs per thread) with fused epilogues: bias + SiLU in the forward
-// pass, the SiLU derivative in the backward pass.  Weight gradients contract
-// over the batch, split into slices whose partial sums are added in slice
-// order by a second kernel, so results do not depend on scheduling.  The
-// three 256 x 256 layers round their operands to BF16 on load (the network's
-// stated numerics); the backward pass reuses the rounded values.
+// The three 256 x 256 layers run on the tensor cores (mlp_train_tc.cu:
+// BF16-rounded operands, the network's stated numerics, with the FP32
+// gradient as a BF16 hi/lo pair); the 6 -> 256 and 256 -> 2 layers are FP32
+// SIMT tiles here (64 x 64 outputs, 16-deep K steps, 4 x 4 outputs per
+// thread).  Both have fused epilogues: bias + SiLU in the forward pass, the
+// SiLU derivative in the backward pass.  Weight gradients contract over the
+// batch, split into slices whose partial sums are added in slice order by a
+// second kernel, so results do not depend on scheduling; the backward pass
+// reuses the rounded values of the forward pass.
 #include <math.h>
 
 #include "aperture.cuh"
@@ -38,11 +40,6 @@ struct GemmArgs {
     const float* zprev;  // EPI_DSILU: pre-activation of the layer below
 };
 
-__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + expf(-z)); }
-__device__ __forceinline__ float silu_grad_f(float z) {
-    const float s = 1.0f / (1.0f + expf(-z));
-    return s * (1.0f + z * (1.0f - s));
-}
 
 template <bool AT, bool BT, bool QA, bool QB, int EPI>
 __global__ void __launch_bounds__(GTHREADS) mlp_gemm_kernel(GemmArgs a) {
@@ -260,9 +257,10 @@ static inline float* cache_h(float* cache, int l, int M) { return cache + (int64
 
 static int dw_slices(int M) { return (M + DW_SLICE - 1) / DW_SLICE; }
 
-// forward; with cache == NULL the hidden activations go to `tmp` ([2][M][256])
+// forward; with cache == NULL the hidden activations go to `tmp` ([2][M][256]);
+// wpk: the packed weights of the 256 x 256 layers (mlp_tc_pack)
 static int mlp_forward_impl(const float* params, const float* x, int M, float* out, float* cache, float* tmp,
-                            cudaStream_t st) {
+                            const unsigned char* wpk, cudaStream_t st) {
     int rc = XLMIMO_OK;
     const float* h = x;
     for (int l = 0; l < MLP_LAYERS && !rc; ++l) {
@@ -284,7 +282,7 @@ static int mlp_forward_impl(const float* params, const float* x, int M, float* o
             a.Z = cache ? cache_z(cache, l, M) : nullptr;
             a.C = cache ? cache_h(cache, l, M) : tmp + (int64_t)(l & 1) * M * MLP_W;
             if (l == 0) rc = gemm<false, false, false, false, EPI_HIDDEN>(a, 1, st);
-            else rc = gemm<false, false, true, true, EPI_HIDDEN>(a, 1, st);
+            else rc = mlp_tc_forward(h, wpk, l, a.bias, a.Z, a.C, M, st);
             h = a.C;
         }
     }
@@ -292,7 +290,7 @@ static int mlp_forward_impl(const float* params, const float* x, int M, float* o
 }
 
 static int mlp_backward_impl(const float* params, const float* x, const float* cache, const float* dout, int M,
-                             float* grad, float* work, cudaStream_t st) {
+                             float* grad, float* work, const unsigned char* wpk, cudaStream_t st) {
     float* dz[2] = {work, work + (int64_t)M * MLP_W};
     float* part = work + 2LL * M * MLP_W;
     const int S = dw_slices(M);
@@ -314,7 +312,7 @@ static int mlp_backward_impl(const float* params, const float* x, const float* c
         a.k_slice = DW_SLICE;
         a.C = part;
         const bool q = (l >= 1 && l <= 3);
-        rc = q ? gemm<true, false, true, false, EPI_PARTIAL>(a, S, st)
+        rc = q ? mlp_tc_weight_grad(hin, g, M, DW_SLICE, part, st)
                : gemm<true, false, false, false, EPI_PARTIAL>(a, S, st);
         if (rc) break;
         const int64_t n = (int64_t)(in + 1) * outd;
@@ -334,7 +332,7 @@ static int mlp_backward_impl(const float* params, const float* x, const float* c
         d.C = dz[l & 1];
         d.ldc = in;
         d.zprev = cache_z(const_cast<float*>(cache), l - 1, M);
-        rc = q ? gemm<false, true, false, true, EPI_DSILU>(d, 1, st)
+        rc = q ? mlp_tc_input_grad(g, wpk, l, d.zprev, d.C, M, st)
                : gemm<false, true, false, false, EPI_DSILU>(d, 1, st);
         g = d.C;
     }
@@ -377,13 +375,15 @@ int xlmimo_mlp_forward(const float* params, const float* x, int M, float* out, f
     if (rc || M == 0) return rc;
     if (!params || !x || !out) { set_error("params, x and out must be non-NULL"); return XLMIMO_EINVAL; }
     float* tmp = nullptr;
+    unsigned char* wpk = nullptr;
     cudaStream_t st = as_stream(stream);
-    if (!cache) {
+    rc = cuda_status(cudaMallocAsync((void**)&wpk, (size_t)MT_PACK_BYTES, st), "forward workspace");
+    if (!rc && !cache)
         rc = cuda_status(cudaMallocAsync((void**)&tmp, sizeof(float) * 2 * (size_t)M * MLP_W, st), "forward workspace");
-        if (rc) return rc;
-    }
-    rc = mlp_forward_impl(params, x, M, out, cache, tmp, st);
+    if (!rc) rc = mlp_tc_pack(params, wpk, st);
+    if (!rc) rc = mlp_forward_impl(params, x, M, out, cache, tmp, wpk, st);
     if (tmp) cudaFreeAsync(tmp, st);
+    if (wpk) cudaFreeAsync(wpk, st);
     return rc;
 }
 
@@ -398,9 +398,13 @@ int xlmimo_mlp_loss(const float* out, const float* target, const float* weight, 
     return cuda_status(cudaGetLastError(), "mlp loss launch");
 }
 
+// workspace: dZ [2][M][256], weight-gradient partials [S][257][256], packed
+// weights of the 256 x 256 layers (MT_PACK_BYTES)
+static int64_t work_pack_off(int M) { return 2LL * M * MLP_W + (int64_t)dw_slices(M) * (MLP_W + 1) * MLP_W; }
+
 int64_t xlmimo_mlp_work_floats(int M) {
     if (M <= 0) return 0;
-    return 2LL * M * MLP_W + (int64_t)dw_slices(M) * (MLP_W + 1) * MLP_W;
+    return work_pack_off(M) + MT_PACK_BYTES / 4;
 }
 
 int xlmimo_mlp_backward(const float* params, const float* x, const float* cache, const float* dout, int M,
@@ -411,7 +415,11 @@ int xlmimo_mlp_backward(const float* params, const float* x, const float* cache,
     if (!params || !grad) { set_error("params and grad must be non-NULL"); return XLMIMO_EINVAL; }
     if (M == 0) return cuda_status(cudaMemsetAsync(grad, 0, sizeof(float) * XLMIMO_MLP_PARAMS, as_stream(stream)), "grad clear");
     if (!x || !cache || !dout || !work) { set_error("x, cache, dout and work must be non-NULL"); return XLMIMO_EINVAL; }
-    return mlp_backward_impl(params, x, cache, dout, M, grad, work, as_stream(stream));
+    if (((uintptr_t)work & 15u) != 0) { set_error("work must be 16-byte aligned"); return XLMIMO_EINVAL; }
+    cudaStream_t st = as_stream(stream);
+    unsigned char* wpk = reinterpret_cast<unsigned char*>(work + work_pack_off(M));
+    rc = mlp_tc_pack(params, wpk, st);
+    return rc ? rc : mlp_backward_impl(params, x, cache, dout, M, grad, work, wpk, st);
 }
 
 int xlmimo_mlp_adam(float* params, float* m, float* v, const float* grad, int64_t step, double lr, double beta1,
@@ -441,15 +449,18 @@ int xlmimo_mlp_train_step(float* params, float* m, float* v, float* grad, int64_
         set_error("params, m, v, grad, x, target, out, cache and work must be non-NULL");
         return XLMIMO_EINVAL;
     }
+    if (((uintptr_t)work & 15u) != 0) { set_error("work must be 16-byte aligned"); return XLMIMO_EINVAL; }
     cudaStream_t st = as_stream(stream);
     // the output gradient reuses the head of the workspace's second slab
     float* dout = work + (int64_t)M * MLP_W;
-    rc = mlp_forward_impl(params, x, M, out, cache, nullptr, st);
+    unsigned char* wpk = reinterpret_cast<unsigned char*>(work + work_pack_off(M));
+    rc = mlp_tc_pack(params, wpk, st);
+    if (!rc) rc = mlp_forward_impl(params, x, M, out, cache, nullptr, wpk, st);
     if (!rc) {
         mlp_loss_kernel<<<1, 1024, 0, st>>>((const float2*)out, (const float2*)target, weight, M, (float2*)dout, loss);
         rc = cuda_status(cudaGetLastError(), "mlp loss launch");
     }
-    if (!rc) rc = mlp_backward_impl(params, x, cache, dout, M, grad, work, st);
+    if (!rc) rc = mlp_backward_impl(params, x, cache, dout, M, grad, work, wpk, st);
     if (!rc) rc = xlmimo_mlp_adam(params, m, v, grad, step, lr, 0.9, 0.999, 1e-8, stream);
     return rc;
 }

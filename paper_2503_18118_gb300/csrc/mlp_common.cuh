@@ -92,4 +92,31 @@ __device__ __forceinline__ void pair_features_dev(const FeatConst& fc, double xi
 
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
+// SiLU and its derivative as the training kernels evaluate them (FP32).
+__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + expf(-z)); }
+__device__ __forceinline__ float silu_grad_f(float z) {
+    const float s = 1.0f / (1.0f + expf(-z));
+    return s * (1.0f + z * (1.0f - s));
+}
+
+// ---- tensor-core training GEMMs of the three 256 x 256 layers (mlp_train_tc.cu)
+// Packed weights of one layer: the forward operand (output unit = row,
+// input = K) then the input-gradient operand (input unit = row, output = K),
+// each 4 tiles of 256 rows x 64 K (BF16, 128-byte swizzle, 32 KB).
+constexpr int MT_B_TILE_BYTES = 256 * 64 * 2;
+constexpr int64_t MT_PACK_LAYER_BYTES = 2LL * 4 * MT_B_TILE_BYTES;
+constexpr int64_t MT_PACK_BYTES = 3 * MT_PACK_LAYER_BYTES;  // layers 1..3
+// round(W_l) of layers 1..3 into `wpk` (MT_PACK_BYTES, 16-byte aligned).
+int mlp_tc_pack(const float* params, unsigned char* wpk, cudaStream_t st);
+// Z = round(H) round(W_l) + b, C = silu(Z) (Z may be NULL): H, Z, C [M][256].
+int mlp_tc_forward(const float* h, const unsigned char* wpk, int l, const float* bias, float* z, float* c, int M,
+                   cudaStream_t st);
+// dZ = (G round(W_l)^T) silu'(Z_below): G, Z_below, dZ [M][256].
+int mlp_tc_input_grad(const float* g, const unsigned char* wpk, int l, const float* zprev, float* dz, int M,
+                      cudaStream_t st);
+// part[s][0..255][256] = round(H_s)^T G_s and part[s][256][256] = the column
+// sums of G_s, for slices s of k_slice rows (a multiple of 64): the weight and
+// bias gradient partials of a 256 x 256 layer, rows of `part` 257 per slice.
+int mlp_tc_weight_grad(const float* h, const float* g, int M, int k_slice, float* part, cudaStream_t st);
+
 }  // namespace xl
