@@ -54,6 +54,8 @@ def parse():
                     help="run one extra section alone (no headline step) and print its JSON; for profiling")
     ap.add_argument("--ragged-count", type=int, default=1 << 14, help="instances of the ragged section")
     ap.add_argument("--no-ragged-tune", action="store_true", help="ragged section with the default tiling (no autotune)")
+    ap.add_argument("--surrogate-train-steps", type=int, default=None,
+                    help="Adam steps of the surrogate section (default: the workload's 8000)")
     return ap.parse_args()
 
 
@@ -212,10 +214,10 @@ def traffic_from_profile(kernel, units=None):
     m = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
     if not m or m.group(1) != source_hash(kernel):
         return None
-    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+-]+)", text)
     if t:
         return float(t.group(1))
-    u = re.search(r"dram_bytes_per_unit:\s*([0-9.eE+]+)", text)
+    u = re.search(r"dram_bytes_per_unit:\s*([0-9.eE+-]+)", text)
     return float(u.group(1)) * units if (u and units) else None
 
 
@@ -432,7 +434,7 @@ def ura_bench(xl, torch):
     return out
 
 
-def surrogate_bench(xl, torch, peaks):
+def surrogate_bench(xl, torch, peaks, train_steps=None):
     """Learned correlation surrogate: labels from the exact kernel, training on
     the GPU, then the fused tensor-core inference timed at 100 GHz, N = 2^18,
     K = 64, 10^4 trials, and judged against the exact Gram and the closed form
@@ -451,7 +453,8 @@ def surrogate_bench(xl, torch, peaks):
     params = torch.from_numpy(inputs.mlp_init_params(ex["train_seed"])).cuda()
     tr = surrogate.Trainer(params, batch=ex["batch"], lr=ex["lr"], seed=ex["train_seed"])
     t0 = time.perf_counter()
-    log = tr.fit(feat, target, steps=ex["steps"], log_every=ex["steps"] // 4)
+    steps = train_steps or ex["steps"]
+    log = tr.fit(feat, target, steps=steps, log_every=max(1, steps // 4))
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     del feat, target
@@ -501,7 +504,7 @@ def surrogate_bench(xl, torch, peaks):
     e_gram = {names[k]: float(np.mean(res["gram_err_" + k])) for k in rows}
     return {
         "workload": f"{wl.name}: 100 GHz, N=2^18, K=64, 10^4 trials, r in [3,30] m",
-        "training": {"pairs": int(n.size * K * (K - 1) // 2), "label_s": label_s, "steps": ex["steps"],
+        "training": {"pairs": int(n.size * K * (K - 1) // 2), "label_s": label_s, "steps": steps,
                      "batch": ex["batch"], "train_s": train_s, "loss": [float(l) for _, l in log],
                      "labels": "exact Gram (bf16x3), N log-uniform [2^10, 2^18], 28/100 GHz"},
         "base": "closed form x finite-aperture Fresnel factor" if ex["base"] == 2 else ex["base"],
@@ -547,7 +550,8 @@ def main():
         mufu = xl.xlmimo_measure_pipe(xl.PIPE_SINCOS)[0] / 1e12
         run = {"ragged": lambda: ragged_bench(xl, torch, mufu, args.ragged_count, not args.no_ragged_tune),
                "appendix_a": lambda: appendix_a_bench(xl, torch, float(peaks.get("sm_max_mhz", 2070.0))),
-               "sweep": lambda: sweep_bench(xl, torch), "surrogate": lambda: surrogate_bench(xl, torch, peaks),
+               "sweep": lambda: sweep_bench(xl, torch),
+               "surrogate": lambda: surrogate_bench(xl, torch, peaks, args.surrogate_train_steps),
                "ura": lambda: ura_bench(xl, torch)}[args.only]
         print(json.dumps({"section": args.only, "result": run()}), flush=True)
         return
