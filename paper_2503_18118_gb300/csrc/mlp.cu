@@ -256,6 +256,7 @@ static inline float* cache_z(float* cache, int l, int M) { return cache + (int64
 static inline float* cache_h(float* cache, int l, int M) { return cache + (int64_t)(2 * l + 1) * M * MLP_W; }
 
 static int dw_slices(int M) { return (M + DW_SLICE - 1) / DW_SLICE; }
+static int dw_slices_tc(int M) { return (M + MT_DW_SLICE - 1) / MT_DW_SLICE; }  // >= dw_slices(M)
 
 // forward; with cache == NULL the hidden activations go to `tmp` ([2][M][256]);
 // wpk: the packed weights of the 256 x 256 layers (mlp_tc_pack)
@@ -312,11 +313,11 @@ static int mlp_backward_impl(const float* params, const float* x, const float* c
         a.k_slice = DW_SLICE;
         a.C = part;
         const bool q = (l >= 1 && l <= 3);
-        rc = q ? mlp_tc_weight_grad(hin, g, M, DW_SLICE, part, st)
+        rc = q ? mlp_tc_weight_grad(hin, g, M, MT_DW_SLICE, part, st)
                : gemm<true, false, false, false, EPI_PARTIAL>(a, S, st);
         if (rc) break;
         const int64_t n = (int64_t)(in + 1) * outd;
-        sum_slices_kernel<<<grid_for(n, 256), 256, 0, st>>>(part, S, n, grad + mlp_off(l));
+        sum_slices_kernel<<<grid_for(n, 256), 256, 0, st>>>(part, q ? dw_slices_tc(M) : S, n, grad + mlp_off(l));
         rc = cuda_status(cudaGetLastError(), "mlp gradient reduce");
         if (rc || l == 0) break;
         // input gradient through W (rounded as in the forward pass) and SiLU'
@@ -398,9 +399,11 @@ int xlmimo_mlp_loss(const float* out, const float* target, const float* weight, 
     return cuda_status(cudaGetLastError(), "mlp loss launch");
 }
 
-// workspace: dZ [2][M][256], weight-gradient partials [S][257][256], packed
+// workspace: dZ [2][M][256], weight-gradient partials [S][257][256] (S for
+// the 256-row slices of the tensor-core layers, which the FP32 layers' 512-row
+// slices fit in), packed
 // weights of the 256 x 256 layers (MT_PACK_BYTES)
-static int64_t work_pack_off(int M) { return 2LL * M * MLP_W + (int64_t)dw_slices(M) * (MLP_W + 1) * MLP_W; }
+static int64_t work_pack_off(int M) { return 2LL * M * MLP_W + (int64_t)dw_slices_tc(M) * (MLP_W + 1) * MLP_W; }
 
 int64_t xlmimo_mlp_work_floats(int M) {
     if (M <= 0) return 0;

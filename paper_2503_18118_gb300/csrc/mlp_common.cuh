@@ -117,6 +117,7 @@ int mlp_tc_input_grad(const float* g, const unsigned char* wpk, int l, const flo
 // part[s][0..255][256] = round(H_s)^T G_s and part[s][256][256] = the column
 // sums of G_s, for slices s of k_slice rows (a multiple of 64): the weight and
 // bias gradient partials of a 256 x 256 layer, rows of `part` 257 per slice.
+constexpr int MT_DW_SLICE = 256;  // batch rows per weight-gradient slice of these layers
 int mlp_tc_weight_grad(const float* h, const float* g, int M, int k_slice, float* part, cudaStream_t st);
 
 }  // namespace xl

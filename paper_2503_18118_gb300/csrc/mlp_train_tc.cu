@@ -10,7 +10,8 @@
 // one.  The FP32 accumulator in TMEM rounds partial sums towards zero, over
 // at most 64 steps here (K = 512 in 16-element steps of two MMAs): below
 // 64 x 2^-23 ~ 8e-6 of the sum of magnitudes.
-// One CTA per 128 x 256 output tile (M = 128, N = 256 MMAs): warps 0-3 turn
+// One CTA per 128 x 128 output tile (M = N = 128 MMAs; 2-3 CTAs per SM, the
+// operand loads being latency-bound): warps 0-3 turn
 // FP32 operands into BF16 tiles (K-major, 128-byte swizzle) in a two-stage
 // ring of 64 contraction elements per stage; the weight operand comes
 // pre-packed (mlp_tc_pack) by a bulk copy; warp 4 owns 256 TMEM columns and
@@ -25,7 +26,8 @@
 namespace xl {
 
 constexpr int MT_ROWS = 128;                       // output rows per CTA (the MMA's M)
-constexpr int MT_COLS = 256;                       // output columns per CTA (the MMA's N)
+constexpr int MT_COLS = 128;                       // output columns per CTA (the MMA's N)
+constexpr int MT_BH_BYTES = MT_COLS * 64 * 2;      // 16 KB: half of a packed weight tile
 constexpr int MT_BK = 64;                          // contraction elements per stage
 constexpr int MT_A_BYTES = MT_ROWS * MT_BK * 2;    // 16 KB
 constexpr int MT_STAGES = 2;
@@ -37,7 +39,7 @@ template <int MODE>
 struct MtCfg {
     static constexpr int A_TERMS = MODE == MT_DX ? 2 : 1;  // BF16 terms of the A operand
     static constexpr int B_TERMS = MODE == MT_DW ? 2 : 1;
-    static constexpr int STAGE = A_TERMS * MT_A_BYTES + B_TERMS * MT_B_TILE_BYTES;
+    static constexpr int STAGE = A_TERMS * MT_A_BYTES + B_TERMS * MT_BH_BYTES;
     static constexpr bool B_BULK = MODE != MT_DW;  // B: packed weight tiles
     static constexpr int SMEM = 1024 + MT_STAGES * STAGE + 128;
 };
@@ -141,13 +143,15 @@ __device__ __forceinline__ void load_cols(const float* __restrict__ X, int f0, i
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(MT_THREADS, 1) mlp_gemm_tc_kernel(MtArgs a) {
+__global__ void __launch_bounds__(MT_THREADS, 2) mlp_gemm_tc_kernel(MtArgs a) {
     using C = MtCfg<MODE>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     MtShared* sh = reinterpret_cast<MtShared*>(base + MT_STAGES * C::STAGE);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row0 = blockIdx.x * MT_ROWS;  // FWD / DX: batch rows; DW: input features
+    const int nh = MODE == MT_DW ? blockIdx.z : blockIdx.y;  // output columns nh * 128 ..
+    const int col0 = nh * MT_COLS;
     const int k0 = MODE == MT_DW ? blockIdx.y * a.k_slice : 0;
     const int kend = MODE == MT_DW ? min(a.M, k0 + a.k_slice) : MLP_W;
     const int nst = (kend - k0 + MT_BK - 1) / MT_BK;
@@ -179,7 +183,7 @@ __global__ void __launch_bounds__(MT_THREADS, 1) mlp_gemm_tc_kernel(MtArgs a) {
     if (warp < 4) {
         // ---------------- operands
         int issued = 0;
-        float csum0 = 0.f, csum1 = 0.f;  // DW, first row tile: column sums of G (the bias gradient)
+        float csum0 = 0.f;  // DW, first row tile: column sums of G (the bias gradient)
         for (int s = 0; s < nst; ++s) {
             const int slot = s % MT_STAGES;
             if (s >= MT_STAGES && !mbar_wait(&sh->empty[slot], (uint32_t)((s / MT_STAGES - 1) & 1), abort)) break;
@@ -187,12 +191,13 @@ __global__ void __launch_bounds__(MT_THREADS, 1) mlp_gemm_tc_kernel(MtArgs a) {
             const int kb = k0 + s * MT_BK;
             if (C::B_BULK && tid == 0) {
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&sh->wtx[slot])),
-                             "r"(MT_B_TILE_BYTES)
+                             "r"(MT_BH_BYTES)
                              : "memory");
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                         sbase + (uint32_t)(slot * C::STAGE + C::A_TERMS * MT_A_BYTES)),
-                    "l"(a.wpk + (int64_t)s * MT_B_TILE_BYTES), "r"(MT_B_TILE_BYTES), "r"(smem_u32(&sh->wtx[slot]))
+                    "l"(a.wpk + (int64_t)s * MT_B_TILE_BYTES + nh * MT_BH_BYTES), "r"(MT_BH_BYTES),
+                    "r"(smem_u32(&sh->wtx[slot]))
                     : "memory");
                 ++issued;
             }
@@ -203,17 +208,14 @@ __global__ void __launch_bounds__(MT_THREADS, 1) mlp_gemm_tc_kernel(MtArgs a) {
             } else {
                 unsigned char* bt = st + MT_A_BYTES;
                 load_cols<false>(a.a, row0, kb, kend, tid, st, nullptr, nullptr);
-                load_cols<true>(a.b, 0, kb, kend, tid, bt, bt + MT_B_TILE_BYTES, row0 == 0 ? &csum0 : nullptr);
-                load_cols<true>(a.b, 128, kb, kend, tid, bt + 128 * 128, bt + MT_B_TILE_BYTES + 128 * 128,
-                                row0 == 0 ? &csum1 : nullptr);
+                load_cols<true>(a.b, col0, kb, kend, tid, bt, bt + MT_BH_BYTES, row0 == 0 ? &csum0 : nullptr);
             }
             fence_async_smem();
             mbar_arrive(&sh->full[slot]);
         }
         if (MODE == MT_DW && row0 == 0) {
             float* bias_row = a.c + ((int64_t)blockIdx.y * (MLP_W + 1) + MLP_W) * MLP_W;
-            bias_row[tid] = csum0;
-            bias_row[128 + tid] = csum1;
+            bias_row[col0 + tid] = csum0;
         }
         // no bulk copy may still be landing when the CTA exits
         if (C::B_BULK && tid == 0)
@@ -232,9 +234,9 @@ __global__ void __launch_bounds__(MT_THREADS, 1) mlp_gemm_tc_kernel(MtArgs a) {
         const float nanv = __int_as_float(0x7fc00000);
         float* out;
         if (MODE == MT_DW)
-            out = a.c + ((int64_t)blockIdx.y * (MLP_W + 1) + row0 + r) * MLP_W;
+            out = a.c + ((int64_t)blockIdx.y * (MLP_W + 1) + row0 + r) * MLP_W + col0;
         else
-            out = a.c + (int64_t)(row0 + r) * MLP_W;
+            out = a.c + (int64_t)(row0 + r) * MLP_W + col0;
         const bool live = MODE == MT_DW || row0 + r < a.M;
 #pragma unroll 1
         for (int c0 = 0; c0 < MT_COLS; c0 += 16) {
@@ -249,17 +251,17 @@ __global__ void __launch_bounds__(MT_THREADS, 1) mlp_gemm_tc_kernel(MtArgs a) {
                 float zz[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    zz[j] = v[j] + a.bias[c0 + j];
+                    zz[j] = v[j] + a.bias[col0 + c0 + j];
                     v[j] = silu_f(zz[j]);
                 }
                 if (a.z) {
-                    float* zr = a.z + (int64_t)(row0 + r) * MLP_W + c0;
+                    float* zr = a.z + (int64_t)(row0 + r) * MLP_W + col0 + c0;
 #pragma unroll
                     for (int j = 0; j < 16; j += 4)
                         *reinterpret_cast<float4*>(zr + j) = make_float4(zz[j], zz[j + 1], zz[j + 2], zz[j + 3]);
                 }
             } else if (MODE == MT_DX) {
-                const float* zp = a.zprev + (int64_t)(row0 + r) * MLP_W + c0;
+                const float* zp = a.zprev + (int64_t)(row0 + r) * MLP_W + col0 + c0;
 #pragma unroll
                 for (int j = 0; j < 16; j += 4) {
                     const float4 q = *reinterpret_cast<const float4*>(zp + j);
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(MT_THREADS, 1) mlp_gemm_tc_kernel(MtArgs a) {
                 const uint64_t da = desc_sw128(st + kk * 32), db = desc_sw128(bt + kk * 32);
                 umma(tmem, da, db, idesc, first);
                 if (C::A_TERMS == 2) umma(tmem, desc_sw128(st + MT_A_BYTES + kk * 32), db, idesc, 1u);
-                if (C::B_TERMS == 2) umma(tmem, da, desc_sw128(bt + MT_B_TILE_BYTES + kk * 32), idesc, 1u);
+                if (C::B_TERMS == 2) umma(tmem, da, desc_sw128(bt + MT_BH_BYTES + kk * 32), idesc, 1u);
             }
             umma_commit(&sh->empty[slot]);
         }
@@ -348,7 +350,7 @@ int mlp_tc_forward(const float* h, const unsigned char* wpk, int l, const float*
     a.z = z;
     a.c = c;
     a.M = M;
-    return launch_mt<MT_FWD>(a, dim3((unsigned)((M + MT_ROWS - 1) / MT_ROWS)), st);
+    return launch_mt<MT_FWD>(a, dim3((unsigned)((M + MT_ROWS - 1) / MT_ROWS), MLP_W / MT_COLS), st);
 }
 
 int mlp_tc_input_grad(const float* g, const unsigned char* wpk, int l, const float* zprev, float* dz, int M,
@@ -359,7 +361,7 @@ int mlp_tc_input_grad(const float* g, const unsigned char* wpk, int l, const flo
     a.zprev = zprev;
     a.c = dz;
     a.M = M;
-    return launch_mt<MT_DX>(a, dim3((unsigned)((M + MT_ROWS - 1) / MT_ROWS)), st);
+    return launch_mt<MT_DX>(a, dim3((unsigned)((M + MT_ROWS - 1) / MT_ROWS), MLP_W / MT_COLS), st);
 }
 
 int mlp_tc_weight_grad(const float* h, const float* g, int M, int k_slice, float* part, cudaStream_t st) {
@@ -370,7 +372,7 @@ int mlp_tc_weight_grad(const float* h, const float* g, int M, int k_slice, float
     a.c = part;
     a.M = M;
     a.k_slice = k_slice;
-    return launch_mt<MT_DW>(a, dim3(2, (unsigned)S), st);
+    return launch_mt<MT_DW>(a, dim3(2, (unsigned)S, MLP_W / MT_COLS), st);
 }
 
 }  // namespace xl

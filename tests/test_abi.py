@@ -117,8 +117,8 @@ def test_surrogate_entries_validate_on_host(xl):
                                    dummy, None, None) == 1
     # workspace: two [M][256] slabs plus one [257][256] partial per 512 rows
     assert L.xlmimo_mlp_work_floats(0) == 0
-    # dZ slabs, two weight-gradient slices, the packed BF16 weights of the three 256 x 256 layers
-    assert L.xlmimo_mlp_work_floats(1000) == 2 * 1000 * 256 + 2 * 257 * 256 + 3 * 2 * 4 * 256 * 64 * 2 // 4
+    # dZ slabs, four 256-row weight-gradient slices, the packed BF16 weights of the three 256 x 256 layers
+    assert L.xlmimo_mlp_work_floats(1000) == 2 * 1000 * 256 + 4 * 257 * 256 + 3 * 2 * 4 * 256 * 64 * 2 // 4
 
 
 def test_capacity_bounds_validates_on_host(xl):
