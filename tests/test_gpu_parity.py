@@ -282,6 +282,38 @@ def test_beamform_modified_zf(xl, orc, K, scheme):
         assert np.all(rel <= mzf_tol(Gc[ok], G[ok], p[ok], s2[ok], scheme))
 
 
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_beamform_mismatched_ill_conditioned_filter(xl, orc, scheme):
+    """The mismatched receivers factor their filter matrix in double-float and
+    hand it to the FP64 Cholesky when a pivot falls below 2^-16 of its
+    diagonal entry (closely spaced users).  Trial 0 has two users 50 um
+    apart (pivot ratio ~1e-6: the FP64 path), trial 1 a well-separated set
+    (ratio ~2e-3: the double-float path); the true channel is the same users
+    moved by 1 mm.  Both against the oracle at the mismatched receivers'
+    tolerance, and the FP32-correction form within its bound."""
+    N, K = 256, 6
+    base = np.array([[10.0, 0.0], [10.0, 5e-5], [12.0, 3.0], [8.0, -2.5], [15.0, 6.0], [20.0, -9.0]])
+    users_f = np.stack([base, base + np.array([[0, 0], [0, 2e-3], [0.01, 0], [0, 0], [0, 0.02], [0, 0]])])
+    users_t = users_f + np.array([[0.0, 1e-3]])
+    Gf = orc.gram(1, N, LAM28, LAM28 / 2, 1.0, users_f)
+    G = orc.gram(1, N, LAM28, LAM28 / 2, 1.0, users_t)
+    p = np.full((2, K), 1e8) / np.real(np.einsum("bii->bi", G))  # 80 dB: the MMSE loading stays below 2^-16 too
+    s2 = np.ones(2)
+    sp = s2[:, None] / p if scheme == 1 else np.zeros((2, K))
+    ratio = [float(np.min(np.abs(np.diag(np.linalg.cholesky(Gf[b] + np.diag(sp[b])))) ** 2
+                          / np.real(np.diag(Gf[b] + np.diag(sp[b]))))) for b in range(2)]
+    assert ratio[0] < 2.0 ** -16 < ratio[1]
+    s_ref, st_ref, _ = orc.beamform(Gf, p, s2, scheme, 0, gram_true=G)
+    assert np.all(st_ref == 0)
+    for flag in (0, xl.MISMATCH_FP32):
+        s, st, _ = xl.xlmimo_beamform(dev(Gf), dev(p), dev(s2), scheme | flag, 0, gram_true=dev(G))
+        s, st = s.cpu().numpy(), st.cpu().numpy()
+        assert np.all(st == 0)
+        rel = np.abs(s - s_ref) / np.abs(s_ref)
+        tol = 1e-7 if flag == 0 else mzf_tol(Gf, G, p, s2, scheme)
+        assert np.all(rel <= tol), (flag, rel.max())
+
+
 @pytest.mark.parametrize("scale_log2", [-300, -150, -80, 80, 150, 300])
 def test_beamform_scale_invariance(xl, orc, scale_log2):
     """The receivers are homogeneous in (G, sigma^2): Gram matrices far outside
