@@ -10,7 +10,8 @@
 // Items that cover a whole instance write its Gram directly; the chunks of a
 // split instance write partial Gram matrices that ragged_reduce_kernel sums
 // in chunk order.  The receivers run one CTA per instance, launched per user
-// count bucket so that shared memory is sized for the bucket.
+// count bucket (K up to 16, 32, 40, 48, 56, 64) so that shared memory, and
+// with it the CTAs per SM, is sized for the bucket.
 #include <math.h>
 #include <string.h>
 
@@ -155,6 +156,11 @@ __global__ void ragged_sumrate_kernel(const DevInst* __restrict__ insts, int n, 
 }
 
 // ---------------------------------------------------------------- plan ----
+// Receiver buckets: instances grouped by user count, each bucket launched with
+// shared memory for its largest K ((2 K^2 + K) 16 bytes): K <= 64 alone would
+// hold one CTA per SM.
+constexpr int RG_BUCKETS[6] = {16, 32, 40, 48, 56, 64};
+
 struct BatchPlan {
     Geom g;
     int prec = XLMIMO_BF16X3;
@@ -163,11 +169,12 @@ struct BatchPlan {
     std::vector<xlmimo_inst> host;
     DevInst* d_inst = nullptr;
     DevItem* d_items = nullptr;
-    int* d_lists = nullptr;  // [small bucket | large bucket | split instances]
+    int* d_lists = nullptr;  // [receiver buckets by K (RG_BUCKETS) | split instances]
     double2* d_part = nullptr;
     RgUser* d_users = nullptr;  // per-user set-up, rewritten by every run
     int* d_iflags = nullptr;    // per-instance flags, rewritten by every run
     int n_items = 0, n_wide = 0, n_small = 0, n_large = 0, n_split = 0;
+    int n_bucket[6] = {0, 0, 0, 0, 0, 0};  // instances per receiver bucket
     int64_t chunk = 0;
     int mode = 2;  // 1: the two layouts one after the other; 2: concurrently on two streams
     cudaStream_t side = nullptr;
@@ -208,7 +215,7 @@ static int build_tables(BatchPlan* p, int64_t chunk, cudaStream_t st) {
     free_tables(p);
     std::vector<DevInst> di(p->count);
     std::vector<DevItem> items;
-    std::vector<int> small, large, split;
+    std::vector<int> small, large, split, buckets[6];
     long long part = 0;
     for (int i = 0; i < p->count; ++i) {
         const xlmimo_inst& h = p->host[i];
@@ -236,6 +243,9 @@ static int build_tables(BatchPlan* p, int64_t chunk, cudaStream_t st) {
             items.push_back(it);
         }
         (h.k <= 32 ? small : large).push_back(i);
+        int bk = 0;
+        while (RG_BUCKETS[bk] < h.k) ++bk;
+        buckets[bk].push_back(i);
         di[i] = d;
     }
     // wide items (K > 32) first, then narrow ones, each list longest first
@@ -252,8 +262,13 @@ static int build_tables(BatchPlan* p, int64_t chunk, cudaStream_t st) {
     p->chunk = chunk;
     p->part_bytes = (size_t)part * sizeof(double2);
     std::vector<int> lists;
-    lists.insert(lists.end(), small.begin(), small.end());
-    lists.insert(lists.end(), large.begin(), large.end());
+    for (int b = 0; b < 6; ++b) {
+        // larger K first inside a bucket (longer receivers start early)
+        std::stable_sort(buckets[b].begin(), buckets[b].end(),
+                         [&](int x, int y) { return p->host[x].k > p->host[y].k; });
+        p->n_bucket[b] = (int)buckets[b].size();
+        lists.insert(lists.end(), buckets[b].begin(), buckets[b].end());
+    }
     lists.insert(lists.end(), split.begin(), split.end());
     int rc = cuda_status(cudaMalloc((void**)&p->d_inst, sizeof(DevInst) * di.size()), "plan tables");
     if (!rc) rc = cuda_status(cudaMalloc((void**)&p->d_items, sizeof(DevItem) * items.size()), "plan tables");
@@ -474,11 +489,10 @@ extern "C" int xlmimo_batch_run(xlmimo_batch_plan plan, const double* users, con
     cudaStream_t st = as_stream(stream);
     int rc = run_gram(p, users, gram, st);
     if (rc || gram_only) return rc;
-    if (p->n_small > 0)
-        beamform_trial_launch_bucket(p->d_inst, p->d_lists, p->n_small, 32, gram, power, power_mode, sinr, status, st);
-    if (p->n_large > 0)
-        beamform_trial_launch_bucket(p->d_inst, p->d_lists + p->n_small, p->n_large, 64, gram, power, power_mode, sinr,
-                                     status, st);
+    for (int b = 0, off = 0; b < 6; off += p->n_bucket[b], ++b)
+        if (p->n_bucket[b] > 0)
+            beamform_trial_launch_bucket(p->d_inst, p->d_lists + off, p->n_bucket[b], RG_BUCKETS[b], gram, power,
+                                         power_mode, sinr, status, st);
     rc = cuda_status(cudaGetLastError(), "ragged receivers");
     if (!rc) {
         int blocks = std::min((p->count + 255) / 256, 16 * num_sms());
