@@ -422,8 +422,12 @@ __device__ void gram_of_lower_ff(const cd* X, int xs, cd* M, int K) {
 // (float pair).  X has row stride K + 1: a warp whose lanes cover several
 // short rows then spreads over the shared-memory banks instead of hitting
 // one bank group once per row.
+// In place (X == T, row stride K): X_ij (j <= i) is kept at T[i K + j], the
+// upper triangle and diagonal of the factor's column-major storage, which
+// the factor's strictly lower part (L_ik at T[k K + i], i > k) never uses.
 __device__ void tri_inverse_ff(cd* T, cd* X, int K, const float2* dinvf, bool t_ff) {
-    const int xs = K + 1;
+    const bool inplace = X == T;
+    const int xs = inplace ? K : K + 1;
     const int tid = threadIdx.x, nt = blockDim.x;
     cf* FT = reinterpret_cast<cf*>(T);
     for (int e = tid; e < K * K; e += nt) {
@@ -436,7 +440,7 @@ __device__ void tri_inverse_ff(cd* T, cd* X, int K, const float2* dinvf, bool t_
     cf* FX = reinterpret_cast<cf*>(X);
     for (int e = tid; e < K * K; e += nt) {
         const int i = e / K, j = e - i * K;
-        FX[i * xs + j] = {make_float2(i == j ? 1.0f : 0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+        if (!inplace || j <= i) FX[i * xs + j] = {make_float2(i == j ? 1.0f : 0.0f, 0.0f), make_float2(0.0f, 0.0f)};
     }
     __syncthreads();
     for (int k = 0; k < K - 1; ++k) {
@@ -504,6 +508,67 @@ __device__ int gj_inverse_dev(cd* A, cd* X, int K, int* flag, int* piv) {
             cd f = A[r * K + c];
             X[r * K + c] = csub(X[r * K + c], cmul(f, X[c * K + c]));
             A[r * K + c] = cmk(0.0, 0.0);
+        }
+        __syncthreads();
+    }
+    return 1;
+}
+
+// Gauss-Jordan inverse with partial pivoting in place: A (row-major) becomes
+// A^{-1}.  The row interchanges made during the elimination are undone at the
+// end as column interchanges, last first.  perm: K ints, col: K complex of
+// shared scratch (the pivot column before each step's update).
+__device__ int gj_inverse_inplace(cd* A, int K, int* flag, int* piv, int* perm, cd* col) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int c = 0; c < K; ++c) {
+        if (tid == 0) {
+            int p = c;
+            double best = cabs2(A[c * K + c]);
+            for (int r = c + 1; r < K; ++r) {
+                double v = cabs2(A[r * K + c]);
+                if (v > best) { best = v; p = r; }
+            }
+            if (!(best > 0.0) || !isfinite(best)) *flag = 1;
+            *piv = p;
+            perm[c] = p;
+        }
+        __syncthreads();
+        const int failed = *flag;
+        const int p = *piv;
+        __syncthreads();  // flag and pivot read by all before they can change
+        if (failed) return 0;
+        if (p != c) {
+            for (int j = tid; j < K; j += nt) {
+                const cd t = A[c * K + j];
+                A[c * K + j] = A[p * K + j];
+                A[p * K + j] = t;
+            }
+        }
+        __syncthreads();
+        // the pivot row divided by the pivot (as gj_inverse_dev does, so that an
+        // exactly dependent row leaves an exactly zero pivot here too)
+        const cd pv = A[c * K + c];
+        const cd inv = cdiv(cmk(1.0, 0.0), pv);
+        for (int r = tid; r < K; r += nt) col[r] = A[r * K + c];
+        __syncthreads();
+        for (int j = tid; j < K; j += nt) A[c * K + j] = j == c ? inv : cdiv(A[c * K + j], pv);
+        __syncthreads();
+        for (int e = tid; e < K * K; e += nt) {
+            const int r = e / K, j = e - r * K;
+            if (r == c) continue;
+            A[e] = j == c ? cmk(-(col[r].x * inv.x - col[r].y * inv.y), -(col[r].x * inv.y + col[r].y * inv.x))
+                          : csub(A[e], cmul(col[r], A[c * K + j]));
+        }
+        __syncthreads();
+    }
+    for (int c = K - 1; c >= 0; --c) {
+        const int q = perm[c];
+        if (q != c) {
+            for (int r = tid; r < K; r += nt) {
+                const cd t = A[r * K + c];
+                A[r * K + c] = A[r * K + q];
+                A[r * K + q] = t;
+            }
         }
         __syncthreads();
     }
@@ -879,14 +944,21 @@ __device__ void mismatched_sinr(const cf* FM, const float2* D, const double* sp,
 // sinr_t, status_t, cap_t: its outputs (cap_t may be NULL).  Dynamic shared
 // memory: (2 K^2 + K) complex doubles plus 2 XLMIMO_MAX_USERS doubles, and
 // BF_DL_EXTRA bytes more for the downlink scheme from another Gram matrix.
+// ONEBUF (matched receivers only: gt == gf, matched = 1): the triangular
+// inverse lives in the upper triangle of the factor's buffer and the
+// Gauss-Jordan fallback works in place, so K^2 complex doubles plus the
+// 2 XLMIMO_MAX_USERS doubles suffice.
+template <bool ONEBUF = false>
 __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __restrict__ gt, int matched,
                                const double* __restrict__ pw, double s2, int K, int scheme, int power_mode,
                                double* __restrict__ sinr_t, int* __restrict__ status_t, double* __restrict__ cap_t) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int KK = K * K;
     cd* Z = reinterpret_cast<cd*>(smem);
-    cd* X = Z + KK;  // K rows of K + 1 (the triangular inverse's padded stride)
-    double* p = reinterpret_cast<double*>(X + KK + K);
+    // K rows of K + 1 (the triangular inverse's padded stride); ONEBUF: the
+    // inverse shares Z (matched receivers only)
+    cd* X = ONEBUF ? Z : Z + KK;
+    double* p = reinterpret_cast<double*>(ONEBUF ? Z + KK : X + KK + K);
     double* dg = p + XLMIMO_MAX_USERS;
     // pivots, MMSE loading and pivot inverses; the mismatched SINR reuses the
     // same bytes for its per-user sums once they are no longer needed
@@ -969,7 +1041,7 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
                 for (int k = tid; k < K; k += nt) {
                     float2 s2a = make_float2(0.f, 0.f), c2a = make_float2(0.f, 0.f);
                     for (int i = k; i < K; ++i) {
-                        const cf x = FX[i * (K + 1) + k];
+                        const cf x = FX[i * (ONEBUF ? K : K + 1) + k];
                         ff2_mac(s2a, c2a, x.hi, x.lo, x.hi, x.lo);  // (re^2, im^2)
                     }
                     dg[k] = ((double)s2a.x + (double)c2a.x) + ((double)s2a.y + (double)c2a.y);
@@ -990,7 +1062,9 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
                 Z[e] = cmk(fma(v.x, c, add), v.y * c);
             }
             __syncthreads();
-            int ok2 = gj_inverse_dev(Z, X, K, &flag, &piv);
+            __shared__ int gjperm[ONEBUF ? XLMIMO_MAX_USERS : 1];
+            __shared__ cd gjcol[ONEBUF ? XLMIMO_MAX_USERS : 1];
+            int ok2 = ONEBUF ? gj_inverse_inplace(Z, K, &flag, &piv, gjperm, gjcol) : gj_inverse_dev(Z, X, K, &flag, &piv);
             if (!ok2) {
                 if (tid == 0) st = XLMIMO_ESINGULAR;
                 __syncthreads();
@@ -1000,7 +1074,7 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
                 return;
             }
             if (matched) {
-                for (int k = tid; k < K; k += nt) dg[k] = X[k * K + k].x;
+                for (int k = tid; k < K; k += nt) dg[k] = (ONEBUF ? Z : X)[k * K + k].x;
                 __syncthreads();
             }
             if (cap_t && mmse_reuse) {
@@ -1123,7 +1197,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) beamform_ragged_kernel(const De
     const int inst = list[blockIdx.x];
     const DevInst in = insts[inst];
     const double2* gm = gram + in.gram_off;
-    beamform_trial(gm, gm, 1, power + in.user_off, in.noise, in.k, in.scheme, power_mode, sinr + in.user_off,
+    beamform_trial<true>(gm, gm, 1, power + in.user_off, in.noise, in.k, in.scheme, power_mode, sinr + in.user_off,
                    status + inst, nullptr);
 }
 
@@ -1134,7 +1208,8 @@ int beamform_ragged_prepare() {
 
 void beamform_trial_launch_bucket(const DevInst* insts, const int* list, int n, int kmax, const double* gram,
                                   const double* power, int power_mode, double* sinr, int* status, cudaStream_t st) {
-    size_t smem = (2 * (size_t)kmax * kmax + kmax) * sizeof(cd) + 2 * XLMIMO_MAX_USERS * sizeof(double);
+    // matched receivers with the inverse in the factor's buffer (ONEBUF)
+    size_t smem = (size_t)kmax * kmax * sizeof(cd) + 2 * XLMIMO_MAX_USERS * sizeof(double);
     beamform_ragged_kernel<<<n, SOLVE_THREADS, smem, st>>>(insts, list, (const double2*)gram, power, power_mode, sinr,
                                                             status);
 }

@@ -176,3 +176,31 @@ def test_ragged_bench_batch_sampled(xl, orc):
             assert sinr_rate_close(out["sinr"][uo:uo + K], out["rate"][i], s_ref[0], R[0], delta, snr[uo:uo + K],
                                    1.0, int(scheme[i])), i
     plan.close()
+
+
+def test_ragged_receivers_match_single_calls(xl):
+    """The ragged receivers keep the triangular inverse in the factor's own
+    shared-memory buffer (and fall back to an in-place Gauss-Jordan
+    elimination) so that each user-count bucket fits more CTAs per SM; on the
+    plan's own Gram matrices they give what the standalone receiver call
+    gives, bit for bit, for user counts at both edges of every bucket, ZF and
+    MMSE; instance 0 (ZF) has a user duplicated, an exactly rank-deficient
+    Gram, and must get the standalone call's status."""
+    k = np.array([2, 1, 16, 17, 32, 33, 40, 41, 48, 49, 56, 57, 64, 64])
+    count = len(k)
+    n = np.array([1024, 300, 2048, 1500, 4096, 3000, 2500, 5000, 2048, 3333, 4000, 2222, 6000, 1024])
+    scheme = np.array([0] + [i % 2 for i in range(1, count)])
+    noise = np.linspace(0.5, 2.0, count)
+    users = inputs.users_polar(91, 1, int(k.sum()), (3.0, 30.0))[0]
+    users[1] = users[0]
+    snr = np.full(int(k.sum()), 10.0)
+    plan = xl.BatchPlan(xl.array(1, LAM), n, k, scheme, noise, prec=3)
+    out = run_plan(xl, plan, users, snr)
+    for i in range(count):
+        g = out["gram"][plan.gram_off[i]:plan.gram_off[i] + k[i] * k[i]].reshape(1, k[i], k[i])
+        u0 = plan.user_off[i]
+        s, st, _ = xl.xlmimo_beamform(torch.from_numpy(np.ascontiguousarray(g)).cuda(),
+                                      torch.from_numpy(snr[u0:u0 + k[i]][None].copy()).cuda(),
+                                      torch.from_numpy(noise[i:i + 1].copy()).cuda(), int(scheme[i]), xl.POWER_RXSNR)
+        assert int(st.item()) == int(out["status"][i]), i
+        assert np.array_equal(s.cpu().numpy()[0], out["sinr"][u0:u0 + k[i]]), i
