@@ -1173,6 +1173,24 @@ __global__ void __launch_bounds__(SOLVE_THREADS, 6) beamform_kernel(const double
     if (rate) trial_rate(sinr + b * K, K, rate + b);
 }
 
+// Matched receivers (gt == gf) with the triangular inverse in the factor's
+// buffer: K^2 complex doubles of shared memory instead of 2K^2 + K, so more
+// trials per SM; the same arithmetic as beamform_kernel, result for result.
+__global__ void __launch_bounds__(SOLVE_THREADS) beamform_matched_kernel(const double2* __restrict__ g,
+                                                                      const double* __restrict__ power,
+                                                                      const double* __restrict__ noise, int K,
+                                                                      int scheme, int power_mode,
+                                                                      double* __restrict__ sinr,
+                                                                      int* __restrict__ status,
+                                                                      double* __restrict__ cap,
+                                                                      double* __restrict__ rate) {
+    const int64_t b = blockIdx.x;
+    const int64_t KK = (int64_t)K * K;
+    beamform_trial<true>(g + b * KK, g + b * KK, 1, power + b * K, noise[b], K, scheme, power_mode, sinr + b * K,
+                         status + b, cap ? cap + b : nullptr);
+    if (rate) trial_rate(sinr + b * K, K, rate + b);
+}
+
 // Two receiver jobs over the same trials in one launch, CTAs interleaved
 // (even: job 0, odd: job 1), so that every SM holds both kinds at once: the
 // matched MMSE receiver keeps the FP64 pipe busy with its Cholesky while the
@@ -1220,6 +1238,16 @@ int launch_beamform(const double* gf, const double* gt, const double* power, con
     int matched = (gt == nullptr || gt == gf) ? 1 : 0;
     if (!gt) gt = gf;
     size_t KK = (size_t)K * K;
+    if (matched) {
+        const size_t sm1 = KK * sizeof(cd) + 2 * XLMIMO_MAX_USERS * sizeof(double);
+        cudaError_t e = cudaFuncSetAttribute(beamform_matched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             200 * 1024);
+        if (e != cudaSuccess) return cuda_status(e, "beamform attribute");
+        beamform_matched_kernel<<<B, SOLVE_THREADS, sm1, st>>>((const double2*)gf, power, noise, K,
+                                                               scheme & ~XLMIMO_MISMATCH_FP32, power_mode, sinr,
+                                                               status, cap, rate);
+        return cuda_status(cudaGetLastError(), "beamform launch");
+    }
     size_t smem = (2 * KK + K) * sizeof(cd) + 2 * XLMIMO_MAX_USERS * sizeof(double);
     if ((scheme & ~XLMIMO_MISMATCH_FP32) == XLMIMO_ZF_DL) smem += BF_DL_EXTRA;
     cudaError_t e = cudaFuncSetAttribute(beamform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
