@@ -309,8 +309,9 @@ int xlmimo_saturation_analytic(const xlmimo_user_dist* dist, int K, double t, do
  * cores as hi*hi + lo*hi + hi*lo with FP32 totals (each product within
  * 3 * 2^-16 of |h_i,n||h_j,n|, ~1e-6 relative per correlation entry in
  * practice); the blocked Cholesky factorisations of R and I + snr R run in
- * FP64.  A trial whose R is not numerically positive definite (coincident
- * users) gets NaN.
+ * FP64 on their diagonal blocks and panels and in double-float (FP32 pairs,
+ * ~2^-48) on their trailing updates.  A trial whose R is not numerically
+ * positive definite (coincident users) gets NaN.
  * Asynchronous on `stream`; allocates 8*B*Kp*Np + 16*B*Kp^2 + 32*B*Kp^2 + 16*B
  * bytes (Kp = K rounded up to 64, Np = n_ant rounded up to 64) of
  * stream-ordered workspace and frees it.

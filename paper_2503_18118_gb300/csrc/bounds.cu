@@ -16,8 +16,9 @@
 //   3. the complex Gram from the real one, then R and I + a R, FP64, padded to
 //      a multiple of 64 with identity rows;
 //   4. a right-looking blocked Cholesky of all 2B matrices at once, 32
-//      columns a step: diagonal block, panel solve, trailing update, each a
-//      batched launch; the log-determinant adds 2 log2 L_kk block by block.
+//      columns a step: diagonal block and panel solve in FP64, trailing
+//      update in double-float on the FP32 pipe (~2^-48), each a batched
+//      launch; the log-determinant adds 2 log2 L_kk block by block.
 // Matrices are column-major (element (i, j) at j * Kp + i), lower triangle.
 #include <math.h>
 
@@ -234,34 +235,55 @@ __global__ void __launch_bounds__(BT) bounds_chol_panel_kernel(double2* __restri
 }
 
 // Trailing update after block p: A_ij -= L_ip L_jp^H for p < j <= i, tile
-// blockIdx.x of that lower triangle; row r = tid / 8, columns 4 (tid % 8)..+3.
+// blockIdx.x of that lower triangle, in double-float on the FP32 pipe (the
+// FP64 pipe issues one warp instruction per ~64 cycles per scheduler): the
+// two 32 x 32 blocks are split into float pairs by integer operations, each
+// entry's 32 products are accumulated with FMA-exact products and two-sums
+// (~2^-48 of the terms' magnitudes), and the sum is subtracted from the FP64
+// entry in FP64.  Thread: row r = tid / 8, columns c = tid % 8 + 8 q
+// (q = 0..3, interleaved so that a warp's 16-byte loads of Lj fill all banks).
 __global__ void __launch_bounds__(256) bounds_chol_update_kernel(double2* __restrict__ A, int Kp, int p) {
-    __shared__ double2 Li[BT][BT + 1], Lj[BT][BT + 1];
+    __shared__ float4 Li[BT][BT + 1], Lj[BT][BT + 1];  // (re hi, im hi, re lo, im lo)
     double2* Am = A + (int64_t)blockIdx.y * Kp * Kp;
     int ti, tj;
     tri_index(blockIdx.x, &ti, &tj);
     const int o = p * BT, io = (p + 1 + ti) * BT, jo = (p + 1 + tj) * BT;
     const int tid = threadIdx.x;
+    auto split2 = [](double2 v) {
+        float rh, rl, ih, il;
+        split_f64(v.x, rh, rl);
+        split_f64(v.y, ih, il);
+        return make_float4(rh, ih, rl, il);
+    };
     for (int e = tid; e < BT * BT; e += 256) {
         const int c = e >> 5, r = e & 31;
-        Li[r][c] = Am[(int64_t)(o + c) * Kp + io + r];
-        Lj[r][c] = Am[(int64_t)(o + c) * Kp + jo + r];
+        Li[r][c] = split2(Am[(int64_t)(o + c) * Kp + io + r]);
+        Lj[r][c] = split2(Am[(int64_t)(o + c) * Kp + jo + r]);
     }
     __syncthreads();
-    const int r = tid >> 3, c0 = (tid & 7) * 4;
+    const int r = tid >> 3, c0 = tid & 7;
+    float2 sh[4], sl[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sh[q] = sl[q] = make_float2(0.f, 0.f);
+#pragma unroll 4
+    for (int l = 0; l < BT; ++l) {
+        const float4 x = Li[r][l];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            // s += x conj(y): lanes (re x re y, im x re y), then (im x im y, -re x im y)
+            const float4 y = Lj[c0 + 8 * q][l];
+            ff2_mac(sh[q], sl[q], make_float2(x.x, x.y), make_float2(x.z, x.w), make_float2(y.x, y.x),
+                    make_float2(y.z, y.z));
+            ff2_mac(sh[q], sl[q], make_float2(x.y, -x.x), make_float2(x.w, -x.z), make_float2(y.y, y.y),
+                    make_float2(y.w, y.w));
+        }
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const int c = c0 + q;
-        double2 s = make_double2(0.0, 0.0);
-#pragma unroll 8
-        for (int l = 0; l < BT; ++l) {  // s += Li_rl conj(Lj_cl)
-            const double2 x = Li[r][l], y = Lj[c][l];
-            s.x = fma(x.x, y.x, fma(x.y, y.y, s.x));
-            s.y = fma(x.y, y.x, fma(-x.x, y.y, s.y));
-        }
+        const int c = c0 + 8 * q;
         double2* t = Am + (int64_t)(jo + c) * Kp + io + r;
         const double2 v = *t;
-        *t = make_double2(v.x - s.x, v.y - s.y);
+        *t = make_double2(v.x - ((double)sh[q].x + (double)sl[q].x), v.y - ((double)sh[q].y + (double)sl[q].y));
     }
 }
 

@@ -10,6 +10,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 namespace xl {
 
@@ -88,6 +89,53 @@ __device__ __forceinline__ ff ff_sqrt(ff a) {
     ff y2 = ff_two_prod(y, y);
     float d = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, y2.hi), y2.lo), a.lo);
     return ff_fast_two_sum(y, __fdiv_rn(d, __fmul_rn(2.0f, y)));
+}
+
+// ---- FP64 values on the FP32 pipe, and packed (FP32x2) double-float
+// products with double-float sums (the receivers and the Appendix A Cholesky)
+
+// Split of an FP64 value into two floats, hi + lo = d to ~2^-48 relative,
+// with integer and FP32 instructions only (FP64 <-> FP32 conversions occupy
+// the FP64 pipe): hi is d truncated to 24 significant bits (sign, rebiased
+// exponent, top 23 stored mantissa bits); the remaining 29 mantissa bits m
+// give lo = RN(m) 2^(e - 1075), RN(m) formed exactly from m's low 23 and high
+// 6 bits (2^23 + a is exact in FP32) by one FMA.  Values whose hi or lo would
+// leave the normal FP32 range (|d| < 2^-74 but not zero, |d| >= 2^128, inf,
+// NaN) take the FP64 conversion; a zero (the imaginary part of every Gram
+// diagonal) is split by integer operations too, since an FP64 instruction
+// costs a full warp's issue even when one lane takes it.
+__device__ __forceinline__ void split_f64(double d, float& hi, float& lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const uint32_t bh = (uint32_t)(b >> 32), bl = (uint32_t)b;
+    const uint32_t e = (bh >> 20) & 0x7FFu;  // biased exponent
+    if (((bh & 0x7FFFFFFFu) | bl) == 0u) {
+        hi = lo = __uint_as_float(bh);  // +0 or -0
+    } else if (e - 949u <= 1150u - 949u) {
+        const uint32_t sg = bh & 0x80000000u;
+        hi = __uint_as_float(sg | ((e - 896u) << 23) | ((bh & 0xFFFFFu) << 3) | (bl >> 29));
+        const uint32_t m = bl & 0x1FFFFFFFu;
+        const float fa = __fsub_rn(__uint_as_float(0x4B000000u | (m & 0x7FFFFFu)), 8388608.0f);
+        const float fb = __fsub_rn(__uint_as_float(0x4B000000u | (m >> 23)), 8388608.0f);
+        const float l = __fmul_rn(__fmaf_rn(fb, 8388608.0f, fa), __uint_as_float((e - 948u) << 23));
+        lo = __uint_as_float(__float_as_uint(l) | sg);
+    } else {
+        hi = (float)d;
+        lo = (float)(d - (double)hi);
+    }
+}
+
+// (s, c) += x * y, lane-wise on two lanes: x, y double-float (hi, lo).
+__device__ __forceinline__ void ff2_mac(float2& s, float2& c, float2 xh, float2 xl, float2 yh, float2 yl) {
+    const float2 p = __fmul2_rn(xh, yh);
+    float2 e = __ffma2_rn(xh, yh, make_float2(-p.x, -p.y));  // exact: xh yh = p + e
+    e = __ffma2_rn(xh, yl, e);
+    e = __ffma2_rn(xl, yh, e);
+    const float2 t = __fadd2_rn(s, p);  // two-sum: s + p = t + err exactly
+    const float2 bb = __fadd2_rn(t, make_float2(-s.x, -s.y));
+    const float2 ea = __fadd2_rn(s, make_float2(-(t.x - bb.x), -(t.y - bb.y)));
+    const float2 eb = __fadd2_rn(p, make_float2(-bb.x, -bb.y));
+    s = t;
+    c = __fadd2_rn(c, __fadd2_rn(__fadd2_rn(ea, eb), e));
 }
 
 }  // namespace xl
