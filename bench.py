@@ -322,7 +322,7 @@ def sweep_bench(xl, torch):
     return out
 
 
-def appendix_a_bench(xl, torch, max_mhz):
+def appendix_a_bench(xl, torch, max_mhz, peaks=None):
     """Appendix A / Fig. 5: the negative empirical expectation -E_K[log2 lambda^R]
     = -(1/K) log2 det R and the capacity bounds at 0 dB receive SNR, for K from
     10 to 1000 users in the Sec. V-A rectangle (x in [1, 10] m, y in [-7.5, 7.5] m,
@@ -359,21 +359,30 @@ def appendix_a_bench(xl, torch, max_mhz):
         if K == ks[-1]:
             flops = 8.0 * N * K * (K + 1) / 2 * B  # Gram complex MACs of the Hermitian half
             t_last = ms
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    peak64 = sms * 2 * 2 * max_mhz * 1e6 / 1e12  # FP64: 2 FMA lanes per SM per clock
+            _, phases = xl.xlmimo_capacity_bounds_timed(arr, U, 1.0)  # the same call, its phases timed
     Kp = (ks[-1] + 63) // 64 * 64
     chol = 2 * B * 4.0 / 3.0 * Kp ** 3  # complex Cholesky of R and I + aR per trial, order Kp
     out["paper_value_at_k1000"] = 0.064
-    # the whole call against its FP64 Cholesky work, 86 % of the call's kernel
-    # time in its ncu launch list; the tensor-core Gram is reported beside it
-    out["roofline"] = {"bound": "alu", "achieved": chol / (t_last / 1e3) / 1e12, "peak": peak64,
-                       "unit": "TFLOP/s (FP64)", "frac": chol / (t_last / 1e3) / 1e12 / peak64,
-                       "kernel": "whole xlmimo_capacity_bounds call at K = 1000 (FP64 blocked Cholesky: 86 % of it)",
-                       "algorithmic": "4/3 Kp^3 flop per complex Cholesky, 2 per trial (Kp = 1024)",
-                       "peak_source": f"FP64 FMA unit counts: {sms} SMs x 2 lanes x 2 flop x {max_mhz:.0f} MHz",
-                       "gram": {"kernel": "gram_hilo_kernel", "algorithmic_tflop": flops / 1e12,
-                                "issued_bf16_tflop": 3 * 2 * 128 * 128 * 40000 * (2 * Kp // 128) * (2 * Kp // 128 + 1) / 2
-                                * B / 1e12, "traffic": traffic_from_profile("gram_hilo_kernel")}}
+    names = ("channels", "gram_tensor_cores", "correlation", "cholesky", "bounds")
+    out["phases_ms_k1000"] = dict(zip(names, phases))
+    # the tensor-core Gram, timed on its own by the call's phase events: the
+    # method's Gram work against the BF16 peak divided by the three products
+    # of the hi/lo split (each FP32-class product costs three BF16 products)
+    peaks = peaks or {}
+    bf16 = float(peaks.get("bf16_tflops", 1935.2))
+    t_gram = phases[1]
+    issued = 3 * 2 * 128 * 128 * float(N) * (2 * Kp // 128) * (2 * Kp // 128 + 1) / 2 * B
+    out["roofline"] = {"bound": "tensor", "kernel": "gram_hilo_kernel", "kernel_ms": t_gram,
+                       "achieved": flops / (t_gram / 1e3) / 1e12, "peak": bf16 / 3.0, "unit": "TFLOP/s",
+                       "frac": flops / (t_gram / 1e3) / 1e12 / (bf16 / 3.0),
+                       "peak_source": "measured BF16 (MEASURED_PEAKS.json bf16_tflops, of measured) / 3: the "
+                                      "three-product BF16 split",
+                       "algorithmic": "8 flop x N K(K+1)/2 complex MACs per trial (Gram of K = 1000, N = 40000)",
+                       "issued_bf16_tflops": issued / (t_gram / 1e3) / 1e12,
+                       "traffic": traffic_from_profile("gram_hilo_kernel"),
+                       "cholesky": {"ms": phases[3], "share_of_call": phases[3] / sum(phases),
+                                    "fp64_class_tflops": chol / (phases[3] / 1e3) / 1e12,
+                                    "how": "diagonal blocks FP64, panels and trailing updates double-float"}}
     return out
 
 
@@ -549,7 +558,7 @@ def main():
             peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         mufu = xl.xlmimo_measure_pipe(xl.PIPE_SINCOS)[0] / 1e12
         run = {"ragged": lambda: ragged_bench(xl, torch, mufu, args.ragged_count, not args.no_ragged_tune),
-               "appendix_a": lambda: appendix_a_bench(xl, torch, float(peaks.get("sm_max_mhz", 2070.0))),
+               "appendix_a": lambda: appendix_a_bench(xl, torch, float(peaks.get("sm_max_mhz", 2070.0)), peaks),
                "sweep": lambda: sweep_bench(xl, torch),
                "surrogate": lambda: surrogate_bench(xl, torch, peaks, args.surrogate_train_steps),
                "ura": lambda: ura_bench(xl, torch)}[args.only]
@@ -708,7 +717,7 @@ def main():
         ragged = ragged_bench(xl, torch, mufu_peak)
         sweep = sweep_bench(xl, torch)
         sur = surrogate_bench(xl, torch, peaks)
-        app_a = appendix_a_bench(xl, torch, float(peaks.get("sm_max_mhz", 2070.0)))
+        app_a = appendix_a_bench(xl, torch, float(peaks.get("sm_max_mhz", 2070.0)), peaks)
         ura = ura_bench(xl, torch)
 
     # peaks from unit counts and the maximum SM clock (per SM per clock:

@@ -309,8 +309,8 @@ int xlmimo_saturation_analytic(const xlmimo_user_dist* dist, int K, double t, do
  * cores as hi*hi + lo*hi + hi*lo with FP32 totals (each product within
  * 3 * 2^-16 of |h_i,n||h_j,n|, ~1e-6 relative per correlation entry in
  * practice); the blocked Cholesky factorisations of R and I + snr R run in
- * FP64 on their diagonal blocks and panels and in double-float (FP32 pairs,
- * ~2^-48) on their trailing updates.  A trial whose R is not numerically
+ * FP64 on their diagonal blocks and in double-float (FP32 pairs, ~2^-48) on
+ * their panels and trailing updates.  A trial whose R is not numerically
  * positive definite (coincident users) gets NaN.
  * Asynchronous on `stream`; allocates 8*B*Kp*Np + 16*B*Kp^2 + 32*B*Kp^2 + 16*B
  * bytes (Kp = K rounded up to 64, Np = n_ant rounded up to 64) of
@@ -319,6 +319,16 @@ int xlmimo_saturation_analytic(const xlmimo_user_dist* dist, int K, double t, do
 #define XLMIMO_MAX_BOUNDS_USERS 1024
 int xlmimo_capacity_bounds(const xlmimo_array* arr, const double* users, int K, int B, double snr,
                            double* out, void* stream);
+
+/* xlmimo_capacity_bounds with the device time of each of its phases, for
+ * measurement: phase_ms[5] (host, written) = {channels, tensor-core Gram,
+ * correlation matrices, Cholesky factorisations, bounds} in milliseconds,
+ * from CUDA events recorded on `stream` between the phases.  Same inputs,
+ * outputs, workspace and errors as xlmimo_capacity_bounds, plus
+ * XLMIMO_EINVAL for a NULL phase_ms.  SYNCHRONOUS: returns once the work is
+ * done. */
+int xlmimo_capacity_bounds_timed(const xlmimo_array* arr, const double* users, int K, int B, double snr,
+                                 double* out, float* phase_ms, void* stream);
 
 /* Capacity-saturation sweep (Sec. IV-C, Fig. 3; Sec. V-C, Fig. 4): for each
  * array size in n_list, over the same B trials of users, the exact Gram (at

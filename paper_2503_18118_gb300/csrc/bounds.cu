@@ -16,9 +16,10 @@
 //   3. the complex Gram from the real one, then R and I + a R, FP64, padded to
 //      a multiple of 64 with identity rows;
 //   4. a right-looking blocked Cholesky of all 2B matrices at once, 32
-//      columns a step: diagonal block and panel solve in FP64, trailing
-//      update in double-float on the FP32 pipe (~2^-48), each a batched
-//      launch; the log-determinant adds 2 log2 L_kk block by block.
+//      columns a step: diagonal block in FP64, panel solve and trailing
+//      update in double-float on the FP32 pipe (~2^-48; the panel hands its
+//      result to the update as float pairs), each a batched launch; the
+//      log-determinant adds 2 log2 L_kk block by block.
 // Matrices are column-major (element (i, j) at j * Kp + i), lower triangle.
 #include <math.h>
 
@@ -168,6 +169,7 @@ __global__ void __launch_bounds__(256) bounds_chol_diag_kernel(double2* __restri
                                                                double* __restrict__ logdet) {
     __shared__ double2 T[BT][BT + 1];
     __shared__ double piv[BT];
+    __shared__ double yk;  // 1 / L_kk of the current column
     __shared__ int bad;
     double2* Am = A + (int64_t)blockIdx.x * Kp * Kp;
     const int tid = threadIdx.x, o = p * BT;
@@ -179,13 +181,20 @@ __global__ void __launch_bounds__(256) bounds_chol_diag_kernel(double2* __restri
     __syncthreads();
     for (int k = 0; k < BT; ++k) {
         if (tid == 0) {
+            // one FP64 reciprocal square root per column (a few FP64
+            // instructions), shared: each FP64 instruction costs a warp's issue
             const double d = T[k][k].x;
             piv[k] = d;
-            if (!(d > 0.0) || !isfinite(d)) bad = 1;
-            T[k][k] = make_double2(sqrt(d), 0.0);
+            double y = 0.0;
+            if (!rsqrt_pivot(d, y)) {
+                bad = 1;
+                y = 0.0;
+            }
+            yk = y;
+            T[k][k] = make_double2(d * y, 0.0);
         }
         __syncthreads();
-        const double inv = 1.0 / T[k][k].x;
+        const double inv = yk;
         for (int r = k + 1 + tid; r < BT; r += 256) T[r][k] = make_double2(T[r][k].x * inv, T[r][k].y * inv);
         __syncthreads();
         const int m = BT - k - 1, tri = m * (m + 1) / 2;
@@ -203,41 +212,66 @@ __global__ void __launch_bounds__(256) bounds_chol_diag_kernel(double2* __restri
         const int c = e >> 5, r = e & 31;
         if (r >= c) Am[(int64_t)(o + c) * Kp + o + r] = T[r][c];
     }
-    if (tid == 0) {
-        double s = 0.0;
-        for (int k = 0; k < BT; ++k) s += log2(piv[k]);  // log2 L_kk^2, in column order
-        logdet[blockIdx.x] = bad ? nan("") : logdet[blockIdx.x] + s;
+    if (tid < 32) {
+        // log2 L_kk^2, one column per lane, summed in a fixed shuffle order
+        double s = bad ? 0.0 : log2(piv[tid]);
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (tid == 0) logdet[blockIdx.x] = bad ? nan("") : logdet[blockIdx.x] + s;
     }
 }
 
 // Panel below block p: L_ip = A_ip L_pp^-H for block row i = p + 1 + blockIdx.x;
-// thread r solves row r of the block by forward substitution.
+// thread r solves row r of the block by forward substitution, in double-float
+// on the FP32 pipe (FMA-exact products, two-sums; the 32 pivot reciprocals
+// are formed once in FP64).  The result is written in place as float pairs
+// (re hi, im hi, re lo, im lo: the same 16 bytes as the FP64 entry): the
+// trailing update of this step is its only reader.
 __global__ void __launch_bounds__(BT) bounds_chol_panel_kernel(double2* __restrict__ A, int Kp, int p) {
-    __shared__ double2 L[BT][BT + 1], X[BT][BT + 1];
+    __shared__ float4 L[BT][BT + 1], X[BT][BT + 1];
+    __shared__ float2 rinv[BT];
     double2* Am = A + (int64_t)blockIdx.y * Kp * Kp;
     const int r = threadIdx.x, o = p * BT, io = (p + 1 + blockIdx.x) * BT;
+    auto split2 = [](double2 v) {
+        float rh, rl, ih, il;
+        split_f64(v.x, rh, rl);
+        split_f64(v.y, ih, il);
+        return make_float4(rh, ih, rl, il);
+    };
     for (int c = 0; c < BT; ++c) {
-        L[r][c] = Am[(int64_t)(o + c) * Kp + o + r];   // rows r >= c used
-        X[r][c] = Am[(int64_t)(o + c) * Kp + io + r];
+        L[r][c] = split2(Am[(int64_t)(o + c) * Kp + o + r]);  // rows r >= c used
+        X[r][c] = split2(Am[(int64_t)(o + c) * Kp + io + r]);
+    }
+    {
+        float h, l;
+        split_f64(1.0 / Am[(int64_t)(o + r) * Kp + o + r].x, h, l);
+        rinv[r] = make_float2(h, l);
     }
     __syncthreads();
     for (int c = 0; c < BT; ++c) {
-        double2 s = X[r][c];
+        const float4 x0 = X[r][c];
+        float2 sh = make_float2(x0.x, x0.y), sl = make_float2(x0.z, x0.w);
         for (int l = 0; l < c; ++l) {  // s -= X_rl conj(L_cl)
-            const double2 x = X[r][l], y = L[c][l];
-            s.x -= fma(x.x, y.x, x.y * y.y);
-            s.y -= fma(x.y, y.x, -x.x * y.y);
+            const float4 x = X[r][l], y = L[c][l];
+            ff2_mac(sh, sl, make_float2(-x.x, -x.y), make_float2(-x.z, -x.w), make_float2(y.x, y.x),
+                    make_float2(y.z, y.z));
+            ff2_mac(sh, sl, make_float2(-x.y, x.x), make_float2(-x.w, x.z), make_float2(y.y, y.y),
+                    make_float2(y.w, y.w));
         }
-        const double inv = 1.0 / L[c][c].x;
-        X[r][c] = make_double2(s.x * inv, s.y * inv);
+        const float2 t = __fadd2_rn(sh, sl);
+        const float2 tl = __fadd2_rn(__fadd2_rn(sh, make_float2(-t.x, -t.y)), sl);
+        const float2 ri = rinv[c];
+        float2 qh = make_float2(0.f, 0.f), ql = qh;
+        ff2_mac(qh, ql, t, tl, make_float2(ri.x, ri.x), make_float2(ri.y, ri.y));
+        const float2 u = __fadd2_rn(qh, ql);
+        X[r][c] = make_float4(u.x, u.y, __fadd_rn(__fadd_rn(qh.x, -u.x), ql.x), __fadd_rn(__fadd_rn(qh.y, -u.y), ql.y));
     }
-    for (int c = 0; c < BT; ++c) Am[(int64_t)(o + c) * Kp + io + r] = X[r][c];
+    for (int c = 0; c < BT; ++c) reinterpret_cast<float4*>(Am)[(int64_t)(o + c) * Kp + io + r] = X[r][c];
 }
 
 // Trailing update after block p: A_ij -= L_ip L_jp^H for p < j <= i, tile
 // blockIdx.x of that lower triangle, in double-float on the FP32 pipe (the
 // FP64 pipe issues one warp instruction per ~64 cycles per scheduler): the
-// two 32 x 32 blocks are split into float pairs by integer operations, each
+// two 32 x 32 blocks come as float pairs from the panel kernel, each
 // entry's 32 products are accumulated with FMA-exact products and two-sums
 // (~2^-48 of the terms' magnitudes), and the sum is subtracted from the FP64
 // entry in FP64.  Thread: row r = tid / 8, columns c = tid % 8 + 8 q
@@ -249,16 +283,11 @@ __global__ void __launch_bounds__(256) bounds_chol_update_kernel(double2* __rest
     tri_index(blockIdx.x, &ti, &tj);
     const int o = p * BT, io = (p + 1 + ti) * BT, jo = (p + 1 + tj) * BT;
     const int tid = threadIdx.x;
-    auto split2 = [](double2 v) {
-        float rh, rl, ih, il;
-        split_f64(v.x, rh, rl);
-        split_f64(v.y, ih, il);
-        return make_float4(rh, ih, rl, il);
-    };
+    const float4* Lf = reinterpret_cast<const float4*>(Am);
     for (int e = tid; e < BT * BT; e += 256) {
         const int c = e >> 5, r = e & 31;
-        Li[r][c] = split2(Am[(int64_t)(o + c) * Kp + io + r]);
-        Lj[r][c] = split2(Am[(int64_t)(o + c) * Kp + jo + r]);
+        Li[r][c] = Lf[(int64_t)(o + c) * Kp + io + r];
+        Lj[r][c] = Lf[(int64_t)(o + c) * Kp + jo + r];
     }
     __syncthreads();
     const int r = tid >> 3, c0 = tid & 7;
@@ -302,9 +331,10 @@ __global__ void bounds_finish_kernel(const double* __restrict__ logdet, int K, i
 
 using namespace xl;
 
-extern "C" int xlmimo_capacity_bounds(const xlmimo_array* arr, const double* users, int K, int B, double snr,
-                                      double* out, void* stream) {
-    clear_error();
+// The whole path; ev (NULL, or 6 events) is recorded on the stream before the
+// channels and after each of the five phases.
+static int capacity_bounds_impl(const xlmimo_array* arr, const double* users, int K, int B, double snr, double* out,
+                                void* stream, cudaEvent_t* ev) {
     Geom g;
     int rc = check_array(arr, &g);
     if (rc) return rc;
@@ -342,22 +372,26 @@ extern "C" int xlmimo_capacity_bounds(const xlmimo_array* arr, const double* use
         rc = cuda_status(cudaFuncSetAttribute(gram_hilo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)gh_smem_bytes()),
                          "bounds gram attribute");
+    if (!rc && ev) rc = cuda_status(cudaEventRecord(ev[0], st), "event record");
     if (!rc) {
         bounds_channel_kernel<<<dim3((unsigned)Kp, (unsigned)B), CH_THREADS, 0, st>>>(g, make_gen_params(g), users, K, Kp,
                                                                                      Np, Xhi, Xlo);
         rc = cuda_status(cudaGetLastError(), "bounds channel launch");
     }
+    if (!rc && ev) rc = cuda_status(cudaEventRecord(ev[1], st), "event record");
     if (!rc) {
         gram_hilo_kernel<<<dim3((unsigned)(nt * (nt + 1) / 2), (unsigned)B), GH_THREADS, gh_smem_bytes(), st>>>(
             mhi, mlo, (int)Np, Kp, Rr);
         rc = cuda_status(cudaGetLastError(), "bounds gram launch");
     }
+    if (!rc && ev) rc = cuda_status(cudaEventRecord(ev[2], st), "event record");
     if (!rc) {
         int64_t blocks = ((int64_t)B * per + 255) / 256;
         if (blocks > 16LL * num_sms()) blocks = 16LL * num_sms();
         bounds_normalize_kernel<<<(unsigned)blocks, 256, 0, st>>>(Rr, K, Kp, snr, B, A);
         rc = cuda_status(cudaGetLastError(), "bounds normalize launch");
     }
+    if (!rc && ev) rc = cuda_status(cudaEventRecord(ev[3], st), "event record");
     if (!rc) rc = cuda_status(cudaMemsetAsync(ld, 0, (size_t)2 * B * sizeof(double), st), "workspace clear");
     for (int p = 0; p < nb && !rc; ++p) {
         bounds_chol_diag_kernel<<<2 * B, 256, 0, st>>>(A, Kp, p, ld);
@@ -369,14 +403,45 @@ extern "C" int xlmimo_capacity_bounds(const xlmimo_array* arr, const double* use
             rc = cuda_status(cudaGetLastError(), "bounds cholesky launch");
         }
     }
+    if (!rc && ev) rc = cuda_status(cudaEventRecord(ev[4], st), "event record");
     if (!rc) {
         bounds_finish_kernel<<<(B + 255) / 256, 256, 0, st>>>(ld, K, B, snr, out);
         rc = cuda_status(cudaGetLastError(), "bounds finish launch");
     }
+    if (!rc && ev) rc = cuda_status(cudaEventRecord(ev[5], st), "event record");
     if (ld) cudaFreeAsync(ld, st);
     if (A) cudaFreeAsync(A, st);
     if (Rr) cudaFreeAsync(Rr, st);
     if (Xlo) cudaFreeAsync(Xlo, st);
     if (Xhi) cudaFreeAsync(Xhi, st);
+    return rc;
+}
+
+extern "C" int xlmimo_capacity_bounds(const xlmimo_array* arr, const double* users, int K, int B, double snr,
+                                      double* out, void* stream) {
+    clear_error();
+    return capacity_bounds_impl(arr, users, K, B, snr, out, stream, nullptr);
+}
+
+extern "C" int xlmimo_capacity_bounds_timed(const xlmimo_array* arr, const double* users, int K, int B, double snr,
+                                            double* out, float* phase_ms, void* stream) {
+    clear_error();
+    if (!phase_ms) {
+        set_error("phase_ms must be non-NULL");
+        return XLMIMO_EINVAL;
+    }
+    cudaEvent_t ev[6] = {};
+    int rc = XLMIMO_OK;
+    for (int i = 0; i < 6 && !rc; ++i) rc = cuda_status(cudaEventCreate(&ev[i]), "event create");
+    if (!rc) rc = capacity_bounds_impl(arr, users, K, B, snr, out, stream, ev);
+    if (!rc && B == 0) {
+        for (int i = 0; i < 5; ++i) phase_ms[i] = 0.0f;  // nothing was enqueued
+    } else {
+        if (!rc) rc = cuda_status(cudaEventSynchronize(ev[5]), "event synchronize");
+        for (int i = 0; i < 5 && !rc; ++i)
+            rc = cuda_status(cudaEventElapsedTime(&phase_ms[i], ev[i], ev[i + 1]), "event time");
+    }
+    for (int i = 0; i < 6; ++i)
+        if (ev[i]) cudaEventDestroy(ev[i]);
     return rc;
 }

@@ -9,6 +9,7 @@
 // break an identity.
 #pragma once
 
+#include <math.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -136,6 +137,32 @@ __device__ __forceinline__ void ff2_mac(float2& s, float2& c, float2 xh, float2 
     const float2 eb = __fadd2_rn(p, make_float2(-bb.x, -bb.y));
     s = t;
     c = __fadd2_rn(c, __fadd2_rn(__fadd2_rn(ea, eb), e));
+}
+
+// Pivot of the Cholesky factorisation: y = 1/sqrt(d) in FP64 with five FP64
+// instructions.  The FP32 seed comes from d's high mantissa bits and goes back
+// to FP64 exactly, both by integer operations; one third-order step
+//   y = y0 (1 + r/2 + 3 r^2/8),  r = 1 - d y0^2  (y0^2 exact in FP64)
+// leaves a truncation error (5/16) r^3 ~ 2^-64, below FP64 rounding (the FP64
+// pipe issues one warp instruction per ~64 cycles per scheduler whatever the
+// active lanes, so the single-lane pivot chain is kept short).  Returns false
+// unless d is a positive finite number.
+__device__ __forceinline__ bool rsqrt_pivot(double d, double& y) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const uint32_t bh = (uint32_t)(b >> 32), bl = (uint32_t)b;
+    const uint32_t e = bh >> 20;  // sign and biased exponent: negative d lands above 2047
+    if (e - 923u <= 1122u - 923u) {  // 2^-100 <= d < 2^100
+        const float sf = __uint_as_float(((e - 896u) << 23) | ((bh & 0xFFFFFu) << 3) | (bl >> 29));
+        const uint32_t yb = __float_as_uint(rsqrtf(sf));
+        const double y0 = __hiloint2double((int)((((yb >> 23) + 896u) << 20) | ((yb & 0x7FFFFFu) >> 3)),
+                                           (int)((yb & 7u) << 29));
+        const double r = fma(-d, y0 * y0, 1.0);
+        y = fma(y0 * r, fma(r, 0.375, 0.5), y0);
+        return true;
+    }
+    if (!(d > 0.0) || !isfinite(d)) return false;
+    y = 1.0 / sqrt(d);
+    return true;
 }
 
 }  // namespace xl

@@ -74,6 +74,7 @@ EXPORTS = ("xlmimo_batch_plan_create", "xlmimo_batch_run", "xlmimo_batch_plan_in
            "xlmimo_mc_step", "xlmimo_channel_gram", "xlmimo_channel_gram_ura", "xlmimo_channel_gram_noalloc",
            "xlmimo_corr_closed_form", "xlmimo_corr_closed_form_aperture", "xlmimo_beamform", "xlmimo_sumrate",
            "xlmimo_saturation", "xlmimo_saturation_analytic", "xlmimo_capacity_sweep", "xlmimo_capacity_bounds",
+           "xlmimo_capacity_bounds_timed",
            "xlmimo_pair_features",
            "xlmimo_mlp_forward", "xlmimo_mlp_loss", "xlmimo_mlp_work_floats", "xlmimo_mlp_backward", "xlmimo_mlp_adam",
            "xlmimo_mlp_train_step", "xlmimo_mlp_pack", "xlmimo_surrogate_gram", "xlmimo_measure_pipe", "xlmimo_shutdown",
@@ -115,6 +116,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.xlmimo_capacity_sweep.argtypes = [ctypes.POINTER(SweepCfg), ctypes.POINTER(SweepResult), vp]
     L.xlmimo_corr_closed_form_aperture.argtypes = [ctypes.POINTER(Array), vp, i32, i32, i32, vp, vp]
     L.xlmimo_capacity_bounds.argtypes = [ctypes.POINTER(Array), vp, i32, i32, dbl, vp, vp]
+    L.xlmimo_capacity_bounds_timed.argtypes = [ctypes.POINTER(Array), vp, i32, i32, dbl, vp, vp, vp]
     L.xlmimo_pair_features.argtypes = [ctypes.POINTER(Array), vp, i32, i32, i32, vp, vp, vp, vp, vp, vp]
     L.xlmimo_mlp_forward.argtypes = [vp, vp, i32, vp, vp, vp]
     L.xlmimo_mlp_loss.argtypes = [vp, vp, vp, i32, vp, vp, vp]
@@ -279,6 +281,21 @@ def xlmimo_capacity_bounds(arr: Array, users: torch.Tensor, snr: float, out: tor
     _check(lib().xlmimo_capacity_bounds(ctypes.byref(arr), _dev(users, torch.float64, "users", (B, K, 2)), K, B,
                                         float(snr), _dev(out, torch.float64, "out", (B, 4)), _stream(stream)))
     return out
+
+
+def xlmimo_capacity_bounds_timed(arr: Array, users: torch.Tensor, snr: float, out: torch.Tensor | None = None,
+                                 stream=None):
+    """(xlmimo_capacity_bounds's output, [5] device milliseconds of its phases:
+    channels, tensor-core Gram, correlation matrices, Cholesky, bounds).
+    Synchronous."""
+    B, K = users.shape[0], users.shape[1]
+    if out is None:
+        out = torch.empty((B, 4), dtype=torch.float64, device=users.device)
+    ms = (ctypes.c_float * 5)()
+    _check(lib().xlmimo_capacity_bounds_timed(ctypes.byref(arr), _dev(users, torch.float64, "users", (B, K, 2)), K,
+                                              B, float(snr), _dev(out, torch.float64, "out", (B, 4)),
+                                              ctypes.cast(ms, ctypes.c_void_p), _stream(stream)))
+    return out, [float(v) for v in ms]
 
 
 def xlmimo_corr_closed_form_aperture(arr: Array, users: torch.Tensor, mode: int, gram: torch.Tensor | None = None,

@@ -96,3 +96,16 @@ def test_empty_batch_and_errors(xl):
     assert out.shape == (0, 4)
     with pytest.raises(RuntimeError):
         xl.xlmimo_capacity_bounds(arr, dev(inputs.users_rect(1, 1, 4, (1.0, 10.0), (-7.5, 7.5))), -1.0)
+
+
+def test_bounds_timed_matches_untimed(xl):
+    """The phase-timed variant gives the same bounds, bit for bit, with five
+    positive phase times (the Gram and the Cholesky present at K = 200)."""
+    users = inputs.users_rect(33, 2, 200, (1.0, 10.0), (-7.5, 7.5))
+    arr = xl.array(3000, LAM100, model=0)
+    a = xl.xlmimo_capacity_bounds(arr, dev(users), 1.0).cpu().numpy()
+    b, ms = xl.xlmimo_capacity_bounds_timed(arr, dev(users), 1.0)
+    assert np.array_equal(a, b.cpu().numpy())
+    assert len(ms) == 5 and all(t > 0.0 for t in ms)
+    _, ms0 = xl.xlmimo_capacity_bounds_timed(arr, dev(users[:0]), 1.0)
+    assert ms0 == [0.0] * 5
