@@ -434,15 +434,18 @@ typedef struct xlmimo_batch_plan_st* xlmimo_batch_plan;
 
 /* Build a plan for `count` instances (host array `insts`) sharing the
  * wavelength, spacing, beta0 and model of *geo (geo->n_ant is ignored).
- * prec: XLMIMO_BF16, XLMIMO_BF16X3 or XLMIMO_F16X3.  If tune_users (device,
- * packed [sum K][2]) is non-NULL the plan times its candidate tilings (element
- * chunk per work item, resident CTAs per SM) on those users and keeps the
- * fastest; otherwise it takes the defaults (8192 elements, 2 CTAs per SM).
- * Chunk candidates 4096, 8192, 16384, 32768 and 131072 elements, each in
- * both modes (xlmimo_batch_plan_info); the accumulator's periodic drain keeps
- * every chunk length accurate, so the choice trades load balance against
- * partial sums.  Work items run one per CTA, K <= 32 instances in the Gram
- * kernel's narrow layout (three CTAs per SM), the others in the wide one.
+ * prec: XLMIMO_BF16, XLMIMO_BF16X3 or XLMIMO_F16X3.  Work items (instance,
+ * element chunk) run one per CTA of the tensor-core Gram kernel, in one of two
+ * tilings: the narrow one (M = 128, N = 64 MMAs over 32 user lanes, three CTAs
+ * per SM) for instances with K up to the plan's narrow cut-off, the wide one
+ * (M = N = 128 MMAs over 64 lanes, two CTAs per SM) for the others.  If
+ * tune_users (device, packed [sum K][2]) is non-NULL the plan times
+ * candidates on those users (Gram phase only) and keeps the fastest: element
+ * chunks of 4096, 8192, 16384, 32768 and 131072 elements x the two launch
+ * modes with cut-off 32, then cut-offs 16 and 0 (every instance on the wide
+ * tiling) at the best of those; otherwise it takes 8192 elements, launch mode
+ * 2 and cut-off 32.  The accumulator's periodic drain keeps every chunk
+ * length accurate, so the chunk trades load balance against partial sums.
  * SYNCHRONOUS on `stream`. */
 int xlmimo_batch_plan_create(const xlmimo_array* geo, const xlmimo_inst* insts, int count, int prec,
                              const double* tune_users, xlmimo_batch_plan* plan, void* stream);
@@ -455,11 +458,23 @@ int xlmimo_batch_plan_create(const xlmimo_array* geo, const xlmimo_inst* insts, 
 int xlmimo_batch_run(xlmimo_batch_plan plan, const double* users, const double* power, int power_mode,
                      double* gram, double* sinr, int32_t* status, double* rate, void* stream);
 
-/* Plan facts (host, written): {work items, element chunk per item, mode
- * (1: the K <= 32 and K > 32 items launched one after the other, 2: both
- * launches at once on two streams), instances with K <= 32, instances with
- * K > 32, workspace bytes, tuned (0/1), candidates timed}. */
-int xlmimo_batch_plan_info(xlmimo_batch_plan plan, int64_t* info8);
+/* Pin a plan's tiling, overriding the tuner: element chunk per work item (a
+ * positive multiple of 128), launch mode (1 or 2, as in
+ * xlmimo_batch_plan_info) and narrow cut-off (0 to 32: instances with K up to
+ * it on the narrow tiling, the others on the wide one).  Waits for the
+ * device to finish pending work (runs may still read the plan's tables), then
+ * rebuilds the tables; SYNCHRONOUS on `stream`.  The plan then reports
+ * tuned = 0. */
+int xlmimo_batch_plan_set_tiling(xlmimo_batch_plan plan, int64_t chunk, int mode, int narrow_kmax, void* stream);
+
+/* Plan facts (host, written; XLMIMO_PLAN_INFO_LEN entries): {work items,
+ * element chunk per item, launch mode (1: the narrow and the wide items
+ * launched one after the other, 2: both launches at once on two streams),
+ * instances with K <= 32, instances with K > 32, workspace bytes, tuned
+ * (0/1), candidates timed, narrow cut-off (largest K on the narrow tiling),
+ * work items on the wide tiling}. */
+#define XLMIMO_PLAN_INFO_LEN 10
+int xlmimo_batch_plan_info(xlmimo_batch_plan plan, int64_t* info);
 
 int xlmimo_batch_plan_destroy(xlmimo_batch_plan plan);
 

@@ -4,9 +4,11 @@
 // receiver / rate launches.
 //
 // Work items are (instance, element chunk) pairs.  Items of instances with
-// K > 32 run the wide layout of gram_engine.cuh (two CTAs per SM), the others
-// the narrow one (three CTAs per SM), one CTA per item, each list ordered
-// longest first so that the block scheduler hands out the long items first.
+// K up to the plan's narrow cut-off (at most 32) run the narrow layout of
+// gram_engine.cuh (M = 128, N = 64 MMAs, 32 user lanes, three CTAs per SM),
+// the others the wide one (M = N = 128, 64 lanes, two CTAs per SM), one CTA
+// per item, each list ordered longest first so that the block scheduler
+// hands out the long items first.
 // Items that cover a whole instance write its Gram directly; the chunks of a
 // split instance write partial Gram matrices that ragged_reduce_kernel sums
 // in chunk order.  The receivers run one CTA per instance, launched per user
@@ -176,6 +178,7 @@ struct BatchPlan {
     int n_items = 0, n_wide = 0, n_small = 0, n_large = 0, n_split = 0;
     int n_bucket[6] = {0, 0, 0, 0, 0, 0};  // instances per receiver bucket
     int64_t chunk = 0;
+    int narrow_kmax = 32;  // largest K on the narrow tile (0: every item on the wide one)
     int mode = 2;  // 1: the two layouts one after the other; 2: concurrently on two streams
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
@@ -248,14 +251,15 @@ static int build_tables(BatchPlan* p, int64_t chunk, cudaStream_t st) {
         buckets[bk].push_back(i);
         di[i] = d;
     }
-    // wide items (K > 32) first, then narrow ones, each list longest first
+    // wide items first, then narrow ones, each list longest first
+    const int nk = p->narrow_kmax;
     std::stable_sort(items.begin(), items.end(), [&](const DevItem& a, const DevItem& b) {
-        const bool wa = p->host[a.inst].k > 32, wb = p->host[b.inst].k > 32;
+        const bool wa = p->host[a.inst].k > nk, wb = p->host[b.inst].k > nk;
         if (wa != wb) return wa;
         return a.n1 - a.n0 > b.n1 - b.n0;
     });
     p->n_items = (int)items.size();
-    p->n_wide = (int)std::count_if(items.begin(), items.end(), [&](const DevItem& a) { return p->host[a.inst].k > 32; });
+    p->n_wide = (int)std::count_if(items.begin(), items.end(), [&](const DevItem& a) { return p->host[a.inst].k > nk; });
     p->n_small = (int)small.size();
     p->n_large = (int)large.size();
     p->n_split = (int)split.size();
@@ -336,8 +340,8 @@ static int prepare_gram(BatchPlan* p) {
     return rc;
 }
 
-// The Gram matrices of a run: per-user set-up, then the wide items (K > 32)
-// and the narrow ones, one CTA per item; mode 1 launches the two layouts one
+// The Gram matrices of a run: per-user set-up, then the wide items (K above
+// the narrow cut-off) and the narrow ones, one CTA per item; mode 1 launches the two layouts one
 // after the other on `st`, mode 2 the narrow ones on the plan's second stream
 // so that the two launches share the GPU (a fork and a join by events).
 static int run_gram(BatchPlan* p, const double* users, double* gram, cudaStream_t st) {
@@ -422,9 +426,12 @@ extern "C" int xlmimo_batch_plan_create(const xlmimo_array* geo, const xlmimo_in
     // any chunk length accurate; the chunk trades load balance against
     // partial sums)
     int64_t best_chunk = 8192;
-    int best_mode = 2;
+    int best_mode = 2, best_nk = 32;
     if (tune_users) {
-        // time the candidate tilings on the given users (Gram phase only)
+        // time candidate tilings on the given users (Gram phase only), in two
+        // stages: element chunk x launch mode with K <= 32 on the narrow tile,
+        // then, at the best of those, the narrow tile's cut-off (K <= 16 or no
+        // instance on it: the wide M = N = 128 tile for the rest)
         int64_t gram_total = 0;
         for (int i = 0; i < count; ++i) gram_total = std::max<int64_t>(gram_total, insts[i].gram_off + (int64_t)insts[i].k * insts[i].k);
         double* scratch = nullptr;
@@ -433,27 +440,33 @@ extern "C" int xlmimo_batch_plan_create(const xlmimo_array* geo, const xlmimo_in
         if (!rc) rc = cuda_status(cudaEventCreate(&e0), "tuning event");
         if (!rc) rc = cuda_status(cudaEventCreate(&e1), "tuning event");
         float best = 1e30f;
-        const int64_t chunks[5] = {4096, 8192, 16384, 32768, 131072};
-        for (int ci = 0; ci < 5 && !rc; ++ci) {
-            rc = build_tables(p, chunks[ci], st);
+        auto trial = [&](int64_t chunk, int nk, int md) {
+            p->narrow_kmax = nk;
+            rc = build_tables(p, chunk, st);
             if (!rc) rc = prepare_gram(p);
-            for (int md = 1; md <= 2 && !rc; ++md) {
-                p->mode = md;
-                if (!rc) rc = run_gram(p, tune_users, scratch, st);  // warm
-                if (!rc) rc = cuda_status(cudaEventRecord(e0, st), "tuning");
-                if (!rc) rc = run_gram(p, tune_users, scratch, st);
-                if (!rc) rc = cuda_status(cudaEventRecord(e1, st), "tuning");
-                if (!rc) rc = cuda_status(cudaEventSynchronize(e1), "tuning");
-                float ms = 0.f;
-                if (!rc) cudaEventElapsedTime(&ms, e0, e1);
-                if (!rc && ms < best) {
-                    best = ms;
-                    best_chunk = chunks[ci];
-                    best_mode = md;
-                }
-                p->candidates += 1;
+            p->mode = md;
+            if (!rc) rc = run_gram(p, tune_users, scratch, st);  // warm
+            if (!rc) rc = cuda_status(cudaEventRecord(e0, st), "tuning");
+            if (!rc) rc = run_gram(p, tune_users, scratch, st);
+            if (!rc) rc = cuda_status(cudaEventRecord(e1, st), "tuning");
+            if (!rc) rc = cuda_status(cudaEventSynchronize(e1), "tuning");
+            float ms = 0.f;
+            if (!rc) cudaEventElapsedTime(&ms, e0, e1);
+            if (!rc && ms < best) {
+                best = ms;
+                best_chunk = chunk;
+                best_mode = md;
+                best_nk = nk;
             }
-        }
+            p->candidates += 1;
+        };
+        const int64_t chunks[5] = {4096, 8192, 16384, 32768, 131072};
+        for (int ci = 0; ci < 5 && !rc; ++ci)
+            for (int md = 1; md <= 2 && !rc; ++md) trial(chunks[ci], 32, md);
+        const int64_t c1 = best_chunk;
+        const int m1 = best_mode;
+        for (int nk : {16, 0})
+            if (!rc) trial(c1, nk, m1);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
         cudaFree(scratch);
@@ -461,6 +474,7 @@ extern "C" int xlmimo_batch_plan_create(const xlmimo_array* geo, const xlmimo_in
     }
     if (!rc) {
         p->mode = best_mode;
+        p->narrow_kmax = best_nk;
         rc = build_tables(p, best_chunk, st);
     }
     if (!rc) rc = prepare_gram(p);
@@ -502,6 +516,26 @@ extern "C" int xlmimo_batch_run(xlmimo_batch_plan plan, const double* users, con
     return rc;
 }
 
+extern "C" int xlmimo_batch_plan_set_tiling(xlmimo_batch_plan plan, int64_t chunk, int mode, int narrow_kmax,
+                                            void* stream) {
+    clear_error();
+    if (!plan) { set_error("plan must be non-NULL"); return XLMIMO_EINVAL; }
+    if (chunk < 128 || chunk % 128 != 0 || chunk > (int64_t(1) << 40) || (mode != 1 && mode != 2) || narrow_kmax < 0 ||
+        narrow_kmax > 32) {
+        set_error("tiling: chunk a positive multiple of 128, mode 1 or 2, narrow cut-off in [0, 32]");
+        return XLMIMO_EINVAL;
+    }
+    BatchPlan* p = &plan->p;
+    // runs in flight may still read the tables that are rebuilt
+    int rc = cuda_status(cudaDeviceSynchronize(), "tiling");
+    p->narrow_kmax = narrow_kmax;
+    p->mode = mode;
+    p->tuned = 0;
+    if (!rc) rc = build_tables(p, chunk, as_stream(stream));
+    if (!rc) rc = prepare_gram(p);
+    return rc;
+}
+
 extern "C" int xlmimo_batch_plan_info(xlmimo_batch_plan plan, int64_t* info) {
     clear_error();
     if (!plan || !info) { set_error("plan and info must be non-NULL"); return XLMIMO_EINVAL; }
@@ -514,6 +548,8 @@ extern "C" int xlmimo_batch_plan_info(xlmimo_batch_plan plan, int64_t* info) {
     info[5] = (int64_t)p->part_bytes;
     info[6] = p->tuned;
     info[7] = p->candidates;
+    info[8] = p->narrow_kmax;
+    info[9] = p->n_wide;
     return XLMIMO_OK;
 }
 

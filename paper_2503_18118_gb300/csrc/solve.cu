@@ -26,6 +26,7 @@
 namespace xl {
 
 constexpr int SOLVE_THREADS = 128;
+static_assert(SOLVE_THREADS >= XLMIMO_MAX_USERS, "load_lower writes the diagonal with one thread per user");
 // downlink scratch of mismatched_sinr: |A_kk|^2, per-warp column sums and trace
 // shares for up to SOLVE_THREADS / 32 warps
 constexpr size_t BF_DL_EXTRA = (size_t)(XLMIMO_MAX_USERS * (1 + SOLVE_THREADS / 32) + SOLVE_THREADS / 32) * sizeof(double);
@@ -506,25 +507,38 @@ __device__ int gj_inverse_inplace(cd* A, int K, int* flag, int* piv, int* perm, 
     return 1;
 }
 
+// Global loads per thread issued together before their results are used
+// (the loads of a trial's Gram are latency-bound: one round trip per batch
+// instead of one per entry).
+constexpr int LOAD_BATCH = 4;
+
 // The lower triangle of c times a Hermitian Gram matrix g (row-major) into
 // shared memory column by column, as chol_lower takes it: column j of the
 // lower triangle is row j of the upper one conjugated, T[j K + i] =
 // c conj(g[j K + i]) for i > j, read and written contiguously.  add[k] (if
-// non-NULL) goes onto the diagonal, which is written by its own pass so that
-// only K lanes execute the FP64 addition; c = 1 (the usual case) costs no
-// multiplication.
+// non-NULL) goes onto the diagonal, which the first K threads write (their
+// loads issued ahead of the batches) so that only they execute the FP64
+// addition; c = 1 (the usual case) costs no multiplication.  Needs
+// blockDim.x >= K.
 __device__ void load_lower(cd* T, const double2* __restrict__ g, int K, const double* add, double c) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int e = tid; e < K * K; e += nt) {
-        const int j = e / K, i = e - j * K;
-        if (i > j) {
-            const double2 v = g[e];
-            T[e] = c == 1.0 ? cmk(v.x, -v.y) : cmk(v.x * c, -(v.y * c));
+    const int tid = threadIdx.x, nt = blockDim.x, KK = K * K;
+    const double dg = tid < K ? g[tid * K + tid].x : 0.0;
+    for (int e0 = tid; e0 < KK; e0 += LOAD_BATCH * nt) {
+        double2 v[LOAD_BATCH];
+#pragma unroll
+        for (int u = 0; u < LOAD_BATCH; ++u) {
+            const int e = e0 + u * nt, j = e / K;
+            if (e < KK && e - j * K > j) v[u] = g[e];
+        }
+#pragma unroll
+        for (int u = 0; u < LOAD_BATCH; ++u) {
+            const int e = e0 + u * nt, j = e / K;
+            if (e < KK && e - j * K > j) T[e] = c == 1.0 ? cmk(v[u].x, -v[u].y) : cmk(v[u].x * c, -(v[u].y * c));
         }
     }
-    for (int k = tid; k < K; k += nt) {
-        const double d = c == 1.0 ? g[k * K + k].x : g[k * K + k].x * c;
-        T[k * K + k] = cmk(add ? d + add[k] : d, 0.0);
+    if (tid < K) {
+        const double d = c == 1.0 ? dg : dg * c;
+        T[tid * K + tid] = cmk(add ? d + add[tid] : d, 0.0);
     }
 }
 
@@ -1106,8 +1120,9 @@ __global__ void __launch_bounds__(SOLVE_THREADS, 6) beamform_kernel(const double
 
 // Matched receivers (gt == gf) with the triangular inverse in the factor's
 // buffer: K^2 complex doubles of shared memory instead of 2K^2 + K, so more
-// trials per SM; the same arithmetic as beamform_kernel, result for result.
-__global__ void __launch_bounds__(SOLVE_THREADS) beamform_matched_kernel(const double2* __restrict__ g,
+// trials per SM (ten at K = 32, registers capped at 48 without spills); the
+// same arithmetic as beamform_kernel, result for result.
+__global__ void __launch_bounds__(SOLVE_THREADS, 10) beamform_matched_kernel(const double2* __restrict__ g,
                                                                       const double* __restrict__ power,
                                                                       const double* __restrict__ noise, int K,
                                                                       int scheme, int power_mode,
@@ -1137,7 +1152,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS, 6) beamform_pair_kernel(BfJob j
     if (j.rate) trial_rate(j.sinr + b * K, K, j.rate + b);
 }
 
-__global__ void __launch_bounds__(SOLVE_THREADS) beamform_ragged_kernel(const DevInst* __restrict__ insts,
+__global__ void __launch_bounds__(SOLVE_THREADS, 10) beamform_ragged_kernel(const DevInst* __restrict__ insts,
                                                                         const int* __restrict__ list,
                                                                         const double2* __restrict__ gram,
                                                                         const double* __restrict__ power, int power_mode,

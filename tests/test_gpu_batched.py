@@ -113,15 +113,18 @@ def test_batch_split_instances(xl, orc):
 def test_batch_graph_capture_and_autotune(xl):
     """The run enqueues kernels only, so it captures into a CUDA graph; replays
     reproduce a direct run exactly.  The autotuned plan picks one of its
-    candidates."""
+    candidates: 5 chunk lengths x 2 launch modes, then the narrow tiling's
+    cut-offs 16 and 0 at the best of those."""
     n, k, scheme, noise, users, snr = make_batch(12, 300, (1024, 131072), (2, 64))
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     U = dev(users)
     arr = xl.array(1, LAM)
     plan = xl.BatchPlan(arr, n, k, scheme, noise, tune_users=U)
     info = plan.info()
-    assert info["tuned"] == 1 and info["candidates"] == 10  # 5 chunk lengths x 2 modes
+    assert info["tuned"] == 1 and info["candidates"] == 12
     assert info["chunk"] in (4096, 8192, 16384, 32768, 131072) and info["mode"] in (1, 2)
+    assert info["narrow_kmax"] in (0, 16, 32)
+    assert info["wide_items"] == sum(-(-int(n[i]) // info["chunk"]) for i in range(len(k)) if k[i] > info["narrow_kmax"])
     P = dev(snr)
     out = dict(gram=torch.empty(plan.gram_total, dtype=torch.complex128, device="cuda"),
                sinr=torch.empty(plan.users_total, dtype=torch.float64, device="cuda"),
@@ -204,3 +207,26 @@ def test_ragged_receivers_match_single_calls(xl):
                                       torch.from_numpy(noise[i:i + 1].copy()).cuda(), int(scheme[i]), xl.POWER_RXSNR)
         assert int(st.item()) == int(out["status"][i]), i
         assert np.array_equal(s.cpu().numpy()[0], out["sinr"][u0:u0 + k[i]]), i
+
+
+@pytest.mark.parametrize("narrow_kmax", [0, 16, 32])
+def test_pinned_tilings_match_oracle(xl, orc, narrow_kmax):
+    """Every tiling the tuner may pick gives the oracle's Gram matrices: the
+    narrow cut-off pinned at 0 (every instance on the wide M = N = 128 tiling,
+    users padded to 64 lanes), 16 and 32, with instances on both sides of it and
+    one split into chunks."""
+    k = np.array([2, 9, 16, 17, 31, 32, 33, 64, 5])
+    n = np.array([1500, 4096, 2048, 3000, 8192, 1024, 5000, 2500, 20000])
+    users = inputs.users_polar(77, 1, int(k.sum()), (3.0, 30.0))[0]
+    plan = xl.BatchPlan(xl.array(1, LAM), n, k, np.zeros(len(k)), np.ones(len(k)), prec=3)
+    plan.set_tiling(8192, 2, narrow_kmax)
+    info = plan.info()
+    assert info["narrow_kmax"] == narrow_kmax and info["chunk"] == 8192 and info["mode"] == 2
+    assert info["wide_items"] == sum(-(-int(n[i]) // 8192) for i in range(len(k)) if k[i] > narrow_kmax)
+    out = run_plan(xl, plan, users, np.full(int(k.sum()), 10.0))
+    for i in range(len(k)):
+        K, uo, go = int(k[i]), int(plan.user_off[i]), int(plan.gram_off[i])
+        G = out["gram"][go:go + K * K].reshape(1, K, K)
+        R = orc.gram(orc.FSPL, int(n[i]), LAM, LAM / 2, 1.0, users[uo:uo + K][None])
+        assert normwise(G, R) <= 2e-5, (i, normwise(G, R))
+    plan.close()
