@@ -371,14 +371,14 @@ int xlmimo_capacity_sweep(const xlmimo_sweep_cfg* cfg, xlmimo_sweep_result* res,
  * rate; the closed-form Gram of modified ZF (Sec. V-B) and the receiver
  * `cf_scheme` built from it and judged on the exact channel, with its sum
  * rate; and the per-trial saturation interval (Eqs. 15-16).
- * The batch is cut into `chunks` pieces that flow through two streams: the
- * Gram kernels run on `stream` while the FP64 receivers of the previous
- * piece run on a second stream owned by the library (one per device,
- * created on first use), so the generation/tensor-core work and the FP64
- * solves overlap.  The call returns once everything is enqueued; all work is
- * ordered before any later work on `stream`.  Concurrent calls on different
- * streams of one device share the library's second stream and are
- * serialised on it.  Batch statistics {mean, M2, count} of both rates are
+ * The batch is cut into `chunks` pieces that flow through three streams: the
+ * Gram kernels run on `stream` while the receivers of the previous piece run
+ * on two streams owned by the library (one pair per device, created on first
+ * use): the exact receivers on one, the closed-form ones beside them on the
+ * other, so the generation/tensor-core work and the FP64 solves overlap.  The
+ * call returns once everything is enqueued; all work is ordered before any
+ * later work on `stream`.  Concurrent calls on different streams of one
+ * device share the library's streams and are serialised on them.  Batch statistics {mean, M2, count} of both rates are
  * reduced over the whole batch in a fixed order.  With an exact Gram below
  * FP64 (prec != XLMIMO_F64) the closed-form receiver takes
  * XLMIMO_MISMATCH_FP32, whose error lies far below that Gram's own. */
@@ -598,7 +598,7 @@ const char* xlmimo_last_error(void);
 /* Interface version, (major << 16) | minor. */
 int xlmimo_version(void);
 
-/* Releases what the library keeps between calls: the stream and events that
+/* Releases what the library keeps between calls: the streams and events that
  * xlmimo_mc_step creates on first use on each device (work already enqueued
  * there completes first).  The library stays usable; the next call creates
  * them again.  Must not run concurrently with another library call.  The

@@ -67,22 +67,6 @@ __device__ __forceinline__ void tri_index(int q, int* r, int* c) {
 int launch_beamform(const double* gf, const double* gt, const double* power, const double* noise, int K,
                     int B, int scheme, int power_mode, double* sinr, int* status, double* cap,
                     cudaStream_t st, double* rate = nullptr);
-// One receiver job over B trials: Gram matrices gf (filter) and gt (true
-// channel; NULL or gf for a matched receiver), powers, noise, scheme, outputs
-// (cap and rate nullable).
-struct BfJob {
-    const double* gf;
-    const double* gt;
-    const double* power;
-    const double* noise;
-    int scheme;
-    double* sinr;
-    int* status;
-    double* cap;
-    double* rate;
-};
-// Two jobs over the same B trials in one launch (CTAs interleaved).
-int launch_beamform_pair(const BfJob& j0, const BfJob& j1, int K, int B, int power_mode, cudaStream_t st);
 int launch_sumrate(const double* sinr, int K, int B, double* rate, double* stats, cudaStream_t st);
 int launch_saturation(const double* users, int K, int B, double t, double spacing, double* sat,
                       cudaStream_t st);

@@ -1137,21 +1137,6 @@ __global__ void __launch_bounds__(SOLVE_THREADS, 10) beamform_matched_kernel(con
     if (rate) trial_rate(sinr + b * K, K, rate + b);
 }
 
-// Two receiver jobs over the same trials in one launch, CTAs interleaved
-// (even: job 0, odd: job 1), so that every SM holds both kinds at once: the
-// matched MMSE receiver keeps the FP64 pipe busy with its Cholesky while the
-// modified-ZF one works mostly in double-float on the FP32 pipe.
-__global__ void __launch_bounds__(SOLVE_THREADS, 6) beamform_pair_kernel(BfJob j0, BfJob j1, int K, int power_mode) {
-    const BfJob j = (blockIdx.x & 1) ? j1 : j0;
-    const int64_t b = blockIdx.x >> 1;
-    const int64_t KK = (int64_t)K * K;
-    const double2* gf = reinterpret_cast<const double2*>(j.gf) + b * KK;
-    const double2* gt = reinterpret_cast<const double2*>(j.gt ? j.gt : j.gf) + b * KK;
-    beamform_trial(gf, gt, j.gt == nullptr ? 1 : 0, j.power + b * K, j.noise[b], K, j.scheme, power_mode,
-                   j.sinr + b * K, j.status + b, j.cap ? j.cap + b : nullptr);
-    if (j.rate) trial_rate(j.sinr + b * K, K, j.rate + b);
-}
-
 __global__ void __launch_bounds__(SOLVE_THREADS, 10) beamform_ragged_kernel(const DevInst* __restrict__ insts,
                                                                         const int* __restrict__ list,
                                                                         const double2* __restrict__ gram,
@@ -1200,21 +1185,6 @@ int launch_beamform(const double* gf, const double* gt, const double* power, con
     if (e != cudaSuccess) return cuda_status(e, "beamform attribute");
     beamform_kernel<<<B, SOLVE_THREADS, smem, st>>>((const double2*)gf, (const double2*)gt, matched, power, noise, K,
                                                     scheme, power_mode, sinr, status, cap, rate);
-    return cuda_status(cudaGetLastError(), "beamform launch");
-}
-
-int launch_beamform_pair(const BfJob& j0, const BfJob& j1, int K, int B, int power_mode, cudaStream_t st) {
-    if (B == 0) return XLMIMO_OK;
-    BfJob a = j0, c = j1;
-    if (a.gt == a.gf) a.gt = nullptr;  // matched
-    if (c.gt == c.gf) c.gt = nullptr;
-    size_t KK = (size_t)K * K;
-    size_t smem = (2 * KK + K) * sizeof(cd) + 2 * XLMIMO_MAX_USERS * sizeof(double);
-    if ((a.scheme & ~XLMIMO_MISMATCH_FP32) == XLMIMO_ZF_DL || (c.scheme & ~XLMIMO_MISMATCH_FP32) == XLMIMO_ZF_DL)
-        smem += BF_DL_EXTRA;
-    cudaError_t e = cudaFuncSetAttribute(beamform_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return cuda_status(e, "beamform attribute");
-    beamform_pair_kernel<<<2 * (int64_t)B, SOLVE_THREADS, smem, st>>>(a, c, K, power_mode);
     return cuda_status(cudaGetLastError(), "beamform launch");
 }
 
