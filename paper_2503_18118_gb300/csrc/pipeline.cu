@@ -106,8 +106,10 @@ extern "C" int xlmimo_mc_step(const xlmimo_mc_batch* j, void* stream) {
     if (j->B == 0) return XLMIMO_OK;
     const int K = j->K, B = j->B;
     int C = j->chunks;
-    // measured at 1e4 trials: one piece 9.33 ms; 2 / 4 pieces 9.41 / 9.64 ms (10.19 / 10.47 ms
-    // when the Gram kernel leaves room for the receivers by running 2 CTAs/SM)
+    // measured at 1e4 headline trials: one piece 7.27 ms, 2 / 4 pieces 7.32 / 7.54 ms (the Gram
+    // kernel fills every SM, so a piece's receivers only take SMs as the next Gram's CTAs finish;
+    // with the interleaved receivers of an earlier build: 9.33 / 9.41 / 9.64 ms, and 10.19 /
+    // 10.47 ms when the Gram kernel left room for the receivers by running 2 CTAs/SM)
     if (C == 0) C = 1;
     if (C > B) C = B;
     cudaStream_t s0 = as_stream(stream);
