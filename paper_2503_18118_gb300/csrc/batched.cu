@@ -7,8 +7,15 @@
 // K up to the plan's narrow cut-off (at most 32) run the narrow layout of
 // gram_engine.cuh (M = 128, N = 64 MMAs, 32 user lanes, three CTAs per SM),
 // the others the wide one (M = N = 128, 64 lanes, two CTAs per SM), one CTA
-// per item, each list ordered longest first so that the block scheduler
-// hands out the long items first.
+// per wide item, each list ordered longest first so that the block scheduler
+// hands out the long items first.  Narrow items share CTAs: items whose user
+// counts add up to at most 32 and whose lengths lie within PACK_LEN_RATIO of
+// the CTA's longest are packed into one CTA's user lanes (the accumulator's
+// blocks between them are computed and dropped), since channel generation
+// costs per lane whatever the instance's K.  Every user's position is taken
+// relative to its own instance's first element (y + (N - 1) d / 2 for the
+// spherical models, the range shifted along the planar wave's direction for
+// UPW), so lanes of instances with different N share one array geometry.
 // Items that cover a whole instance write its Gram directly; the chunks of a
 // split instance write partial Gram matrices that ragged_reduce_kernel sums
 // in chunk order.  The receivers run one CTA per instance, launched per user
@@ -29,6 +36,28 @@ struct DevItem {
     long long n0, n1;
 };
 
+// A narrow CTA: members [m0, m0 + nm) of the member list, the longest
+// member's element count, over which its stages run.
+struct DevPack {
+    int m0, nm;
+    long long len;
+};
+
+// One narrow work item inside a CTA: its users occupy lanes lane0 ..
+// lane0 + K - 1.
+struct DevMember {
+    int inst, chunk;
+    long long n0, n1;
+    int lane0, pad;
+};
+
+// A narrow item joins a CTA whose longest item is at most 1/PACK_LEN_RATIO
+// times its own length (the lanes of the shorter one generate zeros for the
+// rest); larger gaps start a CTA of their own.
+constexpr double PACK_LEN_RATIO = 0.75;
+// A new narrow item is tried against the most recently opened CTAs only.
+constexpr int PACK_WINDOW = 64;
+
 // Per-user set-up of a whole ragged batch, once per run (one warp per
 // instance), which the Gram CTAs of the instance's items then load.
 // iflags[i]: bit 0 an invalid user, bit 1 a user too close for the slice
@@ -45,9 +74,19 @@ __global__ void ragged_user_kernel(Geom g, GenParams gp, const DevInst* __restri
     if (warp >= count) return;
     const DevInst in = insts[warp];
     int flags = 0;
+    // element n of the instance lies at n d - off along the array
+    const double off = 0.5 * (double)(in.n_ant - 1) * g.spacing;
     for (int k = lane; k < in.k; k += 32) {
         const double x = users[(in.user_off + k) * 2], y = users[(in.user_off + k) * 2 + 1];
-        const UserSetup u = user_setup<MODEL, PREC, false>(g, gp, x, y, true);
+        UserSetup u = user_setup<MODEL, PREC, false>(g, gp, x, y, true);
+        if (u.ug.ok) {
+            if (MODEL == XLMIMO_UPW) {
+                const double r0 = sqrt(x * x + y * y);
+                u.ug.r0u = ff_from_double(r0 + off * (y / r0));
+            } else {
+                u.ug.y = ff_from_double(y + off);
+            }
+        }
         out[in.user_off + k] = RgUser{u.ug, u.fac};
         flags |= (u.bad ? 1 : 0) | (u.near ? 2 : 0);
     }
@@ -55,10 +94,9 @@ __global__ void ragged_user_kernel(Geom g, GenParams gp, const DevInst* __restri
     if (lane == 0) iflags[warp] = flags;
 }
 
-// One work item per CTA (items of one layout, longest first: the block
-// scheduler hands them out in that order as SMs free up), running the
-// pipeline of gram_engine.cuh on the item's element range; users come from
-// the per-run set-up.
+// One wide work item per CTA (longest first: the block scheduler hands them
+// out in that order as SMs free up), running the pipeline of gram_engine.cuh
+// on the item's element range; users come from the per-run set-up.
 template <int MODEL, int KMAX, int PREC>
 __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
     gram_tc_items_kernel(Geom g, GenParams gp, const DevInst* __restrict__ insts, const DevItem* __restrict__ items,
@@ -89,10 +127,6 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    Geom gi = g;
-    gi.N = in.n_ant;
-    GenParams gpi = gp;
-    gpi.nm1 = in.n_ant - 1;
     if (tid < KMAX) {
         if (tid < K) {
             const RgUser u = users[in.user_off + tid];
@@ -111,7 +145,7 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
     const uint32_t tmem = sh->tmem_base;
     const int nst = E::stages(itm.n0, itm.n1);
     if (warp < 8) {
-        E::generate(sh, smem_u32(base), tmem, gi, gpi, itm.n0, itm.n1, UraRows{0, 0.0, 0.0, 0}, 0, 0, 0, !sh->near);
+        E::generate(sh, smem_u32(base), tmem, g, gp, itm.n0, itm.n1, UraRows{0, 0.0, 0.0, 0}, 0, 0, 0, !sh->near);
     } else {
         if (lane == 0) E::mma(sh, smem_u32(base), tmem, nst, 0, 0);
         __syncwarp();
@@ -123,6 +157,97 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
     ok = ok && !*(volatile int*)&sh->abort && !sh->bad;
     double2* o = in.nchunks == 1 ? gram + in.gram_off : part + in.part_off + (long long)itm.chunk * K * K;
     E::epilogue(sh, fold, tmem, K, E::drains(nst), ok, o, tid, warp, lane);
+    __syncthreads();
+    if (warp == 8) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * E::WCOLS) : "memory");
+    }
+}
+
+// One narrow CTA: several work items of instances with K <= 32 side by side
+// in the 32 user lanes, each lane over its own item's elements; the
+// accumulator is folded once and every member's diagonal block is written to
+// its instance's Gram (or chunk partial).  A member with an invalid user gets
+// NaN; a member with a user too close for the slice expansion takes the
+// whole CTA to the exact per-entry formula.
+template <int MODEL, int PREC>
+__global__ void __launch_bounds__(TC_THREADS, 3)
+    gram_tc_packed_kernel(Geom g, GenParams gp, const DevInst* __restrict__ insts, const DevPack* __restrict__ packs,
+                          const DevMember* __restrict__ members, const RgUser* __restrict__ users,
+                          const int* __restrict__ iflags, double2* __restrict__ gram, double2* __restrict__ part) {
+    constexpr int NRING = 2;
+    using E = GramEngine<MODEL, 32, PREC, false, NRING>;
+    using SH = EngShared<32, NRING>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    SH* sh = reinterpret_cast<SH*>(base + NRING * E::BYTES);
+    float* fold = reinterpret_cast<float*>(base);
+    __shared__ long long lane_n0[32], lane_len[32];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const DevPack pk = packs[blockIdx.x];
+    if (tid == 0) {
+        eng_init_barriers(sh);
+        int near = 0;
+        for (int m = 0; m < pk.nm; ++m) near |= (iflags[members[pk.m0 + m].inst] >> 1) & 1;
+        sh->bad = 0;
+        sh->near = near;
+    }
+    if (tid < 32) {
+        int mi = -1;
+        for (int m = 0; m < pk.nm; ++m) {
+            const DevMember mb = members[pk.m0 + m];
+            if (tid >= mb.lane0 && tid < mb.lane0 + insts[mb.inst].k) mi = m;
+        }
+        if (mi >= 0) {
+            const DevMember mb = members[pk.m0 + mi];
+            const RgUser u = users[insts[mb.inst].user_off + (tid - mb.lane0)];
+            sh->ug[tid] = u.ug;
+            sh->fac[tid] = u.fac;
+            lane_n0[tid] = mb.n0;
+            lane_len[tid] = mb.n1 - mb.n0;
+        } else {
+            // padding user (1, 0), weight 0, over the longest member's range so
+            // that its lane takes the same path through each stage as the others
+            UserGeo pad = make_user_geo(g, 1.0, 0.0);
+            pad.ampc = 0.f;
+            sh->ug[tid] = pad;
+            sh->fac[tid] = 1.0;
+            lane_n0[tid] = 0;
+            lane_len[tid] = pk.len;
+        }
+    }
+    __syncthreads();
+    if (warp == 8) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
+                     "r"(2 * E::WCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tmem_base;
+    const int nst = E::stages(0, pk.len);
+    if (warp < 8) {
+        E::template generate<SH, true>(sh, smem_u32(base), tmem, g, gp, 0, pk.len, UraRows{0, 0.0, 0.0, 0}, 0, 0, 0,
+                                       !sh->near, lane_n0, lane_len);
+    } else {
+        if (lane == 0) E::mma(sh, smem_u32(base), tmem, nst, 0, 0);
+        __syncwarp();
+    }
+    bool ok = mbar_wait(&sh->done, 0, &sh->abort);
+    tc_fence_before();
+    __syncthreads();  // every MMA done and every drain's tcgen05.st complete
+    tc_fence_after();
+    ok = ok && !*(volatile int*)&sh->abort;
+    E::epilogue_fold(fold, tmem, E::drains(nst), ok, warp, lane);
+    for (int m = 0; m < pk.nm; ++m) {
+        const DevMember mb = members[pk.m0 + m];
+        const DevInst in = insts[mb.inst];
+        double2* o = in.nchunks == 1 ? gram + in.gram_off : part + in.part_off + (long long)mb.chunk * in.k * in.k;
+        E::epilogue_write(sh, fold, in.k, mb.lane0, ok && !(iflags[mb.inst] & 1), o, tid);
+    }
     __syncthreads();
     if (warp == 8) {
         tc_fence_after();
@@ -170,7 +295,9 @@ struct BatchPlan {
     int64_t users_total = 0;
     std::vector<xlmimo_inst> host;
     DevInst* d_inst = nullptr;
-    DevItem* d_items = nullptr;
+    DevItem* d_items = nullptr;     // the wide items, longest first
+    DevPack* d_packs = nullptr;     // the narrow CTAs, longest first
+    DevMember* d_members = nullptr; // their items
     int* d_lists = nullptr;  // [receiver buckets by K (RG_BUCKETS) | split instances]
     double2* d_part = nullptr;
     RgUser* d_users = nullptr;  // per-user set-up, rewritten by every run
@@ -179,6 +306,8 @@ struct BatchPlan {
     int n_bucket[6] = {0, 0, 0, 0, 0, 0};  // instances per receiver bucket
     int64_t chunk = 0;
     int narrow_kmax = 32;  // largest K on the narrow tile (0: every item on the wide one)
+    int pack = 1;          // narrow items share CTAs (else one per CTA)
+    int n_packs = 0;       // narrow CTAs
     int mode = 2;  // 1: the two layouts one after the other; 2: concurrently on two streams
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
@@ -200,12 +329,16 @@ static void release_streams(BatchPlan* p) {
 static void free_tables(BatchPlan* p) {
     cudaFree(p->d_inst);
     cudaFree(p->d_items);
+    cudaFree(p->d_packs);
+    cudaFree(p->d_members);
     cudaFree(p->d_lists);
     cudaFree(p->d_part);
     cudaFree(p->d_users);
     cudaFree(p->d_iflags);
     p->d_inst = nullptr;
     p->d_items = nullptr;
+    p->d_packs = nullptr;
+    p->d_members = nullptr;
     p->d_lists = nullptr;
     p->d_part = nullptr;
     p->d_users = nullptr;
@@ -260,6 +393,51 @@ static int build_tables(BatchPlan* p, int64_t chunk, cudaStream_t st) {
     });
     p->n_items = (int)items.size();
     p->n_wide = (int)std::count_if(items.begin(), items.end(), [&](const DevItem& a) { return p->host[a.inst].k > nk; });
+    // narrow items into CTAs, longest first, so that a CTA's first member is
+    // its longest; each new item goes to the most recent CTA with lanes to
+    // spare and a length within PACK_LEN_RATIO of it (recent CTAs are the
+    // shortest), else opens one
+    std::vector<std::vector<DevMember>> bins;
+    std::vector<int> lanes_used;
+    std::vector<long long> bin_len;
+    for (size_t t = (size_t)p->n_wide; t < items.size(); ++t) {
+        const DevItem& it = items[t];
+        const int k = p->host[it.inst].k;
+        const long long len = it.n1 - it.n0;
+        int b = -1;
+        if (p->pack)
+            for (int c = (int)bins.size() - 1; c >= 0 && c >= (int)bins.size() - PACK_WINDOW; --c)
+                if (lanes_used[c] + k <= 32 && (double)len >= PACK_LEN_RATIO * (double)bin_len[c]) {
+                    b = c;
+                    break;
+                }
+        if (b < 0) {
+            bins.emplace_back();
+            lanes_used.push_back(0);
+            bin_len.push_back(len);
+            b = (int)bins.size() - 1;
+        }
+        DevMember m;
+        m.inst = it.inst;
+        m.chunk = it.chunk;
+        m.n0 = it.n0;
+        m.n1 = it.n1;
+        m.lane0 = lanes_used[b];
+        m.pad = 0;
+        bins[b].push_back(m);
+        lanes_used[b] += k;
+    }
+    std::vector<DevPack> packs;
+    std::vector<DevMember> members;
+    for (size_t b = 0; b < bins.size(); ++b) {
+        DevPack pk;
+        pk.m0 = (int)members.size();
+        pk.nm = (int)bins[b].size();
+        pk.len = bin_len[b];
+        packs.push_back(pk);
+        members.insert(members.end(), bins[b].begin(), bins[b].end());
+    }
+    p->n_packs = (int)packs.size();
     p->n_small = (int)small.size();
     p->n_large = (int)large.size();
     p->n_split = (int)split.size();
@@ -275,7 +453,9 @@ static int build_tables(BatchPlan* p, int64_t chunk, cudaStream_t st) {
     }
     lists.insert(lists.end(), split.begin(), split.end());
     int rc = cuda_status(cudaMalloc((void**)&p->d_inst, sizeof(DevInst) * di.size()), "plan tables");
-    if (!rc) rc = cuda_status(cudaMalloc((void**)&p->d_items, sizeof(DevItem) * items.size()), "plan tables");
+    if (!rc) rc = cuda_status(cudaMalloc((void**)&p->d_items, sizeof(DevItem) * std::max<size_t>(1, items.size())), "plan tables");
+    if (!rc) rc = cuda_status(cudaMalloc((void**)&p->d_packs, sizeof(DevPack) * std::max<size_t>(1, packs.size())), "plan tables");
+    if (!rc) rc = cuda_status(cudaMalloc((void**)&p->d_members, sizeof(DevMember) * std::max<size_t>(1, members.size())), "plan tables");
     if (!rc) rc = cuda_status(cudaMalloc((void**)&p->d_users, sizeof(RgUser) * std::max<int64_t>(1, p->users_total)),
                               "plan tables");
     if (!rc) rc = cuda_status(cudaMalloc((void**)&p->d_iflags, sizeof(int) * p->count), "plan tables");
@@ -283,6 +463,11 @@ static int build_tables(BatchPlan* p, int64_t chunk, cudaStream_t st) {
     if (!rc && part > 0) rc = cuda_status(cudaMalloc((void**)&p->d_part, p->part_bytes), "plan workspace");
     if (!rc) rc = cuda_status(cudaMemcpyAsync(p->d_inst, di.data(), sizeof(DevInst) * di.size(), cudaMemcpyHostToDevice, st), "plan upload");
     if (!rc) rc = cuda_status(cudaMemcpyAsync(p->d_items, items.data(), sizeof(DevItem) * items.size(), cudaMemcpyHostToDevice, st), "plan upload");
+    if (!rc && !packs.empty())
+        rc = cuda_status(cudaMemcpyAsync(p->d_packs, packs.data(), sizeof(DevPack) * packs.size(), cudaMemcpyHostToDevice, st), "plan upload");
+    if (!rc && !members.empty())
+        rc = cuda_status(cudaMemcpyAsync(p->d_members, members.data(), sizeof(DevMember) * members.size(), cudaMemcpyHostToDevice, st),
+                         "plan upload");
     if (!rc && !lists.empty())
         rc = cuda_status(cudaMemcpyAsync(p->d_lists, lists.data(), sizeof(int) * lists.size(), cudaMemcpyHostToDevice, st), "plan upload");
     if (!rc) rc = cuda_status(cudaStreamSynchronize(st), "plan upload");
@@ -304,18 +489,35 @@ static RuKernel ru_pick(int model, int prec) {
                                  : ru_pick_prec<XLMIMO_FSPL_USW>(prec);
 }
 
-template <int MODEL, int KMAX>
+template <int MODEL>
 static RgKernel rg_pick_prec(int prec) {
-    return prec == XLMIMO_BF16 ? gram_tc_items_kernel<MODEL, KMAX, TCP_BF16>
-         : prec == XLMIMO_F16X3 ? gram_tc_items_kernel<MODEL, KMAX, TCP_F16X3>
-                                : gram_tc_items_kernel<MODEL, KMAX, TCP_BF16X3>;
+    return prec == XLMIMO_BF16 ? gram_tc_items_kernel<MODEL, 64, TCP_BF16>
+         : prec == XLMIMO_F16X3 ? gram_tc_items_kernel<MODEL, 64, TCP_F16X3>
+                                : gram_tc_items_kernel<MODEL, 64, TCP_BF16X3>;
 }
 
-template <int KMAX>
+// the wide items' kernel
 static RgKernel rg_pick(int model, int prec) {
-    return model == XLMIMO_PNUSW ? rg_pick_prec<XLMIMO_PNUSW, KMAX>(prec)
-         : model == XLMIMO_UPW   ? rg_pick_prec<XLMIMO_UPW, KMAX>(prec)
-                                 : rg_pick_prec<XLMIMO_FSPL_USW, KMAX>(prec);
+    return model == XLMIMO_PNUSW ? rg_pick_prec<XLMIMO_PNUSW>(prec)
+         : model == XLMIMO_UPW   ? rg_pick_prec<XLMIMO_UPW>(prec)
+                                 : rg_pick_prec<XLMIMO_FSPL_USW>(prec);
+}
+
+using RpKernel = void (*)(Geom, GenParams, const DevInst*, const DevPack*, const DevMember*, const RgUser*, const int*,
+                          double2*, double2*);
+
+template <int MODEL>
+static RpKernel rp_pick_prec(int prec) {
+    return prec == XLMIMO_BF16 ? gram_tc_packed_kernel<MODEL, TCP_BF16>
+         : prec == XLMIMO_F16X3 ? gram_tc_packed_kernel<MODEL, TCP_F16X3>
+                                : gram_tc_packed_kernel<MODEL, TCP_BF16X3>;
+}
+
+// the narrow CTAs' kernel
+static RpKernel rp_pick(int model, int prec) {
+    return model == XLMIMO_PNUSW ? rp_pick_prec<XLMIMO_PNUSW>(prec)
+         : model == XLMIMO_UPW   ? rp_pick_prec<XLMIMO_UPW>(prec)
+                                 : rp_pick_prec<XLMIMO_FSPL_USW>(prec);
 }
 
 template <int KMAX>
@@ -328,10 +530,10 @@ static size_t items_smem() {
 // Kernel attributes and the second stream of the concurrent mode (at plan
 // time, outside any stream capture).
 static int prepare_gram(BatchPlan* p) {
-    int rc = cuda_status(cudaFuncSetAttribute(rg_pick<32>(p->g.model, p->prec),
+    int rc = cuda_status(cudaFuncSetAttribute(rp_pick(p->g.model, p->prec),
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)items_smem<32>()),
                          "ragged attribute");
-    if (!rc) rc = cuda_status(cudaFuncSetAttribute(rg_pick<64>(p->g.model, p->prec),
+    if (!rc) rc = cuda_status(cudaFuncSetAttribute(rg_pick(p->g.model, p->prec),
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)items_smem<64>()),
                               "ragged attribute");
     if (!rc && !p->side) rc = cuda_status(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking), "plan stream");
@@ -351,7 +553,7 @@ static int run_gram(BatchPlan* p, const double* users, double* gram, cudaStream_
                                                                       p->d_iflags);
     int rc = cuda_status(cudaGetLastError(), "ragged user set-up launch");
     if (rc) return rc;
-    const int n_narrow = p->n_items - p->n_wide;
+    const int n_narrow = p->n_packs;
     cudaStream_t sn = st;
     if (p->mode == 2 && n_narrow > 0 && p->n_wide > 0) {
         rc = cuda_status(cudaEventRecord(p->fork, st), "plan fork");
@@ -360,11 +562,11 @@ static int run_gram(BatchPlan* p, const double* users, double* gram, cudaStream_
         sn = p->side;
     }
     if (p->n_wide > 0)
-        rg_pick<64>(p->g.model, p->prec)<<<p->n_wide, TC_THREADS, items_smem<64>(), st>>>(
+        rg_pick(p->g.model, p->prec)<<<p->n_wide, TC_THREADS, items_smem<64>(), st>>>(
             p->g, gp, p->d_inst, p->d_items, p->d_users, p->d_iflags, (double2*)gram, p->d_part);
     if (n_narrow > 0)
-        rg_pick<32>(p->g.model, p->prec)<<<n_narrow, TC_THREADS, items_smem<32>(), sn>>>(
-            p->g, gp, p->d_inst, p->d_items + p->n_wide, p->d_users, p->d_iflags, (double2*)gram, p->d_part);
+        rp_pick(p->g.model, p->prec)<<<n_narrow, TC_THREADS, items_smem<32>(), sn>>>(
+            p->g, gp, p->d_inst, p->d_packs, p->d_members, p->d_users, p->d_iflags, (double2*)gram, p->d_part);
     rc = cuda_status(cudaGetLastError(), "ragged gram launch");
     if (!rc && sn != st) {
         rc = cuda_status(cudaEventRecord(p->join, sn), "plan join");
@@ -426,12 +628,13 @@ extern "C" int xlmimo_batch_plan_create(const xlmimo_array* geo, const xlmimo_in
     // any chunk length accurate; the chunk trades load balance against
     // partial sums)
     int64_t best_chunk = 8192;
-    int best_mode = 2, best_nk = 32;
+    int best_mode = 2, best_nk = 32, best_pack = 1;
     if (tune_users) {
         // time candidate tilings on the given users (Gram phase only), in two
-        // stages: element chunk x launch mode with K <= 32 on the narrow tile,
-        // then, at the best of those, the narrow tile's cut-off (K <= 16 or no
-        // instance on it: the wide M = N = 128 tile for the rest)
+        // stages: element chunk x launch mode with K <= 32 on the narrow tile
+        // and narrow items packed, then, at the best of those, the narrow
+        // tile's cut-off (K <= 16 or no instance on it: the wide M = N = 128
+        // tile for the rest) and one narrow item per CTA
         int64_t gram_total = 0;
         for (int i = 0; i < count; ++i) gram_total = std::max<int64_t>(gram_total, insts[i].gram_off + (int64_t)insts[i].k * insts[i].k);
         double* scratch = nullptr;
@@ -440,8 +643,9 @@ extern "C" int xlmimo_batch_plan_create(const xlmimo_array* geo, const xlmimo_in
         if (!rc) rc = cuda_status(cudaEventCreate(&e0), "tuning event");
         if (!rc) rc = cuda_status(cudaEventCreate(&e1), "tuning event");
         float best = 1e30f;
-        auto trial = [&](int64_t chunk, int nk, int md) {
+        auto trial = [&](int64_t chunk, int nk, int md, int pk) {
             p->narrow_kmax = nk;
+            p->pack = pk;
             rc = build_tables(p, chunk, st);
             if (!rc) rc = prepare_gram(p);
             p->mode = md;
@@ -457,16 +661,18 @@ extern "C" int xlmimo_batch_plan_create(const xlmimo_array* geo, const xlmimo_in
                 best_chunk = chunk;
                 best_mode = md;
                 best_nk = nk;
+                best_pack = pk;
             }
             p->candidates += 1;
         };
         const int64_t chunks[5] = {4096, 8192, 16384, 32768, 131072};
         for (int ci = 0; ci < 5 && !rc; ++ci)
-            for (int md = 1; md <= 2 && !rc; ++md) trial(chunks[ci], 32, md);
+            for (int md = 1; md <= 2 && !rc; ++md) trial(chunks[ci], 32, md, 1);
         const int64_t c1 = best_chunk;
         const int m1 = best_mode;
         for (int nk : {16, 0})
-            if (!rc) trial(c1, nk, m1);
+            if (!rc) trial(c1, nk, m1, 1);
+        if (!rc) trial(c1, 32, m1, 0);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
         cudaFree(scratch);
@@ -475,6 +681,7 @@ extern "C" int xlmimo_batch_plan_create(const xlmimo_array* geo, const xlmimo_in
     if (!rc) {
         p->mode = best_mode;
         p->narrow_kmax = best_nk;
+        p->pack = best_pack;
         rc = build_tables(p, best_chunk, st);
     }
     if (!rc) rc = prepare_gram(p);
@@ -517,18 +724,19 @@ extern "C" int xlmimo_batch_run(xlmimo_batch_plan plan, const double* users, con
 }
 
 extern "C" int xlmimo_batch_plan_set_tiling(xlmimo_batch_plan plan, int64_t chunk, int mode, int narrow_kmax,
-                                            void* stream) {
+                                            int pack, void* stream) {
     clear_error();
     if (!plan) { set_error("plan must be non-NULL"); return XLMIMO_EINVAL; }
     if (chunk < 128 || chunk % 128 != 0 || chunk > (int64_t(1) << 40) || (mode != 1 && mode != 2) || narrow_kmax < 0 ||
-        narrow_kmax > 32) {
-        set_error("tiling: chunk a positive multiple of 128, mode 1 or 2, narrow cut-off in [0, 32]");
+        narrow_kmax > 32 || (pack != 0 && pack != 1)) {
+        set_error("tiling: chunk a positive multiple of 128, mode 1 or 2, narrow cut-off in [0, 32], pack 0 or 1");
         return XLMIMO_EINVAL;
     }
     BatchPlan* p = &plan->p;
     // runs in flight may still read the tables that are rebuilt
     int rc = cuda_status(cudaDeviceSynchronize(), "tiling");
     p->narrow_kmax = narrow_kmax;
+    p->pack = pack;
     p->mode = mode;
     p->tuned = 0;
     if (!rc) rc = build_tables(p, chunk, as_stream(stream));
@@ -550,6 +758,8 @@ extern "C" int xlmimo_batch_plan_info(xlmimo_batch_plan plan, int64_t* info) {
     info[7] = p->candidates;
     info[8] = p->narrow_kmax;
     info[9] = p->n_wide;
+    info[10] = p->pack;
+    info[11] = p->n_packs;
     return XLMIMO_OK;
 }
 

@@ -239,11 +239,16 @@ struct GramEngine {
 
     // Generator warps 0-7 over the item's elements [nbeg, nend).  gs0 / gd0:
     // stages and drains of the CTA before this item.  Returns true if a wait
-    // gave up.
-    template <class SH>
+    // gave up.  PACKED (narrow layout only): the user lanes belong to
+    // instances of their own; lane k's elements are lane_n0[k] + [0,
+    // lane_len[k]) (the stages cover the longest, shorter lanes generate
+    // zeros past their end), nbeg = 0 and nend = the longest length.
+    template <class SH, bool PACKED = false>
     static __device__ __forceinline__ bool generate(SH* sh, uint32_t sbase, uint32_t tmem, const Geom& g, const GenParams& gp,
                                     int64_t nbeg, int64_t nend, const UraRows& ura, int gs0, int gd0, int gsp0,
-                                    bool fast) {
+                                    bool fast, const long long* lane_n0 = nullptr,
+                                    const long long* lane_len = nullptr) {
+        static_assert(!PACKED || (KMAX == 32 && !URA), "packed lanes: narrow ULA layout only");
         // the thread's coordinates read afresh (an opaque read): in a
         // persistent kernel the values derived from them below are then made
         // per item instead of being hoisted across the whole item loop, where
@@ -285,8 +290,8 @@ struct GramEngine {
                     sh->sref_b[slot][kk] = make_float4(c.r0, c.kx, c.xl2, c.aw);
                 }
             } else {
-                const long long ncs = m0 + SPAN / 2;
                 for (int kk = lane; kk < KMAX; kk += 32) {
+                    const long long ncs = (PACKED ? lane_n0[kk] + (long long)sp * SPAN : m0) + SPAN / 2;
                     const UserGeo& ug = sh->ug[kk];
                     const SpanC c = make_span_c(make_user_ref(gp, ug, ncs), ug.xl2, ug.ampc);
                     sh->sref_a[slot][kk] = make_float4(c.frac0, c.ah, c.al, c.e0);
@@ -360,7 +365,11 @@ struct GramEngine {
                     dead = true;
                     continue;
                 }
-                const int rem = it == nst - 1 ? last_rem : T;  // valid elements from this warp's first slice on
+                int rem = it == nst - 1 ? last_rem : T;  // valid elements from this warp's first slice on
+                if (PACKED) {
+                    const long long li = lane_len[lane] - (long long)it * T;  // this lane's elements from the stage on
+                    rem = li >= T ? T : (int)max(li, -(long long)T) - warp * 8;
+                }
                 const uint32_t sb = sbase + (uint32_t)cur * BYTES;
                 const int rem0 = rem, rem1 = KMAX == 32 ? rem - TC_T : rem;
                 const int k1 = KMAX == 32 ? lane : lane + 32;
@@ -376,7 +385,10 @@ struct GramEngine {
                     const int hs = h ^ ((lane >> 3) & 1);
                     uint32_t w[2][4][2];
                     if (FAST) {
-                        if (rem0 >= 8 && rem1 >= 8) slice_words<MODEL, PREC, TRUNC, LO2, false>(co, hs, 8, 8, w);
+                        // packed lanes end at different elements: one warp-wide choice, the
+                        // partial form zeroing each lane's entries past its own end
+                        const bool full = PACKED ? __all_sync(0xffffffffu, rem0 >= 8 && rem1 >= 8) : (rem0 >= 8 && rem1 >= 8);
+                        if (full) slice_words<MODEL, PREC, TRUNC, LO2, false>(co, hs, 8, 8, w);
                         else slice_words<MODEL, PREC, TRUNC, LO2, true>(co, hs, rem0, rem1, w);
                     } else {
 #pragma unroll
@@ -457,6 +469,13 @@ struct GramEngine {
     template <class SH>
     static __device__ __forceinline__ void epilogue(SH* sh, float* fold, uint32_t tmem, int K, int ndrain, bool ok, double2* o,
                                     int tid, int warp, int lane) {
+        epilogue_fold(fold, tmem, ndrain, ok, warp, lane);
+        epilogue_write(sh, fold, K, 0, ok, o, tid);
+    }
+
+    // W (+ T) of the accumulator to the fold buffer (warps 0-3), then a CTA
+    // barrier.
+    static __device__ __forceinline__ void epilogue_fold(float* fold, uint32_t tmem, int ndrain, bool ok, int warp, int lane) {
         if (ok && warp < 4) {
             const int m = warp * 32 + lane;  // row of D
             const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
@@ -474,8 +493,14 @@ struct GramEngine {
         }
         tc_fence_before();
         __syncthreads();
+    }
+
+    // The complex Gram of the K users in lanes u0 .. u0 + K - 1 from the fold
+    // (R = X X^T, 2 KMAX square) times their per-user factors, or NaN if !ok.
+    template <class SH>
+    static __device__ __forceinline__ void epilogue_write(const SH* sh, const float* fold, int K, int u0, bool ok, double2* o,
+                                          int tid) {
         if (ok) {
-            // R (2 KMAX square) from the fold; complex Gram from R times the per-user factors
             const int P = K * (K + 1) / 2;
             for (int q = tid; q < P; q += TC_THREADS) {
                 int i = 0, rl = K, p = q;
@@ -486,9 +511,10 @@ struct GramEngine {
                                             fold[(c + 64) * C::FOLD_LD + r]
                                       : 0.5f * (fold[r * C::FOLD_LD + c] + fold[c * C::FOLD_LD + r]);
                 };
-                double re = (double)(R(i, j) + R(KMAX + i, KMAX + j));
-                double im = (double)(R(i, KMAX + j) - R(KMAX + i, j));
-                const double us = sh->fac[i] * sh->fac[j];
+                const int a = u0 + i, b = u0 + j;
+                double re = (double)(R(a, b) + R(KMAX + a, KMAX + b));
+                double im = (double)(R(a, KMAX + b) - R(KMAX + a, b));
+                const double us = sh->fac[a] * sh->fac[b];
                 re *= us;
                 im *= us;
                 if (i == j) {

@@ -25,7 +25,7 @@ MAX_USERS = 64
 MAX_BOUNDS_USERS = 1024
 MAX_URA_ROWS = 1048576
 NOALLOC_SCRATCH_MIB = 16  # XLMIMO_NOALLOC_SCRATCH_MIB
-PLAN_INFO_LEN = 10  # XLMIMO_PLAN_INFO_LEN
+PLAN_INFO_LEN = 12  # XLMIMO_PLAN_INFO_LEN
 STATUS = {0: "OK", 1: "EINVAL", 2: "ECUDA", 3: "ENOMEM", 4: "ESINGULAR", 5: "ETIMEOUT", 6: "EUNSUPPORTED"}
 
 
@@ -108,7 +108,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
                                            ctypes.POINTER(vp), vp]
     L.xlmimo_batch_run.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp]
     L.xlmimo_batch_plan_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
-    L.xlmimo_batch_plan_set_tiling.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, vp]
+    L.xlmimo_batch_plan_set_tiling.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
     L.xlmimo_batch_plan_destroy.argtypes = [vp]
     L.xlmimo_channel_gram_noalloc.argtypes = [ctypes.POINTER(Array), vp, i32, i32, i32, vp, vp]
     L.xlmimo_corr_closed_form.argtypes = [ctypes.POINTER(Array), vp, i32, i32, vp, vp]
@@ -422,9 +422,10 @@ class BatchPlan:
                                               _stream(stream)))
         self._h = h
 
-    def set_tiling(self, chunk: int, mode: int, narrow_kmax: int, stream=None):
-        """Pin the tiling (element chunk, launch mode, narrow cut-off), overriding the tuner."""
-        _check(lib().xlmimo_batch_plan_set_tiling(self._h, int(chunk), int(mode), int(narrow_kmax), _stream(stream)))
+    def set_tiling(self, chunk: int, mode: int, narrow_kmax: int, pack: int = 1, stream=None):
+        """Pin the tiling (element chunk, launch mode, narrow cut-off, packing), overriding the tuner."""
+        _check(lib().xlmimo_batch_plan_set_tiling(self._h, int(chunk), int(mode), int(narrow_kmax), int(pack),
+                                                  _stream(stream)))
 
     def run(self, users, power, power_mode, gram, sinr, status, rate, stream=None):
         U, n = self.users_total, self.count
@@ -444,7 +445,7 @@ class BatchPlan:
         v = (ctypes.c_int64 * PLAN_INFO_LEN)()
         _check(lib().xlmimo_batch_plan_info(self._h, v))
         keys = ("items", "chunk", "mode", "small", "large", "workspace_bytes", "tuned", "candidates", "narrow_kmax",
-                "wide_items")
+                "wide_items", "pack", "narrow_ctas")
         return dict(zip(keys, list(v)))
 
     def close(self):

@@ -194,7 +194,7 @@ def test_capacity_sweep_and_batch_plan_validate_on_host(xl):
     assert L.xlmimo_batch_plan_create(ctypes.byref(geo), insts, 1, xl.F32, None, ctypes.byref(plan), None) == 1
     bad = (xl.Inst * 1)(xl.Inst(1024, 65, xl.ZF, 0, 0, 1.0))
     assert L.xlmimo_batch_plan_create(ctypes.byref(geo), bad, 1, xl.BF16X3, None, ctypes.byref(plan), None) == 1
-    assert L.xlmimo_batch_plan_set_tiling(None, 8192, 2, 32, None) == 1
+    assert L.xlmimo_batch_plan_set_tiling(None, 8192, 2, 32, 1, None) == 1
 
 
 def test_binding_constants_match_header(xl):

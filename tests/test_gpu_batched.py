@@ -114,14 +114,14 @@ def test_batch_graph_capture_and_autotune(xl):
     """The run enqueues kernels only, so it captures into a CUDA graph; replays
     reproduce a direct run exactly.  The autotuned plan picks one of its
     candidates: 5 chunk lengths x 2 launch modes, then the narrow tiling's
-    cut-offs 16 and 0 at the best of those."""
+    cut-offs 16 and 0 and one narrow item per CTA at the best of those."""
     n, k, scheme, noise, users, snr = make_batch(12, 300, (1024, 131072), (2, 64))
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     U = dev(users)
     arr = xl.array(1, LAM)
     plan = xl.BatchPlan(arr, n, k, scheme, noise, tune_users=U)
     info = plan.info()
-    assert info["tuned"] == 1 and info["candidates"] == 12
+    assert info["tuned"] == 1 and info["candidates"] == 13 and info["pack"] in (0, 1)
     assert info["chunk"] in (4096, 8192, 16384, 32768, 131072) and info["mode"] in (1, 2)
     assert info["narrow_kmax"] in (0, 16, 32)
     assert info["wide_items"] == sum(-(-int(n[i]) // info["chunk"]) for i in range(len(k)) if k[i] > info["narrow_kmax"])
@@ -209,19 +209,22 @@ def test_ragged_receivers_match_single_calls(xl):
         assert np.array_equal(s.cpu().numpy()[0], out["sinr"][u0:u0 + k[i]]), i
 
 
-@pytest.mark.parametrize("narrow_kmax", [0, 16, 32])
-def test_pinned_tilings_match_oracle(xl, orc, narrow_kmax):
+@pytest.mark.parametrize("narrow_kmax,pack", [(0, 1), (16, 1), (32, 1), (32, 0)])
+def test_pinned_tilings_match_oracle(xl, orc, narrow_kmax, pack):
     """Every tiling the tuner may pick gives the oracle's Gram matrices: the
     narrow cut-off pinned at 0 (every instance on the wide M = N = 128 tiling,
-    users padded to 64 lanes), 16 and 32, with instances on both sides of it and
-    one split into chunks."""
+    users padded to 64 lanes), 16 and 32, narrow items packed into shared CTAs
+    or one per CTA, with instances on both sides of the cut-off and one split
+    into chunks."""
     k = np.array([2, 9, 16, 17, 31, 32, 33, 64, 5])
     n = np.array([1500, 4096, 2048, 3000, 8192, 1024, 5000, 2500, 20000])
     users = inputs.users_polar(77, 1, int(k.sum()), (3.0, 30.0))[0]
     plan = xl.BatchPlan(xl.array(1, LAM), n, k, np.zeros(len(k)), np.ones(len(k)), prec=3)
-    plan.set_tiling(8192, 2, narrow_kmax)
+    plan.set_tiling(8192, 2, narrow_kmax, pack)
     info = plan.info()
-    assert info["narrow_kmax"] == narrow_kmax and info["chunk"] == 8192 and info["mode"] == 2
+    assert info["narrow_kmax"] == narrow_kmax and info["chunk"] == 8192 and info["mode"] == 2 and info["pack"] == pack
+    narrow = sum(-(-int(n[i]) // 8192) for i in range(len(k)) if k[i] <= narrow_kmax)
+    assert (info["narrow_ctas"] == narrow) if not pack else (0 < info["narrow_ctas"] <= narrow or narrow == 0)
     assert info["wide_items"] == sum(-(-int(n[i]) // 8192) for i in range(len(k)) if k[i] > narrow_kmax)
     out = run_plan(xl, plan, users, np.full(int(k.sum()), 10.0))
     for i in range(len(k)):
@@ -230,3 +233,38 @@ def test_pinned_tilings_match_oracle(xl, orc, narrow_kmax):
         R = orc.gram(orc.FSPL, int(n[i]), LAM, LAM / 2, 1.0, users[uo:uo + K][None])
         assert normwise(G, R) <= 2e-5, (i, normwise(G, R))
     plan.close()
+
+
+@pytest.mark.parametrize("model", ["FSPL", "PNUSW", "UPW"])
+def test_packed_narrow_items_match_unpacked(xl, orc, model):
+    """Narrow items packed into shared CTAs (user counts adding up to at most
+    32, lengths within 3/4 of the CTA's longest) give, bit for bit, the Gram
+    matrices of the same items one per CTA: a shorter member's extra stages
+    add exact zeros and its drain periods fall at the same stage counts.  A
+    spread of N (chunked instances among them) and K from 1 to 32; a sample
+    against the oracle for each channel model (every user's position is taken
+    relative to its own instance's first element, the planar model's range
+    shifted along its direction)."""
+    g = np.random.Generator(np.random.Philox(key=61))
+    count = 300
+    n = np.rint(np.exp(g.uniform(np.log(1024), np.log(20000), count))).astype(np.int64)
+    k = g.integers(1, 33, count)
+    users = inputs.users_polar(62, 1, int(k.sum()), (3.0, 30.0))[0]
+    arr = xl.array(1, LAM, None, 1.0, getattr(xl, model if model != "FSPL" else "FSPL_USW"))
+    out = {}
+    for pack in (0, 1):
+        plan = xl.BatchPlan(arr, n, k, np.zeros(count), np.ones(count), prec=3)
+        plan.set_tiling(8192, 1, 32, pack)
+        info = plan.info()
+        if pack:  # lanes bound the CTAs from below; packing leaves fewer CTAs than items
+            lanes = sum(int(k[i]) * -(-int(n[i]) // 8192) for i in range(count))
+            assert -(-lanes // 32) <= info["narrow_ctas"] < 0.7 * info["items"]
+        out[pack] = run_plan(xl, plan, users, np.full(int(k.sum()), 10.0))
+        offs = (plan.user_off.copy(), plan.gram_off.copy())
+        plan.close()
+    assert np.array_equal(out[0]["gram"], out[1]["gram"])
+    for i in (0, 1, count // 2, count - 1):
+        K, uo, go = int(k[i]), int(offs[0][i]), int(offs[1][i])
+        G = out[1]["gram"][go:go + K * K].reshape(1, K, K)
+        R = orc.gram(getattr(orc, model), int(n[i]), LAM, LAM / 2, 1.0, users[uo:uo + K][None])
+        assert normwise(G, R) <= 2e-5, (i, normwise(G, R))
