@@ -278,7 +278,7 @@ def ragged_bench(xl, torch, mufu_peak, count=1 << 14, tune=True):
             "receivers_and_rates_ms": ms - gram_ms, "channel_entries": int(entries),
             "plan": info, "plan_seconds": plan_s, "cuda_graph": True, "gram": "bf16x3",
             "roofline": {"bound": "alu", "achieved": achieved, "peak": mufu_peak, "unit": "Tops/s (MUFU)",
-                         "frac": achieved / mufu_peak, "kernel": "gram_tc_items_kernel",
+                         "frac": achieved / mufu_peak, "kernel": "gram_tc_items_kernel + gram_tc_packed_kernel",
                          "traffic": traffic_from_profile("gram_tc_items_kernel", entries),
                          "kernel_ms": gram_ms,
                          "algorithmic": "3 transcendental ops (rsqrt, sin, cos) x sum of N K channel entries",
