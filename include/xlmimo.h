@@ -438,9 +438,10 @@ typedef struct xlmimo_batch_plan_st* xlmimo_batch_plan;
  * element chunk) run one per CTA of the tensor-core Gram kernel, in one of two
  * tilings: the narrow one (M = 128, N = 64 MMAs over 32 user lanes, three CTAs
  * per SM) for instances with K up to the plan's narrow cut-off, the wide one
- * (M = N = 128 MMAs over 64 lanes, two CTAs per SM) for the others.  Narrow
- * work items whose user counts add up to at most 32 and whose lengths are
- * within 3/4 of one another may share one CTA's user lanes (packing).  If
+ * (M = N = 128 MMAs over 64 user slots, two CTAs per SM) for the others.
+ * With packing, narrow work items ride in the spare user slots of wide CTAs
+ * or share a narrow CTA's 32, when the user counts fit and the lengths are
+ * within 3/4 of the CTA's longest.  If
  * tune_users (device, packed [sum K][2]) is non-NULL the plan times
  * candidates on those users (Gram phase only) and keeps the fastest: element
  * chunks of 4096, 8192, 16384, 32768 and 131072 elements x the two launch
@@ -463,8 +464,8 @@ int xlmimo_batch_run(xlmimo_batch_plan plan, const double* users, const double* 
 /* Pin a plan's tiling, overriding the tuner: element chunk per work item (a
  * positive multiple of 128), launch mode (1 or 2, as in
  * xlmimo_batch_plan_info), narrow cut-off (0 to 32: instances with K up to it
- * on the narrow tiling, the others on the wide one) and pack (1: narrow items
- * share CTAs, 0: one per CTA).  Waits for the device to finish pending work
+ * on the narrow tiling, the others on the wide one) and pack (1: items share
+ * CTAs, 0: one per CTA).  Waits for the device to finish pending work
  * (runs may still read the plan's tables), then rebuilds the tables;
  * SYNCHRONOUS on `stream`.  The plan then reports tuned = 0. */
 int xlmimo_batch_plan_set_tiling(xlmimo_batch_plan plan, int64_t chunk, int mode, int narrow_kmax, int pack,
@@ -475,7 +476,7 @@ int xlmimo_batch_plan_set_tiling(xlmimo_batch_plan plan, int64_t chunk, int mode
  * launched one after the other, 2: both launches at once on two streams),
  * instances with K <= 32, instances with K > 32, workspace bytes, tuned
  * (0/1), candidates timed, narrow cut-off (largest K on the narrow tiling),
- * work items on the wide tiling, packing (0/1), CTAs of the narrow tiling}. */
+ * CTAs of the wide tiling, packing (0/1), CTAs of the narrow tiling}. */
 #define XLMIMO_PLAN_INFO_LEN 12
 int xlmimo_batch_plan_info(xlmimo_batch_plan plan, int64_t* info);
 

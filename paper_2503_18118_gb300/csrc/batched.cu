@@ -6,13 +6,14 @@
 // Work items are (instance, element chunk) pairs.  Items of instances with
 // K up to the plan's narrow cut-off (at most 32) run the narrow layout of
 // gram_engine.cuh (M = 128, N = 64 MMAs, 32 user lanes, three CTAs per SM),
-// the others the wide one (M = N = 128, 64 lanes, two CTAs per SM), one CTA
-// per wide item, each list ordered longest first so that the block scheduler
-// hands out the long items first.  Narrow items share CTAs: items whose user
-// counts add up to at most 32 and whose lengths lie within PACK_LEN_RATIO of
-// the CTA's longest are packed into one CTA's user lanes (the accumulator's
-// blocks between them are computed and dropped), since channel generation
-// costs per lane whatever the instance's K.  Every user's position is taken
+// the others the wide one (M = N = 128, 64 user slots, two CTAs per SM),
+// each list ordered longest first so that the block scheduler hands out the
+// long items first.  Items share CTAs: a narrow item rides in the spare user
+// slots of a wide CTA (64 - K of them, generated as padding otherwise) or
+// shares a narrow CTA's 32 lanes with others, when the user counts fit and
+// its length lies within PACK_LEN_RATIO of the CTA's longest (the
+// accumulator's blocks between members are computed and dropped), since
+// channel generation costs per user slot whatever the instance's K.  Every user's position is taken
 // relative to its own instance's first element (y + (N - 1) d / 2 for the
 // spherical models, the range shifted along the planar wave's direction for
 // UPW), so lanes of instances with different N share one array geometry.
@@ -31,19 +32,20 @@
 
 namespace xl {
 
+// A work item (host-side planning).
 struct DevItem {
     int inst, chunk;
     long long n0, n1;
 };
 
-// A narrow CTA: members [m0, m0 + nm) of the member list, the longest
+// A Gram CTA: members [m0, m0 + nm) of the member list, the longest
 // member's element count, over which its stages run.
 struct DevPack {
     int m0, nm;
     long long len;
 };
 
-// One narrow work item inside a CTA: its users occupy lanes lane0 ..
+// One work item inside a CTA: its users occupy user slots lane0 ..
 // lane0 + K - 1.
 struct DevMember {
     int inst, chunk;
@@ -51,9 +53,9 @@ struct DevMember {
     int lane0, pad;
 };
 
-// A narrow item joins a CTA whose longest item is at most 1/PACK_LEN_RATIO
-// times its own length (the lanes of the shorter one generate zeros for the
-// rest); larger gaps start a CTA of their own.
+// An item joins a CTA whose longest item is at most 1/PACK_LEN_RATIO times
+// its own length (the slots of the shorter one generate zeros for the rest);
+// larger gaps start a CTA of their own.
 constexpr double PACK_LEN_RATIO = 0.75;
 // A new narrow item is tried against the most recently opened CTAs only.
 constexpr int PACK_WINDOW = 64;
@@ -94,14 +96,17 @@ __global__ void ragged_user_kernel(Geom g, GenParams gp, const DevInst* __restri
     if (lane == 0) iflags[warp] = flags;
 }
 
-// One wide work item per CTA (longest first: the block scheduler hands them
-// out in that order as SMs free up), running the pipeline of gram_engine.cuh
-// on the item's element range; users come from the per-run set-up.
+// One CTA of either layout (KMAX user slots: 32 narrow, 64 wide): work items
+// side by side in the user slots, each slot over its own item's elements;
+// the accumulator is folded once and every member's diagonal block is written
+// to its instance's Gram (or chunk partial).  A member with an invalid user
+// gets NaN; a member with a user too close for the slice expansion takes the
+// whole CTA to the exact per-entry formula.
 template <int MODEL, int KMAX, int PREC>
 __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
-    gram_tc_items_kernel(Geom g, GenParams gp, const DevInst* __restrict__ insts, const DevItem* __restrict__ items,
-                         const RgUser* __restrict__ users, const int* __restrict__ iflags, double2* __restrict__ gram,
-                         double2* __restrict__ part) {
+    gram_tc_packed_kernel(Geom g, GenParams gp, const DevInst* __restrict__ insts, const DevPack* __restrict__ packs,
+                          const DevMember* __restrict__ members, const RgUser* __restrict__ users,
+                          const int* __restrict__ iflags, double2* __restrict__ gram, double2* __restrict__ part) {
     constexpr int NRING = KMAX == 32 ? 2 : 3;
     using E = GramEngine<MODEL, KMAX, PREC, false, NRING>;
     using SH = EngShared<KMAX, NRING>;
@@ -109,80 +114,7 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     SH* sh = reinterpret_cast<SH*>(base + NRING * E::BYTES);
     float* fold = reinterpret_cast<float*>(base);
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const DevItem itm = items[blockIdx.x];
-    const DevInst in = insts[itm.inst];
-    const int K = in.k;
-    if (tid == 0) {
-        eng_init_barriers(sh);
-        const int f = iflags[itm.inst];
-        sh->bad = f & 1;
-        sh->near = (f >> 1) & 1;
-    }
-    __syncthreads();
-    if (warp == 8) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
-                     "r"(2 * E::WCOLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    if (tid < KMAX) {
-        if (tid < K) {
-            const RgUser u = users[in.user_off + tid];
-            sh->ug[tid] = u.ug;
-            sh->fac[tid] = u.fac;
-        } else {
-            UserGeo pad = make_user_geo(g, 1.0, 0.0);  // padding user (1, 0), weight 0
-            pad.ampc = 0.f;
-            sh->ug[tid] = pad;
-            sh->fac[tid] = 1.0;
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = sh->tmem_base;
-    const int nst = E::stages(itm.n0, itm.n1);
-    if (warp < 8) {
-        E::generate(sh, smem_u32(base), tmem, g, gp, itm.n0, itm.n1, UraRows{0, 0.0, 0.0, 0}, 0, 0, 0, !sh->near);
-    } else {
-        if (lane == 0) E::mma(sh, smem_u32(base), tmem, nst, 0, 0);
-        __syncwarp();
-    }
-    bool ok = mbar_wait(&sh->done, 0, &sh->abort);
-    tc_fence_before();
-    __syncthreads();  // every MMA done and every drain's tcgen05.st complete
-    tc_fence_after();
-    ok = ok && !*(volatile int*)&sh->abort && !sh->bad;
-    double2* o = in.nchunks == 1 ? gram + in.gram_off : part + in.part_off + (long long)itm.chunk * K * K;
-    E::epilogue(sh, fold, tmem, K, E::drains(nst), ok, o, tid, warp, lane);
-    __syncthreads();
-    if (warp == 8) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * E::WCOLS) : "memory");
-    }
-}
-
-// One narrow CTA: several work items of instances with K <= 32 side by side
-// in the 32 user lanes, each lane over its own item's elements; the
-// accumulator is folded once and every member's diagonal block is written to
-// its instance's Gram (or chunk partial).  A member with an invalid user gets
-// NaN; a member with a user too close for the slice expansion takes the
-// whole CTA to the exact per-entry formula.
-template <int MODEL, int PREC>
-__global__ void __launch_bounds__(TC_THREADS, 3)
-    gram_tc_packed_kernel(Geom g, GenParams gp, const DevInst* __restrict__ insts, const DevPack* __restrict__ packs,
-                          const DevMember* __restrict__ members, const RgUser* __restrict__ users,
-                          const int* __restrict__ iflags, double2* __restrict__ gram, double2* __restrict__ part) {
-    constexpr int NRING = 2;
-    using E = GramEngine<MODEL, 32, PREC, false, NRING>;
-    using SH = EngShared<32, NRING>;
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    SH* sh = reinterpret_cast<SH*>(base + NRING * E::BYTES);
-    float* fold = reinterpret_cast<float*>(base);
-    __shared__ long long lane_n0[32], lane_len[32];
+    __shared__ long long lane_n0[KMAX], lane_len[KMAX];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const DevPack pk = packs[blockIdx.x];
@@ -193,7 +125,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
         sh->bad = 0;
         sh->near = near;
     }
-    if (tid < 32) {
+    if (tid < KMAX) {
         int mi = -1;
         for (int m = 0; m < pk.nm; ++m) {
             const DevMember mb = members[pk.m0 + m];
@@ -208,7 +140,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
             lane_len[tid] = mb.n1 - mb.n0;
         } else {
             // padding user (1, 0), weight 0, over the longest member's range so
-            // that its lane takes the same path through each stage as the others
+            // that its slot takes the same path through each stage as the others
             UserGeo pad = make_user_geo(g, 1.0, 0.0);
             pad.ampc = 0.f;
             sh->ug[tid] = pad;
@@ -295,14 +227,13 @@ struct BatchPlan {
     int64_t users_total = 0;
     std::vector<xlmimo_inst> host;
     DevInst* d_inst = nullptr;
-    DevItem* d_items = nullptr;     // the wide items, longest first
-    DevPack* d_packs = nullptr;     // the narrow CTAs, longest first
-    DevMember* d_members = nullptr; // their items
+    DevPack* d_packs = nullptr;     // the wide CTAs, then the narrow ones, each longest first
+    DevMember* d_members = nullptr; // their work items
     int* d_lists = nullptr;  // [receiver buckets by K (RG_BUCKETS) | split instances]
     double2* d_part = nullptr;
     RgUser* d_users = nullptr;  // per-user set-up, rewritten by every run
     int* d_iflags = nullptr;    // per-instance flags, rewritten by every run
-    int n_items = 0, n_wide = 0, n_small = 0, n_large = 0, n_split = 0;
+    int n_items = 0, n_wide = 0, n_small = 0, n_large = 0, n_split = 0;  // n_wide: CTAs of the wide tiling
     int n_bucket[6] = {0, 0, 0, 0, 0, 0};  // instances per receiver bucket
     int64_t chunk = 0;
     int narrow_kmax = 32;  // largest K on the narrow tile (0: every item on the wide one)
@@ -328,7 +259,6 @@ static void release_streams(BatchPlan* p) {
 
 static void free_tables(BatchPlan* p) {
     cudaFree(p->d_inst);
-    cudaFree(p->d_items);
     cudaFree(p->d_packs);
     cudaFree(p->d_members);
     cudaFree(p->d_lists);
@@ -336,7 +266,6 @@ static void free_tables(BatchPlan* p) {
     cudaFree(p->d_users);
     cudaFree(p->d_iflags);
     p->d_inst = nullptr;
-    p->d_items = nullptr;
     p->d_packs = nullptr;
     p->d_members = nullptr;
     p->d_lists = nullptr;
@@ -384,37 +313,40 @@ static int build_tables(BatchPlan* p, int64_t chunk, cudaStream_t st) {
         buckets[bk].push_back(i);
         di[i] = d;
     }
-    // wide items first, then narrow ones, each list longest first
+    // all items longest first, so that a CTA's first member is its longest.
+    // An item with K above the narrow cut-off opens a wide CTA (64 user
+    // slots); any other item goes to the most recent CTA (of the last
+    // PACK_WINDOW: the shortest) with slots to spare and a length within
+    // PACK_LEN_RATIO of it, a wide CTA's spare slots first (they are generated
+    // as padding anyway), else opens a narrow CTA (32 slots).  Without packing
+    // every item opens a CTA of its own kind.
     const int nk = p->narrow_kmax;
-    std::stable_sort(items.begin(), items.end(), [&](const DevItem& a, const DevItem& b) {
-        const bool wa = p->host[a.inst].k > nk, wb = p->host[b.inst].k > nk;
-        if (wa != wb) return wa;
-        return a.n1 - a.n0 > b.n1 - b.n0;
-    });
+    std::stable_sort(items.begin(), items.end(),
+                     [&](const DevItem& a, const DevItem& b) { return a.n1 - a.n0 > b.n1 - b.n0; });
     p->n_items = (int)items.size();
-    p->n_wide = (int)std::count_if(items.begin(), items.end(), [&](const DevItem& a) { return p->host[a.inst].k > nk; });
-    // narrow items into CTAs, longest first, so that a CTA's first member is
-    // its longest; each new item goes to the most recent CTA with lanes to
-    // spare and a length within PACK_LEN_RATIO of it (recent CTAs are the
-    // shortest), else opens one
-    std::vector<std::vector<DevMember>> bins;
-    std::vector<int> lanes_used;
-    std::vector<long long> bin_len;
-    for (size_t t = (size_t)p->n_wide; t < items.size(); ++t) {
-        const DevItem& it = items[t];
+    struct Bin {
+        std::vector<DevMember> m;
+        int used, cap;
+        long long len;
+    };
+    std::vector<Bin> bins;
+    for (const DevItem& it : items) {
         const int k = p->host[it.inst].k;
         const long long len = it.n1 - it.n0;
+        const bool wide = k > nk;
         int b = -1;
         if (p->pack)
-            for (int c = (int)bins.size() - 1; c >= 0 && c >= (int)bins.size() - PACK_WINDOW; --c)
-                if (lanes_used[c] + k <= 32 && (double)len >= PACK_LEN_RATIO * (double)bin_len[c]) {
-                    b = c;
-                    break;
+            for (int pass = 0; pass < 2 && b < 0; ++pass)  // wide CTAs first
+                for (int c = (int)bins.size() - 1; c >= 0 && c >= (int)bins.size() - PACK_WINDOW; --c) {
+                    const Bin& x = bins[c];
+                    if ((x.cap == 64) != (pass == 0) || (wide && x.cap != 64)) continue;
+                    if (x.used + k <= x.cap && (double)len >= PACK_LEN_RATIO * (double)x.len) {
+                        b = c;
+                        break;
+                    }
                 }
         if (b < 0) {
-            bins.emplace_back();
-            lanes_used.push_back(0);
-            bin_len.push_back(len);
+            bins.push_back(Bin{{}, 0, wide ? 64 : 32, len});
             b = (int)bins.size() - 1;
         }
         DevMember m;
@@ -422,22 +354,26 @@ static int build_tables(BatchPlan* p, int64_t chunk, cudaStream_t st) {
         m.chunk = it.chunk;
         m.n0 = it.n0;
         m.n1 = it.n1;
-        m.lane0 = lanes_used[b];
+        m.lane0 = bins[b].used;
         m.pad = 0;
-        bins[b].push_back(m);
-        lanes_used[b] += k;
+        bins[b].m.push_back(m);
+        bins[b].used += k;
     }
+    // the wide CTAs, then the narrow ones, each in the order opened (longest first)
     std::vector<DevPack> packs;
     std::vector<DevMember> members;
-    for (size_t b = 0; b < bins.size(); ++b) {
-        DevPack pk;
-        pk.m0 = (int)members.size();
-        pk.nm = (int)bins[b].size();
-        pk.len = bin_len[b];
-        packs.push_back(pk);
-        members.insert(members.end(), bins[b].begin(), bins[b].end());
-    }
-    p->n_packs = (int)packs.size();
+    for (int cap : {64, 32})
+        for (const Bin& x : bins)
+            if (x.cap == cap) {
+                DevPack pk;
+                pk.m0 = (int)members.size();
+                pk.nm = (int)x.m.size();
+                pk.len = x.len;
+                packs.push_back(pk);
+                members.insert(members.end(), x.m.begin(), x.m.end());
+            }
+    p->n_wide = (int)std::count_if(bins.begin(), bins.end(), [](const Bin& x) { return x.cap == 64; });
+    p->n_packs = (int)packs.size() - p->n_wide;
     p->n_small = (int)small.size();
     p->n_large = (int)large.size();
     p->n_split = (int)split.size();
@@ -453,7 +389,6 @@ static int build_tables(BatchPlan* p, int64_t chunk, cudaStream_t st) {
     }
     lists.insert(lists.end(), split.begin(), split.end());
     int rc = cuda_status(cudaMalloc((void**)&p->d_inst, sizeof(DevInst) * di.size()), "plan tables");
-    if (!rc) rc = cuda_status(cudaMalloc((void**)&p->d_items, sizeof(DevItem) * std::max<size_t>(1, items.size())), "plan tables");
     if (!rc) rc = cuda_status(cudaMalloc((void**)&p->d_packs, sizeof(DevPack) * std::max<size_t>(1, packs.size())), "plan tables");
     if (!rc) rc = cuda_status(cudaMalloc((void**)&p->d_members, sizeof(DevMember) * std::max<size_t>(1, members.size())), "plan tables");
     if (!rc) rc = cuda_status(cudaMalloc((void**)&p->d_users, sizeof(RgUser) * std::max<int64_t>(1, p->users_total)),
@@ -462,7 +397,6 @@ static int build_tables(BatchPlan* p, int64_t chunk, cudaStream_t st) {
     if (!rc) rc = cuda_status(cudaMalloc((void**)&p->d_lists, sizeof(int) * std::max<size_t>(1, lists.size())), "plan tables");
     if (!rc && part > 0) rc = cuda_status(cudaMalloc((void**)&p->d_part, p->part_bytes), "plan workspace");
     if (!rc) rc = cuda_status(cudaMemcpyAsync(p->d_inst, di.data(), sizeof(DevInst) * di.size(), cudaMemcpyHostToDevice, st), "plan upload");
-    if (!rc) rc = cuda_status(cudaMemcpyAsync(p->d_items, items.data(), sizeof(DevItem) * items.size(), cudaMemcpyHostToDevice, st), "plan upload");
     if (!rc && !packs.empty())
         rc = cuda_status(cudaMemcpyAsync(p->d_packs, packs.data(), sizeof(DevPack) * packs.size(), cudaMemcpyHostToDevice, st), "plan upload");
     if (!rc && !members.empty())
@@ -474,8 +408,6 @@ static int build_tables(BatchPlan* p, int64_t chunk, cudaStream_t st) {
     return rc;
 }
 
-using RgKernel = void (*)(Geom, GenParams, const DevInst*, const DevItem*, const RgUser*, const int*, double2*,
-                          double2*);
 using RuKernel = void (*)(Geom, GenParams, const DevInst*, int, const double*, RgUser*, int*);
 
 template <int MODEL>
@@ -489,35 +421,22 @@ static RuKernel ru_pick(int model, int prec) {
                                  : ru_pick_prec<XLMIMO_FSPL_USW>(prec);
 }
 
-template <int MODEL>
-static RgKernel rg_pick_prec(int prec) {
-    return prec == XLMIMO_BF16 ? gram_tc_items_kernel<MODEL, 64, TCP_BF16>
-         : prec == XLMIMO_F16X3 ? gram_tc_items_kernel<MODEL, 64, TCP_F16X3>
-                                : gram_tc_items_kernel<MODEL, 64, TCP_BF16X3>;
-}
-
-// the wide items' kernel
-static RgKernel rg_pick(int model, int prec) {
-    return model == XLMIMO_PNUSW ? rg_pick_prec<XLMIMO_PNUSW>(prec)
-         : model == XLMIMO_UPW   ? rg_pick_prec<XLMIMO_UPW>(prec)
-                                 : rg_pick_prec<XLMIMO_FSPL_USW>(prec);
-}
-
 using RpKernel = void (*)(Geom, GenParams, const DevInst*, const DevPack*, const DevMember*, const RgUser*, const int*,
                           double2*, double2*);
 
-template <int MODEL>
+template <int MODEL, int KMAX>
 static RpKernel rp_pick_prec(int prec) {
-    return prec == XLMIMO_BF16 ? gram_tc_packed_kernel<MODEL, TCP_BF16>
-         : prec == XLMIMO_F16X3 ? gram_tc_packed_kernel<MODEL, TCP_F16X3>
-                                : gram_tc_packed_kernel<MODEL, TCP_BF16X3>;
+    return prec == XLMIMO_BF16 ? gram_tc_packed_kernel<MODEL, KMAX, TCP_BF16>
+         : prec == XLMIMO_F16X3 ? gram_tc_packed_kernel<MODEL, KMAX, TCP_F16X3>
+                                : gram_tc_packed_kernel<MODEL, KMAX, TCP_BF16X3>;
 }
 
-// the narrow CTAs' kernel
+// the Gram kernel of the narrow (KMAX = 32) or the wide (64) tiling
+template <int KMAX>
 static RpKernel rp_pick(int model, int prec) {
-    return model == XLMIMO_PNUSW ? rp_pick_prec<XLMIMO_PNUSW>(prec)
-         : model == XLMIMO_UPW   ? rp_pick_prec<XLMIMO_UPW>(prec)
-                                 : rp_pick_prec<XLMIMO_FSPL_USW>(prec);
+    return model == XLMIMO_PNUSW ? rp_pick_prec<XLMIMO_PNUSW, KMAX>(prec)
+         : model == XLMIMO_UPW   ? rp_pick_prec<XLMIMO_UPW, KMAX>(prec)
+                                 : rp_pick_prec<XLMIMO_FSPL_USW, KMAX>(prec);
 }
 
 template <int KMAX>
@@ -530,10 +449,10 @@ static size_t items_smem() {
 // Kernel attributes and the second stream of the concurrent mode (at plan
 // time, outside any stream capture).
 static int prepare_gram(BatchPlan* p) {
-    int rc = cuda_status(cudaFuncSetAttribute(rp_pick(p->g.model, p->prec),
+    int rc = cuda_status(cudaFuncSetAttribute(rp_pick<32>(p->g.model, p->prec),
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)items_smem<32>()),
                          "ragged attribute");
-    if (!rc) rc = cuda_status(cudaFuncSetAttribute(rg_pick(p->g.model, p->prec),
+    if (!rc) rc = cuda_status(cudaFuncSetAttribute(rp_pick<64>(p->g.model, p->prec),
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)items_smem<64>()),
                               "ragged attribute");
     if (!rc && !p->side) rc = cuda_status(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking), "plan stream");
@@ -562,11 +481,12 @@ static int run_gram(BatchPlan* p, const double* users, double* gram, cudaStream_
         sn = p->side;
     }
     if (p->n_wide > 0)
-        rg_pick(p->g.model, p->prec)<<<p->n_wide, TC_THREADS, items_smem<64>(), st>>>(
-            p->g, gp, p->d_inst, p->d_items, p->d_users, p->d_iflags, (double2*)gram, p->d_part);
-    if (n_narrow > 0)
-        rp_pick(p->g.model, p->prec)<<<n_narrow, TC_THREADS, items_smem<32>(), sn>>>(
+        rp_pick<64>(p->g.model, p->prec)<<<p->n_wide, TC_THREADS, items_smem<64>(), st>>>(
             p->g, gp, p->d_inst, p->d_packs, p->d_members, p->d_users, p->d_iflags, (double2*)gram, p->d_part);
+    if (n_narrow > 0)
+        rp_pick<32>(p->g.model, p->prec)<<<n_narrow, TC_THREADS, items_smem<32>(), sn>>>(
+            p->g, gp, p->d_inst, p->d_packs + p->n_wide, p->d_members, p->d_users, p->d_iflags, (double2*)gram,
+            p->d_part);
     rc = cuda_status(cudaGetLastError(), "ragged gram launch");
     if (!rc && sn != st) {
         rc = cuda_status(cudaEventRecord(p->join, sn), "plan join");

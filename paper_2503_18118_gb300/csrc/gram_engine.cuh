@@ -239,16 +239,16 @@ struct GramEngine {
 
     // Generator warps 0-7 over the item's elements [nbeg, nend).  gs0 / gd0:
     // stages and drains of the CTA before this item.  Returns true if a wait
-    // gave up.  PACKED (narrow layout only): the user lanes belong to
-    // instances of their own; lane k's elements are lane_n0[k] + [0,
-    // lane_len[k]) (the stages cover the longest, shorter lanes generate
-    // zeros past their end), nbeg = 0 and nend = the longest length.
+    // gave up.  PACKED: the user slots belong to instances of their own; slot
+    // k's elements are lane_n0[k] + [0, lane_len[k]) (the stages cover the
+    // longest, shorter slots generate zeros past their end), nbeg = 0 and
+    // nend = the longest length.
     template <class SH, bool PACKED = false>
     static __device__ __forceinline__ bool generate(SH* sh, uint32_t sbase, uint32_t tmem, const Geom& g, const GenParams& gp,
                                     int64_t nbeg, int64_t nend, const UraRows& ura, int gs0, int gd0, int gsp0,
                                     bool fast, const long long* lane_n0 = nullptr,
                                     const long long* lane_len = nullptr) {
-        static_assert(!PACKED || (KMAX == 32 && !URA), "packed lanes: narrow ULA layout only");
+        static_assert(!PACKED || !URA, "packed user slots: ULA only");
         // the thread's coordinates read afresh (an opaque read): in a
         // persistent kernel the values derived from them below are then made
         // per item instead of being hoisted across the whole item loop, where
@@ -365,13 +365,18 @@ struct GramEngine {
                     dead = true;
                     continue;
                 }
-                int rem = it == nst - 1 ? last_rem : T;  // valid elements from this warp's first slice on
-                if (PACKED) {
-                    const long long li = lane_len[lane] - (long long)it * T;  // this lane's elements from the stage on
-                    rem = li >= T ? T : (int)max(li, -(long long)T) - warp * 8;
-                }
+                const int rem = it == nst - 1 ? last_rem : T;  // valid elements from this warp's first slice on
                 const uint32_t sb = sbase + (uint32_t)cur * BYTES;
-                const int rem0 = rem, rem1 = KMAX == 32 ? rem - TC_T : rem;
+                int rem0 = rem, rem1 = KMAX == 32 ? rem - TC_T : rem;
+                if (PACKED) {
+                    // slot k's elements from this warp's first slice of the stage on
+                    auto rem_of = [&](int k) {
+                        const long long li = lane_len[k] - (long long)it * T;
+                        return li >= T ? T : (int)max(li, -(long long)T) - warp * 8;
+                    };
+                    rem0 = rem_of(lane);
+                    rem1 = KMAX == 32 ? rem0 - TC_T : rem_of(lane + 32);
+                }
                 const int k1 = KMAX == 32 ? lane : lane + 32;
                 SliceCo co;
                 if (FAST)

@@ -445,7 +445,7 @@ class BatchPlan:
         v = (ctypes.c_int64 * PLAN_INFO_LEN)()
         _check(lib().xlmimo_batch_plan_info(self._h, v))
         keys = ("items", "chunk", "mode", "small", "large", "workspace_bytes", "tuned", "candidates", "narrow_kmax",
-                "wide_items", "pack", "narrow_ctas")
+                "wide_ctas", "pack", "narrow_ctas")
         return dict(zip(keys, list(v)))
 
     def close(self):

@@ -124,7 +124,8 @@ def test_batch_graph_capture_and_autotune(xl):
     assert info["tuned"] == 1 and info["candidates"] == 13 and info["pack"] in (0, 1)
     assert info["chunk"] in (4096, 8192, 16384, 32768, 131072) and info["mode"] in (1, 2)
     assert info["narrow_kmax"] in (0, 16, 32)
-    assert info["wide_items"] == sum(-(-int(n[i]) // info["chunk"]) for i in range(len(k)) if k[i] > info["narrow_kmax"])
+    wide_items = sum(-(-int(n[i]) // info["chunk"]) for i in range(len(k)) if k[i] > info["narrow_kmax"])
+    assert info["wide_ctas"] == wide_items if (not info["pack"] or info["narrow_kmax"] == 32) else info["wide_ctas"] <= wide_items
     P = dev(snr)
     out = dict(gram=torch.empty(plan.gram_total, dtype=torch.complex128, device="cuda"),
                sinr=torch.empty(plan.users_total, dtype=torch.float64, device="cuda"),
@@ -224,8 +225,9 @@ def test_pinned_tilings_match_oracle(xl, orc, narrow_kmax, pack):
     info = plan.info()
     assert info["narrow_kmax"] == narrow_kmax and info["chunk"] == 8192 and info["mode"] == 2 and info["pack"] == pack
     narrow = sum(-(-int(n[i]) // 8192) for i in range(len(k)) if k[i] <= narrow_kmax)
-    assert (info["narrow_ctas"] == narrow) if not pack else (0 < info["narrow_ctas"] <= narrow or narrow == 0)
-    assert info["wide_items"] == sum(-(-int(n[i]) // 8192) for i in range(len(k)) if k[i] > narrow_kmax)
+    assert (info["narrow_ctas"] == narrow) if not pack else info["narrow_ctas"] <= narrow
+    wide = sum(-(-int(n[i]) // 8192) for i in range(len(k)) if k[i] > narrow_kmax)
+    assert info["wide_ctas"] == wide if (not pack or narrow_kmax == 32) else 0 < info["wide_ctas"] <= wide
     out = run_plan(xl, plan, users, np.full(int(k.sum()), 10.0))
     for i in range(len(k)):
         K, uo, go = int(k[i]), int(plan.user_off[i]), int(plan.gram_off[i])
@@ -267,4 +269,39 @@ def test_packed_narrow_items_match_unpacked(xl, orc, model):
         K, uo, go = int(k[i]), int(offs[0][i]), int(offs[1][i])
         G = out[1]["gram"][go:go + K * K].reshape(1, K, K)
         R = orc.gram(getattr(orc, model), int(n[i]), LAM, LAM / 2, 1.0, users[uo:uo + K][None])
+        assert normwise(G, R) <= 2e-5, (i, normwise(G, R))
+
+
+def test_narrow_items_in_wide_ctas(xl, orc):
+    """With K from 1 to 64, packing puts narrow items (K <= 32) into the spare
+    user slots of wide CTAs (64 - K of them) before opening narrow CTAs: far
+    fewer narrow CTAs than narrow items, and every instance's Gram still the
+    oracle's; items computed in a wide CTA go through the wide layout's MMAs,
+    so against the one-item-per-CTA plan they agree to the tensor-core class,
+    not bit for bit."""
+    g = np.random.Generator(np.random.Philox(key=63))
+    count = 240
+    n = np.rint(np.exp(g.uniform(np.log(1024), np.log(20000), count))).astype(np.int64)
+    k = g.integers(1, 65, count)
+    users = inputs.users_polar(64, 1, int(k.sum()), (3.0, 30.0))[0]
+    arr = xl.array(1, LAM)
+    out, info = {}, {}
+    for pack in (0, 1):
+        plan = xl.BatchPlan(arr, n, k, np.zeros(count), np.ones(count), prec=3)
+        plan.set_tiling(8192, 2, 32, pack)
+        info[pack] = plan.info()
+        out[pack] = run_plan(xl, plan, users, np.full(int(k.sum()), 10.0))
+        offs = (plan.user_off.copy(), plan.gram_off.copy())
+        plan.close()
+    assert info[1]["wide_ctas"] == info[0]["wide_ctas"]  # wide items never share
+    assert info[1]["narrow_ctas"] < 0.5 * info[0]["narrow_ctas"]
+    for i in range(count):
+        K, go = int(k[i]), int(offs[1][i])
+        a = out[1]["gram"][go:go + K * K].reshape(1, K, K)
+        b = out[0]["gram"][go:go + K * K].reshape(1, K, K)
+        assert normwise(a, b) <= 1e-5, i
+    for i in (0, 1, count // 3, count // 2, count - 1):
+        K, uo, go = int(k[i]), int(offs[0][i]), int(offs[1][i])
+        G = out[1]["gram"][go:go + K * K].reshape(1, K, K)
+        R = orc.gram(orc.FSPL, int(n[i]), LAM, LAM / 2, 1.0, users[uo:uo + K][None])
         assert normwise(G, R) <= 2e-5, (i, normwise(G, R))
