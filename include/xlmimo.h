@@ -462,7 +462,7 @@ int xlmimo_batch_run(xlmimo_batch_plan plan, const double* users, const double* 
                      double* gram, double* sinr, int32_t* status, double* rate, void* stream);
 
 /* Pin a plan's tiling, overriding the tuner: element chunk per work item (a
- * positive multiple of 128), launch mode (1 or 2, as in
+ * positive multiple of 128 up to 2^30), launch mode (1 or 2, as in
  * xlmimo_batch_plan_info), narrow cut-off (0 to 32: instances with K up to it
  * on the narrow tiling, the others on the wide one) and pack (1: items share
  * CTAs, 0: one per CTA).  Waits for the device to finish pending work

@@ -114,7 +114,8 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     SH* sh = reinterpret_cast<SH*>(base + NRING * E::BYTES);
     float* fold = reinterpret_cast<float*>(base);
-    __shared__ long long lane_n0[KMAX], lane_len[KMAX];
+    __shared__ long long lane_n0[KMAX];
+    __shared__ int lane_len[KMAX];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const DevPack pk = packs[blockIdx.x];
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
             sh->ug[tid] = u.ug;
             sh->fac[tid] = u.fac;
             lane_n0[tid] = mb.n0;
-            lane_len[tid] = mb.n1 - mb.n0;
+            lane_len[tid] = (int)(mb.n1 - mb.n0);
         } else {
             // padding user (1, 0), weight 0, over the longest member's range so
             // that its slot takes the same path through each stage as the others
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(TC_THREADS, KMAX == 32 ? 3 : 2)
             sh->ug[tid] = pad;
             sh->fac[tid] = 1.0;
             lane_n0[tid] = 0;
-            lane_len[tid] = pk.len;
+            lane_len[tid] = (int)pk.len;
         }
     }
     __syncthreads();
@@ -647,9 +648,9 @@ extern "C" int xlmimo_batch_plan_set_tiling(xlmimo_batch_plan plan, int64_t chun
                                             int pack, void* stream) {
     clear_error();
     if (!plan) { set_error("plan must be non-NULL"); return XLMIMO_EINVAL; }
-    if (chunk < 128 || chunk % 128 != 0 || chunk > (int64_t(1) << 40) || (mode != 1 && mode != 2) || narrow_kmax < 0 ||
+    if (chunk < 128 || chunk % 128 != 0 || chunk > (int64_t(1) << 30) || (mode != 1 && mode != 2) || narrow_kmax < 0 ||
         narrow_kmax > 32 || (pack != 0 && pack != 1)) {
-        set_error("tiling: chunk a positive multiple of 128, mode 1 or 2, narrow cut-off in [0, 32], pack 0 or 1");
+        set_error("tiling: chunk a positive multiple of 128 up to 2^30, mode 1 or 2, narrow cut-off in [0, 32], pack 0 or 1");
         return XLMIMO_EINVAL;
     }
     BatchPlan* p = &plan->p;

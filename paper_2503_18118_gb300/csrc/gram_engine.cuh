@@ -246,8 +246,7 @@ struct GramEngine {
     template <class SH, bool PACKED = false>
     static __device__ __forceinline__ bool generate(SH* sh, uint32_t sbase, uint32_t tmem, const Geom& g, const GenParams& gp,
                                     int64_t nbeg, int64_t nend, const UraRows& ura, int gs0, int gd0, int gsp0,
-                                    bool fast, const long long* lane_n0 = nullptr,
-                                    const long long* lane_len = nullptr) {
+                                    bool fast, const long long* lane_n0 = nullptr, const int* lane_len = nullptr) {
         static_assert(!PACKED || !URA, "packed user slots: ULA only");
         // the thread's coordinates read afresh (an opaque read): in a
         // persistent kernel the values derived from them below are then made
@@ -331,6 +330,9 @@ struct GramEngine {
         // the stage loop, with the slice expansion (FAST) or the exact
         // per-entry formula; CTA-uniform, so each loop keeps its own
         // registers.  Returns whether a wait gave up.
+        // packed: the lengths of this thread's user slots (slot lane, and lane + 32 wide)
+        const int len0 = PACKED ? lane_len[lane] : 0;
+        const int len1 = PACKED && KMAX == 64 ? lane_len[lane + 32] : 0;
         auto gen_loop = [&](auto fast_tag) -> bool {
             constexpr bool FAST = decltype(fast_tag)::value;
             bool dead = false;
@@ -370,12 +372,15 @@ struct GramEngine {
                 int rem0 = rem, rem1 = KMAX == 32 ? rem - TC_T : rem;
                 if (PACKED) {
                     // slot k's elements from this warp's first slice of the stage on
-                    auto rem_of = [&](int k) {
-                        const long long li = lane_len[k] - (long long)it * T;
-                        return li >= T ? T : (int)max(li, -(long long)T) - warp * 8;
-                    };
-                    rem0 = rem_of(lane);
-                    rem1 = KMAX == 32 ? rem0 - TC_T : rem_of(lane + 32);
+                    // (item lengths below 2^31)
+                    const int e0 = len0 - it * T;
+                    rem0 = e0 >= T ? T : max(e0, -T) - warp * 8;
+                    if (KMAX == 64) {
+                        const int e1 = len1 - it * T;
+                        rem1 = e1 >= T ? T : max(e1, -T) - warp * 8;
+                    } else {
+                        rem1 = rem0 - TC_T;
+                    }
                 }
                 const int k1 = KMAX == 32 ? lane : lane + 32;
                 SliceCo co;
