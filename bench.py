@@ -183,13 +183,13 @@ PROFILE_SOURCES = {
     "gram_f64_kernel": ["gram_simt.cu", "chan_gen.cuh", "common.cuh"],
     "mlp_infer_tc_kernel": ["mlp_tc.cu", "mlp_common.cuh", "tc_common.cuh", "common.cuh"],
     "gram_hilo_kernel": ["bounds.cu", "gram_hilo_tc.cuh", "gen_tc.cuh", "tc_common.cuh", "chan_gen.cuh", "common.cuh"],
-    "gram_tc_items_kernel": ["batched.cu", "gram_engine.cuh", "gen_tc.cuh", "tc_common.cuh", "chan_gen.cuh",
+    "gram_tc_packed_kernel": ["batched.cu", "gram_engine.cuh", "gen_tc.cuh", "tc_common.cuh", "chan_gen.cuh",
                               "common.cuh"],
 }
 PROFILE_OF_KERNEL = {"gram_tc_kernel": "gram_tc_kernel_headline.md", "gram_f32_kernel": "gram_f32_kernel_headline.md",
                      "gram_f64_kernel": "gram_f64_kernel_headline.md",
                      "mlp_infer_tc_kernel": "mlp_infer_tc_kernel_surrogate.md",
-                     "gram_tc_items_kernel": "gram_tc_items_kernel_ragged.md",
+                     "gram_tc_packed_kernel": "gram_tc_packed_kernel_ragged.md",
                      "gram_hilo_kernel": "bounds_appendix_a.md"}
 
 
@@ -278,8 +278,8 @@ def ragged_bench(xl, torch, mufu_peak, count=1 << 14, tune=True):
             "receivers_and_rates_ms": ms - gram_ms, "channel_entries": int(entries),
             "plan": info, "plan_seconds": plan_s, "cuda_graph": True, "gram": "bf16x3",
             "roofline": {"bound": "alu", "achieved": achieved, "peak": mufu_peak, "unit": "Tops/s (MUFU)",
-                         "frac": achieved / mufu_peak, "kernel": "gram_tc_items_kernel + gram_tc_packed_kernel",
-                         "traffic": traffic_from_profile("gram_tc_items_kernel", entries),
+                         "frac": achieved / mufu_peak, "kernel": "gram_tc_packed_kernel (both tilings)",
+                         "traffic": traffic_from_profile("gram_tc_packed_kernel", entries),
                          "kernel_ms": gram_ms,
                          "algorithmic": "3 transcendental ops (rsqrt, sin, cos) x sum of N K channel entries",
                          "peak_source": "measured sin/cos MUFU throughput (xlmimo_measure_pipe), of measured"}}

@@ -31,4 +31,4 @@ def test_profile_summaries_parse():
 def test_source_hash_changes_with_sources():
     h = bench.source_hash("gram_tc_kernel")
     assert re.fullmatch(r"[0-9a-f]{64}", h)
-    assert h != bench.source_hash("gram_tc_items_kernel")
+    assert h != bench.source_hash("gram_tc_packed_kernel")
