@@ -305,3 +305,35 @@ def test_narrow_items_in_wide_ctas(xl, orc):
         G = out[1]["gram"][go:go + K * K].reshape(1, K, K)
         R = orc.gram(orc.FSPL, int(n[i]), LAM, LAM / 2, 1.0, users[uo:uo + K][None])
         assert normwise(G, R) <= 2e-5, (i, normwise(G, R))
+
+
+def test_packed_ctas_isolate_invalid_and_near_members(xl, orc):
+    """Small instances of similar length pack into shared CTAs (K = 1 ones up to
+    32 to a CTA).  One member has an invalid user (x <= 0): its own Gram is NaN
+    and its neighbours in the CTA are unaffected; another has a user too close
+    to the array for the slice expansion (x = 0.3 m, below 200 wavelengths at
+    100 GHz), which takes its whole CTA to the exact per-entry formula: every
+    valid instance still gives the oracle's Gram."""
+    g = np.random.Generator(np.random.Philox(key=65))
+    count = 48
+    k = np.concatenate([np.ones(16, dtype=np.int64), g.integers(2, 9, count - 16)])
+    n = g.integers(3000, 3600, count)
+    users = inputs.users_polar(66, 1, int(k.sum()), (3.0, 30.0))[0]
+    plan = xl.BatchPlan(xl.array(1, LAM), n, k, np.zeros(count), np.ones(count), prec=3)
+    plan.set_tiling(8192, 2, 32, 1)
+    info = plan.info()
+    assert info["narrow_ctas"] <= count // 4  # a few CTAs hold them all
+    bad, near = 20, 30
+    users[plan.user_off[bad]] = (-1.0, 2.0)
+    users[plan.user_off[near]] = (0.3, 0.1)
+    out = run_plan(xl, plan, users, np.full(int(k.sum()), 10.0))
+    for i in range(count):
+        K, uo, go = int(k[i]), int(plan.user_off[i]), int(plan.gram_off[i])
+        G = out["gram"][go:go + K * K].reshape(1, K, K)
+        if i == bad:
+            assert np.isnan(G).all()
+            continue
+        assert np.isfinite(G).all(), i
+        R = orc.gram(orc.FSPL, int(n[i]), LAM, LAM / 2, 1.0, users[uo:uo + K][None])
+        assert normwise(G, R) <= 2e-5, (i, normwise(G, R))
+    plan.close()
