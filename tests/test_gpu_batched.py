@@ -337,3 +337,26 @@ def test_packed_ctas_isolate_invalid_and_near_members(xl, orc):
         R = orc.gram(orc.FSPL, int(n[i]), LAM, LAM / 2, 1.0, users[uo:uo + K][None])
         assert normwise(G, R) <= 2e-5, (i, normwise(G, R))
     plan.close()
+
+
+def test_set_tiling_validates_and_keeps_the_plan(xl):
+    """set_tiling refuses a chunk that is not a positive multiple of 128 (or
+    above 2^30), a launch mode other than 1 or 2, a narrow cut-off outside
+    [0, 32] and a pack flag other than 0 or 1, leaving the plan's tiling as it
+    was; a valid call rebuilds the tables and reports the plan untuned."""
+    import ctypes
+    n = np.array([5000, 3000, 9000])
+    k = np.array([40, 7, 20])
+    plan = xl.BatchPlan(xl.array(1, LAM), n, k, np.zeros(3), np.ones(3))
+    before = plan.info()
+    L = xl.lib()
+    for chunk, mode, nk, pack in ((100, 2, 32, 1), (0, 2, 32, 1), ((1 << 30) + 128, 2, 32, 1), (8192, 3, 32, 1),
+                                  (8192, 2, 33, 1), (8192, 2, -1, 1), (8192, 2, 32, 2)):
+        rc = L.xlmimo_batch_plan_set_tiling(plan._h, ctypes.c_int64(chunk), mode, nk, pack, None)
+        assert rc == 1, (chunk, mode, nk, pack)
+        assert plan.info() == before
+    plan.set_tiling(4096, 1, 16, 0)
+    info = plan.info()
+    assert (info["chunk"], info["mode"], info["narrow_kmax"], info["pack"], info["tuned"]) == (4096, 1, 16, 0, 0)
+    assert info["items"] == sum(-(-int(x) // 4096) for x in n)
+    plan.close()
