@@ -108,6 +108,14 @@ typedef enum { XLMIMO_ZF = 0, XLMIMO_MMSE = 1, XLMIMO_MRC = 2, XLMIMO_ZF_DL = 3 
 /* OR-ed into the scheme of xlmimo_beamform: the mismatched SINR from the
  * FP32 correction (see xlmimo_beamform).  No effect on matched receivers. */
 #define XLMIMO_MISMATCH_FP32 0x100
+/* OR-ed into the scheme of a matched receiver (gram_true NULL or equal to
+ * gram_filter): its Cholesky factorisation in double-float on the FP32 pipe
+ * (~2^-48 relative), in FP64 when a pivot falls below 2^-16 of its diagonal
+ * entry (an ill-conditioned system: closely spaced users), the rule that the
+ * mismatched filter always follows.  Ignored where the capacity is asked for
+ * (its log-determinant comes from FP64 pivots).  The ragged batch's receivers
+ * take it. */
+#define XLMIMO_FACTOR_FF 0x200
 
 /* How beamform() reads `power`:
  *   XLMIMO_POWER_ABS    power[b][k] is the transmit power p_k.

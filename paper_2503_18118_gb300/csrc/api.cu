@@ -193,7 +193,7 @@ int xlmimo_beamform(const double* gram_filter, const double* gram_true, const do
     clear_error();
     int rc = check_kb(K, B);
     if (rc) return rc;
-    const int base = scheme & ~XLMIMO_MISMATCH_FP32;
+    const int base = scheme & ~(XLMIMO_MISMATCH_FP32 | XLMIMO_FACTOR_FF);
     if (base < XLMIMO_ZF || base > XLMIMO_ZF_DL) { set_error("unknown scheme %d", scheme); return XLMIMO_EINVAL; }
     if (power_mode != XLMIMO_POWER_ABS && power_mode != XLMIMO_POWER_RXSNR) {
         set_error("unknown power mode %d", power_mode);

@@ -288,7 +288,8 @@ static int build_tables(BatchPlan* p, int64_t chunk, cudaStream_t st) {
         DevInst d;
         d.n_ant = h.n_ant;
         d.k = h.k;
-        d.scheme = h.scheme;
+        // the receivers factor in double-float, in FP64 for an ill-conditioned system
+        d.scheme = h.scheme | XLMIMO_FACTOR_FF;
         d.user_off = h.user_off;
         d.gram_off = h.gram_off;
         d.noise = h.noise;

@@ -915,7 +915,10 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
     __shared__ double cs;
     const int tid = threadIdx.x, nt = blockDim.x;
     const bool fp32_corr = (scheme & XLMIMO_MISMATCH_FP32) != 0;
-    scheme &= ~XLMIMO_MISMATCH_FP32;
+    // a matched receiver factored in double-float (FP64 for an ill-conditioned
+    // system), unless the capacity needs the FP64 pivots
+    const bool ff_factor = (scheme & XLMIMO_FACTOR_FF) != 0 && cap_t == nullptr;
+    scheme &= ~(XLMIMO_MISMATCH_FP32 | XLMIMO_FACTOR_FF);
     bool m_in_z = false;  // M in Z in double-float (else in X in FP64, from Gauss-Jordan)
     if (tid < 32) {
         const double c = trial_scale(gf, gt, K);
@@ -954,9 +957,10 @@ __device__ void beamform_trial(const double2* __restrict__ gf, const double2* __
     } else {
         int ok;
         bool z_ff = false;  // the factor in Z is double-float
-        if (!matched) {
-            // the filter of a mismatched receiver: double-float factorisation,
-            // FP64 when a pivot shows it ill-conditioned (dg is free here)
+        if (!matched || ff_factor) {
+            // the filter of a mismatched receiver (and a matched one with
+            // XLMIMO_FACTOR_FF): double-float factorisation, FP64 when a pivot
+            // shows it ill-conditioned (dg is free here)
             float* d0 = reinterpret_cast<float*>(dg);
             load_lower_ff(reinterpret_cast<cf*>(Z), gf, K, scheme == XLMIMO_MMSE ? sp : nullptr, c, d0);
             __syncthreads();
@@ -1180,7 +1184,7 @@ int launch_beamform(const double* gf, const double* gt, const double* power, con
         return cuda_status(cudaGetLastError(), "beamform launch");
     }
     size_t smem = (2 * KK + K) * sizeof(cd) + 2 * XLMIMO_MAX_USERS * sizeof(double);
-    if ((scheme & ~XLMIMO_MISMATCH_FP32) == XLMIMO_ZF_DL) smem += BF_DL_EXTRA;
+    if ((scheme & ~(XLMIMO_MISMATCH_FP32 | XLMIMO_FACTOR_FF)) == XLMIMO_ZF_DL) smem += BF_DL_EXTRA;
     cudaError_t e = cudaFuncSetAttribute(beamform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return cuda_status(e, "beamform attribute");
     beamform_kernel<<<B, SOLVE_THREADS, smem, st>>>((const double2*)gf, (const double2*)gt, matched, power, noise, K,

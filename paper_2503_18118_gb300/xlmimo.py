@@ -17,6 +17,7 @@ PNUSW, FSPL_USW, UPW = 0, 1, 2
 F64, F32, BF16, BF16X3, F16X3 = 0, 1, 2, 3, 4
 ZF, MMSE, MRC, ZF_DL = 0, 1, 2, 3
 MISMATCH_FP32 = 0x100  # OR-ed into a scheme: mismatched SINR from the FP32 correction
+FACTOR_FF = 0x200  # OR-ed into a matched scheme: double-float factorisation (FP64 if ill-conditioned)
 POWER_ABS, POWER_RXSNR = 0, 1
 DIST_RECT, DIST_POLAR = 0, 1
 APERTURE_NONE, APERTURE_MASK, APERTURE_FRESNEL = 0, 1, 2

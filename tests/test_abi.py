@@ -59,7 +59,7 @@ def test_invalid_arguments_rejected_on_host(xl):
     # unknown precision, scheme, power mode
     assert L.xlmimo_channel_gram(ctypes.byref(arr), dummy, 4, 1, 9, dummy, None) == 1
     assert L.xlmimo_beamform(dummy, None, dummy, dummy, 4, 1, 5, 0, dummy, dummy, None, None) == 1
-    assert L.xlmimo_beamform(dummy, None, dummy, dummy, 4, 1, 0x200, 0, dummy, dummy, None, None) == 1
+    assert L.xlmimo_beamform(dummy, None, dummy, dummy, 4, 1, 0x400, 0, dummy, dummy, None, None) == 1
     assert L.xlmimo_beamform(dummy, None, dummy, dummy, 4, 1, 5 | xl.MISMATCH_FP32, 0, dummy, dummy, None, None) == 1
     assert L.xlmimo_beamform(dummy, None, dummy, dummy, 4, 1, 0, 3, dummy, dummy, None, None) == 1
     # NULL buffers
@@ -205,3 +205,4 @@ def test_binding_constants_match_header(xl):
     assert int(defs["MAX_USERS"]) == xl.MAX_USERS
     assert int(defs["PLAN_INFO_LEN"]) == xl.PLAN_INFO_LEN
     assert int(re.search(r"#define\s+XLMIMO_MISMATCH_FP32\s+0x([0-9a-fA-F]+)", text).group(1), 16) == xl.MISMATCH_FP32
+    assert int(re.search(r"#define\s+XLMIMO_FACTOR_FF\s+0x([0-9a-fA-F]+)", text).group(1), 16) == xl.FACTOR_FF

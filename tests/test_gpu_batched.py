@@ -187,9 +187,10 @@ def test_ragged_receivers_match_single_calls(xl):
     shared-memory buffer (and fall back to an in-place Gauss-Jordan
     elimination) so that each user-count bucket fits more CTAs per SM; on the
     plan's own Gram matrices they give what the standalone receiver call
-    gives, bit for bit, for user counts at both edges of every bucket, ZF and
-    MMSE; instance 0 (ZF) has a user duplicated, an exactly rank-deficient
-    Gram, and must get the standalone call's status."""
+    gives (with the same double-float factorisation, XLMIMO_FACTOR_FF), bit
+    for bit, for user counts at both edges of every bucket, ZF and MMSE;
+    instance 0 (ZF) has a user duplicated, an exactly rank-deficient Gram, and
+    must get the standalone call's status."""
     k = np.array([2, 1, 16, 17, 32, 33, 40, 41, 48, 49, 56, 57, 64, 64])
     count = len(k)
     n = np.array([1024, 300, 2048, 1500, 4096, 3000, 2500, 5000, 2048, 3333, 4000, 2222, 6000, 1024])
@@ -205,7 +206,8 @@ def test_ragged_receivers_match_single_calls(xl):
         u0 = plan.user_off[i]
         s, st, _ = xl.xlmimo_beamform(torch.from_numpy(np.ascontiguousarray(g)).cuda(),
                                       torch.from_numpy(snr[u0:u0 + k[i]][None].copy()).cuda(),
-                                      torch.from_numpy(noise[i:i + 1].copy()).cuda(), int(scheme[i]), xl.POWER_RXSNR)
+                                      torch.from_numpy(noise[i:i + 1].copy()).cuda(), int(scheme[i]) | xl.FACTOR_FF,
+                                      xl.POWER_RXSNR)
         assert int(st.item()) == int(out["status"][i]), i
         assert np.array_equal(s.cpu().numpy()[0], out["sinr"][u0:u0 + k[i]]), i
 

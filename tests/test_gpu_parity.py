@@ -260,6 +260,34 @@ def test_beamform_matched(xl, orc, K, scheme, mode):
 
 
 @pytest.mark.parametrize("K", [2, 8, 32, 64])
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_beamform_matched_double_float_factor(xl, orc, K, scheme):
+    """XLMIMO_FACTOR_FF: matched ZF / MMSE with the Cholesky factorisation in
+    double-float (FP64 for an ill-conditioned system) gives the oracle's SINRs
+    as the FP64 factorisation does, on every trial the oracle solves.  Trial 0
+    has a user duplicated (an exactly rank-deficient Gram): a non-positive
+    double-float pivot sends it to the pivoted Gauss-Jordan elimination, which
+    reports it singular (the oracle's verdict for ZF), where the FP64
+    factorisation may instead run on a rounding-sized positive pivot."""
+    _, G, _, p, s2 = _solve_case(orc, 70 + K, 12, K, max(4 * K, 64))
+    if K > 1:
+        G[0, 1, :] = G[0, 0, :]
+        G[0, :, 1] = G[0, :, 0]
+    p = p / np.real(np.einsum("bii->bi", G))
+    s_ref, st_ref, _ = orc.beamform(G, p, s2, scheme, 0)
+    s64, st64, _ = xl.xlmimo_beamform(dev(G), dev(p), dev(s2), scheme, 0)
+    sff, stff, _ = xl.xlmimo_beamform(dev(G), dev(p), dev(s2), scheme | xl.FACTOR_FF, 0)
+    s64, st64, sff, stff = s64.cpu().numpy(), st64.cpu().numpy(), sff.cpu().numpy(), stff.cpu().numpy()
+    ok = st_ref == 0
+    assert np.all(np.isin(stff[ok], [0, 1])) and np.all(np.isin(st64[ok], [0, 1]))
+    assert np.array_equal(stff[1:], st64[1:])
+    assert stff[0] == st64[0] or stff[0] == 4
+    assert ok.sum() >= 8
+    assert np.max(np.abs(sff[ok] - s_ref[ok]) / np.abs(s_ref[ok])) <= 1e-9
+    assert np.max(np.abs(sff[ok] - s64[ok]) / np.abs(s64[ok])) <= 1e-9
+
+
+@pytest.mark.parametrize("K", [2, 8, 32, 64])
 @pytest.mark.parametrize("scheme", [0, 1, 2])
 def test_beamform_modified_zf(xl, orc, K, scheme):
     """Receiver from the closed-form Gram, judged on the exact channel; small N
