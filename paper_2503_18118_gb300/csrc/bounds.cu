@@ -220,52 +220,76 @@ __global__ void __launch_bounds__(256) bounds_chol_diag_kernel(double2* __restri
     }
 }
 
-// Panel below block p: L_ip = A_ip L_pp^-H for block row i = p + 1 + blockIdx.x;
-// thread r solves row r of the block by forward substitution, in double-float
-// on the FP32 pipe (FMA-exact products, two-sums; the 32 pivot reciprocals
-// are formed once in FP64).  The result is written in place as float pairs
-// (re hi, im hi, re lo, im lo: the same 16 bytes as the FP64 entry): the
+// Panel below block p: L_ip = A_ip L_pp^-H for block row i = p + 1 + blockIdx.x,
+// by forward substitution in double-float on the FP32 pipe (FMA-exact
+// products, two-sums; the 32 pivot reciprocals are formed once in FP64).
+// 256 threads: the two blocks are loaded and stored coalesced, and row r of
+// the block is solved by the 8 threads 8 r .. 8 r + 7 of one warp, thread j
+// summing the terms l = j, j + 8, ... of each column's sum and the 8 partial
+// sums added by a fixed shuffle tree.  The result is written in place as float
+// pairs (re hi, im hi, re lo, im lo: the same 16 bytes as the FP64 entry): the
 // trailing update of this step is its only reader.
-__global__ void __launch_bounds__(BT) bounds_chol_panel_kernel(double2* __restrict__ A, int Kp, int p) {
+constexpr int PANEL_THREADS = 256;
+constexpr int PANEL_SPLIT = PANEL_THREADS / BT;  // threads per row
+
+__global__ void __launch_bounds__(PANEL_THREADS) bounds_chol_panel_kernel(double2* __restrict__ A, int Kp, int p) {
     __shared__ float4 L[BT][BT + 1], X[BT][BT + 1];
     __shared__ float2 rinv[BT];
     double2* Am = A + (int64_t)blockIdx.y * Kp * Kp;
-    const int r = threadIdx.x, o = p * BT, io = (p + 1 + blockIdx.x) * BT;
+    const int tid = threadIdx.x, o = p * BT, io = (p + 1 + blockIdx.x) * BT;
     auto split2 = [](double2 v) {
         float rh, rl, ih, il;
         split_f64(v.x, rh, rl);
         split_f64(v.y, ih, il);
         return make_float4(rh, ih, rl, il);
     };
-    for (int c = 0; c < BT; ++c) {
+    for (int e = tid; e < BT * BT; e += PANEL_THREADS) {
+        const int c = e >> 5, r = e & 31;
         L[r][c] = split2(Am[(int64_t)(o + c) * Kp + o + r]);  // rows r >= c used
         X[r][c] = split2(Am[(int64_t)(o + c) * Kp + io + r]);
     }
-    {
+    if (tid < BT) {
         float h, l;
-        split_f64(1.0 / Am[(int64_t)(o + r) * Kp + o + r].x, h, l);
-        rinv[r] = make_float2(h, l);
+        split_f64(1.0 / Am[(int64_t)(o + tid) * Kp + o + tid].x, h, l);
+        rinv[tid] = make_float2(h, l);
     }
     __syncthreads();
+    const int r = tid / PANEL_SPLIT, j = tid % PANEL_SPLIT;
     for (int c = 0; c < BT; ++c) {
-        const float4 x0 = X[r][c];
-        float2 sh = make_float2(x0.x, x0.y), sl = make_float2(x0.z, x0.w);
-        for (int l = 0; l < c; ++l) {  // s -= X_rl conj(L_cl)
+        float2 sh = make_float2(0.f, 0.f), sl = sh;
+        if (j == 0) {
+            const float4 x0 = X[r][c];
+            sh = make_float2(x0.x, x0.y);
+            sl = make_float2(x0.z, x0.w);
+        }
+        for (int l = j; l < c; l += PANEL_SPLIT) {  // s -= X_rl conj(L_cl)
             const float4 x = X[r][l], y = L[c][l];
             ff2_mac(sh, sl, make_float2(-x.x, -x.y), make_float2(-x.z, -x.w), make_float2(y.x, y.x),
                     make_float2(y.z, y.z));
             ff2_mac(sh, sl, make_float2(-x.y, x.x), make_float2(-x.w, x.z), make_float2(y.y, y.y),
                     make_float2(y.w, y.w));
         }
-        const float2 t = __fadd2_rn(sh, sl);
-        const float2 tl = __fadd2_rn(__fadd2_rn(sh, make_float2(-t.x, -t.y)), sl);
-        const float2 ri = rinv[c];
-        float2 qh = make_float2(0.f, 0.f), ql = qh;
-        ff2_mac(qh, ql, t, tl, make_float2(ri.x, ri.x), make_float2(ri.y, ri.y));
-        const float2 u = __fadd2_rn(qh, ql);
-        X[r][c] = make_float4(u.x, u.y, __fadd_rn(__fadd_rn(qh.x, -u.x), ql.x), __fadd_rn(__fadd_rn(qh.y, -u.y), ql.y));
+        for (int off = PANEL_SPLIT / 2; off > 0; off >>= 1) {
+            const float2 oh = make_float2(__shfl_xor_sync(0xffffffffu, sh.x, off), __shfl_xor_sync(0xffffffffu, sh.y, off));
+            const float2 ol = make_float2(__shfl_xor_sync(0xffffffffu, sl.x, off), __shfl_xor_sync(0xffffffffu, sl.y, off));
+            ff2_add(sh, sl, oh, ol);
+        }
+        if (j == 0) {
+            const float2 t = __fadd2_rn(sh, sl);
+            const float2 tl = __fadd2_rn(__fadd2_rn(sh, make_float2(-t.x, -t.y)), sl);
+            const float2 ri = rinv[c];
+            float2 qh = make_float2(0.f, 0.f), ql = qh;
+            ff2_mac(qh, ql, t, tl, make_float2(ri.x, ri.x), make_float2(ri.y, ri.y));
+            const float2 u = __fadd2_rn(qh, ql);
+            X[r][c] = make_float4(u.x, u.y, __fadd_rn(__fadd_rn(qh.x, -u.x), ql.x), __fadd_rn(__fadd_rn(qh.y, -u.y), ql.y));
+        }
+        __syncwarp();  // the row's 8 threads read X[r][c] from the next column on
     }
-    for (int c = 0; c < BT; ++c) reinterpret_cast<float4*>(Am)[(int64_t)(o + c) * Kp + io + r] = X[r][c];
+    __syncthreads();
+    for (int e = tid; e < BT * BT; e += PANEL_THREADS) {
+        const int c = e >> 5, rr = e & 31;
+        reinterpret_cast<float4*>(Am)[(int64_t)(o + c) * Kp + io + rr] = X[rr][c];
+    }
 }
 
 // Trailing update after block p: A_ij -= L_ip L_jp^H for p < j <= i, tile
@@ -398,7 +422,7 @@ static int capacity_bounds_impl(const xlmimo_array* arr, const double* users, in
         rc = cuda_status(cudaGetLastError(), "bounds cholesky launch");
         const int m = nb - p - 1;
         if (!rc && m > 0) {
-            bounds_chol_panel_kernel<<<dim3((unsigned)m, (unsigned)(2 * B)), BT, 0, st>>>(A, Kp, p);
+            bounds_chol_panel_kernel<<<dim3((unsigned)m, (unsigned)(2 * B)), PANEL_THREADS, 0, st>>>(A, Kp, p);
             bounds_chol_update_kernel<<<dim3((unsigned)(m * (m + 1) / 2), (unsigned)(2 * B)), 256, 0, st>>>(A, Kp, p);
             rc = cuda_status(cudaGetLastError(), "bounds cholesky launch");
         }

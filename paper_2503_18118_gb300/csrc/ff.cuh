@@ -139,6 +139,17 @@ __device__ __forceinline__ void ff2_mac(float2& s, float2& c, float2 xh, float2 
     c = __fadd2_rn(c, __fadd2_rn(__fadd2_rn(ea, eb), e));
 }
 
+// (s, c) += (s2, c2) lane-wise for double-float values (two-sum on the high
+// parts, low parts summed alongside).
+__device__ __forceinline__ void ff2_add(float2& s, float2& c, float2 s2, float2 c2) {
+    const float2 t = __fadd2_rn(s, s2);
+    const float2 bb = __fadd2_rn(t, make_float2(-s.x, -s.y));
+    const float2 ea = __fadd2_rn(s, make_float2(-(t.x - bb.x), -(t.y - bb.y)));
+    const float2 eb = __fadd2_rn(s2, make_float2(-bb.x, -bb.y));
+    s = t;
+    c = __fadd2_rn(__fadd2_rn(c, c2), __fadd2_rn(ea, eb));
+}
+
 // Pivot of the Cholesky factorisation: y = 1/sqrt(d) in FP64 with five FP64
 // instructions.  The FP32 seed comes from d's high mantissa bits and goes back
 // to FP64 exactly, both by integer operations; one third-order step

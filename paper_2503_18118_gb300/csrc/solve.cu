@@ -174,17 +174,6 @@ __device__ __forceinline__ cf to_cf(cd a) {
     return r;
 }
 
-// (s, c) += (s2, c2) lane-wise for double-float values (two-sum on the high
-// parts, low parts summed alongside).
-__device__ __forceinline__ void ff2_add(float2& s, float2& c, float2 s2, float2 c2) {
-    const float2 t = __fadd2_rn(s, s2);
-    const float2 bb = __fadd2_rn(t, make_float2(-s.x, -s.y));
-    const float2 ea = __fadd2_rn(s, make_float2(-(t.x - bb.x), -(t.y - bb.y)));
-    const float2 eb = __fadd2_rn(s2, make_float2(-bb.x, -bb.y));
-    s = t;
-    c = __fadd2_rn(__fadd2_rn(c, c2), __fadd2_rn(ea, eb));
-}
-
 // acc += a b (conj_a: conj(a) b), complex double-float: the real lanes carry
 // (re a re b, re a im b) and the imaginary ones (-+ im a im b, +- im a re b).
 __device__ __forceinline__ void cf_mac(float2& s, float2& c, const cf& a, const cf& b, bool conj_a) {
