@@ -300,11 +300,22 @@ __global__ void __launch_bounds__(PANEL_THREADS) bounds_chol_panel_kernel(double
 // (~2^-48 of the terms' magnitudes), and the sum is subtracted from the FP64
 // entry in FP64.  Thread: row r = tid / 8, columns c = tid % 8 + 8 q
 // (q = 0..3, interleaved so that a warp's 16-byte loads of Lj fill all banks).
-__global__ void __launch_bounds__(256) bounds_chol_update_kernel(double2* __restrict__ A, int Kp, int p) {
+// part: 0 every tile of the trailing triangle; 1 the first block column of
+// it only (tile blockIdx.x, 0: the look-ahead's next panel); 2 the others.
+__global__ void __launch_bounds__(256) bounds_chol_update_kernel(double2* __restrict__ A, int Kp, int p, int part) {
     __shared__ float4 Li[BT][BT + 1], Lj[BT][BT + 1];  // (re hi, im hi, re lo, im lo)
     double2* Am = A + (int64_t)blockIdx.y * Kp * Kp;
     int ti, tj;
-    tri_index(blockIdx.x, &ti, &tj);
+    if (part == 1) {
+        ti = blockIdx.x;
+        tj = 0;
+    } else {
+        tri_index(blockIdx.x, &ti, &tj);
+        if (part == 2) {
+            ++ti;
+            ++tj;
+        }
+    }
     const int o = p * BT, io = (p + 1 + ti) * BT, jo = (p + 1 + tj) * BT;
     const int tid = threadIdx.x;
     const float4* Lf = reinterpret_cast<const float4*>(Am);
@@ -417,16 +428,64 @@ static int capacity_bounds_impl(const xlmimo_array* arr, const double* users, in
     }
     if (!rc && ev) rc = cuda_status(cudaEventRecord(ev[3], st), "event record");
     if (!rc) rc = cuda_status(cudaMemsetAsync(ld, 0, (size_t)2 * B * sizeof(double), st), "workspace clear");
-    for (int p = 0; p < nb && !rc; ++p) {
-        bounds_chol_diag_kernel<<<2 * B, 256, 0, st>>>(A, Kp, p, ld);
+    // Blocked Cholesky with a look-ahead of one block column: after step p's
+    // panel, a library stream of the highest priority updates block column
+    // p + 1 alone, factors its diagonal block and solves its panel (a few CTAs
+    // per matrix, scheduled ahead of the bulk as SMs free up) while `st`
+    // applies step p's update to the rest of the trailing triangle.  Events:
+    // the rest of step p waits for panel p (the L it reads); the column update
+    // of step p + 1 waits for the rest of step p (which updated that column).
+    cudaStream_t sa = nullptr;  // the critical chain; st without a look-ahead
+    cudaEvent_t evs[2 * (XLMIMO_MAX_BOUNDS_USERS / BT + 2)] = {};
+    int nev = 0;
+    auto event = [&](cudaStream_t from, cudaStream_t to) {
+        cudaEvent_t e = nullptr;
+        int r = cuda_status(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cholesky event");
+        if (!r) evs[nev++] = e;
+        if (!r) r = cuda_status(cudaEventRecord(e, from), "cholesky event");
+        if (!r) r = cuda_status(cudaStreamWaitEvent(to, e, 0), "cholesky event");
+        return r;
+    };
+    if (!rc && nb > 2) {
+        int least = 0, greatest = 0;
+        rc = cuda_status(cudaDeviceGetStreamPriorityRange(&least, &greatest), "stream priorities");
+        if (!rc) rc = cuda_status(cudaStreamCreateWithPriority(&sa, cudaStreamNonBlocking, greatest), "cholesky stream");
+        if (!rc) rc = event(st, sa);
+    }
+    cudaStream_t sc = sa ? sa : st;
+    if (!rc) {
+        bounds_chol_diag_kernel<<<2 * B, 256, 0, sc>>>(A, Kp, 0, ld);
+        if (nb > 1) bounds_chol_panel_kernel<<<dim3((unsigned)(nb - 1), (unsigned)(2 * B)), PANEL_THREADS, 0, sc>>>(A, Kp, 0);
         rc = cuda_status(cudaGetLastError(), "bounds cholesky launch");
-        const int m = nb - p - 1;
-        if (!rc && m > 0) {
-            bounds_chol_panel_kernel<<<dim3((unsigned)m, (unsigned)(2 * B)), PANEL_THREADS, 0, st>>>(A, Kp, p);
-            bounds_chol_update_kernel<<<dim3((unsigned)(m * (m + 1) / 2), (unsigned)(2 * B)), 256, 0, st>>>(A, Kp, p);
+    }
+    for (int p = 0; p + 1 < nb && !rc; ++p) {
+        const int m = nb - p - 1;  // block columns after p
+        if (sa && m > 1) {
+            rc = event(sa, st);  // panel p is in place
+            if (!rc) {
+                bounds_chol_update_kernel<<<dim3((unsigned)(m * (m - 1) / 2), (unsigned)(2 * B)), 256, 0, st>>>(A, Kp, p, 2);
+                bounds_chol_update_kernel<<<dim3((unsigned)m, (unsigned)(2 * B)), 256, 0, sa>>>(A, Kp, p, 1);
+                rc = cuda_status(cudaGetLastError(), "bounds cholesky launch");
+            }
+        } else if (!rc) {
+            bounds_chol_update_kernel<<<dim3((unsigned)(m * (m + 1) / 2), (unsigned)(2 * B)), 256, 0, sc>>>(A, Kp, p, 0);
             rc = cuda_status(cudaGetLastError(), "bounds cholesky launch");
         }
+        if (!rc) {
+            bounds_chol_diag_kernel<<<2 * B, 256, 0, sc>>>(A, Kp, p + 1, ld);
+            if (m > 1) bounds_chol_panel_kernel<<<dim3((unsigned)(m - 1), (unsigned)(2 * B)), PANEL_THREADS, 0, sc>>>(A, Kp, p + 1);
+            rc = cuda_status(cudaGetLastError(), "bounds cholesky launch");
+        }
+        // the next column update needs the rest of this step (the column it updates)
+        if (!rc && sa && m > 1) rc = event(st, sa);
     }
+    if (sa) {
+        // joined even after an error, so that nothing on it outlives the call
+        const int r = event(sa, st);
+        if (!rc) rc = r;
+        cudaStreamDestroy(sa);
+    }
+    for (int i = 0; i < nev; ++i) cudaEventDestroy(evs[i]);
     if (!rc && ev) rc = cuda_status(cudaEventRecord(ev[4], st), "event record");
     if (!rc) {
         bounds_finish_kernel<<<(B + 255) / 256, 256, 0, st>>>(ld, K, B, snr, out);
