@@ -493,6 +493,33 @@ def test_headline_pipeline_sampled(xl, orc, prec, gtol, rtol):
     assert np.max(np.abs(d - dc) / d) < 1e-3
 
 
+def test_capacity_sweep_largest_n(xl, orc):
+    """The sweep workload's largest array (N = 65536 at 28 GHz, K = 8, users in
+    [5, 50] m) on 100 trials, three SNRs, FP64 and FP32: the trial-mean rates
+    of the exact and closed-form paths and the capacity against the oracle
+    pipeline on the same users."""
+    K, B, N = 8, 100, 65536
+    users = inputs.users_polar(3, B, K, (5.0, 50.0))
+    snr_db = [0.0, 10.0, 20.0]
+    ref_x = 27.5
+    G = orc.gram(1, N, LAM28, LAM28 / 2, 1.0, users)
+    Gc = orc.closed_form(1, N, LAM28, LAM28 / 2, 1.0, users)
+    glim = math.pi * (LAM28 / (4 * math.pi)) ** 2 / (LAM28 / 2 * ref_x)
+    for prec, tol in ((0, 1e-10), (1, 1e-4)):
+        out = xl.xlmimo_capacity_sweep(dev(users), [N], snr_db, LAM28, prec=prec, ref_x=ref_x)
+        assert abs(out["gram_err"][0] - normwise(Gc, G)) <= 1e-4 * normwise(Gc, G) + 1e-9
+        for si, s in enumerate(snr_db):
+            p = np.full((B, K), 10 ** (s / 10) / glim)
+            for path, gf, gt in ((0, G, None), (1, Gc, G)):
+                for sch in (0, 1):
+                    sr, _, cap = orc.beamform(gf, p, np.ones(B), sch, 0, gram_true=gt, want_capacity=True)
+                    rr, _ = orc.sumrate(sr)
+                    ptol = tol if path == 0 else max(tol, 1e-5)
+                    assert abs(out["rate"][0, path, sch, si] - rr.mean()) <= ptol * abs(rr.mean()) + 1e-12, (prec, s, path, sch)
+                    if path == 0 and sch == 1:
+                        assert abs(out["capacity"][0, si] - cap.mean()) <= tol * abs(cap.mean())
+
+
 def test_capacity_sweep_small(xl, orc):
     """Sweep at a few sizes against the oracle pipeline on the same users."""
     K, B = 4, 20
