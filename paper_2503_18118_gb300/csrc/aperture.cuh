@@ -31,10 +31,12 @@ __device__ __forceinline__ void fresnel_cs_cut(float u, float& c, float& s) {
     }
     const float a = 1.5707963267948966f * u * u;
     float t = 1.0f, sc = 0.0f, ss = 0.0f;
-#pragma unroll 1
+    // fully unrolled: the reciprocals 1/k and 1/(2k + 1) are constants, so
+    // each term costs multiplications and one addition, no division
+#pragma unroll
     for (int k = 0; k < 34; ++k) {
-        if (k > 0) t *= a / (float)k;
-        const float term = ((k >> 1) & 1 ? -t : t) / (float)(2 * k + 1);
+        if (k > 0) t *= a * (1.0f / (float)k);
+        const float term = ((k >> 1) & 1 ? -t : t) * (1.0f / (float)(2 * k + 1));
         if (k & 1) ss += term;
         else sc += term;
     }
