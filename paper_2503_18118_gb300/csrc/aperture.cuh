@@ -15,6 +15,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "ff.cuh"
 
 namespace xl {
 
@@ -46,22 +47,40 @@ __device__ __forceinline__ void fresnel_cs_cut(float u, float& c, float& s) {
 
 // F of the pair (i, j) (complex): mode APERTURE_*, positions in metres,
 // H = N spacing / 2.  The stationary point and the mask decision are taken in
-// FP64, the Fresnel factor in FP32 (~1e-5).
+// double-float on the FP32 pipe (~2^-44 relative: the FP64 values split by
+// integer operations, as GB300's FP64 pipe issues one warp instruction per
+// ~64 cycles per scheduler), the Fresnel factor in FP32 (~1e-5).
 __device__ __forceinline__ float2 aperture_factor(int mode, double xi, double yi, double xj, double yj, double H,
                                                   double inv_lambda) {
     if (mode == APERTURE_NONE) return make_float2(1.0f, 0.0f);
     if (xj == xi) return make_float2(0.0f, 0.0f);
-    const double ys = yi - xi * (yj - yi) / (xj - xi);
-    if (mode == APERTURE_MASK) return make_float2(fabs(ys) <= H ? 1.0f : 0.0f, 0.0f);
-    const float fxi = (float)xi, fxj = (float)xj, dyi = (float)(ys - yi), dyj = (float)(ys - yj);
+    auto split = [](double d) {
+        ff v;
+        split_f64(d, v.hi, v.lo);
+        return v;
+    };
+    const ff Xi = split(xi), Yi = split(yi), Xj = split(xj), Yj = split(yj), Hf = split(H);
+    // y* = y_i - x_i (y_j - y_i) / (x_j - x_i)
+    const ff q = ff_div(ff_mul(Xi, ff_sub(Yj, Yi)), ff_sub(Xj, Xi));
+    const ff ys = ff_sub(Yi, q);
+    const ff hp = ff_sub(Hf, ys), hm = ff_add(Hf, ys);  // H - y*, H + y*
+    if (mode == APERTURE_MASK) {
+        // |y*| <= H: both H - y* and H + y* non-negative
+        const bool in = (hp.hi > 0.0f || (hp.hi == 0.0f && hp.lo >= 0.0f)) &&
+                        (hm.hi > 0.0f || (hm.hi == 0.0f && hm.lo >= 0.0f));
+        return make_float2(in ? 1.0f : 0.0f, 0.0f);
+    }
+    const float fxi = Xi.hi, fxj = Xj.hi, dyi = -q.hi, dyj = ff_sub(ys, Yj).hi;
     const float ri2 = fxi * fxi + dyi * dyi, rj2 = fxj * fxj + dyj * dyj;
     const float ci = fxi * fxi * rsqrtf(ri2) / ri2, cj = fxj * fxj * rsqrtf(rj2) / rj2;  // x^2 / r^3
-    const float p2 = 6.283185307179586f * (float)inv_lambda * (ci - cj);
+    float il_h, il_l;
+    split_f64(inv_lambda, il_h, il_l);
+    const float p2 = 6.283185307179586f * il_h * (ci - cj);
     if (!(p2 != 0.0f)) return make_float2(0.0f, 0.0f);
     const float sc = sqrtf(fabsf(p2) * 0.3183098861837907f);
     float ch, sh, cl, sl;
-    fresnel_cs_cut((float)(H - ys) * sc, ch, sh);
-    fresnel_cs_cut((float)(-H - ys) * sc, cl, sl);
+    fresnel_cs_cut(hp.hi * sc, ch, sh);
+    fresnel_cs_cut(-hm.hi * sc, cl, sl);
     const float a = ch - cl, b = sh - sl, sg = p2 > 0.0f ? 1.0f : -1.0f;
     return make_float2(0.5f * (a + b), 0.5f * sg * (b - a));
 }
