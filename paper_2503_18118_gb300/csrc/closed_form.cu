@@ -35,16 +35,26 @@ __device__ __forceinline__ double2 cis_cycles(double q) {  // e^{j 2 pi q}
 
 // Off-diagonal entries (i < j) come first in the index space, then the K
 // diagonal entries of every trial, so that each warp runs one kind.  The
-// spherical-model off-diagonals reduce the phase sgn (2 pi d / lambda - pi/4)
-// in FP64 (d from an FP32-seeded Newton square root) and evaluate its sine,
-// cosine and the magnitude in FP32: entries carry ~1e-7 relative error,
-// far below the 1e-4-level stationary-phase error of the formula itself.
-__global__ void closed_form_kernel(Geom g, const double* __restrict__ users, int K, int B,
+// spherical-model off-diagonals form the distance d and reduce the phase
+// sgn (2 pi d / lambda - pi/4) in double-float on the FP32 pipe (~2^-44
+// relative, from FP64 positions split by integer operations: GB300's FP64
+// pipe issues one warp instruction per ~64 cycles per scheduler) and
+// evaluate its sine, cosine and the magnitude in FP32: entries carry ~1e-7
+// relative error, far below the 1e-4-level stationary-phase error of the
+// formula itself.  At most 48 registers: the Monte-Carlo step runs it in
+// 64-thread blocks beside three Gram CTAs, which leave 3,328 registers per SM.
+__global__ void __maxnreg__(48) closed_form_kernel(Geom g, const double* __restrict__ users, int K, int B,
                                    double2* __restrict__ gram) {
     const int64_t P = (int64_t)K * (K - 1) / 2;
     const int64_t n_off = (int64_t)B * P;
     const int64_t total = n_off + (int64_t)B * K;
     const float c2f = (float)(g.lambda * g.lambda / (16.0 * 3.14159265358979323846 * 3.14159265358979323846));
+    auto split = [](double d) {
+        ff v;
+        split_f64(d, v.hi, v.lo);
+        return v;
+    };
+    const ff inv_l = split(g.inv_lambda);
     // 32-bit index arithmetic whenever the index space fits (a 64-bit division
     // per entry costs more than the entry's arithmetic)
     const bool narrow = total <= 0x7FFFFFFF;
@@ -104,19 +114,18 @@ __global__ void closed_form_kernel(Geom g, const double* __restrict__ users, int
             }
             v = make_double2(val, 0.0);
         } else {
-            double dx = fabs(xi) - fabs(xj), dy = yi - yj;
-            double d2 = fma(dx, dx, dy * dy);
-            float d0 = sqrtf((float)d2);
-            double d = (double)d0 + (d2 - (double)d0 * (double)d0) * (double)(0.5f / d0);
-            double sg = dx > 0.0 ? 1.0 : -1.0;
-            double q = sg * fma(d, g.inv_lambda, -0.125);  // phase in cycles
-            float fr = (float)(q - rint(q));
+            // x > 0 for valid users
+            const ff Xi = split(xi), Xj = split(xj), dx = ff_sub(Xi, Xj), dy = ff_sub(split(yi), split(yj));
+            const ff d = ff_sqrt(ff_add(ff_mul(dx, dx), ff_mul(dy, dy)));
+            ff q = ff_add(ff_mul(d, inv_l), ff{-0.125f, 0.0f});  // phase in cycles
+            if (!(dx.hi > 0.0f || (dx.hi == 0.0f && dx.lo > 0.0f))) q = ff_neg(q);
+            const float fr = __fadd_rn(__fsub_rn(q.hi, rintf(q.hi)), q.lo);
             float sn, cs;
             __sincosf(6.283185307179586f * fr, &sn, &cs);
-            float df = (float)d, xif = (float)xi, xjf = (float)xj;
+            const float df = d.hi, xif = Xi.hi, xjf = Xj.hi;
             float m;
             if (g.model == XLMIMO_PNUSW)
-                m = (float)(g.beta0 / g.spacing * sqrt(g.lambda)) * fabsf((float)dx) / (df * sqrtf(df) * sqrtf(xif * xjf));
+                m = (float)(g.beta0 / g.spacing * sqrt(g.lambda)) * fabsf(dx.hi) / (df * sqrtf(df) * sqrtf(xif * xjf));
             else
                 m = c2f / (float)g.spacing * sqrtf((float)g.lambda / (df * xif * xjf));
             v = make_double2((double)(m * cs), (double)(m * sn));
