@@ -618,7 +618,8 @@ def test_downlink_zf(xl, orc, K):
 
 def test_mc_step_downlink(xl):
     """The Monte-Carlo step with downlink ZF on both paths gives what the
-    individual calls give (the paired receiver launch carries the downlink scratch)."""
+    individual calls give (the step's two receiver launches, on their own streams, each
+    carry the downlink scratch)."""
     B, K, N = 50, 8, 2000
     users = dev(inputs.users_polar(78, B, K, (3.0, 30.0)))
     snr = dev(np.full((B, K), 10.0))
