@@ -1,6 +1,7 @@
 // Closed-form Gram matrices of "modified ZF" (Sec. V-B), replacing the
-// O(N K^2) inner products by O(K^2) formulas (FP64, except the sine, cosine
-// and magnitude of the spherical-model off-diagonals, see the kernel).
+// O(N K^2) inner products by O(K^2) formulas (FP64, except the spherical-model
+// off-diagonals: distance and phase in double-float, sine, cosine and
+// magnitude in FP32; see the kernel).
 //
 // PNUSW.  Diagonal: the received power of Eq. (4) over P,
 //   G~_ii = beta0 / (spacing x_i) * B_i,

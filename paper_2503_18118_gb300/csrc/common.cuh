@@ -43,7 +43,7 @@ int launch_gram_ura(const Geom& g, int64_t rows, const double* users, int K, int
 bool gram_tc_ura_supported(const Geom& g, int64_t ncol, int prec);
 int launch_gram_tc_ura(const Geom& g, int64_t ncol, int64_t rows, const double* users, int K, int B, double* gram,
                        cudaStream_t st);
-// threads per block: 256 alone; 64 lets a block (44 registers a thread) fit
+// threads per block: 256 alone; 64 lets a block (at most 48 registers a thread) fit
 // beside three tensor-core Gram CTAs on an SM, so that it runs during the Gram.
 int launch_closed_form(const Geom& g, const double* users, int K, int B, double* gram, cudaStream_t st,
                        int threads = 256);
