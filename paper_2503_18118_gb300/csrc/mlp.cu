@@ -345,6 +345,16 @@ static int check_m(int M) {
     return XLMIMO_OK;
 }
 
+// Adam's scalar arguments, checked before a training step enqueues anything
+static int check_adam(int64_t step, double lr, double beta1, double beta2, double eps) {
+    if (step < 1) { set_error("step must be >= 1"); return XLMIMO_EINVAL; }
+    if (!(lr >= 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0)) {
+        set_error("need lr >= 0, beta1 and beta2 in [0, 1), eps > 0");
+        return XLMIMO_EINVAL;
+    }
+    return XLMIMO_OK;
+}
+
 }  // namespace xl
 
 using namespace xl;
@@ -429,11 +439,8 @@ int xlmimo_mlp_adam(float* params, float* m, float* v, const float* grad, int64_
                     double beta2, double eps, void* stream) {
     clear_error();
     if (!params || !m || !v || !grad) { set_error("params, m, v and grad must be non-NULL"); return XLMIMO_EINVAL; }
-    if (step < 1) { set_error("step must be >= 1"); return XLMIMO_EINVAL; }
-    if (!(lr >= 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0)) {
-        set_error("need lr >= 0, beta1 and beta2 in [0, 1), eps > 0");
-        return XLMIMO_EINVAL;
-    }
+    int rc = check_adam(step, lr, beta1, beta2, eps);
+    if (rc) return rc;
     const double c1 = 1.0 / (1.0 - pow(beta1, (double)step)), c2 = 1.0 / (1.0 - pow(beta2, (double)step));
     mlp_adam_kernel<<<grid_for(XLMIMO_MLP_PARAMS, 256), 256, 0, as_stream(stream)>>>(
         params, m, v, grad, XLMIMO_MLP_PARAMS, (float)lr, (float)beta1, (float)(1.0 - beta1), (float)beta2,
@@ -453,6 +460,8 @@ int xlmimo_mlp_train_step(float* params, float* m, float* v, float* grad, int64_
         return XLMIMO_EINVAL;
     }
     if (((uintptr_t)work & 15u) != 0) { set_error("work must be 16-byte aligned"); return XLMIMO_EINVAL; }
+    rc = check_adam(step, lr, 0.9, 0.999, 1e-8);
+    if (rc) return rc;
     cudaStream_t st = as_stream(stream);
     // the output gradient reuses the head of the workspace's second slab
     float* dout = work + (int64_t)M * MLP_W;

@@ -206,3 +206,78 @@ def test_binding_constants_match_header(xl):
     assert int(defs["PLAN_INFO_LEN"]) == xl.PLAN_INFO_LEN
     assert int(re.search(r"#define\s+XLMIMO_MISMATCH_FP32\s+0x([0-9a-fA-F]+)", text).group(1), 16) == xl.MISMATCH_FP32
     assert int(re.search(r"#define\s+XLMIMO_FACTOR_FF\s+0x([0-9a-fA-F]+)", text).group(1), 16) == xl.FACTOR_FF
+
+
+def test_remaining_entries_validate_on_host(xl):
+    """Every entry point rejects bad arguments before any device work: the
+    allocation-free Gram, the timed bounds, the rate and saturation calls, the
+    batch-plan calls, the network's training calls and the pipe probe."""
+    L = xl.lib()
+    dummy = ctypes.c_void_p(16)
+    arr = xl.array(1024, 0.01)
+    # allocation-free Gram: K range, precision, NULL buffers; the tensor-core
+    # precisions are valid requests this entry point does not serve
+    for K in (0, xl.MAX_USERS + 1):
+        assert L.xlmimo_channel_gram_noalloc(ctypes.byref(arr), dummy, K, 1, xl.F32, dummy, None) == 1
+    assert L.xlmimo_channel_gram_noalloc(ctypes.byref(arr), dummy, 4, -1, xl.F32, dummy, None) == 1
+    assert L.xlmimo_channel_gram_noalloc(ctypes.byref(arr), dummy, 4, 1, 9, dummy, None) == 1
+    assert L.xlmimo_channel_gram_noalloc(ctypes.byref(arr), dummy, 4, 1, xl.BF16X3, dummy, None) == 6
+    assert L.xlmimo_channel_gram_noalloc(ctypes.byref(arr), None, 4, 1, xl.F64, dummy, None) == 1
+    assert L.xlmimo_channel_gram_noalloc(ctypes.byref(arr), None, 4, 0, xl.F64, None, None) == 0
+    # timed bounds: the phase times are required
+    assert L.xlmimo_capacity_bounds_timed(ctypes.byref(arr), dummy, 8, 1, 1.0, dummy, None, None) == 1
+    assert b"phase_ms" in L.xlmimo_last_error()
+    # sum rate and per-trial saturation
+    assert L.xlmimo_sumrate(dummy, 0, 1, dummy, None, None) == 1
+    assert L.xlmimo_sumrate(dummy, 4, -1, dummy, None, None) == 1
+    assert L.xlmimo_sumrate(dummy, 4, 1, None, None, None) == 1
+    assert L.xlmimo_sumrate(None, 4, 0, None, None, None) == 0
+    for t, spacing in ((0.0, 0.01), (0.9, 0.0), (0.9, float("inf")), (float("nan"), 0.01)):
+        assert L.xlmimo_saturation(dummy, 4, 1, t, spacing, dummy, None) == 1, (t, spacing)
+    assert L.xlmimo_saturation(dummy, 4, 1, 0.9, 0.01, None, None) == 1
+    # analytic saturation: descriptor, ranges, K, NULL output
+    out = (ctypes.c_double * 6)()
+    rect = xl.UserDist(xl.DIST_RECT, 0, 1.0, 10.0, -7.5, 7.5)
+    assert L.xlmimo_saturation_analytic(None, 4, 0.9, 0.01, out, None) == 1
+    assert L.xlmimo_saturation_analytic(ctypes.byref(rect), 4, 0.9, 0.01, None, None) == 1
+    assert L.xlmimo_saturation_analytic(ctypes.byref(rect), 0, 0.9, 0.01, out, None) == 1
+    assert L.xlmimo_saturation_analytic(ctypes.byref(rect), 4, 0.9, -0.01, out, None) == 1
+    for bad in (xl.UserDist(xl.DIST_RECT, 1, 1.0, 10.0, -7.5, 7.5), xl.UserDist(2, 0, 1.0, 10.0, -7.5, 7.5),
+                xl.UserDist(xl.DIST_RECT, 0, 0.0, 10.0, -7.5, 7.5), xl.UserDist(xl.DIST_RECT, 0, 1.0, 10.0, 7.5, -7.5),
+                xl.UserDist(xl.DIST_POLAR, 0, 3.0, 30.0, -1.0, 1.6)):
+        assert L.xlmimo_saturation_analytic(ctypes.byref(bad), 4, 0.9, 0.01, out, None) == 1
+    # batch plans: a NULL plan is refused, and destroying it is a no-op
+    info = (ctypes.c_int64 * xl.PLAN_INFO_LEN)()
+    assert L.xlmimo_batch_run(None, dummy, dummy, 0, dummy, dummy, dummy, dummy, None) == 1
+    assert L.xlmimo_batch_plan_info(None, info) == 1
+    assert L.xlmimo_batch_plan_destroy(None) == 0
+    # network training calls
+    assert L.xlmimo_mlp_loss(dummy, dummy, None, -1, dummy, dummy, None) == 1
+    assert L.xlmimo_mlp_loss(dummy, None, None, 4, dummy, dummy, None) == 1
+    assert L.xlmimo_mlp_loss(None, None, None, 0, None, None, None) == 0
+    assert L.xlmimo_mlp_backward(dummy, dummy, dummy, dummy, -1, dummy, dummy, None) == 1
+    assert L.xlmimo_mlp_backward(None, dummy, dummy, dummy, 4, dummy, dummy, None) == 1
+    assert L.xlmimo_mlp_backward(dummy, dummy, dummy, dummy, 4, dummy, ctypes.c_void_p(20), None) == 1
+    assert b"16-byte" in L.xlmimo_last_error()
+    for step, lr, b1, b2, eps in ((1, 1e-3, 0.9, 1.0, 1e-8), (1, 1e-3, 0.9, 0.999, 0.0), (1, -1.0, 0.9, 0.999, 1e-8)):
+        assert L.xlmimo_mlp_adam(dummy, dummy, dummy, dummy, step, lr, b1, b2, eps, None) == 1
+    assert L.xlmimo_mlp_adam(None, dummy, dummy, dummy, 1, 1e-3, 0.9, 0.999, 1e-8, None) == 1
+    # a training step checks Adam's step and rate before it enqueues its forward pass
+    step_args = lambda step, lr, work=dummy: (dummy, dummy, dummy, dummy, step, lr, dummy, dummy, None, 4, dummy,
+                                              dummy, work, None, None)
+    assert L.xlmimo_mlp_train_step(*step_args(0, 1e-3)) == 1
+    assert b"step" in L.xlmimo_last_error()
+    assert L.xlmimo_mlp_train_step(*step_args(1, float("nan"))) == 1
+    assert L.xlmimo_mlp_train_step(*step_args(1, 1e-3, ctypes.c_void_p(20))) == 1
+    assert L.xlmimo_mlp_forward(None, dummy, 4, dummy, None, None) == 1
+    # pipe probe
+    res = (ctypes.c_double * 2)()
+    for pipe in (-1, 3):
+        assert L.xlmimo_measure_pipe(pipe, res, None) == 1
+    assert L.xlmimo_measure_pipe(0, None, None) == 1
+    # pair features: K range, base, weights without the closed form
+    assert L.xlmimo_pair_features(ctypes.byref(arr), dummy, xl.MAX_USERS + 1, 1, 0, None, None, dummy, None, None,
+                                  None) == 1
+    assert L.xlmimo_pair_features(ctypes.byref(arr), dummy, 4, 1, -1, None, None, dummy, None, None, None) == 1
+    assert L.xlmimo_pair_features(ctypes.byref(arr), dummy, 4, 1, 0, None, None, dummy, None, dummy, None) == 1
+    assert b"weights need" in L.xlmimo_last_error()
