@@ -100,10 +100,15 @@ static bool tc_device(int* dev) {
 }
 
 // Launch over B trials of g.N elements in S element chunks (multiples of
-// `span`), reducing chunk partials when S > 1.
+// `span`), reducing chunk partials when S > 1.  The engine counts a chunk's
+// 64-element stages in 32 bits, so a chunk holds at most ~2^36 elements: an
+// array longer than that is split whatever the batch size.
 static int launch_tc_chunks(TcKernel kern, size_t smem, const Geom& g, const GenParams& gp, int span,
                             const double* users, int K, int B, double* gram, const UraRows& ura, cudaStream_t st) {
+    constexpr int64_t MAX_CHUNK = int64_t(1) << 36;
     int S = choose_split(g.N, B, span, 4);
+    const int64_t min_s = (g.N + MAX_CHUNK - 1) / MAX_CHUNK;
+    if (S < min_s) S = (int)min_s;
     int64_t spans = (g.N + span - 1) / span;
     int64_t chunk = ((spans + S - 1) / S) * span;
     S = (int)((g.N + chunk - 1) / chunk);
