@@ -48,10 +48,10 @@ __global__ void __launch_bounds__(STATS_THREADS) stats_kernel(const double* __re
                                                               double* __restrict__ stats) {
     __shared__ double sh[STATS_THREADS];
     double s = 0.0;
-    for (int b = threadIdx.x; b < B; b += STATS_THREADS) s += x[b];
+    for (int64_t b = threadIdx.x; b < B; b += STATS_THREADS) s += x[b];
     double mean = block_sum(s, sh) / (double)B;
     double q = 0.0;
-    for (int b = threadIdx.x; b < B; b += STATS_THREADS) {
+    for (int64_t b = threadIdx.x; b < B; b += STATS_THREADS) {
         double d = x[b] - mean;
         q += d * d;
     }
@@ -67,11 +67,11 @@ __global__ void __launch_bounds__(STATS_THREADS) stats_strided_kernel(const doub
                                                                       int stride, double* __restrict__ stats) {
     __shared__ double sh[STATS_THREADS];
     double s = 0.0;
-    for (int b = threadIdx.x; b < B; b += STATS_THREADS) s += x[(int64_t)b * stride];
+    for (int64_t b = threadIdx.x; b < B; b += STATS_THREADS) s += x[b * stride];
     double mean = block_sum(s, sh) / (double)B;
     double q = 0.0;
-    for (int b = threadIdx.x; b < B; b += STATS_THREADS) {
-        double d = x[(int64_t)b * stride] - mean;
+    for (int64_t b = threadIdx.x; b < B; b += STATS_THREADS) {
+        double d = x[b * stride] - mean;
         q += d * d;
     }
     double m2 = block_sum(q, sh);
@@ -89,8 +89,7 @@ int launch_stats_strided(const double* x, int B, int stride, double* out, cudaSt
 
 int launch_sumrate(const double* sinr, int K, int B, double* rate, double* stats, cudaStream_t st) {
     const int threads = 256, wpb = threads / 32;
-    int blocks = (B + wpb - 1) / wpb;
-    if (blocks > 16 * num_sms()) blocks = 16 * num_sms();
+    const int blocks = (int)std::min<int64_t>(((int64_t)B + wpb - 1) / wpb, 16LL * num_sms());
     sumrate_kernel<<<blocks, threads, 0, st>>>(sinr, K, B, rate);
     int rc = cuda_status(cudaGetLastError(), "sumrate launch");
     if (rc || !stats) return rc;
@@ -100,7 +99,7 @@ int launch_sumrate(const double* sinr, int K, int B, double* rate, double* stats
 
 __global__ void saturation_kernel(const double* __restrict__ users, int K, int B, double a, double spacing,
                                   double* __restrict__ sat) {
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < B; b += (int64_t)gridDim.x * blockDim.x) {
         double up = -INFINITY, dn = INFINITY;
         for (int k = 0; k < K; ++k) {
             double x = users[((int64_t)b * K + k) * 2], y = users[((int64_t)b * K + k) * 2 + 1];
@@ -116,8 +115,7 @@ __global__ void saturation_kernel(const double* __restrict__ users, int K, int B
 int launch_saturation(const double* users, int K, int B, double t, double spacing, double* sat, cudaStream_t st) {
     double a = t / sqrt(1.0 - t * t);
     int threads = 256;
-    int blocks = (B + threads - 1) / threads;
-    if (blocks > 16 * num_sms()) blocks = 16 * num_sms();
+    const int blocks = (int)std::min<int64_t>(((int64_t)B + threads - 1) / threads, 16LL * num_sms());
     saturation_kernel<<<blocks, threads, 0, st>>>(users, K, B, a, spacing, sat);
     return cuda_status(cudaGetLastError(), "saturation launch");
 }

@@ -5,6 +5,7 @@
 // every SNR.  Host loop over sizes; every trial-level step is a kernel.
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -21,9 +22,9 @@ __global__ void fill_kernel(double* __restrict__ x, int64_t n, double v) {
 // Per-trial max_ij |A_ij - G_ij| / sqrt(G_ii G_jj).
 __global__ void normwise_err_kernel(const double2* __restrict__ A, const double2* __restrict__ G, int K, int B,
                                     double* __restrict__ err) {
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
-        const double2* a = A + (int64_t)b * K * K;
-        const double2* g = G + (int64_t)b * K * K;
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < B; b += (int64_t)gridDim.x * blockDim.x) {
+        const double2* a = A + b * K * K;
+        const double2* g = G + b * K * K;
         double m = 0.0;
         for (int i = 0; i < K; ++i)
             for (int j = 0; j < K; ++j) {
@@ -38,7 +39,7 @@ __global__ void normwise_err_kernel(const double2* __restrict__ A, const double2
 __global__ void max_kernel(const double* __restrict__ x, int n, double* __restrict__ out) {
     __shared__ double sh[256];
     double m = 0.0;
-    for (int i = threadIdx.x; i < n; i += 256) m = fmax(m, x[i]);
+    for (int64_t i = threadIdx.x; i < n; i += 256) m = fmax(m, x[i]);
     sh[threadIdx.x] = m;
     __syncthreads();
     for (int s = 128; s > 0; s >>= 1) {
@@ -100,7 +101,8 @@ static int sweep_impl(const xlmimo_sweep_cfg* c, xlmimo_sweep_result* r, cudaStr
         }
         if (!rc) rc = launch_closed_form(g, c->users, K, B, g_cf, st);
         if (!rc) {
-            normwise_err_kernel<<<(B + 255) / 256, 256, 0, st>>>((const double2*)g_cf, (const double2*)g_ex, K, B, tmp);
+            const int blocks = (int)std::min<int64_t>(((int64_t)B + 255) / 256, 16LL * num_sms());
+            normwise_err_kernel<<<blocks, 256, 0, st>>>((const double2*)g_cf, (const double2*)g_ex, K, B, tmp);
             max_kernel<<<1, 256, 0, st>>>(tmp, B, acc + 3 * (4 * NS) + 3 * NS);
             rc = cuda_status(cudaGetLastError(), "sweep err");
         }
