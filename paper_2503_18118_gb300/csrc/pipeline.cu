@@ -24,8 +24,8 @@ constexpr int PIPE_MAX_CHUNKS = 64;
 struct PipeState {
     cudaStream_t side = nullptr;
     cudaStream_t side2 = nullptr;  // the closed-form receivers
-    cudaEvent_t gram_done[PIPE_MAX_CHUNKS];
-    cudaEvent_t cf_fork[PIPE_MAX_CHUNKS], cf_join[PIPE_MAX_CHUNKS];
+    cudaEvent_t gram_done[PIPE_MAX_CHUNKS] = {};
+    cudaEvent_t cf_fork[PIPE_MAX_CHUNKS] = {}, cf_join[PIPE_MAX_CHUNKS] = {};
     cudaEvent_t inputs_ready = nullptr;
     cudaEvent_t side_done = nullptr;
     bool ready = false;
@@ -33,6 +33,20 @@ struct PipeState {
 
 static std::mutex g_pipe_mu;
 static std::vector<PipeState> g_pipe;
+
+// Destroy what a PipeState holds (null handles are skipped) and reset it.
+static void release_pipe(PipeState& p) {
+    for (int i = 0; i < PIPE_MAX_CHUNKS; ++i) {
+        if (p.gram_done[i]) cudaEventDestroy(p.gram_done[i]);
+        if (p.cf_fork[i]) cudaEventDestroy(p.cf_fork[i]);
+        if (p.cf_join[i]) cudaEventDestroy(p.cf_join[i]);
+    }
+    if (p.inputs_ready) cudaEventDestroy(p.inputs_ready);
+    if (p.side_done) cudaEventDestroy(p.side_done);
+    if (p.side) cudaStreamDestroy(p.side);
+    if (p.side2) cudaStreamDestroy(p.side2);
+    p = PipeState{};
+}
 
 static int pipe_state(PipeState** out) {
     int dev = 0;
@@ -55,7 +69,10 @@ static int pipe_state(PipeState** out) {
         }
         if (!rc) rc = cuda_status(cudaEventCreateWithFlags(&p.side_done, cudaEventDisableTiming), "pipeline event");
         if (!rc) rc = cuda_status(cudaEventCreateWithFlags(&p.inputs_ready, cudaEventDisableTiming), "pipeline event");
-        if (rc) return rc;
+        if (rc) {
+            release_pipe(p);  // nothing half-made is kept; the next call starts afresh
+            return rc;
+        }
         p.ready = true;
     }
     *out = &p;
@@ -189,16 +206,7 @@ extern "C" int xlmimo_shutdown(void) {
         int r = cuda_status(cudaSetDevice(dev), "cudaSetDevice");
         if (!r) r = cuda_status(cudaStreamSynchronize(p.side), "side stream synchronize");
         if (!r) r = cuda_status(cudaStreamSynchronize(p.side2), "side stream synchronize");
-        for (int i = 0; i < PIPE_MAX_CHUNKS; ++i) {
-            cudaEventDestroy(p.gram_done[i]);
-            cudaEventDestroy(p.cf_fork[i]);
-            cudaEventDestroy(p.cf_join[i]);
-        }
-        cudaEventDestroy(p.inputs_ready);
-        cudaEventDestroy(p.side_done);
-        cudaStreamDestroy(p.side);
-        cudaStreamDestroy(p.side2);
-        p = PipeState();
+        release_pipe(p);
         if (!rc) rc = r;
     }
     if (caller >= 0) {
