@@ -599,9 +599,11 @@ def main():
         xl.xlmimo_channel_gram(arr, U, gram_prec, G)
         ev[1].record(stream)
 
-    # per pipeline piece: gram, beamform, sumrate, closed form, beamform, sumrate, saturation; per step: 2 stats
+    # per pipeline piece: the Gram, the closed form, the saturation interval and the two receivers (each
+    # computes its trials' sum rates); per step: the two batch statistics.  (A Gram split into element
+    # chunks adds a reduction launch; at this batch size every trial is one chunk.)
     pieces = args.chunks if args.chunks else 1
-    launches_per_step = 7 * pieces + 2
+    launches_per_step = 5 * pieces + 2
 
     def timed(gram_prec, steps, warmup, sample_clocks=False):
         for _ in range(warmup):
