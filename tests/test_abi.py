@@ -281,3 +281,15 @@ def test_remaining_entries_validate_on_host(xl):
     assert L.xlmimo_pair_features(ctypes.byref(arr), dummy, 4, 1, -1, None, None, dummy, None, None, None) == 1
     assert L.xlmimo_pair_features(ctypes.byref(arr), dummy, 4, 1, 0, None, None, dummy, None, dummy, None) == 1
     assert b"weights need" in L.xlmimo_last_error()
+
+
+def test_readme_example_uses_the_binding(xl):
+    """Every binding name and workload field the README's Python example uses
+    exists (the calls themselves need a GPU)."""
+    from paper_2503_18118_gb300 import inputs
+    text = open(os.path.join(ROOT, "README.md")).read()
+    src = text.split("```python")[1].split("```")[0]
+    for name in set(re.findall(r"\bxl\.([A-Za-z_0-9]+)", src)):
+        assert hasattr(xl, name), name
+    for name in set(re.findall(r"\bwl\.([A-Za-z_0-9]+)", src)):
+        assert hasattr(inputs.HEADLINE, name), name
