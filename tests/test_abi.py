@@ -293,3 +293,16 @@ def test_readme_example_uses_the_binding(xl):
         assert hasattr(xl, name), name
     for name in set(re.findall(r"\bwl\.([A-Za-z_0-9]+)", src)):
         assert hasattr(inputs.HEADLINE, name), name
+
+
+def test_binding_refuses_host_tensors(xl):
+    """The binding passes device pointers only: host tensors, wrong dtypes and
+    shapes are refused before the library is called."""
+    torch = pytest.importorskip("torch")
+    arr = xl.array(256, 0.01)
+    with pytest.raises(TypeError):
+        xl.xlmimo_channel_gram(arr, torch.zeros((2, 4, 2), dtype=torch.float64))
+    with pytest.raises(TypeError):
+        xl.xlmimo_corr_closed_form(arr, torch.zeros((2, 4, 2), dtype=torch.float32))
+    with pytest.raises(TypeError):
+        xl.xlmimo_saturation(torch.zeros((2, 4, 2), dtype=torch.float64), 0.9, 0.005)
