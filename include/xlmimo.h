@@ -126,7 +126,7 @@ typedef enum { XLMIMO_POWER_ABS = 0, XLMIMO_POWER_RXSNR = 1 } xlmimo_power_mode;
 
 /* Array geometry and channel model (Sec. II-A, II-B). */
 typedef struct {
-    int64_t n_ant;      /* N >= 1 */
+    int64_t n_ant;      /* 1 <= N <= 2^40 */
     double wavelength;  /* lambda > 0 [m] */
     double spacing;     /* element spacing > 0 [m]; the paper uses lambda / 2 */
     double beta0;       /* channel gain constant of PNUSW / UPW (the paper sets 1) */
@@ -141,9 +141,11 @@ typedef struct {
  *   users : [B][K][2] doubles (device)
  *   gram  : [B][K][K] complex doubles (device, written)
  *   prec  : xlmimo_prec
- * Needs device workspace only when B is too small to fill the GPU (the
- * element range is then split and the partial sums reduced in a fixed order);
- * that workspace is stream-ordered memory of the current device. */
+ * Needs device workspace only when the element range is split, the partial
+ * sums then reduced in a fixed order: when B is too small to fill the GPU,
+ * and on the tensor cores for arrays longer than 2^36 elements; that
+ * workspace (B x chunks x K x K complex doubles) is stream-ordered memory of
+ * the current device. */
 int xlmimo_channel_gram(const xlmimo_array* arr, const double* users, int K, int B, int prec,
                         double* gram, void* stream);
 
