@@ -477,7 +477,10 @@ int xlmimo_batch_run(xlmimo_batch_plan plan, const double* users, const double* 
  * on the narrow tiling, the others on the wide one) and pack (1: items share
  * CTAs, 0: one per CTA).  Waits for the device to finish pending work
  * (runs may still read the plan's tables), then rebuilds the tables;
- * SYNCHRONOUS on `stream`.  The plan then reports tuned = 0. */
+ * SYNCHRONOUS on `stream`.  The plan then reports tuned = 0.  If the wait
+ * fails the plan is left as it was; if the rebuild fails (XLMIMO_ENOMEM, ...)
+ * the plan keeps no tables and xlmimo_batch_run refuses it (XLMIMO_EINVAL)
+ * until a later call succeeds. */
 int xlmimo_batch_plan_set_tiling(xlmimo_batch_plan plan, int64_t chunk, int mode, int narrow_kmax, int pack,
                                  void* stream);
 

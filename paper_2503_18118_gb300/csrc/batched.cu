@@ -26,6 +26,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <new>
 #include <vector>
 
 #include "gram_engine.cuh"
@@ -277,7 +278,7 @@ static void free_tables(BatchPlan* p) {
 
 // Host tables for one element chunk: items longest first, split instances'
 // partial offsets, receiver buckets.
-static int build_tables(BatchPlan* p, int64_t chunk, cudaStream_t st) {
+static int build_tables_impl(BatchPlan* p, int64_t chunk, cudaStream_t st) {
     free_tables(p);
     std::vector<DevInst> di(p->count);
     std::vector<DevItem> items;
@@ -410,6 +411,19 @@ static int build_tables(BatchPlan* p, int64_t chunk, cudaStream_t st) {
     return rc;
 }
 
+// The host tables are built before any device table is allocated, so a host
+// allocation failure leaves the plan without tables (which run refuses) and
+// is reported instead of unwinding through the C interface.
+static int build_tables(BatchPlan* p, int64_t chunk, cudaStream_t st) {
+    try {
+        return build_tables_impl(p, chunk, st);
+    } catch (const std::bad_alloc&) {
+        free_tables(p);
+        set_error("plan tables: host memory exhausted");
+        return XLMIMO_ENOMEM;
+    }
+}
+
 using RuKernel = void (*)(Geom, GenParams, const DevInst*, int, const double*, RgUser*, int*);
 
 template <int MODEL>
@@ -538,13 +552,20 @@ extern "C" int xlmimo_batch_plan_create(const xlmimo_array* geo, const xlmimo_in
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
     if (major != 10 || minor != 3) { set_error("batched plans need an sm_103 device (tcgen05)"); return XLMIMO_EUNSUPPORTED; }
-    xlmimo_batch_plan_st* h = new xlmimo_batch_plan_st;
+    xlmimo_batch_plan_st* h = new (std::nothrow) xlmimo_batch_plan_st;
+    if (!h) { set_error("plan: host memory exhausted"); return XLMIMO_ENOMEM; }
     BatchPlan* p = &h->p;
     p->g = g;
     p->prec = prec;
     p->count = count;
     p->users_total = users_total;
-    p->host.assign(insts, insts + count);
+    try {
+        p->host.assign(insts, insts + count);
+    } catch (const std::bad_alloc&) {
+        delete h;
+        set_error("plan: host memory exhausted");
+        return XLMIMO_ENOMEM;
+    }
     cudaStream_t st = as_stream(stream);
     // element chunk per work item (the accumulator's periodic drain keeps
     // any chunk length accurate; the chunk trades load balance against
@@ -629,6 +650,7 @@ extern "C" int xlmimo_batch_run(xlmimo_batch_plan plan, const double* users, con
     }
     if (power_mode != XLMIMO_POWER_ABS && power_mode != XLMIMO_POWER_RXSNR) { set_error("unknown power mode"); return XLMIMO_EINVAL; }
     BatchPlan* p = &plan->p;
+    if (!p->d_inst) { set_error("the plan has no tables: its last xlmimo_batch_plan_set_tiling failed"); return XLMIMO_EINVAL; }
     cudaStream_t st = as_stream(stream);
     int rc = run_gram(p, users, gram, st);
     if (rc || gram_only) return rc;
@@ -657,11 +679,12 @@ extern "C" int xlmimo_batch_plan_set_tiling(xlmimo_batch_plan plan, int64_t chun
     BatchPlan* p = &plan->p;
     // runs in flight may still read the tables that are rebuilt
     int rc = cuda_status(cudaDeviceSynchronize(), "tiling");
+    if (rc) return rc;  // the plan is left as it was
     p->narrow_kmax = narrow_kmax;
     p->pack = pack;
     p->mode = mode;
     p->tuned = 0;
-    if (!rc) rc = build_tables(p, chunk, as_stream(stream));
+    rc = build_tables(p, chunk, as_stream(stream));
     if (!rc) rc = prepare_gram(p);
     return rc;
 }
