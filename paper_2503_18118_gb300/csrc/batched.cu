@@ -22,6 +22,7 @@
 // in chunk order.  The receivers run one CTA per instance, launched per user
 // count bucket (K up to 16, 32, 40, 48, 56, 64) so that shared memory, and
 // with it the CTAs per SM, is sized for the bucket.
+#include <limits.h>
 #include <math.h>
 #include <string.h>
 
@@ -280,6 +281,14 @@ static void free_tables(BatchPlan* p) {
 // partial offsets, receiver buckets.
 static int build_tables_impl(BatchPlan* p, int64_t chunk, cudaStream_t st) {
     free_tables(p);
+    // work items, chunk indices and CTA counts are 32-bit
+    long long total_items = 0;
+    for (int i = 0; i < p->count; ++i) total_items += (p->host[i].n_ant + chunk - 1) / chunk;
+    if (total_items > INT_MAX) {
+        set_error("%lld work items at an element chunk of %lld exceed 2^31 - 1: take a longer chunk", total_items,
+                  (long long)chunk);
+        return XLMIMO_EINVAL;
+    }
     std::vector<DevInst> di(p->count);
     std::vector<DevItem> items;
     std::vector<int> small, large, split, buckets[6];
