@@ -129,3 +129,28 @@ def test_planar_wave_gram_past_2_31_elements(xl, orc):
     assert err <= tol, (err, tol)
     assert np.allclose(np.real(np.einsum("...ii->...i", G)), N_BIG / np.hypot(u[..., 0], u[..., 1]) ** 2,
                        rtol=SUM_TOL_F64, atol=0)
+
+
+def test_closed_forms_match_oracle_sums_at_moderate_n(orc):
+    """The two expected values the large-array tests use, against the oracle's
+    explicit inner products where those are cheap (N = 100,001): the digamma
+    diagonal for users placed the same way (beside an element, 3.3 to 17 m from
+    the array), and the Dirichlet form for users whose sin(theta) differ by
+    fractions of 1/N (every entry a coherent sum)."""
+    n = 100_001
+    xs = np.array([3.3, 17.0, 4.2, 9.0])
+    idx = 70_000 + np.array([0.37, 0.81, 1000.25, -2500.5])
+    u = np.stack([xs, (idx - (n - 1) / 2) * D], -1)[None]
+    G = orc.gram(orc.FSPL, n, LAM, D, 1.0, u)[0]
+    want = np.array([fspl_diagonal(x, y, n, LAM, D) for x, y in u[0]])
+    assert np.allclose(np.real(np.diag(G)), want, rtol=1e-12, atol=0)
+    s = math.sin(0.3) + np.array([0.0, 0.6, 1.7, 3.1]) / n
+    r = np.array([5.0, 12.0, 20.0, 7.0])
+    v = np.stack([r * np.sqrt(1 - s * s), r * s], -1)[None]
+    Gp = orc.gram(orc.UPW, n, LAM, D, 1.0, v)
+    Rp = orc.closed_form(orc.UPW, n, LAM, D, 1.0, v)
+    assert np.min(np.abs(Rp[0]) * np.outer(r, r)) > 0.1 * n
+    d = np.sqrt(np.abs(np.einsum("...ii->...i", Rp)))
+    rmax = float(r.max()) + n * D / 2
+    assert float(np.max(np.abs(Gp - Rp) / (d[..., :, None] * d[..., None, :]))) <= \
+        8 * np.finfo(float).eps * (1.0 + 2 * math.pi * rmax / LAM) + 4 * n * 2.0 ** -53
