@@ -54,6 +54,8 @@ def parse():
                     help="run one extra section alone (no headline step) and print its JSON; for profiling")
     ap.add_argument("--ragged-count", type=int, default=1 << 14, help="instances of the ragged section")
     ap.add_argument("--no-ragged-tune", action="store_true", help="ragged section with the default tiling (no autotune)")
+    ap.add_argument("--ref-seconds", type=float, default=90.0,
+                    help="--impl reference: seconds of oracle work the warm-up and timed steps share")
     ap.add_argument("--surrogate-train-steps", type=int, default=None,
                     help="Adam steps of the surrogate section (default: the workload's 8000)")
     return ap.parse_args()
@@ -161,8 +163,7 @@ def reference_arm(args, wl):
     t0 = time.perf_counter()
     oracle_pipeline(oracle, wl, users[:16])
     per = (time.perf_counter() - t0) / 16
-    total_budget = 90.0
-    n = int(max(8, min(4096, total_budget / max(args.steps + args.warmup, 1) / max(per, 1e-9))))
+    n = int(max(8, min(4096, args.ref_seconds / max(args.steps + args.warmup, 1) / max(per, 1e-9))))
     for _ in range(args.warmup):
         oracle_pipeline(oracle, wl, users[:n])
     t0 = time.perf_counter()
