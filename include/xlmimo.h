@@ -21,7 +21,9 @@
  *     enqueued; the reason is in xlmimo_last_error() (thread-local).
  *     XLMIMO_ECUDA reports a CUDA launch or runtime error.  No C++ exception
  *     crosses this interface.
- *   - B == 0 is a valid empty batch: nothing is enqueued, XLMIMO_OK.
+ *   - B == 0 is a valid empty batch: nothing is enqueued, XLMIMO_OK (except
+ *     that xlmimo_sumrate writes the empty batch's statistics {0, 0, 0} to a
+ *     given `stats`).
  *   - Complex numbers are interleaved (re, im) doubles.  A Gram matrix batch
  *     is [B][K][K] complex, row-major, G[b][i][j] = h_i^H h_j (conjugate on
  *     the row user, as rho_ij of Sec. III), both triangles written.
