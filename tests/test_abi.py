@@ -306,3 +306,16 @@ def test_binding_refuses_host_tensors(xl):
         xl.xlmimo_corr_closed_form(arr, torch.zeros((2, 4, 2), dtype=torch.float32))
     with pytest.raises(TypeError):
         xl.xlmimo_saturation(torch.zeros((2, 4, 2), dtype=torch.float64), 0.9, 0.005)
+
+
+def test_build_tracks_every_source_and_header():
+    """The library is rebuilt when any kernel source, kernel header or the C
+    interface header changes (its staleness check covers all of them)."""
+    import glob
+    from paper_2503_18118_gb300 import build as b
+    deps = set(b._deps())
+    csrc = os.path.join(ROOT, "paper_2503_18118_gb300", "csrc")
+    want = set(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")) +
+               glob.glob(os.path.join(ROOT, "include", "*.h")))
+    assert want and want <= deps
+    assert set(b._sources()) == set(glob.glob(os.path.join(csrc, "*.cu")))
