@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--chunks", type=int, default=0, help="pipeline pieces per step (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-baseline", action="store_true")
-    ap.add_argument("--source-hash", metavar="KERNEL", help="print the source hash a profile summary records, and exit")
+    ap.add_argument("--source-hash", metavar="KERNEL", choices=sorted(PROFILE_SOURCES),
+                    help="print the source hash a profile summary records, and exit")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the precision table, the ragged batch, the sweep and the surrogate")
     ap.add_argument("--only", choices=["ragged", "appendix_a", "sweep", "surrogate", "ura"],
@@ -190,15 +191,12 @@ def reference_arm(args, wl):
 # sources whose bytes the committed ncu summary of each kernel was taken on
 PROFILE_SOURCES = {
     "gram_tc_kernel": ["gram_tc.cu", "gram_engine.cuh", "gen_tc.cuh", "tc_common.cuh", "chan_gen.cuh", "common.cuh"],
-    "gram_f32_kernel": ["gram_simt.cu", "chan_gen.cuh", "common.cuh"],
-    "gram_f64_kernel": ["gram_simt.cu", "chan_gen.cuh", "common.cuh"],
     "mlp_infer_tc_kernel": ["mlp_tc.cu", "mlp_common.cuh", "tc_common.cuh", "common.cuh"],
     "gram_hilo_kernel": ["bounds.cu", "gram_hilo_tc.cuh", "gen_tc.cuh", "tc_common.cuh", "chan_gen.cuh", "common.cuh"],
     "gram_tc_packed_kernel": ["batched.cu", "gram_engine.cuh", "gen_tc.cuh", "tc_common.cuh", "chan_gen.cuh",
                               "common.cuh"],
 }
-PROFILE_OF_KERNEL = {"gram_tc_kernel": "gram_tc_kernel_headline.md", "gram_f32_kernel": "gram_f32_kernel_headline.md",
-                     "gram_f64_kernel": "gram_f64_kernel_headline.md",
+PROFILE_OF_KERNEL = {"gram_tc_kernel": "gram_tc_kernel_headline.md",
                      "mlp_infer_tc_kernel": "mlp_infer_tc_kernel_surrogate.md",
                      "gram_tc_packed_kernel": "gram_tc_packed_kernel_ragged.md",
                      "gram_hilo_kernel": "bounds_appendix_a.md"}
@@ -217,7 +215,10 @@ def traffic_from_profile(kernel, units=None):
     """DRAM bytes per full launch recorded by the committed ncu summary of the
     kernel, valid only while the kernel's sources are unchanged.  A summary
     taken on a smaller case records its bytes per unit (dram_bytes_per_unit);
-    the full launch's is that times `units`."""
+    the full launch's is that times `units`.  A kernel without a committed
+    summary has no traffic figure."""
+    if kernel not in PROFILE_OF_KERNEL:
+        return None
     prof = os.path.join(ROOT, "profiles", PROFILE_OF_KERNEL[kernel])
     if not os.path.exists(prof):
         return None

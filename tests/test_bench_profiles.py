@@ -12,10 +12,10 @@ import bench  # noqa: E402
 
 
 def test_profile_summaries_parse():
+    assert set(bench.PROFILE_OF_KERNEL) == set(bench.PROFILE_SOURCES)
     for kernel, name in bench.PROFILE_OF_KERNEL.items():
         path = os.path.join(ROOT, "profiles", name)
-        if not os.path.exists(path):
-            continue
+        assert os.path.exists(path), name
         text = open(path).read()
         m = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
         assert m, name
@@ -32,3 +32,8 @@ def test_source_hash_changes_with_sources():
     h = bench.source_hash("gram_tc_kernel")
     assert re.fullmatch(r"[0-9a-f]{64}", h)
     assert h != bench.source_hash("gram_tc_packed_kernel")
+
+
+def test_kernels_without_a_summary_have_no_traffic():
+    assert bench.traffic_from_profile("gram_f32_kernel") is None
+    assert bench.traffic_from_profile("gram_f64_kernel") is None
